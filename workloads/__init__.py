@@ -1,0 +1,137 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only draws numbers and lists shapes.  It holds none of the
+method's arithmetic (no GEMM, no rounding to a low-precision format, no
+selection rule), so the CUDA path and the oracle can both take their inputs
+from it without sharing any computation.
+
+The paper's matrix-multiply application scales a square size N from 8 to 8192
+(Table 2); its inputs are not published, so every matrix here is drawn from a
+seeded NumPy ``default_rng`` (PCG64) stream.
+
+Workloads (M, N, K):
+
+* ``PARITY_256``: one 256^3 FP32 product, A and B uniform[-1, 1] (seed 1).
+* ``sweep_shapes()``: FP32-accuracy size sweep, square n = 64, 128, ..., 8192
+  (step 64) plus the skinny 4096x4096x64 and 16x4096x4096 (seed 2).
+* precision study: 4096^3, normal(0, 1) (seed 3); ill-scaled variant multiplies
+  column k of A by 10^u, u ~ U(-3, 3) (seed 4).
+* ``batched_problems()``: 512 GEMMs, M, N, K each round(exp(U(ln 32,
+  ln 2048))) (seed 5), dtype f32 or bf16 with probability 1/2.
+* ``heldout_contexts()``: selector test contexts, M, N, K log-uniform
+  integers in [16, 4096], dtype uniform over {f32, bf16, fp8}, tolerance from
+  {1e-5 (f32 only), 1e-3, 1e-1} (seed 12345).
+"""
+import math
+
+import numpy as np
+
+F32, BF16, F8E4M3 = 0, 1, 2
+DTYPE_NAMES = {F32: "f32", BF16: "bf16", F8E4M3: "f8e4m3"}
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def uniform(rows, cols, seed, lo=-1.0, hi=1.0):
+    """float32 (rows, cols) matrix, entries uniform in [lo, hi)."""
+    return rng(seed).uniform(lo, hi, size=(rows, cols)).astype(np.float32)
+
+
+def normal(rows, cols, seed):
+    """float32 (rows, cols) matrix, entries normal(0, 1)."""
+    return rng(seed).standard_normal(size=(rows, cols)).astype(np.float32)
+
+
+def column_scales(cols, seed, decades=3.0):
+    """Per-column factors 10^u, u ~ U(-decades, decades), float32."""
+    u = rng(seed).uniform(-decades, decades, size=cols)
+    return (10.0 ** u).astype(np.float32)
+
+
+def ill_scaled(rows, cols, seed_values, seed_scales):
+    """normal(0,1) matrix whose column k is multiplied by 10^U(-3, 3)."""
+    return (normal(rows, cols, seed_values)
+            * column_scales(cols, seed_scales)[None, :]).astype(np.float32)
+
+
+def integer_matrix(rows, cols, seed, bound=8):
+    """Integers in [-bound, bound] as float32 (exactly representable)."""
+    return rng(seed).integers(-bound, bound + 1, size=(rows, cols)).astype(np.float32)
+
+
+def bf16_input(rows, cols, seed):
+    """bfloat16 input matrix as uint16 bit patterns.
+
+    Drawn as uniform[-1, 1) float32 whose low 16 bits are cleared, so every
+    value is a bfloat16 number; no rounding rule is applied.
+    """
+    x = uniform(rows, cols, seed)
+    return (x.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def fp8_input(rows, cols, seed, max_exponent_field=10):
+    """FP8 E4M3 input matrix as byte codes.
+
+    Random sign, exponent field in [0, max_exponent_field] and fraction bits;
+    exponent fields at most 14 never form the NaN code, so every code is a
+    finite E4M3 number (magnitudes up to 2^(max_exponent_field-7)*1.875).
+    """
+    g = rng(seed)
+    sign = g.integers(0, 2, size=(rows, cols)).astype(np.uint8) << 7
+    expo = g.integers(0, max_exponent_field + 1, size=(rows, cols)).astype(np.uint8) << 3
+    frac = g.integers(0, 8, size=(rows, cols)).astype(np.uint8)
+    return (sign | expo | frac).astype(np.uint8)
+
+
+PARITY_256 = (256, 256, 256)
+
+
+def sweep_shapes(step=64, top=8192):
+    """The FP32-accuracy sweep: squares step..top (step) plus two skinny shapes."""
+    sq = [(n, n, n) for n in range(step, top + 1, step)]
+    return sq + [(4096, 4096, 64), (16, 4096, 4096)]
+
+
+def pow2_sweep_shapes():
+    """Headline subset of the sweep: powers of two 64..8192 plus the skinny shapes."""
+    return [(1 << e,) * 3 for e in range(6, 14)] + [(4096, 4096, 64), (16, 4096, 4096)]
+
+
+def _log_uniform_int(g, lo, hi, size):
+    return np.rint(np.exp(g.uniform(math.log(lo), math.log(hi), size=size))).astype(np.int64)
+
+
+def batched_problems(count=512, seed=5, lo=32, hi=2048):
+    """List of (m, n, k, dtype) for the uneven batched workload."""
+    g = rng(seed)
+    mnk = _log_uniform_int(g, lo, hi, (count, 3))
+    dt = np.where(g.uniform(size=count) < 0.5, F32, BF16)
+    return [(int(a), int(b), int(c), int(d)) for (a, b, c), d in zip(mnk, dt)]
+
+
+def heldout_contexts(count=2000, seed=12345, lo=16, hi=4096):
+    """List of (m, n, k, dtype, tol) held out from selector training."""
+    g = rng(seed)
+    mnk = _log_uniform_int(g, lo, hi, (count, 3))
+    dts = g.integers(0, 3, size=count)
+    out = []
+    for (m, n, k), d in zip(mnk, dts):
+        if d == F32:
+            tol = [1e-5, 1e-3, 1e-1][int(g.integers(0, 3))]
+        else:
+            tol = [1e-3, 1e-1][int(g.integers(0, 2))]
+        out.append((int(m), int(n), int(k), int(d), float(tol)))
+    return out
+
+
+def training_contexts(count, seed=777, lo=16, hi=8192):
+    """Selector training contexts (seed disjoint from the held-out set)."""
+    return heldout_contexts(count=count, seed=seed, lo=lo, hi=hi)
+
+
+def sample_rows(m, count, seed):
+    """Sorted distinct row indices for checking large products row by row."""
+    count = min(count, m)
+    return np.sort(rng(seed).choice(m, size=count, replace=False)).astype(np.int64)
