@@ -1,0 +1,250 @@
+/*
+ * compar.h — C ABI of a variant-selecting dense matrix multiply for one
+ * B300 GPU (sm_103a).
+ *
+ * The idea follows COMPAR (Sec. 2): one component — here the matrix-multiply
+ * interface "mmul" of Sec. 2.1 / Table 2 — is exposed through several
+ * interchangeable implementation variants, and a runtime picks one variant per
+ * call from the call's context (Sec. 2.2, "Runtime System": a task is mapped to
+ * one of its codelets when it runs).  The lifecycle calls keep the names the
+ * paper's pre-compiler generates (compar_init / compar_terminate, Sec. 2.1).
+ *
+ * The component computes
+ *
+ *     C = alpha * op_scale * (A x B) + beta * C
+ *
+ * with A (M x K), B (K x N), C (M x N), all ROW-MAJOR.  In compar_gemm the
+ * matrices are contiguous (lda = K, ldb = N, ldc = N); compar_gemm_batched
+ * takes explicit leading dimensions.  C is always float32.  op_scale is 1
+ * except for FP8 inputs, where it is scale_a * scale_b (per-tensor
+ * dequantisation factors: the real matrix is scale * decoded codes).
+ *
+ * Ownership: A, B, C are DEVICE pointers owned by the caller (for example
+ * PyTorch tensors) unless a function says otherwise.  Everything else
+ * (workspace, tensor maps, CUDA graphs, cost models, timing records) is owned
+ * by the context and released by compar_terminate.
+ *
+ * Semantics: every compute call is asynchronous and stream-ordered on the
+ * given cudaStream_t (passed as void*; NULL = legacy default stream).  Errors
+ * found on the host are returned synchronously; kernel-side failures (a
+ * bounded wait that ran out) are latched in a device error word and returned
+ * by compar_check_device_error.  No call aborts the process.  A context is not
+ * thread-safe: use one context per host thread.
+ *
+ * beta == 0 means C is not read (BLAS convention).
+ */
+#ifndef COMPAR_H_
+#define COMPAR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COMPAR_ABI_VERSION 1
+
+typedef struct compar_ctx* compar_ctx_t;
+
+/* Element type of A and B (the "type" clause of the parameter directive,
+ * Sec. 2.1).  BF16 is passed as uint16 bit patterns, F8E4M3 as bytes (OCP
+ * E4M3: bias 7, max finite 448, no infinities). */
+typedef enum {
+    COMPAR_F32 = 0,
+    COMPAR_BF16 = 1,
+    COMPAR_F8E4M3 = 2
+} compar_dtype_t;
+
+typedef enum {
+    COMPAR_OK = 0,
+    COMPAR_ERR_INVALID = -1,      /* bad argument, null/misaligned pointer   */
+    COMPAR_ERR_UNSUPPORTED = -2,  /* variant cannot run this call           */
+    COMPAR_ERR_CUDA = -3,         /* a CUDA runtime call failed             */
+    COMPAR_ERR_TIMEOUT = -4,      /* a device-side bounded wait ran out     */
+    COMPAR_ERR_IO = -5,           /* selector/record file error             */
+    COMPAR_ERR_NO_VARIANT = -6    /* no eligible variant meets the tolerance */
+} compar_status_t;
+
+/* Stable implementation-variant ids (Table 2 lists the paper's mmul variants
+ * BLAS/OMP/CUDA/CUBLAS; these are their B300 replacements). */
+enum {
+    COMPAR_V_NAIVE = 0,       /* one thread per C element, FP32 FMA         */
+    COMPAR_V_SIMT = 1,        /* shared-memory tiled FP32 SIMT              */
+    COMPAR_V_TC_TF32 = 2,     /* tcgen05 kind::tf32, TMEM FP32 accumulator  */
+    COMPAR_V_TC_BF16 = 3,     /* tcgen05 kind::f16 (bf16 operands)          */
+    COMPAR_V_TC_FP8 = 4,      /* tcgen05 kind::f8f6f4 (E4M3 operands)       */
+    COMPAR_V_SPLIT3 = 5,      /* 3xBF16 split on tcgen05 (FP32 accuracy)    */
+    COMPAR_V_COUNT = 6,
+    COMPAR_V_GROUPED = 6      /* persistent grouped kernel (batched only)   */
+};
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a context on CUDA device `device` (Sec. 2.1, `initialize` directive
+ * -> compar_init()).  Reads COMPAR_* environment variables (COMPAR_FORCE_VARIANT,
+ * COMPAR_SELECTOR = auto|history|mlp, COMPAR_SELECTOR_FILE, COMPAR_LOG,
+ * COMPAR_WAIT_BUDGET_NS).  *out receives the context.  Returns COMPAR_OK,
+ * COMPAR_ERR_INVALID (out == NULL), COMPAR_ERR_UNSUPPORTED (device is not
+ * sm_103) or COMPAR_ERR_CUDA. */
+int compar_init(compar_ctx_t* out, int device);
+
+/* Release the context and everything it owns (Sec. 2.1, `terminate`
+ * directive -> compar_terminate()).  Synchronises the device first.
+ * NULL is accepted and ignored. */
+int compar_terminate(compar_ctx_t ctx);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* compar_status_string(int status);
+
+/* Text of the last host-side error seen by this thread (CUDA call that
+ * failed, injected failure, ...); empty string when none.  Never NULL. */
+const char* compar_last_error(void);
+
+/* ---------------------------------------------------------------- compute */
+
+/* One GEMM call: the interface call of Sec. 2.1 ("mmul") submitted as a task
+ * that the runtime maps to one variant (Sec. 2.2).
+ *   m, n, k   : sizes, each >= 0 (m == 0 or n == 0: nothing to do;
+ *               k == 0: C = beta * C).
+ *   dtype     : element type of A and B.
+ *   tol       : relative Frobenius error asked for, measured against the
+ *               exact product of the inputs as given; tol <= 0 means the
+ *               default (1e-5 for F32, "best available" for BF16/F8).
+ *   A, B      : device pointers, row-major contiguous (lda = k, ldb = n).
+ *   C         : device float32, row-major contiguous (ldc = n).
+ *   stream    : cudaStream_t.
+ * Variant choice: compar_force_variant > decision cache > learned MLP cost
+ * model (when confident) > history-table model.  Returns COMPAR_OK,
+ * COMPAR_ERR_INVALID, COMPAR_ERR_NO_VARIANT (nothing meets tol) or
+ * COMPAR_ERR_CUDA.  alpha/beta and FP8 scales come from compar_set_scalars /
+ * compar_set_fp8_scales (the listed signature has no slot for them). */
+int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
+                compar_dtype_t dtype, double tol, const void* A,
+                const void* B, float* C, void* stream);
+
+/* One problem of a batched call.  Leading dimensions are in elements and must
+ * be >= the row length (lda >= k, ldb >= n, ldc >= n). */
+typedef struct {
+    int64_t m, n, k;
+    int64_t lda, ldb, ldc;
+    compar_dtype_t dtype;
+    const void* A;
+    const void* B;
+    float* C;
+    float alpha, beta;
+    float scale_a, scale_b;   /* FP8 dequantisation factors, else ignored */
+} compar_problem_t;
+
+/* Many independent GEMMs of uneven sizes in one call.  `probs` is a HOST
+ * array of `count` problems and is copied before return.  F32 problems run at
+ * FP32 accuracy when tol <= 1e-5 (3xBF16 mode), else on TF32; BF16 problems
+ * on bf16 tensor cores.  The selector picks between one persistent grouped
+ * launch captured in a CUDA graph (cached per batch signature) and one launch
+ * per problem.  Returns as compar_gemm. */
+int compar_gemm_batched(compar_ctx_t ctx, int count,
+                        const compar_problem_t* probs, double tol,
+                        void* stream);
+
+/* ---------------------------------------------------------------- control */
+
+/* Force every following call onto `variant_id` (one of COMPAR_V_*), or clear
+ * with -1 (the paper's STARPU_NCUDA / STARPU_NCPU switches, Sec. 3.2, pinned
+ * whole architectures; this pins one variant).  A forced variant that cannot
+ * run a call makes that call return COMPAR_ERR_UNSUPPORTED. */
+int compar_force_variant(compar_ctx_t ctx, int variant_id);
+
+/* alpha and beta used by compar_gemm (defaults 1 and 0). */
+int compar_set_scalars(compar_ctx_t ctx, float alpha, float beta);
+
+/* FP8 dequantisation factors used by compar_gemm for F8E4M3 inputs (default
+ * 1, 1).  Must be finite and > 0. */
+int compar_set_fp8_scales(compar_ctx_t ctx, float scale_a, float scale_b);
+
+/* Selection policy: 0 = auto (MLP when confident, else history table),
+ * 1 = history table only, 2 = MLP only. */
+int compar_set_selector_mode(compar_ctx_t ctx, int mode);
+
+/* Variant chosen by the most recent compar_gemm call (-1 before any). */
+int compar_last_variant(compar_ctx_t ctx);
+
+/* Number of variants and their names (static strings; NULL if out of range). */
+int compar_variant_count(void);
+const char* compar_variant_name(int variant_id);
+
+/* Whether variant `variant_id` can run (m, n, k, dtype) at all (dtype,
+ * alignment and shape rules; the tolerance is not considered).  1 / 0, or a
+ * negative status. */
+int compar_variant_supported(compar_ctx_t ctx, int variant_id, int64_t m,
+                             int64_t n, int64_t k, compar_dtype_t dtype);
+
+/* Drop every cached selection decision. */
+int compar_clear_decisions(compar_ctx_t ctx);
+
+/* ---------------------------------------------------------------- models */
+
+/* Load a selector file (history table, error model, MLP weights, feature
+ * normaliser, grouped tile choice).  On any error (missing file, bad magic,
+ * version, size or checksum) the models already loaded are kept and
+ * COMPAR_ERR_IO is returned. */
+int compar_selector_load(compar_ctx_t ctx, const char* path);
+
+/* Write the current selector state to `path` (binary, versioned, checksummed). */
+int compar_selector_save(compar_ctx_t ctx, const char* path);
+
+/* ---------------------------------------------------------------- timing */
+
+/* Time variant `variant_id` on one call with CUDA events on `stream`:
+ * `warmup` untimed runs, then `reps` timed runs; *median_ms receives the
+ * median.  Adds one timing record per timed run when recording is on, and one
+ * observation to the history table.  Synchronises the stream. */
+int compar_measure(compar_ctx_t ctx, int variant_id, int64_t m, int64_t n,
+                   int64_t k, compar_dtype_t dtype, double tol, const void* A,
+                   const void* B, float* C, int warmup, int reps,
+                   void* stream, float* median_ms);
+
+/* One timing record: the call's context and the measured time (and, when a
+ * residual check ran, the relative error; -1 otherwise). */
+typedef struct {
+    int64_t m, n, k;
+    int32_t dtype;
+    int32_t variant;
+    int32_t batch;
+    float tol;
+    float time_ms;
+    float rel_err;
+} compar_record_t;
+
+/* Recording of timing records (off by default). */
+int compar_record_enable(compar_ctx_t ctx, int on);
+/* Number of records held (ring buffer of 1<<20 records). */
+int64_t compar_record_count(compar_ctx_t ctx);
+/* Copy up to `max` records, oldest first, into host array `out`;
+ * returns the number copied or a negative status. */
+int64_t compar_record_get(compar_ctx_t ctx, compar_record_t* out, int64_t max);
+/* Append externally measured records (host array). */
+int compar_record_add(compar_ctx_t ctx, const compar_record_t* recs,
+                      int64_t count);
+int compar_record_clear(compar_ctx_t ctx);
+
+/* ---------------------------------------------------------------- errors */
+
+/* Read and clear the device error word after synchronising `stream`.
+ * Returns COMPAR_OK, COMPAR_ERR_TIMEOUT (a bounded wait in a kernel ran out;
+ * the kernel returned early and C is undefined) or COMPAR_ERR_CUDA. */
+int compar_check_device_error(compar_ctx_t ctx, void* stream);
+
+/* Budget of every device-side bounded wait, in nanoseconds of %globaltimer
+ * (default 2e9).  Values below 1000 are raised to 1000. */
+int compar_set_wait_budget(compar_ctx_t ctx, uint64_t ns);
+
+/* Launch one small kernel whose wait on an mbarrier can never complete, so
+ * the bounded wait runs out after the wait budget; the kernel records
+ * COMPAR_ERR_TIMEOUT in the device error word and returns.  Used to test the
+ * timeout path without faulting or hanging the GPU.  Asynchronous. */
+int compar_selftest_timeout(compar_ctx_t ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COMPAR_H_ */

@@ -1,0 +1,277 @@
+"""Python binding of libcompar — argument marshalling only.
+
+Every function named ``compar_*`` here has the C signature of the same name
+in ``include/compar.h`` and forwards to it through ctypes; nothing of the
+GEMM, the selection or the cost models runs in Python.  :class:`Context`
+adds a convenience layer that takes PyTorch tensors (device memory and
+streams come from PyTorch) and raises :class:`ComparError` on a negative
+status.
+
+The shared library is built in-tree by :func:`build` (nvcc, sm_103a).  There
+is no fallback: importing this package without ``libcompar.so`` raises.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcompar.so")
+
+# dtypes / statuses / variant ids (values of include/compar.h)
+F32, BF16, F8E4M3 = 0, 1, 2
+OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_IO, ERR_NO_VARIANT = 0, -1, -2, -3, -4, -5, -6
+V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3, V_GROUPED = 0, 1, 2, 3, 4, 5, 6
+NUM_VARIANTS = 6
+VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16"]
+
+
+class ComparError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {compar_status_string(status)} ({status}) {compar_last_error()}")
+
+
+class compar_problem_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("dtype", ctypes.c_int), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("scale_a", ctypes.c_float), ("scale_b", ctypes.c_float)]
+
+
+class compar_record_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("variant", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("tol", ctypes.c_float), ("time_ms", ctypes.c_float), ("rel_err", ctypes.c_float)]
+
+
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+_d = ctypes.c_double
+_f = ctypes.c_float
+_fp = ctypes.POINTER(ctypes.c_float)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "compar_init": (_i, [ctypes.POINTER(_vp), _i]),
+    "compar_terminate": (_i, [_vp]),
+    "compar_status_string": (ctypes.c_char_p, [_i]),
+    "compar_last_error": (ctypes.c_char_p, []),
+    "compar_gemm": (_i, [_vp, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _vp]),
+    "compar_gemm_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp]),
+    "compar_force_variant": (_i, [_vp, _i]),
+    "compar_set_scalars": (_i, [_vp, _f, _f]),
+    "compar_set_fp8_scales": (_i, [_vp, _f, _f]),
+    "compar_set_selector_mode": (_i, [_vp, _i]),
+    "compar_last_variant": (_i, [_vp]),
+    "compar_variant_count": (_i, []),
+    "compar_variant_name": (ctypes.c_char_p, [_i]),
+    "compar_variant_supported": (_i, [_vp, _i, _i64, _i64, _i64, _i]),
+    "compar_clear_decisions": (_i, [_vp]),
+    "compar_selector_load": (_i, [_vp, ctypes.c_char_p]),
+    "compar_selector_save": (_i, [_vp, ctypes.c_char_p]),
+    "compar_measure": (_i, [_vp, _i, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _i, _i, _vp, _fp]),
+    "compar_record_enable": (_i, [_vp, _i]),
+    "compar_record_count": (_i64, [_vp]),
+    "compar_record_get": (_i64, [_vp, ctypes.POINTER(compar_record_t), _i64]),
+    "compar_record_add": (_i, [_vp, ctypes.POINTER(compar_record_t), _i64]),
+    "compar_record_clear": (_i, [_vp]),
+    "compar_check_device_error": (_i, [_vp, _vp]),
+    "compar_set_wait_budget": (_i, [_vp, _u64]),
+    "compar_selftest_timeout": (_i, [_vp, _vp]),
+}
+
+_lib = None
+
+
+def build_library(force=False, verbose=False):
+    """Compile libcompar.so in-tree (nvcc, sm_103a) and load it."""
+    import importlib
+    importlib.import_module(__name__ + ".build").build(force=force, verbose=verbose)
+    return load(reload=True)
+
+
+def _missing(name):
+    def call(*args, **kwargs):
+        raise ImportError(f"{name}: libcompar.so is not built ({LIB_PATH}); run "
+                          "paper_2311_03543_b300.build_library() first")
+    return call
+
+
+def load(reload=False):
+    """Load libcompar.so and bind every C-ABI function; raises if it is missing."""
+    global _lib
+    if _lib is not None and not reload:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcompar.so is not built ({LIB_PATH}); run "
+                          "paper_2311_03543_b300.build_library() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+        globals()[name] = fn
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(SIGNATURES)
+
+
+# Bind at import when the library is present; otherwise every compar_* call
+# raises ImportError (there is no fallback implementation).
+for _name in SIGNATURES:
+    globals()[_name] = _missing(_name)
+if os.path.exists(LIB_PATH):
+    load()
+
+
+def _status(rc, what):
+    if rc < 0:
+        raise ComparError(rc, what)
+    return rc
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def torch_dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    if t.dtype in (torch.uint8, torch.float8_e4m3fn):
+        return F8E4M3
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Context:
+    """A libcompar context bound to one CUDA device (tensor-level API)."""
+
+    def __init__(self, device=0):
+        load()
+        h = ctypes.c_void_p()
+        _status(compar_init(ctypes.byref(h), device), "compar_init")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            compar_terminate(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- compute -----------------------------------------------------------
+    def gemm(self, A, B, C, tol=0.0, stream=None, dtype=None):
+        """C = alpha*A@B + beta*C on the context's scalars; A, B, C CUDA tensors."""
+        m, k = A.shape
+        k2, n = B.shape
+        if k != k2 or tuple(C.shape) != (m, n):
+            raise ValueError("shape mismatch")
+        for t in (A, B, C):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+        dt = torch_dtype_code(A) if dtype is None else dtype
+        rc = compar_gemm(self.handle, m, n, k, dt, float(tol), A.data_ptr(), B.data_ptr(),
+                         C.data_ptr(), _stream_handle(stream))
+        return _status(rc, "compar_gemm")
+
+    def gemm_ptr(self, m, n, k, dtype, tol, a_ptr, b_ptr, c_ptr, stream_handle):
+        return compar_gemm(self.handle, m, n, k, dtype, float(tol), a_ptr, b_ptr, c_ptr,
+                           stream_handle)
+
+    def gemm_batched(self, problems, tol=0.0, stream=None):
+        """problems: list of dicts with keys m n k lda ldb ldc dtype A B C [alpha beta scale_a scale_b]."""
+        arr = (compar_problem_t * len(problems))()
+        for i, p in enumerate(problems):
+            arr[i] = compar_problem_t(p["m"], p["n"], p["k"], p["lda"], p["ldb"], p["ldc"],
+                                      p["dtype"], p["A"], p["B"], p["C"], p.get("alpha", 1.0),
+                                      p.get("beta", 0.0), p.get("scale_a", 1.0),
+                                      p.get("scale_b", 1.0))
+        return _status(compar_gemm_batched(self.handle, len(problems), arr, float(tol),
+                                           _stream_handle(stream)), "compar_gemm_batched")
+
+    def measure(self, variant, A, B, C, tol=0.0, warmup=3, reps=10, stream=None, dtype=None):
+        """Median time (ms) of one variant on this call, CUDA events on `stream`."""
+        m, k = A.shape
+        n = B.shape[1]
+        dt = torch_dtype_code(A) if dtype is None else dtype
+        out = ctypes.c_float()
+        _status(compar_measure(self.handle, variant, m, n, k, dt, float(tol), A.data_ptr(),
+                               B.data_ptr(), C.data_ptr(), warmup, reps, _stream_handle(stream),
+                               ctypes.byref(out)), "compar_measure")
+        return out.value
+
+    # -- control -----------------------------------------------------------
+    def force_variant(self, v):
+        return _status(compar_force_variant(self.handle, -1 if v is None else v), "force_variant")
+
+    def set_scalars(self, alpha, beta):
+        return _status(compar_set_scalars(self.handle, alpha, beta), "set_scalars")
+
+    def set_fp8_scales(self, sa, sb):
+        return _status(compar_set_fp8_scales(self.handle, sa, sb), "set_fp8_scales")
+
+    def set_selector_mode(self, mode):
+        return _status(compar_set_selector_mode(self.handle, mode), "set_selector_mode")
+
+    def last_variant(self):
+        return compar_last_variant(self.handle)
+
+    def supported(self, v, m, n, k, dtype):
+        return _status(compar_variant_supported(self.handle, v, m, n, k, dtype), "supported") == 1
+
+    def clear_decisions(self):
+        return _status(compar_clear_decisions(self.handle), "clear_decisions")
+
+    def selector_load(self, path):
+        return _status(compar_selector_load(self.handle, os.fsencode(path)), "selector_load")
+
+    def selector_save(self, path):
+        return _status(compar_selector_save(self.handle, os.fsencode(path)), "selector_save")
+
+    # -- records / errors ----------------------------------------------------
+    def record_enable(self, on=True):
+        return _status(compar_record_enable(self.handle, 1 if on else 0), "record_enable")
+
+    def records(self):
+        n = _status(compar_record_count(self.handle), "record_count")
+        buf = (compar_record_t * max(n, 1))()
+        got = _status(compar_record_get(self.handle, buf, n), "record_get")
+        return [buf[i] for i in range(got)]
+
+    def record_add(self, recs):
+        arr = (compar_record_t * len(recs))(*recs)
+        return _status(compar_record_add(self.handle, arr, len(recs)), "record_add")
+
+    def record_clear(self):
+        return _status(compar_record_clear(self.handle), "record_clear")
+
+    def check_device_error(self, stream=None):
+        return compar_check_device_error(self.handle, _stream_handle(stream))
+
+    def set_wait_budget(self, ns):
+        return _status(compar_set_wait_budget(self.handle, int(ns)), "set_wait_budget")
+
+    def selftest_timeout(self, stream=None):
+        return _status(compar_selftest_timeout(self.handle, _stream_handle(stream)),
+                       "selftest_timeout")

@@ -1,0 +1,580 @@
+// The C ABI (include/compar.h): lifecycle, per-call variant selection and
+// dispatch, forced variants, timing, records, selector files.
+//
+// Selection order for one call (Sec. 2.2: a task is mapped to one codelet of
+// its set at run time; Sec. 3.2: the environment can pin the choice):
+//   forced variant > decision cache > MLP cost model (when confident)
+//   > history table > roofline prior,
+// always restricted to the variants that can run the call and whose error
+// model meets the tolerance.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <string>
+
+#include "runtime.h"
+
+namespace compar {
+
+// ------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+std::string last_error_text() { return g_last_error; }
+
+int Workspace::ensure(size_t need, cudaStream_t s) {
+  if (need <= bytes) return COMPAR_OK;
+  size_t grow = std::max(need, bytes + bytes / 2);
+  grow = (grow + (1 << 20) - 1) & ~static_cast<size_t>((1 << 20) - 1);
+  if (ptr) COMPAR_CUDA_TRY(cudaFreeAsync(ptr, s));
+  ptr = nullptr;
+  bytes = 0;
+  COMPAR_CUDA_TRY(cudaMallocAsync(&ptr, grow, s));
+  bytes = grow;
+  return COMPAR_OK;
+}
+
+void Workspace::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",
+                                      "tc-bf16",   "tc-fp8",   "split-3xbf16",
+                                      "grouped"};
+
+static double default_tol(double tol) { return tol > 0 ? tol : 1e-5; }
+
+static int tol_class(double tol) { return static_cast<int>(std::floor(2.0 * std::log10(tol))); }
+
+bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
+  (void)ctx;
+  if (c.m > INT32_MAX || c.n > INT32_MAX || c.k > INT32_MAX) return false;
+  switch (v) {
+    case COMPAR_V_NAIVE:
+      return (c.m + 15) / 16 <= 65535;
+    case COMPAR_V_SIMT:
+      return (c.m + 31) / 32 <= 65535;
+    case COMPAR_V_TC_TF32:
+    case COMPAR_V_TC_BF16:
+    case COMPAR_V_TC_FP8:
+    case COMPAR_V_SPLIT3:
+      return tc_supported(v, c);
+    default:
+      return false;
+  }
+}
+
+static int launch_variant(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
+  if (v == ctx->test_fail_variant) {
+    g_last_error = "injected failure (COMPAR_TEST_FAIL_VARIANT)";
+    return COMPAR_ERR_CUDA;
+  }
+  switch (v) {
+    case COMPAR_V_NAIVE: return launch_naive(c, s);
+    case COMPAR_V_SIMT: return launch_simt(c, ctx->ws, ctx->num_sms, s);
+    case COMPAR_V_TC_TF32:
+    case COMPAR_V_TC_BF16:
+    case COMPAR_V_TC_FP8:
+    case COMPAR_V_SPLIT3: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
+    default: return COMPAR_ERR_UNSUPPORTED;
+  }
+}
+
+// Eligible variants for a call: runnable, not quarantined, error model within tol.
+static uint32_t eligible_mask(const compar_ctx* ctx, const GemmCall& c) {
+  uint32_t mask = 0;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (ctx->quarantined[v] || !variant_supported(ctx, v, c)) continue;
+    if (ctx->err.predict(v, c.dtype, c.k) * ctx->err.margin > c.tol) continue;
+    mask |= 1u << v;
+  }
+  return mask;
+}
+
+// MLP choice; returns -1 when the model is untrained or not confident.
+static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* pred_ms) {
+  const MlpModel& mm = ctx->mlp;
+  if (!mm.trained) return -1;
+  auto x = make_features(c.m, c.n, c.k, c.dtype, c.tol, c.batch);
+  for (int i = 0; i < kNumFeatures; ++i) {  // outside the training box -> not confident
+    const float span = mm.feat_max[i] - mm.feat_min[i];
+    if (x[i] < mm.feat_min[i] - mm.box_slack * span - 1e-6f ||
+        x[i] > mm.feat_max[i] + mm.box_slack * span + 1e-6f)
+      return -1;
+  }
+  float out[kEnsemble * kOutputs];
+  if (mlp_predict(ctx, x.data(), 1, out) != COMPAR_OK) return -1;
+  int best = -1;
+  float best_t = INFINITY, best_std = 0;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (!(mask & (1u << v))) continue;
+    float mean_t = 0, mean_e = 0;
+    for (int e = 0; e < kEnsemble; ++e) {
+      mean_t += out[e * kOutputs + v];
+      mean_e += out[e * kOutputs + kNumVariants + v];
+    }
+    mean_t /= kEnsemble;
+    mean_e /= kEnsemble;
+    // learned error head: log10 of the predicted relative error
+    if (std::pow(10.f, mean_e) * ctx->err.margin > c.tol) continue;
+    float var = 0;
+    for (int e = 0; e < kEnsemble; ++e) {
+      const float d = out[e * kOutputs + v] - mean_t;
+      var += d * d;
+    }
+    if (mean_t < best_t) {
+      best_t = mean_t;
+      best = v;
+      best_std = std::sqrt(var / kEnsemble);
+    }
+  }
+  if (best < 0 || best_std > mm.conf_std) return -1;
+  if (pred_ms) *pred_ms = std::exp2(best_t);  // the time head predicts log2(ms)
+  return best;
+}
+
+static int history_choice(const compar_ctx* ctx, const GemmCall& c, uint32_t mask,
+                          double* pred_ms) {
+  int best = -1;
+  double best_t = INFINITY;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (!(mask & (1u << v))) continue;
+    double t = ctx->hist.predict(v, c.dtype, c.m, c.n, c.k, c.batch, nullptr);
+    if (t < 0) t = prior_time_ms(v, c.m, c.n, c.k, c.dtype, ctx->num_sms);
+    if (t < best_t) {
+      best_t = t;
+      best = v;
+    }
+  }
+  if (pred_ms) *pred_ms = best_t;
+  return best;
+}
+
+// Chooses a variant; returns it or a negative status.
+static int select_variant(compar_ctx* ctx, const GemmCall& c) {
+  const uint32_t mask = eligible_mask(ctx, c);
+  if (!mask) return COMPAR_ERR_NO_VARIANT;
+  const DecisionKey key{c.m, c.n, c.k, static_cast<int>(c.dtype), tol_class(c.tol), c.batch};
+  auto it = ctx->decisions.find(key);
+  if (it != ctx->decisions.end() && (mask & (1u << it->second))) return it->second;
+  int v = -1;
+  const char* by = "history";
+  float mlp_ms = 0;
+  double hist_ms = 0;
+  if (ctx->selector_mode != 1) {
+    v = mlp_choice(ctx, c, mask, &mlp_ms);
+    if (v >= 0) by = "mlp";
+  }
+  if (v < 0 && ctx->selector_mode == 2 && ctx->mlp.trained) {
+    // MLP-only mode still needs an answer when the ensemble disagrees
+    by = "history(fallback)";
+  }
+  if (v < 0) v = history_choice(ctx, c, mask, &hist_ms);
+  if (ctx->log)
+    fprintf(stderr, "[compar] m=%lld n=%lld k=%lld dtype=%d tol=%.1e eligible=0x%x -> %s by %s\n",
+            static_cast<long long>(c.m), static_cast<long long>(c.n),
+            static_cast<long long>(c.k), static_cast<int>(c.dtype), c.tol, mask,
+            kVariantNames[v], by);
+  ctx->decisions[key] = v;
+  return v;
+}
+
+static cudaEvent_t take_event(compar_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+static void resolve_pending(compar_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = -1;
+    if (cudaEventSynchronize(p.stop) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+      p.rec.time_ms = ms;
+      ctx->rec.push(p.rec);
+      ctx->hist.observe(p.rec.variant, p.rec.dtype, p.rec.m, p.rec.n, p.rec.k, p.rec.batch, ms);
+    }
+    ctx->event_pool.push_back(p.start);
+    ctx->event_pool.push_back(p.stop);
+  }
+  ctx->pending.clear();
+}
+
+static compar_record_t make_record(const GemmCall& c, int v) {
+  compar_record_t r{};
+  r.m = c.m;
+  r.n = c.n;
+  r.k = c.k;
+  r.dtype = c.dtype;
+  r.variant = v;
+  r.batch = c.batch;
+  r.tol = static_cast<float>(c.tol);
+  r.time_ms = -1;
+  r.rel_err = -1;
+  return r;
+}
+
+// Runs one call on variant v (recording it when recording is on).
+static int run_one(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->rec.on) {
+    e0 = take_event(ctx);
+    e1 = take_event(ctx);
+    if (e0) cudaEventRecord(e0, s);
+  }
+  const int rc = launch_variant(ctx, v, c, s);
+  if (ctx->rec.on && e0 && e1) {
+    cudaEventRecord(e1, s);
+    if (rc == COMPAR_OK) {
+      ctx->pending.push_back(PendingTiming{e0, e1, make_record(c, v)});
+      if (ctx->pending.size() >= 4096) resolve_pending(ctx);
+    } else {
+      ctx->event_pool.push_back(e0);
+      ctx->event_pool.push_back(e1);
+    }
+  }
+  return rc;
+}
+
+int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
+  if (c.m == 0 || c.n == 0) return COMPAR_OK;
+  if (c.k == 0) {
+    ctx->last_variant = -1;
+    return launch_scale_c(c.C, c.m, c.n, c.ldc, c.beta, s);
+  }
+  if (ctx->forced >= 0) {
+    if (!variant_supported(ctx, ctx->forced, c)) return COMPAR_ERR_UNSUPPORTED;
+    ctx->last_variant = ctx->forced;
+    return run_one(ctx, ctx->forced, c, s);
+  }
+  for (int attempt = 0; attempt < kNumVariants; ++attempt) {
+    const int v = select_variant(ctx, c);
+    if (v < 0) return v;
+    ctx->last_variant = v;
+    const int rc = run_one(ctx, v, c, s);
+    if (rc == COMPAR_OK) return rc;
+    // A variant that failed to launch is quarantined for this context and
+    // the call is re-dispatched to the next choice.
+    if (ctx->log)
+      fprintf(stderr, "[compar] variant %s failed (%s); quarantined\n", kVariantNames[v],
+              g_last_error.c_str());
+    ctx->quarantined[v] = true;
+    ctx->decisions.clear();
+  }
+  return COMPAR_ERR_NO_VARIANT;
+}
+
+static bool valid_dtype(int d) { return d == COMPAR_F32 || d == COMPAR_BF16 || d == COMPAR_F8E4M3; }
+
+static int check_ptrs(int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                      const void* C) {
+  if (m < 0 || n < 0 || k < 0) return COMPAR_ERR_INVALID;
+  if (m > 0 && n > 0 && C == nullptr) return COMPAR_ERR_INVALID;
+  if (m > 0 && n > 0 && k > 0 && (A == nullptr || B == nullptr)) return COMPAR_ERR_INVALID;
+  if (C && (reinterpret_cast<uintptr_t>(C) % 4)) return COMPAR_ERR_INVALID;
+  return COMPAR_OK;
+}
+
+}  // namespace compar
+
+using namespace compar;
+
+extern "C" {
+
+int compar_init(compar_ctx_t* out, int device) {
+  if (!out) return COMPAR_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    (void)cudaGetLastError();
+    g_last_error = "no such CUDA device";
+    return COMPAR_ERR_CUDA;
+  }
+  cudaDeviceProp prop{};
+  COMPAR_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) {
+    g_last_error = "libcompar is built for sm_103 (B300) only";
+    return COMPAR_ERR_UNSUPPORTED;
+  }
+  COMPAR_CUDA_TRY(cudaSetDevice(device));
+  auto* ctx = new compar_ctx();
+  ctx->device = device;
+  ctx->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&ctx->guard.err_word, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->guard.err_word, 0, sizeof(int)) != cudaSuccess) {
+    g_last_error = "cannot allocate the device error word";
+    delete ctx;
+    return COMPAR_ERR_CUDA;
+  }
+  if (const char* e = getenv("COMPAR_FORCE_VARIANT")) ctx->forced = atoi(e);
+  if (const char* e = getenv("COMPAR_SELECTOR")) {
+    if (!strcmp(e, "history")) ctx->selector_mode = 1;
+    else if (!strcmp(e, "mlp")) ctx->selector_mode = 2;
+  }
+  if (const char* e = getenv("COMPAR_LOG")) ctx->log = atoi(e) != 0;
+  if (const char* e = getenv("COMPAR_WAIT_BUDGET_NS"))
+    ctx->guard.budget_ns = std::max<unsigned long long>(1000, strtoull(e, nullptr, 10));
+  if (const char* e = getenv("COMPAR_TEST_FAIL_VARIANT")) ctx->test_fail_variant = atoi(e);
+  if (const char* e = getenv("COMPAR_SELECTOR_FILE")) {
+    if (compar_selector_load(ctx, e) != COMPAR_OK && ctx->log)
+      fprintf(stderr, "[compar] could not load selector file %s\n", e);
+  }
+  *out = ctx;
+  return COMPAR_OK;
+}
+
+int compar_terminate(compar_ctx_t ctx) {
+  if (!ctx) return COMPAR_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  resolve_pending(ctx);
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  batched_release(ctx);
+  mlp_release(ctx);
+  ctx->ws.release();
+  if (ctx->guard.err_word) cudaFree(ctx->guard.err_word);
+  delete ctx;
+  return COMPAR_OK;
+}
+
+const char* compar_status_string(int status) {
+  switch (status) {
+    case COMPAR_OK: return "ok";
+    case COMPAR_ERR_INVALID: return "invalid argument";
+    case COMPAR_ERR_UNSUPPORTED: return "unsupported";
+    case COMPAR_ERR_CUDA: return "CUDA error";
+    case COMPAR_ERR_TIMEOUT: return "device wait timed out";
+    case COMPAR_ERR_IO: return "selector/record file error";
+    case COMPAR_ERR_NO_VARIANT: return "no variant meets the tolerance";
+    default: return "unknown status";
+  }
+}
+
+const char* compar_last_error(void) { return g_last_error.c_str(); }
+
+int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
+                double tol, const void* A, const void* B, float* C, void* stream) {
+  if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
+  int rc = check_ptrs(m, n, k, A, B, C);
+  if (rc != COMPAR_OK) return rc;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.lda = k;
+  c.ldb = n;
+  c.ldc = n;
+  c.dtype = dtype;
+  c.tol = default_tol(tol);
+  c.A = A;
+  c.B = B;
+  c.C = C;
+  c.alpha = ctx->alpha;
+  c.beta = ctx->beta;
+  c.scale_a = ctx->scale_a;
+  c.scale_b = ctx->scale_b;
+  return gemm_call(ctx, c, static_cast<cudaStream_t>(stream));
+}
+
+int compar_force_variant(compar_ctx_t ctx, int variant_id) {
+  if (!ctx || variant_id < -1 || variant_id >= kNumVariants) return COMPAR_ERR_INVALID;
+  ctx->forced = variant_id;
+  return COMPAR_OK;
+}
+
+int compar_set_scalars(compar_ctx_t ctx, float alpha, float beta) {
+  if (!ctx || !std::isfinite(alpha) || !std::isfinite(beta)) return COMPAR_ERR_INVALID;
+  ctx->alpha = alpha;
+  ctx->beta = beta;
+  return COMPAR_OK;
+}
+
+int compar_set_fp8_scales(compar_ctx_t ctx, float scale_a, float scale_b) {
+  if (!ctx || !(scale_a > 0) || !(scale_b > 0) || !std::isfinite(scale_a) ||
+      !std::isfinite(scale_b))
+    return COMPAR_ERR_INVALID;
+  ctx->scale_a = scale_a;
+  ctx->scale_b = scale_b;
+  return COMPAR_OK;
+}
+
+int compar_set_selector_mode(compar_ctx_t ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) return COMPAR_ERR_INVALID;
+  ctx->selector_mode = mode;
+  ctx->decisions.clear();
+  return COMPAR_OK;
+}
+
+int compar_last_variant(compar_ctx_t ctx) { return ctx ? ctx->last_variant : COMPAR_ERR_INVALID; }
+
+int compar_variant_count(void) { return kNumVariants; }
+
+const char* compar_variant_name(int v) {
+  return (v >= 0 && v <= COMPAR_V_GROUPED) ? kVariantNames[v] : nullptr;
+}
+
+int compar_variant_supported(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
+                             compar_dtype_t dtype) {
+  if (!ctx || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0)
+    return COMPAR_ERR_INVALID;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.dtype = dtype;
+  return variant_supported(ctx, v, c) ? 1 : 0;
+}
+
+int compar_clear_decisions(compar_ctx_t ctx) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  ctx->decisions.clear();
+  return COMPAR_OK;
+}
+
+int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
+                   compar_dtype_t dtype, double tol, const void* A, const void* B, float* C,
+                   int warmup, int reps, void* stream, float* median_ms) {
+  if (!ctx || !median_ms || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || reps < 1 ||
+      warmup < 0)
+    return COMPAR_ERR_INVALID;
+  int rc = check_ptrs(m, n, k, A, B, C);
+  if (rc != COMPAR_OK) return rc;
+  if (m == 0 || n == 0 || k == 0) return COMPAR_ERR_INVALID;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.lda = k;
+  c.ldb = n;
+  c.ldc = n;
+  c.dtype = dtype;
+  c.tol = default_tol(tol);
+  c.A = A;
+  c.B = B;
+  c.C = C;
+  c.alpha = ctx->alpha;
+  c.beta = ctx->beta;
+  c.scale_a = ctx->scale_a;
+  c.scale_b = ctx->scale_b;
+  if (!variant_supported(ctx, v, c)) return COMPAR_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < warmup; ++i) {
+    rc = launch_variant(ctx, v, c, s);
+    if (rc != COMPAR_OK) return rc;
+  }
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) {
+    e = take_event(ctx);
+    if (!e) return COMPAR_ERR_CUDA;
+  }
+  for (int i = 0; i < reps; ++i) {
+    cudaEventRecord(ev[2 * i], s);
+    rc = launch_variant(ctx, v, c, s);
+    cudaEventRecord(ev[2 * i + 1], s);
+    if (rc != COMPAR_OK) break;
+  }
+  std::vector<float> t;
+  if (rc == COMPAR_OK) {
+    if (cudaEventSynchronize(ev.back()) != cudaSuccess) rc = COMPAR_ERR_CUDA;
+    for (int i = 0; rc == COMPAR_OK && i < reps; ++i) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) {
+        rc = COMPAR_ERR_CUDA;
+        break;
+      }
+      t.push_back(ms);
+      if (ctx->rec.on) {
+        compar_record_t r = make_record(c, v);
+        r.time_ms = ms;
+        ctx->rec.push(r);
+      }
+    }
+  }
+  for (auto e : ev) ctx->event_pool.push_back(e);
+  if (rc != COMPAR_OK) return rc;
+  std::sort(t.begin(), t.end());
+  const float med = (reps % 2) ? t[reps / 2] : 0.5f * (t[reps / 2 - 1] + t[reps / 2]);
+  *median_ms = med;
+  ctx->hist.observe(v, dtype, m, n, k, 1, med);
+  return COMPAR_OK;
+}
+
+int compar_record_enable(compar_ctx_t ctx, int on) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  if (!on) resolve_pending(ctx);
+  ctx->rec.on = on != 0;
+  return COMPAR_OK;
+}
+
+int64_t compar_record_count(compar_ctx_t ctx) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  resolve_pending(ctx);
+  return static_cast<int64_t>(ctx->rec.ring.size());
+}
+
+int64_t compar_record_get(compar_ctx_t ctx, compar_record_t* out, int64_t max) {
+  if (!ctx || (!out && max > 0) || max < 0) return COMPAR_ERR_INVALID;
+  resolve_pending(ctx);
+  auto snap = ctx->rec.snapshot();
+  const int64_t nout = std::min<int64_t>(max, static_cast<int64_t>(snap.size()));
+  if (nout > 0) memcpy(out, snap.data(), static_cast<size_t>(nout) * sizeof(compar_record_t));
+  return nout;
+}
+
+int compar_record_add(compar_ctx_t ctx, const compar_record_t* recs, int64_t count) {
+  if (!ctx || count < 0 || (count > 0 && !recs)) return COMPAR_ERR_INVALID;
+  for (int64_t i = 0; i < count; ++i) {
+    const compar_record_t& r = recs[i];
+    if (r.variant < 0 || r.variant >= kNumVariants || !valid_dtype(r.dtype)) return COMPAR_ERR_INVALID;
+    ctx->rec.push(r);
+    if (r.time_ms > 0) ctx->hist.observe(r.variant, r.dtype, r.m, r.n, r.k, r.batch, r.time_ms);
+  }
+  return COMPAR_OK;
+}
+
+int compar_record_clear(compar_ctx_t ctx) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  resolve_pending(ctx);
+  ctx->rec.clear();
+  return COMPAR_OK;
+}
+
+int compar_check_device_error(compar_ctx_t ctx, void* stream) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int word = 0;
+  COMPAR_CUDA_TRY(cudaMemcpyAsync(&word, ctx->guard.err_word, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s));
+  COMPAR_CUDA_TRY(cudaMemsetAsync(ctx->guard.err_word, 0, sizeof(int), s));
+  COMPAR_CUDA_TRY(cudaStreamSynchronize(s));
+  return word == 0 ? COMPAR_OK : word;
+}
+
+int compar_set_wait_budget(compar_ctx_t ctx, uint64_t ns) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  ctx->guard.budget_ns = std::max<uint64_t>(ns, 1000);
+  return COMPAR_OK;
+}
+
+int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
+  if (!ctx) return COMPAR_ERR_INVALID;
+  return launch_timeout_selftest(ctx->guard, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

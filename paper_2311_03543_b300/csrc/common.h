@@ -1,0 +1,88 @@
+// Internal declarations shared by the host-side parts of libcompar.
+// Nothing here is part of the public C ABI (include/compar.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "compar.h"
+
+namespace compar {
+
+#define COMPAR_CUDA_TRY(expr)                                              \
+  do {                                                                     \
+    cudaError_t e__ = (expr);                                              \
+    if (e__ != cudaSuccess) {                                              \
+      compar::set_last_cuda_error(e__, #expr, __FILE__, __LINE__);         \
+      return COMPAR_ERR_CUDA;                                              \
+    }                                                                      \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Per-call description used by eligibility, selection and launch.
+struct GemmCall {
+  int64_t m = 0, n = 0, k = 0;
+  int64_t lda = 0, ldb = 0, ldc = 0;
+  compar_dtype_t dtype = COMPAR_F32;
+  double tol = 0;
+  const void* A = nullptr;
+  const void* B = nullptr;
+  float* C = nullptr;
+  float alpha = 1.f, beta = 0.f;
+  float scale_a = 1.f, scale_b = 1.f;  // fp8 input dequantisation factors
+  int batch = 1;
+};
+
+// Device scratch owned by a context, grown stream-ordered.
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need, cudaStream_t s);
+  void release();
+};
+
+// ------------------------------------------------------------- kernel entry
+// Each returns a compar_status_t; all are asynchronous on `s`.
+struct DeviceGuard {  // device error word + wait budget handed to kernels
+  int* err_word = nullptr;
+  unsigned long long budget_ns = 2000000000ull;
+};
+
+int launch_naive(const GemmCall& c, cudaStream_t s);
+int launch_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s);
+int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s);
+
+// Tensor-core variants (tcgen05).  kind: COMPAR_V_TC_TF32 / TC_BF16 / TC_FP8 / SPLIT3.
+int launch_tc(int variant, const GemmCall& c, Workspace& ws, const DeviceGuard& g,
+              int num_sms, cudaStream_t s);
+bool tc_supported(int variant, const GemmCall& c);
+
+int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s);
+
+// Pre-pass kernels (prepass.cu).
+int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols,
+                    int64_t ldx, void* Y, int out_kind, int64_t ldy, bool transpose,
+                    void* Y_lo, const float* dscale, cudaStream_t s);
+int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                 unsigned int* d_amax_bits, cudaStream_t s);
+int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_dequant,
+                      cudaStream_t s);
+
+// out_kind values for prepass_convert
+enum PrepassOut { PP_F32 = 0, PP_BF16 = 1, PP_SPLIT_BF16 = 2, PP_E4M3 = 3, PP_COPY = 4 };
+
+// TMA tensor-map encoding (tma.cpp).
+bool tma_available();
+int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, const void* base,
+                  uint64_t inner, uint64_t outer, uint64_t ld_elems, uint32_t box_inner,
+                  uint32_t box_outer);
+
+std::string last_error_text();
+
+}  // namespace compar

@@ -1,0 +1,321 @@
+// FP32 SIMT implementation variants of C = alpha*A*B + beta*C (the
+// matrix-multiply component of Sec. 2.1 / Table 2; the paper's own GPU
+// variant of it is a hand-written CUDA kernel for a Pascal GPU).
+//
+//  * gemm_naive_kernel: one thread per C element, FP32 FMA over k.
+//  * gemm_simt_kernel : shared-memory tiled, register-blocked, with 128-bit
+//    global loads and double-buffered shared-memory tiles; optional split-K
+//    with a separate reduction pass.
+//
+// Row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.h"
+
+namespace compar {
+namespace {
+
+// ------------------------------------------------------------------ naive
+__global__ void gemm_naive_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                  int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                  float beta, float* __restrict__ C, int64_t ldc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= M || j >= N) return;
+  const float* a = A + static_cast<int64_t>(i) * lda;
+  float acc = 0.f;
+  for (int p = 0; p < K; ++p) acc = fmaf(a[p], B[static_cast<int64_t>(p) * ldb + j], acc);
+  float* c = C + static_cast<int64_t>(i) * ldc + j;
+  *c = (beta == 0.f) ? alpha * acc : fmaf(alpha, acc, beta * *c);
+}
+
+__global__ void scale_c_kernel(float* C, int M, int N, int64_t ldc, float beta) {
+  const int64_t total = static_cast<int64_t>(M) * N;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / N, j = t % N;
+    float* c = C + i * ldc + j;
+    *c = (beta == 0.f) ? 0.f : beta * *c;
+  }
+}
+
+// ------------------------------------------------------------------ tiled
+// Thread (ty, tx) owns TM x TN outputs laid out as groups of 4 rows strided
+// by 4*(BM/TM) and groups of 4 columns strided by 4*(BN/TN), so that its
+// shared-memory reads are 128-bit and a warp's B reads cover distinct banks.
+template <int BM, int BN, int BK, int TM, int TN, bool VEC>
+struct SimtCfg {
+  static constexpr int kThreadsX = BN / TN;
+  static constexpr int kThreadsY = BM / TM;
+  static constexpr int kThreads = kThreadsX * kThreadsY;
+  static constexpr int kRowStride = 4 * kThreadsY;  // between 4-row groups
+  static constexpr int kColStride = 4 * kThreadsX;
+  static constexpr int kAElems = BM * BK / kThreads;  // A elements loaded per thread
+  static constexpr int kBElems = BK * BN / kThreads;
+  static_assert(TM % 4 == 0 && TN % 4 == 0, "micro tile in 4-wide groups");
+  static_assert(kAElems % 4 == 0 && kBElems % 4 == 0, "vector loads");
+};
+
+template <int BM, int BN, int BK, int TM, int TN, bool VEC>
+__global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads)
+    gemm_simt_kernel(int M, int N, int K, int k_per_split, float alpha,
+                     const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+                     int64_t ldb, float beta, float* __restrict__ C, int64_t ldc,
+                     float* __restrict__ partial) {
+  using Cfg = SimtCfg<BM, BN, BK, TM, TN, VEC>;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % Cfg::kThreadsX;
+  const int ty = tid / Cfg::kThreadsX;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  const int k_begin = blockIdx.z * k_per_split;
+  const int k_end = min(K, k_begin + k_per_split);
+
+  float ra[Cfg::kAElems];
+  float rb[Cfg::kBElems];
+
+  // A tile: BM rows x BK columns; linear element e -> (row e / BK, col e % BK)
+  auto load_a = [&](int k0) {
+#pragma unroll
+    for (int v = 0; v < Cfg::kAElems / 4; ++v) {
+      const int e = (v * Cfg::kThreads + tid) * 4;
+      const int r = e / BK, c = e % BK;
+      const int gi = m0 + r, gk = k0 + c;
+      if constexpr (VEC) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gi < M && gk < k_end)
+          x = __ldg(reinterpret_cast<const float4*>(A + static_cast<int64_t>(gi) * lda + gk));
+        ra[4 * v + 0] = x.x; ra[4 * v + 1] = x.y; ra[4 * v + 2] = x.z; ra[4 * v + 3] = x.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          ra[4 * v + q] = (gi < M && gk + q < k_end)
+                              ? __ldg(A + static_cast<int64_t>(gi) * lda + gk + q) : 0.f;
+      }
+    }
+  };
+  auto store_a = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < Cfg::kAElems / 4; ++v) {
+      const int e = (v * Cfg::kThreads + tid) * 4;
+      const int r = e / BK, c = e % BK;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) As[buf][c + q][r] = ra[4 * v + q];
+    }
+  };
+  // B tile: BK rows x BN columns
+  auto load_b = [&](int k0) {
+#pragma unroll
+    for (int v = 0; v < Cfg::kBElems / 4; ++v) {
+      const int e = (v * Cfg::kThreads + tid) * 4;
+      const int r = e / BN, c = e % BN;
+      const int gk = k0 + r, gj = n0 + c;
+      if constexpr (VEC) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gk < k_end && gj < N)
+          x = __ldg(reinterpret_cast<const float4*>(B + static_cast<int64_t>(gk) * ldb + gj));
+        rb[4 * v + 0] = x.x; rb[4 * v + 1] = x.y; rb[4 * v + 2] = x.z; rb[4 * v + 3] = x.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          rb[4 * v + q] = (gk < k_end && gj + q < N)
+                              ? __ldg(B + static_cast<int64_t>(gk) * ldb + gj + q) : 0.f;
+      }
+    }
+  };
+  auto store_b = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < Cfg::kBElems / 4; ++v) {
+      const int e = (v * Cfg::kThreads + tid) * 4;
+      const int r = e / BN, c = e % BN;
+      *reinterpret_cast<float4*>(&Bs[buf][r][c]) =
+          make_float4(rb[4 * v + 0], rb[4 * v + 1], rb[4 * v + 2], rb[4 * v + 3]);
+    }
+  };
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (k_begin < k_end) {
+    load_a(k_begin);
+    load_b(k_begin);
+    store_a(0);
+    store_b(0);
+  }
+  __syncthreads();
+
+  for (int k0 = k_begin; k0 < k_end; k0 += BK) {
+    const bool has_next = k0 + BK < k_end;
+    if (has_next) {
+      load_a(k0 + BK);
+      load_b(k0 + BK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int g = 0; g < TM / 4; ++g) {
+        const float4 x = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + g * Cfg::kRowStride]);
+        a[4 * g + 0] = x.x; a[4 * g + 1] = x.y; a[4 * g + 2] = x.z; a[4 * g + 3] = x.w;
+      }
+#pragma unroll
+      for (int g = 0; g < TN / 4; ++g) {
+        const float4 x = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + g * Cfg::kColStride]);
+        b[4 * g + 0] = x.x; b[4 * g + 1] = x.y; b[4 * g + 2] = x.z; b[4 * g + 3] = x.w;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (has_next) {
+      store_a(buf ^ 1);
+      store_b(buf ^ 1);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+
+  // Epilogue: each thread writes its 4-wide column groups; split-K writes raw
+  // partial sums to its slice of the workspace instead of C.
+  const bool vec_store = VEC && partial == nullptr;
+#pragma unroll
+  for (int gi = 0; gi < TM / 4; ++gi) {
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      const int row = m0 + ty * 4 + gi * Cfg::kRowStride + ii;
+      if (row >= M) continue;
+#pragma unroll
+      for (int gj = 0; gj < TN / 4; ++gj) {
+        const int col = n0 + tx * 4 + gj * Cfg::kColStride;
+        const float* v = &acc[gi * 4 + ii][gj * 4];
+        if (partial != nullptr) {
+          float* p = partial + (static_cast<int64_t>(blockIdx.z) * M + row) * N + col;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (col + q < N) p[q] = v[q];
+        } else if (vec_store && col + 3 < N) {
+          float4* c4 = reinterpret_cast<float4*>(C + static_cast<int64_t>(row) * ldc + col);
+          float4 out;
+          if (beta == 0.f) {
+            out = make_float4(alpha * v[0], alpha * v[1], alpha * v[2], alpha * v[3]);
+          } else {
+            const float4 old = *c4;
+            out = make_float4(fmaf(alpha, v[0], beta * old.x), fmaf(alpha, v[1], beta * old.y),
+                              fmaf(alpha, v[2], beta * old.z), fmaf(alpha, v[3], beta * old.w));
+          }
+          *c4 = out;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (col + q >= N) break;
+            float* c = C + static_cast<int64_t>(row) * ldc + col + q;
+            *c = (beta == 0.f) ? alpha * v[q] : fmaf(alpha, v[q], beta * *c);
+          }
+        }
+      }
+    }
+  }
+}
+
+// C = alpha * sum_s partial[s] + beta * C
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
+                                     float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t total = static_cast<int64_t>(M) * N;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += partial[z * total + t];
+    const int64_t i = t / N, j = t % N;
+    float* c = C + i * ldc + j;
+    *c = (beta == 0.f) ? alpha * s : fmaf(alpha, s, beta * *c);
+  }
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+int run_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
+  const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int tiles = tiles_m * tiles_n;
+  // Split K when the tiles alone cannot fill the GPU and K is long.
+  int splits = 1;
+  if (tiles < num_sms && K >= 1024) {
+    splits = std::min<int>((2 * num_sms + tiles - 1) / tiles, K / 256);
+    splits = std::max(1, std::min(splits, 32));
+  }
+  int k_per = K;
+  if (splits > 1) {
+    k_per = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    splits = (K + k_per - 1) / k_per;
+  }
+  float* partial = nullptr;
+  if (splits > 1) {
+    const size_t need = static_cast<size_t>(splits) * M * N * sizeof(float);
+    int rc = ws.ensure(need, s);
+    if (rc != COMPAR_OK) return rc;
+    partial = static_cast<float*>(ws.ptr);
+  }
+  const bool vec = (c.k % 4 == 0) && (c.n % 4 == 0) && (c.lda % 4 == 0) && (c.ldb % 4 == 0) &&
+                   (c.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(c.B) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(c.C) % 16 == 0);
+  dim3 grid(tiles_n, tiles_m, splits);
+  constexpr int threads = SimtCfg<BM, BN, BK, TM, TN, true>::kThreads;
+  const float* A = static_cast<const float*>(c.A);
+  const float* B = static_cast<const float*>(c.B);
+  if (vec)
+    gemm_simt_kernel<BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+  else
+    gemm_simt_kernel<BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  if (splits > 1) {
+    const int64_t total = static_cast<int64_t>(M) * N;
+    const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, partial, c.alpha, c.beta, c.C,
+                                                c.ldc);
+    COMPAR_CUDA_TRY(cudaGetLastError());
+  }
+  return COMPAR_OK;
+}
+
+}  // namespace
+
+int launch_naive(const GemmCall& c, cudaStream_t s) {
+  dim3 block(16, 16);
+  dim3 grid(static_cast<unsigned>((c.n + 15) / 16), static_cast<unsigned>((c.m + 15) / 16));
+  gemm_naive_kernel<<<grid, block, 0, s>>>(static_cast<int>(c.m), static_cast<int>(c.n),
+                                           static_cast<int>(c.k), c.alpha,
+                                           static_cast<const float*>(c.A), c.lda,
+                                           static_cast<const float*>(c.B), c.ldb, c.beta, c.C,
+                                           c.ldc);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+int launch_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
+  // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
+  if (c.m <= 48) return run_simt<32, 128, 32, 4, 8>(c, ws, num_sms, s);
+  return run_simt<128, 128, 16, 8, 8>(c, ws, num_sms, s);
+}
+
+int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s) {
+  const int64_t total = m * n;
+  const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
+  scale_c_kernel<<<blocks, 256, 0, s>>>(C, static_cast<int>(m), static_cast<int>(n), ldc, beta);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+}  // namespace compar

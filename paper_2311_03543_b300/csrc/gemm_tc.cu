@@ -1,0 +1,518 @@
+// Tensor-core implementation variants of C = alpha*A*B + beta*C on sm_103a
+// (the matrix-multiply component of Sec. 2.1 / Table 2; the paper's GPU
+// variants were SIMT CUDA and cuBLAS on a Pascal GPU without tensor cores).
+//
+// One persistent, warp-specialised kernel template serves four variants:
+//   TF32   : kind::tf32 on float32 operands (tensor cores read 19 bits)
+//   BF16   : kind::f16 with bf16 operands
+//   FP8    : kind::f8f6f4 with E4M3 operands, per-tensor dequantisation
+//   SPLIT3 : 3xBF16 — A = Ahi + Alo, B = Bhi + Blo (bf16 pieces) and
+//            Ahi*Bhi + Ahi*Blo + Alo*Bhi accumulated into one FP32 TMEM tile
+//
+// CTA roles (192 threads, one CTA per SM, grid = min(tiles, SMs)):
+//   warp 0      TMA producer: one elected lane streams K-major A and B tiles
+//               (128-byte swizzle) into an S-stage shared-memory ring.
+//   warp 1      TMEM allocator; one lane issues tcgen05.mma into one of two
+//               TMEM accumulators (double buffered across output tiles) and
+//               releases ring stages with tcgen05.commit.
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator lane quarter the warp
+//               may access, alpha/beta and dequantisation, stores to C.
+// Every wait is bounded (ptx.cuh); on expiry the CTA drains its own copies
+// and MMAs, frees TMEM and returns with COMPAR_ERR_TIMEOUT in the error word.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "common.h"
+#include "ptx.cuh"
+
+namespace compar {
+namespace {
+
+using dev::Kind;
+
+constexpr int kBM = 128;
+constexpr int kRowBytes = 128;  // K extent of one stage, in bytes (one swizzle row)
+constexpr int kThreads = 192;
+constexpr int kEpiThreads = 128;
+
+template <int V>
+struct Traits;
+template <>
+struct Traits<COMPAR_V_TC_TF32> {
+  static constexpr Kind kind = Kind::TF32;
+  static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256;
+};
+template <>
+struct Traits<COMPAR_V_TC_BF16> {
+  static constexpr Kind kind = Kind::F16;
+  static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256;
+};
+template <>
+struct Traits<COMPAR_V_TC_FP8> {
+  static constexpr Kind kind = Kind::F8;
+  static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256;
+};
+template <>
+struct Traits<COMPAR_V_SPLIT3> {
+  static constexpr Kind kind = Kind::F16;
+  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 128;
+};
+
+template <int V>
+struct Layout {
+  using T = Traits<V>;
+  static constexpr int BN = T::BN;
+  static constexpr int kABytes = kBM * kRowBytes;
+  static constexpr int kBBytes = BN * kRowBytes;
+  static constexpr int kStageBytes = T::pieces * (kABytes + kBBytes);
+  static constexpr int kMaxSmem = 232448;  // 227 KB opt-in per CTA
+  static constexpr int kBarBytes = 256;
+  static constexpr int kStagesRaw = (kMaxSmem - 1024 - kBarBytes) / kStageBytes;
+  static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
+  static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes;
+  static constexpr int kTmemCols = 2 * BN;  // two accumulators
+  static constexpr int kElemsPerStage = kRowBytes / T::elem;
+  static_assert(kStages >= 2, "pipeline needs two stages");
+  static_assert(kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
+};
+
+struct TcArgs {
+  int M, N, K;
+  int num_kb;
+  int tiles_m, tiles_n;
+  float alpha, beta;
+  const float* dequant_a;  // optional device factors (fp8 of float32 inputs)
+  const float* dequant_b;
+  float* C;
+  int64_t ldc;
+  int* err_word;
+  unsigned long long budget_ns;
+};
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& mb, int& nb) {
+  constexpr int G = 8;  // group of M blocks walked together for L2 reuse of B
+  const int per_group = G * tiles_n;
+  const int group = tile / per_group;
+  const int first_m = group * G;
+  const int gsize = min(tiles_m - first_m, G);
+  const int in = tile - group * per_group;
+  mb = first_m + in % gsize;
+  nb = in / gsize;
+}
+
+// Wait that ignores the CTA abort flag: used only to drain this CTA's own
+// outstanding copies / MMAs before it frees resources and exits.
+__device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity, uint64_t budget) {
+  const uint64_t t0 = dev::globaltimer_ns();
+  while (!dev::mbar_try_wait(bar, parity)) {
+    if (dev::globaltimer_ns() - t0 > budget) return false;
+  }
+  return true;
+}
+
+template <int V>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB2, const TcArgs p) {
+  using T = Traits<V>;
+  using L = Layout<V>;
+  constexpr int P = T::pieces;
+  constexpr int BN = T::BN;
+  constexpr int S = L::kStages;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;                              // [S][P][kABytes]
+  uint8_t* sB = smem + S * P * L::kABytes;         // [S][P][kBBytes]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * P * L::kBBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;   // [2]
+  uint64_t* tempty = tfull + 2;  // [2]
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      dev::mbar_init(&full[s], 1);
+      dev::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      dev::mbar_init(&tfull[a], 1);
+      dev::mbar_init(&tempty[a], kEpiThreads);
+    }
+    dev::mbar_init(drain, 1);
+    *abort_flag = 0;
+    dev::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    dev::tma_prefetch_desc(&tmA);
+    dev::tma_prefetch_desc(&tmB);
+    if constexpr (P == 2) {
+      dev::tma_prefetch_desc(&tmA2);
+      dev::tma_prefetch_desc(&tmB2);
+    }
+  }
+  if (warp == 1) {
+    dev::tmem_alloc(tmem_slot, L::kTmemCols);
+    dev::tmem_relinquish();
+  }
+  dev::tc_fence_before();
+  __syncthreads();
+  dev::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
+  const int num_tiles = p.tiles_m * p.tiles_n;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    uint32_t stage = 0, phase = 0;
+    uint32_t issued = 0, issued_parity = 0;  // per-stage bit masks
+    constexpr uint32_t kTx = static_cast<uint32_t>(L::kStageBytes);
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      int mb, nb;
+      tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
+      for (int kb = 0; kb < p.num_kb; ++kb) {
+        if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
+          ok = false;
+          break;
+        }
+        dev::mbar_arrive_expect_tx(&full[stage], kTx);
+        const int x = kb * L::kElemsPerStage;
+        uint8_t* a_dst = sA + (stage * P) * L::kABytes;
+        uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
+        dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
+        dev::tma_load_2d(b_dst, &tmB, &full[stage], x, nb * BN);
+        if constexpr (P == 2) {
+          dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
+          dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
+        }
+        issued |= 1u << stage;
+        issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      // Let every copy this thread started land before the CTA exits.
+      for (int s = 0; s < S; ++s)
+        if (issued & (1u << s)) drain_wait(&full[s], (issued_parity >> s) & 1, p.budget_ns);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t idesc = dev::make_idesc(T::fmt, T::fmt, kBM, BN);
+    uint32_t stage = 0, phase = 0;
+    int local = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x, ++local) {
+      const uint32_t acc = local & 1;
+      const uint32_t acc_phase = (local >> 1) & 1;
+      if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
+        ok = false;
+        break;
+      }
+      dev::tc_fence_after();
+      const uint32_t d_tmem = tmem_base + acc * BN;
+      for (int kb = 0; kb < p.num_kb; ++kb) {
+        if (!dev::mbar_wait(&full[stage], phase, w)) {
+          ok = false;
+          break;
+        }
+        dev::tc_fence_after();
+        const uint32_t a0 = dev::smem_u32(sA + (stage * P) * L::kABytes);
+        const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
+        const uint64_t da = dev::smem_desc_sw128_kmajor(a0);
+        const uint64_t db = dev::smem_desc_sw128_kmajor(b0);
+#pragma unroll
+        for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+          // each instruction consumes 32 bytes of K; advance the start address
+          const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
+          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+          if constexpr (P == 2) {
+            const uint64_t da_lo = dev::smem_desc_sw128_kmajor(a0 + L::kABytes);
+            const uint64_t db_lo = dev::smem_desc_sw128_kmajor(b0 + L::kBBytes);
+            dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+            dev::mma<T::kind>(d_tmem, da + koff, db_lo + koff, idesc, 1u);
+            dev::mma<T::kind>(d_tmem, da_lo + koff, db + koff, idesc, 1u);
+          } else {
+            dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+          }
+        }
+        dev::mma_commit(&empty[stage]);  // stage reusable once these MMAs finish
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      dev::mma_commit(&tfull[acc]);  // accumulator ready for the epilogue
+    }
+    // All MMAs issued by this thread complete before TMEM is released.
+    dev::mma_commit(drain);
+    drain_wait(drain, 0, p.budget_ns);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    float alpha = p.alpha;
+    if (p.dequant_a) alpha *= *p.dequant_a;
+    if (p.dequant_b) alpha *= *p.dequant_b;
+    const bool vec = (p.N % 4 == 0) && (p.ldc % 4 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0);
+    int local = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
+      const uint32_t acc = local & 1;
+      const uint32_t acc_phase = (local >> 1) & 1;
+      if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
+      dev::tc_fence_after();
+      int mb, nb;
+      tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
+      const int row = mb * kBM + quarter * 32 + lane;
+      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+      float* crow = p.C + static_cast<int64_t>(row) * p.ldc;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+        dev::tmem_ld_wait();
+        const int col0 = nb * BN + c * 32;
+        if (row < p.M && col0 < p.N) {
+          if (vec && col0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
+              float4 o;
+              o.x = alpha * __uint_as_float(r[j + 0]);
+              o.y = alpha * __uint_as_float(r[j + 1]);
+              o.z = alpha * __uint_as_float(r[j + 2]);
+              o.w = alpha * __uint_as_float(r[j + 3]);
+              if (p.beta != 0.f) {
+                const float4 old = *dst;
+                o.x = fmaf(p.beta, old.x, o.x);
+                o.y = fmaf(p.beta, old.y, o.y);
+                o.z = fmaf(p.beta, old.z, o.z);
+                o.w = fmaf(p.beta, old.w, o.w);
+              }
+              *dst = o;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (col0 + j < p.N) {
+                float v = alpha * __uint_as_float(r[j]);
+                if (p.beta != 0.f) v = fmaf(p.beta, crow[col0 + j], v);
+                crow[col0 + j] = v;
+              }
+            }
+          }
+        }
+      }
+      dev::tc_fence_before();
+      dev::mbar_arrive(&tempty[acc]);
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    dev::tc_fence_after();
+    dev::tmem_dealloc(tmem_base, L::kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------------ timeout self-test
+__global__ void timeout_selftest_kernel(int* err_word, unsigned long long budget_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    dev::mbar_init(&bar, 1);
+    abort_flag = 0;
+    dev::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const dev::WaitCtx w{&abort_flag, err_word, budget_ns};
+    // Nothing ever arrives on `bar`: the bounded wait runs out and records
+    // the timeout status, then the kernel returns.
+    (void)dev::mbar_wait(&bar, 0, w);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+int round_up(int64_t x, int64_t m) { return static_cast<int>((x + m - 1) / m * m); }
+
+CUtensorMapDataType map_type(int v) {
+  switch (v) {
+    case COMPAR_V_TC_TF32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    case COMPAR_V_TC_FP8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    default: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  }
+}
+
+template <int V>
+int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
+           const void* A2, const void* B2, const float* dq_a, const float* dq_b,
+           const DeviceGuard& g, int num_sms, cudaStream_t s) {
+  using L = Layout<V>;
+  using T = Traits<V>;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    L::kSmemBytes);
+  });
+  if (attr_err != cudaSuccess) {
+    set_last_cuda_error(attr_err, "cudaFuncSetAttribute(tc)", __FILE__, __LINE__);
+    return COMPAR_ERR_CUDA;
+  }
+  CUtensorMap ta, tb, ta2, tb2;
+  const CUtensorMapDataType dt = map_type(V);
+  const uint32_t box_k = static_cast<uint32_t>(L::kElemsPerStage);
+  int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM);
+  if (rc == COMPAR_OK) rc = tma_encode_2d(&tb, dt, T::elem, B, c.k, c.n, ldb, box_k, T::BN);
+  if (rc != COMPAR_OK) return rc;
+  if (T::pieces == 2) {
+    rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM);
+    if (rc == COMPAR_OK) rc = tma_encode_2d(&tb2, dt, T::elem, B2, c.k, c.n, ldb, box_k, T::BN);
+    if (rc != COMPAR_OK) return rc;
+  } else {
+    ta2 = ta;
+    tb2 = tb;
+  }
+  TcArgs a{};
+  a.M = static_cast<int>(c.m);
+  a.N = static_cast<int>(c.n);
+  a.K = static_cast<int>(c.k);
+  a.num_kb = static_cast<int>((c.k + L::kElemsPerStage - 1) / L::kElemsPerStage);
+  a.tiles_m = static_cast<int>((c.m + kBM - 1) / kBM);
+  a.tiles_n = static_cast<int>((c.n + T::BN - 1) / T::BN);
+  a.alpha = c.alpha * (V == COMPAR_V_TC_FP8 ? c.scale_a * c.scale_b : 1.f);
+  a.beta = c.beta;
+  a.dequant_a = dq_a;
+  a.dequant_b = dq_b;
+  a.C = c.C;
+  a.ldc = c.ldc;
+  a.err_word = g.err_word;
+  a.budget_ns = g.budget_ns;
+  const int tiles = a.tiles_m * a.tiles_n;
+  const int grid = std::min(tiles, num_sms);
+  tc_gemm_kernel<V><<<grid, kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, a);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+bool tma_operand_ok(const void* p, int64_t ld, int elem) {
+  return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * elem) % 16 == 0);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+bool tc_supported(int v, const GemmCall& c) {
+  if (c.m > (1 << 30) || c.n > (1 << 30) || c.k > (1 << 30)) return false;
+  switch (v) {
+    case COMPAR_V_TC_TF32: return c.dtype == COMPAR_F32;
+    case COMPAR_V_TC_BF16: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_BF16;
+    case COMPAR_V_TC_FP8: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_F8E4M3;
+    case COMPAR_V_SPLIT3: return c.dtype == COMPAR_F32;
+    default: return false;
+  }
+}
+
+// Pre-passes + launch.  B is always re-laid out to K-major (N x K); A is used
+// in place when its dtype matches and TMA can address it, else converted.
+int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
+              cudaStream_t s) {
+  if (!tc_supported(v, c)) return COMPAR_ERR_UNSUPPORTED;
+  if (!tma_available()) return COMPAR_ERR_UNSUPPORTED;
+  const int elem = (v == COMPAR_V_TC_TF32) ? 4 : (v == COMPAR_V_TC_FP8 ? 1 : 2);
+  const int pieces = (v == COMPAR_V_SPLIT3) ? 2 : 1;
+  const int64_t ldk = round_up(c.k, 16);  // 16-element pitch: 16-byte rows for every type
+  const bool a_native = (c.dtype != COMPAR_F32 || v == COMPAR_V_TC_TF32);
+  const bool a_in_place = a_native && tma_operand_ok(c.A, c.lda, elem);
+  const bool fp8_from_f32 = (v == COMPAR_V_TC_FP8 && c.dtype == COMPAR_F32);
+
+  // workspace carve: [A pieces][B pieces][fp8 scalars]
+  const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
+  const size_t b_bytes = align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
+  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256;
+  int rc = ws.ensure(need, s);
+  if (rc != COMPAR_OK) return rc;
+  uint8_t* base = static_cast<uint8_t*>(ws.ptr);
+  uint8_t* wb = base;
+  uint8_t* wa = base + pieces * b_bytes;
+  uint8_t* scal = wa + (a_in_place ? 0 : pieces * a_bytes);
+  unsigned int* amax_bits = reinterpret_cast<unsigned int*>(scal);  // [2]
+  float* fscal = reinterpret_cast<float*>(scal + 16);               // sA, dA, sB, dB
+
+  int out_kind;
+  switch (v) {
+    case COMPAR_V_TC_TF32: out_kind = PP_COPY; break;
+    case COMPAR_V_TC_BF16: out_kind = (c.dtype == COMPAR_F32) ? PP_BF16 : PP_COPY; break;
+    case COMPAR_V_TC_FP8: out_kind = fp8_from_f32 ? PP_E4M3 : PP_COPY; break;
+    default: out_kind = PP_SPLIT_BF16; break;
+  }
+  const float* sa = nullptr;
+  const float* sb = nullptr;
+  const float* dqa = nullptr;
+  const float* dqb = nullptr;
+  if (fp8_from_f32) {
+    rc = prepass_amax(static_cast<const float*>(c.A), c.m, c.k, c.lda, amax_bits, s);
+    if (rc == COMPAR_OK)
+      rc = prepass_amax(static_cast<const float*>(c.B), c.k, c.n, c.ldb, amax_bits + 1, s);
+    if (rc == COMPAR_OK) rc = prepass_fp8_scale(amax_bits, fscal + 0, fscal + 1, s);
+    if (rc == COMPAR_OK) rc = prepass_fp8_scale(amax_bits + 1, fscal + 2, fscal + 3, s);
+    if (rc != COMPAR_OK) return rc;
+    sa = fscal + 0;
+    dqa = fscal + 1;
+    sb = fscal + 2;
+    dqb = fscal + 3;
+  }
+  // B: K x N row-major -> N x K (K-major)
+  rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldk, true,
+                       pieces == 2 ? wb + b_bytes : nullptr, sb, s);
+  if (rc != COMPAR_OK) return rc;
+  const void* A = c.A;
+  int64_t lda = c.lda;
+  if (!a_in_place) {
+    rc = prepass_convert(c.A, c.dtype, c.m, c.k, c.lda, wa, out_kind, ldk, false,
+                         pieces == 2 ? wa + a_bytes : nullptr, sa, s);
+    if (rc != COMPAR_OK) return rc;
+    A = wa;
+    lda = ldk;
+  }
+  const void* A2 = pieces == 2 ? static_cast<const void*>(wa + a_bytes) : nullptr;
+  const void* B2 = pieces == 2 ? static_cast<const void*>(wb + b_bytes) : nullptr;
+  switch (v) {
+    case COMPAR_V_TC_TF32:
+      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, g,
+                                      num_sms, s);
+    case COMPAR_V_TC_BF16:
+      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, g,
+                                      num_sms, s);
+    case COMPAR_V_TC_FP8:
+      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, wb, ldk, nullptr, nullptr, dqa, dqb, g, num_sms,
+                                     s);
+    default:
+      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, wb, ldk, A2, B2, nullptr, nullptr, g, num_sms, s);
+  }
+}
+
+int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s) {
+  timeout_selftest_kernel<<<1, 32, 0, s>>>(g.err_word, g.budget_ns);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+}  // namespace compar

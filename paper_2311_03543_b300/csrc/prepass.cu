@@ -1,0 +1,217 @@
+// Operand pre-passes for the tensor-core variants: converting copies that
+// write the K-major, 16-byte-pitched layouts TMA loads from.
+//
+//  * f32 -> bf16 (round to nearest even)                 (BF16 variant on f32 inputs)
+//  * f32 -> (hi, lo) bf16 pair, hi = bf16(x), lo = bf16(x - hi)   (3xBF16 split)
+//  * f32 -> E4M3 codes of x * s, s = 448 / amax(|x|), saturating   (FP8 variant)
+//  * plain copy / transpose of f32, bf16 or fp8 elements
+//
+// B arrives row-major K x N; the tensor-core kernels read it as N x K
+// (K-major), so its pre-pass transposes through a 32 x 32 shared-memory tile.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.h"
+
+namespace compar {
+namespace {
+
+// One element conversion for the float32-input kinds.
+struct F32Out {
+  int kind;
+  float s;  // fp8 scale
+};
+
+__device__ __forceinline__ void store_converted(const F32Out& o, float x, void* Y, void* Ylo,
+                                                int64_t idx) {
+  switch (o.kind) {
+    case PP_F32:
+      static_cast<float*>(Y)[idx] = x;
+      break;
+    case PP_BF16:
+      static_cast<__nv_bfloat16*>(Y)[idx] = __float2bfloat16_rn(x);
+      break;
+    case PP_SPLIT_BF16: {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      const float r = x - __bfloat162float(hi);
+      static_cast<__nv_bfloat16*>(Y)[idx] = hi;
+      static_cast<__nv_bfloat16*>(Ylo)[idx] = __float2bfloat16_rn(r);
+      break;
+    }
+    case PP_E4M3: {
+      const float v = __fmul_rn(x, o.s);
+      static_cast<__nv_fp8_storage_t*>(Y)[idx] =
+          __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Non-transposing f32 conversion: Y[r][c] = f(X[r][c]).
+__global__ void convert_rows_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                    int64_t ldx, void* __restrict__ Y, void* __restrict__ Ylo,
+                                    int64_t ldy, int kind, const float* __restrict__ dscale) {
+  F32Out o{kind, dscale ? *dscale : 1.f};
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t / cols, c = t % cols;
+    store_converted(o, X[r * ldx + c], Y, Ylo, r * ldy + c);
+  }
+}
+
+// Transposing f32 conversion: Y[c][r] = f(X[r][c]) through a 32x32 tile.
+__global__ void convert_transpose_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                         int64_t ldx, void* __restrict__ Y,
+                                         void* __restrict__ Ylo, int64_t ldy, int kind,
+                                         const float* __restrict__ dscale) {
+  __shared__ float tile[32][33];
+  F32Out o{kind, dscale ? *dscale : 1.f};
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? X[r * ldx + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;  // output row c, column r
+    if (c < cols && r < rows) store_converted(o, tile[threadIdx.x][i], Y, Ylo, c * ldy + r);
+  }
+}
+
+// Element-type-preserving copy (optionally transposing) for 1/2/4-byte types.
+template <typename T>
+__global__ void copy_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                            T* __restrict__ Y, int64_t ldy) {
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t / cols, c = t % cols;
+    Y[r * ldy + c] = X[r * ldx + c];
+  }
+}
+
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                 T* __restrict__ Y, int64_t ldy) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = X[r * ldx + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) Y[c * ldy + r] = tile[threadIdx.x][i];
+  }
+}
+
+// amax(|X|) as float bits; non-negative floats order like their bit patterns.
+__global__ void amax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                            unsigned int* __restrict__ out_bits) {
+  float m = 0.f;
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t / cols, c = t % cols;
+    m = fmaxf(m, fabsf(X[r * ldx + c]));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  __shared__ float wmax[32];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  if (lane == 0) wmax[warp] = m;
+  __syncthreads();
+  if (warp == 0) {
+    m = (lane < static_cast<int>(blockDim.x / 32)) ? wmax[lane] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) atomicMax(out_bits, __float_as_uint(m));
+  }
+}
+
+// s = 448 / amax (1 when amax == 0); dequantisation factor 1 / s.
+__global__ void fp8_scale_kernel(const unsigned int* __restrict__ amax_bits,
+                                 float* __restrict__ scale, float* __restrict__ dequant) {
+  const float amax = __uint_as_float(*amax_bits);
+  const float s = (amax > 0.f) ? __fdiv_rn(448.0f, amax) : 1.0f;
+  *scale = s;
+  *dequant = __fdiv_rn(1.0f, s);
+}
+
+int grid_for(int64_t total) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8192)));
+}
+
+}  // namespace
+
+int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols, int64_t ldx,
+                    void* Y, int out_kind, int64_t ldy, bool transpose, void* Y_lo,
+                    const float* dscale, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return COMPAR_OK;
+  const dim3 tb(32, 8);
+  const dim3 tg(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
+  if (out_kind == PP_COPY) {
+    if (in_t == COMPAR_F32) {
+      if (transpose)
+        transpose_kernel<float><<<tg, tb, 0, s>>>(static_cast<const float*>(X), rows, cols, ldx,
+                                                  static_cast<float*>(Y), ldy);
+      else
+        copy_kernel<float><<<grid_for(rows * cols), 256, 0, s>>>(
+            static_cast<const float*>(X), rows, cols, ldx, static_cast<float*>(Y), ldy);
+    } else if (in_t == COMPAR_BF16) {
+      if (transpose)
+        transpose_kernel<uint16_t><<<tg, tb, 0, s>>>(static_cast<const uint16_t*>(X), rows, cols,
+                                                     ldx, static_cast<uint16_t*>(Y), ldy);
+      else
+        copy_kernel<uint16_t><<<grid_for(rows * cols), 256, 0, s>>>(
+            static_cast<const uint16_t*>(X), rows, cols, ldx, static_cast<uint16_t*>(Y), ldy);
+    } else {
+      if (transpose)
+        transpose_kernel<uint8_t><<<tg, tb, 0, s>>>(static_cast<const uint8_t*>(X), rows, cols,
+                                                    ldx, static_cast<uint8_t*>(Y), ldy);
+      else
+        copy_kernel<uint8_t><<<grid_for(rows * cols), 256, 0, s>>>(
+            static_cast<const uint8_t*>(X), rows, cols, ldx, static_cast<uint8_t*>(Y), ldy);
+    }
+  } else {
+    if (in_t != COMPAR_F32) return COMPAR_ERR_INVALID;
+    const float* Xf = static_cast<const float*>(X);
+    if (transpose)
+      convert_transpose_kernel<<<tg, tb, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, out_kind,
+                                                 dscale);
+    else
+      convert_rows_kernel<<<grid_for(rows * cols), 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy,
+                                                                out_kind, dscale);
+  }
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                 unsigned int* d_amax_bits, cudaStream_t s) {
+  COMPAR_CUDA_TRY(cudaMemsetAsync(d_amax_bits, 0, sizeof(unsigned int), s));
+  if (rows <= 0 || cols <= 0) return COMPAR_OK;
+  amax_kernel<<<std::min(grid_for(rows * cols), 1184), 256, 0, s>>>(X, rows, cols, ldx,
+                                                                   d_amax_bits);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_dequant,
+                      cudaStream_t s) {
+  fp8_scale_kernel<<<1, 1, 0, s>>>(d_amax_bits, d_scale, d_dequant);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  return COMPAR_OK;
+}
+
+}  // namespace compar

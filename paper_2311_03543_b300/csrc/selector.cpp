@@ -1,0 +1,255 @@
+// Cost and error models behind the variant choice: features, the error
+// model, the history table, the roofline prior, the recorder and the MLP
+// parameter container.  The paper's runtime chooses among variants with
+// performance models learned from earlier runs and notes that more training
+// of those models should improve the choice (Sec. 3.2, Sec. 5); the history
+// table is that kind of model, the MLP (selector_mlp.cpp) the learned one.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+
+#include "runtime.h"
+
+namespace compar {
+
+std::array<float, kNumFeatures> make_features(int64_t m, int64_t n, int64_t k, int dtype,
+                                              double tol, int batch) {
+  std::array<float, kNumFeatures> x{};
+  x[0] = static_cast<float>(std::log2(static_cast<double>(std::max<int64_t>(m, 1))));
+  x[1] = static_cast<float>(std::log2(static_cast<double>(std::max<int64_t>(n, 1))));
+  x[2] = static_cast<float>(std::log2(static_cast<double>(std::max<int64_t>(k, 1))));
+  x[3] = dtype == COMPAR_F32 ? 1.f : 0.f;
+  x[4] = dtype == COMPAR_BF16 ? 1.f : 0.f;
+  x[5] = dtype == COMPAR_F8E4M3 ? 1.f : 0.f;
+  x[6] = static_cast<float>(std::log10(std::max(tol, 1e-12)));
+  x[7] = static_cast<float>(std::log2(static_cast<double>(std::max(batch, 1))));
+  return x;
+}
+
+// ------------------------------------------------------------- error model
+// Defaults from the arithmetic of each variant (relative Frobenius error of
+// a product of random inputs; u = 2^-24 is float32's unit roundoff):
+//  * FP32 FMA variants and exact-product tensor-core variants on their own
+//    input type: only accumulation error, ~ sqrt(k) u.
+//  * TF32 on float32 inputs: operands keep 10 fraction bits, ~ 2^-11.
+//  * BF16 on float32 inputs: operands rounded to 8 significant bits, ~ 2^-9.
+//  * FP8 E4M3 on float32 inputs: 4 significant bits plus scaling, ~ 2^-5.
+//  * 3xBF16 on float32 inputs: the split keeps ~16 bits and drops lo*lo.
+ErrorModel::ErrorModel() {
+  const float inf = INFINITY;
+  for (auto& r : c0) r.fill(inf);
+  for (auto& r : c1) r.fill(0.f);
+  for (int d = 0; d < 3; ++d) {
+    c0[COMPAR_V_NAIVE][d] = 0.f;  c1[COMPAR_V_NAIVE][d] = 1.0f;
+    c0[COMPAR_V_SIMT][d] = 0.f;   c1[COMPAR_V_SIMT][d] = 1.0f;
+  }
+  c0[COMPAR_V_TC_TF32][COMPAR_F32] = 4e-4f;  c1[COMPAR_V_TC_TF32][COMPAR_F32] = 1.0f;
+  c0[COMPAR_V_TC_BF16][COMPAR_F32] = 3e-3f;  c1[COMPAR_V_TC_BF16][COMPAR_F32] = 1.0f;
+  c0[COMPAR_V_TC_BF16][COMPAR_BF16] = 0.f;   c1[COMPAR_V_TC_BF16][COMPAR_BF16] = 1.0f;
+  c0[COMPAR_V_TC_FP8][COMPAR_F32] = 4e-2f;   c1[COMPAR_V_TC_FP8][COMPAR_F32] = 1.0f;
+  c0[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 0.f;  c1[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 1.0f;
+  c0[COMPAR_V_SPLIT3][COMPAR_F32] = 3e-6f;   c1[COMPAR_V_SPLIT3][COMPAR_F32] = 1.0f;
+}
+
+double ErrorModel::predict(int v, int dtype, int64_t k) const {
+  if (v < 0 || v >= kNumVariants || dtype < 0 || dtype > 2) return INFINITY;
+  const double u = std::ldexp(1.0, -24);
+  return c0[v][dtype] + c1[v][dtype] * std::sqrt(static_cast<double>(std::max<int64_t>(k, 1))) * u;
+}
+
+// ------------------------------------------------------------- history
+bool HistKey::operator<(const HistKey& o) const {
+  return std::tie(v, dtype, lm, ln, lk, batch) < std::tie(o.v, o.dtype, o.lm, o.ln, o.lk, o.batch);
+}
+bool HistKey::operator==(const HistKey& o) const {
+  return v == o.v && dtype == o.dtype && lm == o.lm && ln == o.ln && lk == o.lk && batch == o.batch;
+}
+
+static int16_t qlog(int64_t x) {
+  return static_cast<int16_t>(std::lround(4.0 * std::log2(static_cast<double>(std::max<int64_t>(x, 1)))));
+}
+
+HistKey HistoryModel::key(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch) {
+  HistKey h;
+  h.v = static_cast<int8_t>(v);
+  h.dtype = static_cast<int8_t>(dtype);
+  h.lm = qlog(m);
+  h.ln = qlog(n);
+  h.lk = qlog(k);
+  h.batch = static_cast<int8_t>(std::min(31, static_cast<int>(std::log2(std::max(batch, 1)))));
+  return h;
+}
+
+void HistoryModel::observe(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch, double ms) {
+  HistVal& e = table[key(v, dtype, m, n, k, batch)];
+  e.count += 1;
+  const double d = ms - e.mean_ms;
+  e.mean_ms += d / static_cast<double>(e.count);
+  e.m2 += d * (ms - e.mean_ms);
+}
+
+double HistoryModel::predict(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch,
+                             bool* exact) const {
+  const HistKey q = key(v, dtype, m, n, k, batch);
+  if (exact) *exact = false;
+  auto it = table.find(q);
+  if (it != table.end()) {
+    if (exact) *exact = true;
+    return it->second.mean_ms;
+  }
+  // nearest neighbour among keys of the same variant / dtype / batch bucket
+  HistKey lo = q, hi = q;
+  lo.lm = lo.ln = lo.lk = INT16_MIN;
+  hi.lm = hi.ln = hi.lk = INT16_MAX;
+  int best = INT32_MAX;
+  double best_ms = -1;
+  for (auto i = table.lower_bound(lo); i != table.end() && !(hi < i->first); ++i) {
+    const HistKey& h = i->first;
+    if (h.batch != q.batch) continue;
+    const int d = std::abs(h.lm - q.lm) + std::abs(h.ln - q.ln) + std::abs(h.lk - q.lk);
+    if (d < best) {
+      best = d;
+      // scale by the work ratio 2^((dq)/4) per axis
+      const double ratio = std::exp2((q.lm - h.lm + q.ln - h.ln + q.lk - h.lk) / 4.0);
+      best_ms = i->second.mean_ms * ratio;
+    }
+  }
+  if (best <= kMaxDist) return best_ms;
+  return -1;
+}
+
+// ------------------------------------------------------------- roofline prior
+double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_sms) {
+  const double M = static_cast<double>(m), N = static_cast<double>(n), K = static_cast<double>(k);
+  const double bw = 6.0e12;  // bytes/s
+  const double in_elem = dtype == COMPAR_F32 ? 4 : (dtype == COMPAR_BF16 ? 2 : 1);
+  double flops = 2 * M * N * K, peak = 1, bytes = (M * K + K * N) * in_elem + M * N * 4;
+  double ovh_us = 4;
+  auto tiles = [&](int bm, int bn) {
+    const double t = std::ceil(M / bm) * std::ceil(N / bn);
+    return std::ceil(t / num_sms) * num_sms;  // wave quantisation
+  };
+  switch (v) {
+    case COMPAR_V_NAIVE:
+      peak = 4e12;
+      break;
+    case COMPAR_V_SIMT:
+      peak = 45e12;
+      flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
+      break;
+    case COMPAR_V_TC_TF32:
+      peak = 0.8e15;
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += K * N * 8;
+      ovh_us = 12;
+      break;
+    case COMPAR_V_TC_BF16:
+      peak = 1.5e15;
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += (dtype == COMPAR_F32 ? (M * K + K * N) * 6 : K * N * 4);
+      ovh_us = 14;
+      break;
+    case COMPAR_V_TC_FP8:
+      peak = 3.0e15;
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += (dtype == COMPAR_F32 ? (M * K + K * N) * 9 : K * N * 2);
+      ovh_us = dtype == COMPAR_F32 ? 24 : 14;
+      break;
+    case COMPAR_V_SPLIT3:
+      peak = 1.5e15 / 3;
+      flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
+      bytes += (M * K + K * N) * 8;
+      ovh_us = 14;
+      break;
+    default:
+      return INFINITY;
+  }
+  return 1e3 * std::max(flops / peak, bytes / bw) + ovh_us * 1e-3;
+}
+
+// ------------------------------------------------------------- recorder
+void Recorder::push(const compar_record_t& r) {
+  if (static_cast<int64_t>(ring.size()) < kCap) {
+    ring.push_back(r);
+    size = static_cast<int64_t>(ring.size());
+    head = 0;
+    return;
+  }
+  ring[head] = r;  // full: overwrite the oldest
+  head = (head + 1) % kCap;
+}
+
+std::vector<compar_record_t> Recorder::snapshot() const {
+  std::vector<compar_record_t> out;
+  out.reserve(ring.size());
+  for (int64_t i = 0; i < static_cast<int64_t>(ring.size()); ++i)
+    out.push_back(ring[(head + i) % ring.size()]);
+  return out;
+}
+
+size_t DecisionKeyHash::operator()(const DecisionKey& d) const {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    h ^= x;
+    h *= 1099511628211ull;
+  };
+  mix(static_cast<uint64_t>(d.m));
+  mix(static_cast<uint64_t>(d.n));
+  mix(static_cast<uint64_t>(d.k));
+  mix(static_cast<uint64_t>(d.dtype));
+  mix(static_cast<uint64_t>(d.tol_class));
+  mix(static_cast<uint64_t>(d.batch));
+  return static_cast<size_t>(h);
+}
+
+// ------------------------------------------------------------- MLP params
+size_t MlpParams::count() {
+  return static_cast<size_t>(kHidden) * kNumFeatures + kHidden + kHidden * kHidden + kHidden +
+         static_cast<size_t>(kOutputs) * kHidden + kOutputs;
+}
+
+// He-uniform weights from a splitmix64 stream, zero biases.
+void MlpParams::init(uint64_t seed) {
+  uint64_t s = seed;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0);  // [0,1)
+  };
+  auto fill = [&](std::vector<float>& w, int o, int i) {
+    w.resize(static_cast<size_t>(o) * i);
+    const double bound = std::sqrt(6.0 / i);
+    for (auto& x : w) x = static_cast<float>((2 * next() - 1) * bound);
+  };
+  fill(W1, kHidden, kNumFeatures);
+  b1.assign(kHidden, 0.f);
+  fill(W2, kHidden, kHidden);
+  b2.assign(kHidden, 0.f);
+  fill(W3, kOutputs, kHidden);
+  b3.assign(kOutputs, 0.f);
+}
+
+void MlpParams::flatten(std::vector<float>& out) const {
+  out.clear();
+  out.reserve(count());
+  for (auto* v : {&W1, &b1, &W2, &b2, &W3, &b3}) out.insert(out.end(), v->begin(), v->end());
+}
+
+void MlpParams::unflatten(const float* p) {
+  auto take = [&](std::vector<float>& v, size_t n) {
+    v.assign(p, p + n);
+    p += n;
+  };
+  take(W1, static_cast<size_t>(kHidden) * kNumFeatures);
+  take(b1, kHidden);
+  take(W2, static_cast<size_t>(kHidden) * kHidden);
+  take(b2, kHidden);
+  take(W3, static_cast<size_t>(kOutputs) * kHidden);
+  take(b3, kOutputs);
+}
+
+}  // namespace compar

@@ -1,0 +1,205 @@
+"""Parity of every GEMM variant with the FP64 oracle (GPU, through the C ABI).
+
+Tolerances (relative Frobenius error):
+* FP32-accurate variants (naive, SIMT, 3xBF16) on float32 inputs: <= 1e-5
+  against the oracle on the float32 values.
+* BF16 / FP8 tensor-core variants: <= 1e-5 against the oracle evaluated on
+  the exact values the kernel multiplies (its inputs as given, or the oracle's
+  own bf16 rounding / e4m3 quantisation of the float32 inputs) — only FP32
+  accumulation error remains; the total error against the float32 values is
+  reported and bounded by the format's rounding (2^-8, 2^-4 relative).
+* TF32 (tensor cores read 10 fraction bits): total error <= 2e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import numerics as N
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2311_03543_b300 as cp
+    c = cp.Context(0)
+    yield c
+    c.close()
+
+
+def _run(ctx, v, A, B, dtype=None, alpha=1.0, beta=0.0, C0=None, tol=0.0):
+    from gpu_util import dev, empty_c, host
+    import paper_2311_03543_b300 as cp
+    m, n = A.shape[0], B.shape[1]
+    C = dev(C0.astype(np.float32)) if C0 is not None else empty_c(m, n)
+    ctx.set_scalars(alpha, beta)
+    ctx.force_variant(v)
+    try:
+        ctx.gemm(dev(A), dev(B), C, tol=tol, dtype=dtype)
+        out = host(C)
+    finally:
+        ctx.force_variant(None)
+        ctx.set_scalars(1.0, 0.0)
+    assert ctx.check_device_error() == cp.OK
+    return out
+
+
+SHAPES = [(1, 1, 1), (3, 5, 7), (16, 16, 16), (33, 65, 17), (127, 129, 130),
+          (255, 257, 256), (256, 256, 256), (300, 200, 1000), (129, 520, 64)]
+
+
+@pytest.mark.parametrize("v", [0, 1, 5])
+@pytest.mark.parametrize("m,n,k", SHAPES)
+def test_fp32_accurate_variants(ctx, v, m, n, k):
+    A = W.uniform(m, k, seed=100 + m); B = W.uniform(k, n, seed=200 + n)
+    got = _run(ctx, v, A, B)
+    ref = oracle.gemm(A, B)
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
+def test_config1_naive_then_simt(ctx):
+    """256^3, uniform[-1,1] seed 1, alpha=1 beta=0; naive and SIMT forced in turn."""
+    m, n, k = W.PARITY_256
+    A = W.uniform(m, k, seed=1); B = W.uniform(k, n, seed=1001)
+    ref = oracle.gemm(A, B)
+    for v in (0, 1):
+        assert N.rel_frobenius(_run(ctx, v, A, B), ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
+                                   (256, 512, 1024)])
+def test_tf32_total_error(ctx, m, n, k):
+    A = W.uniform(m, k, seed=3 + m); B = W.uniform(k, n, seed=4 + n)
+    err = N.rel_frobenius(_run(ctx, 2, A, B), oracle.gemm(A, B))
+    assert err <= 2e-3
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
+                                   (256, 512, 1024)])
+def test_bf16_on_f32_inputs(ctx, m, n, k):
+    A = W.uniform(m, k, seed=5 + m); B = W.uniform(k, n, seed=6 + n)
+    got = _run(ctx, 3, A, B)
+    exact_inputs = oracle.gemm(N.bf16_round(A), N.bf16_round(B))
+    assert N.rel_frobenius(got, exact_inputs) <= TOL_F32
+    assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 2.0 ** -7
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 8), (17, 40, 24), (128, 256, 64), (200, 300, 336),
+                                   (256, 512, 1024), (100, 90, 13)])
+def test_bf16_native_inputs(ctx, m, n, k):
+    import paper_2311_03543_b300 as cp
+    A = W.bf16_input(m, k, seed=7 + m); B = W.bf16_input(k, n, seed=8 + n)
+    got = _run(ctx, 3, A, B, dtype=cp.BF16)
+    ref = oracle.gemm(N.bf16_to_f32(A), N.bf16_to_f32(B))
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 16), (17, 40, 48), (128, 256, 128), (200, 300, 336),
+                                   (256, 512, 1024), (100, 90, 13)])
+def test_fp8_native_inputs_with_scales(ctx, m, n, k):
+    import paper_2311_03543_b300 as cp
+    A = W.fp8_input(m, k, seed=9 + m); B = W.fp8_input(k, n, seed=10 + n)
+    ctx.set_fp8_scales(0.5, 0.25)
+    try:
+        got = _run(ctx, 4, A, B, dtype=cp.F8E4M3)
+    finally:
+        ctx.set_fp8_scales(1.0, 1.0)
+    ref = 0.125 * oracle.gemm(N.e4m3_to_f64(A), N.e4m3_to_f64(B))
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
+                                   (256, 512, 1024)])
+def test_fp8_on_f32_inputs(ctx, m, n, k):
+    A = W.normal(m, k, seed=11 + m); B = W.normal(k, n, seed=12 + n)
+    got = _run(ctx, 4, A, B)
+    qa, sa = N.fp8_quantize(A); qb, sb = N.fp8_quantize(B)
+    exact_inputs = oracle.gemm(N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)) / (float(sa) * float(sb))
+    assert N.rel_frobenius(got, exact_inputs) <= TOL_F32
+    assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 0.1
+
+
+def test_split3_matches_its_three_products(ctx):
+    m, n, k = 192, 320, 512
+    A = W.uniform(m, k, seed=13); B = W.uniform(k, n, seed=14)
+    got = _run(ctx, 5, A, B)
+    ah, al, bh, bl = N.split3_operands(A, B)
+    three = oracle.gemm(ah, bh) + oracle.gemm(ah, bl) + oracle.gemm(al, bh)
+    assert N.rel_frobenius(got, three) <= TOL_F32
+
+
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5])
+def test_all_ones_every_entry_is_k(ctx, v):
+    m, n, k = 130, 260, 300
+    got = _run(ctx, v, np.ones((m, k), np.float32), np.ones((k, n), np.float32))
+    if v == 4:   # fp8 of float32 input: the dequantisation factor 1/448 is inexact
+        assert np.allclose(got, k, rtol=1e-6, atol=0)
+    else:
+        assert np.all(got == k)
+
+
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 5])
+def test_identity_exact_on_representable_values(ctx, v):
+    n = 192
+    A = W.integer_matrix(n, n, seed=15)           # integers are exact in every format
+    got = _run(ctx, v, A, np.eye(n, dtype=np.float32))
+    assert np.array_equal(got, A)
+
+
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5])
+def test_alpha_beta(ctx, v):
+    m, n, k = 70, 90, 110
+    A = W.integer_matrix(m, k, seed=16, bound=4)
+    B = W.integer_matrix(k, n, seed=17, bound=4)
+    C0 = W.integer_matrix(m, n, seed=18)
+    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
+    ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
+    tol = 1e-1 if v == 4 else TOL_F32   # fp8 quantises integers up to 16 exactly
+    assert N.rel_frobenius(got, ref) <= tol
+
+
+def test_k_zero_scales_c(ctx):
+    from gpu_util import dev, host
+    import torch
+    C = dev(np.full((5, 6), 2.0, np.float32))
+    ctx.set_scalars(1.0, 3.0)
+    try:
+        ctx.gemm(torch.zeros((5, 0), device="cuda"), torch.zeros((0, 6), device="cuda"), C)
+    finally:
+        ctx.set_scalars(1.0, 0.0)
+    assert np.all(host(C) == 6.0)
+
+
+def test_empty_m_or_n_is_a_no_op(ctx):
+    import torch
+    C = torch.zeros((0, 4), device="cuda")
+    ctx.gemm(torch.zeros((0, 3), device="cuda"), torch.zeros((3, 4), device="cuda"), C)
+
+
+def test_forced_unsupported_variant_is_refused(ctx):
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev, empty_c
+    ctx.force_variant(cp.V_SPLIT3)
+    try:
+        with pytest.raises(cp.ComparError) as e:
+            ctx.gemm(dev(W.bf16_input(8, 8, 1)), dev(W.bf16_input(8, 8, 2)), empty_c(8, 8),
+                     dtype=cp.BF16)
+        assert e.value.status == cp.ERR_UNSUPPORTED
+    finally:
+        ctx.force_variant(None)
+
+
+@pytest.mark.parametrize("v,m,n,k", [(1, 4096, 4096, 64), (1, 16, 4096, 4096),
+                                     (5, 4096, 4096, 64), (5, 16, 4096, 4096),
+                                     (5, 2048, 2048, 2048), (1, 2048, 2048, 2048)])
+def test_sweep_shapes_sampled_rows(ctx, v, m, n, k):
+    """Full-size sweep shapes, checked on 32 seeded rows against the oracle."""
+    A = W.uniform(m, k, seed=20); B = W.uniform(k, n, seed=21)
+    got = _run(ctx, v, A, B)
+    rows = W.sample_rows(m, 32, seed=22)
+    ref = oracle.gemm_rows(A, B, rows)
+    assert N.rel_frobenius(got[rows], ref) <= TOL_F32
+    assert np.all(np.isfinite(got))
