@@ -227,6 +227,22 @@ int compar_record_add(compar_ctx_t ctx, const compar_record_t* recs,
                       int64_t count);
 int compar_record_clear(compar_ctx_t ctx);
 
+/* ---------------------------------------------------------------- profiling */
+
+/* Kernel timing: when on, the main GEMM kernel of every call (not its
+ * operand pre-passes) is bracketed by CUDA events on the call's stream and
+ * its duration added to a per-variant total.  Off by default. */
+int compar_profile_enable(compar_ctx_t ctx, int on);
+/* Total kernel milliseconds and number of timed launches of `variant` since
+ * the last reset (synchronises on the pending events). */
+int compar_profile_read(compar_ctx_t ctx, int variant, double* kernel_ms,
+                        int64_t* launches);
+int compar_profile_reset(compar_ctx_t ctx);
+
+/* Number of CUDA kernels this library has launched in this process (every
+ * variant kernel and every pre-pass kernel). */
+int64_t compar_launch_count(void);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Read and clear the device error word after synchronising `stream`.

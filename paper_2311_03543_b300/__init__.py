@@ -80,6 +80,10 @@ SIGNATURES = {
     "compar_check_device_error": (_i, [_vp, _vp]),
     "compar_set_wait_budget": (_i, [_vp, _u64]),
     "compar_selftest_timeout": (_i, [_vp, _vp]),
+    "compar_profile_enable": (_i, [_vp, _i]),
+    "compar_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
+    "compar_profile_reset": (_i, [_vp]),
+    "compar_launch_count": (_i64, []),
 }
 
 _lib = None
@@ -271,6 +275,20 @@ class Context:
 
     def set_wait_budget(self, ns):
         return _status(compar_set_wait_budget(self.handle, int(ns)), "set_wait_budget")
+
+    # -- kernel profiling ------------------------------------------------------
+    def profile_enable(self, on=True):
+        return _status(compar_profile_enable(self.handle, 1 if on else 0), "profile_enable")
+
+    def profile_read(self, variant):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _status(compar_profile_read(self.handle, variant, ctypes.byref(ms), ctypes.byref(n)),
+                "profile_read")
+        return ms.value, n.value
+
+    def profile_reset(self):
+        return _status(compar_profile_reset(self.handle), "profile_reset")
 
     def selftest_timeout(self, stream=None):
         return _status(compar_selftest_timeout(self.handle, _stream_handle(stream)),

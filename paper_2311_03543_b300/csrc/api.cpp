@@ -81,8 +81,8 @@ static int launch_variant(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_
     return COMPAR_ERR_CUDA;
   }
   switch (v) {
-    case COMPAR_V_NAIVE: return launch_naive(c, s);
-    case COMPAR_V_SIMT: return launch_simt(c, ctx->ws, ctx->num_sms, s);
+    case COMPAR_V_NAIVE: return launch_naive(c, ctx->guard, s);
+    case COMPAR_V_SIMT: return launch_simt(c, ctx->ws, ctx->guard, ctx->num_sms, s);
     case COMPAR_V_TC_TF32:
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
@@ -315,6 +315,7 @@ int compar_init(compar_ctx_t* out, int device) {
   COMPAR_CUDA_TRY(cudaSetDevice(device));
   auto* ctx = new compar_ctx();
   ctx->device = device;
+  ctx->guard.prof = &ctx->prof;
   ctx->num_sms = prop.multiProcessorCount;
   if (cudaMalloc(&ctx->guard.err_word, sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->guard.err_word, 0, sizeof(int)) != cudaSuccess) {
@@ -345,6 +346,7 @@ int compar_terminate(compar_ctx_t ctx) {
   cudaDeviceSynchronize();
   resolve_pending(ctx);
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  ctx->prof.release();
   batched_release(ctx);
   mlp_release(ctx);
   ctx->ws.release();

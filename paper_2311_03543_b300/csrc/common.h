@@ -47,15 +47,42 @@ struct Workspace {
   void release();
 };
 
+// ------------------------------------------------------------- profiling
+// Optional CUDA-event timing of the main GEMM kernel of each call (not its
+// pre-passes), accumulated per variant and resolved lazily.
+struct KernelProfiler {
+  static constexpr int kSlots = 8;
+  bool on = false;
+  struct Pend {
+    cudaEvent_t a, b;
+    int v;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pend> pend;
+  double total_ms[kSlots] = {};
+  int64_t launches[kSlots] = {};
+  cudaEvent_t begin(cudaStream_t s);
+  void end(cudaEvent_t a, cudaStream_t s, int v);
+  void resolve();
+  void reset();
+  void release();
+};
+
+// Process-wide count of kernels this library launched.
+void count_launch(int n = 1);
+int64_t launch_count();
+
 // ------------------------------------------------------------- kernel entry
 // Each returns a compar_status_t; all are asynchronous on `s`.
 struct DeviceGuard {  // device error word + wait budget handed to kernels
   int* err_word = nullptr;
   unsigned long long budget_ns = 2000000000ull;
+  KernelProfiler* prof = nullptr;
 };
 
-int launch_naive(const GemmCall& c, cudaStream_t s);
-int launch_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s);
+int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
+int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
+                cudaStream_t s);
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s);
 
 // Tensor-core variants (tcgen05).  kind: COMPAR_V_TC_TF32 / TC_BF16 / TC_FP8 / SPLIT3.

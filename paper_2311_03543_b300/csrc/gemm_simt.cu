@@ -243,7 +243,8 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
 }
 
 template <int BM, int BN, int BK, int TM, int TN>
-int run_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
+int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
+             cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
   const int tiles = tiles_m * tiles_n;
@@ -273,6 +274,7 @@ int run_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
   constexpr int threads = SimtCfg<BM, BN, BK, TM, TN, true>::kThreads;
   const float* A = static_cast<const float*>(c.A);
   const float* B = static_cast<const float*>(c.B);
+  cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   if (vec)
     gemm_simt_kernel<BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
         M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
@@ -280,20 +282,24 @@ int run_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
     gemm_simt_kernel<BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
         M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  if (g.prof) g.prof->end(ev, s, COMPAR_V_SIMT);
+  count_launch();
   if (splits > 1) {
     const int64_t total = static_cast<int64_t>(M) * N;
     const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
     splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, partial, c.alpha, c.beta, c.C,
                                                 c.ldc);
     COMPAR_CUDA_TRY(cudaGetLastError());
+    count_launch();
   }
   return COMPAR_OK;
 }
 
 }  // namespace
 
-int launch_naive(const GemmCall& c, cudaStream_t s) {
+int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
   dim3 block(16, 16);
+  cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   dim3 grid(static_cast<unsigned>((c.n + 15) / 16), static_cast<unsigned>((c.m + 15) / 16));
   gemm_naive_kernel<<<grid, block, 0, s>>>(static_cast<int>(c.m), static_cast<int>(c.n),
                                            static_cast<int>(c.k), c.alpha,
@@ -301,13 +307,16 @@ int launch_naive(const GemmCall& c, cudaStream_t s) {
                                            static_cast<const float*>(c.B), c.ldb, c.beta, c.C,
                                            c.ldc);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  if (g.prof) g.prof->end(ev, s, COMPAR_V_NAIVE);
+  count_launch();
   return COMPAR_OK;
 }
 
-int launch_simt(const GemmCall& c, Workspace& ws, int num_sms, cudaStream_t s) {
+int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
+                cudaStream_t s) {
   // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
-  if (c.m <= 48) return run_simt<32, 128, 32, 4, 8>(c, ws, num_sms, s);
-  return run_simt<128, 128, 16, 8, 8>(c, ws, num_sms, s);
+  if (c.m <= 48) return run_simt<32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
+  return run_simt<128, 128, 16, 8, 8>(c, ws, g, num_sms, s);
 }
 
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s) {
@@ -315,6 +324,7 @@ int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cuda
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
   scale_c_kernel<<<blocks, 256, 0, s>>>(C, static_cast<int>(m), static_cast<int>(n), ldc, beta);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return COMPAR_OK;
 }
 

@@ -44,22 +44,22 @@ struct Traits;
 template <>
 struct Traits<COMPAR_V_TC_TF32> {
   static constexpr Kind kind = Kind::TF32;
-  static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256;
+  static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, chunk_kb = 0;
 };
 template <>
 struct Traits<COMPAR_V_TC_BF16> {
   static constexpr Kind kind = Kind::F16;
-  static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256;
+  static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, chunk_kb = 0;
 };
 template <>
 struct Traits<COMPAR_V_TC_FP8> {
   static constexpr Kind kind = Kind::F8;
-  static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256;
+  static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, chunk_kb = 0;
 };
 template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
-  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 128;
+  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 128, chunk_kb = 4;  // promote every 256 K elements
 };
 
 template <int V>
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int P = T::pieces;
   constexpr int BN = T::BN;
   constexpr int S = L::kStages;
+  constexpr int kChunkKB = T::chunk_kb;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -214,50 +215,54 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t idesc = dev::make_idesc(T::fmt, T::fmt, kBM, BN);
     uint32_t stage = 0, phase = 0;
-    int local = 0;
+    int acc_iter = 0;  // accumulator-buffer uses (one per K chunk)
+    const int chunk = kChunkKB > 0 ? kChunkKB : p.num_kb;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x, ++local) {
-      const uint32_t acc = local & 1;
-      const uint32_t acc_phase = (local >> 1) & 1;
-      if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
-        ok = false;
-        break;
-      }
-      dev::tc_fence_after();
-      const uint32_t d_tmem = tmem_base + acc * BN;
-      for (int kb = 0; kb < p.num_kb; ++kb) {
-        if (!dev::mbar_wait(&full[stage], phase, w)) {
+    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      for (int kb0 = 0; ok && kb0 < p.num_kb; kb0 += chunk, ++acc_iter) {
+        const uint32_t acc = acc_iter & 1;
+        const uint32_t acc_phase = (acc_iter >> 1) & 1;
+        if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
           ok = false;
           break;
         }
         dev::tc_fence_after();
-        const uint32_t a0 = dev::smem_u32(sA + (stage * P) * L::kABytes);
-        const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
-        const uint64_t da = dev::smem_desc_sw128_kmajor(a0);
-        const uint64_t db = dev::smem_desc_sw128_kmajor(b0);
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        const int kb_end = min(p.num_kb, kb0 + chunk);
+        for (int kb = kb0; kb < kb_end; ++kb) {
+          if (!dev::mbar_wait(&full[stage], phase, w)) {
+            ok = false;
+            break;
+          }
+          dev::tc_fence_after();
+          const uint32_t a0 = dev::smem_u32(sA + (stage * P) * L::kABytes);
+          const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
+          const uint64_t da = dev::smem_desc_sw128_kmajor(a0);
+          const uint64_t db = dev::smem_desc_sw128_kmajor(b0);
 #pragma unroll
-        for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-          // each instruction consumes 32 bytes of K; advance the start address
-          const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
-          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-          if constexpr (P == 2) {
-            const uint64_t da_lo = dev::smem_desc_sw128_kmajor(a0 + L::kABytes);
-            const uint64_t db_lo = dev::smem_desc_sw128_kmajor(b0 + L::kBBytes);
-            dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
-            dev::mma<T::kind>(d_tmem, da + koff, db_lo + koff, idesc, 1u);
-            dev::mma<T::kind>(d_tmem, da_lo + koff, db + koff, idesc, 1u);
-          } else {
-            dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+            // each instruction consumes 32 bytes of K; advance the start address
+            const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
+            const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
+            if constexpr (P == 2) {
+              const uint64_t da_lo = dev::smem_desc_sw128_kmajor(a0 + L::kABytes);
+              const uint64_t db_lo = dev::smem_desc_sw128_kmajor(b0 + L::kBBytes);
+              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+              dev::mma<T::kind>(d_tmem, da + koff, db_lo + koff, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, da_lo + koff, db + koff, idesc, 1u);
+            } else {
+              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+            }
+          }
+          dev::mma_commit(&empty[stage]);  // stage reusable once these MMAs finish
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
           }
         }
-        dev::mma_commit(&empty[stage]);  // stage reusable once these MMAs finish
-        if (++stage == S) {
-          stage = 0;
-          phase ^= 1;
-        }
+        if (!ok) break;
+        dev::mma_commit(&tfull[acc]);  // chunk accumulator ready for the epilogue
       }
-      if (!ok) break;
-      dev::mma_commit(&tfull[acc]);  // accumulator ready for the epilogue
     }
     // All MMAs issued by this thread complete before TMEM is released.
     dev::mma_commit(drain);
@@ -270,17 +275,79 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (p.dequant_b) alpha *= *p.dequant_b;
     const bool vec = (p.N % 4 == 0) && (p.ldc % 4 == 0) &&
                      ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0);
-    int local = 0;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
-      const uint32_t acc = local & 1;
-      const uint32_t acc_phase = (local >> 1) & 1;
-      if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
-      dev::tc_fence_after();
+    int acc_iter = 0;
+    const int num_chunks = kChunkKB > 0 ? (p.num_kb + kChunkKB - 1) / kChunkKB : 1;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       int mb, nb;
       tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
       const int row = mb * kBM + quarter * 32 + lane;
-      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
       float* crow = p.C + static_cast<int64_t>(row) * p.ldc;
+      if constexpr (kChunkKB > 0) {
+        // Promotion: each K chunk's TMEM partial sum is added into FP32
+        // registers (round to nearest), so the tensor core's accumulator
+        // only ever sums kChunkKB k-blocks.
+        float sum[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+        for (int ch = 0; ch < num_chunks; ++ch, ++acc_iter) {
+          const uint32_t acc = acc_iter & 1;
+          const uint32_t acc_phase = (acc_iter >> 1) & 1;
+          if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) {
+            ok = false;
+            break;
+          }
+          dev::tc_fence_after();
+          const uint32_t t_row =
+              tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+#pragma unroll
+          for (int c = 0; c < BN / 32; ++c) {
+            uint32_t r[32];
+            dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+            dev::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __uint_as_float(r[j]);
+          }
+          dev::tc_fence_before();
+          dev::mbar_arrive(&tempty[acc]);
+        }
+        if (!ok) break;
+        const int col0 = nb * BN;
+        if (row < p.M) {
+          if (vec && col0 + BN <= p.N) {
+#pragma unroll
+            for (int j = 0; j < BN; j += 4) {
+              float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
+              float4 o = make_float4(alpha * sum[j], alpha * sum[j + 1], alpha * sum[j + 2],
+                                     alpha * sum[j + 3]);
+              if (p.beta != 0.f) {
+                const float4 old = *dst;
+                o.x = fmaf(p.beta, old.x, o.x);
+                o.y = fmaf(p.beta, old.y, o.y);
+                o.z = fmaf(p.beta, old.z, o.z);
+                o.w = fmaf(p.beta, old.w, o.w);
+              }
+              *dst = o;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+              if (col0 + j < p.N) {
+                float v = alpha * sum[j];
+                if (p.beta != 0.f) v = fmaf(p.beta, crow[col0 + j], v);
+                crow[col0 + j] = v;
+              }
+            }
+          }
+        }
+        continue;
+      }
+      const uint32_t acc = acc_iter & 1;
+      const uint32_t acc_phase = (acc_iter >> 1) & 1;
+      ++acc_iter;
+      if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
+      dev::tc_fence_after();
+      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
@@ -406,8 +473,11 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.budget_ns = g.budget_ns;
   const int tiles = a.tiles_m * a.tiles_n;
   const int grid = std::min(tiles, num_sms);
+  cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   tc_gemm_kernel<V><<<grid, kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, a);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  if (g.prof) g.prof->end(ev, s, V);
+  count_launch();
   return COMPAR_OK;
 }
 
@@ -512,6 +582,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
 int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s) {
   timeout_selftest_kernel<<<1, 32, 0, s>>>(g.err_word, g.budget_ns);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return COMPAR_OK;
 }
 

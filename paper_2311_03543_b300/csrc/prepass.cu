@@ -194,6 +194,7 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
                                                                 out_kind, dscale);
   }
   COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return COMPAR_OK;
 }
 
@@ -204,6 +205,7 @@ int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
   amax_kernel<<<std::min(grid_for(rows * cols), 1184), 256, 0, s>>>(X, rows, cols, ldx,
                                                                    d_amax_bits);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return COMPAR_OK;
 }
 
@@ -211,6 +213,7 @@ int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_
                       cudaStream_t s) {
   fp8_scale_kernel<<<1, 1, 0, s>>>(d_amax_bits, d_scale, d_dequant);
   COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return COMPAR_OK;
 }
 

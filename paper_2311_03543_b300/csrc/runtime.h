@@ -36,7 +36,7 @@ std::array<float, kNumFeatures> make_features(int64_t m, int64_t n, int64_t k, i
 struct ErrorModel {
   std::array<std::array<float, 3>, kNumVariants> c0{};
   std::array<std::array<float, 3>, kNumVariants> c1{};
-  float margin = 2.0f;  // eligibility: predicted * margin <= tol
+  float margin = 1.5f;  // eligibility: predicted * margin <= tol
   ErrorModel();
   double predict(int v, int dtype, int64_t k) const;
 };
@@ -135,6 +135,7 @@ struct compar_ctx {
   std::array<bool, compar::kNumVariants> quarantined{};
   compar::Workspace ws;
   compar::DeviceGuard guard;
+  compar::KernelProfiler prof;
   compar::ErrorModel err;
   compar::HistoryModel hist;
   compar::MlpModel mlp;

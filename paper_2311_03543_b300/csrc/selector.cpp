@@ -49,7 +49,7 @@ ErrorModel::ErrorModel() {
   c0[COMPAR_V_TC_BF16][COMPAR_BF16] = 0.f;   c1[COMPAR_V_TC_BF16][COMPAR_BF16] = 1.0f;
   c0[COMPAR_V_TC_FP8][COMPAR_F32] = 4e-2f;   c1[COMPAR_V_TC_FP8][COMPAR_F32] = 1.0f;
   c0[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 0.f;  c1[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 1.0f;
-  c0[COMPAR_V_SPLIT3][COMPAR_F32] = 3e-6f;   c1[COMPAR_V_SPLIT3][COMPAR_F32] = 1.0f;
+  c0[COMPAR_V_SPLIT3][COMPAR_F32] = 3e-6f;   c1[COMPAR_V_SPLIT3][COMPAR_F32] = 0.3f;
 }
 
 double ErrorModel::predict(int v, int dtype, int64_t k) const {
