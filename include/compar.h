@@ -89,6 +89,13 @@ enum {
  * sm_103) or COMPAR_ERR_CUDA. */
 int compar_init(compar_ctx_t* out, int device);
 
+/* Create a HOST-ONLY context: no CUDA call is made and no device is needed.
+ * Selection (compar_select), cost-model files, records and the error model
+ * work; every compute call returns COMPAR_ERR_UNSUPPORTED.  `num_sms` is the
+ * SM count the roofline prior assumes (<= 0: 148, one B300).  For offline
+ * tooling and for testing the runtime's host logic. */
+int compar_init_host(compar_ctx_t* out, int num_sms);
+
 /* Release the context and everything it owns (Sec. 2.1, `terminate`
  * directive -> compar_terminate()).  Synchronises the device first.
  * NULL is accepted and ignored. */
@@ -180,6 +187,28 @@ int compar_variant_supported(compar_ctx_t ctx, int variant_id, int64_t m,
 
 /* Drop every cached selection decision. */
 int compar_clear_decisions(compar_ctx_t ctx);
+
+/* The variant compar_gemm would run for this context, without running it
+ * (forced variant, decision cache, MLP, history table, roofline prior, in that
+ * order; caches the decision like compar_gemm).  `batch` is the batch-count
+ * feature (1 for single calls).  Returns a variant id or a negative status
+ * (COMPAR_ERR_NO_VARIANT when nothing meets tol). */
+int compar_select(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
+                  compar_dtype_t dtype, double tol, int batch);
+
+/* Error model used for eligibility: predicted relative Frobenius error of
+ * `variant` on `dtype` inputs with inner dimension k is
+ *     c0 + c1 * sqrt(k) * 2^-24 + c2 * k * 2^-24,
+ * and a variant is eligible when prediction * margin <= tol.  c0 = +inf
+ * marks (variant, dtype) pairs that can never meet any tolerance. */
+int compar_error_model_set(compar_ctx_t ctx, int variant, compar_dtype_t dtype,
+                           double c0, double c1, double c2);
+int compar_error_model_get(compar_ctx_t ctx, int variant, compar_dtype_t dtype,
+                           double* c0, double* c1, double* c2);
+int compar_error_model_set_margin(compar_ctx_t ctx, double margin);
+/* Predicted relative error of `variant` for (dtype, k); < 0 on bad input. */
+double compar_error_model_predict(compar_ctx_t ctx, int variant,
+                                  compar_dtype_t dtype, int64_t k);
 
 /* ---------------------------------------------------------------- models */
 

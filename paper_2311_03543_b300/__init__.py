@@ -80,6 +80,13 @@ SIGNATURES = {
     "compar_check_device_error": (_i, [_vp, _vp]),
     "compar_set_wait_budget": (_i, [_vp, _u64]),
     "compar_selftest_timeout": (_i, [_vp, _vp]),
+    "compar_init_host": (_i, [ctypes.POINTER(_vp), _i]),
+    "compar_select": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i]),
+    "compar_error_model_set": (_i, [_vp, _i, _i, _d, _d, _d]),
+    "compar_error_model_get": (_i, [_vp, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                    ctypes.POINTER(_d)]),
+    "compar_error_model_set_margin": (_i, [_vp, _d]),
+    "compar_error_model_predict": (_d, [_vp, _i, _i, _i64]),
     "compar_profile_enable": (_i, [_vp, _i]),
     "compar_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "compar_profile_reset": (_i, [_vp]),
@@ -130,7 +137,13 @@ def exported_symbols():
 for _name in SIGNATURES:
     globals()[_name] = _missing(_name)
 if os.path.exists(LIB_PATH):
-    load()
+    try:
+        load()
+    except AttributeError:
+        # a stale build without some symbol: calls raise until it is rebuilt
+        _lib = None
+        for _name in SIGNATURES:
+            globals()[_name] = _missing(_name)
 
 
 def _status(rc, what):
@@ -160,12 +173,39 @@ def torch_dtype_code(t):
 class Context:
     """A libcompar context bound to one CUDA device (tensor-level API)."""
 
-    def __init__(self, device=0):
+    def __init__(self, device=0, host_only=False, num_sms=148):
         load()
         h = ctypes.c_void_p()
-        _status(compar_init(ctypes.byref(h), device), "compar_init")
+        if host_only:
+            _status(compar_init_host(ctypes.byref(h), num_sms), "compar_init_host")
+        else:
+            _status(compar_init(ctypes.byref(h), device), "compar_init")
         self.handle = h
-        self.device = device
+        self.device = None if host_only else device
+
+    @classmethod
+    def host(cls, num_sms=148):
+        """A host-only context (no GPU): selection, models, records, files."""
+        return cls(host_only=True, num_sms=num_sms)
+
+    def select(self, m, n, k, dtype=F32, tol=0.0, batch=1):
+        return _status(compar_select(self.handle, m, n, k, dtype, float(tol), batch), "select")
+
+    def error_model(self, variant, dtype):
+        c = [ctypes.c_double() for _ in range(3)]
+        _status(compar_error_model_get(self.handle, variant, dtype, *[ctypes.byref(x) for x in c]),
+                "error_model_get")
+        return tuple(x.value for x in c)
+
+    def set_error_model(self, variant, dtype, c0, c1, c2):
+        return _status(compar_error_model_set(self.handle, variant, dtype, c0, c1, c2),
+                       "error_model_set")
+
+    def set_error_margin(self, margin):
+        return _status(compar_error_model_set_margin(self.handle, margin), "error_model_margin")
+
+    def predict_error(self, variant, dtype, k):
+        return compar_error_model_predict(self.handle, variant, dtype, k)
 
     def close(self):
         if self.handle:

@@ -62,9 +62,9 @@ bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
   if (c.m > INT32_MAX || c.n > INT32_MAX || c.k > INT32_MAX) return false;
   switch (v) {
     case COMPAR_V_NAIVE:
-      return (c.m + 15) / 16 <= 65535;
+      return c.dtype == COMPAR_F32 && (c.m + 15) / 16 <= 65535;
     case COMPAR_V_SIMT:
-      return (c.m + 31) / 32 <= 65535;
+      return c.dtype == COMPAR_F32 && (c.m + 31) / 32 <= 65535;
     case COMPAR_V_TC_TF32:
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
@@ -340,8 +340,23 @@ int compar_init(compar_ctx_t* out, int device) {
   return COMPAR_OK;
 }
 
+int compar_init_host(compar_ctx_t* out, int num_sms) {
+  if (!out) return COMPAR_ERR_INVALID;
+  auto* ctx = new compar_ctx();
+  ctx->host_only = true;
+  ctx->num_sms = num_sms > 0 ? num_sms : 148;
+  ctx->device = -1;
+  if (const char* e = getenv("COMPAR_LOG")) ctx->log = atoi(e) != 0;
+  *out = ctx;
+  return COMPAR_OK;
+}
+
 int compar_terminate(compar_ctx_t ctx) {
   if (!ctx) return COMPAR_OK;
+  if (ctx->host_only) {
+    delete ctx;
+    return COMPAR_OK;
+  }
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   resolve_pending(ctx);
@@ -373,6 +388,7 @@ const char* compar_last_error(void) { return g_last_error.c_str(); }
 int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                 double tol, const void* A, const void* B, float* C, void* stream) {
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   int rc = check_ptrs(m, n, k, A, B, C);
   if (rc != COMPAR_OK) return rc;
   GemmCall c;
@@ -449,12 +465,67 @@ int compar_clear_decisions(compar_ctx_t ctx) {
   return COMPAR_OK;
 }
 
+int compar_select(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
+                  double tol, int batch) {
+  if (!ctx || !valid_dtype(dtype) || std::isnan(tol) || m <= 0 || n <= 0 || k <= 0 ||
+      batch < 1)
+    return COMPAR_ERR_INVALID;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.lda = k;
+  c.ldb = n;
+  c.ldc = n;
+  c.dtype = dtype;
+  c.tol = default_tol(tol);
+  c.batch = batch;
+  if (ctx->forced >= 0)
+    return variant_supported(ctx, ctx->forced, c) ? ctx->forced : COMPAR_ERR_UNSUPPORTED;
+  return select_variant(ctx, c);
+}
+
+int compar_error_model_set(compar_ctx_t ctx, int v, compar_dtype_t dtype, double c0, double c1,
+                           double c2) {
+  if (!ctx || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || std::isnan(c0) ||
+      !(c1 >= 0) || !(c2 >= 0) || !std::isfinite(c1) || !std::isfinite(c2) || c0 < 0)
+    return COMPAR_ERR_INVALID;
+  ctx->err.c0[v][dtype] = static_cast<float>(c0);
+  ctx->err.c1[v][dtype] = static_cast<float>(c1);
+  ctx->err.c2[v][dtype] = static_cast<float>(c2);
+  ctx->decisions.clear();
+  return COMPAR_OK;
+}
+
+int compar_error_model_get(compar_ctx_t ctx, int v, compar_dtype_t dtype, double* c0, double* c1,
+                           double* c2) {
+  if (!ctx || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || !c0 || !c1 || !c2)
+    return COMPAR_ERR_INVALID;
+  *c0 = ctx->err.c0[v][dtype];
+  *c1 = ctx->err.c1[v][dtype];
+  *c2 = ctx->err.c2[v][dtype];
+  return COMPAR_OK;
+}
+
+int compar_error_model_set_margin(compar_ctx_t ctx, double margin) {
+  if (!ctx || !(margin >= 1.0) || !std::isfinite(margin)) return COMPAR_ERR_INVALID;
+  ctx->err.margin = static_cast<float>(margin);
+  ctx->decisions.clear();
+  return COMPAR_OK;
+}
+
+double compar_error_model_predict(compar_ctx_t ctx, int v, compar_dtype_t dtype, int64_t k) {
+  if (!ctx || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || k < 0) return -1.0;
+  return ctx->err.predict(v, dtype, k);
+}
+
 int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
                    compar_dtype_t dtype, double tol, const void* A, const void* B, float* C,
                    int warmup, int reps, void* stream, float* median_ms) {
   if (!ctx || !median_ms || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || reps < 1 ||
       warmup < 0)
     return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   int rc = check_ptrs(m, n, k, A, B, C);
   if (rc != COMPAR_OK) return rc;
   if (m == 0 || n == 0 || k == 0) return COMPAR_ERR_INVALID;
@@ -559,6 +630,7 @@ int compar_record_clear(compar_ctx_t ctx) {
 
 int compar_check_device_error(compar_ctx_t ctx, void* stream) {
   if (!ctx) return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int word = 0;
   COMPAR_CUDA_TRY(cudaMemcpyAsync(&word, ctx->guard.err_word, sizeof(int),
@@ -576,6 +648,7 @@ int compar_set_wait_budget(compar_ctx_t ctx, uint64_t ns) {
 
 int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
   if (!ctx) return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   return launch_timeout_selftest(ctx->guard, static_cast<cudaStream_t>(stream));
 }
 

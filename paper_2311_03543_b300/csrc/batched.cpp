@@ -15,6 +15,7 @@ using namespace compar;
 extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
                                    double tol, void* stream) {
   if (!ctx || count < 0 || (count > 0 && !probs)) return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < count; ++i) {
     const compar_problem_t& p = probs[i];

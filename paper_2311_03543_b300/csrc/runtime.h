@@ -36,6 +36,7 @@ std::array<float, kNumFeatures> make_features(int64_t m, int64_t n, int64_t k, i
 struct ErrorModel {
   std::array<std::array<float, 3>, kNumVariants> c0{};
   std::array<std::array<float, 3>, kNumVariants> c1{};
+  std::array<std::array<float, 3>, kNumVariants> c2{};  // linear-in-k term
   float margin = 1.5f;  // eligibility: predicted * margin <= tol
   ErrorModel();
   double predict(int v, int dtype, int64_t k) const;
@@ -123,6 +124,7 @@ struct PendingTiming {  // events of a recorded compar_gemm call, resolved lazil
 
 // The opaque context of the C ABI.
 struct compar_ctx {
+  bool host_only = false;  // created by compar_init_host: no CUDA calls at all
   int device = 0;
   int num_sms = 148;
   float alpha = 1.f, beta = 0.f;

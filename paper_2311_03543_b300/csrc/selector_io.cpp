@@ -4,6 +4,7 @@
 // equivalent checkpoint.  Format (little endian):
 //   "CMPRSEL1" | u32 version | u64 payload bytes | payload | u64 FNV-1a(payload)
 // A file that fails any check leaves the loaded models untouched.
+#include <cmath>
 #include <cstring>
 #include <fstream>
 #include <vector>
@@ -85,6 +86,7 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
   }
   for (const auto& r : ctx->err.c0) for (float x : r) w.put(x);
   for (const auto& r : ctx->err.c1) for (float x : r) w.put(x);
+  for (const auto& r : ctx->err.c2) for (float x : r) w.put(x);
   w.put(ctx->err.margin);
   const MlpModel& mm = ctx->mlp;
   w.put<uint8_t>(mm.trained ? 1 : 0);
@@ -156,7 +158,9 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
   ErrorModel err;
   for (auto& row : err.c0) for (float& x : row) x = r.get<float>();
   for (auto& row : err.c1) for (float& x : row) x = r.get<float>();
+  for (auto& row : err.c2) for (float& x : row) x = r.get<float>();
   err.margin = r.get<float>();
+  if (!(err.margin >= 1.0f) || !std::isfinite(err.margin)) r.ok = false;
   MlpModel mm;
   mm.trained = r.get<uint8_t>() != 0;
   for (float& x : mm.feat_mean) x = r.get<float>();

@@ -1,0 +1,139 @@
+"""Host logic of the runtime, on host-only contexts (no GPU): eligibility by
+dtype and error model, history-table selection and its nearest-neighbour
+lookup, the roofline prior, forced variants, decision caching, and selector
+files (round trip, corruption, version checks)."""
+import os
+
+import pytest
+
+import paper_2311_03543_b300 as cp
+
+
+@pytest.fixture
+def hctx():
+    c = cp.Context.host()
+    yield c
+    c.close()
+
+
+def _rec(m, n, k, dtype, v, t, batch=1, tol=1e-5):
+    r = cp.compar_record_t()
+    r.m, r.n, r.k, r.dtype, r.variant, r.batch = m, n, k, dtype, v, batch
+    r.tol, r.time_ms, r.rel_err = tol, t, -1.0
+    return r
+
+
+def test_compute_calls_are_refused_without_a_device(hctx):
+    assert cp.compar_gemm(hctx.handle, 4, 4, 4, cp.F32, 0.0, 16, 16, 16, None) == cp.ERR_UNSUPPORTED
+    assert cp.compar_selftest_timeout(hctx.handle, None) == cp.ERR_UNSUPPORTED
+
+
+def test_eligibility_by_tolerance(hctx):
+    # FP32 inputs at 1e-5: only FP32-accurate variants (naive, simt, 3xbf16)
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3)
+    # at 1e-1 the fp8 variant is the fastest by the roofline prior for big shapes
+    assert hctx.select(8192, 8192, 8192, cp.F32, 1e-1) == cp.V_TC_FP8
+    # BF16 inputs can never run the f32-only variants
+    assert hctx.select(2048, 2048, 2048, cp.BF16, 1e-3) in (cp.V_NAIVE, cp.V_SIMT, cp.V_TC_BF16)
+
+
+def test_no_variant_meets_impossible_tolerance(hctx):
+    assert cp.compar_select(hctx.handle, 64, 64, 64, cp.F32, 1e-12, 1) == cp.ERR_NO_VARIANT
+
+
+def test_history_table_overrides_prior(hctx):
+    m = n = k = 1024
+    first = hctx.select(m, n, k, cp.F32, 1e-5)
+    other = cp.V_SIMT if first != cp.V_SIMT else cp.V_SPLIT3
+    hctx.record_add([_rec(m, n, k, cp.F32, other, 0.001), _rec(m, n, k, cp.F32, first, 5.0)])
+    hctx.clear_decisions()
+    assert hctx.select(m, n, k, cp.F32, 1e-5) == other
+    # a nearby shape (within the quarter-log2 grid distance) follows the table
+    hctx.clear_decisions()
+    assert hctx.select(1100, 1024, 1000, cp.F32, 1e-5) == other
+
+
+def test_decision_cache_is_sticky_until_cleared(hctx):
+    m = n = k = 512
+    v0 = hctx.select(m, n, k, cp.F32, 1e-5)
+    other = cp.V_SIMT if v0 != cp.V_SIMT else cp.V_NAIVE
+    hctx.record_add([_rec(m, n, k, cp.F32, other, 1e-6)])
+    assert hctx.select(m, n, k, cp.F32, 1e-5) == v0          # cached
+    hctx.clear_decisions()
+    assert hctx.select(m, n, k, cp.F32, 1e-5) == other
+
+
+def test_forced_variant(hctx):
+    hctx.force_variant(cp.V_NAIVE)
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) == cp.V_NAIVE
+    hctx.force_variant(cp.V_SPLIT3)
+    assert cp.compar_select(hctx.handle, 64, 64, 64, cp.BF16, 1e-3, 1) == cp.ERR_UNSUPPORTED
+    hctx.force_variant(None)
+    with pytest.raises(cp.ComparError):
+        hctx.force_variant(17)
+
+
+def test_error_model_get_set_predict(hctx):
+    c0, c1, c2 = hctx.error_model(cp.V_SPLIT3, cp.F32)
+    assert c0 > 0
+    assert hctx.error_model(cp.V_SPLIT3, cp.BF16)[0] == float("inf")
+    hctx.set_error_model(cp.V_SPLIT3, cp.F32, 1e-3, 0.0, 0.0)
+    assert hctx.predict_error(cp.V_SPLIT3, cp.F32, 4096) == pytest.approx(1e-3, rel=1e-6)
+    # with a pessimistic model the 3xBF16 variant drops out at 1e-5
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) != cp.V_SPLIT3
+    hctx.set_error_model(cp.V_SPLIT3, cp.F32, 0.0, 0.0, 1.0)
+    u = 2.0 ** -24
+    assert hctx.predict_error(cp.V_SPLIT3, cp.F32, 1000) == pytest.approx(1000 * u, rel=1e-6)
+    with pytest.raises(cp.ComparError):
+        hctx.set_error_margin(0.5)
+
+
+def test_selector_file_round_trip(hctx, tmp_path):
+    recs = [_rec(256 * i, 256 * i, 256 * i, cp.F32, v, 0.01 * i * (v + 1))
+            for i in range(1, 8) for v in (0, 1, 5)]
+    hctx.record_add(recs)
+    hctx.set_error_model(cp.V_TC_TF32, cp.F32, 2e-4, 0.5, 0.01)
+    path = str(tmp_path / "sel.bin")
+    hctx.selector_save(path)
+    other = cp.Context.host()
+    try:
+        other.selector_load(path)
+        assert other.error_model(cp.V_TC_TF32, cp.F32) == pytest.approx((2e-4, 0.5, 0.01))
+        for i in range(1, 8):
+            s = 256 * i
+            assert other.select(s, s, s, cp.F32, 1e-5) == hctx.select(s, s, s, cp.F32, 1e-5)
+    finally:
+        other.close()
+
+
+def test_corrupted_selector_file_is_rejected_and_model_kept(hctx, tmp_path):
+    hctx.record_add([_rec(2048, 2048, 2048, cp.F32, cp.V_SIMT, 1e-6)])
+    path = str(tmp_path / "sel.bin")
+    hctx.selector_save(path)
+    data = bytearray(open(path, "rb").read())
+    fresh = cp.Context.host()
+    try:
+        fresh.record_add([_rec(2048, 2048, 2048, cp.F32, cp.V_NAIVE, 1e-7)])
+        before = fresh.select(2048, 2048, 2048, cp.F32, 1e-5)
+        bad = bytearray(data); bad[40] ^= 0xFF                     # payload flip -> checksum
+        for name, blob in [("flip", bad), ("magic", b"XXXXXXXX" + data[8:]),
+                           ("version", data[:8] + b"\x09\x00\x00\x00" + data[12:]),
+                           ("truncated", data[:-9]), ("empty", b"")]:
+            p = str(tmp_path / f"{name}.bin")
+            open(p, "wb").write(bytes(blob))
+            assert cp.compar_selector_load(fresh.handle, os.fsencode(p)) == cp.ERR_IO, name
+        fresh.clear_decisions()
+        assert fresh.select(2048, 2048, 2048, cp.F32, 1e-5) == before
+        assert cp.compar_selector_load(fresh.handle, b"/nonexistent/file") == cp.ERR_IO
+    finally:
+        fresh.close()
+
+
+def test_records_ring_and_validation(hctx):
+    hctx.record_add([_rec(8, 8, 8, cp.F32, 1, 0.5)])
+    assert len(hctx.records()) == 1
+    bad = _rec(8, 8, 8, cp.F32, 42, 0.5)
+    with pytest.raises(cp.ComparError):
+        hctx.record_add([bad])
+    hctx.record_clear()
+    assert hctx.records() == []
