@@ -39,10 +39,12 @@ TOL = 1e-5
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweep", default="full", choices=["full", "pow2"])
+    ap.add_argument("--shapes", default=None,
+                    help="comma-separated square sizes replacing the sweep (profiling runs)")
     ap.add_argument("--no-regret", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -190,6 +192,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     shapes = W.sweep_shapes() if args.sweep == "full" else W.pow2_sweep_shapes()
+    if args.shapes:
+        shapes = [(int(s),) * 3 for s in args.shapes.split(",")]
     ctx = cp.Context(dev.index)
     if os.path.exists(args.selector):
         ctx.selector_load(args.selector)
