@@ -153,6 +153,30 @@ int compar_gemm_batched(compar_ctx_t ctx, int count,
                         const compar_problem_t* probs, double tol,
                         void* stream);
 
+/* FP32 SIMT GEMM that allocates nothing, for callers that cannot allocate
+ * device memory where they need the product: a host application or framework
+ * that owns all device memory through its own pool, a latency-critical path
+ * that cannot risk the synchronisation an allocation may cause, or a plug-in
+ * given no allocator.  The paper has no counterpart of this call.
+ *   C = alpha * A x B + beta * C, A (m x k), B (k x n), C (m x n), all float32,
+ *   row-major contiguous DEVICE pointers owned by the caller, on the CURRENT
+ *   device, asynchronous on `stream`.
+ * It needs no context and calls no cudaMalloc / cudaFree or any allocating
+ * routine.  Its only scratch, the split-K partial sums of the SIMT kernel,
+ * is a fixed 16 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  A shape whose split-K
+ * plan needs more than 16 MiB is refused with COMPAR_ERR_INVALID (the text is
+ * in compar_last_error); nothing needs to start zeroed.  The first call on a
+ * device does a one-time set-up (it looks up the array's device address and
+ * the SM count), so make that first call before any stream capture.  All
+ * calls share the one array: calls that may overlap on the GPU (different
+ * streams or host threads without ordering) race on it; calls on one stream
+ * are ordered and safe.  Returns COMPAR_OK, COMPAR_ERR_INVALID,
+ * COMPAR_ERR_UNSUPPORTED (not an sm_103 device) or COMPAR_ERR_CUDA. */
+int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
+                             const float* A, const float* B, float beta,
+                             float* C, void* stream);
+
 /* ---------------------------------------------------------------- control */
 
 /* Force every following call onto `variant_id` (one of COMPAR_V_*), or clear

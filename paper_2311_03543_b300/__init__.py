@@ -80,6 +80,7 @@ SIGNATURES = {
     "compar_check_device_error": (_i, [_vp, _vp]),
     "compar_set_wait_budget": (_i, [_vp, _u64]),
     "compar_selftest_timeout": (_i, [_vp, _vp]),
+    "compar_gemm_simt_noalloc": (_i, [_i64, _i64, _i64, _f, _vp, _vp, _f, _vp, _vp]),
     "compar_init_host": (_i, [ctypes.POINTER(_vp), _i]),
     "compar_select": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i]),
     "compar_error_model_set": (_i, [_vp, _i, _i, _d, _d, _d]),

@@ -30,6 +30,7 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   g_last_error = buf;
 }
 std::string last_error_text() { return g_last_error; }
+void set_last_error_text(const std::string& text) { g_last_error = text; }
 
 int Workspace::ensure(size_t need, cudaStream_t s) {
   if (need <= bytes) return COMPAR_OK;

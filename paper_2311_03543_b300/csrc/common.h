@@ -84,6 +84,9 @@ int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
 int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                 cudaStream_t s);
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s);
+int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
+                        cudaStream_t s, size_t* need_bytes);
+void set_last_error_text(const std::string& text);
 
 // Tensor-core variants (tcgen05).  kind: COMPAR_V_TC_TF32 / TC_BF16 / TC_FP8 / SPLIT3.
 int launch_tc(int variant, const GemmCall& c, Workspace& ws, const DeviceGuard& g,

@@ -328,4 +328,65 @@ int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cuda
   return COMPAR_OK;
 }
 
+// ------------------------------------------------------------------ caller-owned scratch
+// The SIMT variant with the same tiles and split-K plan as launch_simt, but
+// its split-K partial sums go to `scratch` (capacity `scratch_bytes`), which
+// the caller owns; nothing is allocated.  A plan that needs more scratch than
+// that is refused with COMPAR_ERR_INVALID and *need_bytes tells how much.
+namespace {
+template <int BM, int BN, int BK, int TM, int TN>
+int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
+                     cudaStream_t s, size_t* need_bytes) {
+  const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int tiles = tiles_m * tiles_n;
+  int splits = 1;
+  if (tiles < num_sms && K >= 1024) {
+    splits = std::min<int>((2 * num_sms + tiles - 1) / tiles, K / 256);
+    splits = std::max(1, std::min(splits, 32));
+  }
+  int k_per = K;
+  if (splits > 1) {
+    k_per = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    splits = (K + k_per - 1) / k_per;
+  }
+  const size_t need = splits > 1 ? static_cast<size_t>(splits) * M * N * sizeof(float) : 0;
+  if (need_bytes) *need_bytes = need;
+  if (need > scratch_bytes) return COMPAR_ERR_INVALID;
+  float* partial = splits > 1 ? scratch : nullptr;
+  const bool vec = (c.k % 4 == 0) && (c.n % 4 == 0) && (c.lda % 4 == 0) && (c.ldb % 4 == 0) &&
+                   (c.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(c.B) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(c.C) % 16 == 0);
+  dim3 grid(tiles_n, tiles_m, splits);
+  constexpr int threads = SimtCfg<BM, BN, BK, TM, TN, true>::kThreads;
+  const float* A = static_cast<const float*>(c.A);
+  const float* B = static_cast<const float*>(c.B);
+  if (vec)
+    gemm_simt_kernel<BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+  else
+    gemm_simt_kernel<BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  if (splits > 1) {
+    const int64_t total = static_cast<int64_t>(M) * N;
+    const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, partial, c.alpha, c.beta, c.C,
+                                                c.ldc);
+    COMPAR_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  return COMPAR_OK;
+}
+}  // namespace
+
+int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
+                        cudaStream_t s, size_t* need_bytes) {
+  if (c.m <= 48)
+    return run_simt_scratch<32, 128, 32, 4, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
+  return run_simt_scratch<128, 128, 16, 8, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
+}
+
 }  // namespace compar
