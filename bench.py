@@ -280,9 +280,11 @@ def main():
         peak, bound = base * scale, "tensor"
         if scale != 1.0:
             src += f" x nominal ratio {scale}"
+    traffic, traffic_note = measured_traffic(cp.VARIANT_NAMES[dom], dom_flops / max(dom_n, 1))
     roofline = {"bound": bound, "kernel": cp.VARIANT_NAMES[dom], "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                "traffic": None, "peak_source": src, "launches": dom_n,
+                "traffic": traffic, "traffic_note": traffic_note,
+                "peak_source": src + " (of measured)", "launches": dom_n,
                 "kernel_ms_per_step": dom_ms / args.steps,
                 "share_of_step": (dom_ms / args.steps) / ms if ms else None}
 
@@ -355,6 +357,27 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def measured_traffic(kernel, flops_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled to the
+    average launch by work (GEMM traffic grows with 2MNK at fixed tiles); None
+    when there is no capture or the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu capture for this kernel"
+    h = hashlib.sha1()
+    for f in ("gemm_tc.cu", "ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2311_03543_b300", "csrc", f), "rb").read())
+    if h.hexdigest() != rec["src_sha1"]:
+        return None, "kernel changed since the ncu capture"
+    m, n, k = rec["shape"]
+    scale = flops_per_launch / (2.0 * m * n * k * (3 if kernel == "split-3xbf16" else 1))
+    return (rec["dram_bytes_per_launch"] * scale,
+            f"ncu dram read+write of one {m}x{n}x{k} launch ({rec['source']}) scaled by work "
+            f"to the average launch (x{scale:.3f})")
 
 
 def measure_regret(ctx, cp, W, torch, dev):
