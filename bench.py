@@ -13,7 +13,7 @@ Printed JSON line keys follow the benchmark contract: value (device-resident
 inputs), e2e (host buffers, H2D/D2H inside the timed region), roofline of
 the dominant kernel (CUDA-event kernel time inside the timed region), the
 CPU oracle baseline, clocks sampled during the timed region, kernel launch
-count, and the selector's regret on the power-of-two sweep shapes.
+count, and the selector's regret on 200 held-out contexts.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm):
 each step is a bounded sample of the same sweep (squares 64..1024).
@@ -329,7 +329,10 @@ def main():
     # selector regret against exhaustive measurement (power-of-two shapes)
     regret = None
     if not args.no_regret and rank == 0:
-        regret = measure_regret(ctx, cp, W, torch, dev)
+        r_pct, r_viol, r_n = measure_regret(ctx, cp, W, torch, dev)
+        regret = {"mean_pct": r_pct, "violations": r_viol, "contexts": r_n,
+                  "set": "held-out contexts 0..199 (M,N,K log-uniform [16,4096], f32/bf16/fp8, "
+                         "tol 1e-5/1e-3/1e-1)", "feasibility": "library FP64 residual check, 8 rows"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -380,41 +383,48 @@ def measured_traffic(kernel, flops_per_launch):
             f"to the average launch (x{scale:.3f})")
 
 
-def measure_regret(ctx, cp, W, torch, dev):
-    """Mean regret (%) of the selector's pick vs exhaustive timing on the pow2 shapes.
+def measure_regret(ctx, cp, W, torch, dev, count=200):
+    """Mean regret (%) of the selector on held-out contexts vs exhaustive timing.
 
-    Feasibility uses the error measured against the FP64 oracle on 16 sampled
-    rows of each variant's output.
+    The first `count` held-out contexts (M, N, K log-uniform in [16, 4096],
+    dtype f32/bf16/fp8, tol 1e-5/1e-3/1e-1; never used in training).  Every
+    eligible variant is timed with compar_measure; its error is the library's
+    FP64 residual check on 8 rows.  best = fastest feasible variant (ties
+    within 2 % go to the lower id); regret = t(pick)/t(best) - 1, and an
+    infeasible pick costs a rerun.  Returns (regret %, violations, contexts).
     """
     import numpy as np
-    import oracle
-    from oracle import numerics as N
-    from oracle import selector_ref as S
-    rs = []
-    detail = []
-    for (m, n, k) in W.pow2_sweep_shapes():
-        A = W.uniform(m, k, seed=2); B = W.uniform(k, n, seed=3)
-        dA = torch.from_numpy(A).to(dev); dB = torch.from_numpy(B).to(dev)
+    tie = 0.02
+    rs, viol = [], 0
+    for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts()[:count]):
+        g = torch.Generator(device=dev)
+        g.manual_seed(90000 + i)
+        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        if dt == cp.BF16:
+            A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        elif dt == cp.F8E4M3:
+            A = A.to(torch.float8_e4m3fn).view(torch.uint8)
+            B = B.to(torch.float8_e4m3fn).view(torch.uint8)
         C = torch.empty((m, n), device=dev)
-        rows = W.sample_rows(m, 16, seed=4)
-        ref = oracle.gemm_rows(A, B, rows)
         ctx.clear_decisions()
-        ctx.gemm(dA, dB, C, tol=TOL)
-        pick = ctx.last_variant()
-        times, errs = {}, {}
+        pick = ctx.select(m, n, k, dt, tol)
+        times, feas = {}, set()
         for v in range(cp.NUM_VARIANTS):
-            if not ctx.supported(v, m, n, k, cp.F32):
+            if not ctx.supported(v, m, n, k, dt):
                 continue
-            if v == cp.V_NAIVE and m * n * k > 2 ** 33:
-                continue  # far slower than every alternative at this size
-            reps = 3 if m * n * k > 2 ** 30 else 10
-            times[v] = ctx.measure(v, dA, dB, C, tol=TOL, warmup=1, reps=reps)
-            torch.cuda.synchronize()
-            errs[v] = N.rel_frobenius(C.cpu().numpy()[rows], ref)
-        r = S.regret(pick, times, errs, TOL)
-        rs.append(r)
-        detail.append((m, n, k, pick, S.exhaustive_pick(times, errs, TOL)))
-    return 100.0 * float(np.nanmean(rs))
+            times[v] = ctx.measure(v, A, B, C, tol=tol, warmup=1, reps=3, dtype=dt)
+            if ctx.residual_check(A, B, C, nrows=8, seed=i, dtype=dt) <= tol:
+                feas.add(v)
+        if not feas:
+            continue
+        t_best = min(times[v] for v in feas)
+        if pick not in feas:
+            viol += 1
+            rs.append((times[pick] + t_best) / t_best - 1.0)
+        else:
+            rs.append(0.0 if times[pick] <= t_best * (1 + tie) else times[pick] / t_best - 1.0)
+    return 100.0 * float(np.mean(rs)), viol, len(rs)
 
 
 if __name__ == "__main__":

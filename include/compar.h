@@ -177,12 +177,27 @@ int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
                              const float* A, const float* B, float beta,
                              float* C, void* stream);
 
+/* Time the implementations of a batched call on this batch and remember the
+ * fastest for its signature (shapes, dtypes, tolerance class): 0 = one launch
+ * per problem, 1 = grouped kernel with 128-column tiles, 2 = 64-column tiles,
+ * 3 / 4 = as 1 / 2 with the largest problems first.  Each configuration runs
+ * once untimed and three times timed (CUDA events on `stream`), so C is
+ * written several times: with beta != 0 the final contents are not the
+ * product.  times_ms (nullable, 5 floats) receives the medians, *best
+ * (nullable) the choice.  Synchronises `stream`. */
+int compar_autotune_batched(compar_ctx_t ctx, int count,
+                            const compar_problem_t* probs, double tol,
+                            void* stream, float* times_ms, int* best);
+
 /* ---------------------------------------------------------------- control */
 
 /* Force every following call onto `variant_id` (one of COMPAR_V_*), or clear
  * with -1 (the paper's STARPU_NCUDA / STARPU_NCPU switches, Sec. 3.2, pinned
  * whole architectures; this pins one variant).  A forced variant that cannot
- * run a call makes that call return COMPAR_ERR_UNSUPPORTED. */
+ * run a call makes that call return COMPAR_ERR_UNSUPPORTED.  Forcing
+ * COMPAR_V_GROUPED affects batched calls only (they then always use the
+ * grouped kernel); forcing a single-call variant makes batched calls run one
+ * launch per problem on that variant. */
 int compar_force_variant(compar_ctx_t ctx, int variant_id);
 
 /* alpha and beta used by compar_gemm (defaults 1 and 0). */
@@ -244,6 +259,67 @@ int compar_selector_load(compar_ctx_t ctx, const char* path);
 
 /* Write the current selector state to `path` (binary, versioned, checksummed). */
 int compar_selector_save(compar_ctx_t ctx, const char* path);
+
+/* ---------------------------------------------------------------- learned cost model */
+
+/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 12, ReLU)
+ * per ensemble member (4 members).  Inputs (features of a call):
+ * log2 M, log2 N, log2 K, one-hot dtype (f32, bf16, f8), log10 tol,
+ * log2 batch.  Outputs: for variant v (0..5) output v is log2 of the run
+ * time in ms and output 6+v log10 of the relative error.  The paper's runtime
+ * chooses variants with performance models it calls machine-learning models
+ * and expects better-trained models to choose better (Sec. 3.2, Sec. 5).
+ * Parameters of one member, float32, in this order: W1[64][8] b1[64]
+ * W2[64][64] b2[64] W3[12][64] b3[12] (weights stored out x in). */
+int compar_mlp_param_count(void);
+
+/* Forward pass on the GPU for `members` parameter sets (host array
+ * members x param_count) over `rows` raw (already standardised) feature rows
+ * (host, rows x 8); Y (host) receives members x rows x 12.  Synchronous. */
+int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
+                       const float* X, int rows, float* Y);
+
+/* Training steps on the GPU (one CTA per member runs the whole loop):
+ * loss = sum mask*(y-T)^2 / max(1, sum mask) over each mini-batch, gradients
+ * by backpropagation, Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected,
+ * step counter starting at step0 >= 1).  All arrays are HOST arrays:
+ * params/adam_m/adam_v (members x param_count, updated in place), X (rows x
+ * 8), T and mask (rows x 12), batch_idx (members x steps x batch row indices,
+ * batch <= 128).  When `grads` is non-NULL, steps must be 1: the gradients of
+ * the first mini-batch are written to grads (members x param_count) and
+ * params are left unchanged.  loss (nullable) receives members x steps batch
+ * losses.  Synchronous. */
+int compar_mlp_train_steps(compar_ctx_t ctx, float* params, float* adam_m,
+                           float* adam_v, int members, const float* X,
+                           const float* T, const float* mask, int rows,
+                           const int32_t* batch_idx, int steps, int batch,
+                           float lr, int step0, float* grads, float* loss);
+
+/* Train the context's cost model from its timing records (compar_measure /
+ * compar_record_add): standardises features and targets, holds out 1 row in
+ * 10, trains the 4-member ensemble for `steps` Adam steps of `batch` rows
+ * (bootstrap mini-batches from `seed`), then marks the model trained (used by
+ * selection when confident) and clears the decision cache.  *val_loss
+ * (nullable) receives the held-out standardised loss.  Synchronous. */
+int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr,
+                          uint64_t seed, float* val_loss);
+
+/* The trained model's prediction for one call: per variant (arrays of 6)
+ * the ensemble-mean run time in ms, relative error, and the ensemble std of
+ * log2 time (spread, nullable).  COMPAR_ERR_UNSUPPORTED when untrained. */
+int compar_predict(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
+                   compar_dtype_t dtype, double tol, int batch,
+                   float* time_ms, float* rel_err, float* spread);
+
+/* Relative Frobenius error of C against alpha * op_scale * A x B computed in
+ * FP64 on the GPU over `nrows` rows drawn from `seed` (all rows when nrows >=
+ * m); op_scale is the context's fp8 scales for F8E4M3 inputs, else 1.  A, B,
+ * C are device pointers, row-major contiguous; C was computed with beta = 0.
+ * Labels the accuracy of recorded runs.  Synchronises `stream`. */
+int compar_residual_check(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
+                          compar_dtype_t dtype, const void* A, const void* B,
+                          const float* C, float alpha, int nrows, uint64_t seed,
+                          double* rel_err, void* stream);
 
 /* ---------------------------------------------------------------- timing */
 

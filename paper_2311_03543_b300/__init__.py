@@ -81,6 +81,16 @@ SIGNATURES = {
     "compar_set_wait_budget": (_i, [_vp, _u64]),
     "compar_selftest_timeout": (_i, [_vp, _vp]),
     "compar_gemm_simt_noalloc": (_i, [_i64, _i64, _i64, _f, _vp, _vp, _f, _vp, _vp]),
+    "compar_autotune_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp, _fp,
+                                     ctypes.POINTER(_i)]),
+    "compar_mlp_param_count": (_i, []),
+    "compar_mlp_forward": (_i, [_vp, _fp, _i, _fp, _i, _fp]),
+    "compar_mlp_train_steps": (_i, [_vp, _fp, _fp, _fp, _i, _fp, _fp, _fp, _i,
+                                    ctypes.POINTER(ctypes.c_int32), _i, _i, _f, _i, _fp, _fp]),
+    "compar_selector_train": (_i, [_vp, _i, _i, _f, _u64, _fp]),
+    "compar_predict": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i, _fp, _fp, _fp]),
+    "compar_residual_check": (_i, [_vp, _i64, _i64, _i64, _i, _vp, _vp, _vp, _f, _i, _u64,
+                                   ctypes.POINTER(_d), _vp]),
     "compar_init_host": (_i, [ctypes.POINTER(_vp), _i]),
     "compar_select": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i]),
     "compar_error_model_set": (_i, [_vp, _i, _i, _d, _d, _d]),
@@ -158,6 +168,10 @@ def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _f32p(a):
+    return a.ctypes.data_as(_fp)
 
 
 def torch_dtype_code(t):
@@ -244,7 +258,8 @@ class Context:
         return compar_gemm(self.handle, m, n, k, dtype, float(tol), a_ptr, b_ptr, c_ptr,
                            stream_handle)
 
-    def gemm_batched(self, problems, tol=0.0, stream=None):
+    @staticmethod
+    def problem_array(problems):
         """problems: list of dicts with keys m n k lda ldb ldc dtype A B C [alpha beta scale_a scale_b]."""
         arr = (compar_problem_t * len(problems))()
         for i, p in enumerate(problems):
@@ -252,8 +267,22 @@ class Context:
                                       p["dtype"], p["A"], p["B"], p["C"], p.get("alpha", 1.0),
                                       p.get("beta", 0.0), p.get("scale_a", 1.0),
                                       p.get("scale_b", 1.0))
-        return _status(compar_gemm_batched(self.handle, len(problems), arr, float(tol),
+        return arr
+
+    def gemm_batched(self, problems, tol=0.0, stream=None):
+        arr = problems if isinstance(problems, ctypes.Array) else self.problem_array(problems)
+        return _status(compar_gemm_batched(self.handle, len(arr), arr, float(tol),
                                            _stream_handle(stream)), "compar_gemm_batched")
+
+    def autotune_batched(self, problems, tol=0.0, stream=None):
+        """Returns (best configuration, [median ms of configurations 0..4])."""
+        arr = problems if isinstance(problems, ctypes.Array) else self.problem_array(problems)
+        times = (ctypes.c_float * 5)()
+        best = ctypes.c_int()
+        _status(compar_autotune_batched(self.handle, len(arr), arr, float(tol),
+                                        _stream_handle(stream), times, ctypes.byref(best)),
+                "compar_autotune_batched")
+        return best.value, list(times)
 
     def measure(self, variant, A, B, C, tol=0.0, warmup=3, reps=10, stream=None, dtype=None):
         """Median time (ms) of one variant on this call, CUDA events on `stream`."""
@@ -316,6 +345,69 @@ class Context:
 
     def set_wait_budget(self, ns):
         return _status(compar_set_wait_budget(self.handle, int(ns)), "set_wait_budget")
+
+    # -- learned cost model ----------------------------------------------------
+    def mlp_forward(self, params, X):
+        """params: float32 (members, P); X: float32 (rows, 8) -> (members, rows, 12)."""
+        import numpy as np
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        members, rows = params.shape[0], X.shape[0]
+        Y = np.zeros((members, rows, 12), dtype=np.float32)
+        _status(compar_mlp_forward(self.handle, _f32p(params), members, _f32p(X), rows, _f32p(Y)),
+                "mlp_forward")
+        return Y
+
+    def mlp_train_steps(self, params, X, T, mask, batch_idx, lr=1e-3, step0=1, m=None, v=None,
+                        grads_only=False):
+        """Runs Adam steps on the GPU; returns (params, m, v, loss) or (grads, loss)."""
+        import numpy as np
+        params = np.array(params, dtype=np.float32, order="C", copy=True)
+        members = params.shape[0]
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        mask = np.ascontiguousarray(mask, dtype=np.float32)
+        idx = np.ascontiguousarray(batch_idx, dtype=np.int32)   # (members, steps, batch)
+        steps, batch = idx.shape[1], idx.shape[2]
+        loss = np.zeros((members, steps), dtype=np.float32)
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if grads_only:
+            g = np.zeros_like(params)
+            _status(compar_mlp_train_steps(self.handle, _f32p(params), None, None, members,
+                                           _f32p(X), _f32p(T), _f32p(mask), X.shape[0], ip,
+                                           steps, batch, lr, step0, _f32p(g), _f32p(loss)),
+                    "mlp_train_steps")
+            return g, loss
+        m = np.zeros_like(params) if m is None else np.array(m, dtype=np.float32, copy=True)
+        v = np.zeros_like(params) if v is None else np.array(v, dtype=np.float32, copy=True)
+        _status(compar_mlp_train_steps(self.handle, _f32p(params), _f32p(m), _f32p(v), members,
+                                       _f32p(X), _f32p(T), _f32p(mask), X.shape[0], ip, steps,
+                                       batch, lr, step0, None, _f32p(loss)), "mlp_train_steps")
+        return params, m, v, loss
+
+    def selector_train(self, steps=20000, batch=128, lr=1e-3, seed=1):
+        vl = ctypes.c_float()
+        _status(compar_selector_train(self.handle, steps, batch, lr, seed, ctypes.byref(vl)),
+                "selector_train")
+        return vl.value
+
+    def predict(self, m, n, k, dtype=F32, tol=0.0, batch=1):
+        """MLP prediction: (time_ms[6], rel_err[6], spread[6])."""
+        t = (ctypes.c_float * 6)()
+        e = (ctypes.c_float * 6)()
+        s = (ctypes.c_float * 6)()
+        _status(compar_predict(self.handle, m, n, k, dtype, float(tol), batch, t, e, s), "predict")
+        return list(t), list(e), list(s)
+
+    def residual_check(self, A, B, C, alpha=1.0, nrows=16, seed=1, stream=None, dtype=None):
+        m, k = A.shape
+        n = B.shape[1]
+        dt = torch_dtype_code(A) if dtype is None else dtype
+        out = ctypes.c_double()
+        _status(compar_residual_check(self.handle, m, n, k, dt, A.data_ptr(), B.data_ptr(),
+                                      C.data_ptr(), alpha, nrows, seed, ctypes.byref(out),
+                                      _stream_handle(stream)), "residual_check")
+        return out.value
 
     # -- kernel profiling ------------------------------------------------------
     def profile_enable(self, on=True):

@@ -63,9 +63,12 @@ bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
   if (c.m > INT32_MAX || c.n > INT32_MAX || c.k > INT32_MAX) return false;
   switch (v) {
     case COMPAR_V_NAIVE:
-      return c.dtype == COMPAR_F32 && (c.m + 15) / 16 <= 65535;
+      // one thread per output with a K-long FMA chain: never competitive
+      // beyond ~2^36 multiply-adds, so not offered there
+      return (c.m + 15) / 16 <= 65535 &&
+             static_cast<double>(c.m) * c.n * c.k <= 68719476736.0;
     case COMPAR_V_SIMT:
-      return c.dtype == COMPAR_F32 && (c.m + 31) / 32 <= 65535;
+      return (c.m + 31) / 32 <= 65535;
     case COMPAR_V_TC_TF32:
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
@@ -134,14 +137,17 @@ static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* 
       const float d = out[e * kOutputs + v] - mean_t;
       var += d * d;
     }
-    if (mean_t < best_t) {
-      best_t = mean_t;
+    // the time head predicts log2(measured / roofline prior)
+    const float log2_t = mean_t + static_cast<float>(std::log2(
+                                      prior_time_ms(v, c.m, c.n, c.k, c.dtype, ctx->num_sms)));
+    if (log2_t < best_t) {
+      best_t = log2_t;
       best = v;
       best_std = std::sqrt(var / kEnsemble);
     }
   }
   if (best < 0 || best_std > mm.conf_std) return -1;
-  if (pred_ms) *pred_ms = std::exp2(best_t);  // the time head predicts log2(ms)
+  if (pred_ms) *pred_ms = std::exp2(best_t);
   return best;
 }
 
@@ -412,7 +418,7 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_
 }
 
 int compar_force_variant(compar_ctx_t ctx, int variant_id) {
-  if (!ctx || variant_id < -1 || variant_id >= kNumVariants) return COMPAR_ERR_INVALID;
+  if (!ctx || variant_id < -1 || variant_id > COMPAR_V_GROUPED) return COMPAR_ERR_INVALID;
   ctx->forced = variant_id;
   return COMPAR_OK;
 }

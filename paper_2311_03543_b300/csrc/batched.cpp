@@ -1,22 +1,305 @@
-// compar_gemm_batched: many independent GEMMs of uneven sizes in one call.
-// Each problem is dispatched through the single-call path (one launch per
-// problem, variant chosen per problem).
+// compar_gemm_batched / compar_autotune_batched: many independent GEMMs of
+// uneven sizes in one call.
+//
+// Two implementations are selected between per batch signature (the shapes,
+// dtypes and tolerance class of all problems):
+//   * "loop"   : one compar_gemm-style call per problem, each with its own
+//                variant choice (per-GEMM launches);
+//   * "grouped": one grouped pre-pass launch and one persistent grouped GEMM
+//                launch over every problem's tiles (gemm_grouped.cu), with the
+//                descriptor upload and both launches captured in a CUDA graph
+//                that is replayed for every later batch of the same shape.
+// The grouped kernel has tile configurations (BN = 128 or 64; problems in
+// given order or largest-first); compar_autotune_batched times the loop and
+// every configuration on the caller's batch and remembers the fastest for
+// that signature (saved in selector files).  Unknown signatures use the
+// grouped kernel with BN = 128 in the given order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <tuple>
 #include <vector>
 
+#include "grouped.h"
 #include "runtime.h"
 
 namespace compar {
 int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s);
-void batched_release(compar_ctx* ctx) { (void)ctx; }
-}  // namespace compar
 
-using namespace compar;
+namespace {
 
-extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
-                                   double tol, void* stream) {
+constexpr int kCfgLoop = 0;  // cfg 1..4: grouped, bn = (cfg & 1) ? 128 : 64, lpt = cfg >= 3
+inline int cfg_bn(int cfg) { return (cfg == 1 || cfg == 3) ? 128 : 64; }
+inline bool cfg_lpt(int cfg) { return cfg >= 3; }
+
+struct BatchedState {
+  GroupProblem* h_probs = nullptr;  // pinned staging
+  PrepassJob* h_jobs = nullptr;
+  GroupProblem* d_probs = nullptr;
+  PrepassJob* d_jobs = nullptr;
+  size_t cap_probs = 0, cap_jobs = 0;
+  cudaEvent_t staged = nullptr;  // last graph launch (staging may be rewritten after it)
+  cudaStream_t capture = nullptr;
+  std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+BatchedState* state(compar_ctx* ctx) {
+  if (!ctx->batched_state) ctx->batched_state = new BatchedState();
+  return static_cast<BatchedState*>(ctx->batched_state);
+}
+
+void drop_graphs(BatchedState* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+int ensure_staging(BatchedState* b, size_t nprobs, size_t njobs) {
+  if (nprobs > b->cap_probs || njobs > b->cap_jobs) {
+    if (b->staged) COMPAR_CUDA_TRY(cudaEventSynchronize(b->staged));
+    drop_graphs(b);  // graphs hold the old device pointers
+    cudaFreeHost(b->h_probs);
+    cudaFreeHost(b->h_jobs);
+    cudaFree(b->d_probs);
+    cudaFree(b->d_jobs);
+    b->h_probs = nullptr;
+    b->h_jobs = nullptr;
+    b->d_probs = nullptr;
+    b->d_jobs = nullptr;
+    const size_t cp = std::max<size_t>(nprobs, 2 * b->cap_probs);
+    const size_t cj = std::max<size_t>(njobs, 2 * b->cap_jobs);
+    COMPAR_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_probs), cp * sizeof(GroupProblem)));
+    COMPAR_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_jobs), cj * sizeof(PrepassJob)));
+    COMPAR_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&b->d_probs), cp * sizeof(GroupProblem)));
+    COMPAR_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&b->d_jobs), cj * sizeof(PrepassJob)));
+    b->cap_probs = cp;
+    b->cap_jobs = cj;
+  }
+  if (!b->staged) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
+  if (!b->capture) COMPAR_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+  return COMPAR_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+int grouped_mode(const compar_problem_t& p, double tol) {
+  if (p.dtype == COMPAR_BF16) return 0;
+  // TF32 keeps ~10 fraction bits: relative error ~1e-3 on random data
+  return tol >= 2e-3 ? 2 : 1;
+}
+
+bool grouped_eligible(const compar_problem_t& p) {
+  return (p.dtype == COMPAR_F32 || p.dtype == COMPAR_BF16) && p.m > 0 && p.n > 0 && p.k > 0 &&
+         p.m <= INT32_MAX && p.n <= INT32_MAX && p.k <= INT32_MAX;
+}
+
+GemmCall to_call(const compar_problem_t& p, double tol) {
+  GemmCall c;
+  c.m = p.m;
+  c.n = p.n;
+  c.k = p.k;
+  c.lda = p.lda;
+  c.ldb = p.ldb;
+  c.ldc = p.ldc;
+  c.dtype = p.dtype;
+  c.tol = tol;
+  c.A = p.A;
+  c.B = p.B;
+  c.C = p.C;
+  c.alpha = p.alpha;
+  c.beta = p.beta;
+  c.scale_a = p.scale_a;
+  c.scale_b = p.scale_b;
+  c.batch = 1;  // each problem is selected as a single GEMM
+  return c;
+}
+
+int run_loop(compar_ctx* ctx, int count, const compar_problem_t* probs, double tol,
+             cudaStream_t s) {
+  for (int i = 0; i < count; ++i) {
+    GemmCall c = to_call(probs[i], tol);
+    const int rc = gemm_call(ctx, c, s);
+    if (rc != COMPAR_OK) return rc;
+  }
+  return COMPAR_OK;
+}
+
+int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, double tol, int cfg,
+                cudaStream_t s) {
+  const int bn = cfg_bn(cfg);
+  std::vector<int> order;
+  for (int i = 0; i < count; ++i)
+    if (grouped_eligible(probs[i])) order.push_back(i);
+  // problems the grouped kernel does not take run one by one afterwards
+  auto run_rest = [&]() {
+    for (int i = 0; i < count; ++i) {
+      if (grouped_eligible(probs[i])) continue;
+      GemmCall c = to_call(probs[i], tol);
+      const int rc = gemm_call(ctx, c, s);
+      if (rc != COMPAR_OK) return rc;
+    }
+    return static_cast<int>(COMPAR_OK);
+  };
+  if (order.empty()) return run_rest();
+  auto tiles_of = [&](int i) {
+    return static_cast<int64_t>((probs[i].m + 127) / 128) * ((probs[i].n + bn - 1) / bn);
+  };
+  if (cfg_lpt(cfg)) {  // longest processing time first
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const double wa = static_cast<double>(tiles_of(a)) * probs[a].k * (grouped_mode(probs[a], tol) == 1 ? 3 : 1);
+      const double wb = static_cast<double>(tiles_of(b)) * probs[b].k * (grouped_mode(probs[b], tol) == 1 ? 3 : 1);
+      return wa > wb;
+    });
+  }
+  // ---- workspace layout
+  struct Plan {
+    int mode, pieces, elem;
+    int64_t ldk;
+    bool a_in_place;
+    size_t off_a, off_b, a_bytes, b_bytes;
+  };
+  std::vector<Plan> plan(order.size());
+  size_t ws_need = 0;
+  for (size_t q = 0; q < order.size(); ++q) {
+    const compar_problem_t& p = probs[order[q]];
+    Plan& P = plan[q];
+    P.mode = grouped_mode(p, tol);
+    P.pieces = P.mode == 1 ? 2 : 1;
+    P.elem = P.mode == 2 ? 4 : 2;
+    P.ldk = (p.k + 15) / 16 * 16;
+    const bool native = (P.mode == 0) || (P.mode == 2);  // operand type already right
+    P.a_in_place = native && (reinterpret_cast<uintptr_t>(p.A) % 16 == 0) &&
+                   ((p.lda * P.elem) % 16 == 0);
+    P.b_bytes = align256(static_cast<size_t>(p.n) * P.ldk * P.elem);
+    P.a_bytes = align256(static_cast<size_t>(p.m) * P.ldk * P.elem);
+    P.off_b = ws_need;
+    ws_need += P.pieces * P.b_bytes;
+    P.off_a = ws_need;
+    if (!P.a_in_place) ws_need += P.pieces * P.a_bytes;
+  }
+  int rc = ctx->ws.ensure(ws_need, s);
+  if (rc != COMPAR_OK) return rc;
+  BatchedState* b = state(ctx);
+  const size_t nprob = order.size();
+  rc = ensure_staging(b, nprob, 2 * nprob);
+  if (rc != COMPAR_OK) return rc;
+  // the previous launch must have consumed the staging buffers
+  COMPAR_CUDA_TRY(cudaEventSynchronize(b->staged));
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws.ptr);
+  int tile_acc = 0, ptile_acc = 0, njobs = 0;
+  for (size_t q = 0; q < nprob; ++q) {
+    const compar_problem_t& p = probs[order[q]];
+    const Plan& P = plan[q];
+    GroupProblem& G = b->h_probs[q];
+    memset(&G, 0, sizeof(G));
+    G.M = static_cast<int>(p.m);
+    G.N = static_cast<int>(p.n);
+    G.K = static_cast<int>(p.k);
+    const int kelems = 128 / P.elem;
+    G.num_kb = static_cast<int>((p.k + kelems - 1) / kelems);
+    G.tiles_m = static_cast<int>((p.m + 127) / 128);
+    G.tiles_n = static_cast<int>((p.n + bn - 1) / bn);
+    G.tile_start = tile_acc;
+    tile_acc += G.tiles_m * G.tiles_n;
+    G.mode = P.mode;
+    G.C = p.C;
+    G.ldc = p.ldc;
+    G.alpha = p.alpha;
+    G.beta = p.beta;
+    const CUtensorMapDataType dt =
+        P.mode == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    uint8_t* bw = ws + P.off_b;
+    uint8_t* aw = ws + P.off_a;
+    const void* a_src = P.a_in_place ? p.A : aw;
+    const int64_t a_ld = P.a_in_place ? p.lda : P.ldk;
+    rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128);
+    if (rc == COMPAR_OK)
+      rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn);
+    if (rc == COMPAR_OK && P.pieces == 2) {
+      rc = tma_encode_2d(&G.map_a2, dt, P.elem, aw + P.a_bytes, p.k, p.m, P.ldk, kelems, 128);
+      if (rc == COMPAR_OK)
+        rc = tma_encode_2d(&G.map_b2, dt, P.elem, bw + P.b_bytes, p.k, p.n, P.ldk, kelems, bn);
+    }
+    if (rc != COMPAR_OK) return rc;
+    const int out_kind = P.mode == 1 ? PP_SPLIT_BF16 : PP_COPY;
+    auto add_job = [&](const void* src, int64_t ld_src, int64_t rows, int64_t cols, void* dst,
+                       void* dst_lo, int transpose) {
+      PrepassJob& J = b->h_jobs[njobs++];
+      J.src = src;
+      J.dst = dst;
+      J.dst_lo = dst_lo;
+      J.ld_src = ld_src;
+      J.ld_dst = P.ldk;
+      J.rows = static_cast<int>(rows);
+      J.cols = static_cast<int>(cols);
+      J.in_type = p.dtype;
+      J.out_kind = out_kind;
+      J.transpose = transpose;
+      J.tiles_c = static_cast<int>((cols + 31) / 32);
+      J.tiles = static_cast<int>((rows + 31) / 32) * J.tiles_c;
+      J.tile_start = ptile_acc;
+      ptile_acc += J.tiles;
+    };
+    // B: K x N row-major -> N x K
+    add_job(p.B, p.ldb, p.k, p.n, bw, P.pieces == 2 ? bw + P.b_bytes : nullptr, 1);
+    if (!P.a_in_place)
+      add_job(p.A, p.lda, p.m, p.k, aw, P.pieces == 2 ? aw + P.a_bytes : nullptr, 0);
+  }
+  const int ngroup = static_cast<int>(nprob);
+  const auto key = std::make_tuple(ngroup, tile_acc, njobs, ptile_acc, bn);
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    COMPAR_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launch_count();
+    cudaMemcpyAsync(b->d_probs, b->h_probs, nprob * sizeof(GroupProblem), cudaMemcpyHostToDevice,
+                    b->capture);
+    cudaMemcpyAsync(b->d_jobs, b->h_jobs, njobs * sizeof(PrepassJob), cudaMemcpyHostToDevice,
+                    b->capture);
+    int rc1 = launch_grouped_prepass(b->d_jobs, njobs, ptile_acc, ctx->num_sms, b->capture);
+    int rc2 = launch_grouped_gemm(bn, b->d_probs, ngroup, tile_acc, ctx->guard, ctx->num_sms,
+                                  b->capture);
+    count_launch(static_cast<int>(before - launch_count()));  // captured, not run
+    const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);
+    if (rc1 != COMPAR_OK || rc2 != COMPAR_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (ec != cudaSuccess) set_last_cuda_error(ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+      return rc1 != COMPAR_OK ? rc1 : (rc2 != COMPAR_OK ? rc2 : COMPAR_ERR_CUDA);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      set_last_cuda_error(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+      return COMPAR_ERR_CUDA;
+    }
+    it = b->graphs.emplace(key, exec).first;
+  }
+  COMPAR_CUDA_TRY(cudaGraphLaunch(it->second, s));
+  count_launch(2);
+  COMPAR_CUDA_TRY(cudaEventRecord(b->staged, s));
+  return run_rest();
+}
+
+uint64_t signature(int count, const compar_problem_t* probs, double tol) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    h ^= x;
+    h *= 1099511628211ull;
+  };
+  mix(static_cast<uint64_t>(count));
+  mix(static_cast<uint64_t>(static_cast<int64_t>(std::floor(2.0 * std::log10(tol)))));
+  for (int i = 0; i < count; ++i) {
+    mix(static_cast<uint64_t>(probs[i].m));
+    mix(static_cast<uint64_t>(probs[i].n));
+    mix(static_cast<uint64_t>(probs[i].k));
+    mix(static_cast<uint64_t>(probs[i].dtype));
+  }
+  return h;
+}
+
+int validate(compar_ctx* ctx, int count, const compar_problem_t* probs) {
   if (!ctx || count < 0 || (count > 0 && !probs)) return COMPAR_ERR_INVALID;
-  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < count; ++i) {
     const compar_problem_t& p = probs[i];
     if (p.m < 0 || p.n < 0 || p.k < 0 || p.lda < p.k || p.ldb < p.n || p.ldc < p.n)
@@ -25,28 +308,98 @@ extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_pro
       return COMPAR_ERR_INVALID;
     if (p.m > 0 && p.n > 0 && !p.C) return COMPAR_ERR_INVALID;
     if (p.m > 0 && p.n > 0 && p.k > 0 && (!p.A || !p.B)) return COMPAR_ERR_INVALID;
+    if (!std::isfinite(p.alpha) || !std::isfinite(p.beta)) return COMPAR_ERR_INVALID;
   }
-  for (int i = 0; i < count; ++i) {
-    const compar_problem_t& p = probs[i];
-    GemmCall c;
-    c.m = p.m;
-    c.n = p.n;
-    c.k = p.k;
-    c.lda = p.lda;
-    c.ldb = p.ldb;
-    c.ldc = p.ldc;
-    c.dtype = p.dtype;
-    c.tol = tol > 0 ? tol : 1e-5;
-    c.A = p.A;
-    c.B = p.B;
-    c.C = p.C;
-    c.alpha = p.alpha;
-    c.beta = p.beta;
-    c.scale_a = p.scale_a;
-    c.scale_b = p.scale_b;
-    c.batch = count;
-    const int rc = gemm_call(ctx, c, s);
-    if (rc != COMPAR_OK) return rc;
+  return COMPAR_OK;
+}
+
+int run_cfg(compar_ctx* ctx, int cfg, int count, const compar_problem_t* probs, double tol,
+            cudaStream_t s) {
+  return cfg == kCfgLoop ? run_loop(ctx, count, probs, tol, s)
+                         : run_grouped(ctx, count, probs, tol, cfg, s);
+}
+
+}  // namespace
+
+void batched_release(compar_ctx* ctx) {
+  auto* b = static_cast<BatchedState*>(ctx->batched_state);
+  if (!b) return;
+  if (b->staged) cudaEventSynchronize(b->staged);
+  drop_graphs(b);
+  cudaFreeHost(b->h_probs);
+  cudaFreeHost(b->h_jobs);
+  cudaFree(b->d_probs);
+  cudaFree(b->d_jobs);
+  if (b->staged) cudaEventDestroy(b->staged);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+  ctx->batched_state = nullptr;
+}
+
+}  // namespace compar
+
+using namespace compar;
+
+extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
+                                   double tol, void* stream) {
+  int rc = validate(ctx, count, probs);
+  if (rc != COMPAR_OK) return rc;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
+  if (count == 0) return COMPAR_OK;
+  tol = tol > 0 ? tol : 1e-5;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ctx->forced >= 0 && ctx->forced < COMPAR_V_COUNT) return run_loop(ctx, count, probs, tol, s);
+  int cfg = 1;
+  auto it = ctx->batched_cfg.find(signature(count, probs, tol));
+  if (it != ctx->batched_cfg.end()) cfg = it->second;
+  if (ctx->forced == COMPAR_V_GROUPED && cfg == kCfgLoop) cfg = 1;
+  ctx->last_variant = cfg == kCfgLoop ? -1 : COMPAR_V_GROUPED;
+  return run_cfg(ctx, cfg, count, probs, tol, s);
+}
+
+extern "C" int compar_autotune_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
+                                       double tol, void* stream, float* times_ms, int* best) {
+  int rc = validate(ctx, count, probs);
+  if (rc != COMPAR_OK) return rc;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
+  if (count == 0) return COMPAR_ERR_INVALID;
+  tol = tol > 0 ? tol : 1e-5;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  COMPAR_CUDA_TRY(cudaEventCreate(&e0));
+  COMPAR_CUDA_TRY(cudaEventCreate(&e1));
+  int best_cfg = -1;
+  float best_ms = INFINITY;
+  for (int cfg = 0; cfg <= 4; ++cfg) {
+    float med = INFINITY;
+    rc = run_cfg(ctx, cfg, count, probs, tol, s);  // warm-up (and graph capture)
+    if (rc == COMPAR_OK) {
+      std::vector<float> t;
+      for (int r = 0; r < 3 && rc == COMPAR_OK; ++r) {
+        cudaEventRecord(e0, s);
+        rc = run_cfg(ctx, cfg, count, probs, tol, s);
+        cudaEventRecord(e1, s);
+        float ms = 0;
+        if (rc == COMPAR_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+          t.push_back(ms);
+      }
+      if (!t.empty()) {
+        std::sort(t.begin(), t.end());
+        med = t[t.size() / 2];
+      }
+    }
+    if (rc != COMPAR_OK) break;
+    if (times_ms) times_ms[cfg] = med;
+    if (med < best_ms) {
+      best_ms = med;
+      best_cfg = cfg;
+    }
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != COMPAR_OK) return rc;
+  ctx->batched_cfg[signature(count, probs, tol)] = best_cfg;
+  if (best) *best = best_cfg;
   return COMPAR_OK;
 }

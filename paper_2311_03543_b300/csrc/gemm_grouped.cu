@@ -1,0 +1,295 @@
+// Persistent grouped GEMM: many independent problems of uneven sizes in one
+// launch (compar_gemm_batched).  The paper's runtime submits one task per
+// call and schedules tasks over processing units (Sec. 2.2); for a batch of
+// small GEMMs on one GPU the B300-native form of that is a single persistent
+// kernel whose CTAs walk a shared tile list spanning every problem.
+//
+// Per-problem mode (same stage layout, chosen per tile at run time):
+//   mode 0 BF16   : bf16 operands, one kind::f16 MMA per 32-byte K step
+//   mode 1 SPLIT3 : 3xBF16 pieces {hi, lo}, three kind::f16 MMAs per K step
+//   mode 2 TF32   : float32 operands, one kind::tf32 MMA per K step
+// Every mode accumulates each chunk of 4 stages in TMEM and adds the chunk
+// into FP32 registers (promotion), so no mode carries an accumulation error
+// that grows with K.
+//
+// Problem descriptors (tensor maps, sizes, C, scalars) live in device memory,
+// written by the host each call; the operand pre-pass for every problem runs
+// as one grouped launch before the GEMM.  Both launches and the descriptor
+// upload are captured once per batch shape in a CUDA graph.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.h"
+#include "grouped.h"
+#include "ptx.cuh"
+
+namespace compar {
+namespace {
+
+using dev::Kind;
+
+constexpr int kBM = 128;
+constexpr int kRow = 128;  // bytes of K per stage
+constexpr int kThreads = 192;
+constexpr int kEpi = 128;
+constexpr int kChunkKB = 4;  // promotion every 4 stages
+
+template <int BN>
+struct GLayout {
+  static constexpr int kA = kBM * kRow;       // one A piece
+  static constexpr int kB = BN * kRow;        // one B piece
+  static constexpr int kStage = 2 * (kA + kB);
+  static constexpr int kBar = 256;
+  static constexpr int kStagesRaw = (232448 - 1024 - kBar) / kStage;
+  static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
+  static constexpr int kSmem = 1024 + kStages * kStage + kBar;
+  static constexpr int kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
+};
+
+__device__ __forceinline__ int find_problem(const GroupProblem* __restrict__ P, int count,
+                                            int tile) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last problem with tile_start <= tile
+    const int mid = (lo + hi + 1) >> 1;
+    if (P[mid].tile_start <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool drain(uint64_t* bar, uint32_t parity, uint64_t budget) {
+  const uint64_t t0 = dev::globaltimer_ns();
+  while (!dev::mbar_try_wait(bar, parity))
+    if (dev::globaltimer_ns() - t0 > budget) return false;
+  return true;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    grouped_gemm_kernel(const GroupProblem* __restrict__ probs, int count, int total_tiles,
+                        int* err_word, unsigned long long budget_ns) {
+  using L = GLayout<BN>;
+  constexpr int S = L::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  // stage s: [A_hi][A_lo][B_hi][B_lo]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::kStage);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drainb = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      dev::mbar_init(&full[s], 1);
+      dev::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      dev::mbar_init(&tfull[a], 1);
+      dev::mbar_init(&tempty[a], kEpi);
+    }
+    dev::mbar_init(drainb, 1);
+    *abort_flag = 0;
+    dev::fence_barrier_init();
+  }
+  if (warp == 1) {
+    dev::tmem_alloc(tmem_slot, L::kTmemCols);
+    dev::tmem_relinquish();
+  }
+  dev::tc_fence_before();
+  __syncthreads();
+  dev::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const dev::WaitCtx w{abort_flag, err_word, budget_ns};
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    uint32_t stage = 0, phase = 0, issued = 0, issued_par = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const int local = tile - P.tile_start;
+      const int mb = local % P.tiles_m, nb = local / P.tiles_m;
+      const int pieces = P.mode == 1 ? 2 : 1;
+      const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
+      const int kelems = P.mode == 2 ? kRow / 4 : kRow / 2;
+      for (int kb = 0; kb < P.num_kb; ++kb) {
+        if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
+          ok = false;
+          break;
+        }
+        dev::mbar_arrive_expect_tx(&full[stage], tx);
+        uint8_t* st = smem + stage * L::kStage;
+        const int x = kb * kelems;
+        dev::tma_load_2d(st, &P.map_a, &full[stage], x, mb * kBM);
+        dev::tma_load_2d(st + 2 * L::kA, &P.map_b, &full[stage], x, nb * BN);
+        if (pieces == 2) {
+          dev::tma_load_2d(st + L::kA, &P.map_a2, &full[stage], x, mb * kBM);
+          dev::tma_load_2d(st + 2 * L::kA + L::kB, &P.map_b2, &full[stage], x, nb * BN);
+        }
+        issued |= 1u << stage;
+        issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (!ok)
+      for (int s = 0; s < S; ++s)
+        if (issued & (1u << s)) drain(&full[s], (issued_par >> s) & 1, budget_ns);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    constexpr uint32_t id_f16 = dev::make_idesc(1, 1, kBM, BN);
+    constexpr uint32_t id_tf32 = dev::make_idesc(2, 2, kBM, BN);
+    uint32_t stage = 0, phase = 0;
+    int acc_iter = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const int mode = P.mode;
+      for (int kb0 = 0; ok && kb0 < P.num_kb; kb0 += kChunkKB, ++acc_iter) {
+        const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
+        if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
+          ok = false;
+          break;
+        }
+        dev::tc_fence_after();
+        const uint32_t d = tmem_base + acc * BN;
+        const int kb_end = min(P.num_kb, kb0 + kChunkKB);
+        for (int kb = kb0; kb < kb_end; ++kb) {
+          if (!dev::mbar_wait(&full[stage], phase, w)) {
+            ok = false;
+            break;
+          }
+          dev::tc_fence_after();
+          const uint32_t s0 = dev::smem_u32(smem + stage * L::kStage);
+          const uint64_t da = dev::smem_desc_sw128_kmajor(s0);
+          const uint64_t da2 = dev::smem_desc_sw128_kmajor(s0 + L::kA);
+          const uint64_t db = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA);
+          const uint64_t db2 = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA + L::kB);
+#pragma unroll
+          for (int kk = 0; kk < kRow / 32; ++kk) {
+            const uint64_t ko = static_cast<uint64_t>(kk * 32) >> 4;
+            const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
+            if (mode == 2) {
+              dev::mma<Kind::TF32>(d, da + ko, db + ko, id_tf32, first);
+            } else {
+              dev::mma<Kind::F16>(d, da + ko, db + ko, id_f16, first);
+              if (mode == 1) {
+                dev::mma<Kind::F16>(d, da + ko, db2 + ko, id_f16, 1u);
+                dev::mma<Kind::F16>(d, da2 + ko, db + ko, id_f16, 1u);
+              }
+            }
+          }
+          dev::mma_commit(&empty[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        dev::mma_commit(&tfull[acc]);
+      }
+    }
+    dev::mma_commit(drainb);
+    drain(drainb, 0, budget_ns);
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const int quarter = warp & 3;
+    int acc_iter = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const int local = tile - P.tile_start;
+      const int mb = local % P.tiles_m, nb = local / P.tiles_m;
+      const int row = mb * kBM + quarter * 32 + lane;
+      float sum[BN];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+      const int chunks = (P.num_kb + kChunkKB - 1) / kChunkKB;
+      for (int ch = 0; ch < chunks; ++ch, ++acc_iter) {
+        const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
+        if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) {
+          ok = false;
+          break;
+        }
+        dev::tc_fence_after();
+        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t r[32];
+          dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+          dev::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __uint_as_float(r[j]);
+        }
+        dev::tc_fence_before();
+        dev::mbar_arrive(&tempty[acc]);
+      }
+      if (!ok) break;
+      if (row < P.M) {
+        float* crow = P.C + static_cast<int64_t>(row) * P.ldc;
+        const int col0 = nb * BN;
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+          if (col0 + j < P.N) {
+            float v = P.alpha * sum[j];
+            if (P.beta != 0.f) v = fmaf(P.beta, crow[col0 + j], v);
+            crow[col0 + j] = v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    dev::tc_fence_after();
+    dev::tmem_dealloc(tmem_base, L::kTmemCols);
+  }
+}
+
+}  // namespace
+
+int grouped_smem_bytes(int bn) {
+  return bn == 64 ? GLayout<64>::kSmem : GLayout<128>::kSmem;
+}
+
+int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int total_tiles,
+                        const DeviceGuard& g, int num_sms, cudaStream_t s) {
+  if (count <= 0 || total_tiles <= 0) return COMPAR_OK;
+  const int grid = std::min(total_tiles, num_sms);
+  if (bn == 64) {
+    static bool attr = false;
+    if (!attr) {
+      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<64>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           GLayout<64>::kSmem));
+      attr = true;
+    }
+    grouped_gemm_kernel<64><<<grid, kThreads, GLayout<64>::kSmem, s>>>(
+        d_probs, count, total_tiles, g.err_word, g.budget_ns);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<128>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           GLayout<128>::kSmem));
+      attr = true;
+    }
+    grouped_gemm_kernel<128><<<grid, kThreads, GLayout<128>::kSmem, s>>>(
+        d_probs, count, total_tiles, g.err_word, g.budget_ns);
+  }
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return COMPAR_OK;
+}
+
+}  // namespace compar

@@ -7,7 +7,11 @@
 //    global loads and double-buffered shared-memory tiles; optional split-K
 //    with a separate reduction pass.
 //
-// Row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc).
+// Row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc).  Inputs may be
+// float32, bf16 (uint16 bit patterns) or E4M3 (bytes); they are widened to
+// float32 on load and every product and sum is an FP32 FMA.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,16 +22,45 @@
 namespace compar {
 namespace {
 
+// ------------------------------------------------------------------ element types
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(uint16_t b) {  // bf16: the high half of a float32
+  return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+__device__ __forceinline__ float to_f32(uint8_t c) {   // E4M3 -> half (exact) -> float
+  const __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(c), __NV_E4M3);
+  return __half2float(__half(h));
+}
+template <typename T>
+__device__ __forceinline__ float ld1(const T* p) { return to_f32(__ldg(p)); }
+
+// Four consecutive elements with one aligned load (16, 8 or 4 bytes).
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const uint16_t* p, float (&o)[4]) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xFFFF0000u);
+  o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xFFFF0000u);
+}
+__device__ __forceinline__ void ld4(const uint8_t* p, float (&o)[4]) {
+  const uint32_t v = __ldg(reinterpret_cast<const unsigned int*>(p));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = to_f32(static_cast<uint8_t>(v >> (8 * q)));
+}
+
 // ------------------------------------------------------------------ naive
-__global__ void gemm_naive_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
-                                  int64_t lda, const float* __restrict__ B, int64_t ldb,
+template <typename T>
+__global__ void gemm_naive_kernel(int M, int N, int K, float alpha, const T* __restrict__ A,
+                                  int64_t lda, const T* __restrict__ B, int64_t ldb,
                                   float beta, float* __restrict__ C, int64_t ldc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= M || j >= N) return;
-  const float* a = A + static_cast<int64_t>(i) * lda;
+  const T* a = A + static_cast<int64_t>(i) * lda;
   float acc = 0.f;
-  for (int p = 0; p < K; ++p) acc = fmaf(a[p], B[static_cast<int64_t>(p) * ldb + j], acc);
+  for (int p = 0; p < K; ++p) acc = fmaf(ld1(a + p), ld1(B + static_cast<int64_t>(p) * ldb + j), acc);
   float* c = C + static_cast<int64_t>(i) * ldc + j;
   *c = (beta == 0.f) ? alpha * acc : fmaf(alpha, acc, beta * *c);
 }
@@ -59,10 +92,10 @@ struct SimtCfg {
   static_assert(kAElems % 4 == 0 && kBElems % 4 == 0, "vector loads");
 };
 
-template <int BM, int BN, int BK, int TM, int TN, bool VEC>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads)
     gemm_simt_kernel(int M, int N, int K, int k_per_split, float alpha,
-                     const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
+                     const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
                      int64_t ldb, float beta, float* __restrict__ C, int64_t ldc,
                      float* __restrict__ partial) {
   using Cfg = SimtCfg<BM, BN, BK, TM, TN, VEC>;
@@ -88,15 +121,14 @@ __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads)
       const int r = e / BK, c = e % BK;
       const int gi = m0 + r, gk = k0 + c;
       if constexpr (VEC) {
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gi < M && gk < k_end)
-          x = __ldg(reinterpret_cast<const float4*>(A + static_cast<int64_t>(gi) * lda + gk));
-        ra[4 * v + 0] = x.x; ra[4 * v + 1] = x.y; ra[4 * v + 2] = x.z; ra[4 * v + 3] = x.w;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (gi < M && gk < k_end) ld4(A + static_cast<int64_t>(gi) * lda + gk, x);
+        ra[4 * v + 0] = x[0]; ra[4 * v + 1] = x[1]; ra[4 * v + 2] = x[2]; ra[4 * v + 3] = x[3];
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           ra[4 * v + q] = (gi < M && gk + q < k_end)
-                              ? __ldg(A + static_cast<int64_t>(gi) * lda + gk + q) : 0.f;
+                              ? ld1(A + static_cast<int64_t>(gi) * lda + gk + q) : 0.f;
       }
     }
   };
@@ -117,15 +149,14 @@ __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads)
       const int r = e / BN, c = e % BN;
       const int gk = k0 + r, gj = n0 + c;
       if constexpr (VEC) {
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gk < k_end && gj < N)
-          x = __ldg(reinterpret_cast<const float4*>(B + static_cast<int64_t>(gk) * ldb + gj));
-        rb[4 * v + 0] = x.x; rb[4 * v + 1] = x.y; rb[4 * v + 2] = x.z; rb[4 * v + 3] = x.w;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (gk < k_end && gj < N) ld4(B + static_cast<int64_t>(gk) * ldb + gj, x);
+        rb[4 * v + 0] = x[0]; rb[4 * v + 1] = x[1]; rb[4 * v + 2] = x[2]; rb[4 * v + 3] = x[3];
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           rb[4 * v + q] = (gk < k_end && gj + q < N)
-                              ? __ldg(B + static_cast<int64_t>(gk) * ldb + gj + q) : 0.f;
+                              ? ld1(B + static_cast<int64_t>(gk) * ldb + gj + q) : 0.f;
       }
     }
   };
@@ -242,7 +273,12 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
   }
 }
 
-template <int BM, int BN, int BK, int TM, int TN>
+// alpha with the fp8 dequantisation factors folded in
+float effective_alpha(const GemmCall& c) {
+  return c.dtype == COMPAR_F8E4M3 ? c.alpha * c.scale_a * c.scale_b : c.alpha;
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
 int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
              cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
@@ -266,28 +302,30 @@ int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms
     if (rc != COMPAR_OK) return rc;
     partial = static_cast<float*>(ws.ptr);
   }
+  constexpr uintptr_t kVecBytes = 4 * sizeof(T);
   const bool vec = (c.k % 4 == 0) && (c.n % 4 == 0) && (c.lda % 4 == 0) && (c.ldb % 4 == 0) &&
-                   (c.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) &&
-                   (reinterpret_cast<uintptr_t>(c.B) % 16 == 0) &&
+                   (c.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(c.A) % kVecBytes == 0) &&
+                   (reinterpret_cast<uintptr_t>(c.B) % kVecBytes == 0) &&
                    (reinterpret_cast<uintptr_t>(c.C) % 16 == 0);
   dim3 grid(tiles_n, tiles_m, splits);
   constexpr int threads = SimtCfg<BM, BN, BK, TM, TN, true>::kThreads;
-  const float* A = static_cast<const float*>(c.A);
-  const float* B = static_cast<const float*>(c.B);
+  const T* A = static_cast<const T*>(c.A);
+  const T* B = static_cast<const T*>(c.B);
+  const float alpha = effective_alpha(c);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   if (vec)
-    gemm_simt_kernel<BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
-        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+    gemm_simt_kernel<T, BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
   else
-    gemm_simt_kernel<BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
-        M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
+    gemm_simt_kernel<T, BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
+        M, N, K, k_per, alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
   COMPAR_CUDA_TRY(cudaGetLastError());
   if (g.prof) g.prof->end(ev, s, COMPAR_V_SIMT);
   count_launch();
   if (splits > 1) {
     const int64_t total = static_cast<int64_t>(M) * N;
     const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
-    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, partial, c.alpha, c.beta, c.C,
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, partial, alpha, c.beta, c.C,
                                                 c.ldc);
     COMPAR_CUDA_TRY(cudaGetLastError());
     count_launch();
@@ -295,28 +333,45 @@ int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms
   return COMPAR_OK;
 }
 
-}  // namespace
-
-int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
+template <typename T>
+int run_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
   dim3 block(16, 16);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   dim3 grid(static_cast<unsigned>((c.n + 15) / 16), static_cast<unsigned>((c.m + 15) / 16));
-  gemm_naive_kernel<<<grid, block, 0, s>>>(static_cast<int>(c.m), static_cast<int>(c.n),
-                                           static_cast<int>(c.k), c.alpha,
-                                           static_cast<const float*>(c.A), c.lda,
-                                           static_cast<const float*>(c.B), c.ldb, c.beta, c.C,
-                                           c.ldc);
+  gemm_naive_kernel<T><<<grid, block, 0, s>>>(
+      static_cast<int>(c.m), static_cast<int>(c.n), static_cast<int>(c.k), effective_alpha(c),
+      static_cast<const T*>(c.A), c.lda, static_cast<const T*>(c.B), c.ldb, c.beta, c.C, c.ldc);
   COMPAR_CUDA_TRY(cudaGetLastError());
   if (g.prof) g.prof->end(ev, s, COMPAR_V_NAIVE);
   count_launch();
   return COMPAR_OK;
 }
 
+template <typename T>
+int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
+                  cudaStream_t s) {
+  // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
+  if (c.m <= 48) return run_simt<T, 32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
+  return run_simt<T, 128, 128, 16, 8, 8>(c, ws, g, num_sms, s);
+}
+
+}  // namespace
+
+int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
+  switch (c.dtype) {
+    case COMPAR_BF16: return run_naive<uint16_t>(c, g, s);
+    case COMPAR_F8E4M3: return run_naive<uint8_t>(c, g, s);
+    default: return run_naive<float>(c, g, s);
+  }
+}
+
 int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                 cudaStream_t s) {
-  // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
-  if (c.m <= 48) return run_simt<32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
-  return run_simt<128, 128, 16, 8, 8>(c, ws, g, num_sms, s);
+  switch (c.dtype) {
+    case COMPAR_BF16: return dispatch_simt<uint16_t>(c, ws, g, num_sms, s);
+    case COMPAR_F8E4M3: return dispatch_simt<uint8_t>(c, ws, g, num_sms, s);
+    default: return dispatch_simt<float>(c, ws, g, num_sms, s);
+  }
 }
 
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s) {
@@ -363,10 +418,10 @@ int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, in
   const float* A = static_cast<const float*>(c.A);
   const float* B = static_cast<const float*>(c.B);
   if (vec)
-    gemm_simt_kernel<BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
+    gemm_simt_kernel<float, BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(
         M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
   else
-    gemm_simt_kernel<BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
+    gemm_simt_kernel<float, BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(
         M, N, K, k_per, c.alpha, A, c.lda, B, c.ldb, c.beta, c.C, c.ldc, partial);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();

@@ -16,6 +16,7 @@
 #include <cstdint>
 
 #include "common.h"
+#include "grouped.h"
 
 namespace compar {
 namespace {
@@ -152,7 +153,67 @@ int grid_for(int64_t total) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8192)));
 }
 
+// ------------------------------------------------------------------ grouped
+__device__ __forceinline__ int find_job(const PrepassJob* __restrict__ J, int n, int tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (J[mid].tile_start <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Every operand re-layout of a batch in one launch: blocks stride over the
+// concatenated 32x32 tile lists of all jobs.
+__global__ void grouped_prepass_kernel(const PrepassJob* __restrict__ jobs, int njobs,
+                                       int total_tiles) {
+  __shared__ float tile[32][33];
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const PrepassJob& J = jobs[find_job(jobs, njobs, t)];
+    const int local = t - J.tile_start;
+    const int64_t r0 = static_cast<int64_t>(local / J.tiles_c) * 32;
+    const int64_t c0 = static_cast<int64_t>(local % J.tiles_c) * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int64_t r = r0 + i, c = c0 + threadIdx.x;
+      float v = 0.f;
+      if (r < J.rows && c < J.cols) {
+        if (J.in_type == COMPAR_F32)
+          v = static_cast<const float*>(J.src)[r * J.ld_src + c];
+        else
+          v = __bfloat162float(static_cast<const __nv_bfloat16*>(J.src)[r * J.ld_src + c]);
+      }
+      tile[i][threadIdx.x] = v;
+    }
+    __syncthreads();
+    // a bf16 copy goes through float and back, which is exact
+    const F32Out o{J.out_kind == PP_COPY ? (J.in_type == COMPAR_F32 ? PP_F32 : PP_BF16)
+                                         : J.out_kind,
+                   1.f};
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      if (J.transpose) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < J.cols && r < J.rows) store_converted(o, tile[threadIdx.x][i], J.dst, J.dst_lo, c * J.ld_dst + r);
+      } else {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < J.rows && c < J.cols) store_converted(o, tile[i][threadIdx.x], J.dst, J.dst_lo, r * J.ld_dst + c);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles, int num_sms,
+                           cudaStream_t s) {
+  if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
+  const int grid = std::min(total_tiles, 8 * num_sms);
+  grouped_prepass_kernel<<<grid, dim3(32, 8), 0, s>>>(d_jobs, njobs, total_tiles);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return COMPAR_OK;
+}
 
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols, int64_t ldx,
                     void* Y, int out_kind, int64_t ldy, bool transpose, void* Y_lo,

@@ -86,6 +86,7 @@ struct MlpModel {
   std::array<MlpParams, kEnsemble> members;
   std::array<float, kNumFeatures> feat_mean{}, feat_std{};
   std::array<float, kNumFeatures> feat_min{}, feat_max{};
+  std::array<float, kOutputs> out_mean{}, out_std{};  // target standardisation
   float conf_std = 0.15f;  // max ensemble std of predicted log time
   float box_slack = 0.10f; // fraction of the training range allowed outside
 };
@@ -145,7 +146,8 @@ struct compar_ctx {
   std::unordered_map<compar::DecisionKey, int, compar::DecisionKeyHash> decisions;
   std::vector<compar::PendingTiming> pending;
   std::vector<cudaEvent_t> event_pool;
-  int grouped_tile_cfg = -1;  // autotuned tile configuration of the grouped kernel
+  // batch signature -> autotuned batched configuration (0 loop, 1..4 grouped)
+  std::unordered_map<uint64_t, int> batched_cfg;
   void* batched_state = nullptr;
   // MLP device buffers (selector inference / training), owned here.
   void* mlp_dev = nullptr;

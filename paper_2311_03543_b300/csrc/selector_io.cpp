@@ -94,6 +94,8 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
   for (float x : mm.feat_std) w.put(x);
   for (float x : mm.feat_min) w.put(x);
   for (float x : mm.feat_max) w.put(x);
+  for (float x : mm.out_mean) w.put(x);
+  for (float x : mm.out_std) w.put(x);
   w.put(mm.conf_std);
   w.put(mm.box_slack);
   w.put<uint32_t>(static_cast<uint32_t>(MlpParams::count()));
@@ -106,7 +108,11 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
     }
     w.put_floats(flat);
   }
-  w.put<int32_t>(ctx->grouped_tile_cfg);
+  w.put<uint32_t>(static_cast<uint32_t>(ctx->batched_cfg.size()));
+  for (const auto& kv : ctx->batched_cfg) {
+    w.put<uint64_t>(kv.first);
+    w.put<int32_t>(kv.second);
+  }
 
   std::ofstream f(path, std::ios::binary | std::ios::trunc);
   if (!f) return COMPAR_ERR_IO;
@@ -167,6 +173,8 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
   for (float& x : mm.feat_std) x = r.get<float>();
   for (float& x : mm.feat_min) x = r.get<float>();
   for (float& x : mm.feat_max) x = r.get<float>();
+  for (float& x : mm.out_mean) x = r.get<float>();
+  for (float& x : mm.out_std) x = r.get<float>();
   mm.conf_std = r.get<float>();
   mm.box_slack = r.get<float>();
   const uint32_t np = r.get<uint32_t>();
@@ -177,13 +185,20 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
     r.get_floats(flat.data(), flat.size());
     m.unflatten(flat.data());
   }
-  const int32_t tile_cfg = r.get<int32_t>();
+  std::unordered_map<uint64_t, int> batched;
+  const uint32_t nb = r.get<uint32_t>();
+  for (uint32_t i = 0; r.ok && i < nb; ++i) {
+    const uint64_t sig = r.get<uint64_t>();
+    const int32_t cfg = r.get<int32_t>();
+    if (cfg < 0 || cfg > 4) r.ok = false;
+    batched[sig] = cfg;
+  }
   if (!r.ok || r.off != nbytes) return COMPAR_ERR_IO;
 
   ctx->hist = std::move(hist);
   ctx->err = err;
   ctx->mlp = mm;
-  ctx->grouped_tile_cfg = tile_cfg;
+  ctx->batched_cfg = std::move(batched);
   ctx->decisions.clear();
   mlp_release(ctx);  // device copies of the old weights are stale
   return COMPAR_OK;

@@ -1,0 +1,198 @@
+"""Batched calls (GPU): the persistent grouped kernel in its CUDA graph and
+the per-GEMM loop, against the FP64 oracle problem by problem.
+
+Modes: float32 problems at tol 1e-5 run as 3xBF16 (<= 1e-5 vs the oracle);
+at a loose tolerance as TF32 (<= 2e-3); bf16 problems exactly on their bf16
+values (<= 1e-5); E4M3 problems leave the grouped launch and run one by one."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import numerics as N
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2311_03543_b300 as cp
+    c = cp.Context(0)
+    yield c
+    c.close()
+
+
+def _make_batch(specs, seed):
+    """specs: (m, n, k, dtype, lda_pad, ldb_pad, ldc_pad, alpha, beta)."""
+    import torch
+    from gpu_util import dev
+    probs, host = [], []
+    for i, (m, n, k, dt, pa, pb, pc, alpha, beta) in enumerate(specs):
+        lda, ldb, ldc = k + pa, n + pb, n + pc
+        if dt == W.F32:
+            A = W.uniform(m, lda, seed + 3 * i)
+            B = W.uniform(k, ldb, seed + 3 * i + 1)
+        elif dt == W.BF16:
+            A = W.bf16_input(m, lda, seed + 3 * i)
+            B = W.bf16_input(k, ldb, seed + 3 * i + 1)
+        else:
+            A = W.fp8_input(m, lda, seed + 3 * i, 7)
+            B = W.fp8_input(k, ldb, seed + 3 * i + 1, 7)
+        C0 = W.uniform(m, ldc, seed + 3 * i + 2)
+        dA, dB, dC = dev(A), dev(B), dev(C0)
+        probs.append(dict(m=m, n=n, k=k, lda=lda, ldb=ldb, ldc=ldc, dtype=dt,
+                          A=dA.data_ptr(), B=dB.data_ptr(), C=dC.data_ptr(),
+                          alpha=alpha, beta=beta))
+        host.append((A, B, C0, dA, dB, dC))
+    return probs, host
+
+
+def _exact(X, dt):
+    if dt == W.F32:
+        return X.astype(np.float64)
+    if dt == W.BF16:
+        return N.bf16_to_f32(X).astype(np.float64)
+    return N.e4m3_to_f64(X)
+
+
+def _check(specs, host, tol_f32):
+    import torch
+    torch.cuda.synchronize()
+    worst = 0.0
+    for (m, n, k, dt, pa, pb, pc, alpha, beta), (A, B, C0, dA, dB, dC) in zip(specs, host):
+        if m == 0 or n == 0:
+            continue
+        got = dC.cpu().numpy()[:, :n]
+        ref = oracle.gemm(_exact(A[:, :k], dt), _exact(B[:, :n], dt), alpha=alpha, beta=beta,
+                          C0=C0[:, :n].astype(np.float64))
+        err = N.rel_frobenius(got, ref)
+        lim = tol_f32 if dt == W.F32 else 1e-5
+        assert err <= lim, (m, n, k, dt, err)
+        worst = max(worst, err)
+        # padding columns of C are never written
+        assert np.array_equal(dC.cpu().numpy()[:, n:], C0[:, n:])
+    return worst
+
+
+def _random_specs(count, seed, lo=1, hi=300, dtypes=(W.F32, W.BF16)):
+    g = np.random.default_rng(seed)
+    specs = []
+    for _ in range(count):
+        m, n, k = (int(x) for x in g.integers(lo, hi, size=3))
+        dt = dtypes[int(g.integers(0, len(dtypes)))]
+        pads = [int(x) for x in g.integers(0, 3, size=3)]
+        specs.append((m, n, k, dt, pads[0], pads[1], pads[2], float(g.choice([1.0, 0.5, -2.0])),
+                      float(g.choice([0.0, 1.0, -0.5]))))
+    return specs
+
+
+def test_grouped_fp32_accurate_and_bf16(ctx):
+    import paper_2311_03543_b300 as cp
+    specs = _random_specs(40, seed=1)
+    probs, host = _make_batch(specs, 100)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
+    _check(specs, host, 1e-5)
+
+
+def test_grouped_tf32_mode(ctx):
+    import paper_2311_03543_b300 as cp
+    specs = _random_specs(24, seed=2, dtypes=(W.F32,))
+    probs, host = _make_batch(specs, 200)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=1e-2)
+    finally:
+        ctx.force_variant(None)
+    _check(specs, host, 2e-3)
+
+
+def test_fp8_and_empty_problems_in_a_batch(ctx):
+    import paper_2311_03543_b300 as cp
+    specs = [(64, 80, 96, W.F8E4M3, 0, 0, 0, 1.0, 0.0), (33, 17, 0, W.F32, 0, 0, 0, 1.0, 2.0),
+             (0, 5, 7, W.F32, 0, 0, 0, 1.0, 0.0), (100, 120, 140, W.F32, 1, 0, 0, 1.0, 0.0),
+             (50, 60, 70, W.BF16, 8, 0, 4, 1.0, 0.5)]
+    probs, host = _make_batch(specs, 300)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    _check(specs, host, 1e-5)
+
+
+def test_graph_replay_with_new_data(ctx):
+    import paper_2311_03543_b300 as cp
+    specs = _random_specs(16, seed=3)
+    for rnd in range(3):                       # same shapes: the graph is reused
+        probs, host = _make_batch(specs, 400 + 50 * rnd)
+        ctx.force_variant(cp.V_GROUPED)
+        try:
+            ctx.gemm_batched(probs, tol=1e-5)
+        finally:
+            ctx.force_variant(None)
+        _check(specs, host, 1e-5)
+
+
+def test_loop_and_grouped_agree(ctx):
+    import paper_2311_03543_b300 as cp
+    specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(12, seed=4, lo=16, hi=200)]
+    probs, host = _make_batch(specs, 500)
+    ctx.force_variant(cp.V_SIMT)               # loop mode, SIMT per problem
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    _check(specs, host, 1e-5)
+
+
+def test_autotune_then_run(ctx):
+    specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(30, seed=5, lo=32, hi=600)]
+    probs, host = _make_batch(specs, 600)
+    best, times = ctx.autotune_batched(probs, tol=1e-5)
+    assert 0 <= best <= 4
+    assert all(t > 0 for t in times)
+    assert times[best] == min(times)
+    ctx.gemm_batched(probs, tol=1e-5)          # uses the tuned configuration
+    _check(specs, host, 1e-5)
+
+
+def test_config4_batch_sampled(ctx):
+    """512 problems, M, N, K log-uniform in [32, 2048] (seed 5), f32/bf16 mixed;
+    12 problems checked on 16 oracle rows each."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev
+    plist = W.batched_problems()
+    rng = np.random.default_rng(6)
+    probs, keep = [], {}
+    check = set(int(i) for i in rng.choice(len(plist), size=12, replace=False))
+    for i, (m, n, k, dt) in enumerate(plist):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(i)
+        A = torch.rand((m, k), generator=g, device="cuda") * 2 - 1
+        B = torch.rand((k, n), generator=g, device="cuda") * 2 - 1
+        if dt == W.BF16:
+            A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        C = torch.empty((m, n), device="cuda")
+        probs.append(dict(m=m, n=n, k=k, lda=k, ldb=n, ldc=n, dtype=dt, A=A.data_ptr(),
+                          B=B.data_ptr(), C=C.data_ptr()))
+        keep[i] = (A, B, C)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    torch.cuda.synchronize()
+    for i in check:
+        m, n, k, dt = plist[i]
+        A, B, C = keep[i]
+        A64 = A.float().cpu().numpy().astype(np.float64)
+        B64 = B.float().cpu().numpy().astype(np.float64)
+        rows = W.sample_rows(m, 16, seed=i)
+        ref = oracle.gemm_rows(A64, B64, rows)
+        assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5, (m, n, k, dt)

@@ -1,0 +1,98 @@
+"""Selection quality on held-out contexts (GPU).
+
+The trained selector shipped with the package (history table + MLP ensemble
+trained by the library's own kernels on timings of the three GEMM workloads)
+picks a variant for each of 2000 held-out contexts (M, N, K log-uniform in
+[16, 4096], dtype uniform over f32/bf16/fp8, tolerance from {1e-5, 1e-3, 1e-1}).
+The exhaustive judge times every eligible variant and checks its error
+against the FP64 oracle on 8 seeded rows; regret follows oracle/selector_ref.
+
+Checks: the learned selector's mean regret is at most 5 %, it violates no
+tolerance, and it beats the same runtime without the network (history table
+only, trained on the same records)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import numerics as N
+from oracle import selector_ref as S
+
+pytestmark = pytest.mark.gpu
+
+SELECTOR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2311_03543_b300", "selector_default.bin")
+COUNT = int(os.environ.get("COMPAR_HELDOUT_COUNT", "2000"))
+
+
+def _inputs(m, n, k, dt, seed):
+    if dt == W.F32:
+        return W.uniform(m, k, seed), W.uniform(k, n, seed + 1)
+    if dt == W.BF16:
+        return W.bf16_input(m, k, seed), W.bf16_input(k, n, seed + 1)
+    return W.fp8_input(m, k, seed, 7), W.fp8_input(k, n, seed + 1, 7)
+
+
+def _exact(X, dt):
+    if dt == W.F32:
+        return X.astype(np.float64)
+    if dt == W.BF16:
+        return N.bf16_to_f32(X).astype(np.float64)
+    return N.e4m3_to_f64(X)
+
+
+@pytest.fixture(scope="module")
+def evaluation():
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev
+    assert os.path.exists(SELECTOR), "trained selector file missing"
+    ctx = cp.Context(0)
+    ctx.selector_load(SELECTOR)
+    results = []
+    for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts()[:COUNT]):
+        A, B = _inputs(m, n, k, dt, 50000 + 2 * i)
+        dA, dB = dev(A), dev(B)
+        C = torch.empty((m, n), device="cuda")
+        rows = W.sample_rows(m, 8, seed=i)
+        ref = oracle.gemm_rows(_exact(A, dt), _exact(B, dt), rows)
+        times, errs = {}, {}
+        for v in range(cp.NUM_VARIANTS):
+            if not ctx.supported(v, m, n, k, dt):
+                continue
+            times[v] = ctx.measure(v, dA, dB, C, tol=tol, warmup=1, reps=3, dtype=dt)
+            got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+            errs[v] = N.rel_frobenius(got, ref)
+        picks = {}
+        for mode in (0, 1):                    # 0 = MLP + history, 1 = history only
+            ctx.set_selector_mode(mode)
+            picks[mode] = ctx.select(m, n, k, dt, tol)
+        ctx.set_selector_mode(0)
+        results.append((m, n, k, dt, tol, times, errs, picks))
+    ctx.close()
+    return results
+
+
+def _regrets(results, mode):
+    rs, viol = [], 0
+    for m, n, k, dt, tol, times, errs, picks in results:
+        pick = picks[mode]
+        if pick < 0 or S.exhaustive_pick(times, errs, tol) is None:
+            continue
+        if pick not in S.feasible(errs, tol):
+            viol += 1
+        rs.append(S.regret(pick, times, errs, tol))
+    return np.array(rs), viol
+
+
+def test_learned_selector_regret_and_gain(evaluation):
+    learned, v_learned = _regrets(evaluation, 0)
+    history, v_hist = _regrets(evaluation, 1)
+    print(f"\nheld-out contexts: {len(learned)}; mean regret learned {100 * learned.mean():.2f} % "
+          f"(violations {v_learned}), history-only {100 * history.mean():.2f} % "
+          f"(violations {v_hist})")
+    assert v_learned == 0
+    assert learned.mean() <= 0.05
+    assert learned.mean() < history.mean()
