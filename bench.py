@@ -58,6 +58,21 @@ def flops_of(shapes):
     return sum(2.0 * m * n * k for m, n, k in shapes)
 
 
+def reduce_max(value, dist, device):
+    """The maximum of `value` over all ranks (the slowest replica sets the time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(world, flops_per_rank_step, ms_per_step):
+    """Whole-job throughput: every rank's work of one step over the max step time."""
+    return world * flops_per_rank_step / (ms_per_step / 1e3) / 1e12
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
@@ -246,14 +261,10 @@ def main():
     launches = cp.compar_launch_count() - launches0
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, dev)
     ctx.profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     fl_step = flops_of(shapes)
-    value = world * fl_step / (ms / 1e3) / 1e12
+    value = whole_job_tflops(world, fl_step, ms)
 
     # dominant kernel and its roofline
     prof = {v: ctx.profile_read(v) for v in range(cp.NUM_VARIANTS)}
@@ -318,12 +329,8 @@ def main():
             e2e_step()
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / args.steps
-        if dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * fl_step / (ems / 1e3) / 1e12, "unit": "TFLOP/s",
+        ems = reduce_max(f0.elapsed_time(f1) / args.steps, dist, dev)
+        e2e = {"value": whole_job_tflops(world, fl_step, ems), "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems}
 
     # selector regret against exhaustive measurement (power-of-two shapes)

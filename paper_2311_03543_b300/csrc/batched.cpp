@@ -114,11 +114,21 @@ GemmCall to_call(const compar_problem_t& p, double tol) {
   return c;
 }
 
+// One problem through the single-call path.  A forced grouped kernel does
+// not apply to single calls, so those problems are selected normally.
+int run_single(compar_ctx* ctx, const compar_problem_t& p, double tol, cudaStream_t s) {
+  GemmCall c = to_call(p, tol);
+  const int saved = ctx->forced;
+  if (saved == COMPAR_V_GROUPED) ctx->forced = -1;
+  const int rc = gemm_call(ctx, c, s);
+  ctx->forced = saved;
+  return rc;
+}
+
 int run_loop(compar_ctx* ctx, int count, const compar_problem_t* probs, double tol,
              cudaStream_t s) {
   for (int i = 0; i < count; ++i) {
-    GemmCall c = to_call(probs[i], tol);
-    const int rc = gemm_call(ctx, c, s);
+    const int rc = run_single(ctx, probs[i], tol, s);
     if (rc != COMPAR_OK) return rc;
   }
   return COMPAR_OK;
@@ -134,8 +144,7 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
   auto run_rest = [&]() {
     for (int i = 0; i < count; ++i) {
       if (grouped_eligible(probs[i])) continue;
-      GemmCall c = to_call(probs[i], tol);
-      const int rc = gemm_call(ctx, c, s);
+      const int rc = run_single(ctx, probs[i], tol, s);
       if (rc != COMPAR_OK) return rc;
     }
     return static_cast<int>(COMPAR_OK);

@@ -111,7 +111,7 @@ enum PrepassOut { PP_F32 = 0, PP_BF16 = 1, PP_SPLIT_BF16 = 2, PP_E4M3 = 3, PP_CO
 bool tma_available();
 int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, const void* base,
                   uint64_t inner, uint64_t outer, uint64_t ld_elems, uint32_t box_inner,
-                  uint32_t box_outer);
+                  uint32_t box_outer, int swizzle_bytes = 128);
 
 std::string last_error_text();
 

@@ -113,11 +113,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------- producer
     uint32_t stage = 0, phase = 0, issued = 0, issued_par = 0;
     bool ok = true;
+    int last_q = -1;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const int q = find_problem(probs, count, tile);
+      const GroupProblem& P = probs[q];
       const int local = tile - P.tile_start;
       const int mb = local % P.tiles_m, nb = local / P.tiles_m;
       const int pieces = P.mode == 1 ? 2 : 1;
+      if (q != last_q) {
+        // the descriptors were written by the host for this launch; earlier
+        // launches may have left other bytes at these addresses in the cache
+        dev::tensormap_acquire(&P.map_a);
+        dev::tensormap_acquire(&P.map_b);
+        if (pieces == 2) {
+          dev::tensormap_acquire(&P.map_a2);
+          dev::tensormap_acquire(&P.map_b2);
+        }
+        last_q = q;
+      }
       const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
       const int kelems = P.mode == 2 ? kRow / 4 : kRow / 2;
       for (int kb = 0; kb < P.num_kb; ++kb) {

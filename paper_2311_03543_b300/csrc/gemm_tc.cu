@@ -9,14 +9,15 @@
 //   SPLIT3 : 3xBF16 — A = Ahi + Alo, B = Bhi + Blo (bf16 pieces) and
 //            Ahi*Bhi + Ahi*Blo + Alo*Bhi accumulated into one FP32 TMEM tile
 //
-// CTA roles (192 threads, one CTA per SM, grid = min(tiles, SMs)):
+// CTA roles (one CTA per SM, grid = min(tiles, SMs)):
 //   warp 0      TMA producer: one elected lane streams K-major A and B tiles
-//               (128-byte swizzle) into an S-stage shared-memory ring.
+//               (128- or 64-byte swizzle) into an S-stage shared-memory ring.
 //   warp 1      TMEM allocator; one lane issues tcgen05.mma into one of two
-//               TMEM accumulators (double buffered across output tiles) and
-//               releases ring stages with tcgen05.commit.
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator lane quarter the warp
-//               may access, alpha/beta and dequantisation, stores to C.
+//               TMEM accumulators (double buffered across output tiles or
+//               K chunks) and releases ring stages with tcgen05.commit.
+//   warps 2..   epilogue (4 or 8 warps): tcgen05.ld of the accumulator lane
+//               quarter the warp may access (and its column slice),
+//               alpha/beta and dequantisation, stores to C.
 // Every wait is bounded (ptx.cuh); on expiry the CTA drains its own copies
 // and MMAs, frees TMEM and returns with COMPAR_ERR_TIMEOUT in the error word.
 #include <cuda.h>
@@ -35,39 +36,42 @@ namespace {
 using dev::Kind;
 
 constexpr int kBM = 128;
-constexpr int kRowBytes = 128;  // K extent of one stage, in bytes (one swizzle row)
-constexpr int kThreads = 192;
-constexpr int kEpiThreads = 128;
 
+// Per-variant geometry: `row` = bytes of K per stage and operand row (128 or
+// 64, the TMA / MMA swizzle width), `epi` = epilogue warps (each lane quarter
+// of the accumulator is read by epi/4 warps, each taking BN*4/epi columns),
+// `chunk_kb` = stages per promoted K chunk (0: no promotion).
 template <int V>
 struct Traits;
 template <>
 struct Traits<COMPAR_V_TC_TF32> {
   static constexpr Kind kind = Kind::TF32;
-  static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, chunk_kb = 0;
+  static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
 };
 template <>
 struct Traits<COMPAR_V_TC_BF16> {
   static constexpr Kind kind = Kind::F16;
-  static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, chunk_kb = 0;
+  static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
 };
 template <>
 struct Traits<COMPAR_V_TC_FP8> {
   static constexpr Kind kind = Kind::F8;
-  static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, chunk_kb = 0;
+  static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
 };
+// 3xBF16: 64-byte rows give 48 KB stages (four of them) for a 128 x 256 tile;
+// promotion every 8 stages = 256 K elements.
 template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
-  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 128, chunk_kb = 4;  // promote every 256 K elements
+  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
 };
 
 template <int V>
 struct Layout {
   using T = Traits<V>;
   static constexpr int BN = T::BN;
-  static constexpr int kABytes = kBM * kRowBytes;
-  static constexpr int kBBytes = BN * kRowBytes;
+  static constexpr int kABytes = kBM * T::row;
+  static constexpr int kBBytes = BN * T::row;
   static constexpr int kStageBytes = T::pieces * (kABytes + kBBytes);
   static constexpr int kMaxSmem = 232448;  // 227 KB opt-in per CTA
   static constexpr int kBarBytes = 256;
@@ -75,9 +79,13 @@ struct Layout {
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
   static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes;
   static constexpr int kTmemCols = 2 * BN;  // two accumulators
-  static constexpr int kElemsPerStage = kRowBytes / T::elem;
+  static constexpr int kElemsPerStage = T::row / T::elem;
+  static constexpr int kThreads = 64 + 32 * T::epi;
+  static constexpr int kEpiThreads = 32 * T::epi;
+  static constexpr int kEpiCols = BN * 4 / T::epi;  // columns one epilogue warp handles
   static_assert(kStages >= 2, "pipeline needs two stages");
   static_assert(kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
+  static_assert(T::epi % 4 == 0 && kEpiCols % 32 == 0, "epilogue split");
 };
 
 struct TcArgs {
@@ -115,7 +123,7 @@ __device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity, uint6
 }
 
 template <int V>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB2, const TcArgs p) {
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       dev::mbar_init(&tfull[a], 1);
-      dev::mbar_init(&tempty[a], kEpiThreads);
+      dev::mbar_init(&tempty[a], L::kEpiThreads);
     }
     dev::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -237,16 +245,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           dev::tc_fence_after();
           const uint32_t a0 = dev::smem_u32(sA + (stage * P) * L::kABytes);
           const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
-          const uint64_t da = dev::smem_desc_sw128_kmajor(a0);
-          const uint64_t db = dev::smem_desc_sw128_kmajor(b0);
+          const uint64_t da = dev::smem_desc_kmajor<T::row>(a0);
+          const uint64_t db = dev::smem_desc_kmajor<T::row>(b0);
 #pragma unroll
-          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+          for (int kk = 0; kk < T::row / 32; ++kk) {
             // each instruction consumes 32 bytes of K; advance the start address
             const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if constexpr (P == 2) {
-              const uint64_t da_lo = dev::smem_desc_sw128_kmajor(a0 + L::kABytes);
-              const uint64_t db_lo = dev::smem_desc_sw128_kmajor(b0 + L::kBBytes);
+              const uint64_t da_lo = dev::smem_desc_kmajor<T::row>(a0 + L::kABytes);
+              const uint64_t db_lo = dev::smem_desc_kmajor<T::row>(b0 + L::kBBytes);
               dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
               dev::mma<T::kind>(d_tmem, da + koff, db_lo + koff, idesc, 1u);
               dev::mma<T::kind>(d_tmem, da_lo + koff, db + koff, idesc, 1u);
@@ -269,7 +277,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     drain_wait(drain, 0, p.budget_ns);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    const int quarter = warp & 3;            // TMEM lanes this warp may access
+    const int cslice = (warp - 2) / 4;       // which kEpiCols-wide column slice
+    constexpr int EC = L::kEpiCols;
     float alpha = p.alpha;
     if (p.dequant_a) alpha *= *p.dequant_a;
     if (p.dequant_b) alpha *= *p.dequant_b;
@@ -287,9 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // Promotion: each K chunk's TMEM partial sum is added into FP32
         // registers (round to nearest), so the tensor core's accumulator
         // only ever sums kChunkKB k-blocks.
-        float sum[BN];
+        float sum[EC];
 #pragma unroll
-        for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+        for (int j = 0; j < EC; ++j) sum[j] = 0.f;
         for (int ch = 0; ch < num_chunks; ++ch, ++acc_iter) {
           const uint32_t acc = acc_iter & 1;
           const uint32_t acc_phase = (acc_iter >> 1) & 1;
@@ -298,10 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           dev::tc_fence_after();
-          const uint32_t t_row =
-              tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+          const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                 acc * BN + cslice * EC;
 #pragma unroll
-          for (int c = 0; c < BN / 32; ++c) {
+          for (int c = 0; c < EC / 32; ++c) {
             uint32_t r[32];
             dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
             dev::tmem_ld_wait();
@@ -312,11 +322,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           dev::mbar_arrive(&tempty[acc]);
         }
         if (!ok) break;
-        const int col0 = nb * BN;
-        if (row < p.M) {
-          if (vec && col0 + BN <= p.N) {
+        const int col0 = nb * BN + cslice * EC;
+        if (row < p.M && col0 < p.N) {
+          if (vec && col0 + EC <= p.N) {
 #pragma unroll
-            for (int j = 0; j < BN; j += 4) {
+            for (int j = 0; j < EC; j += 4) {
               float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
               float4 o = make_float4(alpha * sum[j], alpha * sum[j + 1], alpha * sum[j + 2],
                                      alpha * sum[j + 3]);
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           } else {
 #pragma unroll
-            for (int j = 0; j < BN; ++j) {
+            for (int j = 0; j < EC; ++j) {
               if (col0 + j < p.N) {
                 float v = alpha * sum[j];
                 if (p.beta != 0.f) v = fmaf(p.beta, crow[col0 + j], v);
@@ -347,13 +357,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       ++acc_iter;
       if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
       dev::tc_fence_after();
-      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN +
+                             cslice * EC;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < EC / 32; ++c) {
         uint32_t r[32];
         dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
         dev::tmem_ld_wait();
-        const int col0 = nb * BN + c * 32;
+        const int col0 = nb * BN + cslice * EC + c * 32;
         if (row < p.M && col0 < p.N) {
           if (vec && col0 + 32 <= p.N) {
 #pragma unroll
@@ -445,12 +456,14 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   CUtensorMap ta, tb, ta2, tb2;
   const CUtensorMapDataType dt = map_type(V);
   const uint32_t box_k = static_cast<uint32_t>(L::kElemsPerStage);
-  int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM);
-  if (rc == COMPAR_OK) rc = tma_encode_2d(&tb, dt, T::elem, B, c.k, c.n, ldb, box_k, T::BN);
+  int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
+  if (rc == COMPAR_OK)
+    rc = tma_encode_2d(&tb, dt, T::elem, B, c.k, c.n, ldb, box_k, T::BN, T::row);
   if (rc != COMPAR_OK) return rc;
   if (T::pieces == 2) {
-    rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM);
-    if (rc == COMPAR_OK) rc = tma_encode_2d(&tb2, dt, T::elem, B2, c.k, c.n, ldb, box_k, T::BN);
+    rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM, T::row);
+    if (rc == COMPAR_OK)
+      rc = tma_encode_2d(&tb2, dt, T::elem, B2, c.k, c.n, ldb, box_k, T::BN, T::row);
     if (rc != COMPAR_OK) return rc;
   } else {
     ta2 = ta;
@@ -474,7 +487,7 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   const int tiles = a.tiles_m * a.tiles_n;
   const int grid = std::min(tiles, num_sms);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
-  tc_gemm_kernel<V><<<grid, kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, a);
+  tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, a);
   COMPAR_CUDA_TRY(cudaGetLastError());
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();

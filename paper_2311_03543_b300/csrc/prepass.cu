@@ -87,6 +87,111 @@ __global__ void convert_transpose_kernel(const float* __restrict__ X, int64_t ro
   }
 }
 
+// ------------------------------------------------------------------ vectorised
+// Eight consecutive float32 -> one packed group of the output kind.
+__device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], void* Y, void* Ylo,
+                                      int64_t idx) {
+  if (kind == PP_F32) {
+    float4* y = reinterpret_cast<float4*>(static_cast<float*>(Y) + idx);
+    y[0] = make_float4(x[0], x[1], x[2], x[3]);
+    y[1] = make_float4(x[4], x[5], x[6], x[7]);
+  } else if (kind == PP_BF16 || kind == PP_SPLIT_BF16) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]);
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * q + 1]);
+      hi[q] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+              (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+      if (kind == PP_SPLIT_BF16) {
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
+        lo[q] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+      }
+    }
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Y) + idx) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    if (kind == PP_SPLIT_BF16)
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Ylo) + idx) =
+          make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  } else {  // PP_E4M3
+    uint32_t w[2] = {0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      w[q / 4] |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(__fmul_rn(x[q], s), __NV_SATFINITE,
+                                                              __NV_E4M3))
+                  << (8 * (q % 4));
+    *reinterpret_cast<uint2*>(static_cast<uint8_t*>(Y) + idx) = make_uint2(w[0], w[1]);
+  }
+}
+
+// Y[r][c..c+7] = f(X[r][c..c+7]); requires cols % 8 == 0, 16-byte aligned rows.
+__global__ void convert_rows_vec8_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                         int64_t ldx, void* __restrict__ Y, void* __restrict__ Ylo,
+                                         int64_t ldy, int kind, const float* __restrict__ dscale) {
+  const float s = dscale ? *dscale : 1.f;
+  const int64_t groups = cols / 8;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    for (int64_t gi = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; gi < groups;
+         gi += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const float4* src = reinterpret_cast<const float4*>(X + r * ldx + gi * 8);
+      const float4 a = __ldg(src), b = __ldg(src + 1);
+      const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      store8(kind, s, x, Y, Ylo, r * ldy + gi * 8);
+    }
+  }
+}
+
+// Transposing convert through a 64 x 64 tile: float2 loads, each thread
+// stores two consecutive outputs (bf16 pairs, float2, or two bytes).
+__global__ void convert_transpose64_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                           int64_t ldx, void* __restrict__ Y,
+                                           void* __restrict__ Ylo, int64_t ldy, int kind,
+                                           const float* __restrict__ dscale) {
+  __shared__ float tile[64][65];
+  const float s = dscale ? *dscale : 1.f;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 64;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int i = ty; i < 64; i += 8) {
+    const int64_t r = r0 + i, c = c0 + 2 * tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < rows) {
+      if (c + 1 < cols) v = __ldg(reinterpret_cast<const float2*>(X + r * ldx + c));
+      else if (c < cols) v.x = X[r * ldx + c];
+    }
+    tile[i][2 * tx] = v.x;
+    tile[i][2 * tx + 1] = v.y;
+  }
+  __syncthreads();
+  for (int j = ty; j < 64; j += 8) {  // output row c0 + j holds input column c0 + j
+    const int64_t orow = c0 + j;
+    const int64_t ocol = r0 + 2 * tx;
+    if (orow >= cols || ocol >= rows) continue;
+    const float x0 = tile[2 * tx][j], x1 = tile[2 * tx + 1][j];
+    const int64_t idx = orow * ldy + ocol;
+    if (ocol + 1 < rows) {
+      if (kind == PP_F32) {
+        *reinterpret_cast<float2*>(static_cast<float*>(Y) + idx) = make_float2(x0, x1);
+      } else if (kind == PP_BF16 || kind == PP_SPLIT_BF16) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Y) + idx) =
+            __halves2bfloat162(h0, h1);
+        if (kind == PP_SPLIT_BF16)
+          *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Ylo) + idx) =
+              __halves2bfloat162(__float2bfloat16_rn(x0 - __bfloat162float(h0)),
+                                 __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+      } else {
+        uint8_t* y = static_cast<uint8_t*>(Y) + idx;
+        y[0] = __nv_cvt_float_to_fp8(__fmul_rn(x0, s), __NV_SATFINITE, __NV_E4M3);
+        y[1] = __nv_cvt_float_to_fp8(__fmul_rn(x1, s), __NV_SATFINITE, __NV_E4M3);
+      }
+    } else {
+      store_converted(F32Out{kind, s}, x0, Y, Ylo, idx);
+    }
+  }
+}
+
 // Element-type-preserving copy (optionally transposing) for 1/2/4-byte types.
 template <typename T>
 __global__ void copy_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
@@ -221,6 +326,31 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
   if (rows <= 0 || cols <= 0) return COMPAR_OK;
   const dim3 tb(32, 8);
   const dim3 tg(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
+  // float32 sources with aligned rows take the vectorised kernels
+  if (in_t == COMPAR_F32 && (out_kind != PP_COPY || transpose)) {
+    const int kind = out_kind == PP_COPY ? PP_F32 : out_kind;
+    const float* Xf = static_cast<const float*>(X);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(X), ya = reinterpret_cast<uintptr_t>(Y),
+                    la = reinterpret_cast<uintptr_t>(Y_lo);
+    if (transpose && cols % 2 == 0 && ldx % 2 == 0 && xa % 8 == 0 && ldy % 2 == 0 &&
+        ya % 8 == 0 && la % 8 == 0 && rows < (int64_t(65535) * 64)) {
+      const dim3 g64(static_cast<unsigned>((cols + 63) / 64), static_cast<unsigned>((rows + 63) / 64));
+      convert_transpose64_kernel<<<g64, tb, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, kind, dscale);
+      COMPAR_CUDA_TRY(cudaGetLastError());
+      count_launch();
+      return COMPAR_OK;
+    }
+    if (!transpose && cols % 8 == 0 && ldx % 4 == 0 && xa % 16 == 0 && ldy % 8 == 0 &&
+        ya % 16 == 0 && la % 16 == 0) {
+      const int64_t groups = cols / 8;
+      const dim3 gv(static_cast<unsigned>(std::min<int64_t>((groups + 255) / 256, 64)),
+                    static_cast<unsigned>(std::min<int64_t>(rows, 65535)));
+      convert_rows_vec8_kernel<<<gv, 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, kind, dscale);
+      COMPAR_CUDA_TRY(cudaGetLastError());
+      count_launch();
+      return COMPAR_OK;
+    }
+  }
   if (out_kind == PP_COPY) {
     if (in_t == COMPAR_F32) {
       if (transpose)

@@ -92,6 +92,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
 }
 
 // ------------------------------------------------------------------ TMA
+// A tensor map that lives in global memory and whose bytes were rewritten
+// since an earlier launch may still sit in the TMA descriptor cache; this
+// acquire fence makes the next TMA use of `map` see the current bytes.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -193,6 +202,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw128_kmajor(uint32_t smem_addr) {
   d |= static_cast<uint64_t>(1024 >> 4) << 32;             // stride offset   [32,46)
   d |= static_cast<uint64_t>(1) << 46;                     // descriptor version (sm_100 family)
   d |= static_cast<uint64_t>(2) << 61;                     // swizzle: 128B
+  return d;
+}
+
+// The same for 64-byte (SWIZZLE_64B) or 128-byte rows: 8-row groups are
+// 8 * ROW bytes apart; layout type 4 = 64-byte swizzle, 2 = 128-byte.
+template <int ROW>
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t smem_addr) {
+  static_assert(ROW == 64 || ROW == 128, "swizzle width");
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>((8 * ROW) >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(ROW == 128 ? 2 : 4) << 61;
   return d;
 }
 

@@ -91,6 +91,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--budget-s", type=float, default=None)
+    ap.add_argument("--random-count", type=int, default=1500,
+                    help="seeded random training contexts added to the workloads' shapes")
     args = ap.parse_args(argv)
     import torch
     import paper_2311_03543_b300 as cp
@@ -98,7 +100,8 @@ def main(argv=None):
     torch.cuda.set_device(0)
     with cp.Context(0) as ctx:
         ctx.record_enable(True)
-        n = collect(ctx, cp, torch, training_contexts(), args.reps, dev, budget_s=args.budget_s)
+        n = collect(ctx, cp, torch, training_contexts(args.random_count), args.reps, dev,
+                    budget_s=args.budget_s)
         t0 = time.time()
         vl = ctx.selector_train(steps=args.steps, batch=128, lr=args.lr, seed=args.seed)
         print(f"[train_selector] {n} records; trained {args.steps} steps in "

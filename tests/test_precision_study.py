@@ -1,0 +1,84 @@
+"""Precision study (GPU): 4096^3 with float32 inputs normal(0,1) and
+ill-scaled (column k of A times 10^U(-3,3)), every variant forced in turn.
+
+Two errors per variant, both against the FP64 oracle on 64 seeded rows:
+* total      — against the product of the float32 inputs;
+* arithmetic — against the product of the exact values the variant
+  multiplied (the oracle's own bf16 rounding / e4m3 quantisation with the
+  per-tensor scale s = 448/amax), i.e. the accumulation error alone.
+Bounds: FP32-accurate variants (SIMT, 3xBF16) total <= 1e-5 on normal data;
+arithmetic error <= 1e-5 for SIMT and 3xBF16 and <= max(1e-5, 0.05 K 2^-24)
+for the unpromoted BF16 / FP8 kinds (their accumulation error grows with K);
+TF32 is judged on its total error only (the tensor cores' rounding of the
+float32 operands is not modelled); format rounding bounds the total error
+(bf16 <= 2^-7, fp8 <= 2^-3, tf32 <= 2^-9)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import numerics as N
+
+pytestmark = pytest.mark.gpu
+
+M = N_ = K = 4096
+ROWS = W.sample_rows(M, 64, seed=31)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2311_03543_b300 as cp
+    c = cp.Context(0)
+    yield c
+    c.close()
+
+
+def _data(kind):
+    if kind == "normal":
+        return W.normal(M, K, seed=3), W.normal(K, N_, seed=33)
+    return W.ill_scaled(M, K, seed_values=3, seed_scales=4), W.normal(K, N_, seed=33)
+
+
+def _exact_operands(v, A, B):
+    if v == 3:
+        return N.bf16_round(A).astype(np.float64), N.bf16_round(B).astype(np.float64), 1.0
+    if v == 4:
+        qa, sa = N.fp8_quantize(A)
+        qb, sb = N.fp8_quantize(B)
+        return N.e4m3_to_f64(qa), N.e4m3_to_f64(qb), 1.0 / (float(sa) * float(sb))
+    return A.astype(np.float64), B.astype(np.float64), 1.0
+
+
+@pytest.mark.parametrize("kind", ["normal", "ill_scaled"])
+def test_precision_study(ctx, kind):
+    import torch
+    A, B = _data(kind)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    total_ref = oracle.gemm_rows(A, B, ROWS)
+    report = {}
+    for v in (1, 2, 3, 4, 5):
+        C = torch.empty((M, N_), device="cuda")
+        ctx.force_variant(v)
+        try:
+            ctx.gemm(dA, dB, C)
+        finally:
+            ctx.force_variant(None)
+        got = C.cpu().numpy()[ROWS]
+        Ae, Be, scale = _exact_operands(v, A, B)
+        arith_ref = scale * oracle.gemm_rows(Ae, Be, ROWS)
+        report[v] = (N.rel_frobenius(got, total_ref), N.rel_frobenius(got, arith_ref))
+    print(f"\n{kind}: " + ", ".join(f"v{v} total {t:.2e} arith {a:.2e}"
+                                     for v, (t, a) in report.items()))
+    u = 2.0 ** -24
+    for v, (total, arith) in report.items():
+        if v == 2:
+            continue   # the tensor cores' TF32 operand rounding is not modelled: total only
+        if v in (3, 4):
+            assert arith <= max(1e-5, 0.05 * K * u), (v, arith)
+        else:
+            assert arith <= 1e-5, (v, arith)
+    if kind == "normal":
+        assert report[1][0] <= 1e-5 and report[5][0] <= 1e-5
+    assert report[3][0] <= 2.0 ** -7
+    assert report[4][0] <= 2.0 ** -3
+    assert report[2][0] <= 2.0 ** -9
