@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-regret", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--selector", default=os.path.join(ROOT, "paper_2311_03543_b300",
                                                         "selector_default.bin"))
     ap.add_argument("--detail", default=None, help="write per-shape detail JSON here")
@@ -309,15 +310,38 @@ def main():
         h2d = sum((m * k + k * n) * 4 for m, n, k in shapes)
         d2h = sum(m * n * 4 for m, n, k in shapes)
 
+        # Copies overlap the GEMMs: inputs go up on one stream, products
+        # come down on another, the GEMMs run on the timed stream; per-shape
+        # events order each shape's copy -> GEMM -> copy, and the next step's
+        # upload into a buffer waits for this step's GEMM that reads it.
+        s_up = torch.cuda.Stream(device=dev)
+        s_down = torch.cuda.Stream(device=dev)
+        ev_in = [torch.cuda.Event() for _ in shapes]
+        ev_mm = [torch.cuda.Event() for _ in shapes]
+        ev_out = [torch.cuda.Event() for _ in shapes]
+        for e in ev_mm + ev_out:
+            e.record(stream)
+
         def e2e_step():
-            for (m, n, k), (A, B, C) in zip(shapes, bufs):
-                A.view(-1).copy_(hA[: m * k], non_blocking=True)
-                B.view(-1).copy_(hB[: k * n], non_blocking=True)
+            for i, ((m, n, k), (A, B, C)) in enumerate(zip(shapes, bufs)):
+                with torch.cuda.stream(s_up):
+                    s_up.wait_event(ev_mm[i])          # previous GEMM on A, B done
+                    A.view(-1).copy_(hA[: m * k], non_blocking=True)
+                    B.view(-1).copy_(hB[: k * n], non_blocking=True)
+                    ev_in[i].record(s_up)
+                stream.wait_event(ev_in[i])
+                stream.wait_event(ev_out[i])           # previous download of C done
                 rc = cp.compar_gemm(ctx.handle, m, n, k, cp.F32, TOL, A.data_ptr(),
                                     B.data_ptr(), C.data_ptr(), ctypes_stream)
                 if rc != 0:
                     raise cp.ComparError(rc, "compar_gemm (e2e)")
-                hC[: m * n].copy_(C.view(-1), non_blocking=True)
+                ev_mm[i].record(stream)
+                with torch.cuda.stream(s_down):
+                    s_down.wait_event(ev_mm[i])
+                    hC[: m * n].copy_(C.view(-1), non_blocking=True)
+                    ev_out[i].record(s_down)
+            for e in ev_out:                           # the step ends when all is home
+                stream.wait_event(e)
         e2e_step()
         torch.cuda.synchronize()
         if dist:
@@ -341,6 +365,10 @@ def main():
                   "set": "held-out contexts 0..199 (M,N,K log-uniform [16,4096], f32/bf16/fp8, "
                          "tol 1e-5/1e-3/1e-1)", "feasibility": "library FP64 residual check, 8 rows"}
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = measure_batched(ctx, cp, W, torch, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_sample()
@@ -358,7 +386,7 @@ def main():
                            "selected": {cp.VARIANT_NAMES[v]: picks.count(v)
                                         for v in sorted(set(picks))}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": launches, "regret_pct": regret}
+                "gpu_launches": launches, "regret_pct": regret, "batched_512": batched}
         print(json.dumps(line), flush=True)
         if args.detail:
             with open(args.detail, "w") as f:
@@ -390,6 +418,57 @@ def measured_traffic(kernel, flops_per_launch):
             f"to the average launch (x{scale:.3f})")
 
 
+def measure_batched(ctx, cp, W, torch, dev, reps=5):
+    """The uneven batched workload: 512 GEMMs, M, N, K log-uniform in [32, 2048]
+    (seed 5), f32 (tol 1e-5 -> 3xBF16) or bf16 with probability 1/2.  The
+    autotuner times the per-GEMM loop and the grouped kernel's configurations;
+    then the chosen one and the loop are each timed over `reps` calls."""
+    import ctypes
+    plist = W.batched_problems()
+    keep, probs = [], []
+    for i, (m, n, k, dt) in enumerate(plist):
+        g = torch.Generator(device=dev)
+        g.manual_seed(5000 + i)
+        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        if dt == cp.BF16:
+            A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        C = torch.empty((m, n), device=dev)
+        keep.append((A, B, C))
+        probs.append(dict(m=m, n=n, k=k, lda=k, ldb=n, ldc=n, dtype=dt, A=A.data_ptr(),
+                          B=B.data_ptr(), C=C.data_ptr()))
+    arr = cp.Context.problem_array(probs)
+    best, tuned_ms = ctx.autotune_batched(arr, tol=TOL)
+    stream = torch.cuda.current_stream()
+
+    def timed(force):
+        ctx.force_variant(force)
+        try:
+            ctx.gemm_batched(arr, tol=TOL)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.gemm_batched(arr, tol=TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            ctx.force_variant(None)
+        return e0.elapsed_time(e1) / reps
+
+    ms_best = timed(None)                      # the autotuned choice
+    ms_loop = tuned_ms[0]                      # per-GEMM launches (autotuner's median)
+    flops = sum(2.0 * m * n * k for m, n, k, _ in plist)
+    del keep
+    names = ["per-GEMM launches", "grouped BN=128", "grouped BN=64",
+             "grouped BN=128 largest-first", "grouped BN=64 largest-first"]
+    return {"problems": len(plist), "gflop": flops / 1e9, "chosen": names[best],
+            "ms_chosen": ms_best, "tflops_chosen": flops / (ms_best / 1e3) / 1e12,
+            "ms_per_gemm_launches": ms_loop,
+            "tflops_per_gemm_launches": flops / (ms_loop / 1e3) / 1e12,
+            "autotune_ms": dict(zip(names, tuned_ms))}
+
+
 def measure_regret(ctx, cp, W, torch, dev, count=200):
     """Mean regret (%) of the selector on held-out contexts vs exhaustive timing.
 
@@ -403,6 +482,7 @@ def measure_regret(ctx, cp, W, torch, dev, count=200):
     import numpy as np
     tie = 0.02
     rs, viol = [], 0
+    judge = cp.Context(dev.index)   # measures; the selector's history never sees it
     for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts()[:count]):
         g = torch.Generator(device=dev)
         g.manual_seed(90000 + i)
@@ -418,10 +498,10 @@ def measure_regret(ctx, cp, W, torch, dev, count=200):
         pick = ctx.select(m, n, k, dt, tol)
         times, feas = {}, set()
         for v in range(cp.NUM_VARIANTS):
-            if not ctx.supported(v, m, n, k, dt):
+            if not judge.supported(v, m, n, k, dt):
                 continue
-            times[v] = ctx.measure(v, A, B, C, tol=tol, warmup=1, reps=3, dtype=dt)
-            if ctx.residual_check(A, B, C, nrows=8, seed=i, dtype=dt) <= tol:
+            times[v] = judge.measure(v, A, B, C, tol=tol, warmup=1, reps=3, dtype=dt)
+            if judge.residual_check(A, B, C, nrows=8, seed=i, dtype=dt) <= tol:
                 feas.add(v)
         if not feas:
             continue
@@ -431,6 +511,7 @@ def measure_regret(ctx, cp, W, torch, dev, count=200):
             rs.append((times[pick] + t_best) / t_best - 1.0)
         else:
             rs.append(0.0 if times[pick] <= t_best * (1 + tie) else times[pick] / t_best - 1.0)
+    judge.close()
     return 100.0 * float(np.mean(rs)), viol, len(rs)
 
 

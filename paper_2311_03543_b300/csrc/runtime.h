@@ -37,7 +37,7 @@ struct ErrorModel {
   std::array<std::array<float, 3>, kNumVariants> c0{};
   std::array<std::array<float, 3>, kNumVariants> c1{};
   std::array<std::array<float, 3>, kNumVariants> c2{};  // linear-in-k term
-  float margin = 1.5f;  // eligibility: predicted * margin <= tol
+  float margin = 1.25f;  // eligibility: predicted * margin <= tol
   ErrorModel();
   double predict(int v, int dtype, int64_t k) const;
 };

@@ -48,13 +48,13 @@ ErrorModel::ErrorModel() {
   // FP64 oracle for uniform[-1,1] and normal(0,1) inputs, k = 64 .. 16384:
   // naive FMA chain ~0.3 sqrt(k) u; SIMT below that; unpromoted tensor-core
   // accumulation ~0.018 k u; TF32 / BF16 / FP8 operand rounding of float32
-  // inputs ~8e-4 / 2.4e-3 / 3.8e-2; promoted 3xBF16 flat at ~4.6e-6.
+  // inputs ~7-8e-4 / 2.4e-3 / 3.8e-2; promoted 3xBF16 flat at ~4.6e-6.
   for (int v : {COMPAR_V_TC_TF32, COMPAR_V_TC_BF16, COMPAR_V_TC_FP8}) c2[v].fill(0.025f);
   for (int d = 0; d < 3; ++d) {
     c0[COMPAR_V_NAIVE][d] = 0.f;  c1[COMPAR_V_NAIVE][d] = 0.4f;
     c0[COMPAR_V_SIMT][d] = 0.f;   c1[COMPAR_V_SIMT][d] = 0.4f;
   }
-  c0[COMPAR_V_TC_TF32][COMPAR_F32] = 9e-4f;
+  c0[COMPAR_V_TC_TF32][COMPAR_F32] = 7.8e-4f;
   c0[COMPAR_V_TC_BF16][COMPAR_F32] = 2.6e-3f;
   c0[COMPAR_V_TC_BF16][COMPAR_BF16] = 0.f;
   c0[COMPAR_V_TC_FP8][COMPAR_F32] = 4.2e-2f;
@@ -145,6 +145,9 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
   switch (v) {
     case COMPAR_V_NAIVE:
       peak = 4e12;
+      // each output is one serial K-long FMA chain: with few outputs the
+      // kernel is bound by that chain's latency (~60 ns per step measured)
+      ovh_us += K * 0.06;
       break;
     case COMPAR_V_SIMT:
       peak = 45e12;

@@ -49,10 +49,19 @@ def evaluation():
     import paper_2311_03543_b300 as cp
     from gpu_util import dev
     assert os.path.exists(SELECTOR), "trained selector file missing"
-    ctx = cp.Context(0)
-    ctx.selector_load(SELECTOR)
+    # The selector context only selects; a separate judge context measures,
+    # so the judge's timings never reach the selector's history table.
+    sel = cp.Context(0)
+    sel.selector_load(SELECTOR)
+    judge = cp.Context(0)
     results = []
     for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts()[:COUNT]):
+        picks = {}
+        for mode in (0, 1):                    # 0 = MLP + history, 1 = history only
+            sel.set_selector_mode(mode)
+            sel.clear_decisions()
+            picks[mode] = sel.select(m, n, k, dt, tol)
+        sel.set_selector_mode(0)
         A, B = _inputs(m, n, k, dt, 50000 + 2 * i)
         dA, dB = dev(A), dev(B)
         C = torch.empty((m, n), device="cuda")
@@ -60,18 +69,14 @@ def evaluation():
         ref = oracle.gemm_rows(_exact(A, dt), _exact(B, dt), rows)
         times, errs = {}, {}
         for v in range(cp.NUM_VARIANTS):
-            if not ctx.supported(v, m, n, k, dt):
+            if not judge.supported(v, m, n, k, dt):
                 continue
-            times[v] = ctx.measure(v, dA, dB, C, tol=tol, warmup=1, reps=3, dtype=dt)
+            times[v] = judge.measure(v, dA, dB, C, tol=tol, warmup=1, reps=3, dtype=dt)
             got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
             errs[v] = N.rel_frobenius(got, ref)
-        picks = {}
-        for mode in (0, 1):                    # 0 = MLP + history, 1 = history only
-            ctx.set_selector_mode(mode)
-            picks[mode] = ctx.select(m, n, k, dt, tol)
-        ctx.set_selector_mode(0)
         results.append((m, n, k, dt, tol, times, errs, picks))
-    ctx.close()
+    sel.close()
+    judge.close()
     return results
 
 
