@@ -44,11 +44,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweep", default="full", choices=["full", "pow2"])
     ap.add_argument("--shapes", default=None,
-                    help="comma-separated square sizes replacing the sweep (profiling runs)")
+                    help="comma-separated sizes replacing the sweep (profiling runs): "
+                         "n for n x n x n, or MxNxK")
     ap.add_argument("--no-regret", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the roofline denominators and exit")
+    ap.add_argument("--variants", action="store_true",
+                    help="time every variant on the headline shapes and exit")
     ap.add_argument("--selector", default=os.path.join(ROOT, "paper_2311_03543_b300",
                                                         "selector_default.bin"))
     ap.add_argument("--detail", default=None, help="write per-shape detail JSON here")
@@ -186,11 +191,111 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- peaks / variants
+def measure_peaks(ctx, torch, dev):
+    """Roofline denominators on this GPU: the FP32 FMA pipe (the library's own
+    microkernel), dense GEMM peaks of the tensor formats through PyTorch's
+    library matmuls (bf16, TF32, FP8 E4M3 via _scaled_mm; 8192^3, best of 10),
+    and copy bandwidth (1 GiB, read + write bytes)."""
+    out = {"ffma_tflops": ctx.peak_ffma()}
+    n = 8192
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def best_of(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+    x = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+    y = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+    out["bf16_tflops"] = 2 * n ** 3 / (best_of(lambda: x @ y) / 1e3) / 1e12
+    xf, yf = x.float(), y.float()
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["tf32_tflops"] = 2 * n ** 3 / (best_of(lambda: xf @ yf) / 1e3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        x8 = x.to(torch.float8_e4m3fn)
+        y8 = y.to(torch.float8_e4m3fn).t().contiguous().t()
+        one = torch.ones((), device=dev)
+        out["fp8_tflops"] = 2 * n ** 3 / (best_of(
+            lambda: torch._scaled_mm(x8, y8, scale_a=one, scale_b=one,
+                                     out_dtype=torch.bfloat16)) / 1e3) / 1e12
+    except Exception as e:  # library without an fp8 path on this build
+        out["fp8_tflops"] = None
+        out["fp8_note"] = str(e)[:120]
+    src = torch.empty(1 << 28, device=dev)
+    dst = torch.empty_like(src)
+    out["copy_gbs"] = 2 * src.numel() * 4 / (best_of(lambda: dst.copy_(src)) / 1e3) / 1e9
+    return out
+
+
+def measure_variants(ctx, cp, torch, dev, peaks):
+    """Every variant forced on the headline shapes: whole-call time (operand
+    pre-passes included) and kernel-only time (the library's CUDA-event
+    profiler), TFLOP/s, and the fraction of the variant's own roofline:
+    min(pipe peak, arithmetic intensity x copy bandwidth)."""
+    shapes = [(1024,) * 3, (4096,) * 3, (8192,) * 3, (4096, 4096, 64), (16, 4096, 4096)]
+    pipe = {cp.V_NAIVE: peaks["ffma_tflops"], cp.V_SIMT: peaks["ffma_tflops"],
+            cp.V_TC_TF32: peaks["tf32_tflops"], cp.V_TC_BF16: peaks["bf16_tflops"],
+            cp.V_TC_FP8: peaks.get("fp8_tflops") or 2 * peaks["bf16_tflops"],
+            cp.V_SPLIT3: peaks["bf16_tflops"] / 3}
+    rows = []
+    for (m, n, k) in shapes:
+        g = torch.Generator(device=dev)
+        g.manual_seed(m + n + k)
+        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        C = torch.empty((m, n), device=dev)
+        flops = 2.0 * m * n * k
+        for v in range(cp.NUM_VARIANTS):
+            if not ctx.supported(v, m, n, k, cp.F32):
+                continue
+            reps = 3 if (v == cp.V_NAIVE and m * n * k > 2 ** 33) else 10
+            ctx.profile_reset()
+            ctx.profile_enable(True)
+            t_call = ctx.measure(v, A, B, C, tol=1.0, warmup=2, reps=reps)
+            ctx.profile_enable(False)
+            kms, kn = ctx.profile_read(v)
+            t_kern = kms / max(kn, 1)
+            byts = 4.0 * (m * k + k * n + m * n)
+            roof = min(pipe[v], flops / byts * peaks["copy_gbs"] / 1e3)
+            rows.append({"shape": [m, n, k], "variant": cp.VARIANT_NAMES[v],
+                         "call_ms": t_call, "kernel_ms": t_kern,
+                         "call_tflops": flops / t_call / 1e9,
+                         "kernel_tflops": flops / t_kern / 1e9,
+                         "roofline_tflops": roof,
+                         "kernel_frac_of_roofline": flops / t_kern / 1e9 / roof,
+                         "call_gbs": byts / t_call / 1e6})
+    return rows
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.peaks or args.variants:
+        import torch
+        import paper_2311_03543_b300 as cp
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        with cp.Context(0) as ctx:
+            peaks = measure_peaks(ctx, torch, dev)
+            out = {"peaks": peaks}
+            if args.variants:
+                out["variants"] = measure_variants(ctx, cp, torch, dev, peaks)
+        print(json.dumps(out), flush=True)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(out, f, indent=1)
+        return 0
     import torch
     import workloads as W
     import paper_2311_03543_b300 as cp
@@ -208,8 +313,9 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     shapes = W.sweep_shapes() if args.sweep == "full" else W.pow2_sweep_shapes()
-    if args.shapes:
-        shapes = [(int(s),) * 3 for s in args.shapes.split(",")]
+    if args.shapes:   # "4096" (square) or "4096x4096x64" (M x N x K)
+        shapes = [tuple(int(x) for x in s.split("x")) if "x" in s else (int(s),) * 3
+                  for s in args.shapes.split(",")]
     ctx = cp.Context(dev.index)
     if os.path.exists(args.selector):
         ctx.selector_load(args.selector)

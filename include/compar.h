@@ -372,6 +372,12 @@ int compar_profile_reset(compar_ctx_t ctx);
  * variant kernel and every pre-pass kernel). */
 int64_t compar_launch_count(void);
 
+/* Measured FP32 FMA-pipe throughput of this GPU (TFLOP/s, 2 flops per FMA):
+ * register-resident independent FMA chains at full occupancy, median of 5
+ * timed launches on `stream`.  The roofline denominator of the naive and SIMT
+ * variants.  Synchronises `stream`. */
+int compar_peak_ffma(compar_ctx_t ctx, float* tflops, void* stream);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Read and clear the device error word after synchronising `stream`.

@@ -102,6 +102,7 @@ SIGNATURES = {
     "compar_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "compar_profile_reset": (_i, [_vp]),
     "compar_launch_count": (_i64, []),
+    "compar_peak_ffma": (_i, [_vp, _fp, _vp]),
 }
 
 _lib = None
@@ -422,6 +423,12 @@ class Context:
 
     def profile_reset(self):
         return _status(compar_profile_reset(self.handle), "profile_reset")
+
+    def peak_ffma(self, stream=None):
+        out = ctypes.c_float()
+        _status(compar_peak_ffma(self.handle, ctypes.byref(out), _stream_handle(stream)),
+                "peak_ffma")
+        return out.value
 
     def selftest_timeout(self, stream=None):
         return _status(compar_selftest_timeout(self.handle, _stream_handle(stream)),

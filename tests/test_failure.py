@@ -1,0 +1,75 @@
+"""Failure detection without faulting the GPU.
+
+* Device side: a kernel whose bounded wait can never complete (an mbarrier
+  nothing arrives on) gives up after the wait budget, records
+  COMPAR_ERR_TIMEOUT in the context's error word and returns; the context
+  stays usable.
+* Host side: COMPAR_TEST_FAIL_VARIANT makes the dispatcher treat one variant's
+  launch as failed; the runtime quarantines it and re-dispatches the call to
+  the next choice, which still computes the right product.
+* Bad arguments are refused synchronously."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import numerics as N
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    import torch
+    import paper_2311_03543_b300 as cp
+    with cp.Context(0) as ctx:
+        ctx.set_wait_budget(2_000_000)           # 2 ms
+        ctx.selftest_timeout()
+        assert ctx.check_device_error() == cp.ERR_TIMEOUT
+        assert ctx.check_device_error() == cp.OK  # read-and-clear
+        A = torch.from_numpy(W.uniform(64, 64, 1)).cuda()
+        B = torch.from_numpy(W.uniform(64, 64, 2)).cuda()
+        C = torch.empty((64, 64), device="cuda")
+        ctx.gemm(A, B, C)
+        torch.cuda.synchronize()
+        assert N.rel_frobenius(C.cpu().numpy(), oracle.gemm(A.cpu().numpy(),
+                                                            B.cpu().numpy())) <= 1e-5
+        assert ctx.check_device_error() == cp.OK
+
+
+def test_injected_variant_failure_is_quarantined(monkeypatch):
+    import torch
+    import paper_2311_03543_b300 as cp
+    m = n = k = 2048
+    A = torch.from_numpy(W.uniform(m, k, 3)).cuda()
+    B = torch.from_numpy(W.uniform(k, n, 4)).cuda()
+    with cp.Context(0) as probe:
+        first = probe.select(m, n, k, cp.F32, 1e-5)
+    monkeypatch.setenv("COMPAR_TEST_FAIL_VARIANT", str(first))
+    with cp.Context(0) as ctx:
+        C = torch.empty((m, n), device="cuda")
+        ctx.gemm(A, B, C, tol=1e-5)
+        used = ctx.last_variant()
+        assert used != first and used >= 0
+        torch.cuda.synchronize()
+        rows = W.sample_rows(m, 16, 5)
+        ref = oracle.gemm_rows(A.cpu().numpy(), B.cpu().numpy(), rows)
+        assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5
+        # the quarantined variant stays out of later calls of this context
+        ctx.clear_decisions()
+        assert ctx.select(m, n, k, cp.F32, 1e-5) != first
+
+
+def test_bad_arguments_are_refused():
+    import torch
+    import paper_2311_03543_b300 as cp
+    with cp.Context(0) as ctx:
+        h = ctx.handle
+        assert cp.compar_gemm(h, -1, 4, 4, cp.F32, 0.0, 16, 16, 16, None) == cp.ERR_INVALID
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 0.0, None, 16, 16, None) == cp.ERR_INVALID
+        assert cp.compar_gemm(h, 4, 4, 4, 7, 0.0, 16, 16, 16, None) == cp.ERR_INVALID
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, float("nan"), 16, 16, 16, None) == cp.ERR_INVALID
+        assert cp.compar_set_fp8_scales(h, 0.0, 1.0) == cp.ERR_INVALID
+        assert cp.compar_set_scalars(h, float("inf"), 0.0) == cp.ERR_INVALID
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 1e-30, 16, 16, 16, None) == cp.ERR_NO_VARIANT
