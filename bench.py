@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the 512-GEMM batched measurement (profiling runs)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the roofline denominators and exit")
     ap.add_argument("--variants", action="store_true",
@@ -281,6 +283,16 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched_only:
+        import torch
+        import workloads as W
+        import paper_2311_03543_b300 as cp
+        torch.cuda.set_device(0)
+        with cp.Context(0) as ctx:
+            print(json.dumps({"batched_512": measure_batched(ctx, cp, W, torch,
+                                                             torch.device("cuda", 0))}),
+                  flush=True)
+        return 0
     if args.peaks or args.variants:
         import torch
         import paper_2311_03543_b300 as cp

@@ -304,6 +304,25 @@ int compar_mlp_train_steps(compar_ctx_t ctx, float* params, float* adam_m,
 int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr,
                           uint64_t seed, float* val_loss);
 
+/* Continue training the current model from its weights and standardisation
+ * on all records (fine-tuning; a fresh training when none exists yet).
+ * Arguments as compar_selector_train. */
+int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr,
+                             uint64_t seed, float* val_loss);
+
+/* Online selection (the paper expects better-trained models to choose
+ * better, Sec. 3.2 and Sec. 5).  With probability `epsilon` a call whose
+ * context misses the decision cache runs a uniformly drawn eligible variant
+ * instead of the model's pick (exploration; that choice is not cached), every
+ * call is recorded, and once `retrain_every` (> 0) new records have
+ * accumulated the MLP is fine-tuned for `finetune_steps` (0: 500) steps
+ * inside the call that crosses the threshold (synchronous).  epsilon = 0 and
+ * retrain_every = 0 turn it off; recording stays as it was set. */
+int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
+                      int finetune_steps);
+/* Exploratory picks and online fine-tunings so far. */
+int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains);
+
 /* The trained model's prediction for one call: per variant (arrays of 6)
  * the ensemble-mean run time in ms, relative error, and the ensemble std of
  * log2 time (spread, nullable).  COMPAR_ERR_UNSUPPORTED when untrained. */

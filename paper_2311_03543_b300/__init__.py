@@ -88,6 +88,9 @@ SIGNATURES = {
     "compar_mlp_train_steps": (_i, [_vp, _fp, _fp, _fp, _i, _fp, _fp, _fp, _i,
                                     ctypes.POINTER(ctypes.c_int32), _i, _i, _f, _i, _fp, _fp]),
     "compar_selector_train": (_i, [_vp, _i, _i, _f, _u64, _fp]),
+    "compar_selector_finetune": (_i, [_vp, _i, _i, _f, _u64, _fp]),
+    "compar_set_online": (_i, [_vp, _d, _i64, _i]),
+    "compar_online_stats": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "compar_predict": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i, _fp, _fp, _fp]),
     "compar_residual_check": (_i, [_vp, _i64, _i64, _i64, _i, _vp, _vp, _vp, _f, _i, _u64,
                                    ctypes.POINTER(_d), _vp]),
@@ -391,6 +394,22 @@ class Context:
         _status(compar_selector_train(self.handle, steps, batch, lr, seed, ctypes.byref(vl)),
                 "selector_train")
         return vl.value
+
+    def selector_finetune(self, steps=500, batch=128, lr=5e-4, seed=1):
+        vl = ctypes.c_float()
+        _status(compar_selector_finetune(self.handle, steps, batch, lr, seed, ctypes.byref(vl)),
+                "selector_finetune")
+        return vl.value
+
+    def set_online(self, epsilon=0.05, retrain_every=0, finetune_steps=0):
+        return _status(compar_set_online(self.handle, float(epsilon), int(retrain_every),
+                                         int(finetune_steps)), "set_online")
+
+    def online_stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _status(compar_online_stats(self.handle, ctypes.byref(a), ctypes.byref(b)),
+                "online_stats")
+        return a.value, b.value
 
     def predict(self, m, n, k, dtype=F32, tol=0.0, batch=1):
         """MLP prediction: (time_ms[6], rel_err[6], spread[6])."""

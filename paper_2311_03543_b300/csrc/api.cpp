@@ -175,6 +175,23 @@ static int select_variant(compar_ctx* ctx, const GemmCall& c) {
   const DecisionKey key{c.m, c.n, c.k, static_cast<int>(c.dtype), tol_class(c.tol), c.batch};
   auto it = ctx->decisions.find(key);
   if (it != ctx->decisions.end() && (mask & (1u << it->second))) return it->second;
+  if (ctx->online.epsilon > 0) {
+    // Exploration: with probability epsilon run a uniformly drawn eligible
+    // variant once (not cached), so its timing is recorded for the models.
+    auto next = [&]() {
+      uint64_t z = (ctx->online.rng += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    if (static_cast<double>(next() >> 11) * (1.0 / 9007199254740992.0) < ctx->online.epsilon) {
+      int ids[kNumVariants], nids = 0;
+      for (int v = 0; v < kNumVariants; ++v)
+        if (mask & (1u << v)) ids[nids++] = v;
+      ctx->online.explored += 1;
+      return ids[next() % static_cast<uint64_t>(nids)];
+    }
+  }
   int v = -1;
   const char* by = "history";
   float mlp_ms = 0;
@@ -259,6 +276,23 @@ static int run_one(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
   return rc;
 }
 
+// Online mode: after `retrain_every` new timing records, fine-tune the MLP
+// from its current weights on every record (synchronous, on the model's own
+// stream) and start using it for new decisions.
+static void maybe_retrain(compar_ctx* ctx) {
+  auto& o = ctx->online;
+  if (o.retrain_every <= 0) return;
+  const int64_t have = static_cast<int64_t>(ctx->rec.ring.size() + ctx->pending.size());
+  if (have - o.records_at_train < o.retrain_every) return;
+  resolve_pending(ctx);
+  const int steps = o.finetune_steps > 0 ? o.finetune_steps : 500;
+  float vl = 0;
+  const int rc = compar_selector_finetune(ctx, steps, 128, 5e-4f, 0xC0FFEEull + o.retrains, &vl);
+  o.records_at_train = static_cast<int64_t>(ctx->rec.ring.size());
+  if (rc == COMPAR_OK) o.retrains += 1;
+  if (ctx->log) fprintf(stderr, "[compar] online fine-tune rc=%d loss=%.4f\n", rc, vl);
+}
+
 int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
   if (c.m == 0 || c.n == 0) return COMPAR_OK;
   if (c.k == 0) {
@@ -275,7 +309,10 @@ int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
     if (v < 0) return v;
     ctx->last_variant = v;
     const int rc = run_one(ctx, v, c, s);
-    if (rc == COMPAR_OK) return rc;
+    if (rc == COMPAR_OK) {
+      maybe_retrain(ctx);
+      return rc;
+    }
     // A variant that failed to launch is quarantined for this context and
     // the call is re-dispatched to the next choice.
     if (ctx->log)

@@ -36,6 +36,7 @@ constexpr int kRow = 128;  // bytes of K per stage
 constexpr int kThreads = 192;
 constexpr int kEpi = 128;
 constexpr int kChunkKB = 4;  // promotion every 4 stages
+constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
 
 template <int BN>
 struct GLayout {
@@ -43,18 +44,23 @@ struct GLayout {
   static constexpr int kB = BN * kRow;        // one B piece
   static constexpr int kStage = 2 * (kA + kB);
   static constexpr int kBar = 256;
-  static constexpr int kStagesRaw = (232448 - 1024 - kBar) / kStage;
+  static constexpr int kStaging = 4 * 32 * 33 * 4;  // one 32 x 32 (+pad) block per epilogue warp
+  static constexpr int kIndex = kMaxIndexed * 4;    // problems' tile_start values
+  static constexpr int kStagesRaw = (232448 - 1024 - kBar - kStaging - kIndex) / kStage;
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
-  static constexpr int kSmem = 1024 + kStages * kStage + kBar;
+  static constexpr int kSmem = 1024 + kStages * kStage + kBar + kStaging + kIndex;
   static constexpr int kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
 };
 
-__device__ __forceinline__ int find_problem(const GroupProblem* __restrict__ P, int count,
-                                            int tile) {
+// Last problem whose first tile is <= tile; s_start holds every problem's
+// tile_start in shared memory when the batch has at most kMaxIndexed problems.
+__device__ __forceinline__ int find_problem(const GroupProblem* __restrict__ P,
+                                            const int* s_start, int count, int tile) {
   int lo = 0, hi = count - 1;
-  while (lo < hi) {  // last problem with tile_start <= tile
+  while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (P[mid].tile_start <= tile) lo = mid;
+    const int st = s_start ? s_start[mid] : P[mid].tile_start;
+    if (st <= tile) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -84,6 +90,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drainb = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* staging = reinterpret_cast<float*>(smem + S * L::kStage + L::kBar);
+  int* s_index = reinterpret_cast<int*>(smem + S * L::kStage + L::kBar + L::kStaging);
+  const int* s_start = count <= kMaxIndexed ? s_index : nullptr;
+  if (s_start)
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s_index[i] = probs[i].tile_start;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     int last_q = -1;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const int q = find_problem(probs, count, tile);
+      const int q = find_problem(probs, s_start, count, tile);
       const GroupProblem& P = probs[q];
       const int local = tile - P.tile_start;
       const int mb = local % P.tiles_m, nb = local / P.tiles_m;
@@ -133,7 +144,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
       const int kelems = P.mode == 2 ? kRow / 4 : kRow / 2;
-      for (int kb = 0; kb < P.num_kb; ++kb) {
+      // problem fields go to registers once: the loop's asm statements clobber
+      // memory, so fields read through P would be reloaded every iteration
+      const int num_kb = P.num_kb;
+      for (int kb = 0; kb < num_kb; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
           ok = false;
           break;
@@ -166,9 +180,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc_iter = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
       const int mode = P.mode;
-      for (int kb0 = 0; ok && kb0 < P.num_kb; kb0 += kChunkKB, ++acc_iter) {
+      const int num_kb = P.num_kb;
+      for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kChunkKB, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
           ok = false;
@@ -176,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         dev::tc_fence_after();
         const uint32_t d = tmem_base + acc * BN;
-        const int kb_end = min(P.num_kb, kb0 + kChunkKB);
+        const int kb_end = min(num_kb, kb0 + kChunkKB);
         for (int kb = kb0; kb < kb_end; ++kb) {
           if (!dev::mbar_wait(&full[stage], phase, w)) {
             ok = false;
@@ -220,14 +235,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc_iter = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const GroupProblem& P = probs[find_problem(probs, count, tile)];
+      const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
       const int local = tile - P.tile_start;
       const int mb = local % P.tiles_m, nb = local / P.tiles_m;
-      const int row = mb * kBM + quarter * 32 + lane;
+      const int pM = P.M, pN = P.N, num_kb = P.num_kb;
+      float* const pC = P.C;
+      const int64_t ldc = P.ldc;
+      const float alpha = P.alpha, beta = P.beta;
       float sum[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) sum[j] = 0.f;
-      const int chunks = (P.num_kb + kChunkKB - 1) / kChunkKB;
+      const int chunks = (num_kb + kChunkKB - 1) / kChunkKB;
       for (int ch = 0; ch < chunks; ++ch, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) {
@@ -248,17 +266,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         dev::mbar_arrive(&tempty[acc]);
       }
       if (!ok) break;
-      if (row < P.M) {
-        float* crow = P.C + static_cast<int64_t>(row) * P.ldc;
-        const int col0 = nb * BN;
+      // Coalesced stores: each 32 x 32 block goes through shared memory so
+      // that lane j then writes column j of one row per instruction (one
+      // 128-byte segment) instead of 32 rows at once.
+      float (*stg)[33] = reinterpret_cast<float (*)[33]>(staging + (warp - 2) * 32 * 33);
+      const int row0 = mb * kBM + quarter * 32;
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          if (col0 + j < P.N) {
-            float v = P.alpha * sum[j];
-            if (P.beta != 0.f) v = fmaf(P.beta, crow[col0 + j], v);
-            crow[col0 + j] = v;
+      for (int c = 0; c < BN / 32; ++c) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[lane][j] = sum[c * 32 + j];
+        __syncwarp();
+        const int col = nb * BN + c * 32 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int r = row0 + rr;
+          if (r < pM && col < pN) {
+            float* dst = pC + static_cast<int64_t>(r) * ldc + col;
+            float v = alpha * stg[rr][lane];
+            if (beta != 0.f) v = fmaf(beta, *dst, v);
+            *dst = v;
           }
         }
+        __syncwarp();
       }
     }
   }

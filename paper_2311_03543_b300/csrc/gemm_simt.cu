@@ -93,7 +93,9 @@ struct SimtCfg {
 };
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
-__global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads)
+// Two CTAs per SM (registers capped at 128) so one CTA's global loads and
+// barrier overlap the other's FMAs.
+__global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads, 2)
     gemm_simt_kernel(int M, int N, int K, int k_per_split, float alpha,
                      const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
                      int64_t ldb, float beta, float* __restrict__ C, int64_t ldc,

@@ -13,7 +13,8 @@ namespace compar {
 // (A: M x K, B re-laid out as N x K); map_a2 / map_b2 are the lo pieces of
 // the 3xBF16 mode.  Tiles of all problems form one list; this problem owns
 // tiles [tile_start, tile_start + tiles_m * tiles_n), column-major by tile.
-struct alignas(64) GroupProblem {
+// (CUtensorMap members make the struct 128-byte aligned, as TMA requires.)
+struct GroupProblem {
   CUtensorMap map_a, map_b, map_a2, map_b2;
   int M, N, K, num_kb;
   int tiles_m, tiles_n, tile_start, mode;  // mode: 0 bf16, 1 3xbf16, 2 tf32

@@ -72,6 +72,36 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   for (int o = 0; o < kOut; ++o) Y[(static_cast<int64_t>(e) * rows + r) * kOut + o] = y[o];
 }
 
+// Inference for a few rows (a selection decision): one 64-thread block per
+// (row, member); thread j computes hidden unit j of each layer, so a row's
+// forward pass takes three short dependent steps instead of one long serial
+// loop.
+__global__ void __launch_bounds__(64) mlp_forward_small_kernel(const float* __restrict__ params,
+                                                               const float* __restrict__ X,
+                                                               int rows, float* __restrict__ Y) {
+  __shared__ float x[kIn], h1[kH], h2[kH];
+  const int r = blockIdx.x, e = blockIdx.y, j = threadIdx.x;
+  const float* p = params + static_cast<int64_t>(e) * kP;
+  if (j < kIn) x[j] = X[r * kIn + j];
+  __syncthreads();
+  float z = p[ob1 + j];
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) z = fmaf(p[oW1 + j * kIn + i], x[i], z);
+  h1[j] = fmaxf(z, 0.f);
+  __syncthreads();
+  z = p[ob2 + j];
+#pragma unroll 16
+  for (int i = 0; i < kH; ++i) z = fmaf(p[oW2 + j * kH + i], h1[i], z);
+  h2[j] = fmaxf(z, 0.f);
+  __syncthreads();
+  if (j < kOut) {
+    z = p[ob3 + j];
+#pragma unroll 16
+    for (int i = 0; i < kH; ++i) z = fmaf(p[oW3 + j * kH + i], h2[i], z);
+    Y[(static_cast<int64_t>(e) * rows + r) * kOut + j] = z;
+  }
+}
+
 __device__ __forceinline__ float block_sum(float v, float* red) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -255,8 +285,12 @@ int mlp_param_count() { return kP; }
 int mlp_forward_device(const float* d_params, int members, const float* d_X, int rows,
                        float* d_Y, cudaStream_t s) {
   if (rows <= 0 || members <= 0) return COMPAR_OK;
-  dim3 grid((rows + 127) / 128, members);
-  mlp_forward_kernel<<<grid, 128, 0, s>>>(d_params, d_X, rows, d_Y);
+  if (rows <= 64) {
+    mlp_forward_small_kernel<<<dim3(rows, members), 64, 0, s>>>(d_params, d_X, rows, d_Y);
+  } else {
+    dim3 grid((rows + 127) / 128, members);
+    mlp_forward_kernel<<<grid, 128, 0, s>>>(d_params, d_X, rows, d_Y);
+  }
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;

@@ -259,49 +259,57 @@ int grid_for(int64_t total) {
 }
 
 // ------------------------------------------------------------------ grouped
-__device__ __forceinline__ int find_job(const PrepassJob* __restrict__ J, int n, int tile) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (J[mid].tile_start <= tile) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
-// Every operand re-layout of a batch in one launch: blocks stride over the
-// concatenated 32x32 tile lists of all jobs.
-__global__ void grouped_prepass_kernel(const PrepassJob* __restrict__ jobs, int njobs,
-                                       int total_tiles) {
-  __shared__ float tile[32][33];
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    const PrepassJob& J = jobs[find_job(jobs, njobs, t)];
-    const int local = t - J.tile_start;
-    const int64_t r0 = static_cast<int64_t>(local / J.tiles_c) * 32;
-    const int64_t c0 = static_cast<int64_t>(local % J.tiles_c) * 32;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-      const int64_t r = r0 + i, c = c0 + threadIdx.x;
-      float v = 0.f;
-      if (r < J.rows && c < J.cols) {
-        if (J.in_type == COMPAR_F32)
-          v = static_cast<const float*>(J.src)[r * J.ld_src + c];
-        else
-          v = __bfloat162float(static_cast<const __nv_bfloat16*>(J.src)[r * J.ld_src + c]);
+// Every operand re-layout of a batch in one launch.  Block row y works on
+// job y (its fields read once); its gridDim.x blocks stride over the job's
+// 64 x 64 tiles, 16 independent loads and stores per thread per tile.
+constexpr int kPrepassBlocksPerJob = 16;
+
+__global__ void __launch_bounds__(256) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
+                                                              int njobs) {
+  __shared__ float tile[64][65];
+  const PrepassJob J = jobs[blockIdx.y];
+  const int tiles_c = (J.cols + 63) / 64;
+  const int tiles = ((J.rows + 63) / 64) * tiles_c;
+  // a bf16 copy goes through float and back, which is exact
+  const F32Out o{J.out_kind == PP_COPY ? (J.in_type == COMPAR_F32 ? PP_F32 : PP_BF16)
+                                       : J.out_kind,
+                 1.f};
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t r0 = static_cast<int64_t>(t / tiles_c) * 64;
+    const int64_t c0 = static_cast<int64_t>(t % tiles_c) * 64;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int li = ty + 8 * i, lj = tx + 32 * h;
+        const int64_t r = r0 + li, c = c0 + lj;
+        float v = 0.f;
+        if (r < J.rows && c < J.cols) {
+          if (J.in_type == COMPAR_F32)
+            v = __ldg(static_cast<const float*>(J.src) + r * J.ld_src + c);
+          else
+            v = __bfloat162float(static_cast<const __nv_bfloat16*>(J.src)[r * J.ld_src + c]);
+        }
+        tile[li][lj] = v;
       }
-      tile[i][threadIdx.x] = v;
     }
     __syncthreads();
-    // a bf16 copy goes through float and back, which is exact
-    const F32Out o{J.out_kind == PP_COPY ? (J.in_type == COMPAR_F32 ? PP_F32 : PP_BF16)
-                                         : J.out_kind,
-                   1.f};
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-      if (J.transpose) {
-        const int64_t c = c0 + i, r = r0 + threadIdx.x;
-        if (c < J.cols && r < J.rows) store_converted(o, tile[threadIdx.x][i], J.dst, J.dst_lo, c * J.ld_dst + r);
-      } else {
-        const int64_t r = r0 + i, c = c0 + threadIdx.x;
-        if (r < J.rows && c < J.cols) store_converted(o, tile[i][threadIdx.x], J.dst, J.dst_lo, r * J.ld_dst + c);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int li = ty + 8 * i, lj = tx + 32 * h;
+        if (J.transpose) {  // output row c0 + li holds input column c0 + li
+          const int64_t c = c0 + li, r = r0 + lj;
+          if (c < J.cols && r < J.rows)
+            store_converted(o, tile[lj][li], J.dst, J.dst_lo, c * J.ld_dst + r);
+        } else {
+          const int64_t r = r0 + li, c = c0 + lj;
+          if (r < J.rows && c < J.cols)
+            store_converted(o, tile[li][lj], J.dst, J.dst_lo, r * J.ld_dst + c);
+        }
       }
     }
     __syncthreads();
@@ -312,9 +320,10 @@ __global__ void grouped_prepass_kernel(const PrepassJob* __restrict__ jobs, int 
 
 int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles, int num_sms,
                            cudaStream_t s) {
+  (void)num_sms;
   if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
-  const int grid = std::min(total_tiles, 8 * num_sms);
-  grouped_prepass_kernel<<<grid, dim3(32, 8), 0, s>>>(d_jobs, njobs, total_tiles);
+  if (njobs > 65535) return COMPAR_ERR_INVALID;
+  grouped_prepass_kernel<<<dim3(kPrepassBlocksPerJob, njobs), dim3(32, 8), 0, s>>>(d_jobs, njobs);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;

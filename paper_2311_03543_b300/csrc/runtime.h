@@ -148,6 +148,16 @@ struct compar_ctx {
   std::vector<cudaEvent_t> event_pool;
   // batch signature -> autotuned batched configuration (0 loop, 1..4 grouped)
   std::unordered_map<uint64_t, int> batched_cfg;
+  // online selection: exploration probability on decision-cache misses and
+  // warm-start fine-tuning of the MLP every `retrain_every` new records
+  struct Online {
+    double epsilon = 0.0;
+    int64_t retrain_every = 0;
+    int finetune_steps = 0;
+    int64_t records_at_train = 0;
+    uint64_t rng = 0x243F6A8885A308D3ull;
+    int64_t explored = 0, retrains = 0;
+  } online;
   void* batched_state = nullptr;
   // MLP device buffers (selector inference / training), owned here.
   void* mlp_dev = nullptr;

@@ -240,10 +240,14 @@ int compar_mlp_train_steps(compar_ctx_t ctx, float* params, float* adam_m, float
   return COMPAR_OK;
 }
 
-int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
-                          float* val_loss) {
+// Training from the records.  warm = continue from the current parameters
+// and standardisation (fine-tuning); otherwise fresh statistics and a fresh
+// initialisation.
+static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed, bool warm,
+                      float* val_loss) {
   if (!ctx || steps <= 0 || batch <= 0 || batch > 128 || !(lr > 0)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
+  warm = warm && ctx->mlp.trained;
   // ---- assemble rows from the records
   auto recs = ctx->rec.snapshot();
   std::vector<std::array<float, kNumFeatures>> feats;
@@ -287,12 +291,17 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint
     }
     const double mean = s / rows;
     const double var = std::max(0.0, s2 / rows - mean * mean);
+    if (warm) {  // the parameters were fitted to the current standardisation
+      mm.feat_min[j] = std::min(mm.feat_min[j], lo);
+      mm.feat_max[j] = std::max(mm.feat_max[j], hi);
+      continue;
+    }
     mm.feat_mean[j] = static_cast<float>(mean);
     mm.feat_std[j] = static_cast<float>(std::max(std::sqrt(var), 1e-3));
     mm.feat_min[j] = lo;
     mm.feat_max[j] = hi;
   }
-  for (int o = 0; o < kOutputs; ++o) {
+  for (int o = 0; !warm && o < kOutputs; ++o) {
     double s = 0, s2 = 0, c = 0;
     for (int r = 0; r < rows; ++r)
       if (msk[r][o] > 0) {
@@ -323,9 +332,13 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint
   const size_t P = MlpParams::count();
   std::vector<float> params(kEnsemble * P), flat;
   for (int e = 0; e < kEnsemble; ++e) {
-    MlpParams p;
-    p.init(seed * 7919ull + 17ull * e + 1);
-    p.flatten(flat);
+    if (warm) {
+      mm.members[e].flatten(flat);
+    } else {
+      MlpParams p;
+      p.init(seed * 7919ull + 17ull * e + 1);
+      p.flatten(flat);
+    }
     std::copy(flat.begin(), flat.end(), params.begin() + e * P);
   }
   const int B = std::min<int>(batch, static_cast<int>(train_rows.size()));
@@ -368,6 +381,36 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint
   auto* d = static_cast<MlpDevice*>(ctx->mlp_dev);
   if (d) d->uploaded = false;
   ctx->decisions.clear();
+  return COMPAR_OK;
+}
+
+int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
+                          float* val_loss) {
+  return train_impl(ctx, steps, batch, lr, seed, false, val_loss);
+}
+
+int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
+                             float* val_loss) {
+  return train_impl(ctx, steps, batch, lr, seed, true, val_loss);
+}
+
+int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
+                      int finetune_steps) {
+  if (!ctx || !(epsilon >= 0.0 && epsilon <= 1.0) || retrain_every < 0 || finetune_steps < 0)
+    return COMPAR_ERR_INVALID;
+  ctx->online.epsilon = epsilon;
+  ctx->online.retrain_every = retrain_every;
+  ctx->online.finetune_steps = finetune_steps;
+  ctx->online.records_at_train =
+      static_cast<int64_t>(ctx->rec.ring.size() + ctx->pending.size());
+  if (epsilon > 0 || retrain_every > 0) ctx->rec.on = true;
+  return COMPAR_OK;
+}
+
+int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains) {
+  if (!ctx || !explored || !retrains) return COMPAR_ERR_INVALID;
+  *explored = ctx->online.explored;
+  *retrains = ctx->online.retrains;
   return COMPAR_OK;
 }
 

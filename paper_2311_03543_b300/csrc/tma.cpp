@@ -4,12 +4,40 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 #include "common.h"
 
 namespace compar {
 namespace {
+
+// Encoded maps are cached by their full argument list: a tensor map depends
+// on nothing else, so a hit is exactly the map the driver would return.
+// Batched calls encode hundreds of maps per call; with the cache a repeated
+// batch encodes none.
+struct MapKey {
+  uintptr_t base;
+  uint64_t inner, outer, ld;
+  uint32_t box_inner, box_outer;
+  int dt, elem, swizzle;
+  bool operator==(const MapKey& o) const { return memcmp(this, &o, sizeof(MapKey)) == 0; }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    const auto* p = reinterpret_cast<const unsigned char*>(&k);
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < sizeof(MapKey); ++i) {
+      h ^= p[i];
+      h *= 1099511628211ull;
+    }
+    return static_cast<size_t>(h);
+  }
+};
+constexpr size_t kMapCacheMax = 1 << 16;
+std::mutex g_cache_mu;
+std::unordered_map<MapKey, CUtensorMap, MapKeyHash>* g_cache = nullptr;
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -51,6 +79,26 @@ int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, cons
       box_inner * elem_bytes != static_cast<uint32_t>(swizzle_bytes) || box_outer == 0 ||
       box_outer > 256)
     return COMPAR_ERR_INVALID;
+  MapKey key;
+  memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
+  key.base = reinterpret_cast<uintptr_t>(base);
+  key.inner = inner;
+  key.outer = outer;
+  key.ld = ld_elems;
+  key.box_inner = box_inner;
+  key.box_outer = box_outer;
+  key.dt = static_cast<int>(dt);
+  key.elem = elem_bytes;
+  key.swizzle = swizzle_bytes;
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    if (!g_cache) g_cache = new std::unordered_map<MapKey, CUtensorMap, MapKeyHash>();
+    auto it = g_cache->find(key);
+    if (it != g_cache->end()) {
+      *map = it->second;
+      return COMPAR_OK;
+    }
+  }
   const cuuint64_t dims[2] = {inner, outer};
   const cuuint64_t strides[1] = {ld_elems * static_cast<uint64_t>(elem_bytes)};
   const cuuint32_t box[2] = {box_inner, box_outer};
@@ -61,7 +109,11 @@ int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, cons
                                                    : CU_TENSOR_MAP_SWIZZLE_64B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? COMPAR_OK : COMPAR_ERR_CUDA;
+  if (r != CUDA_SUCCESS) return COMPAR_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  if (g_cache->size() >= kMapCacheMax) g_cache->clear();
+  (*g_cache)[key] = *map;
+  return COMPAR_OK;
 }
 
 }  // namespace compar

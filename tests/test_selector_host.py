@@ -137,3 +137,22 @@ def test_records_ring_and_validation(hctx):
         hctx.record_add([bad])
     hctx.record_clear()
     assert hctx.records() == []
+
+
+def test_online_exploration_stays_within_eligible_variants(hctx):
+    # epsilon = 1: every decision-cache miss explores; picks vary, are never
+    # cached, and never leave the variants that meet the tolerance
+    hctx.set_online(epsilon=1.0)
+    seen = set()
+    for _ in range(200):
+        v = hctx.select(2048, 2048, 2048, cp.F32, 1e-5)
+        assert v in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3)
+        seen.add(v)
+    assert len(seen) >= 2
+    explored, retrains = hctx.online_stats()
+    assert explored == 200 and retrains == 0
+    hctx.set_online(epsilon=0.0)
+    first = hctx.select(2048, 2048, 2048, cp.F32, 1e-5)
+    assert all(hctx.select(2048, 2048, 2048, cp.F32, 1e-5) == first for _ in range(20))
+    with pytest.raises(cp.ComparError):
+        hctx.set_online(epsilon=1.5)
