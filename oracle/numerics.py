@@ -145,6 +145,33 @@ def split_bf16(x):
     return hi, lo
 
 
+def split_bf16_3(x):
+    """Three-piece split: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid).
+
+    Both residuals are formed in float32 and are exact there (each piece holds
+    the leading bits of what remains), so only the roundings to bf16 lose
+    information; hi + mid + lo carries ~24 significant bits of x.
+    """
+    x = np.asarray(x, dtype=np.float32)
+    hi = bf16_bits(x)
+    r1 = (x - bf16_to_f32(hi)).astype(np.float32)
+    mid = bf16_bits(r1)
+    r2 = (r1 - bf16_to_f32(mid)).astype(np.float32)
+    lo = bf16_bits(r2)
+    return hi, mid, lo
+
+
+def split6_product(A, B, gemm):
+    """The 6-product sum of the 3-piece split, in float64 via `gemm`:
+    hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi (the mid*lo, lo*mid and
+    lo*lo terms are dropped)."""
+    f = lambda b: bf16_to_f32(b).astype(np.float64)
+    ah, am, al = (f(p) for p in split_bf16_3(A))
+    bh, bm, bl = (f(p) for p in split_bf16_3(B))
+    return (gemm(ah, bh) + gemm(ah, bm) + gemm(am, bh) + gemm(ah, bl) + gemm(am, bm)
+            + gemm(al, bh))
+
+
 def split3_operands(A, B):
     """The three bf16 products of the 3xBF16 method, as float64 matrices.
 

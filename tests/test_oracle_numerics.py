@@ -115,6 +115,35 @@ def test_split_residual_bound():
     assert np.all(err <= 2.0 ** -17 * np.abs(x.astype(np.float64)))
 
 
+def test_three_piece_split_is_exact_for_24_bit_significands():
+    # every float32 has 24 significant bits: hi + mid + lo reproduces it
+    # exactly unless the exponent range of the pieces runs out (not for
+    # moderate magnitudes)
+    x = np.concatenate([W.uniform(1, 5000, seed=12).ravel(), W.normal(1, 5000, seed=13).ravel()])
+    hi, mid, lo = N.split_bf16_3(x)
+    recon = sum(N.bf16_to_f32(p).astype(np.float64) for p in (hi, mid, lo))
+    assert np.array_equal(recon, x.astype(np.float64))
+
+
+def test_three_piece_split_pieces_shrink():
+    x = W.normal(64, 64, seed=14)
+    hi, mid, lo = N.split_bf16_3(x)
+    h, m, l = (np.abs(N.bf16_to_f32(p).astype(np.float64)) for p in (hi, mid, lo))
+    ax = np.abs(x.astype(np.float64))
+    assert np.all(m <= 2.0 ** -8 * ax + 1e-45)
+    assert np.all(l <= 2.0 ** -16 * ax + 1e-45)
+
+
+def test_split6_product_on_exact_pieces():
+    # matrices whose entries are exact bf16 values: mid = lo = 0 and the
+    # 6-product sum is the plain product
+    import oracle
+    A = N.bf16_to_f32(W.bf16_input(7, 9, seed=15)).astype(np.float32)
+    B = N.bf16_to_f32(W.bf16_input(9, 5, seed=16)).astype(np.float32)
+    got = N.split6_product(A, B, oracle.gemm)
+    assert np.array_equal(got, oracle.gemm(A, B))
+
+
 def test_rel_frobenius_closed_forms():
     a = np.array([[3.0, 4.0]])
     assert N.rel_frobenius(a, a) == 0.0
