@@ -247,7 +247,7 @@ def measure_variants(ctx, cp, torch, dev, peaks):
     pipe = {cp.V_NAIVE: peaks["ffma_tflops"], cp.V_SIMT: peaks["ffma_tflops"],
             cp.V_TC_TF32: peaks["tf32_tflops"], cp.V_TC_BF16: peaks["bf16_tflops"],
             cp.V_TC_FP8: peaks.get("fp8_tflops") or 2 * peaks["bf16_tflops"],
-            cp.V_SPLIT3: peaks["bf16_tflops"] / 3}
+            cp.V_SPLIT3: peaks["bf16_tflops"] / 3, cp.V_SPLIT6: peaks["bf16_tflops"] / 6}
     rows = []
     for (m, n, k) in shapes:
         g = torch.Generator(device=dev)
@@ -389,7 +389,7 @@ def main():
     prof = {v: ctx.profile_read(v) for v in range(cp.NUM_VARIANTS)}
     dom = max(prof, key=lambda v: prof[v][0])
     dom_ms, dom_n = prof[dom]
-    pieces = {cp.V_SPLIT3: 3}.get(dom, 1)
+    pieces = {cp.V_SPLIT3: 3, cp.V_SPLIT6: 6}.get(dom, 1)
     dom_flops = args.steps * sum(2.0 * m * n * k * pieces
                                  for (m, n, k), v in zip(shapes, picks) if v == dom)
     achieved = dom_flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
@@ -479,9 +479,13 @@ def main():
     regret = None
     if not args.no_regret and rank == 0:
         r_pct, r_viol, r_n = measure_regret(ctx, cp, W, torch, dev)
+        t_pct, t_viol, t_n = measure_regret(ctx, cp, W, torch, dev, count=50,
+                                            contexts=W.heldout_tight_contexts())
         regret = {"mean_pct": r_pct, "violations": r_viol, "contexts": r_n,
                   "set": "held-out contexts 0..199 (M,N,K log-uniform [16,4096], f32/bf16/fp8, "
-                         "tol 1e-5/1e-3/1e-1)", "feasibility": "library FP64 residual check, 8 rows"}
+                         "tol 1e-5/1e-3/1e-1)", "feasibility": "library FP64 residual check, 8 rows",
+                  "tight": {"mean_pct": t_pct, "violations": t_viol, "contexts": t_n,
+                            "set": "f32 contexts 0..49 at tol 1e-6 (same shape law)"}}
 
     batched = None
     if not args.no_batched and rank == 0:
@@ -587,7 +591,7 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
             "autotune_ms": dict(zip(names, tuned_ms))}
 
 
-def measure_regret(ctx, cp, W, torch, dev, count=200):
+def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):
     """Mean regret (%) of the selector on held-out contexts vs exhaustive timing.
 
     The first `count` held-out contexts (M, N, K log-uniform in [16, 4096],
@@ -601,7 +605,8 @@ def measure_regret(ctx, cp, W, torch, dev, count=200):
     tie = 0.02
     rs, viol = [], 0
     judge = cp.Context(dev.index)   # measures; the selector's history never sees it
-    for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts()[:count]):
+    contexts = W.heldout_contexts() if contexts is None else contexts
+    for i, (m, n, k, dt, tol) in enumerate(contexts[:count]):
         g = torch.Generator(device=dev)
         g.manual_seed(90000 + i)
         A = torch.rand((m, k), generator=g, device=dev) * 2 - 1

@@ -75,8 +75,10 @@ enum {
     COMPAR_V_TC_BF16 = 3,     /* tcgen05 kind::f16 (bf16 operands)          */
     COMPAR_V_TC_FP8 = 4,      /* tcgen05 kind::f8f6f4 (E4M3 operands)       */
     COMPAR_V_SPLIT3 = 5,      /* 3xBF16 split on tcgen05 (FP32 accuracy)    */
-    COMPAR_V_COUNT = 6,
-    COMPAR_V_GROUPED = 6      /* persistent grouped kernel (batched only)   */
+    COMPAR_V_SPLIT6 = 6,      /* 6-product 3-piece bf16 split on tcgen05
+                                 (below-FP32-SIMT error level)              */
+    COMPAR_V_COUNT = 7,
+    COMPAR_V_GROUPED = 7      /* persistent grouped kernel (batched only)   */
 };
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -262,20 +264,20 @@ int compar_selector_save(compar_ctx_t ctx, const char* path);
 
 /* ---------------------------------------------------------------- learned cost model */
 
-/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 12, ReLU)
+/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 14, ReLU)
  * per ensemble member (4 members).  Inputs (features of a call):
  * log2 M, log2 N, log2 K, one-hot dtype (f32, bf16, f8), log10 tol,
- * log2 batch.  Outputs: for variant v (0..5) output v is log2 of the run
- * time in ms and output 6+v log10 of the relative error.  The paper's runtime
+ * log2 batch.  Outputs: for variant v (0..COMPAR_V_COUNT-1) output v is log2 of the run
+ * time in ms and output COMPAR_V_COUNT+v log10 of the relative error.  The paper's runtime
  * chooses variants with performance models it calls machine-learning models
  * and expects better-trained models to choose better (Sec. 3.2, Sec. 5).
  * Parameters of one member, float32, in this order: W1[64][8] b1[64]
- * W2[64][64] b2[64] W3[12][64] b3[12] (weights stored out x in). */
+ * W2[64][64] b2[64] W3[14][64] b3[14] (weights stored out x in). */
 int compar_mlp_param_count(void);
 
 /* Forward pass on the GPU for `members` parameter sets (host array
  * members x param_count) over `rows` raw (already standardised) feature rows
- * (host, rows x 8); Y (host) receives members x rows x 12.  Synchronous. */
+ * (host, rows x 8); Y (host) receives members x rows x 14.  Synchronous. */
 int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
                        const float* X, int rows, float* Y);
 

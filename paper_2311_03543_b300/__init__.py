@@ -19,9 +19,12 @@ LIB_PATH = os.path.join(_HERE, "libcompar.so")
 # dtypes / statuses / variant ids (values of include/compar.h)
 F32, BF16, F8E4M3 = 0, 1, 2
 OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_IO, ERR_NO_VARIANT = 0, -1, -2, -3, -4, -5, -6
-V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3, V_GROUPED = 0, 1, 2, 3, 4, 5, 6
-NUM_VARIANTS = 6
-VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16"]
+V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3, V_SPLIT6 = 0, 1, 2, 3, 4, 5, 6
+V_GROUPED = 7
+NUM_VARIANTS = 7
+MLP_OUTPUTS = 2 * NUM_VARIANTS   # log2 time and log10 error per variant
+VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16",
+                 "split-6xbf16"]
 
 
 class ComparError(RuntimeError):
@@ -352,12 +355,17 @@ class Context:
 
     # -- learned cost model ----------------------------------------------------
     def mlp_forward(self, params, X):
-        """params: float32 (members, P); X: float32 (rows, 8) -> (members, rows, 12)."""
+        """params: float32 (members, P); X: float32 (rows, 8) ->
+        (members, rows, 2 * NUM_VARIANTS)."""
         import numpy as np
         params = np.ascontiguousarray(params, dtype=np.float32)
         X = np.ascontiguousarray(X, dtype=np.float32)
+        if params.ndim != 2 or params.shape[1] != compar_mlp_param_count():
+            raise ValueError(f"params must be (members, {compar_mlp_param_count()})")
+        if X.ndim != 2 or X.shape[1] != 8:
+            raise ValueError("X must be (rows, 8)")
         members, rows = params.shape[0], X.shape[0]
-        Y = np.zeros((members, rows, 12), dtype=np.float32)
+        Y = np.zeros((members, rows, MLP_OUTPUTS), dtype=np.float32)
         _status(compar_mlp_forward(self.handle, _f32p(params), members, _f32p(X), rows, _f32p(Y)),
                 "mlp_forward")
         return Y
@@ -372,6 +380,16 @@ class Context:
         T = np.ascontiguousarray(T, dtype=np.float32)
         mask = np.ascontiguousarray(mask, dtype=np.float32)
         idx = np.ascontiguousarray(batch_idx, dtype=np.int32)   # (members, steps, batch)
+        rows = X.shape[0]
+        if params.ndim != 2 or params.shape[1] != compar_mlp_param_count():
+            raise ValueError(f"params must be (members, {compar_mlp_param_count()})")
+        if X.ndim != 2 or X.shape[1] != 8:
+            raise ValueError("X must be (rows, 8)")
+        if T.shape != (rows, MLP_OUTPUTS) or mask.shape != (rows, MLP_OUTPUTS):
+            raise ValueError(f"T and mask must be (rows, {MLP_OUTPUTS})")
+        if idx.ndim != 3 or idx.shape[0] != members or (idx.size and
+                                                         (idx.min() < 0 or idx.max() >= rows)):
+            raise ValueError("batch_idx must be (members, steps, batch) row indices")
         steps, batch = idx.shape[1], idx.shape[2]
         loss = np.zeros((members, steps), dtype=np.float32)
         ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))

@@ -52,7 +52,7 @@ void Workspace::release() {
 
 static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",
                                       "tc-bf16",   "tc-fp8",   "split-3xbf16",
-                                      "grouped"};
+                                      "split-6xbf16", "grouped"};
 
 static double default_tol(double tol) { return tol > 0 ? tol : 1e-5; }
 
@@ -73,6 +73,7 @@ bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
     case COMPAR_V_SPLIT3:
+    case COMPAR_V_SPLIT6:
       return tc_supported(v, c);
     default:
       return false;
@@ -90,7 +91,8 @@ static int launch_variant(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_
     case COMPAR_V_TC_TF32:
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
-    case COMPAR_V_SPLIT3: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
+    case COMPAR_V_SPLIT3:
+    case COMPAR_V_SPLIT6: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
     default: return COMPAR_ERR_UNSUPPORTED;
   }
 }
@@ -100,7 +102,9 @@ static uint32_t eligible_mask(const compar_ctx* ctx, const GemmCall& c) {
   uint32_t mask = 0;
   for (int v = 0; v < kNumVariants; ++v) {
     if (ctx->quarantined[v] || !variant_supported(ctx, v, c)) continue;
-    if (ctx->err.predict(v, c.dtype, c.k) * ctx->err.margin > c.tol) continue;
+    // SIMT's error follows its longest FMA chain (split K shortens it)
+    const int64_t k_chain = v == COMPAR_V_SIMT ? simt_plan(c.m, c.n, c.k, ctx->num_sms).k_per : c.k;
+    if (ctx->err.predict(v, c.dtype, k_chain) * ctx->err.margin > c.tol) continue;
     mask |= 1u << v;
   }
   return mask;

@@ -97,9 +97,20 @@ int grouped_mode(const compar_problem_t& p, double tol) {
   return tol >= 2e-3 ? 2 : 1;
 }
 
-bool grouped_eligible(const compar_problem_t& p) {
-  return (p.dtype == COMPAR_F32 || p.dtype == COMPAR_BF16) && p.m > 0 && p.n > 0 && p.k > 0 &&
-         p.m <= INT32_MAX && p.n <= INT32_MAX && p.k <= INT32_MAX;
+// The single-call variant whose error model covers a grouped mode (the
+// grouped kernel promotes its accumulators like the single-call kernels).
+int mode_variant(int mode) {
+  return mode == 0 ? COMPAR_V_TC_BF16 : (mode == 1 ? COMPAR_V_SPLIT3 : COMPAR_V_TC_TF32);
+}
+
+// A problem joins the grouped launch only if its mode meets the tolerance;
+// the others (e.g. below 3xBF16's error level) are selected one by one.
+bool grouped_eligible(const compar_ctx* ctx, const compar_problem_t& p, double tol) {
+  if (!((p.dtype == COMPAR_F32 || p.dtype == COMPAR_BF16) && p.m > 0 && p.n > 0 && p.k > 0 &&
+        p.m <= INT32_MAX && p.n <= INT32_MAX && p.k <= INT32_MAX))
+    return false;
+  const int v = mode_variant(grouped_mode(p, tol));
+  return ctx->err.predict(v, p.dtype, p.k) * ctx->err.margin <= tol;
 }
 
 GemmCall to_call(const compar_problem_t& p, double tol) {
@@ -148,11 +159,11 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
   const int bn = cfg_bn(cfg);
   std::vector<int> order;
   for (int i = 0; i < count; ++i)
-    if (grouped_eligible(probs[i])) order.push_back(i);
+    if (grouped_eligible(ctx, probs[i], tol)) order.push_back(i);
   // problems the grouped kernel does not take run one by one afterwards
   auto run_rest = [&]() {
     for (int i = 0; i < count; ++i) {
-      if (grouped_eligible(probs[i])) continue;
+      if (grouped_eligible(ctx, probs[i], tol)) continue;
       const int rc = run_single(ctx, probs[i], tol, s);
       if (rc != COMPAR_OK) return rc;
     }
@@ -265,10 +276,14 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
       J.in_type = p.dtype;
       J.out_kind = out_kind;
       J.transpose = transpose;
-      J.tiles_c = static_cast<int>((cols + 31) / 32);
-      J.tiles = static_cast<int>((rows + 31) / 32) * J.tiles_c;
+      J.tiles_c = static_cast<int>((cols + 63) / 64);
+      J.tiles = static_cast<int>((rows + 63) / 64) * J.tiles_c;
       J.tile_start = ptile_acc;
       ptile_acc += J.tiles;
+      // 4-wide loads need 4-element-aligned rows (16 B for f32, 8 B for bf16);
+      // the outputs (pitch ldk, a multiple of 16) are always aligned
+      const int in_elem = p.dtype == COMPAR_F32 ? 4 : 2;
+      J.vec = (reinterpret_cast<uintptr_t>(src) % (4 * in_elem) == 0) && (ld_src % 4 == 0);
     };
     // B: K x N row-major -> N x K
     add_job(p.B, p.ldb, p.k, p.n, bw, P.pieces == 2 ? bw + P.b_bytes : nullptr, 1);

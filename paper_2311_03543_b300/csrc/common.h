@@ -84,11 +84,20 @@ int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
 int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                 cudaStream_t s);
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s);
+// Tile shape and split-K plan of the SIMT variant: each output is the sum
+// of `splits` partial dot products, each at most `k_per` terms long.
+struct SimtPlan {
+  int bm, bn, bk;
+  int splits;
+  int64_t k_per;
+};
+SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int num_sms);
 int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
                         cudaStream_t s, size_t* need_bytes);
 void set_last_error_text(const std::string& text);
 
-// Tensor-core variants (tcgen05).  kind: COMPAR_V_TC_TF32 / TC_BF16 / TC_FP8 / SPLIT3.
+// Tensor-core variants (tcgen05).  kind: COMPAR_V_TC_TF32 / TC_BF16 / TC_FP8 / SPLIT3 /
+// SPLIT6.
 int launch_tc(int variant, const GemmCall& c, Workspace& ws, const DeviceGuard& g,
               int num_sms, cudaStream_t s);
 bool tc_supported(int variant, const GemmCall& c);
@@ -104,8 +113,18 @@ int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
 int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_dequant,
                       cudaStream_t s);
 
-// out_kind values for prepass_convert
-enum PrepassOut { PP_F32 = 0, PP_BF16 = 1, PP_SPLIT_BF16 = 2, PP_E4M3 = 3, PP_COPY = 4 };
+// out_kind values for prepass_convert.  The split kinds write piece p of
+// element idx at Y + p * (Y_lo - Y) (pieces equally spaced, Y_lo = piece 1):
+//   PP_SPLIT_BF16    hi = bf16(x), lo = bf16(x - hi)
+//   PP_SPLIT_BF16_3P hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
+enum PrepassOut {
+  PP_F32 = 0,
+  PP_BF16 = 1,
+  PP_SPLIT_BF16 = 2,
+  PP_E4M3 = 3,
+  PP_COPY = 4,
+  PP_SPLIT_BF16_3P = 5
+};
 
 // TMA tensor-map encoding (tma.cpp).
 bool tma_available();

@@ -285,18 +285,8 @@ int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms
              cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const int tiles = tiles_m * tiles_n;
-  // Split K when the tiles alone cannot fill the GPU and K is long.
-  int splits = 1;
-  if (tiles < num_sms && K >= 1024) {
-    splits = std::min<int>((2 * num_sms + tiles - 1) / tiles, K / 256);
-    splits = std::max(1, std::min(splits, 32));
-  }
-  int k_per = K;
-  if (splits > 1) {
-    k_per = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    splits = (K + k_per - 1) / k_per;
-  }
+  const SimtPlan plan = simt_plan(c.m, c.n, c.k, num_sms);
+  const int splits = plan.splits, k_per = static_cast<int>(plan.k_per);
   float* partial = nullptr;
   if (splits > 1) {
     const size_t need = static_cast<size_t>(splits) * M * N * sizeof(float);
@@ -352,12 +342,38 @@ int run_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
 template <typename T>
 int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                   cudaStream_t s) {
-  // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
-  if (c.m <= 48) return run_simt<T, 32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
+  if (simt_plan(c.m, c.n, c.k, num_sms).bm == 32)
+    return run_simt<T, 32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
   return run_simt<T, 128, 128, 16, 8, 8>(c, ws, g, num_sms, s);
 }
 
 }  // namespace
+
+SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int num_sms) {
+  SimtPlan p;
+  // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
+  if (m <= 48) {
+    p.bm = 32;
+    p.bk = 32;
+  } else {
+    p.bm = 128;
+    p.bk = 16;
+  }
+  p.bn = 128;
+  p.splits = 1;
+  p.k_per = k;
+  // Split K when the tiles alone cannot fill the GPU and K is long.
+  const int64_t tiles = ((m + p.bm - 1) / p.bm) * ((n + p.bn - 1) / p.bn);
+  if (tiles < num_sms && k >= 1024) {
+    int64_t sp = std::min<int64_t>((2 * static_cast<int64_t>(num_sms) + tiles - 1) / tiles, k / 256);
+    sp = std::max<int64_t>(1, std::min<int64_t>(sp, 32));
+    if (sp > 1) {
+      p.k_per = ((k + sp - 1) / sp + p.bk - 1) / p.bk * p.bk;
+      p.splits = static_cast<int>((k + p.k_per - 1) / p.k_per);
+    }
+  }
+  return p;
+}
 
 int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
   switch (c.dtype) {
@@ -396,17 +412,8 @@ int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, in
                      cudaStream_t s, size_t* need_bytes) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const int tiles = tiles_m * tiles_n;
-  int splits = 1;
-  if (tiles < num_sms && K >= 1024) {
-    splits = std::min<int>((2 * num_sms + tiles - 1) / tiles, K / 256);
-    splits = std::max(1, std::min(splits, 32));
-  }
-  int k_per = K;
-  if (splits > 1) {
-    k_per = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    splits = (K + k_per - 1) / k_per;
-  }
+  const SimtPlan plan = simt_plan(c.m, c.n, c.k, num_sms);
+  const int splits = plan.splits, k_per = static_cast<int>(plan.k_per);
   const size_t need = splits > 1 ? static_cast<size_t>(splits) * M * N * sizeof(float) : 0;
   if (need_bytes) *need_bytes = need;
   if (need > scratch_bytes) return COMPAR_ERR_INVALID;
@@ -441,7 +448,7 @@ int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, in
 
 int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
                         cudaStream_t s, size_t* need_bytes) {
-  if (c.m <= 48)
+  if (simt_plan(c.m, c.n, c.k, num_sms).bm == 32)
     return run_simt_scratch<32, 128, 32, 4, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
   return run_simt_scratch<128, 128, 16, 8, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
 }

@@ -8,6 +8,10 @@
 //   FP8    : kind::f8f6f4 with E4M3 operands, per-tensor dequantisation
 //   SPLIT3 : 3xBF16 — A = Ahi + Alo, B = Bhi + Blo (bf16 pieces) and
 //            Ahi*Bhi + Ahi*Blo + Alo*Bhi accumulated into one FP32 TMEM tile
+//   SPLIT6 : 3-piece split A = Ah + Am + Al (likewise B) and the six products
+//            whose size is at least 2^-16 of Ah*Bh: Ah*Bm, Am*Bh, Ah*Bl,
+//            Am*Bm, Al*Bh first, Ah*Bh last, promoted into FP32 registers
+//            after every stage
 //
 // CTA roles (one CTA per SM, grid = min(tiles, SMs)):
 //   warp 0      TMA producer: one elected lane streams K-major A and B tiles
@@ -64,6 +68,15 @@ template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
+};
+// 6-product split: three pieces per operand make 72 KB stages (three of
+// them).  Each stage is its own promoted chunk: within it the five small
+// products are summed first, so the tensor core's truncating accumulator
+// adds the leading product once per K step onto a partial 2^-8 its size.
+template <>
+struct Traits<COMPAR_V_SPLIT6> {
+  static constexpr Kind kind = Kind::F16;
+  static constexpr int elem = 2, fmt = 1, pieces = 3, BN = 256, row = 64, chunk_kb = 1, epi = 8;
 };
 
 template <int V>
@@ -126,7 +139,9 @@ template <int V>
 __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2,
-                   const __grid_constant__ CUtensorMap tmB2, const TcArgs p) {
+                   const __grid_constant__ CUtensorMap tmB2,
+                   const __grid_constant__ CUtensorMap tmA3,
+                   const __grid_constant__ CUtensorMap tmB3, const TcArgs p) {
   using T = Traits<V>;
   using L = Layout<V>;
   constexpr int P = T::pieces;
@@ -166,9 +181,13 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
   if (warp == 0 && lane == 0) {
     dev::tma_prefetch_desc(&tmA);
     dev::tma_prefetch_desc(&tmB);
-    if constexpr (P == 2) {
+    if constexpr (P >= 2) {
       dev::tma_prefetch_desc(&tmA2);
       dev::tma_prefetch_desc(&tmB2);
+    }
+    if constexpr (P == 3) {
+      dev::tma_prefetch_desc(&tmA3);
+      dev::tma_prefetch_desc(&tmB3);
     }
   }
   if (warp == 1) {
@@ -202,9 +221,13 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
         dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
         dev::tma_load_2d(b_dst, &tmB, &full[stage], x, nb * BN);
-        if constexpr (P == 2) {
+        if constexpr (P >= 2) {
           dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
           dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
+        }
+        if constexpr (P == 3) {
+          dev::tma_load_2d(a_dst + 2 * L::kABytes, &tmA3, &full[stage], x, mb * kBM);
+          dev::tma_load_2d(b_dst + 2 * L::kBBytes, &tmB3, &full[stage], x, nb * BN);
         }
         issued |= 1u << stage;
         issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
@@ -247,8 +270,30 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
           const uint64_t da = dev::smem_desc_kmajor<T::row>(a0);
           const uint64_t db = dev::smem_desc_kmajor<T::row>(b0);
+          if constexpr (P == 3) {
+            const uint64_t da1 = dev::smem_desc_kmajor<T::row>(a0 + L::kABytes);
+            const uint64_t db1 = dev::smem_desc_kmajor<T::row>(b0 + L::kBBytes);
+            const uint64_t da2 = dev::smem_desc_kmajor<T::row>(a0 + 2 * L::kABytes);
+            const uint64_t db2 = dev::smem_desc_kmajor<T::row>(b0 + 2 * L::kBBytes);
+            // small products of every K step of the stage, then the leading ones
 #pragma unroll
-          for (int kk = 0; kk < T::row / 32; ++kk) {
+            for (int kk = 0; kk < T::row / 32; ++kk) {
+              const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
+              const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
+              dev::mma<T::kind>(d_tmem, da + koff, db1 + koff, idesc, first);
+              dev::mma<T::kind>(d_tmem, da1 + koff, db + koff, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, da + koff, db2 + koff, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, da1 + koff, db1 + koff, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, da2 + koff, db + koff, idesc, 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < T::row / 32; ++kk) {
+              const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
+              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, 1u);
+            }
+          }
+#pragma unroll
+          for (int kk = 0; P < 3 && kk < T::row / 32; ++kk) {
             // each instruction consumes 32 bytes of K; advance the start address
             const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
@@ -439,8 +484,8 @@ CUtensorMapDataType map_type(int v) {
 
 template <int V>
 int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
-           const void* A2, const void* B2, const float* dq_a, const float* dq_b,
-           const DeviceGuard& g, int num_sms, cudaStream_t s) {
+           const void* A2, const void* B2, const void* A3, const void* B3, const float* dq_a,
+           const float* dq_b, const DeviceGuard& g, int num_sms, cudaStream_t s) {
   using L = Layout<V>;
   using T = Traits<V>;
   static std::once_flag attr_once;
@@ -453,21 +498,26 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
     set_last_cuda_error(attr_err, "cudaFuncSetAttribute(tc)", __FILE__, __LINE__);
     return COMPAR_ERR_CUDA;
   }
-  CUtensorMap ta, tb, ta2, tb2;
+  CUtensorMap ta, tb, ta2, tb2, ta3, tb3;
   const CUtensorMapDataType dt = map_type(V);
   const uint32_t box_k = static_cast<uint32_t>(L::kElemsPerStage);
   int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
   if (rc == COMPAR_OK)
     rc = tma_encode_2d(&tb, dt, T::elem, B, c.k, c.n, ldb, box_k, T::BN, T::row);
   if (rc != COMPAR_OK) return rc;
-  if (T::pieces == 2) {
+  ta2 = ta3 = ta;
+  tb2 = tb3 = tb;
+  if (T::pieces >= 2) {
     rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM, T::row);
     if (rc == COMPAR_OK)
       rc = tma_encode_2d(&tb2, dt, T::elem, B2, c.k, c.n, ldb, box_k, T::BN, T::row);
     if (rc != COMPAR_OK) return rc;
-  } else {
-    ta2 = ta;
-    tb2 = tb;
+  }
+  if (T::pieces == 3) {
+    rc = tma_encode_2d(&ta3, dt, T::elem, A3, c.k, c.m, lda, box_k, kBM, T::row);
+    if (rc == COMPAR_OK)
+      rc = tma_encode_2d(&tb3, dt, T::elem, B3, c.k, c.n, ldb, box_k, T::BN, T::row);
+    if (rc != COMPAR_OK) return rc;
   }
   TcArgs a{};
   a.M = static_cast<int>(c.m);
@@ -487,7 +537,7 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   const int tiles = a.tiles_m * a.tiles_n;
   const int grid = std::min(tiles, num_sms);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
-  tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, a);
+  tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, ta3, tb3, a);
   COMPAR_CUDA_TRY(cudaGetLastError());
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();
@@ -508,7 +558,8 @@ bool tc_supported(int v, const GemmCall& c) {
     case COMPAR_V_TC_TF32: return c.dtype == COMPAR_F32;
     case COMPAR_V_TC_BF16: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_BF16;
     case COMPAR_V_TC_FP8: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_F8E4M3;
-    case COMPAR_V_SPLIT3: return c.dtype == COMPAR_F32;
+    case COMPAR_V_SPLIT3:
+    case COMPAR_V_SPLIT6: return c.dtype == COMPAR_F32;
     default: return false;
   }
 }
@@ -520,7 +571,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   if (!tc_supported(v, c)) return COMPAR_ERR_UNSUPPORTED;
   if (!tma_available()) return COMPAR_ERR_UNSUPPORTED;
   const int elem = (v == COMPAR_V_TC_TF32) ? 4 : (v == COMPAR_V_TC_FP8 ? 1 : 2);
-  const int pieces = (v == COMPAR_V_SPLIT3) ? 2 : 1;
+  const int pieces = (v == COMPAR_V_SPLIT3) ? 2 : (v == COMPAR_V_SPLIT6 ? 3 : 1);
   const int64_t ldk = round_up(c.k, 16);  // 16-element pitch: 16-byte rows for every type
   const bool a_native = (c.dtype != COMPAR_F32 || v == COMPAR_V_TC_TF32);
   const bool a_in_place = a_native && tma_operand_ok(c.A, c.lda, elem);
@@ -544,7 +595,8 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     case COMPAR_V_TC_TF32: out_kind = PP_COPY; break;
     case COMPAR_V_TC_BF16: out_kind = (c.dtype == COMPAR_F32) ? PP_BF16 : PP_COPY; break;
     case COMPAR_V_TC_FP8: out_kind = fp8_from_f32 ? PP_E4M3 : PP_COPY; break;
-    default: out_kind = PP_SPLIT_BF16; break;
+    case COMPAR_V_SPLIT3: out_kind = PP_SPLIT_BF16; break;
+    default: out_kind = PP_SPLIT_BF16_3P; break;
   }
   const float* sa = nullptr;
   const float* sb = nullptr;
@@ -564,31 +616,37 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   }
   // B: K x N row-major -> N x K (K-major)
   rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldk, true,
-                       pieces == 2 ? wb + b_bytes : nullptr, sb, s);
+                       pieces >= 2 ? wb + b_bytes : nullptr, sb, s);
   if (rc != COMPAR_OK) return rc;
   const void* A = c.A;
   int64_t lda = c.lda;
   if (!a_in_place) {
     rc = prepass_convert(c.A, c.dtype, c.m, c.k, c.lda, wa, out_kind, ldk, false,
-                         pieces == 2 ? wa + a_bytes : nullptr, sa, s);
+                         pieces >= 2 ? wa + a_bytes : nullptr, sa, s);
     if (rc != COMPAR_OK) return rc;
     A = wa;
     lda = ldk;
   }
-  const void* A2 = pieces == 2 ? static_cast<const void*>(wa + a_bytes) : nullptr;
-  const void* B2 = pieces == 2 ? static_cast<const void*>(wb + b_bytes) : nullptr;
+  const void* A2 = pieces >= 2 ? static_cast<const void*>(wa + a_bytes) : nullptr;
+  const void* B2 = pieces >= 2 ? static_cast<const void*>(wb + b_bytes) : nullptr;
+  const void* A3 = pieces == 3 ? static_cast<const void*>(wa + 2 * a_bytes) : nullptr;
+  const void* B3 = pieces == 3 ? static_cast<const void*>(wb + 2 * b_bytes) : nullptr;
   switch (v) {
     case COMPAR_V_TC_TF32:
-      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, g,
-                                      num_sms, s);
+      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, nullptr, g, num_sms, s);
     case COMPAR_V_TC_BF16:
-      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, g,
-                                      num_sms, s);
+      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, nullptr, g, num_sms, s);
     case COMPAR_V_TC_FP8:
-      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, wb, ldk, nullptr, nullptr, dqa, dqb, g, num_sms,
-                                     s);
+      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, dqa,
+                                     dqb, g, num_sms, s);
+    case COMPAR_V_SPLIT3:
+      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, wb, ldk, A2, B2, nullptr, nullptr, nullptr,
+                                     nullptr, g, num_sms, s);
     default:
-      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, wb, ldk, A2, B2, nullptr, nullptr, g, num_sms, s);
+      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, wb, ldk, A2, B2, A3, B3, nullptr, nullptr, g,
+                                     num_sms, s);
   }
 }
 

@@ -25,7 +25,8 @@ struct GroupProblem {
 
 // One operand re-layout of the grouped pre-pass: converts `rows x cols` of
 // `src` (row pitch ld_src) into dst (and dst_lo for the split), transposing
-// when asked; owns 32x32 tiles [tile_start, tile_start + tiles).
+// when asked; owns 64x64 tiles [tile_start, tile_start + tiles) of the
+// batch's tile list.
 struct PrepassJob {
   const void* src;
   void* dst;
@@ -38,6 +39,7 @@ struct PrepassJob {
   int tile_start;
   int tiles_c;    // tiles along cols
   int tiles;
+  int vec;        // src rows 16-byte aligned (f32) / 8-byte (bf16): 4-wide loads
 };
 
 int grouped_smem_bytes(int bn);

@@ -1,5 +1,5 @@
-// Learned cost model kernels: a 3-layer perceptron (8 -> 64 -> 64 -> 12,
-// ReLU) that predicts, for each of the 6 variants, log2 of the run time and
+// Learned cost model kernels: a 3-layer perceptron (8 -> 64 -> 64 -> 14,
+// ReLU) that predicts, for each of the 7 variants, log2 of the run time and
 // log10 of the relative error of a call from the call's context.  The paper's
 // runtime selects variants with performance models it calls machine-learning
 // models and expects more training to select better (Sec. 3.2, Sec. 5).
@@ -13,7 +13,7 @@
 //                        gradients instead of updating (used for gradient checks).
 //
 // Parameter layout per member (floats): W1[64][8] b1[64] W2[64][64] b2[64]
-// W3[12][64] b3[12] — weights stored (out, in), row-major.
+// W3[14][64] b3[14] — weights stored (out, in), row-major.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,7 +23,7 @@
 namespace compar {
 namespace {
 
-constexpr int kIn = 8, kH = 64, kOut = 12;
+constexpr int kIn = 8, kH = 64, kOut = 2 * COMPAR_V_COUNT;
 constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
               oW3 = ob2 + kH, ob3 = oW3 + kOut * kH, kP = ob3 + kOut;
 constexpr int kB = 128;       // rows per training step (one per thread)

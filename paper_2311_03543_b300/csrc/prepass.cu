@@ -3,6 +3,8 @@
 //
 //  * f32 -> bf16 (round to nearest even)                 (BF16 variant on f32 inputs)
 //  * f32 -> (hi, lo) bf16 pair, hi = bf16(x), lo = bf16(x - hi)   (3xBF16 split)
+//  * f32 -> (hi, mid, lo) bf16 triple, mid = bf16(x - hi),
+//           lo = bf16(x - hi - mid)                         (6-product split)
 //  * f32 -> E4M3 codes of x * s, s = 448 / amax(|x|), saturating   (FP8 variant)
 //  * plain copy / transpose of f32, bf16 or fp8 elements
 //
@@ -20,6 +22,22 @@
 
 namespace compar {
 namespace {
+
+// Three-piece split; both residuals are exact in float32.
+__device__ __forceinline__ void split3p(float x, __nv_bfloat16& h, __nv_bfloat16& m,
+                                        __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Piece 2 of a split output: pieces are equally spaced, Y_lo = piece 1.
+__device__ __forceinline__ __nv_bfloat16* piece2(void* Y, void* Ylo) {
+  __nv_bfloat16* y = static_cast<__nv_bfloat16*>(Y);
+  __nv_bfloat16* y1 = static_cast<__nv_bfloat16*>(Ylo);
+  return y1 + (y1 - y);
+}
 
 // One element conversion for the float32-input kinds.
 struct F32Out {
@@ -41,6 +59,14 @@ __device__ __forceinline__ void store_converted(const F32Out& o, float x, void* 
       const float r = x - __bfloat162float(hi);
       static_cast<__nv_bfloat16*>(Y)[idx] = hi;
       static_cast<__nv_bfloat16*>(Ylo)[idx] = __float2bfloat16_rn(r);
+      break;
+    }
+    case PP_SPLIT_BF16_3P: {
+      __nv_bfloat16 h, m, l;
+      split3p(x, h, m, l);
+      static_cast<__nv_bfloat16*>(Y)[idx] = h;
+      static_cast<__nv_bfloat16*>(Ylo)[idx] = m;
+      piece2(Y, Ylo)[idx] = l;
       break;
     }
     case PP_E4M3: {
@@ -95,6 +121,22 @@ __device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], v
     float4* y = reinterpret_cast<float4*>(static_cast<float*>(Y) + idx);
     y[0] = make_float4(x[0], x[1], x[2], x[3]);
     y[1] = make_float4(x[4], x[5], x[6], x[7]);
+  } else if (kind == PP_SPLIT_BF16_3P) {
+    uint32_t w[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+      split3p(x[2 * q], h0, m0, l0);
+      split3p(x[2 * q + 1], h1, m1, l1);
+      w[0][q] = __bfloat16_as_ushort(h0) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+      w[1][q] = __bfloat16_as_ushort(m0) | (static_cast<uint32_t>(__bfloat16_as_ushort(m1)) << 16);
+      w[2][q] = __bfloat16_as_ushort(l0) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+    }
+    __nv_bfloat16* dst[3] = {static_cast<__nv_bfloat16*>(Y), static_cast<__nv_bfloat16*>(Ylo),
+                             piece2(Y, Ylo)};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+      *reinterpret_cast<uint4*>(dst[p] + idx) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
   } else if (kind == PP_BF16 || kind == PP_SPLIT_BF16) {
     uint32_t hi[4], lo[4];
 #pragma unroll
@@ -181,6 +223,15 @@ __global__ void convert_transpose64_kernel(const float* __restrict__ X, int64_t 
           *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Ylo) + idx) =
               __halves2bfloat162(__float2bfloat16_rn(x0 - __bfloat162float(h0)),
                                  __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+      } else if (kind == PP_SPLIT_BF16_3P) {
+        __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+        split3p(x0, h0, m0, l0);
+        split3p(x1, h1, m1, l1);
+        *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Y) + idx) =
+            __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Ylo) + idx) =
+            __halves2bfloat162(m0, m1);
+        *reinterpret_cast<__nv_bfloat162*>(piece2(Y, Ylo) + idx) = __halves2bfloat162(l0, l1);
       } else {
         uint8_t* y = static_cast<uint8_t*>(Y) + idx;
         y[0] = __nv_cvt_float_to_fp8(__fmul_rn(x0, s), __NV_SATFINITE, __NV_E4M3);
@@ -260,59 +311,194 @@ int grid_for(int64_t total) {
 
 // ------------------------------------------------------------------ grouped
 
-// Every operand re-layout of a batch in one launch.  Block row y works on
-// job y (its fields read once); its gridDim.x blocks stride over the job's
-// 64 x 64 tiles, 16 independent loads and stores per thread per tile.
-constexpr int kPrepassBlocksPerJob = 16;
+// Every operand re-layout of a batch in one launch.  The 64 x 64 tiles of
+// all jobs form one list (job j owns [tile_start, tile_start + tiles)); each
+// block converts one contiguous run of that list, so big and small jobs
+// spread evenly over the grid and a block changes job only at a boundary.
+//
+// Per tile the work is specialised on (input type, output kind, transpose):
+// no per-element switch, 4-wide global loads when the job's rows are 16-byte
+// aligned, and stores of two (transposed) or four (row-wise) consecutive
+// outputs per thread, so a warp writes whole 128-byte lines.
+
+// Output of 1, 2 or 4 consecutive elements of one piece row.
+template <int KIND>
+struct PieceOut;
+template <>
+struct PieceOut<PP_F32> {
+  static __device__ __forceinline__ void put2(void* Y, void*, int64_t i, float a, float b) {
+    *reinterpret_cast<float2*>(static_cast<float*>(Y) + i) = make_float2(a, b);
+  }
+  static __device__ __forceinline__ void put4(void* Y, void*, int64_t i, float4 v) {
+    *reinterpret_cast<float4*>(static_cast<float*>(Y) + i) = v;
+  }
+  static __device__ __forceinline__ void put1(void* Y, void*, int64_t i, float a) {
+    static_cast<float*>(Y)[i] = a;
+  }
+};
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(a))) |
+         (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(b))) << 16);
+}
+template <>
+struct PieceOut<PP_BF16> {
+  static __device__ __forceinline__ void put2(void* Y, void*, int64_t i, float a, float b) {
+    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(Y) + i) = pack_bf16(a, b);
+  }
+  static __device__ __forceinline__ void put4(void* Y, void*, int64_t i, float4 v) {
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(Y) + i) =
+        make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+  }
+  static __device__ __forceinline__ void put1(void* Y, void*, int64_t i, float a) {
+    static_cast<__nv_bfloat16*>(Y)[i] = __float2bfloat16_rn(a);
+  }
+};
+template <>
+struct PieceOut<PP_SPLIT_BF16> {
+  static __device__ __forceinline__ float lo(float x) {
+    return x - __bfloat162float(__float2bfloat16_rn(x));
+  }
+  static __device__ __forceinline__ void put2(void* Y, void* L, int64_t i, float a, float b) {
+    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(Y) + i) = pack_bf16(a, b);
+    *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(L) + i) = pack_bf16(lo(a), lo(b));
+  }
+  static __device__ __forceinline__ void put4(void* Y, void* L, int64_t i, float4 v) {
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(Y) + i) =
+        make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(L) + i) =
+        make_uint2(pack_bf16(lo(v.x), lo(v.y)), pack_bf16(lo(v.z), lo(v.w)));
+  }
+  static __device__ __forceinline__ void put1(void* Y, void* L, int64_t i, float a) {
+    static_cast<__nv_bfloat16*>(Y)[i] = __float2bfloat16_rn(a);
+    static_cast<__nv_bfloat16*>(L)[i] = __float2bfloat16_rn(lo(a));
+  }
+};
+
+// Four consecutive inputs as float (vector load when `vec`).
+template <typename In>
+__device__ __forceinline__ float4 load4(const In* p, bool vec, int n_valid);
+template <>
+__device__ __forceinline__ float4 load4<float>(const float* p, bool vec, int n_valid) {
+  if (vec && n_valid >= 4) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (n_valid > 0) v.x = __ldg(p);
+  if (n_valid > 1) v.y = __ldg(p + 1);
+  if (n_valid > 2) v.z = __ldg(p + 2);
+  if (n_valid > 3) v.w = __ldg(p + 3);
+  return v;
+}
+template <>
+__device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16* p, bool vec,
+                                                       int n_valid) {
+  if (vec && n_valid >= 4) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+  }
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (n_valid > 0) v.x = __bfloat162float(p[0]);
+  if (n_valid > 1) v.y = __bfloat162float(p[1]);
+  if (n_valid > 2) v.z = __bfloat162float(p[2]);
+  if (n_valid > 3) v.w = __bfloat162float(p[3]);
+  return v;
+}
+
+// Row-wise job: Y[r][c] = f(X[r][c]); thread = 4 consecutive columns.
+template <typename In, int KIND>
+__device__ __forceinline__ void tile_rows(const PrepassJob& J, int64_t r0, int64_t c0) {
+  const In* X = static_cast<const In*>(J.src);
+  const bool vec = J.vec != 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = threadIdx.x + 256 * q;  // 64 rows x 16 groups of 4
+    const int64_t r = r0 + (idx >> 4);
+    const int64_t c = c0 + 4 * (idx & 15);
+    if (r >= J.rows || c >= J.cols) continue;
+    const int64_t rem = J.cols - c;
+    const int n_valid = rem >= 4 ? 4 : static_cast<int>(rem);
+    const float4 v = load4<In>(X + r * J.ld_src + c, vec, n_valid);
+    const int64_t o = r * J.ld_dst + c;
+    if (n_valid == 4) {  // outputs rows have pitch ldk (a multiple of 16): aligned
+      PieceOut<KIND>::put4(J.dst, J.dst_lo, o, v);
+    } else {  // ragged right edge: 1 to 3 columns
+      PieceOut<KIND>::put1(J.dst, J.dst_lo, o, v.x);
+      if (n_valid > 1) PieceOut<KIND>::put1(J.dst, J.dst_lo, o + 1, v.y);
+      if (n_valid > 2) PieceOut<KIND>::put1(J.dst, J.dst_lo, o + 2, v.z);
+    }
+  }
+}
+
+// Transposing job: Y[c][r] = f(X[r][c]) through shared memory.  Loads: a
+// thread reads 4 consecutive columns of a row; stores: a warp writes 64
+// consecutive r of one output row, two per thread.
+template <typename In, int KIND>
+__device__ __forceinline__ void tile_transpose(const PrepassJob& J, int64_t r0, int64_t c0,
+                                               float (*tile)[65]) {
+  const In* X = static_cast<const In*>(J.src);
+  const bool vec = J.vec != 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    const int lr = idx >> 4, lc = 4 * (idx & 15);
+    const int64_t r = r0 + lr, c = c0 + lc;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < J.rows && c < J.cols) {
+      const int64_t rem = J.cols - c;
+      v = load4<In>(X + r * J.ld_src + c, vec, rem >= 4 ? 4 : static_cast<int>(rem));
+    }
+    tile[lr][lc] = v.x;
+    tile[lr][lc + 1] = v.y;
+    tile[lr][lc + 2] = v.z;
+    tile[lr][lc + 3] = v.w;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = 2 * lane;
+  const int64_t r = r0 + lr;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int lc = warp * 8 + i;  // output row c0 + lc
+    const int64_t c = c0 + lc;
+    if (c >= J.cols || r >= J.rows) continue;
+    const float a = tile[lr][lc], b = tile[lr + 1][lc];
+    const int64_t o = c * J.ld_dst + r;
+    if (r + 1 < J.rows) PieceOut<KIND>::put2(J.dst, J.dst_lo, o, a, b);
+    else PieceOut<KIND>::put1(J.dst, J.dst_lo, o, a);
+  }
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(256) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
-                                                              int njobs) {
+                                                              int njobs, int total_tiles) {
   __shared__ float tile[64][65];
-  const PrepassJob J = jobs[blockIdx.y];
-  const int tiles_c = (J.cols + 63) / 64;
-  const int tiles = ((J.rows + 63) / 64) * tiles_c;
-  // a bf16 copy goes through float and back, which is exact
-  const F32Out o{J.out_kind == PP_COPY ? (J.in_type == COMPAR_F32 ? PP_F32 : PP_BF16)
-                                       : J.out_kind,
-                 1.f};
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t r0 = static_cast<int64_t>(t / tiles_c) * 64;
-    const int64_t c0 = static_cast<int64_t>(t % tiles_c) * 64;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int li = ty + 8 * i, lj = tx + 32 * h;
-        const int64_t r = r0 + li, c = c0 + lj;
-        float v = 0.f;
-        if (r < J.rows && c < J.cols) {
-          if (J.in_type == COMPAR_F32)
-            v = __ldg(static_cast<const float*>(J.src) + r * J.ld_src + c);
-          else
-            v = __bfloat162float(static_cast<const __nv_bfloat16*>(J.src)[r * J.ld_src + c]);
-        }
-        tile[li][lj] = v;
-      }
+  const int per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const int t_begin = blockIdx.x * per;
+  const int t_end = min(total_tiles, t_begin + per);
+  if (t_begin >= t_end) return;
+  // the last job starting at or before t_begin (jobs are in tile order)
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&jobs[mid].tile_start) <= t_begin) lo = mid;
+    else hi = mid - 1;
+  }
+  int j = lo;
+  PrepassJob J = jobs[j];
+  for (int t = t_begin; t < t_end; ++t) {
+    while (t >= J.tile_start + J.tiles && j + 1 < njobs) J = jobs[++j];
+    const int lt = t - J.tile_start;
+    const int64_t r0 = static_cast<int64_t>(lt / J.tiles_c) * 64;
+    const int64_t c0 = static_cast<int64_t>(lt % J.tiles_c) * 64;
+    const bool f32 = J.in_type == COMPAR_F32;
+    if (J.transpose) {
+      if (!f32) tile_transpose<__nv_bfloat16, PP_BF16>(J, r0, c0, tile);
+      else if (J.out_kind == PP_SPLIT_BF16) tile_transpose<float, PP_SPLIT_BF16>(J, r0, c0, tile);
+      else tile_transpose<float, PP_F32>(J, r0, c0, tile);
+    } else {
+      if (!f32) tile_rows<__nv_bfloat16, PP_BF16>(J, r0, c0);
+      else if (J.out_kind == PP_SPLIT_BF16) tile_rows<float, PP_SPLIT_BF16>(J, r0, c0);
+      else tile_rows<float, PP_F32>(J, r0, c0);
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int li = ty + 8 * i, lj = tx + 32 * h;
-        if (J.transpose) {  // output row c0 + li holds input column c0 + li
-          const int64_t c = c0 + li, r = r0 + lj;
-          if (c < J.cols && r < J.rows)
-            store_converted(o, tile[lj][li], J.dst, J.dst_lo, c * J.ld_dst + r);
-        } else {
-          const int64_t r = r0 + li, c = c0 + lj;
-          if (r < J.rows && c < J.cols)
-            store_converted(o, tile[li][lj], J.dst, J.dst_lo, r * J.ld_dst + c);
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -320,10 +506,16 @@ __global__ void __launch_bounds__(256) grouped_prepass_kernel(const PrepassJob* 
 
 int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles, int num_sms,
                            cudaStream_t s) {
-  (void)num_sms;
   if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
-  if (njobs > 65535) return COMPAR_ERR_INVALID;
-  grouped_prepass_kernel<<<dim3(kPrepassBlocksPerJob, njobs), dim3(32, 8), 0, s>>>(d_jobs, njobs);
+  // one full wave of resident blocks
+  static int resident = 0;
+  if (resident == 0) {
+    int r = 0;
+    COMPAR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, grouped_prepass_kernel, 256, 0));
+    resident = std::max(r, 1);
+  }
+  const int grid = static_cast<int>(std::min<int64_t>(total_tiles, static_cast<int64_t>(num_sms) * resident));
+  grouped_prepass_kernel<<<grid, 256, 0, s>>>(d_jobs, njobs, total_tiles);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;

@@ -48,7 +48,8 @@ ErrorModel::ErrorModel() {
   // FP64 oracle for uniform[-1,1] and normal(0,1) inputs, k = 64 .. 16384:
   // naive FMA chain ~0.3 sqrt(k) u; SIMT below that; unpromoted tensor-core
   // accumulation ~0.018 k u; TF32 / BF16 / FP8 operand rounding of float32
-  // inputs ~7-8e-4 / 2.4e-3 / 3.8e-2; promoted 3xBF16 flat at ~4.6e-6.
+  // inputs ~7-8e-4 / 2.4e-3 / 3.8e-2; promoted 3xBF16 flat at ~4.6e-6;
+  // the 6-product split below SIMT's level.
   for (int v : {COMPAR_V_TC_TF32, COMPAR_V_TC_BF16, COMPAR_V_TC_FP8}) c2[v].fill(0.025f);
   for (int d = 0; d < 3; ++d) {
     c0[COMPAR_V_NAIVE][d] = 0.f;  c1[COMPAR_V_NAIVE][d] = 0.4f;
@@ -61,6 +62,12 @@ ErrorModel::ErrorModel() {
   c0[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 0.f;
   c0[COMPAR_V_SPLIT3][COMPAR_F32] = 5e-6f;
   c1[COMPAR_V_SPLIT3][COMPAR_F32] = 0.05f;
+  // 6-product split: the pieces hold all 24 bits, the dropped terms are
+  // ~2^-26 relative; what remains is FP32 accumulation of the promoted
+  // per-stage partials (SIMT-like) and the tensor core's truncating adds.
+  // Measured 6.2e-8 (k = 64) .. 4.1e-7 (k = 16384), ill-scaled columns alike.
+  c0[COMPAR_V_SPLIT6][COMPAR_F32] = 6e-8f;
+  c1[COMPAR_V_SPLIT6][COMPAR_F32] = 0.07f;
 }
 
 double ErrorModel::predict(int v, int dtype, int64_t k) const {
@@ -176,6 +183,12 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
       flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
       bytes += (M * K + K * N) * 8;
       ovh_us = 14;
+      break;
+    case COMPAR_V_SPLIT6:
+      peak = 1.5e15 / 6;
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += (M * K + K * N) * 10;
+      ovh_us = 16;
       break;
     default:
       return INFINITY;

@@ -253,12 +253,15 @@ static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t
   std::vector<std::array<float, kNumFeatures>> feats;
   std::vector<std::array<float, kOutputs>> tgt, msk;
   uint64_t st = seed ^ 0x5EEDull;
-  const double tols[3] = {1e-5, 1e-3, 1e-1};
+  // The records' own tolerance is not a property of the timing or the
+  // error; each row gets a tolerance class drawn from the ones callers use,
+  // so that the tolerance feature's training box spans them.
+  const double tols[4] = {1e-6, 1e-5, 1e-3, 1e-1};
   for (const auto& r : recs) {
     if (r.variant < 0 || r.variant >= kNumVariants) continue;
     const bool has_t = r.time_ms > 0, has_e = r.rel_err > 0;
     if (!has_t && !has_e) continue;
-    const double tol = tols[splitmix(st) % 3];
+    const double tol = tols[splitmix(st) % 4];
     feats.push_back(make_features(r.m, r.n, r.k, r.dtype, tol, std::max(1, r.batch)));
     std::array<float, kOutputs> t{}, m{};
     if (has_t) {

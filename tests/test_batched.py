@@ -3,7 +3,8 @@ the per-GEMM loop, against the FP64 oracle problem by problem.
 
 Modes: float32 problems at tol 1e-5 run as 3xBF16 (<= 1e-5 vs the oracle);
 at a loose tolerance as TF32 (<= 2e-3); bf16 problems exactly on their bf16
-values (<= 1e-5); E4M3 problems leave the grouped launch and run one by one."""
+values (<= 1e-5); E4M3 problems, and float32 problems at a tolerance below
+3xBF16's error level, leave the grouped launch and run one by one."""
 import numpy as np
 import pytest
 
@@ -109,6 +110,22 @@ def test_grouped_tf32_mode(ctx):
     finally:
         ctx.force_variant(None)
     _check(specs, host, 2e-3)
+
+
+def test_tolerance_below_3xbf16_runs_those_problems_singly(ctx):
+    """At tol 2e-6 the grouped kernel's float32 mode (3xBF16, ~4e-6) does not
+    qualify: float32 problems are selected one by one (6-product split or
+    FP32 SIMT) and still meet the tolerance; bf16 problems stay grouped."""
+    import paper_2311_03543_b300 as cp
+    specs = _random_specs(16, seed=6)
+    probs, host = _make_batch(specs, 600)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=2e-6)
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
+    _check(specs, host, 2e-6)
 
 
 def test_fp8_and_empty_problems_in_a_batch(ctx):

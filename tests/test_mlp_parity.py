@@ -9,11 +9,12 @@ largest gradient of each tensor (sums over a 128-row batch)."""
 import numpy as np
 import pytest
 
+import paper_2311_03543_b300 as cp
 from oracle import mlp_ref as M
 
 pytestmark = pytest.mark.gpu
 
-IN, H, OUT = 8, 64, 12
+IN, H, OUT = 8, 64, 2 * cp.NUM_VARIANTS
 
 
 @pytest.fixture(scope="module")
@@ -130,7 +131,18 @@ def test_training_reduces_loss(ctx):
 
 
 def test_invalid_batch_index_is_refused(ctx):
+    import ctypes
     import paper_2311_03543_b300 as cp
     p, X, T, mask = _problem(11, rows=10)
-    with pytest.raises(cp.ComparError):
-        ctx.mlp_train_steps(_flat(p)[None], X, T, mask, np.array([[[0, 10]]]), grads_only=True)
+    params = _flat(p)[None].copy()
+    with pytest.raises(ValueError):       # the binding checks before the call
+        ctx.mlp_train_steps(params, X, T, mask, np.array([[[0, 10]]]), grads_only=True)
+    # and the C ABI refuses the out-of-range row by itself
+    f = lambda a: np.ascontiguousarray(a, np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    idx = np.array([[[0, 10]]], np.int32)
+    g, loss = np.zeros_like(params), np.zeros((1, 1), np.float32)
+    Xc, Tc, Mc = (np.ascontiguousarray(a, np.float32) for a in (X, T, mask))
+    rc = cp.compar_mlp_train_steps(ctx.handle, f(params), None, None, 1, f(Xc), f(Tc), f(Mc), 10,
+                                   idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 1, 2,
+                                   1e-3, 1, f(g), f(loss))
+    assert rc == cp.ERR_INVALID

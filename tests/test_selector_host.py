@@ -30,11 +30,23 @@ def test_compute_calls_are_refused_without_a_device(hctx):
 
 def test_eligibility_by_tolerance(hctx):
     # FP32 inputs at 1e-5: only FP32-accurate variants (naive, simt, 3xbf16)
-    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3)
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3,
+                                                            cp.V_SPLIT6)
     # at 1e-1 the fp8 variant is the fastest by the roofline prior for big shapes
     assert hctx.select(8192, 8192, 8192, cp.F32, 1e-1) == cp.V_TC_FP8
     # BF16 inputs can never run the f32-only variants
     assert hctx.select(2048, 2048, 2048, cp.BF16, 1e-3) in (cp.V_NAIVE, cp.V_SIMT, cp.V_TC_BF16)
+
+
+def test_tolerance_below_3xbf16(hctx):
+    # tol 1e-6 on float32: 3xBF16 (~4e-6) no longer qualifies; a big square
+    # goes to the 6-product split, the only tensor-core variant left
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-6) == cp.V_SPLIT6
+    # SIMT's error follows its longest FMA chain: a 32 x 32 x 4096 product is
+    # split 16 ways along K (256-term chains), so SIMT qualifies there, while
+    # the naive variant's 4096-term chain does not
+    assert hctx.predict_error(cp.V_NAIVE, cp.F32, 4096) * 1.25 > 1e-6
+    assert hctx.select(32, 32, 4096, cp.F32, 1e-6) in (cp.V_SIMT, cp.V_SPLIT6)
 
 
 def test_no_variant_meets_impossible_tolerance(hctx):
@@ -146,7 +158,7 @@ def test_online_exploration_stays_within_eligible_variants(hctx):
     seen = set()
     for _ in range(200):
         v = hctx.select(2048, 2048, 2048, cp.F32, 1e-5)
-        assert v in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3)
+        assert v in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3, cp.V_SPLIT6)
         seen.add(v)
     assert len(seen) >= 2
     explored, retrains = hctx.online_stats()

@@ -20,7 +20,8 @@ Workloads (M, N, K):
   ln 2048))) (seed 5), dtype f32 or bf16 with probability 1/2.
 * ``heldout_contexts()``: selector test contexts, M, N, K log-uniform
   integers in [16, 4096], dtype uniform over {f32, bf16, fp8}, tolerance from
-  {1e-5 (f32 only), 1e-3, 1e-1} (seed 12345).
+  {1e-5 (f32 only), 1e-3, 1e-1} (seed 12345); ``heldout_tight_contexts()``:
+  float32 only at tolerance 1e-6, same shape law (seed 24680).
 """
 import math
 
@@ -124,6 +125,14 @@ def heldout_contexts(count=2000, seed=12345, lo=16, hi=4096):
             tol = [1e-3, 1e-1][int(g.integers(0, 2))]
         out.append((int(m), int(n), int(k), int(d), float(tol)))
     return out
+
+
+def heldout_tight_contexts(count=300, seed=24680, lo=16, hi=4096):
+    """Float32 contexts at tolerance 1e-6 (below 3xBF16's error level),
+    held out from selector training: (m, n, k, dtype, tol)."""
+    g = rng(seed)
+    mnk = _log_uniform_int(g, lo, hi, (count, 3))
+    return [(int(m), int(n), int(k), F32, 1e-6) for (m, n, k) in mnk]
 
 
 def training_contexts(count, seed=777, lo=16, hi=8192):
