@@ -33,8 +33,10 @@ using dev::Kind;
 
 constexpr int kBM = 128;
 constexpr int kRow = 128;  // bytes of K per stage
-constexpr int kThreads = 192;
-constexpr int kEpi = 128;
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each half the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpi = 32 * kEpiWarps;
+constexpr int kStgPitch = 36;  // staging row pitch (floats): 16-byte rows, no bank conflicts
 constexpr int kChunkKB = 4;  // promotion every 4 stages
 constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
 
@@ -44,7 +46,7 @@ struct GLayout {
   static constexpr int kB = BN * kRow;        // one B piece
   static constexpr int kStage = 2 * (kA + kB);
   static constexpr int kBar = 256;
-  static constexpr int kStaging = 4 * 32 * 33 * 4;  // one 32 x 32 (+pad) block per epilogue warp
+  static constexpr int kStaging = kEpiWarps * 32 * kStgPitch * 4;  // a 32 x 32 block per warp
   static constexpr int kIndex = kMaxIndexed * 4;    // problems' tile_start values
   static constexpr int kStagesRaw = (232448 - 1024 - kBar - kStaging - kIndex) / kStage;
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
@@ -231,9 +233,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     drain(drainb, 0, budget_ns);
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
+    // Warp w reads TMEM lane quarter w % 4 (the hardware's access rule) and
+    // one half of the columns.
+    constexpr int EC = BN / 2;
     const int quarter = warp & 3;
+    const int cslice = (warp - 2) / 4;
     int acc_iter = 0;
     bool ok = true;
+    float* stg = staging + (warp - 2) * 32 * kStgPitch;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
       const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
       const int local = tile - P.tile_start;
@@ -242,9 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       float* const pC = P.C;
       const int64_t ldc = P.ldc;
       const float alpha = P.alpha, beta = P.beta;
-      float sum[BN];
+      float sum[EC];
 #pragma unroll
-      for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+      for (int j = 0; j < EC; ++j) sum[j] = 0.f;
       const int chunks = (num_kb + kChunkKB - 1) / kChunkKB;
       for (int ch = 0; ch < chunks; ++ch, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
@@ -253,9 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         dev::tc_fence_after();
-        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN;
+        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                               acc * BN + cslice * EC;
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = 0; c < EC / 32; ++c) {
           uint32_t r[32];
           dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
           dev::tmem_ld_wait();
@@ -266,24 +274,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         dev::mbar_arrive(&tempty[acc]);
       }
       if (!ok) break;
-      // Coalesced stores: each 32 x 32 block goes through shared memory so
-      // that lane j then writes column j of one row per instruction (one
-      // 128-byte segment) instead of 32 rows at once.
-      float (*stg)[33] = reinterpret_cast<float (*)[33]>(staging + (warp - 2) * 32 * 33);
+      // Each 32 x 32 block goes through shared memory (lane = row there) so
+      // that a warp then stores four 128-byte row segments per instruction.
+      // Blocks wholly outside the problem are skipped.
       const int row0 = mb * kBM + quarter * 32;
+      if (row0 >= pM) continue;
+      const bool vec = (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(pC) & 15) == 0);
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < EC / 32; ++c) {
+        const int col0 = nb * BN + cslice * EC + c * 32;
+        if (col0 >= pN) break;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) stg[lane][j] = sum[c * 32 + j];
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(stg + lane * kStgPitch + 4 * q) =
+              make_float4(sum[c * 32 + 4 * q], sum[c * 32 + 4 * q + 1], sum[c * 32 + 4 * q + 2],
+                          sum[c * 32 + 4 * q + 3]);
         __syncwarp();
-        const int col = nb * BN + c * 32 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int r = row0 + rr;
+        const int sub = lane >> 3;           // row within a group of four
+        const int cc = 4 * (lane & 7);       // column offset in the block
+        const int col = col0 + cc;
+#pragma unroll 2
+        for (int rr = 0; rr < 32; rr += 4) {
+          const int r = row0 + rr + sub;
           if (r < pM && col < pN) {
+            const float4 a = *reinterpret_cast<const float4*>(stg + (rr + sub) * kStgPitch + cc);
             float* dst = pC + static_cast<int64_t>(r) * ldc + col;
-            float v = alpha * stg[rr][lane];
-            if (beta != 0.f) v = fmaf(beta, *dst, v);
-            *dst = v;
+            if (vec && col + 3 < pN) {
+              float4 o = make_float4(alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w);
+              if (beta != 0.f) {
+                const float4 old = *reinterpret_cast<const float4*>(dst);
+                o.x = fmaf(beta, old.x, o.x);
+                o.y = fmaf(beta, old.y, o.y);
+                o.z = fmaf(beta, old.z, o.z);
+                o.w = fmaf(beta, old.w, o.w);
+              }
+              *reinterpret_cast<float4*>(dst) = o;
+            } else {
+              const float e[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                if (col + i < pN) {
+                  float v = alpha * e[i];
+                  if (beta != 0.f) v = fmaf(beta, dst[i], v);
+                  dst[i] = v;
+                }
+              }
+            }
           }
         }
         __syncwarp();

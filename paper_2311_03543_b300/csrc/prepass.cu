@@ -468,7 +468,7 @@ __device__ __forceinline__ void tile_transpose(const PrepassJob& J, int64_t r0, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 6) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
                                                               int njobs, int total_tiles) {
   __shared__ float tile[64][65];
   const int per = (total_tiles + gridDim.x - 1) / gridDim.x;
