@@ -542,22 +542,25 @@ def measured_traffic(kernel, flops_per_launch):
 
 def measure_batched(ctx, cp, W, torch, dev, reps=5):
     """The uneven batched workload: 512 GEMMs, M, N, K log-uniform in [32, 2048]
-    (seed 5), f32 (tol 1e-5 -> 3xBF16) or bf16 with probability 1/2.  The
-    autotuner times the per-GEMM loop and the grouped kernel's configurations;
-    then the chosen one and the loop are each timed over `reps` calls."""
+    (seed 5), f32 (tol 1e-5 -> 3xBF16) or bf16 with probability 1/2, every
+    leading dimension rounded up to 16 bytes.  The autotuner times the
+    per-GEMM loop and the grouped kernel's configurations; then the chosen one
+    and the loop are each timed over `reps` calls."""
     import ctypes
     plist = W.batched_problems()
     keep, probs = [], []
     for i, (m, n, k, dt) in enumerate(plist):
         g = torch.Generator(device=dev)
         g.manual_seed(5000 + i)
-        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
-        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        per16 = 8 if dt == cp.BF16 else 4            # elements per 16 bytes
+        lda, ldb, ldc = -(-k // per16) * per16, -(-n // per16) * per16, -(-n // 4) * 4
+        A = torch.rand((m, lda), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, ldb), generator=g, device=dev) * 2 - 1
         if dt == cp.BF16:
             A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
-        C = torch.empty((m, n), device=dev)
+        C = torch.empty((m, ldc), device=dev)
         keep.append((A, B, C))
-        probs.append(dict(m=m, n=n, k=k, lda=k, ldb=n, ldc=n, dtype=dt, A=A.data_ptr(),
+        probs.append(dict(m=m, n=n, k=k, lda=lda, ldb=ldb, ldc=ldc, dtype=dt, A=A.data_ptr(),
                           B=B.data_ptr(), C=C.data_ptr()))
     arr = cp.Context.problem_array(probs)
     best, tuned_ms = ctx.autotune_batched(arr, tol=TOL)
@@ -584,7 +587,8 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
     del keep
     names = ["per-GEMM launches", "grouped BN=128", "grouped BN=64",
              "grouped BN=128 largest-first", "grouped BN=64 largest-first"]
-    return {"problems": len(plist), "gflop": flops / 1e9, "chosen": names[best],
+    return {"problems": len(plist), "gflop": flops / 1e9, "ld": "rounded up to 16 bytes",
+            "chosen": names[best],
             "ms_chosen": ms_best, "tflops_chosen": flops / (ms_best / 1e3) / 1e12,
             "ms_per_gemm_launches": ms_loop,
             "tflops_per_gemm_launches": flops / (ms_loop / 1e3) / 1e12,

@@ -183,8 +183,9 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
   // ---- workspace layout
   struct Plan {
     int mode, pieces, elem;
-    int64_t ldk;
-    bool a_in_place;
+    int64_t ldk;   // K pitch of K-major copies (A; B in TF32 mode)
+    int64_t ldn;   // N pitch of B copies in the bf16 modes (B stays K x N)
+    bool a_in_place, b_in_place;
     size_t off_a, off_b, a_bytes, b_bytes;
   };
   std::vector<Plan> plan(order.size());
@@ -199,7 +200,13 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     const bool native = (P.mode == 0) || (P.mode == 2);  // operand type already right
     P.a_in_place = native && (reinterpret_cast<uintptr_t>(p.A) % 16 == 0) &&
                    ((p.lda * P.elem) % 16 == 0);
-    P.b_bytes = align256(static_cast<size_t>(p.n) * P.ldk * P.elem);
+    P.ldn = (p.n + 7) / 8 * 8;
+    // bf16 B is read K x N as stored when TMA can address it
+    P.b_in_place = P.mode == 0 && (reinterpret_cast<uintptr_t>(p.B) % 16 == 0) &&
+                   ((p.ldb * 2) % 16 == 0);
+    P.b_bytes = P.b_in_place ? 0
+                : P.mode == 2 ? align256(static_cast<size_t>(p.n) * P.ldk * P.elem)
+                              : align256(static_cast<size_t>(p.k) * P.ldn * 2);
     P.a_bytes = align256(static_cast<size_t>(p.m) * P.ldk * P.elem);
     P.off_b = ws_need;
     ws_need += P.pieces * P.b_bytes;
@@ -254,23 +261,30 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     const void* a_src = P.a_in_place ? p.A : aw;
     const int64_t a_ld = P.a_in_place ? p.lda : P.ldk;
     rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128);
-    if (rc == COMPAR_OK)
-      rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn);
+    if (rc == COMPAR_OK) {
+      if (P.mode == 2) {  // K-major copy of B: N rows of K
+        rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn);
+      } else {            // B as K rows of N: 64-column x 64-row boxes
+        const void* b_src = P.b_in_place ? p.B : bw;
+        const int64_t b_ld = P.b_in_place ? p.ldb : P.ldn;
+        rc = tma_encode_2d(&G.map_b, dt, 2, b_src, p.n, p.k, b_ld, 64, 64);
+      }
+    }
     if (rc == COMPAR_OK && P.pieces == 2) {
       rc = tma_encode_2d(&G.map_a2, dt, P.elem, aw + P.a_bytes, p.k, p.m, P.ldk, kelems, 128);
       if (rc == COMPAR_OK)
-        rc = tma_encode_2d(&G.map_b2, dt, P.elem, bw + P.b_bytes, p.k, p.n, P.ldk, kelems, bn);
+        rc = tma_encode_2d(&G.map_b2, dt, 2, bw + P.b_bytes, p.n, p.k, P.ldn, 64, 64);
     }
     if (rc != COMPAR_OK) return rc;
     const int out_kind = P.mode == 1 ? PP_SPLIT_BF16 : PP_COPY;
     auto add_job = [&](const void* src, int64_t ld_src, int64_t rows, int64_t cols, void* dst,
-                       void* dst_lo, int transpose) {
+                       void* dst_lo, int transpose, int64_t ld_dst) {
       PrepassJob& J = b->h_jobs[njobs++];
       J.src = src;
       J.dst = dst;
       J.dst_lo = dst_lo;
       J.ld_src = ld_src;
-      J.ld_dst = P.ldk;
+      J.ld_dst = ld_dst;
       J.rows = static_cast<int>(rows);
       J.cols = static_cast<int>(cols);
       J.in_type = p.dtype;
@@ -285,10 +299,13 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
       const int in_elem = p.dtype == COMPAR_F32 ? 4 : 2;
       J.vec = (reinterpret_cast<uintptr_t>(src) % (4 * in_elem) == 0) && (ld_src % 4 == 0);
     };
-    // B: K x N row-major -> N x K
-    add_job(p.B, p.ldb, p.k, p.n, bw, P.pieces == 2 ? bw + P.b_bytes : nullptr, 1);
+    // B: TF32 reads a K-major (N x K) copy; the bf16 modes keep K x N
+    if (P.mode == 2)
+      add_job(p.B, p.ldb, p.k, p.n, bw, nullptr, 1, P.ldk);
+    else if (!P.b_in_place)
+      add_job(p.B, p.ldb, p.k, p.n, bw, P.pieces == 2 ? bw + P.b_bytes : nullptr, 0, P.ldn);
     if (!P.a_in_place)
-      add_job(p.A, p.lda, p.m, p.k, aw, P.pieces == 2 ? aw + P.a_bytes : nullptr, 0);
+      add_job(p.A, p.lda, p.m, p.k, aw, P.pieces == 2 ? aw + P.a_bytes : nullptr, 0, P.ldk);
   }
   const int ngroup = static_cast<int>(nprob);
   const auto key = std::make_tuple(ngroup, tile_acc, njobs, ptile_acc, bn);

@@ -4,10 +4,13 @@
 // small GEMMs on one GPU the B300-native form of that is a single persistent
 // kernel whose CTAs walk a shared tile list spanning every problem.
 //
-// Per-problem mode (same stage layout, chosen per tile at run time):
+// Per-problem mode (same stage sizes, chosen per tile at run time):
 //   mode 0 BF16   : bf16 operands, one kind::f16 MMA per 32-byte K step
 //   mode 1 SPLIT3 : 3xBF16 pieces {hi, lo}, three kind::f16 MMAs per K step
 //   mode 2 TF32   : float32 operands, one kind::tf32 MMA per K step
+// A is K-major (row-major M x K).  In the bf16 modes B is read as stored,
+// K x N with N contiguous (MN-major): TMA boxes of 64 columns x 64 K rows,
+// so a bf16 B needs no re-layout at all; TF32 reads a K-major copy of B.
 // Every mode accumulates each chunk of 4 stages in TMEM and adds the chunk
 // into FP32 registers (promotion), so no mode carries an accumulation error
 // that grows with K.
@@ -37,6 +40,7 @@ constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each half the column
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpi = 32 * kEpiWarps;
 constexpr int kStgPitch = 36;  // staging row pitch (floats): 16-byte rows, no bank conflicts
+constexpr int kMnBox = 64 * kRow;  // one MN-major B box: 64 columns x 64 K rows of bf16
 constexpr int kChunkKB = 4;  // promotion every 4 stages
 constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
 
@@ -145,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         last_q = q;
       }
       const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
-      const int kelems = P.mode == 2 ? kRow / 4 : kRow / 2;
+      const bool tf32 = P.mode == 2;
+      const int kelems = tf32 ? kRow / 4 : kRow / 2;
       // problem fields go to registers once: the loop's asm statements clobber
       // memory, so fields read through P would be reloaded every iteration
       const int num_kb = P.num_kb;
@@ -158,10 +163,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* st = smem + stage * L::kStage;
         const int x = kb * kelems;
         dev::tma_load_2d(st, &P.map_a, &full[stage], x, mb * kBM);
-        dev::tma_load_2d(st + 2 * L::kA, &P.map_b, &full[stage], x, nb * BN);
-        if (pieces == 2) {
-          dev::tma_load_2d(st + L::kA, &P.map_a2, &full[stage], x, mb * kBM);
-          dev::tma_load_2d(st + 2 * L::kA + L::kB, &P.map_b2, &full[stage], x, nb * BN);
+        if (pieces == 2) dev::tma_load_2d(st + L::kA, &P.map_a2, &full[stage], x, mb * kBM);
+        if (tf32) {
+          dev::tma_load_2d(st + 2 * L::kA, &P.map_b, &full[stage], x, nb * BN);
+        } else {
+#pragma unroll
+          for (int h = 0; h < BN / 64; ++h) {
+            dev::tma_load_2d(st + 2 * L::kA + h * kMnBox, &P.map_b, &full[stage],
+                             nb * BN + h * 64, x);
+            if (pieces == 2)
+              dev::tma_load_2d(st + 2 * L::kA + L::kB + h * kMnBox, &P.map_b2, &full[stage],
+                               nb * BN + h * 64, x);
+          }
         }
         issued |= 1u << stage;
         issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (issued & (1u << s)) drain(&full[s], (issued_par >> s) & 1, budget_ns);
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
-    constexpr uint32_t id_f16 = dev::make_idesc(1, 1, kBM, BN);
+    constexpr uint32_t id_f16 = dev::make_idesc_bmn(1, 1, kBM, BN);
     constexpr uint32_t id_tf32 = dev::make_idesc(2, 2, kBM, BN);
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;
@@ -203,19 +216,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t s0 = dev::smem_u32(smem + stage * L::kStage);
           const uint64_t da = dev::smem_desc_sw128_kmajor(s0);
           const uint64_t da2 = dev::smem_desc_sw128_kmajor(s0 + L::kA);
-          const uint64_t db = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA);
-          const uint64_t db2 = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA + L::kB);
 #pragma unroll
           for (int kk = 0; kk < kRow / 32; ++kk) {
+            // A: 32 bytes of K per instruction inside the swizzled row
             const uint64_t ko = static_cast<uint64_t>(kk * 32) >> 4;
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if (mode == 2) {
+              const uint64_t db = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA);
               dev::mma<Kind::TF32>(d, da + ko, db + ko, id_tf32, first);
             } else {
-              dev::mma<Kind::F16>(d, da + ko, db + ko, id_f16, first);
+              // B (MN-major): 16 K rows per instruction, 2048 bytes
+              const uint32_t bk = s0 + 2 * L::kA + kk * 2048;
+              const uint64_t db = dev::smem_desc_sw128_mnmajor(bk, kMnBox);
+              dev::mma<Kind::F16>(d, da + ko, db, id_f16, first);
               if (mode == 1) {
-                dev::mma<Kind::F16>(d, da + ko, db2 + ko, id_f16, 1u);
-                dev::mma<Kind::F16>(d, da2 + ko, db + ko, id_f16, 1u);
+                const uint64_t db2 = dev::smem_desc_sw128_mnmajor(bk + L::kB, kMnBox);
+                dev::mma<Kind::F16>(d, da + ko, db2, id_f16, 1u);
+                dev::mma<Kind::F16>(d, da2 + ko, db, id_f16, 1u);
               }
             }
           }

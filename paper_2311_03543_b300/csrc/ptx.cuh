@@ -219,6 +219,22 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t smem_addr) {
   return d;
 }
 
+// MN-major operand tile with the 128-byte swizzle, as TMA writes a box of
+// 64 MN-elements (128 bytes, 16-bit types) by K rows: one 128-byte row per K
+// index; 8-row K groups are 1024 bytes apart (stride byte offset) and
+// successive 64-element MN groups `mn_group_bytes` apart (leading byte
+// offset).  A K step of 16 rows advances the start address by 2048 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128_mnmajor(uint32_t smem_addr,
+                                                            uint32_t mn_group_bytes) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>((mn_group_bytes >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
 // Instruction descriptor: D = F32, K-major A and B, shape M x N.
 // a_fmt/b_fmt: kind::f16 -> 0 f16 / 1 bf16; kind::tf32 -> 2; kind::f8f6f4 -> 0 e4m3.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t a_fmt, uint32_t b_fmt, int M, int N) {
@@ -227,6 +243,11 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t a_fmt, uint32_t b_fmt
          | (0u << 15) | (0u << 16)                  // A, B K-major
          | (static_cast<uint32_t>(N >> 3) << 17)    // N / 8
          | (static_cast<uint32_t>(M >> 4) << 24);   // M / 16
+}
+// The same with B MN-major (transposed: B stored K x N, N contiguous).
+__host__ __device__ constexpr uint32_t make_idesc_bmn(uint32_t a_fmt, uint32_t b_fmt, int M,
+                                                      int N) {
+  return make_idesc(a_fmt, b_fmt, M, N) | (1u << 16);
 }
 
 }  // namespace dev

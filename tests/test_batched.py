@@ -100,6 +100,25 @@ def test_grouped_fp32_accurate_and_bf16(ctx):
     _check(specs, host, 1e-5)
 
 
+def test_grouped_bf16_operands_read_in_place(ctx):
+    """bf16 problems whose rows are 16-byte aligned (ld a multiple of 8) are
+    read by TMA as stored: A row-major M x K, B row-major K x N (MN-major),
+    no pre-pass.  Shapes straddle the 128-row, 64/128-column and 64-deep K
+    tiles."""
+    import paper_2311_03543_b300 as cp
+    shapes = [(1, 8, 1), (17, 64, 63), (128, 128, 64), (129, 136, 65), (200, 320, 129),
+              (64, 8, 300), (300, 72, 40)]
+    specs = [(m, n, k, W.BF16, (-k) % 8, 0, 0, 1.0, 0.0) for (m, n, k) in shapes]
+    probs, host = _make_batch(specs, 700)
+    ctx.force_variant(cp.V_GROUPED)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
+    _check(specs, host, 1e-5)
+
+
 def test_grouped_tf32_mode(ctx):
     import paper_2311_03543_b300 as cp
     specs = _random_specs(24, seed=2, dtypes=(W.F32,))
