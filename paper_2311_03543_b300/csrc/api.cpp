@@ -599,6 +599,9 @@ int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
     rc = launch_variant(ctx, v, c, s);
     if (rc != COMPAR_OK) return rc;
   }
+  // a kernel whose bounded wait ran out reports it here, before any timing
+  rc = compar_check_device_error(ctx, s);
+  if (rc != COMPAR_OK) return rc;
   std::vector<cudaEvent_t> ev(2 * reps);
   for (auto& e : ev) {
     e = take_event(ctx);
@@ -620,15 +623,18 @@ int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
         break;
       }
       t.push_back(ms);
-      if (ctx->rec.on) {
-        compar_record_t r = make_record(c, v);
-        r.time_ms = ms;
-        ctx->rec.push(r);
-      }
     }
   }
   for (auto e : ev) ctx->event_pool.push_back(e);
-  if (rc != COMPAR_OK) return rc;
+  if (rc == COMPAR_OK) rc = compar_check_device_error(ctx, s);
+  if (rc != COMPAR_OK) return rc;  // no timing of a failed run reaches the models
+  if (ctx->rec.on) {
+    for (float ms : t) {
+      compar_record_t r = make_record(c, v);
+      r.time_ms = ms;
+      ctx->rec.push(r);
+    }
+  }
   std::sort(t.begin(), t.end());
   const float med = (reps % 2) ? t[reps / 2] : 0.5f * (t[reps / 2 - 1] + t[reps / 2]);
   *median_ms = med;

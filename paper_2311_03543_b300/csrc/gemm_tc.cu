@@ -51,16 +51,19 @@ template <>
 struct Traits<COMPAR_V_TC_TF32> {
   static constexpr Kind kind = Kind::TF32;
   static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
+  static constexpr bool b_mn = false;
 };
 template <>
 struct Traits<COMPAR_V_TC_BF16> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
+  static constexpr bool b_mn = true;
 };
 template <>
 struct Traits<COMPAR_V_TC_FP8> {
   static constexpr Kind kind = Kind::F8;
   static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
+  static constexpr bool b_mn = false;
 };
 // 3xBF16: 64-byte rows give 48 KB stages (four of them) for a 128 x 256 tile;
 // promotion every 8 stages = 256 K elements.
@@ -68,6 +71,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
+  static constexpr bool b_mn = false;
 };
 // 6-product split: three pieces per operand make 72 KB stages (three of
 // them).  Each stage is its own promoted chunk: within it the five small
@@ -77,6 +81,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT6> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 3, BN = 256, row = 64, chunk_kb = 1, epi = 8;
+  static constexpr bool b_mn = false;
 };
 
 template <int V>
@@ -93,6 +98,9 @@ struct Layout {
   static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes;
   static constexpr int kTmemCols = 2 * BN;  // two accumulators
   static constexpr int kElemsPerStage = T::row / T::elem;
+  // MN-major B (16-bit types): boxes of 64 columns x kElemsPerStage K rows,
+  // 128-byte rows, one per 64 columns of the tile
+  static constexpr int kMnBox = 64 * 2 * kElemsPerStage;
   static constexpr int kThreads = 64 + 32 * T::epi;
   static constexpr int kEpiThreads = 32 * T::epi;
   static constexpr int kEpiCols = BN * 4 / T::epi;  // columns one epilogue warp handles
@@ -220,14 +228,25 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         uint8_t* a_dst = sA + (stage * P) * L::kABytes;
         uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
         dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
-        dev::tma_load_2d(b_dst, &tmB, &full[stage], x, nb * BN);
-        if constexpr (P >= 2) {
-          dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
-          dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
-        }
-        if constexpr (P == 3) {
+        if constexpr (P >= 2) dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
+        if constexpr (P == 3)
           dev::tma_load_2d(a_dst + 2 * L::kABytes, &tmA3, &full[stage], x, mb * kBM);
-          dev::tma_load_2d(b_dst + 2 * L::kBBytes, &tmB3, &full[stage], x, nb * BN);
+        if constexpr (T::b_mn) {
+#pragma unroll
+          for (int h = 0; h < BN / 64; ++h) {
+            const int n0 = nb * BN + h * 64;
+            dev::tma_load_2d(b_dst + h * L::kMnBox, &tmB, &full[stage], n0, x);
+            if constexpr (P >= 2)
+              dev::tma_load_2d(b_dst + L::kBBytes + h * L::kMnBox, &tmB2, &full[stage], n0, x);
+            if constexpr (P == 3)
+              dev::tma_load_2d(b_dst + 2 * L::kBBytes + h * L::kMnBox, &tmB3, &full[stage], n0,
+                               x);
+          }
+        } else {
+          dev::tma_load_2d(b_dst, &tmB, &full[stage], x, nb * BN);
+          if constexpr (P >= 2) dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
+          if constexpr (P == 3)
+            dev::tma_load_2d(b_dst + 2 * L::kBBytes, &tmB3, &full[stage], x, nb * BN);
         }
         issued |= 1u << stage;
         issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
@@ -244,7 +263,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t idesc = dev::make_idesc(T::fmt, T::fmt, kBM, BN);
+    constexpr uint32_t idesc = T::b_mn ? dev::make_idesc_bmn(T::fmt, T::fmt, kBM, BN)
+                                       : dev::make_idesc(T::fmt, T::fmt, kBM, BN);
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;  // accumulator-buffer uses (one per K chunk)
     const int chunk = kChunkKB > 0 ? kChunkKB : p.num_kb;
@@ -268,43 +288,45 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           dev::tc_fence_after();
           const uint32_t a0 = dev::smem_u32(sA + (stage * P) * L::kABytes);
           const uint32_t b0 = dev::smem_u32(sB + (stage * P) * L::kBBytes);
-          const uint64_t da = dev::smem_desc_kmajor<T::row>(a0);
-          const uint64_t db = dev::smem_desc_kmajor<T::row>(b0);
+          // Descriptors of K step kk: A (K-major) advances 32 bytes inside its
+          // swizzled rows; an MN-major B advances 16 K rows (2048 bytes).
+          auto b_desc = [&](int piece, int kk) -> uint64_t {
+            const uint32_t base = b0 + piece * L::kBBytes;
+            if constexpr (T::b_mn)
+              return dev::smem_desc_sw128_mnmajor(base + kk * 2048, L::kMnBox);
+            else
+              return dev::smem_desc_kmajor<T::row>(base) + (static_cast<uint64_t>(kk * 32) >> 4);
+          };
+          auto a_desc = [&](int piece, int kk) -> uint64_t {
+            return dev::smem_desc_kmajor<T::row>(a0 + piece * L::kABytes) +
+                   (static_cast<uint64_t>(kk * 32) >> 4);
+          };
           if constexpr (P == 3) {
-            const uint64_t da1 = dev::smem_desc_kmajor<T::row>(a0 + L::kABytes);
-            const uint64_t db1 = dev::smem_desc_kmajor<T::row>(b0 + L::kBBytes);
-            const uint64_t da2 = dev::smem_desc_kmajor<T::row>(a0 + 2 * L::kABytes);
-            const uint64_t db2 = dev::smem_desc_kmajor<T::row>(b0 + 2 * L::kBBytes);
             // small products of every K step of the stage, then the leading ones
 #pragma unroll
             for (int kk = 0; kk < T::row / 32; ++kk) {
-              const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
-              dev::mma<T::kind>(d_tmem, da + koff, db1 + koff, idesc, first);
-              dev::mma<T::kind>(d_tmem, da1 + koff, db + koff, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, da + koff, db2 + koff, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, da1 + koff, db1 + koff, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, da2 + koff, db + koff, idesc, 1u);
+              const uint64_t a_0 = a_desc(0, kk), a_1 = a_desc(1, kk), a_2 = a_desc(2, kk);
+              const uint64_t b_0 = b_desc(0, kk), b_1 = b_desc(1, kk), b_2 = b_desc(2, kk);
+              dev::mma<T::kind>(d_tmem, a_0, b_1, idesc, first);
+              dev::mma<T::kind>(d_tmem, a_1, b_0, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, a_0, b_2, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, a_1, b_1, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, a_2, b_0, idesc, 1u);
             }
 #pragma unroll
-            for (int kk = 0; kk < T::row / 32; ++kk) {
-              const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
-              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, 1u);
-            }
+            for (int kk = 0; kk < T::row / 32; ++kk)
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, 1u);
           }
 #pragma unroll
           for (int kk = 0; P < 3 && kk < T::row / 32; ++kk) {
-            // each instruction consumes 32 bytes of K; advance the start address
-            const uint64_t koff = static_cast<uint64_t>(kk * 32) >> 4;
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if constexpr (P == 2) {
-              const uint64_t da_lo = dev::smem_desc_kmajor<T::row>(a0 + L::kABytes);
-              const uint64_t db_lo = dev::smem_desc_kmajor<T::row>(b0 + L::kBBytes);
-              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
-              dev::mma<T::kind>(d_tmem, da + koff, db_lo + koff, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, da_lo + koff, db + koff, idesc, 1u);
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, first);
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(1, kk), idesc, 1u);
+              dev::mma<T::kind>(d_tmem, a_desc(1, kk), b_desc(0, kk), idesc, 1u);
             } else {
-              dev::mma<T::kind>(d_tmem, da + koff, db + koff, idesc, first);
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, first);
             }
           }
           dev::mma_commit(&empty[stage]);  // stage reusable once these MMAs finish
@@ -501,22 +523,27 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   CUtensorMap ta, tb, ta2, tb2, ta3, tb3;
   const CUtensorMapDataType dt = map_type(V);
   const uint32_t box_k = static_cast<uint32_t>(L::kElemsPerStage);
+  // A: M rows of K.  B: N rows of K (K-major), or, MN-major, K rows of N
+  // read in 64-column boxes.
+  auto enc_b = [&](CUtensorMap* m, const void* base) {
+    if constexpr (T::b_mn)
+      return tma_encode_2d(m, dt, 2, base, c.n, c.k, ldb, 64, box_k, 128);
+    else
+      return tma_encode_2d(m, dt, T::elem, base, c.k, c.n, ldb, box_k, T::BN, T::row);
+  };
   int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
-  if (rc == COMPAR_OK)
-    rc = tma_encode_2d(&tb, dt, T::elem, B, c.k, c.n, ldb, box_k, T::BN, T::row);
+  if (rc == COMPAR_OK) rc = enc_b(&tb, B);
   if (rc != COMPAR_OK) return rc;
   ta2 = ta3 = ta;
   tb2 = tb3 = tb;
   if (T::pieces >= 2) {
     rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM, T::row);
-    if (rc == COMPAR_OK)
-      rc = tma_encode_2d(&tb2, dt, T::elem, B2, c.k, c.n, ldb, box_k, T::BN, T::row);
+    if (rc == COMPAR_OK) rc = enc_b(&tb2, B2);
     if (rc != COMPAR_OK) return rc;
   }
   if (T::pieces == 3) {
     rc = tma_encode_2d(&ta3, dt, T::elem, A3, c.k, c.m, lda, box_k, kBM, T::row);
-    if (rc == COMPAR_OK)
-      rc = tma_encode_2d(&tb3, dt, T::elem, B3, c.k, c.n, ldb, box_k, T::BN, T::row);
+    if (rc == COMPAR_OK) rc = enc_b(&tb3, B3);
     if (rc != COMPAR_OK) return rc;
   }
   TcArgs a{};
@@ -564,8 +591,11 @@ bool tc_supported(int v, const GemmCall& c) {
   }
 }
 
-// Pre-passes + launch.  B is always re-laid out to K-major (N x K); A is used
-// in place when its dtype matches and TMA can address it, else converted.
+// Pre-passes + launch.  The BF16 variant reads B MN-major, K x N as stored:
+// bf16 B with 16-byte rows is used in place, else converted row by row
+// (pitch N rounded up to 8).  TF32, FP8 and the splits read a K-major
+// (N x K) copy of B.  A is used in place when its dtype
+// matches and TMA can address it, else converted.
 int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
               cudaStream_t s) {
   if (!tc_supported(v, c)) return COMPAR_ERR_UNSUPPORTED;
@@ -576,10 +606,16 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const bool a_native = (c.dtype != COMPAR_F32 || v == COMPAR_V_TC_TF32);
   const bool a_in_place = a_native && tma_operand_ok(c.A, c.lda, elem);
   const bool fp8_from_f32 = (v == COMPAR_V_TC_FP8 && c.dtype == COMPAR_F32);
+  // (MN-major B measured slower for the split variants' 64-byte stages)
+  const bool b_mn = (v == COMPAR_V_TC_BF16);
+  const int64_t ldn = round_up(c.n, 8);  // MN-major copies: 16-byte rows
+  const bool b_in_place = b_mn && c.dtype == COMPAR_BF16 && tma_operand_ok(c.B, c.ldb, 2);
 
-  // workspace carve: [A pieces][B pieces][fp8 scalars]
+  // workspace carve: [B pieces][A pieces][fp8 scalars]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
-  const size_t b_bytes = align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
+  const size_t b_bytes = b_in_place ? 0
+                         : b_mn     ? align_up(static_cast<size_t>(c.k) * ldn * 2, 256)
+                                    : align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
   size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256;
   int rc = ws.ensure(need, s);
   if (rc != COMPAR_OK) return rc;
@@ -614,10 +650,17 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     sb = fscal + 2;
     dqb = fscal + 3;
   }
-  // B: K x N row-major -> N x K (K-major)
-  rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldk, true,
-                       pieces >= 2 ? wb + b_bytes : nullptr, sb, s);
-  if (rc != COMPAR_OK) return rc;
+  const void* Bop = wb;
+  int64_t ldb_op = b_mn ? ldn : ldk;
+  if (b_in_place) {
+    Bop = c.B;
+    ldb_op = c.ldb;
+  } else {
+    // B: K x N row-major -> K x N pieces (MN-major) or N x K (K-major)
+    rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldb_op, !b_mn,
+                         pieces >= 2 ? wb + b_bytes : nullptr, sb, s);
+    if (rc != COMPAR_OK) return rc;
+  }
   const void* A = c.A;
   int64_t lda = c.lda;
   if (!a_in_place) {
@@ -633,19 +676,19 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const void* B3 = pieces == 3 ? static_cast<const void*>(wb + 2 * b_bytes) : nullptr;
   switch (v) {
     case COMPAR_V_TC_TF32:
-      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr,
+      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
                                       nullptr, nullptr, g, num_sms, s);
     case COMPAR_V_TC_BF16:
-      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr,
+      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
                                       nullptr, nullptr, g, num_sms, s);
     case COMPAR_V_TC_FP8:
-      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, wb, ldk, nullptr, nullptr, nullptr, nullptr, dqa,
-                                     dqb, g, num_sms, s);
+      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
+                                     dqa, dqb, g, num_sms, s);
     case COMPAR_V_SPLIT3:
-      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, wb, ldk, A2, B2, nullptr, nullptr, nullptr,
+      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr, nullptr,
                                      nullptr, g, num_sms, s);
     default:
-      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, wb, ldk, A2, B2, A3, B3, nullptr, nullptr, g,
+      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr, g,
                                      num_sms, s);
   }
 }
