@@ -243,7 +243,7 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     G.M = static_cast<int>(p.m);
     G.N = static_cast<int>(p.n);
     G.K = static_cast<int>(p.k);
-    const int kelems = 128 / P.elem;
+    const int kelems = kGroupedRow / P.elem;
     G.num_kb = static_cast<int>((p.k + kelems - 1) / kelems);
     G.tiles_m = static_cast<int>((p.m + 127) / 128);
     G.tiles_n = static_cast<int>((p.n + bn - 1) / bn);
@@ -260,20 +260,21 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     uint8_t* aw = ws + P.off_a;
     const void* a_src = P.a_in_place ? p.A : aw;
     const int64_t a_ld = P.a_in_place ? p.lda : P.ldk;
-    rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128);
+    rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128, kGroupedRow);
     if (rc == COMPAR_OK) {
       if (P.mode == 2) {  // K-major copy of B: N rows of K
-        rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn);
+        rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn, kGroupedRow);
       } else {            // B as K rows of N: 64-column x 64-row boxes
         const void* b_src = P.b_in_place ? p.B : bw;
         const int64_t b_ld = P.b_in_place ? p.ldb : P.ldn;
-        rc = tma_encode_2d(&G.map_b, dt, 2, b_src, p.n, p.k, b_ld, 64, 64);
+        rc = tma_encode_2d(&G.map_b, dt, 2, b_src, p.n, p.k, b_ld, 64, kGroupedRow / 2);
       }
     }
     if (rc == COMPAR_OK && P.pieces == 2) {
-      rc = tma_encode_2d(&G.map_a2, dt, P.elem, aw + P.a_bytes, p.k, p.m, P.ldk, kelems, 128);
+      rc = tma_encode_2d(&G.map_a2, dt, P.elem, aw + P.a_bytes, p.k, p.m, P.ldk, kelems, 128,
+                         kGroupedRow);
       if (rc == COMPAR_OK)
-        rc = tma_encode_2d(&G.map_b2, dt, 2, bw + P.b_bytes, p.n, p.k, P.ldn, 64, 64);
+        rc = tma_encode_2d(&G.map_b2, dt, 2, bw + P.b_bytes, p.n, p.k, P.ldn, 64, kGroupedRow / 2);
     }
     if (rc != COMPAR_OK) return rc;
     const int out_kind = P.mode == 1 ? PP_SPLIT_BF16 : PP_COPY;

@@ -9,8 +9,8 @@
 //   mode 1 SPLIT3 : 3xBF16 pieces {hi, lo}, three kind::f16 MMAs per K step
 //   mode 2 TF32   : float32 operands, one kind::tf32 MMA per K step
 // A is K-major (row-major M x K).  In the bf16 modes B is read as stored,
-// K x N with N contiguous (MN-major): TMA boxes of 64 columns x 64 K rows,
-// so a bf16 B needs no re-layout at all; TF32 reads a K-major copy of B.
+// K x N with N contiguous (MN-major): TMA boxes of 64 columns x kRow/2 K
+// rows, so a bf16 B needs no re-layout at all; TF32 reads a K-major copy.
 // Every mode accumulates each chunk of 4 stages in TMEM and adds the chunk
 // into FP32 registers (promotion), so no mode carries an accumulation error
 // that grows with K.
@@ -35,13 +35,13 @@ namespace {
 using dev::Kind;
 
 constexpr int kBM = 128;
-constexpr int kRow = 128;  // bytes of K per stage
+constexpr int kRow = kGroupedRow;  // bytes of K per stage and operand row
 constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each half the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpi = 32 * kEpiWarps;
 constexpr int kStgPitch = 36;  // staging row pitch (floats): 16-byte rows, no bank conflicts
-constexpr int kMnBox = 64 * kRow;  // one MN-major B box: 64 columns x 64 K rows of bf16
-constexpr int kChunkKB = 4;  // promotion every 4 stages
+constexpr int kMnBox = 64 * kRow;  // one MN-major B box: 64 columns x kRow/2 K rows of bf16
+constexpr int kChunkKB = 512 / kRow;  // promotion every 256 bf16 K elements
 constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
 
 template <int BN>
@@ -214,15 +214,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           dev::tc_fence_after();
           const uint32_t s0 = dev::smem_u32(smem + stage * L::kStage);
-          const uint64_t da = dev::smem_desc_sw128_kmajor(s0);
-          const uint64_t da2 = dev::smem_desc_sw128_kmajor(s0 + L::kA);
+          const uint64_t da = dev::smem_desc_kmajor<kRow>(s0);
+          const uint64_t da2 = dev::smem_desc_kmajor<kRow>(s0 + L::kA);
 #pragma unroll
           for (int kk = 0; kk < kRow / 32; ++kk) {
             // A: 32 bytes of K per instruction inside the swizzled row
             const uint64_t ko = static_cast<uint64_t>(kk * 32) >> 4;
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if (mode == 2) {
-              const uint64_t db = dev::smem_desc_sw128_kmajor(s0 + 2 * L::kA);
+              const uint64_t db = dev::smem_desc_kmajor<kRow>(s0 + 2 * L::kA);
               dev::mma<Kind::TF32>(d, da + ko, db + ko, id_tf32, first);
             } else {
               // B (MN-major): 16 K rows per instruction, 2048 bytes

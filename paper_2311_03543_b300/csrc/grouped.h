@@ -9,6 +9,10 @@
 
 namespace compar {
 
+// Bytes of K per pipeline stage and operand row in the grouped kernel (the
+// TMA / MMA swizzle width: 64 -> 64-byte swizzle, 128 -> 128-byte).
+constexpr int kGroupedRow = 64;
+
 // One problem of a grouped launch.  Tensor maps cover the K-major operands
 // (A: M x K, B re-laid out as N x K); map_a2 / map_b2 are the lo pieces of
 // the 3xBF16 mode.  Tiles of all problems form one list; this problem owns
