@@ -534,7 +534,8 @@ def measured_traffic(kernel, flops_per_launch):
     if h.hexdigest() != rec["src_sha1"]:
         return None, "kernel changed since the ncu capture"
     m, n, k = rec["shape"]
-    scale = flops_per_launch / (2.0 * m * n * k * (3 if kernel == "split-3xbf16" else 1))
+    products = {"split-3xbf16": 3, "split-6xbf16": 6}.get(kernel, 1)
+    scale = flops_per_launch / (2.0 * m * n * k * products)
     return (rec["dram_bytes_per_launch"] * scale,
             f"ncu dram read+write of one {m}x{n}x{k} launch ({rec['source']}) scaled by work "
             f"to the average launch (x{scale:.3f})")
