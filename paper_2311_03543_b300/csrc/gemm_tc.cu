@@ -19,9 +19,10 @@
 //   warp 1      TMEM allocator; one lane issues tcgen05.mma into one of two
 //               TMEM accumulators (double buffered across output tiles or
 //               K chunks) and releases ring stages with tcgen05.commit.
-//   warps 2..   epilogue (4 or 8 warps): tcgen05.ld of the accumulator lane
-//               quarter the warp may access (and its column slice),
-//               alpha/beta and dequantisation, stores to C.
+//   warps 2..   epilogue (4 or 8 warps): tcgen05.ld (16x256b fragments) of
+//               the accumulator lane quarter the warp may access (and its
+//               column slice), alpha/beta and dequantisation, sector-wide
+//               float2 stores to C.
 // Every wait is bounded (ptx.cuh); on expiry the CTA drains its own copies
 // and MMAs, frees TMEM and returns with COMPAR_ERR_TIMEOUT in the error word.
 #include <cuda.h>
@@ -131,6 +132,39 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   const int in = tile - group * per_group;
   mb = first_m + in % gsize;
   nb = in / gsize;
+}
+
+// Stores one 16-row x 64-column fragment in the 16x256b.x8 register layout:
+// v[4j + 2h + e] is row row0 + lane/4 + 8h, column col0 + 8j + 2(lane%4) + e.
+// C = alpha * v + beta * C; float2 stores (vec2: even pitch, 8-byte base).
+__device__ __forceinline__ void store_frag16x64(const float (&v)[32], float* C, int64_t ldc,
+                                                int M, int N, int row0, int col0, float alpha,
+                                                float beta, bool vec2, int lane) {
+  const int rq = lane >> 2, cq = 2 * (lane & 3);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int row = row0 + rq + 8 * h;
+    if (row >= M) continue;
+    float* crow = C + static_cast<int64_t>(row) * ldc;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int col = col0 + 8 * j + cq;
+      const float a = alpha * v[4 * j + 2 * h], b = alpha * v[4 * j + 2 * h + 1];
+      if (vec2 && col + 1 < N) {
+        float2* dst = reinterpret_cast<float2*>(crow + col);
+        float2 o = make_float2(a, b);
+        if (beta != 0.f) {
+          const float2 old = *dst;
+          o.x = fmaf(beta, old.x, o.x);
+          o.y = fmaf(beta, old.y, o.y);
+        }
+        *dst = o;
+      } else {
+        if (col < N) crow[col] = beta != 0.f ? fmaf(beta, crow[col], a) : a;
+        if (col + 1 < N) crow[col + 1] = beta != 0.f ? fmaf(beta, crow[col + 1], b) : b;
+      }
+    }
+  }
 }
 
 // Wait that ignores the CTA abort flag: used only to drain this CTA's own
@@ -344,29 +378,39 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     drain_wait(drain, 0, p.budget_ns);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
+    // The accumulator is read in 16-row x 64-column fragments (16x256b
+    // shape): four consecutive lanes hold 8 consecutive columns of a row, so
+    // every store instruction writes whole 32-byte sectors of 8 rows.
     const int quarter = warp & 3;            // TMEM lanes this warp may access
     const int cslice = (warp - 2) / 4;       // which kEpiCols-wide column slice
     constexpr int EC = L::kEpiCols;
+    constexpr int NF = 2 * (EC / 64);        // fragments: 2 row halves x EC/64 column blocks
+    static_assert(EC % 64 == 0, "epilogue column slice");
     float alpha = p.alpha;
     if (p.dequant_a) alpha *= *p.dequant_a;
     if (p.dequant_b) alpha *= *p.dequant_b;
-    const bool vec = (p.N % 4 == 0) && (p.ldc % 4 == 0) &&
-                     ((reinterpret_cast<uintptr_t>(p.C) & 15) == 0);
+    const bool vec2 = (p.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(p.C) & 7) == 0);
     int acc_iter = 0;
     const int num_chunks = kChunkKB > 0 ? (p.num_kb + kChunkKB - 1) / kChunkKB : 1;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       int mb, nb;
       tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
-      const int row = mb * kBM + quarter * 32 + lane;
-      float* crow = p.C + static_cast<int64_t>(row) * p.ldc;
+      const int row_q = mb * kBM + quarter * 32;     // first row of this warp's quarter
+      const int col_s = nb * BN + cslice * EC;       // first column of its slice
+      auto frag_taddr = [&](uint32_t acc, int f) {
+        return tmem_base + (static_cast<uint32_t>(quarter * 32 + 16 * (f & 1)) << 16) +
+               acc * BN + cslice * EC + 64 * (f >> 1);
+      };
       if constexpr (kChunkKB > 0) {
         // Promotion: each K chunk's TMEM partial sum is added into FP32
         // registers (round to nearest), so the tensor core's accumulator
         // only ever sums kChunkKB k-blocks.
-        float sum[EC];
+        float sum[NF][32];
 #pragma unroll
-        for (int j = 0; j < EC; ++j) sum[j] = 0.f;
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[f][j] = 0.f;
         for (int ch = 0; ch < num_chunks; ++ch, ++acc_iter) {
           const uint32_t acc = acc_iter & 1;
           const uint32_t acc_phase = (acc_iter >> 1) & 1;
@@ -375,47 +419,23 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
             break;
           }
           dev::tc_fence_after();
-          const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                 acc * BN + cslice * EC;
 #pragma unroll
-          for (int c = 0; c < EC / 32; ++c) {
+          for (int f = 0; f < NF; ++f) {
             uint32_t r[32];
-            dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+            dev::tmem_ld_16x256b_x8(frag_taddr(acc, f), r);
             dev::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) sum[f][j] += __uint_as_float(r[j]);
           }
           dev::tc_fence_before();
           dev::mbar_arrive(&tempty[acc]);
         }
         if (!ok) break;
-        const int col0 = nb * BN + cslice * EC;
-        if (row < p.M && col0 < p.N) {
-          if (vec && col0 + EC <= p.N) {
+        if (row_q < p.M && col_s < p.N) {
 #pragma unroll
-            for (int j = 0; j < EC; j += 4) {
-              float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
-              float4 o = make_float4(alpha * sum[j], alpha * sum[j + 1], alpha * sum[j + 2],
-                                     alpha * sum[j + 3]);
-              if (p.beta != 0.f) {
-                const float4 old = *dst;
-                o.x = fmaf(p.beta, old.x, o.x);
-                o.y = fmaf(p.beta, old.y, o.y);
-                o.z = fmaf(p.beta, old.z, o.z);
-                o.w = fmaf(p.beta, old.w, o.w);
-              }
-              *dst = o;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < EC; ++j) {
-              if (col0 + j < p.N) {
-                float v = alpha * sum[j];
-                if (p.beta != 0.f) v = fmaf(p.beta, crow[col0 + j], v);
-                crow[col0 + j] = v;
-              }
-            }
-          }
+          for (int f = 0; f < NF; ++f)
+            store_frag16x64(sum[f], p.C, p.ldc, p.M, p.N, row_q + 16 * (f & 1),
+                            col_s + 64 * (f >> 1), alpha, p.beta, vec2, lane);
         }
         continue;
       }
@@ -424,44 +444,17 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
       ++acc_iter;
       if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
       dev::tc_fence_after();
-      const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * BN +
-                             cslice * EC;
 #pragma unroll 1
-      for (int c = 0; c < EC / 32; ++c) {
+      for (int f = 0; f < NF; ++f) {
         uint32_t r[32];
-        dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+        dev::tmem_ld_16x256b_x8(frag_taddr(acc, f), r);
         dev::tmem_ld_wait();
-        const int col0 = nb * BN + cslice * EC + c * 32;
-        if (row < p.M && col0 < p.N) {
-          if (vec && col0 + 32 <= p.N) {
+        float v[32];
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
-              float4 o;
-              o.x = alpha * __uint_as_float(r[j + 0]);
-              o.y = alpha * __uint_as_float(r[j + 1]);
-              o.z = alpha * __uint_as_float(r[j + 2]);
-              o.w = alpha * __uint_as_float(r[j + 3]);
-              if (p.beta != 0.f) {
-                const float4 old = *dst;
-                o.x = fmaf(p.beta, old.x, o.x);
-                o.y = fmaf(p.beta, old.y, o.y);
-                o.z = fmaf(p.beta, old.z, o.z);
-                o.w = fmaf(p.beta, old.w, o.w);
-              }
-              *dst = o;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (col0 + j < p.N) {
-                float v = alpha * __uint_as_float(r[j]);
-                if (p.beta != 0.f) v = fmaf(p.beta, crow[col0 + j], v);
-                crow[col0 + j] = v;
-              }
-            }
-          }
-        }
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        if (row_q < p.M && col_s < p.N)
+          store_frag16x64(v, p.C, p.ldc, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                          alpha, p.beta, vec2, lane);
       }
       dev::tc_fence_before();
       dev::mbar_arrive(&tempty[acc]);
