@@ -84,6 +84,9 @@ int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
 int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                 cudaStream_t s);
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s);
+// C = alpha * sum over s < splits of partial[s][m][n] + beta * C.
+int launch_splitk_reduce(int m, int n, int splits, const float* partial, float alpha, float beta,
+                         float* C, int64_t ldc, int num_sms, cudaStream_t s);
 // Tile shape and split-K plan of the SIMT variant: each output is the sum
 // of `splits` partial dot products, each at most `k_per` terms long.
 struct SimtPlan {

@@ -392,6 +392,17 @@ int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_
   }
 }
 
+int launch_splitk_reduce(int m, int n, int splits, const float* partial, float alpha, float beta,
+                         float* C, int64_t ldc, int num_sms, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(m) * n;
+  if (total <= 0) return COMPAR_OK;
+  const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
+  splitk_reduce_kernel<<<blocks, 256, 0, s>>>(m, n, splits, partial, alpha, beta, C, ldc);
+  COMPAR_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return COMPAR_OK;
+}
+
 int launch_scale_c(float* C, int64_t m, int64_t n, int64_t ldc, float beta, cudaStream_t s) {
   const int64_t total = m * n;
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));

@@ -114,6 +114,11 @@ struct TcArgs {
   int M, N, K;
   int num_kb;
   int tiles_m, tiles_n;
+  // Split K (few tiles, long K): work unit u = tile u / splits, K blocks
+  // [(u % splits) * kb_per_split, +kb_per_split); each unit writes
+  // alpha * partial to partial[split][M][N] and a reduce kernel forms C.
+  int splits, kb_per_split;
+  float* partial;
   float alpha, beta;
   const float* dequant_a;  // optional device factors (fp8 of float32 inputs)
   const float* dequant_b;
@@ -241,7 +246,12 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
   dev::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
-  const int num_tiles = p.tiles_m * p.tiles_n;
+  const int num_units = p.tiles_m * p.tiles_n * p.splits;
+  // K-block range of unit u
+  auto unit_kb = [&](int u, int& kb_begin, int& kb_end) {
+    kb_begin = (u % p.splits) * p.kb_per_split;
+    kb_end = min(p.num_kb, kb_begin + p.kb_per_split);
+  };
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
@@ -249,10 +259,11 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     uint32_t issued = 0, issued_parity = 0;  // per-stage bit masks
     constexpr uint32_t kTx = static_cast<uint32_t>(L::kStageBytes);
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-      int mb, nb;
-      tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
-      for (int kb = 0; kb < p.num_kb; ++kb) {
+    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
+      int mb, nb, kb_begin, kb_end;
+      tile_coords(u / p.splits, p.tiles_m, p.tiles_n, mb, nb);
+      unit_kb(u, kb_begin, kb_end);
+      for (int kb = kb_begin; kb < kb_end; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
           ok = false;
           break;
@@ -301,10 +312,12 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
                                        : dev::make_idesc(T::fmt, T::fmt, kBM, BN);
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;  // accumulator-buffer uses (one per K chunk)
-    const int chunk = kChunkKB > 0 ? kChunkKB : p.num_kb;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-      for (int kb0 = 0; ok && kb0 < p.num_kb; kb0 += chunk, ++acc_iter) {
+    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
+      int kb_begin, kb_end;
+      unit_kb(u, kb_begin, kb_end);
+      const int chunk = kChunkKB > 0 ? kChunkKB : kb_end - kb_begin;
+      for (int kb0 = kb_begin; ok && kb0 < kb_end; kb0 += chunk, ++acc_iter) {
         const uint32_t acc = acc_iter & 1;
         const uint32_t acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
@@ -313,8 +326,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         }
         dev::tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * BN;
-        const int kb_end = min(p.num_kb, kb0 + chunk);
-        for (int kb = kb0; kb < kb_end; ++kb) {
+        const int kb_stop = min(kb_end, kb0 + chunk);
+        for (int kb = kb0; kb < kb_stop; ++kb) {
           if (!dev::mbar_wait(&full[stage], phase, w)) {
             ok = false;
             break;
@@ -391,11 +404,18 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     if (p.dequant_b) alpha *= *p.dequant_b;
     const bool vec2 = (p.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(p.C) & 7) == 0);
     int acc_iter = 0;
-    const int num_chunks = kChunkKB > 0 ? (p.num_kb + kChunkKB - 1) / kChunkKB : 1;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-      int mb, nb;
-      tile_coords(tile, p.tiles_m, p.tiles_n, mb, nb);
+    // split units write alpha * partial (no beta) into their own slab
+    const bool split = p.splits > 1;
+    const int64_t out_ld = split ? p.N : p.ldc;
+    const bool vec_out = split ? (p.N % 2 == 0) : vec2;
+    const float beta = split ? 0.f : p.beta;
+    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
+      int mb, nb, kb_begin, kb_end;
+      tile_coords(u / p.splits, p.tiles_m, p.tiles_n, mb, nb);
+      unit_kb(u, kb_begin, kb_end);
+      const int num_chunks = kChunkKB > 0 ? (kb_end - kb_begin + kChunkKB - 1) / kChunkKB : 1;
+      float* out = split ? p.partial + static_cast<int64_t>(u % p.splits) * p.M * p.N : p.C;
       const int row_q = mb * kBM + quarter * 32;     // first row of this warp's quarter
       const int col_s = nb * BN + cslice * EC;       // first column of its slice
       auto frag_taddr = [&](uint32_t acc, int f) {
@@ -434,8 +454,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         if (row_q < p.M && col_s < p.N) {
 #pragma unroll
           for (int f = 0; f < NF; ++f)
-            store_frag16x64(sum[f], p.C, p.ldc, p.M, p.N, row_q + 16 * (f & 1),
-                            col_s + 64 * (f >> 1), alpha, p.beta, vec2, lane);
+            store_frag16x64(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
+                            col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
         }
         continue;
       }
@@ -453,8 +473,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
         if (row_q < p.M && col_s < p.N)
-          store_frag16x64(v, p.C, p.ldc, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
-                          alpha, p.beta, vec2, lane);
+          store_frag16x64(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                          alpha, beta, vec_out, lane);
       }
       dev::tc_fence_before();
       dev::mbar_arrive(&tempty[acc]);
@@ -497,10 +517,35 @@ CUtensorMapDataType map_type(int v) {
   }
 }
 
+// Launch plan of a tensor-core call: K blocks, tiles, and the split of K
+// when the tiles alone would leave most SMs idle (at least 8 K blocks per
+// split, at most one unit per SM).
+struct TcPlan {
+  int num_kb, tiles, splits, kb_per;
+};
+
+TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
+  const int kelems = v == COMPAR_V_TC_FP8 ? 128 : (v == COMPAR_V_TC_BF16 ? 64 : 32);
+  TcPlan p;
+  p.num_kb = static_cast<int>((c.k + kelems - 1) / kelems);
+  p.tiles = static_cast<int>(((c.m + kBM - 1) / kBM) * ((c.n + 255) / 256));
+  p.splits = 1;
+  p.kb_per = p.num_kb;
+  if (p.tiles * 2 <= num_sms && p.num_kb >= 16) {
+    const int sp = std::min(num_sms / p.tiles, p.num_kb / 8);
+    if (sp > 1) {
+      p.kb_per = (p.num_kb + sp - 1) / sp;
+      p.splits = (p.num_kb + p.kb_per - 1) / p.kb_per;
+    }
+  }
+  return p;
+}
+
 template <int V>
 int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
            const void* A2, const void* B2, const void* A3, const void* B3, const float* dq_a,
-           const float* dq_b, const DeviceGuard& g, int num_sms, cudaStream_t s) {
+           const float* dq_b, const TcPlan& plan, float* partial, const DeviceGuard& g,
+           int num_sms, cudaStream_t s) {
   using L = Layout<V>;
   using T = Traits<V>;
   static std::once_flag attr_once;
@@ -544,6 +589,9 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.N = static_cast<int>(c.n);
   a.K = static_cast<int>(c.k);
   a.num_kb = static_cast<int>((c.k + L::kElemsPerStage - 1) / L::kElemsPerStage);
+  a.splits = plan.splits;
+  a.kb_per_split = plan.splits > 1 ? plan.kb_per : a.num_kb;
+  a.partial = partial;
   a.tiles_m = static_cast<int>((c.m + kBM - 1) / kBM);
   a.tiles_n = static_cast<int>((c.n + T::BN - 1) / T::BN);
   a.alpha = c.alpha * (V == COMPAR_V_TC_FP8 ? c.scale_a * c.scale_b : 1.f);
@@ -554,13 +602,16 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.ldc = c.ldc;
   a.err_word = g.err_word;
   a.budget_ns = g.budget_ns;
-  const int tiles = a.tiles_m * a.tiles_n;
-  const int grid = std::min(tiles, num_sms);
+  const int units = a.tiles_m * a.tiles_n * a.splits;
+  const int grid = std::min(units, num_sms);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, ta3, tb3, a);
   COMPAR_CUDA_TRY(cudaGetLastError());
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();
+  // the split units already applied alpha (and the dequantisation)
+  if (a.splits > 1)
+    return launch_splitk_reduce(a.M, a.N, a.splits, partial, 1.f, c.beta, c.C, c.ldc, num_sms, s);
   return COMPAR_OK;
 }
 
@@ -604,12 +655,15 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const int64_t ldn = round_up(c.n, 8);  // MN-major copies: 16-byte rows
   const bool b_in_place = b_mn && c.dtype == COMPAR_BF16 && tma_operand_ok(c.B, c.ldb, 2);
 
-  // workspace carve: [B pieces][A pieces][fp8 scalars]
+  const TcPlan plan = tc_plan(v, c, num_sms);
+  const size_t part_bytes =
+      plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
+  // workspace carve: [B pieces][A pieces][fp8 scalars][split-K partials]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
   const size_t b_bytes = b_in_place ? 0
                          : b_mn     ? align_up(static_cast<size_t>(c.k) * ldn * 2, 256)
                                     : align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
-  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256;
+  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256 + part_bytes;
   int rc = ws.ensure(need, s);
   if (rc != COMPAR_OK) return rc;
   uint8_t* base = static_cast<uint8_t*>(ws.ptr);
@@ -618,6 +672,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   uint8_t* scal = wa + (a_in_place ? 0 : pieces * a_bytes);
   unsigned int* amax_bits = reinterpret_cast<unsigned int*>(scal);  // [2]
   float* fscal = reinterpret_cast<float*>(scal + 16);               // sA, dA, sB, dB
+  float* partial = part_bytes ? reinterpret_cast<float*>(scal + 256) : nullptr;
 
   int out_kind;
   switch (v) {
@@ -670,19 +725,19 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   switch (v) {
     case COMPAR_V_TC_TF32:
       return run_tc<COMPAR_V_TC_TF32>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, g, num_sms, s);
+                                      nullptr, nullptr, plan, partial, g, num_sms, s);
     case COMPAR_V_TC_BF16:
       return run_tc<COMPAR_V_TC_BF16>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, g, num_sms, s);
+                                      nullptr, nullptr, plan, partial, g, num_sms, s);
     case COMPAR_V_TC_FP8:
       return run_tc<COMPAR_V_TC_FP8>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                     dqa, dqb, g, num_sms, s);
+                                     dqa, dqb, plan, partial, g, num_sms, s);
     case COMPAR_V_SPLIT3:
       return run_tc<COMPAR_V_SPLIT3>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr, nullptr,
-                                     nullptr, g, num_sms, s);
+                                     nullptr, plan, partial, g, num_sms, s);
     default:
-      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr, g,
-                                     num_sms, s);
+      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr,
+                                     plan, partial, g, num_sms, s);
   }
 }
 

@@ -185,6 +185,21 @@ def test_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 6])
+def test_split_k_few_tiles_with_alpha_beta(ctx, v):
+    """Few output tiles and a long K: the tensor-core variants split K over
+    the SMs (partials reduced afterwards, beta applied once)."""
+    m, n, k = 100, 300, 2048
+    A = W.integer_matrix(m, k, seed=27, bound=2)
+    B = W.integer_matrix(k, n, seed=28, bound=2)
+    C0 = W.integer_matrix(m, n, seed=29)
+    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
+    ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
+    # small integers are exact in every format (fp8 scaling of 2 -> 448 too)
+    tol = 1e-3 if v == 4 else TOL_F32
+    assert N.rel_frobenius(got, ref) <= tol
+
+
 def test_k_zero_scales_c(ctx):
     from gpu_util import dev, host
     import torch
