@@ -75,10 +75,11 @@ enum {
     COMPAR_V_TC_BF16 = 3,     /* tcgen05 kind::f16 (bf16 operands)          */
     COMPAR_V_TC_FP8 = 4,      /* tcgen05 kind::f8f6f4 (E4M3 operands)       */
     COMPAR_V_SPLIT3 = 5,      /* 3xBF16 split on tcgen05 (FP32 accuracy)    */
-    COMPAR_V_SPLIT6 = 6,      /* 6-product 3-piece bf16 split on tcgen05
-                                 (below-FP32-SIMT error level)              */
-    COMPAR_V_COUNT = 7,
-    COMPAR_V_GROUPED = 7      /* persistent grouped kernel (batched only)   */
+    COMPAR_V_GROUPED = 6,     /* persistent grouped kernel (batched only)   */
+    COMPAR_V_SPLIT6 = 7,      /* 6-product 3-piece bf16 split on tcgen05
+                                 (at or below the FP32 SIMT error level)    */
+    COMPAR_V_COUNT = 8        /* ids 0 .. COUNT-1; ids never change once
+                                 assigned, new variants take new ids        */
 };
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -216,7 +217,8 @@ int compar_set_selector_mode(compar_ctx_t ctx, int mode);
 /* Variant chosen by the most recent compar_gemm call (-1 before any). */
 int compar_last_variant(compar_ctx_t ctx);
 
-/* Number of variants and their names (static strings; NULL if out of range). */
+/* Number of variant ids (COMPAR_V_COUNT; id 6, the grouped kernel, runs
+ * batched calls only) and their names (static strings; NULL if out of range). */
 int compar_variant_count(void);
 const char* compar_variant_name(int variant_id);
 
@@ -264,20 +266,21 @@ int compar_selector_save(compar_ctx_t ctx, const char* path);
 
 /* ---------------------------------------------------------------- learned cost model */
 
-/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 14, ReLU)
+/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 16, ReLU)
  * per ensemble member (4 members).  Inputs (features of a call):
  * log2 M, log2 N, log2 K, one-hot dtype (f32, bf16, f8), log10 tol,
  * log2 batch.  Outputs: for variant v (0..COMPAR_V_COUNT-1) output v is log2 of the run
- * time in ms and output COMPAR_V_COUNT+v log10 of the relative error.  The paper's runtime
+ * time in ms and output COMPAR_V_COUNT+v log10 of the relative error (the
+ * outputs of id 6, the batched-only grouped kernel, are never trained).  The paper's runtime
  * chooses variants with performance models it calls machine-learning models
  * and expects better-trained models to choose better (Sec. 3.2, Sec. 5).
  * Parameters of one member, float32, in this order: W1[64][8] b1[64]
- * W2[64][64] b2[64] W3[14][64] b3[14] (weights stored out x in). */
+ * W2[64][64] b2[64] W3[16][64] b3[16] (weights stored out x in). */
 int compar_mlp_param_count(void);
 
 /* Forward pass on the GPU for `members` parameter sets (host array
  * members x param_count) over `rows` raw (already standardised) feature rows
- * (host, rows x 8); Y (host) receives members x rows x 14.  Synchronous. */
+ * (host, rows x 8); Y (host) receives members x rows x 16.  Synchronous. */
 int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
                        const float* X, int rows, float* Y);
 
@@ -286,7 +289,7 @@ int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
  * by backpropagation, Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected,
  * step counter starting at step0 >= 1).  All arrays are HOST arrays:
  * params/adam_m/adam_v (members x param_count, updated in place), X (rows x
- * 8), T and mask (rows x 12), batch_idx (members x steps x batch row indices,
+ * 8), T and mask (rows x 16), batch_idx (members x steps x batch row indices,
  * batch <= 128).  When `grads` is non-NULL, steps must be 1: the gradients of
  * the first mini-batch are written to grads (members x param_count) and
  * params are left unchanged.  loss (nullable) receives members x steps batch

@@ -19,12 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libcompar.so")
 # dtypes / statuses / variant ids (values of include/compar.h)
 F32, BF16, F8E4M3 = 0, 1, 2
 OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_IO, ERR_NO_VARIANT = 0, -1, -2, -3, -4, -5, -6
-V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3, V_SPLIT6 = 0, 1, 2, 3, 4, 5, 6
-V_GROUPED = 7
-NUM_VARIANTS = 7
+V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3 = 0, 1, 2, 3, 4, 5
+V_GROUPED = 6      # batched calls only
+V_SPLIT6 = 7
+NUM_VARIANTS = 8   # ids 0 .. 7 (id 6 never runs a single call)
 MLP_OUTPUTS = 2 * NUM_VARIANTS   # log2 time and log10 error per variant
 VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16",
-                 "split-6xbf16"]
+                 "grouped", "split-6xbf16"]
 
 
 class ComparError(RuntimeError):

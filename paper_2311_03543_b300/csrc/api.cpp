@@ -52,7 +52,9 @@ void Workspace::release() {
 
 static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",
                                       "tc-bf16",   "tc-fp8",   "split-3xbf16",
-                                      "split-6xbf16", "grouped"};
+                                      "grouped",   "split-6xbf16"};
+static_assert(sizeof(kVariantNames) / sizeof(kVariantNames[0]) == COMPAR_V_COUNT,
+              "one name per variant id");
 
 static double default_tol(double tol) { return tol > 0 ? tol : 1e-5; }
 
@@ -459,7 +461,7 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_
 }
 
 int compar_force_variant(compar_ctx_t ctx, int variant_id) {
-  if (!ctx || variant_id < -1 || variant_id > COMPAR_V_GROUPED) return COMPAR_ERR_INVALID;
+  if (!ctx || variant_id < -1 || variant_id >= COMPAR_V_COUNT) return COMPAR_ERR_INVALID;
   ctx->forced = variant_id;
   return COMPAR_OK;
 }
@@ -492,7 +494,7 @@ int compar_last_variant(compar_ctx_t ctx) { return ctx ? ctx->last_variant : COM
 int compar_variant_count(void) { return kNumVariants; }
 
 const char* compar_variant_name(int v) {
-  return (v >= 0 && v <= COMPAR_V_GROUPED) ? kVariantNames[v] : nullptr;
+  return (v >= 0 && v < COMPAR_V_COUNT) ? kVariantNames[v] : nullptr;
 }
 
 int compar_variant_supported(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,

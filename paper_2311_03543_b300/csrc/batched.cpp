@@ -417,7 +417,8 @@ extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_pro
   if (count == 0) return COMPAR_OK;
   tol = tol > 0 ? tol : 1e-5;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (ctx->forced >= 0 && ctx->forced < COMPAR_V_COUNT) return run_loop(ctx, count, probs, tol, s);
+  if (ctx->forced >= 0 && ctx->forced != COMPAR_V_GROUPED)
+    return run_loop(ctx, count, probs, tol, s);
   int cfg = 1;
   auto it = ctx->batched_cfg.find(signature(count, probs, tol));
   if (it != ctx->batched_cfg.end()) cfg = it->second;

@@ -17,7 +17,7 @@
 
 namespace compar {
 
-constexpr int kNumVariants = COMPAR_V_COUNT;  // single-call variants 0..6
+constexpr int kNumVariants = COMPAR_V_COUNT;  // variant ids 0..7 (6: batched only)
 constexpr int kNumFeatures = 8;
 constexpr int kHidden = 64;
 constexpr int kOutputs = 2 * kNumVariants;  // log time, log error per variant

@@ -15,7 +15,7 @@ namespace compar {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'M', 'P', 'R', 'S', 'E', 'L', '1'};
-constexpr uint32_t kVersion = 2;  // 2: seven variants (14 MLP outputs)
+constexpr uint32_t kVersion = 3;  // 3: variant ids 0..7 (16 MLP outputs)
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
   uint64_t h = 1469598103934665603ull;

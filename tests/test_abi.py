@@ -48,6 +48,24 @@ def test_host_only_queries():
     assert cp.compar_status_string(12345).decode() == "unknown status"
 
 
+def test_variant_ids_are_stable():
+    # ids 0-5 and 6 (grouped, batched only) as first assigned; later variants
+    # take new ids
+    assert [cp.compar_variant_name(i).decode() for i in range(7)] == [
+        "naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16", "grouped"]
+    assert cp.compar_variant_name(7).decode() == "split-6xbf16"
+    assert (cp.V_GROUPED, cp.V_SPLIT6) == (6, 7)
+    h = cp.Context.host()
+    try:
+        assert not h.supported(cp.V_GROUPED, 64, 64, 64, cp.F32)   # never a single call
+        assert h.supported(cp.V_SPLIT6, 64, 64, 64, cp.F32)
+        assert cp.compar_force_variant(h.handle, cp.V_GROUPED) == cp.OK
+        assert cp.compar_force_variant(h.handle, cp.NUM_VARIANTS) == cp.ERR_INVALID
+        assert cp.compar_force_variant(h.handle, -1) == cp.OK
+    finally:
+        h.close()
+
+
 def test_null_context_is_rejected():
     assert cp.compar_gemm(None, 1, 1, 1, cp.F32, 0.0, None, None, None, None) == cp.ERR_INVALID
     assert cp.compar_force_variant(None, 1) == cp.ERR_INVALID
