@@ -133,6 +133,21 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
                 compar_dtype_t dtype, double tol, const void* A,
                 const void* B, float* C, void* stream);
 
+/* The same GEMM on HOST matrices (no counterpart in the paper, whose tasks
+ * received host data through StarPU's data management, Sec. 2.2): A (m x k),
+ * B (k x n) and C (m x n, float32) are host pointers, row-major contiguous;
+ * page-locked memory makes the transfers asynchronous.  The library uploads
+ * B, then A (and C when beta != 0) in row panels on its own copy streams,
+ * runs one selected-variant GEMM per panel on `stream` and downloads each
+ * panel of C as soon as it is done, so transfers overlap the products; two
+ * sets of context-owned device buffers let consecutive calls overlap too.
+ * Ordering: A and B are read from the moment of the call (they must be
+ * ready in host memory then, not merely by the time `stream` gets there);
+ * C is in host memory once `stream` reaches the end of the call.  Errors
+ * as compar_gemm. */
+int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
+                     double tol, const void* A, const void* B, float* C, void* stream);
+
 /* One problem of a batched call.  Leading dimensions are in elements and must
  * be >= the row length (lda >= k, ldb >= n, ldc >= n). */
 typedef struct {

@@ -63,6 +63,7 @@ SIGNATURES = {
     "compar_status_string": (ctypes.c_char_p, [_i]),
     "compar_last_error": (ctypes.c_char_p, []),
     "compar_gemm": (_i, [_vp, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _vp]),
+    "compar_gemm_host": (_i, [_vp, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _vp]),
     "compar_gemm_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp]),
     "compar_force_variant": (_i, [_vp, _i]),
     "compar_set_scalars": (_i, [_vp, _f, _f]),
@@ -261,6 +262,31 @@ class Context:
         rc = compar_gemm(self.handle, m, n, k, dt, float(tol), A.data_ptr(), B.data_ptr(),
                          C.data_ptr(), _stream_handle(stream))
         return _status(rc, "compar_gemm")
+
+    def gemm_host(self, A, B, C, tol=0.0, stream=None, dtype=None):
+        """The same on host matrices: A, B, C CPU torch tensors or NumPy
+        arrays (C float32), row-major contiguous; pinned tensors transfer
+        asynchronously.  C is ready once `stream` passes the call."""
+        def ptr(x):
+            if hasattr(x, "data_ptr"):
+                if x.is_cuda or not x.is_contiguous():
+                    raise ValueError("host tensors must be CPU and contiguous")
+                return x.data_ptr()
+            if not x.flags["C_CONTIGUOUS"]:
+                raise ValueError("arrays must be C-contiguous")
+            return x.ctypes.data
+        m, k = A.shape
+        k2, n = B.shape
+        if k != k2 or tuple(C.shape) != (m, n):
+            raise ValueError("shape mismatch")
+        if dtype is None:
+            if hasattr(A, "data_ptr"):
+                dtype = torch_dtype_code(A)
+            else:   # NumPy: float32, bf16 bit patterns (uint16) or E4M3 codes (uint8)
+                dtype = {"float32": F32, "uint16": BF16, "uint8": F8E4M3}[str(A.dtype)]
+        rc = compar_gemm_host(self.handle, m, n, k, dtype, float(tol), ptr(A), ptr(B), ptr(C),
+                              _stream_handle(stream))
+        return _status(rc, "compar_gemm_host")
 
     def gemm_ptr(self, m, n, k, dtype, tol, a_ptr, b_ptr, c_ptr, stream_handle):
         return compar_gemm(self.handle, m, n, k, dtype, float(tol), a_ptr, b_ptr, c_ptr,

@@ -413,6 +413,7 @@ int compar_terminate(compar_ctx_t ctx) {
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   ctx->prof.release();
   batched_release(ctx);
+  hostio_release(ctx);
   mlp_release(ctx);
   ctx->ws.release();
   if (ctx->guard.err_word) cudaFree(ctx->guard.err_word);
@@ -458,6 +459,26 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_
   c.scale_a = ctx->scale_a;
   c.scale_b = ctx->scale_b;
   return gemm_call(ctx, c, static_cast<cudaStream_t>(stream));
+}
+
+int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
+                     double tol, const void* A, const void* B, float* C, void* stream) {
+  if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
+  if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
+  int rc = check_ptrs(m, n, k, A, B, C);
+  if (rc != COMPAR_OK) return rc;
+  if (m == 0 || n == 0) return COMPAR_OK;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.dtype = dtype;
+  c.tol = default_tol(tol);
+  c.alpha = ctx->alpha;
+  c.beta = ctx->beta;
+  c.scale_a = ctx->scale_a;
+  c.scale_b = ctx->scale_b;
+  return gemm_host(ctx, c, A, B, C, static_cast<cudaStream_t>(stream));
 }
 
 int compar_force_variant(compar_ctx_t ctx, int variant_id) {

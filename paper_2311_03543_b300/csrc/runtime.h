@@ -159,6 +159,7 @@ struct compar_ctx {
     int64_t explored = 0, retrains = 0;
   } online;
   void* batched_state = nullptr;
+  void* hostio_state = nullptr;  // device buffers and streams of compar_gemm_host
   // MLP device buffers (selector inference / training), owned here.
   void* mlp_dev = nullptr;
 };
@@ -169,4 +170,8 @@ int mlp_predict(compar_ctx* ctx, const float* feats, int rows, float* out_host);
 void mlp_release(compar_ctx* ctx);
 // Implemented in batched.cpp
 void batched_release(compar_ctx* ctx);
+// Implemented in hostio.cpp
+int gemm_host(compar_ctx* ctx, GemmCall base, const void* hA, const void* hB, float* hC,
+              cudaStream_t s);
+void hostio_release(compar_ctx* ctx);
 }  // namespace compar
