@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--selector", default=os.path.join(ROOT, "paper_2311_03543_b300",
                                                         "selector_default.bin"))
     ap.add_argument("--detail", default=None, help="write per-shape detail JSON here")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="CPU oracle beside the selected GPU variant on 256^3 .. 8192^3")
     return ap.parse_args()
 
 
@@ -158,6 +160,46 @@ def cpu_oracle_sample(budget_s=15.0, shapes=None):
             "kind": "oracle",
             "sample": f"FP64 triple-loop oracle on squares n={done[0]}..{done[-1]} step 64 "
                       f"({len(done)} GEMMs, {t_total:.1f} s)"}
+
+
+def cpu_table():
+    """FP64 oracle (all host cores) beside the library's selected variant at
+    tol 1e-5 on 256^3, 1024^3, 4096^3 (median of 3 CPU runs) and 8192^3 (one
+    CPU run); GPU: median of 20 calls, CUDA events, inputs resident."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2311_03543_b300 as cp
+    import workloads as W
+    torch.cuda.set_device(0)
+    rows = []
+    with cp.Context(0) as ctx:
+        for n in (256, 1024, 4096, 8192):
+            A = W.uniform(n, n, seed=2); B = W.uniform(n, n, seed=3)
+            reps = 1 if n == 8192 else 3
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                oracle.gemm(A, B)
+                ts.append(time.perf_counter() - t0)
+            t_cpu = sorted(ts)[len(ts) // 2]
+            dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            C = torch.empty((n, n), device="cuda")
+            ctx.gemm(dA, dB, C, tol=TOL)
+            v = ctx.last_variant()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(40)]
+            for i in range(20):
+                ev[2 * i].record()
+                ctx.gemm(dA, dB, C, tol=TOL)
+                ev[2 * i + 1].record()
+            torch.cuda.synchronize()
+            t_gpu = sorted(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(20))[10] / 1e3
+            fl = 2.0 * n ** 3
+            rows.append({"n": n, "cpu_s": t_cpu, "cpu_tflops": fl / t_cpu / 1e12,
+                         "cpu_cores": oracle.num_threads(), "gpu_variant": cp.VARIANT_NAMES[v],
+                         "gpu_s": t_gpu, "gpu_tflops": fl / t_gpu / 1e12, "speedup": t_cpu / t_gpu})
+            print(json.dumps(rows[-1]), flush=True)
+    return rows
 
 
 def run_reference(args):
@@ -293,6 +335,9 @@ def main():
             print(json.dumps({"batched_512": measure_batched(ctx, cp, W, torch,
                                                              torch.device("cuda", 0))}),
                   flush=True)
+        return 0
+    if args.cpu_table:
+        print(json.dumps({"cpu_vs_gpu": cpu_table()}), flush=True)
         return 0
     if args.peaks or args.variants:
         import torch
