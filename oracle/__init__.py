@@ -18,6 +18,9 @@ Parts:
   loss, backward, Adam.
 * :mod:`oracle.selector_ref` — exhaustive (measure-every-variant) selection
   and the regret of a pick.
+* :mod:`oracle.stencil_ref` — the thermal 2-D stencil (the hotspot-like
+  second component): one explicit heat-equation step, array form and
+  cell-by-cell form, float64.
 
 Pinned by ``tests/test_oracle_*.py`` against closed forms, exact integer
 arithmetic, exact rational brute force, library routines and finite

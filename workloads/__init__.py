@@ -22,6 +22,9 @@ Workloads (M, N, K):
   integers in [16, 4096], dtype uniform over {f32, bf16, fp8}, tolerance from
   {1e-5 (f32 only), 1e-3, 1e-1} (seed 12345); ``heldout_tight_contexts()``:
   float32 only at tolerance 1e-6, same shape law (seed 24680).
+* thermal stencil: ``stencil_inputs()`` (seeded chip: temperature, power map
+  with hot blocks), ``STENCIL_PARAMS``, ``stencil_contexts()`` (grid sizes
+  64 - 8192, 1 - 1000 iterations; training and held-out seeds differ).
 """
 import math
 
@@ -138,6 +141,38 @@ def heldout_tight_contexts(count=300, seed=24680, lo=16, hi=4096):
 def training_contexts(count, seed=777, lo=16, hi=8192):
     """Selector training contexts (seed disjoint from the held-out set)."""
     return heldout_contexts(count=count, seed=seed, lo=lo, hi=hi)
+
+
+# ---------------------------------------------------------------- stencil
+# Thermal-stencil workload (the hotspot-like component; Table 2 lists Hotspot
+# on square grids 64 - 8192).  Rodinia's input files are not available, so a
+# seeded chip stands in: ambient 80, an initial temperature 80 + U(0, 20), a
+# background power U(0, 1) and a few hot rectangular blocks of U(5, 20).
+STENCIL_PARAMS = {"c": 0.2, "gx": 0.5, "gy": 0.5, "gz": 0.01, "amb": 80.0}
+STENCIL_HEADLINE = (8192, 8192, 100)   # rows, cols, iterations
+
+
+def stencil_inputs(rows, cols, seed, hot_blocks=6):
+    """(T0, P) float32 arrays of shape rows x cols."""
+    g = rng(seed)
+    T0 = (80.0 + g.uniform(0.0, 20.0, size=(rows, cols))).astype(np.float32)
+    P = g.uniform(0.0, 1.0, size=(rows, cols))
+    for _ in range(hot_blocks):
+        h = max(1, int(rows * g.uniform(0.05, 0.2)))
+        w = max(1, int(cols * g.uniform(0.05, 0.2)))
+        r0 = int(g.integers(0, max(1, rows - h + 1)))
+        c0 = int(g.integers(0, max(1, cols - w + 1)))
+        P[r0:r0 + h, c0:c0 + w] += g.uniform(5.0, 20.0)
+    return T0, P.astype(np.float32)
+
+
+def stencil_contexts(count, seed, lo=64, hi=8192, it_lo=1, it_hi=1000):
+    """(rows, cols, iters): sizes log-uniform in [lo, hi], iterations
+    log-uniform in [it_lo, it_hi]."""
+    g = rng(seed)
+    rc = _log_uniform_int(g, lo, hi, (count, 2))
+    it = _log_uniform_int(g, it_lo, it_hi, count)
+    return [(int(r), int(c), int(i)) for (r, c), i in zip(rc, it)]
 
 
 def sample_rows(m, count, seed):
