@@ -395,11 +395,72 @@ int compar_record_add(compar_ctx_t ctx, const compar_record_t* recs,
                       int64_t count);
 int compar_record_clear(compar_ctx_t ctx);
 
+/* ---------------------------------------------------------------- stencil */
+
+/* The second component behind the same runtime: a thermal 2-D stencil (the
+ * paper evaluates Rodinia's Hotspot, Table 2, with CUDA and OpenMP variants;
+ * the computation is read here as the explicit step of the 2-D heat
+ * equation).  One step updates every cell of a rows x cols grid:
+ *   T'[i][j] = T[i][j] + c * ( P[i][j]
+ *                + (T[i-1][j] + T[i+1][j] - 2 T[i][j]) * gy
+ *                + (T[i][j-1] + T[i][j+1] - 2 T[i][j]) * gx
+ *                + (amb - T[i][j]) * gz )
+ * with a neighbour outside the grid replaced by the cell itself (insulated
+ * edge).  Stable for c * (2 gx + 2 gy + gz) <= 1. */
+typedef struct {
+    float c;              /* time step / heat capacity                     */
+    float gx, gy, gz;     /* conductance to column / row neighbours, ambient */
+    float amb;            /* ambient temperature                           */
+} compar_stencil_params_t;
+
+/* Stencil variant ids (their own id space). */
+enum {
+    COMPAR_S_NAIVE = 0,   /* one thread per cell, one launch per step       */
+    COMPAR_S_TILED = 1,   /* shared-memory temporal blocking, 8 steps/launch */
+    COMPAR_S_TMA = 2,     /* the same with TMA region loads                 */
+    COMPAR_S_COUNT = 3
+};
+
+/* `iters` steps from T_in into T_out (device float32 grids, row-major
+ * contiguous, rows x cols; P the power grid).  T_in and P are not written;
+ * T_out must not overlap T_in or P.  iters == 0 copies T_in.  The variant is
+ * the forced one, else the decision cache, else the fastest by the stencil
+ * history table (compar_stencil_measure feeds it; selector files carry it),
+ * else by a roofline prior.  Every variant computes bit-identical grids.
+ * Returns COMPAR_OK, COMPAR_ERR_INVALID (bad sizes, parameters, pointers or
+ * overlap), COMPAR_ERR_UNSUPPORTED (forced variant cannot run this grid) or
+ * COMPAR_ERR_CUDA; a TMA wait that runs out is reported through
+ * compar_check_device_error.  Scratch (one grid) comes from the context's
+ * workspace. */
+int compar_stencil(compar_ctx_t ctx, int64_t rows, int64_t cols, int iters,
+                   const compar_stencil_params_t* params, const float* T_in,
+                   const float* P, float* T_out, void* stream);
+
+/* Force stencil variant `v` (COMPAR_S_*), or clear with -1. */
+int compar_stencil_force_variant(compar_ctx_t ctx, int v);
+/* Variant used by the most recent compar_stencil call (-1 before any). */
+int compar_stencil_last_variant(compar_ctx_t ctx);
+/* Static name of stencil variant v, NULL if out of range. */
+const char* compar_stencil_variant_name(int v);
+/* Whether variant v can run a rows x cols grid (16-byte aligned grids
+ * assumed): 1 / 0, or COMPAR_ERR_INVALID. */
+int compar_stencil_supported(compar_ctx_t ctx, int v, int64_t rows, int64_t cols);
+/* The variant compar_stencil would choose (works on host-only contexts). */
+int compar_stencil_select(compar_ctx_t ctx, int64_t rows, int64_t cols, int iters);
+/* Median time (ms, CUDA events on `stream`) of `reps` runs of variant v
+ * after `warmup` runs; the result also feeds the stencil history table. */
+int compar_stencil_measure(compar_ctx_t ctx, int v, int64_t rows, int64_t cols, int iters,
+                           const compar_stencil_params_t* params, const float* T_in,
+                           const float* P, float* T_out, int warmup, int reps,
+                           void* stream, float* median_ms);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Kernel timing: when on, the main GEMM kernel of every call (not its
  * operand pre-passes) is bracketed by CUDA events on the call's stream and
- * its duration added to a per-variant total.  Off by default. */
+ * its duration added to a per-variant total; for a stencil call, all its
+ * launches together.  Off by default.  Slots: 0..7 the GEMM variant ids,
+ * 8 + s the stencil variant s. */
 int compar_profile_enable(compar_ctx_t ctx, int on);
 /* Total kernel milliseconds and number of timed launches of `variant` since
  * the last reset (synchronises on the pending events). */

@@ -28,6 +28,16 @@ VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split
                  "grouped", "split-6xbf16"]
 
 
+S_NAIVE, S_TILED, S_TMA = 0, 1, 2
+NUM_STENCIL_VARIANTS = 3
+STENCIL_NAMES = ["stencil-naive", "stencil-tiled", "stencil-tma"]
+
+
+class compar_stencil_params_t(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_float), ("gx", ctypes.c_float), ("gy", ctypes.c_float),
+                ("gz", ctypes.c_float), ("amb", ctypes.c_float)]
+
+
 class ComparError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -64,6 +74,16 @@ SIGNATURES = {
     "compar_last_error": (ctypes.c_char_p, []),
     "compar_gemm": (_i, [_vp, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _vp]),
     "compar_gemm_host": (_i, [_vp, _i64, _i64, _i64, _i, _d, _vp, _vp, _vp, _vp]),
+    "compar_stencil": (_i, [_vp, _i64, _i64, _i, ctypes.POINTER(compar_stencil_params_t),
+                            _vp, _vp, _vp, _vp]),
+    "compar_stencil_force_variant": (_i, [_vp, _i]),
+    "compar_stencil_last_variant": (_i, [_vp]),
+    "compar_stencil_variant_name": (ctypes.c_char_p, [_i]),
+    "compar_stencil_supported": (_i, [_vp, _i, _i64, _i64]),
+    "compar_stencil_select": (_i, [_vp, _i64, _i64, _i]),
+    "compar_stencil_measure": (_i, [_vp, _i, _i64, _i64, _i,
+                                    ctypes.POINTER(compar_stencil_params_t), _vp, _vp, _vp,
+                                    _i, _i, _vp, ctypes.POINTER(ctypes.c_float)]),
     "compar_gemm_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp]),
     "compar_force_variant": (_i, [_vp, _i]),
     "compar_set_scalars": (_i, [_vp, _f, _f]),
@@ -287,6 +307,47 @@ class Context:
         rc = compar_gemm_host(self.handle, m, n, k, dtype, float(tol), ptr(A), ptr(B), ptr(C),
                               _stream_handle(stream))
         return _status(rc, "compar_gemm_host")
+
+    # -- thermal stencil (second component) ---------------------------------
+    @staticmethod
+    def stencil_params(c, gx, gy, gz, amb):
+        return compar_stencil_params_t(c, gx, gy, gz, amb)
+
+    def stencil(self, T_in, P, T_out, iters, params, stream=None):
+        """T_out = `iters` explicit heat steps from T_in (CUDA float32 grids)."""
+        rows, cols = T_in.shape
+        if tuple(P.shape) != (rows, cols) or tuple(T_out.shape) != (rows, cols):
+            raise ValueError("shape mismatch")
+        for t in (T_in, P, T_out):
+            if not t.is_contiguous():
+                raise ValueError("grids must be contiguous")
+        return _status(compar_stencil(self.handle, rows, cols, int(iters), ctypes.byref(params),
+                                      T_in.data_ptr(), P.data_ptr(), T_out.data_ptr(),
+                                      _stream_handle(stream)), "compar_stencil")
+
+    def stencil_force_variant(self, v):
+        return _status(compar_stencil_force_variant(self.handle, -1 if v is None else v),
+                       "stencil_force_variant")
+
+    def stencil_last_variant(self):
+        return compar_stencil_last_variant(self.handle)
+
+    def stencil_supported(self, v, rows, cols):
+        return _status(compar_stencil_supported(self.handle, v, rows, cols),
+                       "stencil_supported") == 1
+
+    def stencil_select(self, rows, cols, iters):
+        return _status(compar_stencil_select(self.handle, rows, cols, int(iters)),
+                       "stencil_select")
+
+    def stencil_measure(self, v, T_in, P, T_out, iters, params, warmup=1, reps=3, stream=None):
+        rows, cols = T_in.shape
+        out = ctypes.c_float()
+        _status(compar_stencil_measure(self.handle, v, rows, cols, int(iters),
+                                       ctypes.byref(params), T_in.data_ptr(), P.data_ptr(),
+                                       T_out.data_ptr(), warmup, reps, _stream_handle(stream),
+                                       ctypes.byref(out)), "compar_stencil_measure")
+        return out.value
 
     def gemm_ptr(self, m, n, k, dtype, tol, a_ptr, b_ptr, c_ptr, stream_handle):
         return compar_gemm(self.handle, m, n, k, dtype, float(tol), a_ptr, b_ptr, c_ptr,

@@ -50,8 +50,10 @@ struct Workspace {
 // ------------------------------------------------------------- profiling
 // Optional CUDA-event timing of the main GEMM kernel of each call (not its
 // pre-passes), accumulated per variant and resolved lazily.
+// Slots 0..7: GEMM variant ids; kStencilProfileBase + s: stencil variant s.
+constexpr int kStencilProfileBase = 8;
 struct KernelProfiler {
-  static constexpr int kSlots = 8;
+  static constexpr int kSlots = 16;
   bool on = false;
   struct Pend {
     cudaEvent_t a, b;
@@ -128,6 +130,13 @@ enum PrepassOut {
   PP_COPY = 4,
   PP_SPLIT_BF16_3P = 5
 };
+
+// Thermal stencil (stencil.cu).  `tmp` is a rows x cols scratch grid;
+// aligned16: T_in, P, T_out and tmp are 16-byte aligned.
+int stencil_launch(int v, int64_t rows, int64_t cols, int iters,
+                   const compar_stencil_params_t& prm, const float* T_in, const float* P,
+                   float* T_out, float* tmp, const DeviceGuard& g, cudaStream_t s);
+bool stencil_supported(int v, int64_t rows, int64_t cols, bool aligned16);
 
 // TMA tensor-map encoding (tma.cpp).
 bool tma_available();

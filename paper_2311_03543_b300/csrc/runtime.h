@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <map>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -116,6 +117,16 @@ struct DecisionKeyHash {
   size_t operator()(const DecisionKey& d) const;
 };
 
+// Selection state of the thermal-stencil component: forced variant, the
+// variant of the last call, a history table keyed by (variant, rows, cols,
+// iterations) and the decision cache.
+struct StencilSel {
+  int forced = -1;
+  int last = -1;
+  HistoryModel hist;
+  std::map<std::tuple<int64_t, int64_t, int>, int> decisions;
+};
+
 struct PendingTiming {  // events of a recorded compar_gemm call, resolved lazily
   cudaEvent_t start, stop;
   compar_record_t rec;
@@ -160,6 +171,7 @@ struct compar_ctx {
   } online;
   void* batched_state = nullptr;
   void* hostio_state = nullptr;  // device buffers and streams of compar_gemm_host
+  compar::StencilSel stencil;    // the second component's selection state
   // MLP device buffers (selector inference / training), owned here.
   void* mlp_dev = nullptr;
 };

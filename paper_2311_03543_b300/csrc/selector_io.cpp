@@ -1,5 +1,6 @@
 // Selector files: the persisted state of the cost models (history table,
-// error model, MLP ensemble and feature normaliser, grouped tile choice).
+// error model, MLP ensemble and feature normaliser, grouped tile choice,
+// stencil history table).
 // The paper's runtime keeps its performance models across runs; this is the
 // equivalent checkpoint.  Format (little endian):
 //   "CMPRSEL1" | u32 version | u64 payload bytes | payload | u64 FNV-1a(payload)
@@ -15,7 +16,7 @@ namespace compar {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'M', 'P', 'R', 'S', 'E', 'L', '1'};
-constexpr uint32_t kVersion = 3;  // 3: variant ids 0..7 (16 MLP outputs)
+constexpr uint32_t kVersion = 4;  // 4: + stencil history table
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
   uint64_t h = 1469598103934665603ull;
@@ -64,16 +65,10 @@ struct Reader {
   }
 };
 
-}  // namespace
-}  // namespace compar
-
-using namespace compar;
-
-extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
-  if (!ctx || !path) return COMPAR_ERR_INVALID;
-  Writer w;
-  w.put<uint32_t>(static_cast<uint32_t>(ctx->hist.table.size()));
-  for (const auto& kv : ctx->hist.table) {
+// History tables: count, then (key, running mean, M2, count) per entry.
+void put_hist(Writer& w, const HistoryModel& h) {
+  w.put<uint32_t>(static_cast<uint32_t>(h.table.size()));
+  for (const auto& kv : h.table) {
     w.put(kv.first.v);
     w.put(kv.first.dtype);
     w.put(kv.first.lm);
@@ -84,6 +79,36 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
     w.put(kv.second.m2);
     w.put(kv.second.count);
   }
+}
+
+void get_hist(Reader& r, HistoryModel& h, int num_variants) {
+  const uint32_t n = r.get<uint32_t>();
+  for (uint32_t i = 0; r.ok && i < n; ++i) {
+    HistKey k;
+    k.v = r.get<int8_t>();
+    k.dtype = r.get<int8_t>();
+    k.lm = r.get<int16_t>();
+    k.ln = r.get<int16_t>();
+    k.lk = r.get<int16_t>();
+    k.batch = r.get<int8_t>();
+    HistVal v;
+    v.mean_ms = r.get<double>();
+    v.m2 = r.get<double>();
+    v.count = r.get<int64_t>();
+    if (k.v < 0 || k.v >= num_variants || k.dtype < 0 || k.dtype > 2) r.ok = false;
+    h.table[k] = v;
+  }
+}
+
+}  // namespace
+}  // namespace compar
+
+using namespace compar;
+
+extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
+  if (!ctx || !path) return COMPAR_ERR_INVALID;
+  Writer w;
+  put_hist(w, ctx->hist);
   for (const auto& r : ctx->err.c0) for (float x : r) w.put(x);
   for (const auto& r : ctx->err.c1) for (float x : r) w.put(x);
   for (const auto& r : ctx->err.c2) for (float x : r) w.put(x);
@@ -113,6 +138,7 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
     w.put<uint64_t>(kv.first);
     w.put<int32_t>(kv.second);
   }
+  put_hist(w, ctx->stencil.hist);
 
   std::ofstream f(path, std::ios::binary | std::ios::trunc);
   if (!f) return COMPAR_ERR_IO;
@@ -145,22 +171,7 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
 
   Reader r{payload, nbytes};
   HistoryModel hist;
-  const uint32_t nh = r.get<uint32_t>();
-  for (uint32_t i = 0; r.ok && i < nh; ++i) {
-    HistKey k;
-    k.v = r.get<int8_t>();
-    k.dtype = r.get<int8_t>();
-    k.lm = r.get<int16_t>();
-    k.ln = r.get<int16_t>();
-    k.lk = r.get<int16_t>();
-    k.batch = r.get<int8_t>();
-    HistVal v;
-    v.mean_ms = r.get<double>();
-    v.m2 = r.get<double>();
-    v.count = r.get<int64_t>();
-    if (k.v < 0 || k.v >= kNumVariants || k.dtype < 0 || k.dtype > 2) r.ok = false;
-    hist.table[k] = v;
-  }
+  get_hist(r, hist, kNumVariants);
   ErrorModel err;
   for (auto& row : err.c0) for (float& x : row) x = r.get<float>();
   for (auto& row : err.c1) for (float& x : row) x = r.get<float>();
@@ -193,12 +204,16 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
     if (cfg < 0 || cfg > 4) r.ok = false;
     batched[sig] = cfg;
   }
+  HistoryModel stencil_hist;
+  get_hist(r, stencil_hist, COMPAR_S_COUNT);
   if (!r.ok || r.off != nbytes) return COMPAR_ERR_IO;
 
   ctx->hist = std::move(hist);
   ctx->err = err;
   ctx->mlp = mm;
   ctx->batched_cfg = std::move(batched);
+  ctx->stencil.hist = std::move(stencil_hist);
+  ctx->stencil.decisions.clear();
   ctx->decisions.clear();
   mlp_release(ctx);  // device copies of the old weights are stale
   return COMPAR_OK;

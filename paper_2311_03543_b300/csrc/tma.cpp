@@ -67,18 +67,25 @@ bool tma_available() {
 
 // 2-D map over a row-major matrix: `inner` contiguous elements per row,
 // `outer` rows, row pitch `ld_elems`.  Box = box_inner x box_outer elements
-// whose rows are exactly one swizzle width (64 or 128 bytes) long;
-// out-of-bounds elements read as zero.
+// whose rows are exactly one swizzle width (64 or 128 bytes) long, or, with
+// swizzle_bytes == 0, unswizzled rows of any multiple of 16 bytes up to 256
+// elements; out-of-bounds elements read as zero.
 int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, const void* base,
                   uint64_t inner, uint64_t outer, uint64_t ld_elems, uint32_t box_inner,
                   uint32_t box_outer, int swizzle_bytes) {
   if (!tma_available()) return COMPAR_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return COMPAR_ERR_INVALID;
   if ((ld_elems * elem_bytes) % 16 != 0) return COMPAR_ERR_INVALID;
-  if ((swizzle_bytes != 64 && swizzle_bytes != 128) ||
-      box_inner * elem_bytes != static_cast<uint32_t>(swizzle_bytes) || box_outer == 0 ||
-      box_outer > 256)
+  if (swizzle_bytes == 0) {
+    // unswizzled box: rows of box_inner elements, a multiple of 16 bytes
+    if (box_inner == 0 || box_inner > 256 || (box_inner * elem_bytes) % 16 != 0 ||
+        box_outer == 0 || box_outer > 256)
+      return COMPAR_ERR_INVALID;
+  } else if ((swizzle_bytes != 64 && swizzle_bytes != 128) ||
+             box_inner * elem_bytes != static_cast<uint32_t>(swizzle_bytes) || box_outer == 0 ||
+             box_outer > 256) {
     return COMPAR_ERR_INVALID;
+  }
   MapKey key;
   memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
   key.base = reinterpret_cast<uintptr_t>(base);
@@ -105,8 +112,9 @@ int tma_encode_2d(CUtensorMap* map, CUtensorMapDataType dt, int elem_bytes, cons
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = g_encode(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                                   : CU_TENSOR_MAP_SWIZZLE_64B,
+                              swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                              : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                    : CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return COMPAR_ERR_CUDA;
