@@ -13,12 +13,11 @@
 //
 //   NAIVE : one thread per cell, one launch per step, neighbours from global
 //           memory (through L1/L2); ping-pong between two device grids.
-//   TILED : temporal blocking: a CTA loads a (64+2h) x (64+2h) region of T
-//           and P into shared memory and advances it h <= 8 steps there (the
-//           valid region shrinks by one cell per step), writing the 64 x 64
-//           centre; ceil(steps / 8) launches.
-//   TMA   : TILED with the region loaded by two TMA boxes (T and P) into
-//           shared memory, completion on an mbarrier (bounded wait).
+//   TILED : temporal blocking: a CTA loads the 80 x 80 region around its
+//           64 x 64 tile into shared memory and advances it up to 8 steps
+//           there, writing the centre; ceil(steps / 8) launches.
+//   TMA   : TILED with the region loaded by one TMA box into shared memory,
+//           completion on an mbarrier (bounded wait).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -63,102 +62,141 @@ __global__ void stencil_naive_kernel(const float* __restrict__ T, const float* _
 }
 
 // ------------------------------------------------------------------ TILED / TMA
-constexpr int kTile = 64;            // output cells per side
-constexpr int kHalo = 8;             // steps per launch at most
-constexpr int kReg = kTile + 2 * kHalo;  // 80: region side
-constexpr int kBlockThreads = 256;
-constexpr int kRegionBytes = kReg * kReg * 4;
-constexpr int kTiledSmem = 3 * kRegionBytes + 64 + 128;  // T ping, T pong, P, barrier, alignment
+// A CTA owns a 64 x 64 output tile and advances the 80 x 80 region around it
+// (8-cell halo) up to 8 steps in shared memory.  The region sits in an
+// 82 x 88 buffer: one pad row above and below, 4 pad columns left and 4
+// right (row pitch 88 floats = 352 bytes, a TMA-friendly multiple of 16).
+// Thread t owns column t % 80 of the region and the 20 rows of group t / 80:
+// it keeps its 20 power values in registers and walks its column with the
+// north / centre / south values in registers, so a cell costs three shared
+// loads and one store.  Every step recomputes the whole region; cells at
+// distance d from the region border are exact for d >= steps (pad and stale
+// values only reach inward one cell per step), and the 64 x 64 centre is at
+// distance >= 8.  A cell on the grid edge takes itself as the missing
+// neighbour, so tiles on the grid edge need no halo there.
+constexpr int kTile = 64;               // output cells per side
+constexpr int kHalo = 8;                // steps per launch at most
+constexpr int kReg = kTile + 2 * kHalo; // 80: region side
+constexpr int kPitch = 88;              // buffer row pitch (floats)
+constexpr int kBufRows = kReg + 2;      // 82: region + pad row above and below
+constexpr int kColOff = 4;              // region column 0 sits at buffer column 4
+constexpr int kGroupRows = 20;          // rows per thread
+constexpr int kBlockThreads = kReg * (kReg / kGroupRows);  // 320
+constexpr int kBufBytes = kBufRows * kPitch * 4;            // 28,864
+constexpr int kTiledSmem = 2 * kBufBytes + 64 + 128;        // two buffers, barrier, alignment
 
-// Advances the region in shared memory by `steps` steps.  Region cell
-// (li, lj) is grid cell (r0 + li, c0 + lj) with r0 = tile row - kHalo.  At
-// step s the cells at distance >= s from the region border are computed
-// (their neighbours were valid after step s-1); a neighbour outside the grid
-// is the cell itself, so grid-edge cells never need a halo.
-__device__ __forceinline__ float* advance(float* Ta, float* Tb, const float* Ps, int steps,
-                                          int r0, int c0, int rows, int cols, const Coef& k) {
-  float* cur = Ta;
-  float* nxt = Tb;
-  for (int s = 1; s <= steps; ++s) {
-    const int lo = s, hi = kReg - s;  // computed region [lo, hi) in both dims
-    for (int li = lo + static_cast<int>(threadIdx.x) / 32; li < hi; li += kBlockThreads / 32) {
-      const int gi = r0 + li;
-      if (gi < 0 || gi >= rows) continue;
-      const float* row = cur + li * kReg;
-      const float* up = gi > 0 ? row - kReg : row;
-      const float* dn = gi < rows - 1 ? row + kReg : row;
-      for (int lj = lo + static_cast<int>(threadIdx.x % 32); lj < hi; lj += 32) {
-        const int gj = c0 + lj;
-        if (gj < 0 || gj >= cols) continue;
-        const float t = row[lj];
-        const float w = gj > 0 ? row[lj - 1] : t;
-        const float e = gj < cols - 1 ? row[lj + 1] : t;
-        nxt[li * kReg + lj] = cell_update(t, up[lj], dn[lj], w, e, Ps[li * kReg + lj], k);
+// Buffer (row, col) of region cell (li, lj): (li + 1, lj + kColOff).  The
+// buffer covers grid rows r0 - 1 .. r0 + 80 and columns c0 - 4 .. c0 + 83,
+// r0 / c0 the grid coordinates of region cell (0, 0).
+template <bool kEdge>
+__device__ __forceinline__ const float* advance(float* A, float* B, const float (&p)[kGroupRows],
+                                                int steps, int r0, int c0, int rows, int cols,
+                                                const Coef& k) {
+  const int lj = threadIdx.x % kReg, grp = threadIdx.x / kReg;
+  const int sc = lj + kColOff;
+  const int br0 = 1 + grp * kGroupRows;          // first buffer row of this thread
+  const int gi0 = r0 + grp * kGroupRows, gj = c0 + lj;
+  const bool w_in = !kEdge || gj > 0, e_in = !kEdge || gj < cols - 1;
+  float* cur = A;
+  float* nxt = B;
+  for (int s = 0; s < steps; ++s) {
+    const float* col = cur + br0 * kPitch + sc;
+    float tn = col[-kPitch], tc = col[0];
+#pragma unroll
+    for (int i = 0; i < kGroupRows; ++i) {
+      const float ts = col[(i + 1) * kPitch];
+      float w = col[i * kPitch - 1], e = col[i * kPitch + 1];
+      float n = tn, so = ts;
+      if (kEdge) {
+        const int gi = gi0 + i;
+        if (gi <= 0) n = tc;
+        if (gi >= rows - 1) so = tc;
+        if (!w_in) w = tc;
+        if (!e_in) e = tc;
       }
+      nxt[(br0 + i) * kPitch + sc] = cell_update(tc, n, so, w, e, p[i], k);
+      tn = tc;
+      tc = ts;
     }
     __syncthreads();
     float* tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
+  (void)rows;
   return cur;
 }
 
-// Writes the tile's centre (cells inside the grid) from the region.
-__device__ __forceinline__ void store_centre(const float* reg, float* out, int tr, int tc,
-                                             int rows, int cols) {
-  for (int li = static_cast<int>(threadIdx.x) / 32; li < kTile; li += kBlockThreads / 32) {
-    const int gi = tr + li;
-    if (gi >= rows) break;
-    for (int lj = static_cast<int>(threadIdx.x % 32); lj < kTile; lj += 32) {
-      const int gj = tc + lj;
-      if (gj < cols)
-        out[static_cast<int64_t>(gi) * cols + gj] = reg[(li + kHalo) * kReg + lj + kHalo];
-    }
+// The thread's power values (0 outside the grid).
+__device__ __forceinline__ void load_power(const float* __restrict__ P, int r0, int c0, int rows,
+                                           int cols, float (&p)[kGroupRows]) {
+  const int lj = threadIdx.x % kReg, grp = threadIdx.x / kReg;
+  const int gj = c0 + lj;
+#pragma unroll
+  for (int i = 0; i < kGroupRows; ++i) {
+    const int gi = r0 + grp * kGroupRows + i;
+    p[i] = (gi >= 0 && gi < rows && gj >= 0 && gj < cols)
+               ? __ldg(P + static_cast<int64_t>(gi) * cols + gj)
+               : 0.f;
   }
+}
+
+// Writes the tile's 64 x 64 centre (cells inside the grid).
+__device__ __forceinline__ void store_centre(const float* buf, float* out, int tr, int tc,
+                                             int rows, int cols) {
+  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kBlockThreads) {
+    const int li = idx / kTile, lj = idx % kTile;
+    const int gi = tr + li, gj = tc + lj;
+    if (gi < rows && gj < cols)
+      out[static_cast<int64_t>(gi) * cols + gj] =
+          buf[(li + kHalo + 1) * kPitch + lj + kHalo + kColOff];
+  }
+}
+
+__device__ __forceinline__ bool edge_tile(int r0, int c0, int rows, int cols) {
+  return r0 <= 0 || c0 <= 0 || r0 + kReg >= rows || c0 + kReg >= cols;
 }
 
 __global__ void __launch_bounds__(kBlockThreads)
     stencil_tiled_kernel(const float* __restrict__ T, const float* __restrict__ P,
                          float* __restrict__ out, int rows, int cols, int steps, Coef k) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  float* Ta = reinterpret_cast<float*>(smem);
-  float* Tb = Ta + kReg * kReg;
-  float* Ps = Tb + kReg * kReg;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  float* A = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                      ~static_cast<uintptr_t>(127));
+  float* B = A + kBufRows * kPitch;
   const int tr = blockIdx.y * kTile, tc = blockIdx.x * kTile;
   const int r0 = tr - kHalo, c0 = tc - kHalo;
-  for (int idx = threadIdx.x; idx < kReg * kReg; idx += kBlockThreads) {
-    const int li = idx / kReg, lj = idx % kReg;
-    const int gi = r0 + li, gj = c0 + lj;
-    float t = 0.f, p = 0.f;
-    if (gi >= 0 && gi < rows && gj >= 0 && gj < cols) {
-      const int64_t g = static_cast<int64_t>(gi) * cols + gj;
-      t = __ldg(T + g);
-      p = __ldg(P + g);
-    }
-    Ta[idx] = t;
-    Ps[idx] = p;
+  // buffer rows r0-1 .. r0+80, columns c0-4 .. c0+83 (0 outside the grid)
+  for (int idx = threadIdx.x; idx < kBufRows * kPitch; idx += kBlockThreads) {
+    const int bi = idx / kPitch, bj = idx % kPitch;
+    const int gi = r0 - 1 + bi, gj = c0 - kColOff + bj;
+    A[idx] = (gi >= 0 && gi < rows && gj >= 0 && gj < cols)
+                 ? __ldg(T + static_cast<int64_t>(gi) * cols + gj)
+                 : 0.f;
   }
+  float p[kGroupRows];
+  load_power(P, r0, c0, rows, cols, p);
   __syncthreads();
-  const float* res = advance(Ta, Tb, Ps, steps, r0, c0, rows, cols, k);
+  const float* res = edge_tile(r0, c0, rows, cols)
+                         ? advance<true>(A, B, p, steps, r0, c0, rows, cols, k)
+                         : advance<false>(A, B, p, steps, r0, c0, rows, cols, k);
   store_centre(res, out, tr, tc, rows, cols);
 }
 
 struct TmaMaps {
-  CUtensorMap t, p;
+  CUtensorMap t;
 };
 
 __global__ void __launch_bounds__(kBlockThreads)
-    stencil_tma_kernel(const __grid_constant__ TmaMaps maps, float* __restrict__ out, int rows,
-                       int cols, int steps, Coef k, int* err_word,
-                       unsigned long long budget_ns) {
+    stencil_tma_kernel(const __grid_constant__ TmaMaps maps, const float* __restrict__ P,
+                       float* __restrict__ out, int rows, int cols, int steps, Coef k,
+                       int* err_word, unsigned long long budget_ns) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // TMA writes to 128-byte aligned shared memory
-  float* Ta = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
-                                       ~static_cast<uintptr_t>(127));
-  float* Tb = Ta + kReg * kReg;
-  float* Ps = Tb + kReg * kReg;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Ps + kReg * kReg);
+  float* A = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                      ~static_cast<uintptr_t>(127));
+  float* B = A + kBufRows * kPitch;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(B + kBufRows * kPitch);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 1);
   const int tr = blockIdx.y * kTile, tc = blockIdx.x * kTile;
   const int r0 = tr - kHalo, c0 = tc - kHalo;
@@ -169,17 +207,18 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // x = c0 is a multiple of 8 elements (32 bytes); cells outside the grid
-    // read as zero and are never used
-    dev::mbar_arrive_expect_tx(bar, 2 * kRegionBytes);
-    dev::tma_load_2d(Ta, &maps.t, bar, c0, r0);
-    dev::tma_load_2d(Ps, &maps.p, bar, c0, r0);
+    // one 88 x 82 box at x = c0 - 4 (a multiple of 4 floats: 16 bytes),
+    // y = r0 - 1; cells outside the grid read as zero
+    dev::mbar_arrive_expect_tx(bar, kBufBytes);
+    dev::tma_load_2d(A, &maps.t, bar, c0 - kColOff, r0 - 1);
   }
+  float p[kGroupRows];
+  load_power(P, r0, c0, rows, cols, p);   // overlaps the box load
   const dev::WaitCtx w{abort_flag, err_word, budget_ns};
   const bool ok = dev::mbar_wait(bar, 0, w);
   __syncthreads();
   if (!ok) {
-    // let the copies land before the CTA's shared memory goes away
+    // let the copy land before the CTA's shared memory goes away
     if (threadIdx.x == 0) {
       const uint64_t t0 = dev::globaltimer_ns();
       while (!dev::mbar_try_wait(bar, 0) && dev::globaltimer_ns() - t0 < budget_ns) {
@@ -188,7 +227,9 @@ __global__ void __launch_bounds__(kBlockThreads)
     __syncthreads();
     return;
   }
-  const float* res = advance(Ta, Tb, Ps, steps, r0, c0, rows, cols, k);
+  const float* res = edge_tile(r0, c0, rows, cols)
+                         ? advance<true>(A, B, p, steps, r0, c0, rows, cols, k)
+                         : advance<false>(A, B, p, steps, r0, c0, rows, cols, k);
   store_centre(res, out, tr, tc, rows, cols);
 }
 
@@ -240,14 +281,11 @@ int stencil_launch(int v, int64_t rows64, int64_t cols64, int iters,
           attr = true;
         }
         TmaMaps maps;
-        int rc = tma_encode_2d(&maps.t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, src, cols, rows, cols,
-                               kReg, kReg, 0);
-        if (rc == COMPAR_OK)
-          rc = tma_encode_2d(&maps.p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P, cols, rows, cols,
-                             kReg, kReg, 0);
+        const int rc = tma_encode_2d(&maps.t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, src, cols, rows,
+                                     cols, kPitch, kBufRows, 0);
         if (rc != COMPAR_OK) return rc;
-        stencil_tma_kernel<<<grid, kBlockThreads, kTiledSmem, s>>>(maps, dst, rows, cols, steps,
-                                                                     k, g.err_word, g.budget_ns);
+        stencil_tma_kernel<<<grid, kBlockThreads, kTiledSmem, s>>>(
+            maps, P, dst, rows, cols, steps, k, g.err_word, g.budget_ns);
       }
     }
     COMPAR_CUDA_TRY(cudaGetLastError());
