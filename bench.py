@@ -49,6 +49,7 @@ def parse():
                          "n for n x n x n, or MxNxK")
     ap.add_argument("--no-regret", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
@@ -515,6 +516,10 @@ def main():
     if not args.no_batched and rank == 0:
         batched = measure_batched(ctx, cp, W, torch, dev)
 
+    stencil = None
+    if not args.no_stencil and rank == 0:
+        stencil = measure_stencil(ctx, cp, W, torch, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_sample()
@@ -532,7 +537,8 @@ def main():
                            "selected": {cp.VARIANT_NAMES[v]: picks.count(v)
                                         for v in sorted(set(picks))}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": launches, "regret_pct": regret, "batched_512": batched}
+                "gpu_launches": launches, "regret_pct": regret, "batched_512": batched,
+                "stencil": stencil}
         print(json.dumps(line), flush=True)
         if args.detail:
             with open(args.detail, "w") as f:
@@ -618,6 +624,56 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
             "ms_per_gemm_launches": ms_loop,
             "tflops_per_gemm_launches": flops / (ms_loop / 1e3) / 1e12,
             "autotune_ms": dict(zip(names, tuned_ms))}
+
+
+def measure_stencil(ctx, cp, W, torch, dev, reps=5):
+    """The thermal-stencil component on its headline workload (8192 x 8192
+    grid, 100 steps, seeded chip on the device): the selected variant timed
+    over `reps` calls after two warm-ups (CUDA events; three grids of 268 MB,
+    larger than L2), every variant timed for context, and the roofline of the
+    selected one: HBM for the naive variant (12 bytes per cell and step), the
+    shared-memory pipe for temporal blocking (three 4-byte loads and one store
+    per cell and step over the 80 x 80 region of each 64 x 64 tile), against
+    148 SMs x 128 bytes per clock x 2032 MHz = 38.5 TB/s."""
+    rows, cols, iters = W.STENCIL_HEADLINE
+    prm = cp.Context.stencil_params(**W.STENCIL_PARAMS)
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    T = torch.rand((rows, cols), generator=g, device=dev) * 20 + 80
+    P = torch.rand((rows, cols), generator=g, device=dev)
+    out = torch.empty_like(T)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.stencil(T, P, out, iters, prm)
+    chosen = ctx.stencil_last_variant()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.stencil(T, P, out, iters, prm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    per_variant = {cp.STENCIL_NAMES[v]: ctx.stencil_measure(v, T, P, out, iters, prm, warmup=1,
+                                                            reps=3)
+                   for v in range(cp.NUM_STENCIL_VARIANTS) if ctx.stencil_supported(v, rows, cols)}
+    cell_steps = float(rows) * cols * iters
+    if chosen == cp.S_NAIVE:
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": cell_steps * 12 / (ms / 1e3) / 1e9}
+        try:
+            roof["peak"] = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+            roof["peak_source"] = "measured copy bandwidth (MEASURED_PEAKS.json)"
+        except (OSError, ValueError, KeyError):
+            roof["peak"], roof["peak_source"] = 6400.0, "fallback 6.4 TB/s"
+    else:
+        region = (80.0 * 80.0) / (64.0 * 64.0)
+        roof = {"bound": "smem", "unit": "TB/s",
+                "achieved": cell_steps * region * 16 / (ms / 1e3) / 1e12, "peak": 38.5,
+                "peak_source": "derived: 148 SMs x 128 B/clock x 2032 MHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return {"workload": f"thermal stencil {rows}x{cols}, {iters} steps, seeded chip",
+            "chosen": cp.STENCIL_NAMES[chosen], "ms": ms,
+            "gcells_per_s": cell_steps / (ms / 1e3) / 1e9, "variants_ms": per_variant,
+            "roofline": roof}
 
 
 def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):

@@ -15,7 +15,9 @@ run it, ``compar_measure`` times the variant (one record per timed run) and
 ``compar_residual_check`` labels its relative error (one more record).  The
 MLP ensemble is then trained by the library's own CUDA kernels
 (``compar_selector_train``); the history table is filled by the same
-measurements.  Everything runs through the C ABI; nothing here computes.
+measurements.  The thermal-stencil component's history table is filled by
+timing its variants on 150 seeded stencil contexts (grids 64 - 8192, 1 - 1000
+steps).  Everything runs through the C ABI; nothing here computes.
 """
 import argparse
 import os
@@ -82,6 +84,25 @@ def collect(ctx, cp, torch, contexts, reps, dev, log=print, budget_s=None):
     return n_rec
 
 
+def collect_stencil(ctx, cp, torch, contexts, reps, dev, log=print):
+    """Time every stencil variant on each (rows, cols, iters) context; the
+    measurements feed the context's stencil history table."""
+    import workloads as W
+    prm = cp.Context.stencil_params(**W.STENCIL_PARAMS)
+    t0 = time.time()
+    for i, (rows, cols, iters) in enumerate(contexts):
+        g = torch.Generator(device=dev)
+        g.manual_seed(3000 + i)
+        T = torch.rand((rows, cols), generator=g, device=dev) * 20 + 80
+        P = torch.rand((rows, cols), generator=g, device=dev)
+        out = torch.empty_like(T)
+        for v in range(cp.NUM_STENCIL_VARIANTS):
+            if ctx.stencil_supported(v, rows, cols):
+                ctx.stencil_measure(v, T, P, out, iters, prm, warmup=1, reps=reps)
+        if i % 20 == 0:
+            log(f"[train_selector] stencil {i}/{len(contexts)} contexts, {time.time() - t0:.0f} s")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2311_03543_b300",
@@ -93,6 +114,8 @@ def main(argv=None):
     ap.add_argument("--budget-s", type=float, default=None)
     ap.add_argument("--random-count", type=int, default=1500,
                     help="seeded random training contexts added to the workloads' shapes")
+    ap.add_argument("--stencil-count", type=int, default=150,
+                    help="seeded stencil training contexts (grids 64-8192, 1-1000 steps)")
     args = ap.parse_args(argv)
     import torch
     import paper_2311_03543_b300 as cp
@@ -102,6 +125,8 @@ def main(argv=None):
         ctx.record_enable(True)
         n = collect(ctx, cp, torch, training_contexts(args.random_count), args.reps, dev,
                     budget_s=args.budget_s)
+        import workloads as W
+        collect_stencil(ctx, cp, torch, W.stencil_contexts(args.stencil_count, seed=777), 3, dev)
         t0 = time.time()
         vl = ctx.selector_train(steps=args.steps, batch=128, lr=args.lr, seed=args.seed)
         print(f"[train_selector] {n} records; trained {args.steps} steps in "
