@@ -64,8 +64,10 @@ __global__ void stencil_naive_kernel(const float* __restrict__ T, const float* _
 // ------------------------------------------------------------------ TILED / TMA
 // A CTA owns a 64 x 64 output tile and advances the 80 x 80 region around it
 // (8-cell halo) up to 8 steps in shared memory.  The region sits in an
-// 82 x 88 buffer: one pad row above and below, 4 pad columns left and 4
-// right (row pitch 88 floats = 352 bytes, a TMA-friendly multiple of 16).
+// 82 x 92 buffer: one pad row above and below, 4 pad columns left and 8
+// right (row pitch 92 floats = 368 bytes, a TMA-friendly multiple of 16; 20
+// rows are 1840 floats = 16 banks apart, so a warp that spans two row groups
+// reads 32 different banks).
 // Thread t owns column t % 80 of the region and the 20 rows of group t / 80:
 // it keeps its 20 power values in registers and walks its column with the
 // north / centre / south values in registers, so a cell costs three shared
@@ -77,16 +79,16 @@ __global__ void stencil_naive_kernel(const float* __restrict__ T, const float* _
 constexpr int kTile = 64;               // output cells per side
 constexpr int kHalo = 8;                // steps per launch at most
 constexpr int kReg = kTile + 2 * kHalo; // 80: region side
-constexpr int kPitch = 88;              // buffer row pitch (floats)
+constexpr int kPitch = 92;              // buffer row pitch (floats)
 constexpr int kBufRows = kReg + 2;      // 82: region + pad row above and below
 constexpr int kColOff = 4;              // region column 0 sits at buffer column 4
 constexpr int kGroupRows = 20;          // rows per thread
 constexpr int kBlockThreads = kReg * (kReg / kGroupRows);  // 320
-constexpr int kBufBytes = kBufRows * kPitch * 4;            // 28,864
+constexpr int kBufBytes = kBufRows * kPitch * 4;            // 30,176
 constexpr int kTiledSmem = 2 * kBufBytes + 64 + 128;        // two buffers, barrier, alignment
 
 // Buffer (row, col) of region cell (li, lj): (li + 1, lj + kColOff).  The
-// buffer covers grid rows r0 - 1 .. r0 + 80 and columns c0 - 4 .. c0 + 83,
+// buffer covers grid rows r0 - 1 .. r0 + 80 and columns c0 - 4 .. c0 + 87,
 // r0 / c0 the grid coordinates of region cell (0, 0).
 template <bool kEdge>
 __device__ __forceinline__ const float* advance(float* A, float* B, const float (&p)[kGroupRows],
@@ -157,7 +159,7 @@ __device__ __forceinline__ bool edge_tile(int r0, int c0, int rows, int cols) {
   return r0 <= 0 || c0 <= 0 || r0 + kReg >= rows || c0 + kReg >= cols;
 }
 
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, 3)
     stencil_tiled_kernel(const float* __restrict__ T, const float* __restrict__ P,
                          float* __restrict__ out, int rows, int cols, int steps, Coef k) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   float* B = A + kBufRows * kPitch;
   const int tr = blockIdx.y * kTile, tc = blockIdx.x * kTile;
   const int r0 = tr - kHalo, c0 = tc - kHalo;
-  // buffer rows r0-1 .. r0+80, columns c0-4 .. c0+83 (0 outside the grid)
+  // buffer rows r0-1 .. r0+80, columns c0-4 .. c0+87 (0 outside the grid)
   for (int idx = threadIdx.x; idx < kBufRows * kPitch; idx += kBlockThreads) {
     const int bi = idx / kPitch, bj = idx % kPitch;
     const int gi = r0 - 1 + bi, gj = c0 - kColOff + bj;
@@ -187,7 +189,7 @@ struct TmaMaps {
   CUtensorMap t;
 };
 
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, 3)
     stencil_tma_kernel(const __grid_constant__ TmaMaps maps, const float* __restrict__ P,
                        float* __restrict__ out, int rows, int cols, int steps, Coef k,
                        int* err_word, unsigned long long budget_ns) {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // one 88 x 82 box at x = c0 - 4 (a multiple of 4 floats: 16 bytes),
+    // one 92 x 82 box at x = c0 - 4 (a multiple of 4 floats: 16 bytes),
     // y = r0 - 1; cells outside the grid read as zero
     dev::mbar_arrive_expect_tx(bar, kBufBytes);
     dev::tma_load_2d(A, &maps.t, bar, c0 - kColOff, r0 - 1);
