@@ -559,7 +559,7 @@ def measured_traffic(kernel, flops_per_launch):
     except (OSError, ValueError, KeyError):
         return None, "no ncu capture for this kernel"
     h = hashlib.sha1()
-    for f in ("gemm_tc.cu", "ptx.cuh"):
+    for f in ("gemm_tc.cu", "ptx.cuh", "epilogue.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2311_03543_b300", "csrc", f), "rb").read())
     if h.hexdigest() != rec["src_sha1"]:
         return None, "kernel changed since the ncu capture"

@@ -26,6 +26,7 @@
 #include <cstdint>
 
 #include "common.h"
+#include "epilogue.cuh"
 #include "grouped.h"
 #include "ptx.cuh"
 
@@ -39,7 +40,6 @@ constexpr int kRow = kGroupedRow;  // bytes of K per stage and operand row
 constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each half the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpi = 32 * kEpiWarps;
-constexpr int kStgPitch = 36;  // staging row pitch (floats): 16-byte rows, no bank conflicts
 constexpr int kMnBox = 64 * kRow;  // one MN-major B box: 64 columns x kRow/2 K rows of bf16
 constexpr int kChunkKB = 512 / kRow;  // promotion every 256 bf16 K elements
 constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
@@ -50,11 +50,10 @@ struct GLayout {
   static constexpr int kB = BN * kRow;        // one B piece
   static constexpr int kStage = 2 * (kA + kB);
   static constexpr int kBar = 256;
-  static constexpr int kStaging = kEpiWarps * 32 * kStgPitch * 4;  // a 32 x 32 block per warp
   static constexpr int kIndex = kMaxIndexed * 4;    // problems' tile_start values
-  static constexpr int kStagesRaw = (232448 - 1024 - kBar - kStaging - kIndex) / kStage;
+  static constexpr int kStagesRaw = (232448 - 1024 - kBar - kIndex) / kStage;
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
-  static constexpr int kSmem = 1024 + kStages * kStage + kBar + kStaging + kIndex;
+  static constexpr int kSmem = 1024 + kStages * kStage + kBar + kIndex;
   static constexpr int kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
 };
 
@@ -96,8 +95,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drainb = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* staging = reinterpret_cast<float*>(smem + S * L::kStage + L::kBar);
-  int* s_index = reinterpret_cast<int*>(smem + S * L::kStage + L::kBar + L::kStaging);
+  int* s_index = reinterpret_cast<int*>(smem + S * L::kStage + L::kBar);
   const int* s_start = count <= kMaxIndexed ? s_index : nullptr;
   if (s_start)
     for (int i = threadIdx.x; i < count; i += blockDim.x) s_index[i] = probs[i].tile_start;
@@ -252,12 +250,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------- epilogue
     // Warp w reads TMEM lane quarter w % 4 (the hardware's access rule) and
     // one half of the columns.
-    constexpr int EC = BN / 2;
+    constexpr int EC = BN / 2;       // columns of this warp's slice
+    constexpr int J = EC / 8;        // 16x256b repetitions per fragment
     const int quarter = warp & 3;
     const int cslice = (warp - 2) / 4;
     int acc_iter = 0;
     bool ok = true;
-    float* stg = staging + (warp - 2) * 32 * kStgPitch;
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
       const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
       const int local = tile - P.tile_start;
@@ -266,9 +264,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       float* const pC = P.C;
       const int64_t ldc = P.ldc;
       const float alpha = P.alpha, beta = P.beta;
-      float sum[EC];
+      // two 16-row fragments (row halves of the warp's lane quarter)
+      float sum[2][4 * J];
 #pragma unroll
-      for (int j = 0; j < EC; ++j) sum[j] = 0.f;
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4 * J; ++j) sum[h][j] = 0.f;
       const int chunks = (num_kb + kChunkKB - 1) / kChunkKB;
       for (int ch = 0; ch < chunks; ++ch, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
@@ -277,70 +278,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         dev::tc_fence_after();
-        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                               acc * BN + cslice * EC;
 #pragma unroll
-        for (int c = 0; c < EC / 32; ++c) {
-          uint32_t r[32];
-          dev::tmem_ld_32x32b_x32(t_row + c * 32, r);
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t taddr = tmem_base +
+                                 (static_cast<uint32_t>(quarter * 32 + 16 * h) << 16) +
+                                 acc * BN + cslice * EC;
+          uint32_t r[4 * J];
+          if constexpr (J == 8) dev::tmem_ld_16x256b_x8(taddr, r);
+          else dev::tmem_ld_16x256b_x4(taddr, r);
           dev::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __uint_as_float(r[j]);
+          for (int j = 0; j < 4 * J; ++j) sum[h][j] += __uint_as_float(r[j]);
         }
         dev::tc_fence_before();
         dev::mbar_arrive(&tempty[acc]);
       }
       if (!ok) break;
-      // Each 32 x 32 block goes through shared memory (lane = row there) so
-      // that a warp then stores four 128-byte row segments per instruction.
-      // Blocks wholly outside the problem are skipped.
+      // Sector-wide stores straight from the fragments; warps whose rows or
+      // columns lie wholly outside the problem store nothing.
       const int row0 = mb * kBM + quarter * 32;
-      if (row0 >= pM) continue;
-      const bool vec = (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(pC) & 15) == 0);
+      const int col0 = nb * BN + cslice * EC;
+      if (row0 >= pM || col0 >= pN) continue;
+      const bool vec2 = (ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(pC) & 7) == 0);
 #pragma unroll
-      for (int c = 0; c < EC / 32; ++c) {
-        const int col0 = nb * BN + cslice * EC + c * 32;
-        if (col0 >= pN) break;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(stg + lane * kStgPitch + 4 * q) =
-              make_float4(sum[c * 32 + 4 * q], sum[c * 32 + 4 * q + 1], sum[c * 32 + 4 * q + 2],
-                          sum[c * 32 + 4 * q + 3]);
-        __syncwarp();
-        const int sub = lane >> 3;           // row within a group of four
-        const int cc = 4 * (lane & 7);       // column offset in the block
-        const int col = col0 + cc;
-#pragma unroll 2
-        for (int rr = 0; rr < 32; rr += 4) {
-          const int r = row0 + rr + sub;
-          if (r < pM && col < pN) {
-            const float4 a = *reinterpret_cast<const float4*>(stg + (rr + sub) * kStgPitch + cc);
-            float* dst = pC + static_cast<int64_t>(r) * ldc + col;
-            if (vec && col + 3 < pN) {
-              float4 o = make_float4(alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w);
-              if (beta != 0.f) {
-                const float4 old = *reinterpret_cast<const float4*>(dst);
-                o.x = fmaf(beta, old.x, o.x);
-                o.y = fmaf(beta, old.y, o.y);
-                o.z = fmaf(beta, old.z, o.z);
-                o.w = fmaf(beta, old.w, o.w);
-              }
-              *reinterpret_cast<float4*>(dst) = o;
-            } else {
-              const float e[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                if (col + i < pN) {
-                  float v = alpha * e[i];
-                  if (beta != 0.f) v = fmaf(beta, dst[i], v);
-                  dst[i] = v;
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
-      }
+      for (int h = 0; h < 2; ++h)
+        store_frag<J>(sum[h], pC, ldc, pM, pN, row0 + 16 * h, col0, alpha, beta, vec2, lane);
     }
   }
   __syncthreads();

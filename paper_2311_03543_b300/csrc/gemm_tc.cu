@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "epilogue.cuh"
 #include "ptx.cuh"
 
 namespace compar {
@@ -137,39 +138,6 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   const int in = tile - group * per_group;
   mb = first_m + in % gsize;
   nb = in / gsize;
-}
-
-// Stores one 16-row x 64-column fragment in the 16x256b.x8 register layout:
-// v[4j + 2h + e] is row row0 + lane/4 + 8h, column col0 + 8j + 2(lane%4) + e.
-// C = alpha * v + beta * C; float2 stores (vec2: even pitch, 8-byte base).
-__device__ __forceinline__ void store_frag16x64(const float (&v)[32], float* C, int64_t ldc,
-                                                int M, int N, int row0, int col0, float alpha,
-                                                float beta, bool vec2, int lane) {
-  const int rq = lane >> 2, cq = 2 * (lane & 3);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int row = row0 + rq + 8 * h;
-    if (row >= M) continue;
-    float* crow = C + static_cast<int64_t>(row) * ldc;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int col = col0 + 8 * j + cq;
-      const float a = alpha * v[4 * j + 2 * h], b = alpha * v[4 * j + 2 * h + 1];
-      if (vec2 && col + 1 < N) {
-        float2* dst = reinterpret_cast<float2*>(crow + col);
-        float2 o = make_float2(a, b);
-        if (beta != 0.f) {
-          const float2 old = *dst;
-          o.x = fmaf(beta, old.x, o.x);
-          o.y = fmaf(beta, old.y, o.y);
-        }
-        *dst = o;
-      } else {
-        if (col < N) crow[col] = beta != 0.f ? fmaf(beta, crow[col], a) : a;
-        if (col + 1 < N) crow[col + 1] = beta != 0.f ? fmaf(beta, crow[col + 1], b) : b;
-      }
-    }
-  }
 }
 
 // Wait that ignores the CTA abort flag: used only to drain this CTA's own
@@ -454,7 +422,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         if (row_q < p.M && col_s < p.N) {
 #pragma unroll
           for (int f = 0; f < NF; ++f)
-            store_frag16x64(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
+            store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
                             col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
         }
         continue;
@@ -473,7 +441,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
         if (row_q < p.M && col_s < p.N)
-          store_frag16x64(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+          store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
                           alpha, beta, vec_out, lane);
       }
       dev::tc_fence_before();
