@@ -168,3 +168,42 @@ def test_online_exploration_stays_within_eligible_variants(hctx):
     assert all(hctx.select(2048, 2048, 2048, cp.F32, 1e-5) == first for _ in range(20))
     with pytest.raises(cp.ComparError):
         hctx.set_online(epsilon=1.5)
+
+
+def test_stencil_selection_on_host_context(hctx):
+    # roofline prior only: a long run on a big grid goes to temporal blocking,
+    # a single step to the one-launch-per-step variant; forcing overrides
+    assert hctx.stencil_select(8192, 8192, 100) in (cp.S_TILED, cp.S_TMA)
+    assert hctx.stencil_select(8192, 8192, 1) == cp.S_NAIVE
+    assert hctx.stencil_select(64, 62, 100) != cp.S_TMA          # rows not 16-byte multiples
+    hctx.stencil_force_variant(cp.S_NAIVE)
+    try:
+        assert hctx.stencil_select(8192, 8192, 100) == cp.S_NAIVE
+    finally:
+        hctx.stencil_force_variant(None)
+    assert cp.compar_stencil_select(hctx.handle, 0, 8, 1) == cp.ERR_INVALID
+    assert cp.compar_stencil_force_variant(hctx.handle, cp.NUM_STENCIL_VARIANTS) == cp.ERR_INVALID
+    assert [cp.compar_stencil_variant_name(v).decode() for v in range(cp.NUM_STENCIL_VARIANTS)] \
+        == cp.STENCIL_NAMES
+    assert cp.compar_stencil_variant_name(3) is None
+
+
+def test_stencil_history_round_trips_through_selector_file(hctx, tmp_path):
+    # the shipped selector file carries a stencil history table; saving and
+    # loading it on a host context keeps the choices
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2311_03543_b300", "selector_default.bin")
+    hctx.selector_load(path)
+    picks = [hctx.stencil_select(r, c, i) for r, c, i in [(8192, 8192, 100), (512, 512, 1000),
+                                                            (128, 128, 10), (4096, 256, 1)]]
+    out = str(tmp_path / "sel.bin")
+    hctx.selector_save(out)
+    h2 = cp.Context.host()
+    try:
+        h2.selector_load(out)
+        assert [h2.stencil_select(r, c, i) for r, c, i in [(8192, 8192, 100), (512, 512, 1000),
+                                                             (128, 128, 10), (4096, 256, 1)]] \
+            == picks
+    finally:
+        h2.close()
