@@ -200,6 +200,19 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
+@pytest.mark.parametrize("v", [2, 3, 5, 7])
+def test_partial_last_wave_with_alpha_beta(ctx, v):
+    """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
+    persistent CTAs), integer inputs, alpha and beta."""
+    m, n, k = 2560, 2304, 1024
+    A = W.integer_matrix(m, k, seed=41, bound=2)
+    B = W.integer_matrix(k, n, seed=42, bound=2)
+    C0 = W.integer_matrix(m, n, seed=43)
+    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
+    ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
 def test_k_zero_scales_c(ctx):
     from gpu_util import dev, host
     import torch
