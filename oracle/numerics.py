@@ -17,6 +17,9 @@ not from any GPU code:
 * Two-piece bf16 split (3xBF16): ``hi = bf16(x)``, ``lo = bf16(x - hi)``; the
   product is ``hi_a*hi_b + hi_a*lo_b + lo_a*hi_b`` (the ``lo*lo`` term is
   dropped).
+* TF32 (the tensor cores' 19-bit float: 8 exponent, 10 fraction bits):
+  rounding to nearest with ties away from zero; the two-piece TF32 split
+  ``hi = tf32(x)``, ``lo = tf32(x - hi)`` and its three products.
 * Relative Frobenius error ``||C - C_ref||_F / ||C_ref||_F``.
 
 All rounding that decides a bit pattern is done in float32 where the GPU
@@ -129,6 +132,39 @@ def fp8_quantize(x):
     x = np.asarray(x, dtype=np.float32)
     s = fp8_scale(x)
     return e4m3_codes((x * s).astype(np.float32)), s
+
+
+# ---------------------------------------------------------------- TF32
+def tf32_round(x):
+    """float32 -> nearest TF32 value (10 fraction bits), ties away from zero,
+    returned as float32 with the low 13 fraction bits zero.
+
+    On the binary32 pattern: the dropped part is the low 13 bits; adding half
+    of the kept unit (0x1000) to the pattern and clearing the low 13 bits
+    rounds the magnitude to nearest with ties away from zero (a carry moves
+    into the exponent as it should).  Finite inputs only.
+    """
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if not np.all(np.isfinite(x)):
+        raise ValueError("tf32_round: finite inputs only")
+    u = x.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+def split_tf32(x):
+    """Two-piece TF32 split: hi = tf32(x), lo = tf32(x - hi), as float32."""
+    x = np.asarray(x, dtype=np.float32)
+    hi = tf32_round(x)
+    lo = tf32_round((x - hi).astype(np.float32))
+    return hi, lo
+
+
+def split3_tf32_product(A, B, gemm):
+    """hi_a*hi_b + hi_a*lo_b + lo_a*hi_b of the TF32 split, float64 via `gemm`."""
+    ah, al = (p.astype(np.float64) for p in split_tf32(A))
+    bh, bl = (p.astype(np.float64) for p in split_tf32(B))
+    return gemm(ah, bh) + gemm(ah, bl) + gemm(al, bh)
 
 
 # ---------------------------------------------------------------- 3xBF16 split

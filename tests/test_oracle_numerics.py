@@ -144,6 +144,49 @@ def test_split6_product_on_exact_pieces():
     assert np.array_equal(got, oracle.gemm(A, B))
 
 
+def _tf32_by_fractions(v):
+    """Nearest value with 11 significant bits, ties away from zero (exact
+    rational arithmetic; normal float32 values)."""
+    from fractions import Fraction
+    import math
+    f = Fraction(float(v))
+    if f == 0:
+        return 0.0
+    e = math.floor(math.log2(abs(float(v))))
+    unit = Fraction(2) ** (e - 10)          # spacing of 11-bit significands
+    q = abs(f) / unit
+    n = math.floor(q)
+    if q - n >= Fraction(1, 2):
+        n += 1
+    return float(math.copysign(float(n * unit), float(v)))
+
+
+def test_tf32_round_matches_exact_rounding():
+    x = np.concatenate([W.uniform(1, 2000, seed=17).ravel(), W.normal(1, 2000, seed=18).ravel()])
+    got = N.tf32_round(x)
+    want = np.array([_tf32_by_fractions(v) for v in x], np.float64)
+    assert np.array_equal(got.astype(np.float64), want)
+
+
+def test_tf32_ties_away_and_exact_values():
+    one_half_ulp = np.float32(1.0 + 2.0 ** -11)          # halfway between 1 and 1 + 2^-10
+    assert N.tf32_round(one_half_ulp) == np.float32(1.0 + 2.0 ** -10)
+    assert N.tf32_round(-one_half_ulp) == np.float32(-(1.0 + 2.0 ** -10))
+    exact = np.float32(1.0 + 2.0 ** -10 + 2.0 ** -9)   # 11 significant bits
+    assert N.tf32_round(exact) == exact
+    assert N.tf32_round(np.float32(0.0)) == 0.0
+
+
+def test_tf32_split_reconstructs_22_bit_values():
+    x = W.uniform(64, 64, seed=19)
+    x22 = (x.view(np.uint32) & np.uint32(0xFFFFFFFC)).view(np.float32)   # 22 significant bits
+    hi, lo = N.split_tf32(x22)
+    assert np.array_equal(hi.astype(np.float64) + lo.astype(np.float64), x22.astype(np.float64))
+    hi, lo = N.split_tf32(x)
+    err = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - x.astype(np.float64))
+    assert np.all(err <= 2.0 ** -21 * np.abs(x.astype(np.float64)))
+
+
 def test_rel_frobenius_closed_forms():
     a = np.array([[3.0, 4.0]])
     assert N.rel_frobenius(a, a) == 0.0
