@@ -291,7 +291,8 @@ def measure_variants(ctx, cp, torch, dev, peaks):
     pipe = {cp.V_NAIVE: peaks["ffma_tflops"], cp.V_SIMT: peaks["ffma_tflops"],
             cp.V_TC_TF32: peaks["tf32_tflops"], cp.V_TC_BF16: peaks["bf16_tflops"],
             cp.V_TC_FP8: peaks.get("fp8_tflops") or 2 * peaks["bf16_tflops"],
-            cp.V_SPLIT3: peaks["bf16_tflops"] / 3, cp.V_SPLIT6: peaks["bf16_tflops"] / 6}
+            cp.V_SPLIT3: peaks["bf16_tflops"] / 3, cp.V_SPLIT6: peaks["bf16_tflops"] / 6,
+            cp.V_SPLIT3_TF32: peaks["tf32_tflops"] / 3}
     rows = []
     for (m, n, k) in shapes:
         g = torch.Generator(device=dev)
@@ -564,7 +565,7 @@ def measured_traffic(kernel, flops_per_launch):
     if h.hexdigest() != rec["src_sha1"]:
         return None, "kernel changed since the ncu capture"
     m, n, k = rec["shape"]
-    products = {"split-3xbf16": 3, "split-6xbf16": 6}.get(kernel, 1)
+    products = {"split-3xbf16": 3, "split-6xbf16": 6, "split-3xtf32": 3}.get(kernel, 1)
     scale = flops_per_launch / (2.0 * m * n * k * products)
     return (rec["dram_bytes_per_launch"] * scale,
             f"ncu dram read+write of one {m}x{n}x{k} launch ({rec['source']}) scaled by work "

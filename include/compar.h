@@ -78,7 +78,9 @@ enum {
     COMPAR_V_GROUPED = 6,     /* persistent grouped kernel (batched only)   */
     COMPAR_V_SPLIT6 = 7,      /* 6-product 3-piece bf16 split on tcgen05
                                  (at or below the FP32 SIMT error level)    */
-    COMPAR_V_COUNT = 8        /* ids 0 .. COUNT-1; ids never change once
+    COMPAR_V_SPLIT3_TF32 = 8, /* 3xTF32: 2-piece TF32 split, 3 kind::tf32
+                                 products                                  */
+    COMPAR_V_COUNT = 9        /* ids 0 .. COUNT-1; ids never change once
                                  assigned, new variants take new ids        */
 };
 
@@ -281,7 +283,7 @@ int compar_selector_save(compar_ctx_t ctx, const char* path);
 
 /* ---------------------------------------------------------------- learned cost model */
 
-/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 16, ReLU)
+/* The learned cost model is a 3-layer perceptron (8 -> 64 -> 64 -> 18, ReLU)
  * per ensemble member (4 members).  Inputs (features of a call):
  * log2 M, log2 N, log2 K, one-hot dtype (f32, bf16, f8), log10 tol,
  * log2 batch.  Outputs: for variant v (0..COMPAR_V_COUNT-1) output v is log2 of the run
@@ -290,12 +292,12 @@ int compar_selector_save(compar_ctx_t ctx, const char* path);
  * chooses variants with performance models it calls machine-learning models
  * and expects better-trained models to choose better (Sec. 3.2, Sec. 5).
  * Parameters of one member, float32, in this order: W1[64][8] b1[64]
- * W2[64][64] b2[64] W3[16][64] b3[16] (weights stored out x in). */
+ * W2[64][64] b2[64] W3[18][64] b3[18] (weights stored out x in). */
 int compar_mlp_param_count(void);
 
 /* Forward pass on the GPU for `members` parameter sets (host array
  * members x param_count) over `rows` raw (already standardised) feature rows
- * (host, rows x 8); Y (host) receives members x rows x 16.  Synchronous. */
+ * (host, rows x 8); Y (host) receives members x rows x 18.  Synchronous. */
 int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
                        const float* X, int rows, float* Y);
 
@@ -304,7 +306,7 @@ int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members,
  * by backpropagation, Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected,
  * step counter starting at step0 >= 1).  All arrays are HOST arrays:
  * params/adam_m/adam_v (members x param_count, updated in place), X (rows x
- * 8), T and mask (rows x 16), batch_idx (members x steps x batch row indices,
+ * 8), T and mask (rows x 18), batch_idx (members x steps x batch row indices,
  * batch <= 128).  When `grads` is non-NULL, steps must be 1: the gradients of
  * the first mini-batch are written to grads (members x param_count) and
  * params are left unchanged.  loss (nullable) receives members x steps batch
@@ -343,9 +345,10 @@ int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
 /* Exploratory picks and online fine-tunings so far. */
 int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains);
 
-/* The trained model's prediction for one call: per variant (arrays of 6)
- * the ensemble-mean run time in ms, relative error, and the ensemble std of
- * log2 time (spread, nullable).  COMPAR_ERR_UNSUPPORTED when untrained. */
+/* The trained model's prediction for one call: per variant (arrays of
+ * COMPAR_V_COUNT floats, indexed by variant id) the ensemble-mean run time in
+ * ms, relative error, and the ensemble std of log2 time (spread, nullable).
+ * COMPAR_ERR_UNSUPPORTED when untrained. */
 int compar_predict(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
                    compar_dtype_t dtype, double tol, int batch,
                    float* time_ms, float* rel_err, float* spread);
@@ -459,8 +462,8 @@ int compar_stencil_measure(compar_ctx_t ctx, int v, int64_t rows, int64_t cols, 
 /* Kernel timing: when on, the main GEMM kernel of every call (not its
  * operand pre-passes) is bracketed by CUDA events on the call's stream and
  * its duration added to a per-variant total; for a stencil call, all its
- * launches together.  Off by default.  Slots: 0..7 the GEMM variant ids,
- * 8 + s the stencil variant s. */
+ * launches together.  Off by default.  Slots: 0..COMPAR_V_COUNT-1
+ * the GEMM variant ids, COMPAR_V_COUNT + s the stencil variant s. */
 int compar_profile_enable(compar_ctx_t ctx, int on);
 /* Total kernel milliseconds and number of timed launches of `variant` since
  * the last reset (synchronises on the pending events). */

@@ -22,10 +22,11 @@ OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_IO, ERR_NO_VARIANT 
 V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3 = 0, 1, 2, 3, 4, 5
 V_GROUPED = 6      # batched calls only
 V_SPLIT6 = 7
-NUM_VARIANTS = 8   # ids 0 .. 7 (id 6 never runs a single call)
+V_SPLIT3_TF32 = 8
+NUM_VARIANTS = 9   # ids 0 .. 8 (id 6 never runs a single call)
 MLP_OUTPUTS = 2 * NUM_VARIANTS   # log2 time and log10 error per variant
 VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16",
-                 "grouped", "split-6xbf16"]
+                 "grouped", "split-6xbf16", "split-3xtf32"]
 
 
 S_NAIVE, S_TILED, S_TMA = 0, 1, 2
@@ -518,10 +519,10 @@ class Context:
         return a.value, b.value
 
     def predict(self, m, n, k, dtype=F32, tol=0.0, batch=1):
-        """MLP prediction: (time_ms[6], rel_err[6], spread[6])."""
-        t = (ctypes.c_float * 6)()
-        e = (ctypes.c_float * 6)()
-        s = (ctypes.c_float * 6)()
+        """MLP prediction: (time_ms, rel_err, spread), one entry per variant id."""
+        t = (ctypes.c_float * NUM_VARIANTS)()
+        e = (ctypes.c_float * NUM_VARIANTS)()
+        s = (ctypes.c_float * NUM_VARIANTS)()
         _status(compar_predict(self.handle, m, n, k, dtype, float(tol), batch, t, e, s), "predict")
         return list(t), list(e), list(s)
 

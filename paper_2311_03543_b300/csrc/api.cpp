@@ -52,7 +52,7 @@ void Workspace::release() {
 
 static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",
                                       "tc-bf16",   "tc-fp8",   "split-3xbf16",
-                                      "grouped",   "split-6xbf16"};
+                                      "grouped",   "split-6xbf16", "split-3xtf32"};
 static_assert(sizeof(kVariantNames) / sizeof(kVariantNames[0]) == COMPAR_V_COUNT,
               "one name per variant id");
 
@@ -76,6 +76,7 @@ bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
     case COMPAR_V_TC_FP8:
     case COMPAR_V_SPLIT3:
     case COMPAR_V_SPLIT6:
+    case COMPAR_V_SPLIT3_TF32:
       return tc_supported(v, c);
     default:
       return false;
@@ -94,7 +95,8 @@ static int launch_variant(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_
     case COMPAR_V_TC_BF16:
     case COMPAR_V_TC_FP8:
     case COMPAR_V_SPLIT3:
-    case COMPAR_V_SPLIT6: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
+    case COMPAR_V_SPLIT6:
+    case COMPAR_V_SPLIT3_TF32: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
     default: return COMPAR_ERR_UNSUPPORTED;
   }
 }

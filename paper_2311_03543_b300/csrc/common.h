@@ -50,8 +50,9 @@ struct Workspace {
 // ------------------------------------------------------------- profiling
 // Optional CUDA-event timing of the main GEMM kernel of each call (not its
 // pre-passes), accumulated per variant and resolved lazily.
-// Slots 0..7: GEMM variant ids; kStencilProfileBase + s: stencil variant s.
-constexpr int kStencilProfileBase = 8;
+// Slots 0..COMPAR_V_COUNT-1: GEMM variant ids; kStencilProfileBase + s:
+// stencil variant s.
+constexpr int kStencilProfileBase = COMPAR_V_COUNT;
 struct KernelProfiler {
   static constexpr int kSlots = 16;
   bool on = false;
@@ -61,6 +62,7 @@ struct KernelProfiler {
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Pend> pend;
+  static_assert(kStencilProfileBase + COMPAR_S_COUNT <= 16, "profiler slots");
   double total_ms[kSlots] = {};
   int64_t launches[kSlots] = {};
   cudaEvent_t begin(cudaStream_t s);
@@ -122,13 +124,15 @@ int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_
 // element idx at Y + p * (Y_lo - Y) (pieces equally spaced, Y_lo = piece 1):
 //   PP_SPLIT_BF16    hi = bf16(x), lo = bf16(x - hi)
 //   PP_SPLIT_BF16_3P hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
+//   PP_SPLIT_TF32    hi = tf32(x), lo = tf32(x - hi) (float32 pieces, RNA)
 enum PrepassOut {
   PP_F32 = 0,
   PP_BF16 = 1,
   PP_SPLIT_BF16 = 2,
   PP_E4M3 = 3,
   PP_COPY = 4,
-  PP_SPLIT_BF16_3P = 5
+  PP_SPLIT_BF16_3P = 5,
+  PP_SPLIT_TF32 = 6
 };
 
 // Thermal stencil (stencil.cu).  `tmp` is a rows x cols scratch grid;

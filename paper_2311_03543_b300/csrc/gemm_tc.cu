@@ -8,6 +8,9 @@
 //   FP8    : kind::f8f6f4 with E4M3 operands, per-tensor dequantisation
 //   SPLIT3 : 3xBF16 — A = Ahi + Alo, B = Bhi + Blo (bf16 pieces) and
 //            Ahi*Bhi + Ahi*Blo + Alo*Bhi accumulated into one FP32 TMEM tile
+//   SPLIT3_TF32 : 3xTF32 — A = Ahi + Alo, B = Bhi + Blo (TF32 pieces, kept
+//            in float32) and the three products on kind::tf32, the two small
+//            ones first, promoted after every stage
 //   SPLIT6 : 3-piece split A = Ah + Am + Al (likewise B) and the six products
 //            whose size is at least 2^-16 of Ah*Bh: Ah*Bm, Am*Bh, Ah*Bl,
 //            Am*Bm, Al*Bh first, Ah*Bh last, promoted into FP32 registers
@@ -53,19 +56,29 @@ template <>
 struct Traits<COMPAR_V_TC_TF32> {
   static constexpr Kind kind = Kind::TF32;
   static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = false;
+  static constexpr bool b_mn = false, small_first = false;
+};
+// 3xTF32: float32 pieces, 64-byte rows (16 K elements per 48 KB stage); each
+// stage is a promoted chunk with the two small products issued first, so
+// the truncating accumulator adds the leading product once per K step onto
+// a partial 2^-11 its size.
+template <>
+struct Traits<COMPAR_V_SPLIT3_TF32> {
+  static constexpr Kind kind = Kind::TF32;
+  static constexpr int elem = 4, fmt = 2, pieces = 2, BN = 256, row = 64, chunk_kb = 1, epi = 8;
+  static constexpr bool b_mn = false, small_first = true;
 };
 template <>
 struct Traits<COMPAR_V_TC_BF16> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = true;
+  static constexpr bool b_mn = true, small_first = false;
 };
 template <>
 struct Traits<COMPAR_V_TC_FP8> {
   static constexpr Kind kind = Kind::F8;
   static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = false;
+  static constexpr bool b_mn = false, small_first = false;
 };
 // 3xBF16: 64-byte rows give 48 KB stages (four of them) for a 128 x 256 tile;
 // promotion every 8 stages = 256 K elements.
@@ -73,7 +86,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
-  static constexpr bool b_mn = false;
+  static constexpr bool b_mn = false, small_first = false;
 };
 // 6-product split: three pieces per operand make 72 KB stages (three of
 // them).  Each stage is its own promoted chunk: within it the five small
@@ -83,7 +96,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT6> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 3, BN = 256, row = 64, chunk_kb = 1, epi = 8;
-  static constexpr bool b_mn = false;
+  static constexpr bool b_mn = false, small_first = true;
 };
 
 template <int V>
@@ -333,8 +346,20 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
             for (int kk = 0; kk < T::row / 32; ++kk)
               dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, 1u);
           }
+          if constexpr (P == 2 && T::small_first) {
+            // the cross products of every K step of the stage, then hi * hi
 #pragma unroll
-          for (int kk = 0; P < 3 && kk < T::row / 32; ++kk) {
+            for (int kk = 0; kk < T::row / 32; ++kk) {
+              const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(1, kk), idesc, first);
+              dev::mma<T::kind>(d_tmem, a_desc(1, kk), b_desc(0, kk), idesc, 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < T::row / 32; ++kk)
+              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, 1u);
+          }
+#pragma unroll
+          for (int kk = 0; P < 3 && !T::small_first && kk < T::row / 32; ++kk) {
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if constexpr (P == 2) {
               dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, first);
@@ -479,7 +504,8 @@ int round_up(int64_t x, int64_t m) { return static_cast<int>((x + m - 1) / m * m
 
 CUtensorMapDataType map_type(int v) {
   switch (v) {
-    case COMPAR_V_TC_TF32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    case COMPAR_V_TC_TF32:
+    case COMPAR_V_SPLIT3_TF32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     case COMPAR_V_TC_FP8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
     default: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   }
@@ -493,7 +519,10 @@ struct TcPlan {
 };
 
 TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
-  const int kelems = v == COMPAR_V_TC_FP8 ? 128 : (v == COMPAR_V_TC_BF16 ? 64 : 32);
+  const int kelems = v == COMPAR_V_TC_FP8 ? 128
+                     : v == COMPAR_V_TC_BF16 ? 64
+                     : v == COMPAR_V_SPLIT3_TF32 ? 16
+                                                 : 32;
   TcPlan p;
   p.num_kb = static_cast<int>((c.k + kelems - 1) / kelems);
   p.tiles = static_cast<int>(((c.m + kBM - 1) / kBM) * ((c.n + 255) / 256));
@@ -598,7 +627,8 @@ bool tc_supported(int v, const GemmCall& c) {
     case COMPAR_V_TC_BF16: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_BF16;
     case COMPAR_V_TC_FP8: return c.dtype == COMPAR_F32 || c.dtype == COMPAR_F8E4M3;
     case COMPAR_V_SPLIT3:
-    case COMPAR_V_SPLIT6: return c.dtype == COMPAR_F32;
+    case COMPAR_V_SPLIT6:
+    case COMPAR_V_SPLIT3_TF32: return c.dtype == COMPAR_F32;
     default: return false;
   }
 }
@@ -612,8 +642,10 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
               cudaStream_t s) {
   if (!tc_supported(v, c)) return COMPAR_ERR_UNSUPPORTED;
   if (!tma_available()) return COMPAR_ERR_UNSUPPORTED;
-  const int elem = (v == COMPAR_V_TC_TF32) ? 4 : (v == COMPAR_V_TC_FP8 ? 1 : 2);
-  const int pieces = (v == COMPAR_V_SPLIT3) ? 2 : (v == COMPAR_V_SPLIT6 ? 3 : 1);
+  const int elem = (v == COMPAR_V_TC_TF32 || v == COMPAR_V_SPLIT3_TF32) ? 4
+                   : (v == COMPAR_V_TC_FP8 ? 1 : 2);
+  const int pieces =
+      (v == COMPAR_V_SPLIT3 || v == COMPAR_V_SPLIT3_TF32) ? 2 : (v == COMPAR_V_SPLIT6 ? 3 : 1);
   const int64_t ldk = round_up(c.k, 16);  // 16-element pitch: 16-byte rows for every type
   const bool a_native = (c.dtype != COMPAR_F32 || v == COMPAR_V_TC_TF32);
   const bool a_in_place = a_native && tma_operand_ok(c.A, c.lda, elem);
@@ -648,6 +680,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     case COMPAR_V_TC_BF16: out_kind = (c.dtype == COMPAR_F32) ? PP_BF16 : PP_COPY; break;
     case COMPAR_V_TC_FP8: out_kind = fp8_from_f32 ? PP_E4M3 : PP_COPY; break;
     case COMPAR_V_SPLIT3: out_kind = PP_SPLIT_BF16; break;
+    case COMPAR_V_SPLIT3_TF32: out_kind = PP_SPLIT_TF32; break;
     default: out_kind = PP_SPLIT_BF16_3P; break;
   }
   const float* sa = nullptr;
@@ -703,6 +736,9 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     case COMPAR_V_SPLIT3:
       return run_tc<COMPAR_V_SPLIT3>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr, nullptr,
                                      nullptr, plan, partial, g, num_sms, s);
+    case COMPAR_V_SPLIT3_TF32:
+      return run_tc<COMPAR_V_SPLIT3_TF32>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr,
+                                          nullptr, nullptr, plan, partial, g, num_sms, s);
     default:
       return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr,
                                      plan, partial, g, num_sms, s);

@@ -5,6 +5,8 @@
 //  * f32 -> (hi, lo) bf16 pair, hi = bf16(x), lo = bf16(x - hi)   (3xBF16 split)
 //  * f32 -> (hi, mid, lo) bf16 triple, mid = bf16(x - hi),
 //           lo = bf16(x - hi - mid)                         (6-product split)
+//  * f32 -> (hi, lo) TF32 pair as float32, hi = tf32(x), lo = tf32(x - hi),
+//           rounding to nearest, ties away from zero        (3xTF32 split)
 //  * f32 -> E4M3 codes of x * s, s = 448 / amax(|x|), saturating   (FP8 variant)
 //  * plain copy / transpose of f32, bf16 or fp8 elements
 //
@@ -30,6 +32,13 @@ __device__ __forceinline__ void split3p(float x, __nv_bfloat16& h, __nv_bfloat16
   const float r1 = x - __bfloat162float(h);
   m = __float2bfloat16_rn(r1);
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Nearest TF32 value (10 fraction bits, ties away from zero) of a finite
+// float32, as a float32 with the low 13 bits clear: add half of the kept
+// unit to the pattern and clear the dropped bits.
+__device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Piece 2 of a split output: pieces are equally spaced, Y_lo = piece 1.
@@ -67,6 +76,12 @@ __device__ __forceinline__ void store_converted(const F32Out& o, float x, void* 
       static_cast<__nv_bfloat16*>(Y)[idx] = h;
       static_cast<__nv_bfloat16*>(Ylo)[idx] = m;
       piece2(Y, Ylo)[idx] = l;
+      break;
+    }
+    case PP_SPLIT_TF32: {
+      const float h = tf32_rna(x);
+      static_cast<float*>(Y)[idx] = h;
+      static_cast<float*>(Ylo)[idx] = tf32_rna(x - h);
       break;
     }
     case PP_E4M3: {
@@ -121,6 +136,19 @@ __device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], v
     float4* y = reinterpret_cast<float4*>(static_cast<float*>(Y) + idx);
     y[0] = make_float4(x[0], x[1], x[2], x[3]);
     y[1] = make_float4(x[4], x[5], x[6], x[7]);
+  } else if (kind == PP_SPLIT_TF32) {
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      h[q] = tf32_rna(x[q]);
+      l[q] = tf32_rna(x[q] - h[q]);
+    }
+    float4* y = reinterpret_cast<float4*>(static_cast<float*>(Y) + idx);
+    float4* z = reinterpret_cast<float4*>(static_cast<float*>(Ylo) + idx);
+    y[0] = make_float4(h[0], h[1], h[2], h[3]);
+    y[1] = make_float4(h[4], h[5], h[6], h[7]);
+    z[0] = make_float4(l[0], l[1], l[2], l[3]);
+    z[1] = make_float4(l[4], l[5], l[6], l[7]);
   } else if (kind == PP_SPLIT_BF16_3P) {
     uint32_t w[3][4];
 #pragma unroll
@@ -215,6 +243,11 @@ __global__ void convert_transpose64_kernel(const float* __restrict__ X, int64_t 
     if (ocol + 1 < rows) {
       if (kind == PP_F32) {
         *reinterpret_cast<float2*>(static_cast<float*>(Y) + idx) = make_float2(x0, x1);
+      } else if (kind == PP_SPLIT_TF32) {
+        const float h0 = tf32_rna(x0), h1 = tf32_rna(x1);
+        *reinterpret_cast<float2*>(static_cast<float*>(Y) + idx) = make_float2(h0, h1);
+        *reinterpret_cast<float2*>(static_cast<float*>(Ylo) + idx) =
+            make_float2(tf32_rna(x0 - h0), tf32_rna(x1 - h1));
       } else if (kind == PP_BF16 || kind == PP_SPLIT_BF16) {
         const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
         *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(Y) + idx) =

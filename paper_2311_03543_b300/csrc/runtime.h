@@ -18,7 +18,7 @@
 
 namespace compar {
 
-constexpr int kNumVariants = COMPAR_V_COUNT;  // variant ids 0..7 (6: batched only)
+constexpr int kNumVariants = COMPAR_V_COUNT;  // variant ids 0..8 (6: batched only)
 constexpr int kNumFeatures = 8;
 constexpr int kHidden = 64;
 constexpr int kOutputs = 2 * kNumVariants;  // log time, log error per variant

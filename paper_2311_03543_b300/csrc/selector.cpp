@@ -68,6 +68,10 @@ ErrorModel::ErrorModel() {
   // Measured 6.2e-8 (k = 64) .. 4.1e-7 (k = 16384), ill-scaled columns alike.
   c0[COMPAR_V_SPLIT6][COMPAR_F32] = 6e-8f;
   c1[COMPAR_V_SPLIT6][COMPAR_F32] = 0.07f;
+  // 3xTF32: 22-bit pieces and the dropped lo*lo term, ~2^-22 relative.
+  // Measured 1.0e-7 (k = 64) .. 1.8e-7 (k = 16384), ill-scaled columns alike.
+  c0[COMPAR_V_SPLIT3_TF32][COMPAR_F32] = 1.1e-7f;
+  c1[COMPAR_V_SPLIT3_TF32][COMPAR_F32] = 0.07f;
 }
 
 double ErrorModel::predict(int v, int dtype, int64_t k) const {
@@ -188,6 +192,12 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
       peak = 1.5e15 / 6;
       flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
       bytes += (M * K + K * N) * 10;
+      ovh_us = 16;
+      break;
+    case COMPAR_V_SPLIT3_TF32:
+      peak = 1.5e15 / 2 / 3;  // three products at the TF32 rate
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += (M * K + K * N) * 12;
       ovh_us = 16;
       break;
     default:

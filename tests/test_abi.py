@@ -54,7 +54,8 @@ def test_variant_ids_are_stable():
     assert [cp.compar_variant_name(i).decode() for i in range(7)] == [
         "naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16", "grouped"]
     assert cp.compar_variant_name(7).decode() == "split-6xbf16"
-    assert (cp.V_GROUPED, cp.V_SPLIT6) == (6, 7)
+    assert cp.compar_variant_name(8).decode() == "split-3xtf32"
+    assert (cp.V_GROUPED, cp.V_SPLIT6, cp.V_SPLIT3_TF32) == (6, 7, 8)
     h = cp.Context.host()
     try:
         assert not h.supported(cp.V_GROUPED, 64, 64, 64, cp.F32)   # never a single call

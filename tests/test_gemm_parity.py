@@ -1,10 +1,10 @@
 """Parity of every GEMM variant with the FP64 oracle (GPU, through the C ABI).
 
 Tolerances (relative Frobenius error):
-* FP32-accurate variants (naive, SIMT, 3xBF16, 6-product split) on float32
-  inputs: <= 1e-5 against the oracle on the float32 values; the 6-product
-  split also <= 2e-6 (its pieces hold every bit of float32 and it drops only
-  terms ~2^-26 relative, so accumulation error alone remains).
+* FP32-accurate variants (naive, SIMT, 3xBF16, 6-product split, 3xTF32) on
+  float32 inputs: <= 1e-5 against the oracle on the float32 values; the
+  6-product split and 3xTF32 also <= 2e-6 (their pieces hold 24 / 22 bits
+  and the dropped terms are ~2^-26 / 2^-22 relative).
 * BF16 / FP8 tensor-core variants: <= 1e-5 against the oracle evaluated on
   the exact values the kernel multiplies (its inputs as given, or the oracle's
   own bf16 rounding / e4m3 quantisation of the float32 inputs) — only FP32
@@ -54,13 +54,13 @@ SHAPES = [(1, 1, 1), (3, 5, 7), (16, 16, 16), (33, 65, 17), (127, 129, 130),
           (255, 257, 256), (256, 256, 256), (300, 200, 1000), (129, 520, 64)]
 
 
-@pytest.mark.parametrize("v", [0, 1, 5, 7])
+@pytest.mark.parametrize("v", [0, 1, 5, 7, 8])
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_fp32_accurate_variants(ctx, v, m, n, k):
     A = W.uniform(m, k, seed=100 + m); B = W.uniform(k, n, seed=200 + n)
     got = _run(ctx, v, A, B)
     ref = oracle.gemm(A, B)
-    assert N.rel_frobenius(got, ref) <= (TOL_SPLIT6 if v == 7 else TOL_F32)
+    assert N.rel_frobenius(got, ref) <= (TOL_SPLIT6 if v in (7, 8) else TOL_F32)
 
 
 def test_config1_naive_then_simt(ctx):
@@ -134,6 +134,15 @@ def test_split3_matches_its_three_products(ctx):
     assert N.rel_frobenius(got, three) <= TOL_F32
 
 
+def test_split3_tf32_matches_its_three_products(ctx):
+    import paper_2311_03543_b300 as cp
+    m, n, k = 192, 320, 512
+    A = W.normal(m, k, seed=44); B = W.normal(k, n, seed=45)
+    got = _run(ctx, cp.V_SPLIT3_TF32, A, B)
+    three = N.split3_tf32_product(A, B, oracle.gemm)
+    assert N.rel_frobenius(got, three) <= TOL_SPLIT6
+
+
 def test_split6_matches_its_six_products(ctx):
     m, n, k = 192, 320, 512
     A = W.normal(m, k, seed=23); B = W.normal(k, n, seed=24)
@@ -155,7 +164,7 @@ def test_split6_at_simt_error_level(ctx, m, n, k):
     assert e6 <= 0.5 * e5
 
 
-@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7])
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7, 8])
 def test_all_ones_every_entry_is_k(ctx, v):
     m, n, k = 130, 260, 300
     got = _run(ctx, v, np.ones((m, k), np.float32), np.ones((k, n), np.float32))
@@ -165,7 +174,7 @@ def test_all_ones_every_entry_is_k(ctx, v):
         assert np.all(got == k)
 
 
-@pytest.mark.parametrize("v", [0, 1, 2, 3, 5, 7])
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 5, 7, 8])
 def test_identity_exact_on_representable_values(ctx, v):
     n = 192
     A = W.integer_matrix(n, n, seed=15)           # integers are exact in every format
@@ -173,7 +182,7 @@ def test_identity_exact_on_representable_values(ctx, v):
     assert np.array_equal(got, A)
 
 
-@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7])
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7, 8])
 def test_alpha_beta(ctx, v):
     m, n, k = 70, 90, 110
     A = W.integer_matrix(m, k, seed=16, bound=4)
@@ -185,7 +194,7 @@ def test_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
-@pytest.mark.parametrize("v", [2, 3, 4, 5, 7])
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8])
 def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     """Few output tiles and a long K: the tensor-core variants split K over
     the SMs (partials reduced afterwards, beta applied once)."""
@@ -200,7 +209,7 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
-@pytest.mark.parametrize("v", [2, 3, 5, 7])
+@pytest.mark.parametrize("v", [2, 3, 5, 7, 8])
 def test_partial_last_wave_with_alpha_beta(ctx, v):
     """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
     persistent CTAs), integer inputs, alpha and beta."""
@@ -248,7 +257,8 @@ def test_forced_unsupported_variant_is_refused(ctx):
                                      (5, 4096, 4096, 64), (5, 16, 4096, 4096),
                                      (5, 2048, 2048, 2048), (1, 2048, 2048, 2048),
                                      (7, 2048, 2048, 2048), (7, 16, 4096, 4096),
-                                     (7, 4096, 4096, 64)])
+                                     (7, 4096, 4096, 64), (8, 2048, 2048, 2048),
+                                     (8, 16, 4096, 4096)])
 def test_sweep_shapes_sampled_rows(ctx, v, m, n, k):
     """Full-size sweep shapes, checked on 32 seeded rows against the oracle."""
     A = W.uniform(m, k, seed=20); B = W.uniform(k, n, seed=21)
