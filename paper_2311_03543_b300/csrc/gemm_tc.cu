@@ -133,6 +133,15 @@ struct TcArgs {
   // alpha * partial to partial[split][M][N] and a reduce kernel forms C.
   int splits, kb_per_split;
   float* partial;
+  // Work list of a CTA: the `dp_units` classic units (whole tiles, or tile x
+  // K-split units when splits > 1) dealt round-robin, then, when sk_q > 0, a
+  // stream-K tail: tiles sk_tile0.. are cut into promotion chunks (sk_cpt
+  // per tile, sk_q in all) and CTA b < sk_ctas takes the contiguous chunks
+  // [b sk_q / sk_ctas, (b+1) sk_q / sk_ctas), at most two pieces of tiles.
+  int dp_units;
+  int sk_tile0, sk_cpt, sk_q, sk_ctas;
+  float* sk_slab;               // [sk_ctas][2][kBM * BN] published pieces
+  unsigned int* sk_count;       // [tail tiles] arrivals, zero at launch
   float alpha, beta;
   const float* dequant_a;  // optional device factors (fp8 of float32 inputs)
   const float* dequant_b;
@@ -151,6 +160,51 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
   const int in = tile - group * per_group;
   mb = first_m + in % gsize;
   nb = in / gsize;
+}
+
+// One item of a CTA's work list: K blocks [kb_begin, kb_end) of a tile.
+// piece = -1: a classic unit (split = its K-split index); piece 0 / 1: the
+// first / second stream-K piece of this CTA.
+struct WorkItem {
+  int tile, kb_begin, kb_end, split, piece;
+};
+
+__device__ __forceinline__ int sk_start(const TcArgs& p, int b) {
+  return static_cast<int>(static_cast<long long>(b) * p.sk_q / p.sk_ctas);
+}
+// The stream-K CTA whose chunk range holds chunk q (ranges are never empty).
+__device__ __forceinline__ int sk_cta_of(const TcArgs& p, int q) {
+  return static_cast<int>((static_cast<long long>(q + 1) * p.sk_ctas - 1) / p.sk_q);
+}
+
+// Item i of this CTA's list; false past its end.  Every role of the CTA
+// walks the same list.
+template <int kChunkKB>
+__device__ __forceinline__ bool get_item(const TcArgs& p, int i, WorkItem& it) {
+  const int b = blockIdx.x, grid = gridDim.x;
+  const int u = b + i * grid;
+  if (u < p.dp_units) {
+    it.tile = u / p.splits;
+    it.split = u % p.splits;
+    it.kb_begin = it.split * p.kb_per_split;
+    it.kb_end = min(p.num_kb, it.kb_begin + p.kb_per_split);
+    it.piece = -1;
+    return true;
+  }
+  if (kChunkKB == 0 || p.sk_q == 0 || b >= p.sk_ctas) return false;
+  const int n_dp = b < p.dp_units ? (p.dp_units - 1 - b) / grid + 1 : 0;
+  const int k = i - n_dp;
+  const int q0 = sk_start(p, b), q1 = sk_start(p, b + 1);
+  const int q = k == 0 ? q0 : (q0 / p.sk_cpt + 1) * p.sk_cpt;
+  if (k > 1 || q >= q1) return false;
+  const int t = q / p.sk_cpt;
+  const int qe = min(q1, (t + 1) * p.sk_cpt);
+  it.tile = p.sk_tile0 + t;
+  it.split = 0;
+  it.kb_begin = (q - t * p.sk_cpt) * kChunkKB;
+  it.kb_end = min(p.num_kb, (qe - t * p.sk_cpt) * kChunkKB);
+  it.piece = k;
+  return true;
 }
 
 // Wait that ignores the CTA abort flag: used only to drain this CTA's own
@@ -187,8 +241,10 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
   uint64_t* tfull = empty + S;   // [2]
   uint64_t* tempty = tfull + 2;  // [2]
   uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* epi_bar = drain + 1;  // rendezvous of the epilogue warps (stream-K)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* last_flag = abort_flag + 1;
 
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
@@ -203,6 +259,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
       dev::mbar_init(&tempty[a], L::kEpiThreads);
     }
     dev::mbar_init(drain, 1);
+    dev::mbar_init(epi_bar, L::kEpiThreads);
     *abort_flag = 0;
     dev::fence_barrier_init();
   }
@@ -227,12 +284,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
   dev::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
-  const int num_units = p.tiles_m * p.tiles_n * p.splits;
-  // K-block range of unit u
-  auto unit_kb = [&](int u, int& kb_begin, int& kb_end) {
-    kb_begin = (u % p.splits) * p.kb_per_split;
-    kb_end = min(p.num_kb, kb_begin + p.kb_per_split);
-  };
+  WorkItem it;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
@@ -240,11 +292,10 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     uint32_t issued = 0, issued_parity = 0;  // per-stage bit masks
     constexpr uint32_t kTx = static_cast<uint32_t>(L::kStageBytes);
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
-      int mb, nb, kb_begin, kb_end;
-      tile_coords(u / p.splits, p.tiles_m, p.tiles_n, mb, nb);
-      unit_kb(u, kb_begin, kb_end);
-      for (int kb = kb_begin; kb < kb_end; ++kb) {
+    for (int i = 0; ok && get_item<kChunkKB>(p, i, it); ++i) {
+      int mb, nb;
+      tile_coords(it.tile, p.tiles_m, p.tiles_n, mb, nb);
+      for (int kb = it.kb_begin; kb < it.kb_end; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
           ok = false;
           break;
@@ -294,9 +345,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;  // accumulator-buffer uses (one per K chunk)
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
-      int kb_begin, kb_end;
-      unit_kb(u, kb_begin, kb_end);
+    for (int i = 0; ok && get_item<kChunkKB>(p, i, it); ++i) {
+      const int kb_begin = it.kb_begin, kb_end = it.kb_end;
       const int chunk = kChunkKB > 0 ? kChunkKB : kb_end - kb_begin;
       for (int kb0 = kb_begin; ok && kb0 < kb_end; kb0 += chunk, ++acc_iter) {
         const uint32_t acc = acc_iter & 1;
@@ -403,12 +453,14 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     const int64_t out_ld = split ? p.N : p.ldc;
     const bool vec_out = split ? (p.N % 2 == 0) : vec2;
     const float beta = split ? 0.f : p.beta;
-    for (int u = blockIdx.x; ok && u < num_units; u += gridDim.x) {
-      int mb, nb, kb_begin, kb_end;
-      tile_coords(u / p.splits, p.tiles_m, p.tiles_n, mb, nb);
-      unit_kb(u, kb_begin, kb_end);
-      const int num_chunks = kChunkKB > 0 ? (kb_end - kb_begin + kChunkKB - 1) / kChunkKB : 1;
-      float* out = split ? p.partial + static_cast<int64_t>(u % p.splits) * p.M * p.N : p.C;
+    uint32_t epi_uses = 0;  // completed phases of epi_bar
+    const int etid = threadIdx.x - 64;
+    for (int i = 0; ok && get_item<kChunkKB>(p, i, it); ++i) {
+      int mb, nb;
+      tile_coords(it.tile, p.tiles_m, p.tiles_n, mb, nb);
+      const int num_chunks =
+          kChunkKB > 0 ? (it.kb_end - it.kb_begin + kChunkKB - 1) / kChunkKB : 1;
+      float* out = split ? p.partial + static_cast<int64_t>(it.split) * p.M * p.N : p.C;
       const int row_q = mb * kBM + quarter * 32;     // first row of this warp's quarter
       const int col_s = nb * BN + cslice * EC;       // first column of its slice
       auto frag_taddr = [&](uint32_t acc, int f) {
@@ -444,6 +496,94 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           dev::mbar_arrive(&tempty[acc]);
         }
         if (!ok) break;
+        if (it.piece >= 0) {
+          // Stream-K piece.  Every contributor of the tile publishes its
+          // partial sum, then counts itself in; the last to arrive adds the
+          // pieces in contributor order (so the result does not depend on
+          // which CTA finished last) and stores the tile.  No CTA waits for
+          // another.
+          const int t = it.tile - p.sk_tile0;
+          const int first = t * p.sk_cpt;
+          const int b0 = sk_cta_of(p, first);
+          const int nc = sk_cta_of(p, first + p.sk_cpt - 1) - b0 + 1;
+          if (nc > 1) {
+            constexpr int64_t kSlab = static_cast<int64_t>(kBM) * BN / 4;  // float4 per piece
+            auto slab = [&](int cta, int k) {
+              return reinterpret_cast<float4*>(p.sk_slab) +
+                     (2 * static_cast<int64_t>(cta) + k) * kSlab;
+            };
+            float4* mine = slab(blockIdx.x, it.piece);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+              for (int j4 = 0; j4 < 8; ++j4)
+                mine[(f * 8 + j4) * L::kEpiThreads + etid] =
+                    make_float4(sum[f][4 * j4], sum[f][4 * j4 + 1], sum[f][4 * j4 + 2],
+                                sum[f][4 * j4 + 3]);
+            __threadfence();
+            // bounded rendezvous: a CTA that gave up elsewhere cannot hang here
+            dev::mbar_arrive(epi_bar);
+            if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) {
+              ok = false;
+              break;
+            }
+            if (etid == 0) {
+              __threadfence();
+              *last_flag = atomicAdd(p.sk_count + t, 1u) == static_cast<unsigned int>(nc - 1);
+            }
+            dev::mbar_arrive(epi_bar);
+            if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) {
+              ok = false;
+              break;
+            }
+            if (!*last_flag) continue;
+            __threadfence();
+            // the pieces in contributor order, this CTA's own from its slab
+            // too, so that its registers are free for the sums
+            const int k0 = sk_start(p, b0) < first ? 1 : 0;  // b0's piece of this tile
+            if (row_q < p.M && col_s < p.N) {
+              // two fragments at a time: 16 independent loads in flight per
+              // contributor, so a tile costs NF / 2 * nc L2 round trips
+              static_assert(NF % 2 == 0, "fragment pairs");
+#pragma unroll 1
+              for (int f2 = 0; f2 < NF; f2 += 2) {
+                const int64_t base = f2 * 8 * L::kEpiThreads + etid;
+                float4 acc[16];
+                const float4* s0 = slab(b0, k0) + base;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[e] = __ldcg(s0 + e * L::kEpiThreads);
+                for (int jj = 1; jj < nc; ++jj) {
+                  const float4* sj = slab(b0 + jj, 0) + base;
+                  float4 c[16];
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) c[e] = __ldcg(sj + e * L::kEpiThreads);
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) {
+                    acc[e].x += c[e].x;
+                    acc[e].y += c[e].y;
+                    acc[e].z += c[e].z;
+                    acc[e].w += c[e].w;
+                  }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  float v[32];
+#pragma unroll
+                  for (int j4 = 0; j4 < 8; ++j4) {
+                    v[4 * j4] = acc[8 * h + j4].x;
+                    v[4 * j4 + 1] = acc[8 * h + j4].y;
+                    v[4 * j4 + 2] = acc[8 * h + j4].z;
+                    v[4 * j4 + 3] = acc[8 * h + j4].w;
+                  }
+                  const int f = f2 + h;
+                  store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
+                                col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
+                }
+              }
+            }
+            continue;
+          }
+        }
         if (row_q < p.M && col_s < p.N) {
 #pragma unroll
           for (int f = 0; f < NF; ++f)
@@ -513,10 +653,30 @@ CUtensorMapDataType map_type(int v) {
 
 // Launch plan of a tensor-core call: K blocks, tiles, and the split of K
 // when the tiles alone would leave most SMs idle (at least 8 K blocks per
-// split, at most one unit per SM).
+// split, at most one unit per SM).  Promoted variants whose last wave of
+// tiles is partial cut that wave into stream-K pieces instead (whole
+// promotion chunks, at least a quarter tile each, so that a tile has at most
+// five contributors), when that shortens the wave by a quarter or more.
 struct TcPlan {
   int num_kb, tiles, splits, kb_per;
+  int sk_tile0 = 0, sk_cpt = 0, sk_q = 0, sk_ctas = 0;
 };
+
+// Tile width of every promoted variant (stream-K piece size on the host).
+constexpr int kPromotedBN = 256;
+static_assert(Traits<COMPAR_V_SPLIT3>::BN == kPromotedBN &&
+                  Traits<COMPAR_V_SPLIT6>::BN == kPromotedBN &&
+                  Traits<COMPAR_V_SPLIT3_TF32>::BN == kPromotedBN,
+              "stream-K pieces are kBM x kPromotedBN");
+
+int chunk_kb_of(int v) {
+  switch (v) {
+    case COMPAR_V_SPLIT3: return Traits<COMPAR_V_SPLIT3>::chunk_kb;
+    case COMPAR_V_SPLIT6: return Traits<COMPAR_V_SPLIT6>::chunk_kb;
+    case COMPAR_V_SPLIT3_TF32: return Traits<COMPAR_V_SPLIT3_TF32>::chunk_kb;
+    default: return 0;
+  }
+}
 
 TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
   const int kelems = v == COMPAR_V_TC_FP8 ? 128
@@ -535,14 +695,30 @@ TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
       p.splits = (p.num_kb + p.kb_per - 1) / p.kb_per;
     }
   }
+  const int chunk = chunk_kb_of(v);
+  const int rem = p.tiles % num_sms;
+  if (chunk > 0 && p.splits == 1 && rem > 0) {
+    const int64_t cpt = (p.num_kb + chunk - 1) / chunk;
+    const int64_t q = static_cast<int64_t>(rem) * cpt;
+    const int64_t lmin = std::max<int64_t>(1, (cpt + 3) / 4);
+    const int64_t ctas = std::min<int64_t>(num_sms, q / lmin);
+    // worth it only when the tail wave shrinks by a quarter or more: the
+    // fixup (publish, count, sum the pieces) costs a few L2 round trips
+    if (cpt >= 2 && ctas >= 1 && q < (int64_t{1} << 30) && 4 * ((q + ctas - 1) / ctas) <= 3 * cpt) {
+      p.sk_tile0 = p.tiles - rem;
+      p.sk_cpt = static_cast<int>(cpt);
+      p.sk_q = static_cast<int>(q);
+      p.sk_ctas = static_cast<int>(ctas);
+    }
+  }
   return p;
 }
 
 template <int V>
 int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
            const void* A2, const void* B2, const void* A3, const void* B3, const float* dq_a,
-           const float* dq_b, const TcPlan& plan, float* partial, const DeviceGuard& g,
-           int num_sms, cudaStream_t s) {
+           const float* dq_b, const TcPlan& plan, float* partial, float* sk_slab,
+           unsigned int* sk_count, const DeviceGuard& g, int num_sms, cudaStream_t s) {
   using L = Layout<V>;
   using T = Traits<V>;
   static std::once_flag attr_once;
@@ -589,6 +765,12 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.splits = plan.splits;
   a.kb_per_split = plan.splits > 1 ? plan.kb_per : a.num_kb;
   a.partial = partial;
+  a.sk_tile0 = plan.sk_tile0;
+  a.sk_cpt = plan.sk_cpt;
+  a.sk_q = plan.sk_q;
+  a.sk_ctas = plan.sk_ctas;
+  a.sk_slab = sk_slab;
+  a.sk_count = sk_count;
   a.tiles_m = static_cast<int>((c.m + kBM - 1) / kBM);
   a.tiles_n = static_cast<int>((c.n + T::BN - 1) / T::BN);
   a.alpha = c.alpha * (V == COMPAR_V_TC_FP8 ? c.scale_a * c.scale_b : 1.f);
@@ -600,7 +782,16 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.err_word = g.err_word;
   a.budget_ns = g.budget_ns;
   const int units = a.tiles_m * a.tiles_n * a.splits;
-  const int grid = std::min(units, num_sms);
+  int grid = std::min(units, num_sms);
+  a.dp_units = units;
+  if (plan.sk_q > 0) {
+    // whole waves of tiles, then the stream-K tail on sk_ctas CTAs
+    if (sk_count == nullptr || sk_slab == nullptr) return COMPAR_ERR_INVALID;
+    a.dp_units = plan.sk_tile0;
+    grid = plan.sk_tile0 > 0 ? num_sms : plan.sk_ctas;
+    COMPAR_CUDA_TRY(
+        cudaMemsetAsync(sk_count, 0, sizeof(unsigned int) * (units - plan.sk_tile0), s));
+  }
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, ta3, tb3, a);
   COMPAR_CUDA_TRY(cudaGetLastError());
@@ -658,12 +849,17 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const TcPlan plan = tc_plan(v, c, num_sms);
   const size_t part_bytes =
       plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
+  // stream-K: two published pieces per CTA and one counter per tail tile
+  const size_t slab_bytes =
+      plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kPromotedBN * 4 : 0;
+  const size_t count_bytes = plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
   // workspace carve: [B pieces][A pieces][fp8 scalars][split-K partials]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
   const size_t b_bytes = b_in_place ? 0
                          : b_mn     ? align_up(static_cast<size_t>(c.k) * ldn * 2, 256)
                                     : align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
-  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256 + part_bytes;
+  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256 + part_bytes +
+                slab_bytes + count_bytes;
   int rc = ws.ensure(need, s);
   if (rc != COMPAR_OK) return rc;
   uint8_t* base = static_cast<uint8_t*>(ws.ptr);
@@ -673,6 +869,9 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   unsigned int* amax_bits = reinterpret_cast<unsigned int*>(scal);  // [2]
   float* fscal = reinterpret_cast<float*>(scal + 16);               // sA, dA, sB, dB
   float* partial = part_bytes ? reinterpret_cast<float*>(scal + 256) : nullptr;
+  float* sk_slab = slab_bytes ? reinterpret_cast<float*>(scal + 256 + part_bytes) : nullptr;
+  unsigned int* sk_count =
+      count_bytes ? reinterpret_cast<unsigned int*>(scal + 256 + part_bytes + slab_bytes) : nullptr;
 
   int out_kind;
   switch (v) {
@@ -726,22 +925,25 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   switch (v) {
     case COMPAR_V_TC_TF32:
       return run_tc<COMPAR_V_TC_TF32>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, plan, partial, g, num_sms, s);
+                                      nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
+                                      num_sms, s);
     case COMPAR_V_TC_BF16:
       return run_tc<COMPAR_V_TC_BF16>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, plan, partial, g, num_sms, s);
+                                      nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
+                                      num_sms, s);
     case COMPAR_V_TC_FP8:
       return run_tc<COMPAR_V_TC_FP8>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                     dqa, dqb, plan, partial, g, num_sms, s);
+                                     dqa, dqb, plan, partial, sk_slab, sk_count, g, num_sms, s);
     case COMPAR_V_SPLIT3:
       return run_tc<COMPAR_V_SPLIT3>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr, nullptr,
-                                     nullptr, plan, partial, g, num_sms, s);
+                                     nullptr, plan, partial, sk_slab, sk_count, g, num_sms, s);
     case COMPAR_V_SPLIT3_TF32:
       return run_tc<COMPAR_V_SPLIT3_TF32>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr,
-                                          nullptr, nullptr, plan, partial, g, num_sms, s);
+                                          nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
+                                          num_sms, s);
     default:
       return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr,
-                                     plan, partial, g, num_sms, s);
+                                     plan, partial, sk_slab, sk_count, g, num_sms, s);
   }
 }
 

@@ -212,7 +212,8 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
 @pytest.mark.parametrize("v", [2, 3, 5, 7, 8])
 def test_partial_last_wave_with_alpha_beta(ctx, v):
     """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
-    persistent CTAs), integer inputs, alpha and beta."""
+    persistent CTAs, cut into stream-K pieces for the promoted variants),
+    integer inputs, alpha and beta."""
     m, n, k = 2560, 2304, 1024
     A = W.integer_matrix(m, k, seed=41, bound=2)
     B = W.integer_matrix(k, n, seed=42, bound=2)
@@ -220,6 +221,26 @@ def test_partial_last_wave_with_alpha_beta(ctx, v):
     got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
     ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
     assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("v,m,n,k", [(5, 2500, 2000, 1000), (7, 2500, 2000, 1000),
+                                     (8, 2500, 2000, 1000), (5, 1536, 2048, 2048),
+                                     (7, 1400, 2048, 777)])
+def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
+    """A partial last wave of tiles (160 tiles: one full wave and 12 more) or
+    a single partial wave (96 or 88 tiles) is cut into stream-K pieces of
+    whole promotion chunks; 2 - 5 CTAs contribute to a tile and the last to
+    finish adds the pieces in a fixed order.  Ragged M, N and K, alpha and
+    beta; the same call twice gives the same bits."""
+    A = W.uniform(m, k, seed=61)
+    B = W.uniform(k, n, seed=62)
+    C0 = W.uniform(m, n, seed=63)
+    got = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
+    again = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
+    assert np.array_equal(got, again)
+    rows = W.sample_rows(m, 96, seed=64)
+    ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.25, C0=C0)
+    assert N.rel_frobenius(got[rows], ref) <= (TOL_F32 if v == 5 else TOL_SPLIT6)
 
 
 def test_k_zero_scales_c(ctx):
