@@ -292,7 +292,8 @@ def measure_variants(ctx, cp, torch, dev, peaks):
             cp.V_TC_TF32: peaks["tf32_tflops"], cp.V_TC_BF16: peaks["bf16_tflops"],
             cp.V_TC_FP8: peaks.get("fp8_tflops") or 2 * peaks["bf16_tflops"],
             cp.V_SPLIT3: peaks["bf16_tflops"] / 3, cp.V_SPLIT6: peaks["bf16_tflops"] / 6,
-            cp.V_SPLIT3_TF32: peaks["tf32_tflops"] / 3}
+            cp.V_SPLIT3_TF32: peaks["tf32_tflops"] / 3,
+            cp.V_SPLIT3_FUSED: peaks["bf16_tflops"] / 3}
     rows = []
     for (m, n, k) in shapes:
         g = torch.Generator(device=dev)
@@ -437,7 +438,8 @@ def main():
     prof = {v: ctx.profile_read(v) for v in range(cp.NUM_VARIANTS)}
     dom = max(prof, key=lambda v: prof[v][0])
     dom_ms, dom_n = prof[dom]
-    pieces = {cp.V_SPLIT3: 3, cp.V_SPLIT6: 6}.get(dom, 1)
+    pieces = {cp.V_SPLIT3: 3, cp.V_SPLIT6: 6, cp.V_SPLIT3_FUSED: 3,
+              cp.V_SPLIT3_TF32: 3}.get(dom, 1)
     dom_flops = args.steps * sum(2.0 * m * n * k * pieces
                                  for (m, n, k), v in zip(shapes, picks) if v == dom)
     achieved = dom_flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
@@ -450,7 +452,7 @@ def main():
         mhz = peaks.get("sm_max_mhz", 2032.0)
         peak, bound, src = 148 * 128 * 2 * mhz * 1e6 / 1e12, "alu", "derived: 148 SM x 128 FP32 lanes x 2 x max clock"
     else:
-        scale = {cp.V_TC_TF32: 0.5, cp.V_TC_FP8: 2.0}.get(dom, 1.0)
+        scale = {cp.V_TC_TF32: 0.5, cp.V_SPLIT3_TF32: 0.5, cp.V_TC_FP8: 2.0}.get(dom, 1.0)
         base = peaks.get("bf16_tflops_sustained")
         src = "measured bf16 sustained (MEASURED_PEAKS.json)"
         if base is None:
@@ -565,7 +567,8 @@ def measured_traffic(kernel, flops_per_launch):
     if h.hexdigest() != rec["src_sha1"]:
         return None, "kernel changed since the ncu capture"
     m, n, k = rec["shape"]
-    products = {"split-3xbf16": 3, "split-6xbf16": 6, "split-3xtf32": 3}.get(kernel, 1)
+    products = {"split-3xbf16": 3, "split-6xbf16": 6, "split-3xtf32": 3,
+                "split-3xbf16-fused": 3}.get(kernel, 1)
     scale = flops_per_launch / (2.0 * m * n * k * products)
     return (rec["dram_bytes_per_launch"] * scale,
             f"ncu dram read+write of one {m}x{n}x{k} launch ({rec['source']}) scaled by work "

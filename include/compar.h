@@ -80,7 +80,11 @@ enum {
                                  (at or below the FP32 SIMT error level)    */
     COMPAR_V_SPLIT3_TF32 = 8, /* 3xTF32: 2-piece TF32 split, 3 kind::tf32
                                  products                                  */
-    COMPAR_V_COUNT = 9        /* ids 0 .. COUNT-1; ids never change once
+    COMPAR_V_SPLIT3_FUSED = 9,/* 3xBF16 with the split done inside the GEMM
+                                 kernel (float32 tiles split in shared
+                                 memory, no pre-pass); float32 A and B with
+                                 16-byte rows and 16-byte aligned bases    */
+    COMPAR_V_COUNT = 10       /* ids 0 .. COUNT-1; ids never change once
                                  assigned, new variants take new ids        */
 };
 
@@ -239,7 +243,8 @@ int compar_last_variant(compar_ctx_t ctx);
 int compar_variant_count(void);
 const char* compar_variant_name(int variant_id);
 
-/* Whether variant `variant_id` can run (m, n, k, dtype) at all (dtype,
+/* Whether variant `variant_id` can run (m, n, k, dtype) at all on
+ * contiguous row-major operands with 16-byte aligned bases (dtype, row
  * alignment and shape rules; the tolerance is not considered).  1 / 0, or a
  * negative status. */
 int compar_variant_supported(compar_ctx_t ctx, int variant_id, int64_t m,

@@ -23,10 +23,11 @@ V_NAIVE, V_SIMT, V_TC_TF32, V_TC_BF16, V_TC_FP8, V_SPLIT3 = 0, 1, 2, 3, 4, 5
 V_GROUPED = 6      # batched calls only
 V_SPLIT6 = 7
 V_SPLIT3_TF32 = 8
-NUM_VARIANTS = 9   # ids 0 .. 8 (id 6 never runs a single call)
+V_SPLIT3_FUSED = 9
+NUM_VARIANTS = 10  # ids 0 .. 9 (id 6 never runs a single call)
 MLP_OUTPUTS = 2 * NUM_VARIANTS   # log2 time and log10 error per variant
 VARIANT_NAMES = ["naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16",
-                 "grouped", "split-6xbf16", "split-3xtf32"]
+                 "grouped", "split-6xbf16", "split-3xtf32", "split-3xbf16-fused"]
 
 
 S_NAIVE, S_TILED, S_TMA = 0, 1, 2

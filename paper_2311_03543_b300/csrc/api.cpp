@@ -52,7 +52,8 @@ void Workspace::release() {
 
 static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",
                                       "tc-bf16",   "tc-fp8",   "split-3xbf16",
-                                      "grouped",   "split-6xbf16", "split-3xtf32"};
+                                      "grouped",   "split-6xbf16", "split-3xtf32",
+                                      "split-3xbf16-fused"};
 static_assert(sizeof(kVariantNames) / sizeof(kVariantNames[0]) == COMPAR_V_COUNT,
               "one name per variant id");
 
@@ -77,6 +78,7 @@ bool variant_supported(const compar_ctx* ctx, int v, const GemmCall& c) {
     case COMPAR_V_SPLIT3:
     case COMPAR_V_SPLIT6:
     case COMPAR_V_SPLIT3_TF32:
+    case COMPAR_V_SPLIT3_FUSED:
       return tc_supported(v, c);
     default:
       return false;
@@ -96,7 +98,8 @@ static int launch_variant(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_
     case COMPAR_V_TC_FP8:
     case COMPAR_V_SPLIT3:
     case COMPAR_V_SPLIT6:
-    case COMPAR_V_SPLIT3_TF32: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
+    case COMPAR_V_SPLIT3_TF32:
+    case COMPAR_V_SPLIT3_FUSED: return launch_tc(v, c, ctx->ws, ctx->guard, ctx->num_sms, s);
     default: return COMPAR_ERR_UNSUPPORTED;
   }
 }
@@ -528,6 +531,9 @@ int compar_variant_supported(compar_ctx_t ctx, int v, int64_t m, int64_t n, int6
   c.m = m;
   c.n = n;
   c.k = k;
+  c.lda = k;  // contiguous operands
+  c.ldb = n;
+  c.ldc = n;
   c.dtype = dtype;
   return variant_supported(ctx, v, c) ? 1 : 0;
 }

@@ -11,6 +11,9 @@
 //   SPLIT3_TF32 : 3xTF32 — A = Ahi + Alo, B = Bhi + Blo (TF32 pieces, kept
 //            in float32) and the three products on kind::tf32, the two small
 //            ones first, promoted after every stage
+//   SPLIT3_FUSED : 3xBF16 on float32 A and B read by TMA as they are; the
+//            epilogue warps split every stage in shared memory, in place
+//            (hi and lo 512-byte atoms interleaved), between promotions
 //   SPLIT6 : 3-piece split A = Ah + Am + Al (likewise B) and the six products
 //            whose size is at least 2^-16 of Ah*Bh: Ah*Bm, Am*Bh, Ah*Bl,
 //            Am*Bm, Al*Bh first, Ah*Bh last, promoted into FP32 registers
@@ -29,6 +32,7 @@
 // Every wait is bounded (ptx.cuh); on expiry the CTA drains its own copies
 // and MMAs, frees TMEM and returns with COMPAR_ERR_TIMEOUT in the error word.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,7 +60,7 @@ template <>
 struct Traits<COMPAR_V_TC_TF32> {
   static constexpr Kind kind = Kind::TF32;
   static constexpr int elem = 4, fmt = 2, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = false, small_first = false;
+  static constexpr bool b_mn = false, small_first = false, fused = false;
 };
 // 3xTF32: float32 pieces, 64-byte rows (16 K elements per 48 KB stage); each
 // stage is a promoted chunk with the two small products issued first, so
@@ -66,19 +70,19 @@ template <>
 struct Traits<COMPAR_V_SPLIT3_TF32> {
   static constexpr Kind kind = Kind::TF32;
   static constexpr int elem = 4, fmt = 2, pieces = 2, BN = 256, row = 64, chunk_kb = 1, epi = 8;
-  static constexpr bool b_mn = false, small_first = true;
+  static constexpr bool b_mn = false, small_first = true, fused = false;
 };
 template <>
 struct Traits<COMPAR_V_TC_BF16> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = true, small_first = false;
+  static constexpr bool b_mn = true, small_first = false, fused = false;
 };
 template <>
 struct Traits<COMPAR_V_TC_FP8> {
   static constexpr Kind kind = Kind::F8;
   static constexpr int elem = 1, fmt = 0, pieces = 1, BN = 256, row = 128, chunk_kb = 0, epi = 4;
-  static constexpr bool b_mn = false, small_first = false;
+  static constexpr bool b_mn = false, small_first = false, fused = false;
 };
 // 3xBF16: 64-byte rows give 48 KB stages (four of them) for a 128 x 256 tile;
 // promotion every 8 stages = 256 K elements.
@@ -86,7 +90,17 @@ template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
-  static constexpr bool b_mn = false, small_first = false;
+  static constexpr bool b_mn = false, small_first = false, fused = false;
+};
+// Fused 3xBF16: a stage holds the float32 A tile (128 rows x 32 K, 16 KB)
+// and B tile (32 K x 256 N in 16 boxes of 16 columns, 32 KB) as TMA wrote
+// them; the split overwrites each with its bf16 hi and lo pieces, which take
+// the same bytes, so the ring keeps the four 48 KB stages of SPLIT3.
+template <>
+struct Traits<COMPAR_V_SPLIT3_FUSED> {
+  static constexpr Kind kind = Kind::F16;
+  static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
+  static constexpr bool b_mn = false, small_first = false, fused = true;
 };
 // 6-product split: three pieces per operand make 72 KB stages (three of
 // them).  Each stage is its own promoted chunk: within it the five small
@@ -96,7 +110,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT6> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 3, BN = 256, row = 64, chunk_kb = 1, epi = 8;
-  static constexpr bool b_mn = false, small_first = true;
+  static constexpr bool b_mn = false, small_first = true, fused = false;
 };
 
 template <int V>
@@ -217,6 +231,196 @@ __device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity, uint6
   return true;
 }
 
+// ------------------------------------------------------------------ in-place split
+// bf16 pieces of 8 floats: hi = bf16(x) (round to nearest even), lo =
+// bf16(x - hi) (the residual is exact in float32), packed low element first.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(a))) |
+         (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(b))) << 16);
+}
+__device__ __forceinline__ float bf16_residual(float x) {
+  return x - __bfloat162float(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+  hi = make_uint4(bf16_pair(x[0], x[1]), bf16_pair(x[2], x[3]), bf16_pair(x[4], x[5]),
+                  bf16_pair(x[6], x[7]));
+  lo = make_uint4(bf16_pair(bf16_residual(x[0]), bf16_residual(x[1])),
+                  bf16_pair(bf16_residual(x[2]), bf16_residual(x[3])),
+                  bf16_pair(bf16_residual(x[4]), bf16_residual(x[5])),
+                  bf16_pair(bf16_residual(x[6]), bf16_residual(x[7])));
+}
+
+// The same for x[o .. o+7] with each packed pair's halves permuted by
+// __byte_perm selector `perm` (0x3210 keeps them, 0x1032 swaps them).
+__device__ __forceinline__ void split8_perm(const float (&x)[16], int o, uint32_t perm, uint4& hi,
+                                            uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = __byte_perm(bf16_pair(x[o + 2 * i], x[o + 2 * i + 1]), 0, perm);
+    l[i] = __byte_perm(bf16_pair(bf16_residual(x[o + 2 * i]), bf16_residual(x[o + 2 * i + 1])), 0,
+                       perm);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Splits one stage of the fused 3xBF16 variant in place.  As TMA wrote it,
+// A is [128 rows][32 K] float32 (128-byte rows) and B is 16 boxes of
+// [32 K][16 N] float32 (64-byte rows, box h at 2048 h).  Afterwards every
+// 1024 bytes hold an 8-row atom of the hi piece (+0) and of the lo piece
+// (+512), K-major with the 64-byte swizzle (16-byte chunk c of row r at
+// c ^ ((r >> 1) & 3)): A rows 8j..8j+7 in [1024 j, +1024), B columns
+// 8j..8j+7 likewise.  Each region is read whole by one warp before that warp
+// writes it (warp cw: A rows 16cw..16cw+15, B boxes 2cw and 2cw+1), so no
+// other warp's data is overwritten.  Loads and stores are bank-conflict free.
+__device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_st, int cw,
+                                                     int lane) {
+  {
+    // A: lane = (row r of the 8-row group, 32-byte quarter q of the row)
+    const int r = lane >> 2, q = lane & 3, h0 = r & 1;
+    const int off = 64 * r + 16 * (q ^ ((r >> 1) & 3));
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+      uint8_t* g = a_st + 1024 * (2 * cw + gi);
+      const float4 u = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * h0);
+      const float4 v = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * (h0 ^ 1));
+      __syncwarp();
+      const float4 lo4 = h0 ? v : u, hi4 = h0 ? u : v;  // elements 8q..8q+3, 8q+4..8q+7
+      const float x[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+      uint4 hi, lo;
+      split8(x, hi, lo);
+      *reinterpret_cast<uint4*>(g + off) = hi;
+      *reinterpret_cast<uint4*>(g + 512 + off) = lo;
+    }
+  }
+#pragma unroll
+  for (int bi = 0; bi < 2; ++bi) {
+    // B: lane = (column nn of the box, K half kh); in load i the two halves
+    // read rows i and 16 + (i ^ 1), 64 bytes apart modulo 128
+    uint8_t* box = b_st + 2048 * (2 * cw + bi);
+    const int nn = lane & 15, kh = lane >> 4;
+    float t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      t[i] = *reinterpret_cast<const float*>(box + 64 * (16 * kh + (i ^ kh)) + 4 * nn);
+    __syncwarp();
+    // t[i] holds K 16kh + (i ^ kh): for kh = 1 each pair is swapped, which
+    // swapping the halves of its packed bf16 pair undoes
+    const uint32_t perm = kh ? 0x1032u : 0x3210u;
+    uint4 hi0, lo0, hi1, lo1;
+    split8_perm(t, 0, perm, hi0, lo0);
+    split8_perm(t, 8, perm, hi1, lo1);
+    const int rr = nn & 7, sw = (rr >> 1) & 3;
+    uint8_t* atom = box + 1024 * (nn >> 3) + 64 * rr;
+    *reinterpret_cast<uint4*>(atom + 16 * ((2 * kh) ^ sw)) = hi0;
+    *reinterpret_cast<uint4*>(atom + 512 + 16 * ((2 * kh) ^ sw)) = lo0;
+    *reinterpret_cast<uint4*>(atom + 16 * ((2 * kh + 1) ^ sw)) = hi1;
+    *reinterpret_cast<uint4*>(atom + 512 + 16 * ((2 * kh + 1) ^ sw)) = lo1;
+  }
+}
+
+// End of a promoted item in the epilogue: stores the tile from `sum` (a
+// classic unit, or a stream-K tile with one contributor) or publishes this
+// CTA's stream-K piece and, if this CTA arrived last, sums the pieces and
+// stores the tile.  Returns false when a bounded wait gave up.  `sum` is not
+// used after the store or the publication, so the registers of the sums are
+// free.  Every contributor of a stream-K tile publishes its partial sum and
+// counts itself in; the last to arrive adds the pieces in contributor order
+// (so the result does not depend on which CTA finished last).  No CTA waits
+// for another.
+template <int NF, int kEpiThreads, int BN>
+__device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem& it,
+                                               const float (&sum)[NF][32], uint64_t* epi_bar,
+                                               uint32_t& epi_uses, volatile int* last_flag,
+                                               const dev::WaitCtx& w, int etid, int lane,
+                                               float* out, int64_t out_ld, int row_q, int col_s,
+                                               float alpha, float beta, bool vec_out) {
+  int nc = 1, b0 = 0, first = 0, t = 0;
+  if (it.piece >= 0) {
+    t = it.tile - p.sk_tile0;
+    first = t * p.sk_cpt;
+    b0 = sk_cta_of(p, first);
+    nc = sk_cta_of(p, first + p.sk_cpt - 1) - b0 + 1;
+  }
+  if (nc == 1) {
+    if (row_q < p.M && col_s < p.N) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                      alpha, beta, vec_out, lane);
+    }
+    return true;
+  }
+  constexpr int64_t kSlab = static_cast<int64_t>(kBM) * BN / 4;  // float4 per piece
+  auto slab = [&](int cta, int k) {
+    return reinterpret_cast<float4*>(p.sk_slab) + (2 * static_cast<int64_t>(cta) + k) * kSlab;
+  };
+  float4* mine = slab(blockIdx.x, it.piece);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4)
+      mine[(f * 8 + j4) * kEpiThreads + etid] =
+          make_float4(sum[f][4 * j4], sum[f][4 * j4 + 1], sum[f][4 * j4 + 2], sum[f][4 * j4 + 3]);
+  __threadfence();
+  // bounded rendezvous: a CTA that gave up elsewhere cannot hang here
+  dev::mbar_arrive(epi_bar);
+  if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
+  if (etid == 0) {
+    __threadfence();
+    *last_flag = atomicAdd(p.sk_count + t, 1u) == static_cast<unsigned int>(nc - 1);
+  }
+  dev::mbar_arrive(epi_bar);
+  if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
+  if (!*last_flag) return true;
+  __threadfence();
+  // the pieces in contributor order, this CTA's own from its slab too, so
+  // that its registers are free for the sums
+  const int k0 = sk_start(p, b0) < first ? 1 : 0;  // b0's piece of this tile
+  if (row_q < p.M && col_s < p.N) {
+    // two fragments at a time: 16 independent loads in flight per
+    // contributor, so a tile costs NF / 2 * nc L2 round trips
+    static_assert(NF % 2 == 0, "fragment pairs");
+#pragma unroll 1
+    for (int f2 = 0; f2 < NF; f2 += 2) {
+      const int64_t base = f2 * 8 * kEpiThreads + etid;
+      float4 acc[16];
+      const float4* s0 = slab(b0, k0) + base;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[e] = __ldcg(s0 + e * kEpiThreads);
+      for (int jj = 1; jj < nc; ++jj) {
+        const float4* sj = slab(b0 + jj, 0) + base;
+        float4 c[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) c[e] = __ldcg(sj + e * kEpiThreads);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          acc[e].x += c[e].x;
+          acc[e].y += c[e].y;
+          acc[e].z += c[e].z;
+          acc[e].w += c[e].w;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          v[4 * j4] = acc[8 * h + j4].x;
+          v[4 * j4 + 1] = acc[8 * h + j4].y;
+          v[4 * j4 + 2] = acc[8 * h + j4].z;
+          v[4 * j4 + 3] = acc[8 * h + j4].w;
+        }
+        const int f = f2 + h;
+        store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                      alpha, beta, vec_out, lane);
+      }
+    }
+  }
+  return true;
+}
+
 template <int V>
 __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -242,7 +446,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
   uint64_t* tempty = tfull + 2;  // [2]
   uint64_t* drain = tempty + 2;
   uint64_t* epi_bar = drain + 1;  // rendezvous of the epilogue warps (stream-K)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_bar + 1);
+  uint64_t* split_done = epi_bar + 1;  // [S] fused variant: stage split, MMA may read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(split_done + S);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* last_flag = abort_flag + 1;
 
@@ -260,6 +465,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     }
     dev::mbar_init(drain, 1);
     dev::mbar_init(epi_bar, L::kEpiThreads);
+    for (int s = 0; s < S; ++s) dev::mbar_init(&split_done[s], T::epi);
     *abort_flag = 0;
     dev::fence_barrier_init();
   }
@@ -304,6 +510,13 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         const int x = kb * L::kElemsPerStage;
         uint8_t* a_dst = sA + (stage * P) * L::kABytes;
         uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
+        if constexpr (T::fused) {
+          // float32 tiles as stored: A [128 rows][32 K], B 16 boxes [32 K][16 N]
+          dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
+#pragma unroll
+          for (int h = 0; h < BN / 16; ++h)
+            dev::tma_load_2d(b_dst + 2048 * h, &tmB, &full[stage], nb * BN + 16 * h, x);
+        } else {
         dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
         if constexpr (P >= 2) dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
         if constexpr (P == 3)
@@ -324,6 +537,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           if constexpr (P >= 2) dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
           if constexpr (P == 3)
             dev::tma_load_2d(b_dst + 2 * L::kBBytes, &tmB3, &full[stage], x, nb * BN);
+        }
         }
         issued |= 1u << stage;
         issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
@@ -359,7 +573,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         const uint32_t d_tmem = tmem_base + acc * BN;
         const int kb_stop = min(kb_end, kb0 + chunk);
         for (int kb = kb0; kb < kb_stop; ++kb) {
-          if (!dev::mbar_wait(&full[stage], phase, w)) {
+          if (!dev::mbar_wait(T::fused ? &split_done[stage] : &full[stage], phase, w)) {
             ok = false;
             break;
           }
@@ -369,6 +583,9 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           // Descriptors of K step kk: A (K-major) advances 32 bytes inside its
           // swizzled rows; an MN-major B advances 16 K rows (2048 bytes).
           auto b_desc = [&](int piece, int kk) -> uint64_t {
+            if constexpr (T::fused)
+              return dev::smem_desc_sw64_kmajor_strided(b0 + piece * 512, 1024) +
+                     (static_cast<uint64_t>(kk * 32) >> 4);
             const uint32_t base = b0 + piece * L::kBBytes;
             if constexpr (T::b_mn)
               return dev::smem_desc_sw128_mnmajor(base + kk * 2048, L::kMnBox);
@@ -376,6 +593,9 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
               return dev::smem_desc_kmajor<T::row>(base) + (static_cast<uint64_t>(kk * 32) >> 4);
           };
           auto a_desc = [&](int piece, int kk) -> uint64_t {
+            if constexpr (T::fused)
+              return dev::smem_desc_sw64_kmajor_strided(a0 + piece * 512, 1024) +
+                     (static_cast<uint64_t>(kk * 32) >> 4);
             return dev::smem_desc_kmajor<T::row>(a0 + piece * L::kABytes) +
                    (static_cast<uint64_t>(kk * 32) >> 4);
           };
@@ -455,7 +675,89 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     const float beta = split ? 0.f : p.beta;
     uint32_t epi_uses = 0;  // completed phases of epi_bar
     const int etid = threadIdx.x - 64;
-    for (int i = 0; ok && get_item<kChunkKB>(p, i, it); ++i) {
+    if constexpr (T::fused) {
+      // The epilogue warps also split the stages: each stage is split as
+      // soon as TMA has landed it, and a K chunk is promoted once the split
+      // has run kLag stages past the chunk's end, so the MMA still has split
+      // stages queued while these warps read TMEM or store a tile.
+      constexpr int kLag = 2;
+      const int cw = warp - 2;
+      uint32_t stage = 0, phase = 0;
+      int g = 0;              // stages split so far
+      WorkItem cit, pit;      // split cursor, promotion cursor
+      int ci = 0;
+      bool c_have = get_item<kChunkKB>(p, 0, cit);
+      int ckb = cit.kb_begin;
+      int p_g0 = 0;           // split index of the promotion item's first stage
+      for (int pi = 0; ok && get_item<kChunkKB>(p, pi, pit); ++pi) {
+        // one promoted item: sum lives only here
+        float sum[NF][32];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[f][j] = 0.f;
+        for (int kb0 = pit.kb_begin; ok && kb0 < pit.kb_end; kb0 += kChunkKB) {
+          // split up to kLag stages past this chunk's last stage
+          const int last = p_g0 + min(pit.kb_end, kb0 + kChunkKB) - pit.kb_begin - 1;
+          while (c_have && g <= last + kLag) {
+            if (!dev::mbar_wait(&full[stage], phase, w)) {
+              ok = false;
+              break;
+            }
+            split_stage_in_place(sA + (stage * P) * L::kABytes, sB + (stage * P) * L::kBBytes,
+                                 cw, lane);
+            dev::fence_proxy_async_smem();  // generic writes before the MMA's reads
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&split_done[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+            ++g;
+            if (++ckb == cit.kb_end) {
+              c_have = get_item<kChunkKB>(p, ++ci, cit);
+              if (c_have) ckb = cit.kb_begin;
+            }
+          }
+          if (!ok) break;
+          const uint32_t acc = acc_iter & 1;
+          const uint32_t acc_phase = (acc_iter >> 1) & 1;
+          if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) {
+            ok = false;
+            break;
+          }
+          dev::tc_fence_after();
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            uint32_t r[32];
+            dev::tmem_ld_16x256b_x8(
+                tmem_base + (static_cast<uint32_t>(quarter * 32 + 16 * (f & 1)) << 16) +
+                    acc * BN + cslice * EC + 64 * (f >> 1),
+                r);
+            dev::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[f][j] += __uint_as_float(r[j]);
+          }
+          dev::tc_fence_before();
+          dev::mbar_arrive(&tempty[acc]);
+          ++acc_iter;
+        }
+        if (!ok) break;
+        int mb, nb;
+        tile_coords(pit.tile, p.tiles_m, p.tiles_n, mb, nb);
+        const int row_q = mb * kBM + quarter * 32;
+        const int col_s = nb * BN + cslice * EC;
+        float* out = split ? p.partial + static_cast<int64_t>(pit.split) * p.M * p.N : p.C;
+        if (!finish_promoted<NF, L::kEpiThreads, BN>(p, pit, sum, epi_bar, epi_uses, last_flag,
+                                                     w, etid, lane, out, out_ld, row_q, col_s,
+                                                     alpha, beta, vec_out)) {
+          ok = false;
+          break;
+        }
+        p_g0 += pit.kb_end - pit.kb_begin;
+      }
+    }
+    for (int i = 0; !T::fused && ok && get_item<kChunkKB>(p, i, it); ++i) {
       int mb, nb;
       tile_coords(it.tile, p.tiles_m, p.tiles_n, mb, nb);
       const int num_chunks =
@@ -496,99 +798,11 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           dev::mbar_arrive(&tempty[acc]);
         }
         if (!ok) break;
-        if (it.piece >= 0) {
-          // Stream-K piece.  Every contributor of the tile publishes its
-          // partial sum, then counts itself in; the last to arrive adds the
-          // pieces in contributor order (so the result does not depend on
-          // which CTA finished last) and stores the tile.  No CTA waits for
-          // another.
-          const int t = it.tile - p.sk_tile0;
-          const int first = t * p.sk_cpt;
-          const int b0 = sk_cta_of(p, first);
-          const int nc = sk_cta_of(p, first + p.sk_cpt - 1) - b0 + 1;
-          if (nc > 1) {
-            constexpr int64_t kSlab = static_cast<int64_t>(kBM) * BN / 4;  // float4 per piece
-            auto slab = [&](int cta, int k) {
-              return reinterpret_cast<float4*>(p.sk_slab) +
-                     (2 * static_cast<int64_t>(cta) + k) * kSlab;
-            };
-            float4* mine = slab(blockIdx.x, it.piece);
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-#pragma unroll
-              for (int j4 = 0; j4 < 8; ++j4)
-                mine[(f * 8 + j4) * L::kEpiThreads + etid] =
-                    make_float4(sum[f][4 * j4], sum[f][4 * j4 + 1], sum[f][4 * j4 + 2],
-                                sum[f][4 * j4 + 3]);
-            __threadfence();
-            // bounded rendezvous: a CTA that gave up elsewhere cannot hang here
-            dev::mbar_arrive(epi_bar);
-            if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) {
-              ok = false;
-              break;
-            }
-            if (etid == 0) {
-              __threadfence();
-              *last_flag = atomicAdd(p.sk_count + t, 1u) == static_cast<unsigned int>(nc - 1);
-            }
-            dev::mbar_arrive(epi_bar);
-            if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) {
-              ok = false;
-              break;
-            }
-            if (!*last_flag) continue;
-            __threadfence();
-            // the pieces in contributor order, this CTA's own from its slab
-            // too, so that its registers are free for the sums
-            const int k0 = sk_start(p, b0) < first ? 1 : 0;  // b0's piece of this tile
-            if (row_q < p.M && col_s < p.N) {
-              // two fragments at a time: 16 independent loads in flight per
-              // contributor, so a tile costs NF / 2 * nc L2 round trips
-              static_assert(NF % 2 == 0, "fragment pairs");
-#pragma unroll 1
-              for (int f2 = 0; f2 < NF; f2 += 2) {
-                const int64_t base = f2 * 8 * L::kEpiThreads + etid;
-                float4 acc[16];
-                const float4* s0 = slab(b0, k0) + base;
-#pragma unroll
-                for (int e = 0; e < 16; ++e) acc[e] = __ldcg(s0 + e * L::kEpiThreads);
-                for (int jj = 1; jj < nc; ++jj) {
-                  const float4* sj = slab(b0 + jj, 0) + base;
-                  float4 c[16];
-#pragma unroll
-                  for (int e = 0; e < 16; ++e) c[e] = __ldcg(sj + e * L::kEpiThreads);
-#pragma unroll
-                  for (int e = 0; e < 16; ++e) {
-                    acc[e].x += c[e].x;
-                    acc[e].y += c[e].y;
-                    acc[e].z += c[e].z;
-                    acc[e].w += c[e].w;
-                  }
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  float v[32];
-#pragma unroll
-                  for (int j4 = 0; j4 < 8; ++j4) {
-                    v[4 * j4] = acc[8 * h + j4].x;
-                    v[4 * j4 + 1] = acc[8 * h + j4].y;
-                    v[4 * j4 + 2] = acc[8 * h + j4].z;
-                    v[4 * j4 + 3] = acc[8 * h + j4].w;
-                  }
-                  const int f = f2 + h;
-                  store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
-                                col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
-                }
-              }
-            }
-            continue;
-          }
-        }
-        if (row_q < p.M && col_s < p.N) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f)
-            store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
-                            col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
+        if (!finish_promoted<NF, L::kEpiThreads, BN>(p, it, sum, epi_bar, epi_uses, last_flag, w,
+                                                     etid, lane, out, out_ld, row_q, col_s,
+                                                     alpha, beta, vec_out)) {
+          ok = false;
+          break;
         }
         continue;
       }
@@ -645,7 +859,8 @@ int round_up(int64_t x, int64_t m) { return static_cast<int>((x + m - 1) / m * m
 CUtensorMapDataType map_type(int v) {
   switch (v) {
     case COMPAR_V_TC_TF32:
-    case COMPAR_V_SPLIT3_TF32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    case COMPAR_V_SPLIT3_TF32:
+    case COMPAR_V_SPLIT3_FUSED: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     case COMPAR_V_TC_FP8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
     default: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   }
@@ -666,7 +881,8 @@ struct TcPlan {
 constexpr int kPromotedBN = 256;
 static_assert(Traits<COMPAR_V_SPLIT3>::BN == kPromotedBN &&
                   Traits<COMPAR_V_SPLIT6>::BN == kPromotedBN &&
-                  Traits<COMPAR_V_SPLIT3_TF32>::BN == kPromotedBN,
+                  Traits<COMPAR_V_SPLIT3_TF32>::BN == kPromotedBN &&
+                  Traits<COMPAR_V_SPLIT3_FUSED>::BN == kPromotedBN,
               "stream-K pieces are kBM x kPromotedBN");
 
 int chunk_kb_of(int v) {
@@ -674,6 +890,7 @@ int chunk_kb_of(int v) {
     case COMPAR_V_SPLIT3: return Traits<COMPAR_V_SPLIT3>::chunk_kb;
     case COMPAR_V_SPLIT6: return Traits<COMPAR_V_SPLIT6>::chunk_kb;
     case COMPAR_V_SPLIT3_TF32: return Traits<COMPAR_V_SPLIT3_TF32>::chunk_kb;
+    case COMPAR_V_SPLIT3_FUSED: return Traits<COMPAR_V_SPLIT3_FUSED>::chunk_kb;
     default: return 0;
   }
 }
@@ -742,12 +959,20 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
     else
       return tma_encode_2d(m, dt, T::elem, base, c.k, c.n, ldb, box_k, T::BN, T::row);
   };
-  int rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
-  if (rc == COMPAR_OK) rc = enc_b(&tb, B);
+  int rc;
+  if constexpr (T::fused) {
+    // float32 A [rows][K] in boxes of 32 K x 128 rows, B [K][N] in boxes of
+    // 16 N x 32 K, unswizzled (the kernel splits them in shared memory)
+    rc = tma_encode_2d(&ta, dt, 4, A, c.k, c.m, lda, box_k, kBM, 0);
+    if (rc == COMPAR_OK) rc = tma_encode_2d(&tb, dt, 4, B, c.n, c.k, ldb, 16, box_k, 0);
+  } else {
+    rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
+    if (rc == COMPAR_OK) rc = enc_b(&tb, B);
+  }
   if (rc != COMPAR_OK) return rc;
   ta2 = ta3 = ta;
   tb2 = tb3 = tb;
-  if (T::pieces >= 2) {
+  if (T::pieces >= 2 && !T::fused) {
     rc = tma_encode_2d(&ta2, dt, T::elem, A2, c.k, c.m, lda, box_k, kBM, T::row);
     if (rc == COMPAR_OK) rc = enc_b(&tb2, B2);
     if (rc != COMPAR_OK) return rc;
@@ -820,6 +1045,12 @@ bool tc_supported(int v, const GemmCall& c) {
     case COMPAR_V_SPLIT3:
     case COMPAR_V_SPLIT6:
     case COMPAR_V_SPLIT3_TF32: return c.dtype == COMPAR_F32;
+    case COMPAR_V_SPLIT3_FUSED:
+      // TMA reads the caller's float32 A and B: 16-byte rows and bases
+      // (null pointers: a query about contiguous operands)
+      return c.dtype == COMPAR_F32 && c.lda % 4 == 0 && c.ldb % 4 == 0 &&
+             (reinterpret_cast<uintptr_t>(c.A) & 15) == 0 &&
+             (reinterpret_cast<uintptr_t>(c.B) & 15) == 0;
     default: return false;
   }
 }
@@ -833,6 +1064,30 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
               cudaStream_t s) {
   if (!tc_supported(v, c)) return COMPAR_ERR_UNSUPPORTED;
   if (!tma_available()) return COMPAR_ERR_UNSUPPORTED;
+  if (v == COMPAR_V_SPLIT3_FUSED) {
+    // no pre-pass: workspace only for split-K partials or stream-K pieces
+    const TcPlan plan = tc_plan(v, c, num_sms);
+    const size_t part_bytes =
+        plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
+    const size_t slab_bytes =
+        plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kPromotedBN * 4 : 0;
+    const size_t count_bytes =
+        plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
+    float* partial = nullptr;
+    float* sk_slab = nullptr;
+    unsigned int* sk_count = nullptr;
+    if (part_bytes + slab_bytes + count_bytes > 0) {
+      const int rc = ws.ensure(part_bytes + slab_bytes + count_bytes, s);
+      if (rc != COMPAR_OK) return rc;
+      uint8_t* base = static_cast<uint8_t*>(ws.ptr);
+      if (part_bytes) partial = reinterpret_cast<float*>(base);
+      if (slab_bytes) sk_slab = reinterpret_cast<float*>(base + part_bytes);
+      if (count_bytes) sk_count = reinterpret_cast<unsigned int*>(base + part_bytes + slab_bytes);
+    }
+    return run_tc<COMPAR_V_SPLIT3_FUSED>(c, c.A, c.lda, c.B, c.ldb, nullptr, nullptr, nullptr,
+                                         nullptr, nullptr, nullptr, plan, partial, sk_slab,
+                                         sk_count, g, num_sms, s);
+  }
   const int elem = (v == COMPAR_V_TC_TF32 || v == COMPAR_V_SPLIT3_TF32) ? 4
                    : (v == COMPAR_V_TC_FP8 ? 1 : 2);
   const int pieces =

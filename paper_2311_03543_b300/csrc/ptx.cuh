@@ -248,6 +248,21 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t smem_addr) {
   return d;
 }
 
+// K-major tile with the 64-byte swizzle whose 8-row groups (512-byte
+// atoms) are `group_stride` bytes apart: with stride 1024 two tiles can
+// interleave atom by atom (the in-place split of the fused 3xBF16 variant
+// puts hi at +0 and lo at +512 of every 1024 bytes).
+__device__ __forceinline__ uint64_t smem_desc_sw64_kmajor_strided(uint32_t smem_addr,
+                                                                  uint32_t group_stride) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>((group_stride >> 4) & 0x3FFF) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
+
 // MN-major operand tile with the 128-byte swizzle, as TMA writes a box of
 // 64 MN-elements (128 bytes, 16-bit types) by K rows: one 128-byte row per K
 // index; 8-row K groups are 1024 bytes apart (stride byte offset) and

@@ -62,6 +62,9 @@ ErrorModel::ErrorModel() {
   c0[COMPAR_V_TC_FP8][COMPAR_F8E4M3] = 0.f;
   c0[COMPAR_V_SPLIT3][COMPAR_F32] = 5e-6f;
   c1[COMPAR_V_SPLIT3][COMPAR_F32] = 0.05f;
+  // the fused variant computes the same products in the same order
+  c0[COMPAR_V_SPLIT3_FUSED][COMPAR_F32] = 5e-6f;
+  c1[COMPAR_V_SPLIT3_FUSED][COMPAR_F32] = 0.05f;
   // 6-product split: the pieces hold all 24 bits, the dropped terms are
   // ~2^-26 relative; what remains is FP32 accumulation of the promoted
   // per-stage partials (SIMT-like) and the tensor core's truncating adds.
@@ -187,6 +190,13 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
       flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
       bytes += (M * K + K * N) * 8;
       ovh_us = 14;
+      break;
+    case COMPAR_V_SPLIT3_FUSED:
+      // no pre-pass: float32 operands read by the GEMM kernel itself
+      peak = 1.5e15 / 3;
+      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      bytes += (M * K + K * N) * 4;
+      ovh_us = 8;
       break;
     case COMPAR_V_SPLIT6:
       peak = 1.5e15 / 6;

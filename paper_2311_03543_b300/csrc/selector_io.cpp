@@ -16,7 +16,7 @@ namespace compar {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'M', 'P', 'R', 'S', 'E', 'L', '1'};
-constexpr uint32_t kVersion = 5;  // 5: variant ids 0..8 (18 MLP outputs)
+constexpr uint32_t kVersion = 6;  // 6: variant ids 0..9 (20 MLP outputs)
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
   uint64_t h = 1469598103934665603ull;

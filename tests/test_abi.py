@@ -55,7 +55,8 @@ def test_variant_ids_are_stable():
         "naive-f32", "simt-f32", "tc-tf32", "tc-bf16", "tc-fp8", "split-3xbf16", "grouped"]
     assert cp.compar_variant_name(7).decode() == "split-6xbf16"
     assert cp.compar_variant_name(8).decode() == "split-3xtf32"
-    assert (cp.V_GROUPED, cp.V_SPLIT6, cp.V_SPLIT3_TF32) == (6, 7, 8)
+    assert cp.compar_variant_name(9).decode() == "split-3xbf16-fused"
+    assert (cp.V_GROUPED, cp.V_SPLIT6, cp.V_SPLIT3_TF32, cp.V_SPLIT3_FUSED) == (6, 7, 8, 9)
     h = cp.Context.host()
     try:
         assert not h.supported(cp.V_GROUPED, 64, 64, 64, cp.F32)   # never a single call

@@ -134,6 +134,41 @@ def test_split3_matches_its_three_products(ctx):
     assert N.rel_frobenius(got, three) <= TOL_F32
 
 
+@pytest.mark.parametrize("m,n,k", [(1, 4, 4), (3, 8, 12), (17, 40, 12), (33, 68, 20),
+                                   (127, 132, 128), (128, 256, 64), (200, 300, 332),
+                                   (300, 520, 1000), (2500, 2000, 1000), (16, 4096, 512)])
+def test_fused_split_matches_split3_bitwise(ctx, m, n, k):
+    """The fused variant splits in shared memory what the 3xBF16 pre-pass
+    splits in global memory (same rounding), and issues the same products in
+    the same order, tile decomposition and promotion: the results agree bit
+    for bit, ragged edges, split K and stream-K tails included.  (It needs
+    16-byte rows: N and K multiples of 4 for contiguous operands.)"""
+    A = W.normal(m, k, seed=71)
+    B = W.normal(k, n, seed=72)
+    C0 = W.uniform(m, n, seed=73)
+    got = _run(ctx, 9, A, B, alpha=0.75, beta=0.5, C0=C0)
+    ref3 = _run(ctx, 5, A, B, alpha=0.75, beta=0.5, C0=C0)
+    assert np.array_equal(got, ref3)
+    assert N.rel_frobenius(got, oracle.gemm(A, B, alpha=0.75, beta=0.5, C0=C0)) <= TOL_F32
+
+
+def test_fused_split_refuses_unaligned_operands(ctx):
+    import torch
+    import paper_2311_03543_b300 as cp
+    m, n, k = 64, 64, 30                      # 120-byte rows of A
+    A = torch.zeros((m, k), device="cuda")
+    B = torch.zeros((k, n), device="cuda")
+    C = torch.zeros((m, n), device="cuda")
+    ctx.force_variant(cp.V_SPLIT3_FUSED)
+    try:
+        with pytest.raises(cp.ComparError):
+            ctx.gemm(A, B, C)
+    finally:
+        ctx.force_variant(None)
+    assert ctx.supported(cp.V_SPLIT3_FUSED, 64, 64, 32, cp.F32)
+    assert not ctx.supported(cp.V_SPLIT3_FUSED, 64, 64, 30, cp.F32)
+
+
 def test_split3_tf32_matches_its_three_products(ctx):
     import paper_2311_03543_b300 as cp
     m, n, k = 192, 320, 512
@@ -164,7 +199,7 @@ def test_split6_at_simt_error_level(ctx, m, n, k):
     assert e6 <= 0.5 * e5
 
 
-@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 4, 5, 7, 8, 9])
 def test_all_ones_every_entry_is_k(ctx, v):
     m, n, k = 130, 260, 300
     got = _run(ctx, v, np.ones((m, k), np.float32), np.ones((k, n), np.float32))
@@ -174,7 +209,7 @@ def test_all_ones_every_entry_is_k(ctx, v):
         assert np.all(got == k)
 
 
-@pytest.mark.parametrize("v", [0, 1, 2, 3, 5, 7, 8])
+@pytest.mark.parametrize("v", [0, 1, 2, 3, 5, 7, 8, 9])
 def test_identity_exact_on_representable_values(ctx, v):
     n = 192
     A = W.integer_matrix(n, n, seed=15)           # integers are exact in every format
@@ -194,7 +229,7 @@ def test_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
-@pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8, 9])
 def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     """Few output tiles and a long K: the tensor-core variants split K over
     the SMs (partials reduced afterwards, beta applied once)."""
@@ -209,7 +244,7 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
-@pytest.mark.parametrize("v", [2, 3, 5, 7, 8])
+@pytest.mark.parametrize("v", [2, 3, 5, 7, 8, 9])
 def test_partial_last_wave_with_alpha_beta(ctx, v):
     """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
     persistent CTAs, cut into stream-K pieces for the promoted variants),
@@ -225,7 +260,8 @@ def test_partial_last_wave_with_alpha_beta(ctx, v):
 
 @pytest.mark.parametrize("v,m,n,k", [(5, 2500, 2000, 1000), (7, 2500, 2000, 1000),
                                      (8, 2500, 2000, 1000), (5, 1536, 2048, 2048),
-                                     (7, 1400, 2048, 777)])
+                                     (7, 1400, 2048, 777), (9, 2500, 2000, 1000),
+                                     (9, 1536, 2048, 2048)])
 def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     """A partial last wave of tiles (160 tiles: one full wave and 12 more) or
     a single partial wave (96 or 88 tiles) is cut into stream-K pieces of
@@ -240,7 +276,7 @@ def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     assert np.array_equal(got, again)
     rows = W.sample_rows(m, 96, seed=64)
     ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.25, C0=C0)
-    assert N.rel_frobenius(got[rows], ref) <= (TOL_F32 if v == 5 else TOL_SPLIT6)
+    assert N.rel_frobenius(got[rows], ref) <= (TOL_F32 if v in (5, 9) else TOL_SPLIT6)
 
 
 def test_k_zero_scales_c(ctx):

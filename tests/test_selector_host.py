@@ -30,8 +30,9 @@ def test_compute_calls_are_refused_without_a_device(hctx):
 
 def test_eligibility_by_tolerance(hctx):
     # FP32 inputs at 1e-5: only FP32-accurate variants (naive, simt, 3xbf16)
-    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3, cp.V_SPLIT3_TF32,
-                                                            cp.V_SPLIT6)
+    assert hctx.select(4096, 4096, 4096, cp.F32, 1e-5) in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3,
+                                                            cp.V_SPLIT3_TF32, cp.V_SPLIT6,
+                                                            cp.V_SPLIT3_FUSED)
     # at 1e-1 the fp8 variant is the fastest by the roofline prior for big shapes
     assert hctx.select(8192, 8192, 8192, cp.F32, 1e-1) == cp.V_TC_FP8
     # BF16 inputs can never run the f32-only variants
@@ -158,7 +159,8 @@ def test_online_exploration_stays_within_eligible_variants(hctx):
     seen = set()
     for _ in range(200):
         v = hctx.select(2048, 2048, 2048, cp.F32, 1e-5)
-        assert v in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3, cp.V_SPLIT6, cp.V_SPLIT3_TF32)
+        assert v in (cp.V_NAIVE, cp.V_SIMT, cp.V_SPLIT3, cp.V_SPLIT6, cp.V_SPLIT3_TF32,
+                     cp.V_SPLIT3_FUSED)
         seen.add(v)
     assert len(seen) >= 2
     explored, retrains = hctx.online_stats()
