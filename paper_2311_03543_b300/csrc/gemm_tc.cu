@@ -93,14 +93,15 @@ struct Traits<COMPAR_V_SPLIT3> {
   static constexpr bool b_mn = false, small_first = false, fused = false;
 };
 // Fused 3xBF16: a stage holds the float32 A tile (128 rows x 32 K, 16 KB)
-// and B tile (32 K x 256 N in 16 boxes of 16 columns, 32 KB) as TMA wrote
+// and B tile (32 K x 256 N in 16 boxes of 64 N x 8 K, 32 KB) as TMA wrote
 // them; the split overwrites each with its bf16 hi and lo pieces, which take
-// the same bytes, so the ring keeps the four 48 KB stages of SPLIT3.
+// the same bytes, so the ring keeps the four 48 KB stages of SPLIT3.  A
+// becomes K-major, B stays MN-major (as stored, no transpose).
 template <>
 struct Traits<COMPAR_V_SPLIT3_FUSED> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
-  static constexpr bool b_mn = false, small_first = false, fused = true;
+  static constexpr bool b_mn = true, small_first = false, fused = true;
 };
 // 6-product split: three pieces per operand make 72 KB stages (three of
 // them).  Each stage is its own promoted chunk: within it the five small
@@ -232,48 +233,33 @@ __device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity, uint6
 }
 
 // ------------------------------------------------------------------ in-place split
-// bf16 pieces of 8 floats: hi = bf16(x) (round to nearest even), lo =
+// bf16 pieces of a float4: hi = bf16(x) (round to nearest even), lo =
 // bf16(x - hi) (the residual is exact in float32), packed low element first.
-__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
-  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(a))) |
-         (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(b))) << 16);
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
-__device__ __forceinline__ float bf16_residual(float x) {
-  return x - __bfloat162float(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
-  hi = make_uint4(bf16_pair(x[0], x[1]), bf16_pair(x[2], x[3]), bf16_pair(x[4], x[5]),
-                  bf16_pair(x[6], x[7]));
-  lo = make_uint4(bf16_pair(bf16_residual(x[0]), bf16_residual(x[1])),
-                  bf16_pair(bf16_residual(x[2]), bf16_residual(x[3])),
-                  bf16_pair(bf16_residual(x[4]), bf16_residual(x[5])),
-                  bf16_pair(bf16_residual(x[6]), bf16_residual(x[7])));
-}
-
-// The same for x[o .. o+7] with each packed pair's halves permuted by
-// __byte_perm selector `perm` (0x3210 keeps them, 0x1032 swaps them).
-__device__ __forceinline__ void split8_perm(const float (&x)[16], int o, uint32_t perm, uint4& hi,
-                                            uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    h[i] = __byte_perm(bf16_pair(x[o + 2 * i], x[o + 2 * i + 1]), 0, perm);
-    l[i] = __byte_perm(bf16_pair(bf16_residual(x[o + 2 * i]), bf16_residual(x[o + 2 * i + 1])), 0,
-                       perm);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
+__device__ __forceinline__ void split4(const float4 v, uint2& hi, uint2& lo) {
+  hi.x = bf16x2_bits(v.x, v.y);
+  hi.y = bf16x2_bits(v.z, v.w);
+  // the hi values as float32: the bf16 bits in the upper half
+  const float hx = __uint_as_float(hi.x << 16), hy = __uint_as_float(hi.x & 0xFFFF0000u);
+  const float hz = __uint_as_float(hi.y << 16), hw = __uint_as_float(hi.y & 0xFFFF0000u);
+  lo.x = bf16x2_bits(v.x - hx, v.y - hy);
+  lo.y = bf16x2_bits(v.z - hz, v.w - hw);
 }
 
 // Splits one stage of the fused 3xBF16 variant in place.  As TMA wrote it,
 // A is [128 rows][32 K] float32 (128-byte rows) and B is 16 boxes of
-// [32 K][16 N] float32 (64-byte rows, box h at 2048 h).  Afterwards every
-// 1024 bytes hold an 8-row atom of the hi piece (+0) and of the lo piece
-// (+512), K-major with the 64-byte swizzle (16-byte chunk c of row r at
-// c ^ ((r >> 1) & 3)): A rows 8j..8j+7 in [1024 j, +1024), B columns
-// 8j..8j+7 likewise.  Each region is read whole by one warp before that warp
-// writes it (warp cw: A rows 16cw..16cw+15, B boxes 2cw and 2cw+1), so no
-// other warp's data is overwritten.  Loads and stores are bank-conflict free.
+// [8 K][64 N] float32 (256-byte rows; box (ng, kg) at 2048 (4 ng + kg)).
+// Afterwards every A region of 1024 bytes holds an 8-row atom of the hi
+// piece (+0) and of the lo piece (+512), K-major with the 64-byte swizzle
+// (16-byte chunk c of row r at c ^ ((r >> 1) & 3)); every B box holds an
+// 8-K-row atom of hi (+0) and lo (+1024), MN-major with the 128-byte swizzle
+// (chunk c of K row k at c ^ k).  Each region is read whole by one warp
+// before that warp writes it (warp cw: A rows 16cw..16cw+15, B boxes 2cw
+// and 2cw+1), so no other warp's data is overwritten.  Loads and stores are
+// bank-conflict free.
 __device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_st, int cw,
                                                      int lane) {
   {
@@ -286,37 +272,32 @@ __device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_s
       const float4 u = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * h0);
       const float4 v = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * (h0 ^ 1));
       __syncwarp();
-      const float4 lo4 = h0 ? v : u, hi4 = h0 ? u : v;  // elements 8q..8q+3, 8q+4..8q+7
-      const float x[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      *reinterpret_cast<uint4*>(g + off) = hi;
-      *reinterpret_cast<uint4*>(g + 512 + off) = lo;
+      uint2 h1, l1, h2, l2;
+      split4(h0 ? v : u, h1, l1);  // elements 8q..8q+3
+      split4(h0 ? u : v, h2, l2);  // elements 8q+4..8q+7
+      *reinterpret_cast<uint4*>(g + off) = make_uint4(h1.x, h1.y, h2.x, h2.y);
+      *reinterpret_cast<uint4*>(g + 512 + off) = make_uint4(l1.x, l1.y, l2.x, l2.y);
     }
   }
 #pragma unroll
   for (int bi = 0; bi < 2; ++bi) {
-    // B: lane = (column nn of the box, K half kh); in load i the two halves
-    // read rows i and 16 + (i ^ 1), 64 bytes apart modulo 128
+    // B: load i gives lane the float4 (N 4c..4c+3) of K row k = 2i + lane/16
     uint8_t* box = b_st + 2048 * (2 * cw + bi);
-    const int nn = lane & 15, kh = lane >> 4;
-    float t[16];
+    const int c = lane & 15, kh = lane >> 4;
+    float4 v[4];
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      t[i] = *reinterpret_cast<const float*>(box + 64 * (16 * kh + (i ^ kh)) + 4 * nn);
+    for (int i = 0; i < 4; ++i)
+      v[i] = *reinterpret_cast<const float4*>(box + 256 * (2 * i + kh) + 16 * c);
     __syncwarp();
-    // t[i] holds K 16kh + (i ^ kh): for kh = 1 each pair is swapped, which
-    // swapping the halves of its packed bf16 pair undoes
-    const uint32_t perm = kh ? 0x1032u : 0x3210u;
-    uint4 hi0, lo0, hi1, lo1;
-    split8_perm(t, 0, perm, hi0, lo0);
-    split8_perm(t, 8, perm, hi1, lo1);
-    const int rr = nn & 7, sw = (rr >> 1) & 3;
-    uint8_t* atom = box + 1024 * (nn >> 3) + 64 * rr;
-    *reinterpret_cast<uint4*>(atom + 16 * ((2 * kh) ^ sw)) = hi0;
-    *reinterpret_cast<uint4*>(atom + 512 + 16 * ((2 * kh) ^ sw)) = lo0;
-    *reinterpret_cast<uint4*>(atom + 16 * ((2 * kh + 1) ^ sw)) = hi1;
-    *reinterpret_cast<uint4*>(atom + 512 + 16 * ((2 * kh + 1) ^ sw)) = lo1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 2 * i + kh;
+      const int off = 128 * k + 16 * ((c >> 1) ^ k) + 8 * (c & 1);
+      uint2 hi, lo;
+      split4(v[i], hi, lo);
+      *reinterpret_cast<uint2*>(box + off) = hi;
+      *reinterpret_cast<uint2*>(box + 1024 + off) = lo;
+    }
   }
 }
 
@@ -511,11 +492,15 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
         uint8_t* a_dst = sA + (stage * P) * L::kABytes;
         uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
         if constexpr (T::fused) {
-          // float32 tiles as stored: A [128 rows][32 K], B 16 boxes [32 K][16 N]
+          // float32 tiles as stored: A [128 rows][32 K]; B box (ng, kg) =
+          // [8 K][64 N] at 2048 (4 ng + kg)
           dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
 #pragma unroll
-          for (int h = 0; h < BN / 16; ++h)
-            dev::tma_load_2d(b_dst + 2048 * h, &tmB, &full[stage], nb * BN + 16 * h, x);
+          for (int ng = 0; ng < BN / 64; ++ng)
+#pragma unroll
+            for (int kg = 0; kg < 4; ++kg)
+              dev::tma_load_2d(b_dst + 2048 * (4 * ng + kg), &tmB, &full[stage],
+                               nb * BN + 64 * ng, x + 8 * kg);
         } else {
         dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
         if constexpr (P >= 2) dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
@@ -583,9 +568,9 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           // Descriptors of K step kk: A (K-major) advances 32 bytes inside its
           // swizzled rows; an MN-major B advances 16 K rows (2048 bytes).
           auto b_desc = [&](int piece, int kk) -> uint64_t {
-            if constexpr (T::fused)
-              return dev::smem_desc_sw64_kmajor_strided(b0 + piece * 512, 1024) +
-                     (static_cast<uint64_t>(kk * 32) >> 4);
+            if constexpr (T::fused)  // MN-major: a K step of 16 rows is two 8-row groups
+              return dev::smem_desc_sw128_mnmajor_strided(b0 + piece * 1024 + kk * 4096, 8192,
+                                                          2048);
             const uint32_t base = b0 + piece * L::kBBytes;
             if constexpr (T::b_mn)
               return dev::smem_desc_sw128_mnmajor(base + kk * 2048, L::kMnBox);
@@ -962,9 +947,9 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   int rc;
   if constexpr (T::fused) {
     // float32 A [rows][K] in boxes of 32 K x 128 rows, B [K][N] in boxes of
-    // 16 N x 32 K, unswizzled (the kernel splits them in shared memory)
+    // 64 N x 8 K, unswizzled (the kernel splits them in shared memory)
     rc = tma_encode_2d(&ta, dt, 4, A, c.k, c.m, lda, box_k, kBM, 0);
-    if (rc == COMPAR_OK) rc = tma_encode_2d(&tb, dt, 4, B, c.n, c.k, ldb, 16, box_k, 0);
+    if (rc == COMPAR_OK) rc = tma_encode_2d(&tb, dt, 4, B, c.n, c.k, ldb, 64, 8, 0);
   } else {
     rc = tma_encode_2d(&ta, dt, T::elem, A, c.k, c.m, lda, box_k, kBM, T::row);
     if (rc == COMPAR_OK) rc = enc_b(&tb, B);

@@ -279,6 +279,21 @@ __device__ __forceinline__ uint64_t smem_desc_sw128_mnmajor(uint32_t smem_addr,
   return d;
 }
 
+// The same layout with hi/lo atoms interleaved (fused 3xBF16 split): 8-row
+// K groups `k_group_bytes` apart, 64-element MN groups `mn_group_bytes`
+// apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128_mnmajor_strided(uint32_t smem_addr,
+                                                                    uint32_t mn_group_bytes,
+                                                                    uint32_t k_group_bytes) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>((mn_group_bytes >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((k_group_bytes >> 4) & 0x3FFF) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
 // Instruction descriptor: D = F32, K-major A and B, shape M x N.
 // a_fmt/b_fmt: kind::f16 -> 0 f16 / 1 bf16; kind::tf32 -> 2; kind::f8f6f4 -> 0 e4m3.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t a_fmt, uint32_t b_fmt, int M, int N) {
