@@ -96,7 +96,8 @@ struct Traits<COMPAR_V_SPLIT3> {
 // and B tile (32 K x 256 N in 16 boxes of 64 N x 8 K, 32 KB) as TMA wrote
 // them; the split overwrites each with its bf16 hi and lo pieces, which take
 // the same bytes, so the ring keeps the four 48 KB stages of SPLIT3.  A
-// becomes K-major, B stays MN-major (as stored, no transpose).
+// becomes K-major, B stays MN-major (as stored, no transpose).  (Sixteen
+// epilogue warps with 64 sums each were slower: 96 registers a thread.)
 template <>
 struct Traits<COMPAR_V_SPLIT3_FUSED> {
   static constexpr Kind kind = Kind::F16;
@@ -257,18 +258,21 @@ __device__ __forceinline__ void split4(const float4 v, uint2& hi, uint2& lo) {
 // (16-byte chunk c of row r at c ^ ((r >> 1) & 3)); every B box holds an
 // 8-K-row atom of hi (+0) and lo (+1024), MN-major with the 128-byte swizzle
 // (chunk c of K row k at c ^ k).  Each region is read whole by one warp
-// before that warp writes it (warp cw: A rows 16cw..16cw+15, B boxes 2cw
-// and 2cw+1), so no other warp's data is overwritten.  Loads and stores are
-// bank-conflict free.
+// before that warp writes it (warp cw of kWarps: kPer = 16 / kWarps A row
+// groups and B boxes from kPer cw on), so no other warp's data is
+// overwritten.  Loads and stores are bank-conflict free.
+template <int kWarps>
 __device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_st, int cw,
                                                      int lane) {
+  static_assert(kWarps == 8 || kWarps == 16, "16 A row groups and 16 B boxes per stage");
+  constexpr int kPer = 16 / kWarps;  // A groups and B boxes per warp
   {
     // A: lane = (row r of the 8-row group, 32-byte quarter q of the row)
     const int r = lane >> 2, q = lane & 3, h0 = r & 1;
     const int off = 64 * r + 16 * (q ^ ((r >> 1) & 3));
 #pragma unroll
-    for (int gi = 0; gi < 2; ++gi) {
-      uint8_t* g = a_st + 1024 * (2 * cw + gi);
+    for (int gi = 0; gi < kPer; ++gi) {
+      uint8_t* g = a_st + 1024 * (kPer * cw + gi);
       const float4 u = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * h0);
       const float4 v = *reinterpret_cast<const float4*>(g + 128 * r + 32 * q + 16 * (h0 ^ 1));
       __syncwarp();
@@ -280,9 +284,9 @@ __device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_s
     }
   }
 #pragma unroll
-  for (int bi = 0; bi < 2; ++bi) {
+  for (int bi = 0; bi < kPer; ++bi) {
     // B: load i gives lane the float4 (N 4c..4c+3) of K row k = 2i + lane/16
-    uint8_t* box = b_st + 2048 * (2 * cw + bi);
+    uint8_t* box = b_st + 2048 * (kPer * cw + bi);
     const int c = lane & 15, kh = lane >> 4;
     float4 v[4];
 #pragma unroll
@@ -360,23 +364,25 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
   // that its registers are free for the sums
   const int k0 = sk_start(p, b0) < first ? 1 : 0;  // b0's piece of this tile
   if (row_q < p.M && col_s < p.N) {
-    // two fragments at a time: 16 independent loads in flight per
-    // contributor, so a tile costs NF / 2 * nc L2 round trips
-    static_assert(NF % 2 == 0, "fragment pairs");
+    // G fragments at a time (8 G independent loads in flight per
+    // contributor), so a tile costs NF / G * nc L2 round trips; G = 1 when
+    // the epilogue warps have few registers
+    constexpr int G = NF >= 4 ? 2 : 1;
+    static_assert(NF % G == 0, "fragment groups");
 #pragma unroll 1
-    for (int f2 = 0; f2 < NF; f2 += 2) {
-      const int64_t base = f2 * 8 * kEpiThreads + etid;
-      float4 acc[16];
+    for (int f0 = 0; f0 < NF; f0 += G) {
+      const int64_t base = f0 * 8 * kEpiThreads + etid;
+      float4 acc[8 * G];
       const float4* s0 = slab(b0, k0) + base;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) acc[e] = __ldcg(s0 + e * kEpiThreads);
+      for (int e = 0; e < 8 * G; ++e) acc[e] = __ldcg(s0 + e * kEpiThreads);
       for (int jj = 1; jj < nc; ++jj) {
         const float4* sj = slab(b0 + jj, 0) + base;
-        float4 c[16];
+        float4 c[8 * G];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) c[e] = __ldcg(sj + e * kEpiThreads);
+        for (int e = 0; e < 8 * G; ++e) c[e] = __ldcg(sj + e * kEpiThreads);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < 8 * G; ++e) {
           acc[e].x += c[e].x;
           acc[e].y += c[e].y;
           acc[e].z += c[e].z;
@@ -384,7 +390,7 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
         }
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < G; ++h) {
         float v[32];
 #pragma unroll
         for (int j4 = 0; j4 < 8; ++j4) {
@@ -393,7 +399,7 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
           v[4 * j4 + 2] = acc[8 * h + j4].z;
           v[4 * j4 + 3] = acc[8 * h + j4].w;
         }
-        const int f = f2 + h;
+        const int f = f0 + h;
         store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
                       alpha, beta, vec_out, lane);
       }
@@ -689,8 +695,8 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
               ok = false;
               break;
             }
-            split_stage_in_place(sA + (stage * P) * L::kABytes, sB + (stage * P) * L::kBBytes,
-                                 cw, lane);
+            split_stage_in_place<T::epi>(sA + (stage * P) * L::kABytes,
+                                         sB + (stage * P) * L::kBBytes, cw, lane);
             dev::fence_proxy_async_smem();  // generic writes before the MMA's reads
             __syncwarp();
             if (lane == 0) dev::mbar_arrive(&split_done[stage]);
