@@ -620,8 +620,8 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
     ms_loop = tuned_ms[0]                      # per-GEMM launches (autotuner's median)
     flops = sum(2.0 * m * n * k for m, n, k, _ in plist)
     del keep
-    names = ["per-GEMM launches", "grouped BN=128", "grouped BN=64",
-             "grouped BN=128 largest-first", "grouped BN=64 largest-first"]
+    names = ["per-GEMM launches", "grouped BN=128", "grouped BN=256",
+             "grouped BN=128 largest-first", "grouped BN=256 largest-first"]
     return {"problems": len(plist), "gflop": flops / 1e9, "ld": "rounded up to 16 bytes",
             "chosen": names[best],
             "ms_chosen": ms_best, "tflops_chosen": flops / (ms_best / 1e3) / 1e12,

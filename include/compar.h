@@ -203,7 +203,7 @@ int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
 
 /* Time the implementations of a batched call on this batch and remember the
  * fastest for its signature (shapes, dtypes, tolerance class): 0 = one launch
- * per problem, 1 = grouped kernel with 128-column tiles, 2 = 64-column tiles,
+ * per problem, 1 = grouped kernel with 128-column tiles, 2 = 256-column tiles,
  * 3 / 4 = as 1 / 2 with the largest problems first.  Each configuration runs
  * once untimed and three times timed (CUDA events on `stream`), so C is
  * written several times: with beta != 0 the final contents are not the
@@ -212,6 +212,13 @@ int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
 int compar_autotune_batched(compar_ctx_t ctx, int count,
                             const compar_problem_t* probs, double tol,
                             void* stream, float* times_ms, int* best);
+
+/* Run every following batched call in configuration `config` (0..4, as
+ * numbered for compar_autotune_batched), or clear with -1 (autotuned choice
+ * for known batch signatures, else configuration 1).  A forced variant
+ * other than COMPAR_V_GROUPED still runs the per-GEMM loop.
+ * COMPAR_ERR_INVALID for other values. */
+int compar_set_batched_config(compar_ctx_t ctx, int config);
 
 /* ---------------------------------------------------------------- control */
 

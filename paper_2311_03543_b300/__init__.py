@@ -110,6 +110,7 @@ SIGNATURES = {
     "compar_gemm_simt_noalloc": (_i, [_i64, _i64, _i64, _f, _vp, _vp, _f, _vp, _vp]),
     "compar_autotune_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp, _fp,
                                      ctypes.POINTER(_i)]),
+    "compar_set_batched_config": (_i, [_vp, _i]),
     "compar_mlp_param_count": (_i, []),
     "compar_mlp_forward": (_i, [_vp, _fp, _i, _fp, _i, _fp]),
     "compar_mlp_train_steps": (_i, [_vp, _fp, _fp, _fp, _i, _fp, _fp, _fp, _i,
@@ -370,6 +371,11 @@ class Context:
         arr = problems if isinstance(problems, ctypes.Array) else self.problem_array(problems)
         return _status(compar_gemm_batched(self.handle, len(arr), arr, float(tol),
                                            _stream_handle(stream)), "compar_gemm_batched")
+
+    def set_batched_config(self, config):
+        """Force batched configuration 0..4 (None: autotuned / default)."""
+        return _status(compar_set_batched_config(self.handle, -1 if config is None else
+                                                 int(config)), "set_batched_config")
 
     def autotune_batched(self, problems, tol=0.0, stream=None):
         """Returns (best configuration, [median ms of configurations 0..4])."""

@@ -9,7 +9,7 @@
 //                launch over every problem's tiles (gemm_grouped.cu), with the
 //                descriptor upload and both launches captured in a CUDA graph
 //                that is replayed for every later batch of the same shape.
-// The grouped kernel has tile configurations (BN = 128 or 64; problems in
+// The grouped kernel has tile configurations (BN = 128 or 256; problems in
 // given order or largest-first); compar_autotune_batched times the loop and
 // every configuration on the caller's batch and remembers the fastest for
 // that signature (saved in selector files).  Unknown signatures use the
@@ -29,8 +29,8 @@ int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s);
 
 namespace {
 
-constexpr int kCfgLoop = 0;  // cfg 1..4: grouped, bn = (cfg & 1) ? 128 : 64, lpt = cfg >= 3
-inline int cfg_bn(int cfg) { return (cfg == 1 || cfg == 3) ? 128 : 64; }
+constexpr int kCfgLoop = 0;  // cfg 1..4: grouped, bn = (cfg & 1) ? 128 : 256, lpt = cfg >= 3
+inline int cfg_bn(int cfg) { return (cfg == 1 || cfg == 3) ? 128 : 256; }
 inline bool cfg_lpt(int cfg) { return cfg >= 3; }
 
 struct BatchedState {
@@ -422,9 +422,16 @@ extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_pro
   int cfg = 1;
   auto it = ctx->batched_cfg.find(signature(count, probs, tol));
   if (it != ctx->batched_cfg.end()) cfg = it->second;
+  if (ctx->batched_forced >= 0) cfg = ctx->batched_forced;
   if (ctx->forced == COMPAR_V_GROUPED && cfg == kCfgLoop) cfg = 1;
   ctx->last_variant = cfg == kCfgLoop ? -1 : COMPAR_V_GROUPED;
   return run_cfg(ctx, cfg, count, probs, tol, s);
+}
+
+extern "C" int compar_set_batched_config(compar_ctx_t ctx, int config) {
+  if (!ctx || config < -1 || config > 4) return COMPAR_ERR_INVALID;
+  ctx->batched_forced = config;
+  return COMPAR_OK;
 }
 
 extern "C" int compar_autotune_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,

@@ -71,6 +71,35 @@ __device__ __forceinline__ int find_problem(const GroupProblem* __restrict__ P,
   return lo;
 }
 
+// The fields of a tile's problem that the roles need, fetched one tile
+// ahead: the loads are issued while the current tile runs, so a role does
+// not stall on global memory at every tile boundary (tiles of small problems
+// take only a few stages).
+struct TileInfo {
+  int q, local, tiles_m, num_kb, mode, M, N;
+  float* C;
+  int64_t ldc;
+  float alpha, beta;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const GroupProblem* __restrict__ P,
+                                              const int* s_start, int count, int tile) {
+  TileInfo t;
+  t.q = find_problem(P, s_start, count, tile);
+  const GroupProblem& g = P[t.q];
+  t.local = tile - (s_start ? s_start[t.q] : g.tile_start);
+  t.tiles_m = g.tiles_m;
+  t.num_kb = g.num_kb;
+  t.mode = g.mode;
+  t.M = g.M;
+  t.N = g.N;
+  t.C = g.C;
+  t.ldc = g.ldc;
+  t.alpha = g.alpha;
+  t.beta = g.beta;
+  return t;
+}
+
 __device__ __forceinline__ bool drain(uint64_t* bar, uint32_t parity, uint64_t budget) {
   const uint64_t t0 = dev::globaltimer_ns();
   while (!dev::mbar_try_wait(bar, parity))
@@ -128,30 +157,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------- producer
     uint32_t stage = 0, phase = 0, issued = 0, issued_par = 0;
     bool ok = true;
-    int last_q = -1;
-    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const int q = find_problem(probs, s_start, count, tile);
+    // The descriptors were written by the host for this launch; earlier
+    // launches may have left other bytes at these addresses in the cache:
+    // acquire (and prefetch) a problem's maps before its first TMA use, one
+    // tile ahead.
+    auto acquire_maps = [&](int q) {
       const GroupProblem& P = probs[q];
-      const int local = tile - P.tile_start;
-      const int mb = local % P.tiles_m, nb = local / P.tiles_m;
-      const int pieces = P.mode == 1 ? 2 : 1;
-      if (q != last_q) {
-        // the descriptors were written by the host for this launch; earlier
-        // launches may have left other bytes at these addresses in the cache
-        dev::tensormap_acquire(&P.map_a);
-        dev::tensormap_acquire(&P.map_b);
-        if (pieces == 2) {
-          dev::tensormap_acquire(&P.map_a2);
-          dev::tensormap_acquire(&P.map_b2);
-        }
-        last_q = q;
+      dev::tensormap_acquire(&P.map_a);
+      dev::tensormap_acquire(&P.map_b);
+      dev::tensormap_acquire(&P.map_a2);
+      dev::tensormap_acquire(&P.map_b2);
+      dev::tma_prefetch_desc(&P.map_a);
+      dev::tma_prefetch_desc(&P.map_b);
+    };
+    TileInfo cur{};
+    if (blockIdx.x < total_tiles) {
+      cur = tile_info(probs, s_start, count, blockIdx.x);
+      acquire_maps(cur.q);
+    }
+    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+      TileInfo nxt{};
+      const int tn = tile + gridDim.x;
+      if (tn < total_tiles) {
+        nxt = tile_info(probs, s_start, count, tn);
+        if (nxt.q != cur.q) acquire_maps(nxt.q);
       }
+      const GroupProblem& P = probs[cur.q];
+      const int mb = cur.local % cur.tiles_m, nb = cur.local / cur.tiles_m;
+      const int pieces = cur.mode == 1 ? 2 : 1;
       const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
-      const bool tf32 = P.mode == 2;
+      const bool tf32 = cur.mode == 2;
       const int kelems = tf32 ? kRow / 4 : kRow / 2;
-      // problem fields go to registers once: the loop's asm statements clobber
-      // memory, so fields read through P would be reloaded every iteration
-      const int num_kb = P.num_kb;
+      const int num_kb = cur.num_kb;
       for (int kb = 0; kb < num_kb; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
           ok = false;
@@ -181,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           phase ^= 1;
         }
       }
+      cur = nxt;
     }
     if (!ok)
       for (int s = 0; s < S; ++s)
@@ -192,10 +230,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;
     bool ok = true;
+    TileInfo cur{};
+    if (blockIdx.x < total_tiles) cur = tile_info(probs, s_start, count, blockIdx.x);
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
-      const int mode = P.mode;
-      const int num_kb = P.num_kb;
+      TileInfo nxt{};
+      if (tile + static_cast<int>(gridDim.x) < total_tiles)
+        nxt = tile_info(probs, s_start, count, tile + gridDim.x);
+      const int mode = cur.mode;
+      const int num_kb = cur.num_kb;
+      cur = nxt;
       for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kChunkKB, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
@@ -252,18 +295,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // one half of the columns.
     constexpr int EC = BN / 2;       // columns of this warp's slice
     constexpr int J = EC / 8;        // 16x256b repetitions per fragment
+    static_assert(J == 4 || J == 8 || J == 16, "epilogue slice of 32, 64 or 128 columns");
     const int quarter = warp & 3;
     const int cslice = (warp - 2) / 4;
     int acc_iter = 0;
     bool ok = true;
+    TileInfo cur{};
+    if (blockIdx.x < total_tiles) cur = tile_info(probs, s_start, count, blockIdx.x);
     for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const GroupProblem& P = probs[find_problem(probs, s_start, count, tile)];
-      const int local = tile - P.tile_start;
-      const int mb = local % P.tiles_m, nb = local / P.tiles_m;
-      const int pM = P.M, pN = P.N, num_kb = P.num_kb;
-      float* const pC = P.C;
-      const int64_t ldc = P.ldc;
-      const float alpha = P.alpha, beta = P.beta;
+      const TileInfo t = cur;
+      if (tile + static_cast<int>(gridDim.x) < total_tiles)
+        cur = tile_info(probs, s_start, count, tile + gridDim.x);
+      const int mb = t.local % t.tiles_m, nb = t.local / t.tiles_m;
+      const int pM = t.M, pN = t.N, num_kb = t.num_kb;
+      float* const pC = t.C;
+      const int64_t ldc = t.ldc;
+      const float alpha = t.alpha, beta = t.beta;
       // two 16-row fragments (row halves of the warp's lane quarter)
       float sum[2][4 * J];
 #pragma unroll
@@ -283,12 +330,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t taddr = tmem_base +
                                  (static_cast<uint32_t>(quarter * 32 + 16 * h) << 16) +
                                  acc * BN + cslice * EC;
-          uint32_t r[4 * J];
-          if constexpr (J == 8) dev::tmem_ld_16x256b_x8(taddr, r);
-          else dev::tmem_ld_16x256b_x4(taddr, r);
-          dev::tmem_ld_wait();
+          if constexpr (J == 16) {
+            // two 64-column loads: repetitions 0-7 and 8-15 of the fragment
 #pragma unroll
-          for (int j = 0; j < 4 * J; ++j) sum[h][j] += __uint_as_float(r[j]);
+            for (int half = 0; half < 2; ++half) {
+              uint32_t r[32];
+              dev::tmem_ld_16x256b_x8(taddr + 64 * half, r);
+              dev::tmem_ld_wait();
+#pragma unroll
+              for (int j = 0; j < 32; ++j) sum[h][32 * half + j] += __uint_as_float(r[j]);
+            }
+          } else {
+            uint32_t r[4 * J];
+            if constexpr (J == 8) dev::tmem_ld_16x256b_x8(taddr, r);
+            else dev::tmem_ld_16x256b_x4(taddr, r);
+            dev::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 4 * J; ++j) sum[h][j] += __uint_as_float(r[j]);
+          }
         }
         dev::tc_fence_before();
         dev::mbar_arrive(&tempty[acc]);
@@ -315,22 +374,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int grouped_smem_bytes(int bn) {
-  return bn == 64 ? GLayout<64>::kSmem : GLayout<128>::kSmem;
+  return bn == 256 ? GLayout<256>::kSmem : GLayout<128>::kSmem;
 }
 
 int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int total_tiles,
                         const DeviceGuard& g, int num_sms, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return COMPAR_OK;
   const int grid = std::min(total_tiles, num_sms);
-  if (bn == 64) {
+  if (bn == 256) {
     static bool attr = false;
     if (!attr) {
-      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<64>,
+      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<256>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           GLayout<64>::kSmem));
+                                           GLayout<256>::kSmem));
       attr = true;
     }
-    grouped_gemm_kernel<64><<<grid, kThreads, GLayout<64>::kSmem, s>>>(
+    grouped_gemm_kernel<256><<<grid, kThreads, GLayout<256>::kSmem, s>>>(
         d_probs, count, total_tiles, g.err_word, g.budget_ns);
   } else {
     static bool attr = false;

@@ -159,6 +159,7 @@ struct compar_ctx {
   std::vector<cudaEvent_t> event_pool;
   // batch signature -> autotuned batched configuration (0 loop, 1..4 grouped)
   std::unordered_map<uint64_t, int> batched_cfg;
+  int batched_forced = -1;  // compar_set_batched_config
   // online selection: exploration probability on decision-cache misses and
   // warm-start fine-tuning of the MLP every `retrain_every` new records
   struct Online {

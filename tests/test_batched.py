@@ -100,6 +100,29 @@ def test_grouped_fp32_accurate_and_bf16(ctx):
     _check(specs, host, 1e-5)
 
 
+@pytest.mark.parametrize("config", [1, 2, 3, 4])
+def test_every_grouped_configuration(ctx, config):
+    """Tiles of 128 or 256 columns, problems in given order or largest
+    first: same products."""
+    import paper_2311_03543_b300 as cp
+    specs = _random_specs(30, seed=11, hi=600)
+    probs, host = _make_batch(specs, 900)
+    ctx.set_batched_config(config)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.set_batched_config(None)
+    assert ctx.check_device_error() == cp.OK
+    assert ctx.last_variant() == cp.V_GROUPED
+    _check(specs, host, 1e-5)
+
+
+def test_batched_config_is_validated(ctx):
+    import paper_2311_03543_b300 as cp
+    assert cp.compar_set_batched_config(ctx.handle, 5) == cp.ERR_INVALID
+    assert cp.compar_set_batched_config(ctx.handle, -2) == cp.ERR_INVALID
+
+
 def test_grouped_bf16_operands_read_in_place(ctx):
     """bf16 problems whose rows are 16-byte aligned (ld a multiple of 8) are
     read by TMA as stored: A row-major M x K, B row-major K x N (MN-major),
