@@ -273,7 +273,7 @@ def measure_peaks(ctx, torch, dev):
         out["fp8_tflops"] = 2 * n ** 3 / (best_of(
             lambda: torch._scaled_mm(x8, y8, scale_a=one, scale_b=one,
                                      out_dtype=torch.bfloat16)) / 1e3) / 1e12
-    except Exception as e:  # library without an fp8 path on this build
+    except Exception as e:  # a library without an fp8 path
         out["fp8_tflops"] = None
         out["fp8_note"] = str(e)[:120]
     src = torch.empty(1 << 28, device=dev)

@@ -51,7 +51,7 @@ def _evaluate(contexts, seed0):
     from gpu_util import dev
     assert os.path.exists(SELECTOR), "trained selector file missing"
     # The selector context only selects; a separate judge context measures,
-    # so the judge's timings never reach the selector's history table.
+    # so the exhaustive measurement's timings never reach the selector's history table.
     sel = cp.Context(0)
     sel.selector_load(SELECTOR)
     judge = cp.Context(0)
