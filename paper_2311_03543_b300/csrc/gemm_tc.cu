@@ -193,10 +193,15 @@ __device__ __forceinline__ int sk_cta_of(const TcArgs& p, int q) {
   return static_cast<int>((static_cast<long long>(q + 1) * p.sk_ctas - 1) / p.sk_q);
 }
 
+// K blocks per stream-K chunk of the variants without promotion (their
+// accumulator spans the whole piece); promoted variants use their chunk.
+constexpr int kPlainSkChunk = 2;
+
 // Item i of this CTA's list; false past its end.  Every role of the CTA
 // walks the same list.
 template <int kChunkKB>
 __device__ __forceinline__ bool get_item(const TcArgs& p, int i, WorkItem& it) {
+  constexpr int kSk = kChunkKB > 0 ? kChunkKB : kPlainSkChunk;
   const int b = blockIdx.x, grid = gridDim.x;
   const int u = b + i * grid;
   if (u < p.dp_units) {
@@ -207,7 +212,7 @@ __device__ __forceinline__ bool get_item(const TcArgs& p, int i, WorkItem& it) {
     it.piece = -1;
     return true;
   }
-  if (kChunkKB == 0 || p.sk_q == 0 || b >= p.sk_ctas) return false;
+  if (p.sk_q == 0 || b >= p.sk_ctas) return false;
   const int n_dp = b < p.dp_units ? (p.dp_units - 1 - b) / grid + 1 : 0;
   const int k = i - n_dp;
   const int q0 = sk_start(p, b), q1 = sk_start(p, b + 1);
@@ -217,8 +222,8 @@ __device__ __forceinline__ bool get_item(const TcArgs& p, int i, WorkItem& it) {
   const int qe = min(q1, (t + 1) * p.sk_cpt);
   it.tile = p.sk_tile0 + t;
   it.split = 0;
-  it.kb_begin = (q - t * p.sk_cpt) * kChunkKB;
-  it.kb_end = min(p.num_kb, (qe - t * p.sk_cpt) * kChunkKB);
+  it.kb_begin = (q - t * p.sk_cpt) * kSk;
+  it.kb_end = min(p.num_kb, (qe - t * p.sk_cpt) * kSk);
   it.piece = k;
   return true;
 }
@@ -305,64 +310,55 @@ __device__ __forceinline__ void split_stage_in_place(uint8_t* a_st, uint8_t* b_s
   }
 }
 
-// End of a promoted item in the epilogue: stores the tile from `sum` (a
-// classic unit, or a stream-K tile with one contributor) or publishes this
-// CTA's stream-K piece and, if this CTA arrived last, sums the pieces and
-// stores the tile.  Returns false when a bounded wait gave up.  `sum` is not
-// used after the store or the publication, so the registers of the sums are
-// free.  Every contributor of a stream-K tile publishes its partial sum and
-// counts itself in; the last to arrive adds the pieces in contributor order
-// (so the result does not depend on which CTA finished last).  No CTA waits
-// for another.
+// Stream-K piece bookkeeping: the piece's tail tile t, the tile's first
+// chunk, its first contributing CTA b0 and the number of contributors nc.
+struct SkPiece {
+  int t, first, b0, nc;
+};
+__device__ __forceinline__ SkPiece sk_piece(const TcArgs& p, const WorkItem& it) {
+  SkPiece sp{0, 0, 0, 1};
+  if (it.piece < 0) return sp;
+  sp.t = it.tile - p.sk_tile0;
+  sp.first = sp.t * p.sk_cpt;
+  sp.b0 = sk_cta_of(p, sp.first);
+  sp.nc = sk_cta_of(p, sp.first + p.sk_cpt - 1) - sp.b0 + 1;
+  return sp;
+}
+
+// Published partial tile of CTA `cta`'s piece k: kBM x BN floats as float4,
+// element (f * 8 + j4) * kEpiThreads + epilogue thread.
+template <int BN>
+__device__ __forceinline__ float4* sk_slab(const TcArgs& p, int cta, int k) {
+  constexpr int64_t kSlab = static_cast<int64_t>(kBM) * BN / 4;
+  return reinterpret_cast<float4*>(p.sk_slab) + (2 * static_cast<int64_t>(cta) + k) * kSlab;
+}
+
+// After this CTA has published its piece of a tile with several
+// contributors: count it in, and if it arrived last add the pieces in
+// contributor order (so the result does not depend on which CTA finished
+// last) and store the tile.  No CTA waits for another.  False when a bounded
+// wait gave up.
 template <int NF, int kEpiThreads, int BN>
-__device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem& it,
-                                               const float (&sum)[NF][32], uint64_t* epi_bar,
-                                               uint32_t& epi_uses, volatile int* last_flag,
-                                               const dev::WaitCtx& w, int etid, int lane,
-                                               float* out, int64_t out_ld, int row_q, int col_s,
-                                               float alpha, float beta, bool vec_out) {
-  int nc = 1, b0 = 0, first = 0, t = 0;
-  if (it.piece >= 0) {
-    t = it.tile - p.sk_tile0;
-    first = t * p.sk_cpt;
-    b0 = sk_cta_of(p, first);
-    nc = sk_cta_of(p, first + p.sk_cpt - 1) - b0 + 1;
-  }
-  if (nc == 1) {
-    if (row_q < p.M && col_s < p.N) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
-                      alpha, beta, vec_out, lane);
-    }
-    return true;
-  }
-  constexpr int64_t kSlab = static_cast<int64_t>(kBM) * BN / 4;  // float4 per piece
-  auto slab = [&](int cta, int k) {
-    return reinterpret_cast<float4*>(p.sk_slab) + (2 * static_cast<int64_t>(cta) + k) * kSlab;
-  };
-  float4* mine = slab(blockIdx.x, it.piece);
-#pragma unroll
-  for (int f = 0; f < NF; ++f)
-#pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4)
-      mine[(f * 8 + j4) * kEpiThreads + etid] =
-          make_float4(sum[f][4 * j4], sum[f][4 * j4 + 1], sum[f][4 * j4 + 2], sum[f][4 * j4 + 3]);
+__device__ __forceinline__ bool sk_count_and_sum(const TcArgs& p, const SkPiece& sp,
+                                                 uint64_t* epi_bar, uint32_t& epi_uses,
+                                                 volatile int* last_flag, const dev::WaitCtx& w,
+                                                 int etid, int lane, float* out, int64_t out_ld,
+                                                 int row_q, int col_s, float alpha, float beta,
+                                                 bool vec_out) {
   __threadfence();
   // bounded rendezvous: a CTA that gave up elsewhere cannot hang here
   dev::mbar_arrive(epi_bar);
   if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
   if (etid == 0) {
     __threadfence();
-    *last_flag = atomicAdd(p.sk_count + t, 1u) == static_cast<unsigned int>(nc - 1);
+    *last_flag = atomicAdd(p.sk_count + sp.t, 1u) == static_cast<unsigned int>(sp.nc - 1);
   }
   dev::mbar_arrive(epi_bar);
   if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
   if (!*last_flag) return true;
   __threadfence();
-  // the pieces in contributor order, this CTA's own from its slab too, so
-  // that its registers are free for the sums
-  const int k0 = sk_start(p, b0) < first ? 1 : 0;  // b0's piece of this tile
+  // the pieces in contributor order, this CTA's own from its slab too
+  const int k0 = sk_start(p, sp.b0) < sp.first ? 1 : 0;  // b0's piece of this tile
   if (row_q < p.M && col_s < p.N) {
     // G fragments at a time (8 G independent loads in flight per
     // contributor), so a tile costs NF / G * nc L2 round trips; G = 1 when
@@ -373,11 +369,11 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
     for (int f0 = 0; f0 < NF; f0 += G) {
       const int64_t base = f0 * 8 * kEpiThreads + etid;
       float4 acc[8 * G];
-      const float4* s0 = slab(b0, k0) + base;
+      const float4* s0 = sk_slab<BN>(p, sp.b0, k0) + base;
 #pragma unroll
       for (int e = 0; e < 8 * G; ++e) acc[e] = __ldcg(s0 + e * kEpiThreads);
-      for (int jj = 1; jj < nc; ++jj) {
-        const float4* sj = slab(b0 + jj, 0) + base;
+      for (int jj = 1; jj < sp.nc; ++jj) {
+        const float4* sj = sk_slab<BN>(p, sp.b0 + jj, 0) + base;
         float4 c[8 * G];
 #pragma unroll
         for (int e = 0; e < 8 * G; ++e) c[e] = __ldcg(sj + e * kEpiThreads);
@@ -406,6 +402,40 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
     }
   }
   return true;
+}
+
+// End of a promoted item in the epilogue: stores the tile from `sum` (a
+// classic unit, or a stream-K tile with one contributor) or publishes this
+// CTA's stream-K piece and takes part in the count-and-sum.  `sum` is not
+// used after the store or the publication, so its registers are free for
+// the sums.  False when a bounded wait gave up.
+template <int NF, int kEpiThreads, int BN>
+__device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem& it,
+                                                const float (&sum)[NF][32], uint64_t* epi_bar,
+                                                uint32_t& epi_uses, volatile int* last_flag,
+                                                const dev::WaitCtx& w, int etid, int lane,
+                                                float* out, int64_t out_ld, int row_q, int col_s,
+                                                float alpha, float beta, bool vec_out) {
+  const SkPiece sp = sk_piece(p, it);
+  if (sp.nc == 1) {
+    if (row_q < p.M && col_s < p.N) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                      alpha, beta, vec_out, lane);
+    }
+    return true;
+  }
+  float4* mine = sk_slab<BN>(p, blockIdx.x, it.piece);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4)
+      mine[(f * 8 + j4) * kEpiThreads + etid] =
+          make_float4(sum[f][4 * j4], sum[f][4 * j4 + 1], sum[f][4 * j4 + 2], sum[f][4 * j4 + 3]);
+  return sk_count_and_sum<NF, kEpiThreads, BN>(p, sp, epi_bar, epi_uses, last_flag, w, etid,
+                                               lane, out, out_ld, row_q, col_s, alpha, beta,
+                                               vec_out);
 }
 
 template <int V>
@@ -802,6 +832,30 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
       ++acc_iter;
       if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) break;
       dev::tc_fence_after();
+      const SkPiece sp = sk_piece(p, it);
+      if (sp.nc > 1) {
+        // stream-K piece: publish the accumulator straight from TMEM, free
+        // it, then count in (and sum the tile if this CTA is the last)
+        float4* mine = sk_slab<BN>(p, blockIdx.x, it.piece);
+#pragma unroll 1
+        for (int f = 0; f < NF; ++f) {
+          uint32_t r[32];
+          dev::tmem_ld_16x256b_x8(frag_taddr(acc, f), r);
+          dev::tmem_ld_wait();
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4)
+            mine[(f * 8 + j4) * L::kEpiThreads + etid] =
+                make_float4(__uint_as_float(r[4 * j4]), __uint_as_float(r[4 * j4 + 1]),
+                            __uint_as_float(r[4 * j4 + 2]), __uint_as_float(r[4 * j4 + 3]));
+        }
+        dev::tc_fence_before();
+        dev::mbar_arrive(&tempty[acc]);
+        if (!sk_count_and_sum<NF, L::kEpiThreads, BN>(p, sp, epi_bar, epi_uses, last_flag, w,
+                                                      etid, lane, out, out_ld, row_q, col_s,
+                                                      alpha, beta, vec_out))
+          break;
+        continue;
+      }
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         uint32_t r[32];
@@ -859,32 +913,58 @@ CUtensorMapDataType map_type(int v) {
 
 // Launch plan of a tensor-core call: K blocks, tiles, and the split of K
 // when the tiles alone would leave most SMs idle (at least 8 K blocks per
-// split, at most one unit per SM).  Promoted variants whose last wave of
-// tiles is partial cut that wave into stream-K pieces instead (whole
-// promotion chunks, at least a quarter tile each, so that a tile has at most
-// five contributors), when that shortens the wave by a quarter or more.
+// split, at most one unit per SM).  A partial last wave of tiles is cut
+// into stream-K pieces instead (whole chunks: the promotion chunk, or
+// kPlainSkChunk K blocks for the variants without promotion; at least a
+// quarter tile each, so that a tile has at most five contributors), when
+// that shortens the wave by a quarter or more and saves more time than the
+// fixup costs.
 struct TcPlan {
   int num_kb, tiles, splits, kb_per;
   int sk_tile0 = 0, sk_cpt = 0, sk_q = 0, sk_ctas = 0;
 };
 
-// Tile width of every promoted variant (stream-K piece size on the host).
-constexpr int kPromotedBN = 256;
-static_assert(Traits<COMPAR_V_SPLIT3>::BN == kPromotedBN &&
-                  Traits<COMPAR_V_SPLIT6>::BN == kPromotedBN &&
-                  Traits<COMPAR_V_SPLIT3_TF32>::BN == kPromotedBN &&
-                  Traits<COMPAR_V_SPLIT3_FUSED>::BN == kPromotedBN,
-              "stream-K pieces are kBM x kPromotedBN");
+// Tile width of every tensor-core variant (stream-K piece size on the host).
+constexpr int kTileN = 256;
+static_assert(Traits<COMPAR_V_TC_TF32>::BN == kTileN && Traits<COMPAR_V_TC_BF16>::BN == kTileN &&
+                  Traits<COMPAR_V_TC_FP8>::BN == kTileN && Traits<COMPAR_V_SPLIT3>::BN == kTileN &&
+                  Traits<COMPAR_V_SPLIT6>::BN == kTileN &&
+                  Traits<COMPAR_V_SPLIT3_TF32>::BN == kTileN &&
+                  Traits<COMPAR_V_SPLIT3_FUSED>::BN == kTileN,
+              "stream-K pieces are kBM x kTileN");
 
-int chunk_kb_of(int v) {
+// K blocks per stream-K chunk: the promotion chunk where there is one.
+int sk_chunk_of(int v) {
   switch (v) {
     case COMPAR_V_SPLIT3: return Traits<COMPAR_V_SPLIT3>::chunk_kb;
     case COMPAR_V_SPLIT6: return Traits<COMPAR_V_SPLIT6>::chunk_kb;
     case COMPAR_V_SPLIT3_TF32: return Traits<COMPAR_V_SPLIT3_TF32>::chunk_kb;
     case COMPAR_V_SPLIT3_FUSED: return Traits<COMPAR_V_SPLIT3_FUSED>::chunk_kb;
-    default: return 0;
+    default: return kPlainSkChunk;
   }
 }
+
+// Time of one 128 x 256 tile's MMAs over K (us) at the sustained per-SM
+// tensor rate of the variant's kind (bf16 ~9.4e12 flop/s per SM; fp8 twice,
+// tf32 half), times its products per output.
+double tile_us(int v, int64_t k) {
+  double rate = 9.4e12, products = 1;
+  switch (v) {
+    case COMPAR_V_TC_FP8: rate *= 2; break;
+    case COMPAR_V_TC_TF32: rate /= 2; break;
+    case COMPAR_V_SPLIT3:
+    case COMPAR_V_SPLIT3_FUSED: products = 3; break;
+    case COMPAR_V_SPLIT6: products = 6; break;
+    case COMPAR_V_SPLIT3_TF32: rate /= 2; products = 3; break;
+    default: break;
+  }
+  return 2.0 * kBM * kTileN * static_cast<double>(k) * products / rate * 1e6;
+}
+
+// The stream-K fixup (publish a 128 KB piece, count, the last contributor
+// sums 2-5 of them) costs ~10 us; a tail cut is taken only when it saves
+// clearly more.
+constexpr double kSkMinSavingUs = 12.0;
 
 TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
   const int kelems = v == COMPAR_V_TC_FP8 ? 128
@@ -903,16 +983,19 @@ TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
       p.splits = (p.num_kb + p.kb_per - 1) / p.kb_per;
     }
   }
-  const int chunk = chunk_kb_of(v);
+  const int chunk = sk_chunk_of(v);
   const int rem = p.tiles % num_sms;
   if (chunk > 0 && p.splits == 1 && rem > 0) {
     const int64_t cpt = (p.num_kb + chunk - 1) / chunk;
     const int64_t q = static_cast<int64_t>(rem) * cpt;
     const int64_t lmin = std::max<int64_t>(1, (cpt + 3) / 4);
     const int64_t ctas = std::min<int64_t>(num_sms, q / lmin);
-    // worth it only when the tail wave shrinks by a quarter or more: the
-    // fixup (publish, count, sum the pieces) costs a few L2 round trips
-    if (cpt >= 2 && ctas >= 1 && q < (int64_t{1} << 30) && 4 * ((q + ctas - 1) / ctas) <= 3 * cpt) {
+    // worth it only when the tail wave shrinks by a quarter or more and the
+    // time saved clearly exceeds the fixup's
+    const int64_t longest = ctas >= 1 ? (q + ctas - 1) / ctas : cpt;
+    const double saved_us = tile_us(v, c.k) * (1.0 - static_cast<double>(longest) / cpt);
+    if (cpt >= 2 && ctas >= 1 && q < (int64_t{1} << 30) && 4 * longest <= 3 * cpt &&
+        saved_us >= kSkMinSavingUs) {
       p.sk_tile0 = p.tiles - rem;
       p.sk_cpt = static_cast<int>(cpt);
       p.sk_q = static_cast<int>(q);
@@ -1061,7 +1144,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     const size_t part_bytes =
         plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
     const size_t slab_bytes =
-        plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kPromotedBN * 4 : 0;
+        plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kTileN * 4 : 0;
     const size_t count_bytes =
         plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
     float* partial = nullptr;
@@ -1097,7 +1180,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
       plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
   // stream-K: two published pieces per CTA and one counter per tail tile
   const size_t slab_bytes =
-      plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kPromotedBN * 4 : 0;
+      plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kTileN * 4 : 0;
   const size_t count_bytes = plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
   // workspace carve: [B pieces][A pieces][fp8 scalars][split-K partials]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);

@@ -244,7 +244,7 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
-@pytest.mark.parametrize("v", [2, 3, 5, 7, 8, 9])
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8, 9])
 def test_partial_last_wave_with_alpha_beta(ctx, v):
     """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
     persistent CTAs, cut into stream-K pieces for the promoted variants),
@@ -259,9 +259,9 @@ def test_partial_last_wave_with_alpha_beta(ctx, v):
 
 
 @pytest.mark.parametrize("v,m,n,k", [(5, 2500, 2000, 1000), (7, 2500, 2000, 1000),
-                                     (8, 2500, 2000, 1000), (5, 1536, 2048, 2048),
+                                     (8, 2500, 2000, 1000), (5, 1536, 2048, 4096),
                                      (7, 1400, 2048, 777), (9, 2500, 2000, 1000),
-                                     (9, 1536, 2048, 2048)])
+                                     (9, 1536, 2048, 4096)])
 def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     """A partial last wave of tiles (160 tiles: one full wave and 12 more) or
     a single partial wave (96 or 88 tiles) is cut into stream-K pieces of
@@ -277,6 +277,25 @@ def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     rows = W.sample_rows(m, 96, seed=64)
     ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.25, C0=C0)
     assert N.rel_frobenius(got[rows], ref) <= (TOL_F32 if v in (5, 9) else TOL_SPLIT6)
+
+
+@pytest.mark.parametrize("v,tol,m,n,k", [(2, 2e-3, 2500, 2000, 4096), (2, 2e-3, 1536, 2048, 8192),
+                                         (3, 5e-3, 2500, 2000, 4096), (3, 5e-3, 1536, 2048, 8192),
+                                         (4, 6e-2, 2500, 2000, 8192)])
+def test_stream_k_plain_variants(ctx, v, tol, m, n, k):
+    """TF32, BF16 and FP8 (float32 inputs) with a stream-K tail: each piece
+    is an accumulator of its own K range, published from TMEM; the result is
+    within the variant's error level of the oracle and repeatable bit for
+    bit."""
+    A = W.uniform(m, k, seed=81)
+    B = W.uniform(k, n, seed=82)
+    C0 = W.uniform(m, n, seed=83)
+    got = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
+    again = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
+    assert np.array_equal(got, again)
+    rows = W.sample_rows(m, 96, seed=84)
+    ref = oracle.gemm_rows(A, B, rows, alpha=1.25, beta=0.5, C0=C0)
+    assert N.rel_frobenius(got[rows], ref) <= tol
 
 
 def test_k_zero_scales_c(ctx):
