@@ -115,10 +115,12 @@ int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s);
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols,
                     int64_t ldx, void* Y, int out_kind, int64_t ldy, bool transpose,
                     void* Y_lo, const float* dscale, cudaStream_t s);
-int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
-                 unsigned int* d_amax_bits, cudaStream_t s);
-int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_dequant,
-                      cudaStream_t s);
+// amax(|X|) and amax(|Y|) (float bits, d_amax_bits[0..1]) in one launch.
+int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
+                  int64_t yc, int64_t ldy, unsigned int* d_amax_bits, int num_sms,
+                  cudaStream_t s);
+// {s_x, 1/s_x, s_y, 1/s_y} with s = 448 / amax (1 when amax == 0).
+int prepass_fp8_scales(const unsigned int* d_amax_bits, float* d_out, cudaStream_t s);
 
 // out_kind values for prepass_convert.  The split kinds write piece p of
 // element idx at Y + p * (Y_lo - Y) (pieces equally spaced, Y_lo = piece 1):

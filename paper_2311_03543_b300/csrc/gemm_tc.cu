@@ -1216,11 +1216,9 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const float* dqa = nullptr;
   const float* dqb = nullptr;
   if (fp8_from_f32) {
-    rc = prepass_amax(static_cast<const float*>(c.A), c.m, c.k, c.lda, amax_bits, s);
-    if (rc == COMPAR_OK)
-      rc = prepass_amax(static_cast<const float*>(c.B), c.k, c.n, c.ldb, amax_bits + 1, s);
-    if (rc == COMPAR_OK) rc = prepass_fp8_scale(amax_bits, fscal + 0, fscal + 1, s);
-    if (rc == COMPAR_OK) rc = prepass_fp8_scale(amax_bits + 1, fscal + 2, fscal + 3, s);
+    rc = prepass_amax2(static_cast<const float*>(c.A), c.m, c.k, c.lda,
+                       static_cast<const float*>(c.B), c.k, c.n, c.ldb, amax_bits, num_sms, s);
+    if (rc == COMPAR_OK) rc = prepass_fp8_scales(amax_bits, fscal, s);
     if (rc != COMPAR_OK) return rc;
     sa = fscal + 0;
     dqa = fscal + 1;

@@ -305,37 +305,75 @@ __global__ void transpose_kernel(const T* __restrict__ X, int64_t rows, int64_t 
   }
 }
 
-// amax(|X|) as float bits; non-negative floats order like their bit patterns.
-__global__ void amax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
-                            unsigned int* __restrict__ out_bits) {
+// amax(|X|) and amax(|Y|) in one launch, as float bits (non-negative floats
+// order like their bit patterns): warp w of the grid takes rows w, w + warps,
+// ... of the rows of X followed by those of Y, reading each row with 16-byte
+// loads when its start is 16-byte aligned.
+__device__ __forceinline__ float row_amax(const float* __restrict__ row, int64_t cols, int lane) {
   float m = 0.f;
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t r = t / cols, c = t % cols;
-    m = fmaxf(m, fabsf(X[r * ldx + c]));
+  int64_t c = 0;
+  if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    const int64_t n4 = cols / 4;
+    for (int64_t i = lane; i < n4; i += 32) {
+      const float4 v = __ldg(r4 + i);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    c = n4 * 4;
+  }
+  for (int64_t i = c + lane; i < cols; i += 32) m = fmaxf(m, fabsf(__ldg(row + i)));
+  return m;
+}
+
+__global__ void amax2_kernel(const float* __restrict__ X, int64_t xr, int64_t xc, int64_t ldx,
+                             const float* __restrict__ Y, int64_t yr, int64_t yc, int64_t ldy,
+                             unsigned int* __restrict__ out_bits) {
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+  float mx = 0.f, my = 0.f;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + warp; r < xr + yr;
+       r += nwarps) {
+    if (r < xr) mx = fmaxf(mx, row_amax(X + r * ldx, xc, lane));
+    else my = fmaxf(my, row_amax(Y + (r - xr) * ldy, yc, lane));
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-  __shared__ float wmax[32];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  if (lane == 0) wmax[warp] = m;
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, off));
+  }
+  __shared__ float wx[32], wy[32];
+  if (lane == 0) {
+    wx[warp] = mx;
+    wy[warp] = my;
+  }
   __syncthreads();
   if (warp == 0) {
-    m = (lane < static_cast<int>(blockDim.x / 32)) ? wmax[lane] : 0.f;
+    const bool in = lane < static_cast<int>(blockDim.x / 32);
+    mx = in ? wx[lane] : 0.f;
+    my = in ? wy[lane] : 0.f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) atomicMax(out_bits, __float_as_uint(m));
+    for (int off = 16; off > 0; off >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, off));
+    }
+    if (lane == 0) {
+      atomicMax(out_bits, __float_as_uint(mx));
+      atomicMax(out_bits + 1, __float_as_uint(my));
+    }
   }
 }
 
-// s = 448 / amax (1 when amax == 0); dequantisation factor 1 / s.
-__global__ void fp8_scale_kernel(const unsigned int* __restrict__ amax_bits,
-                                 float* __restrict__ scale, float* __restrict__ dequant) {
-  const float amax = __uint_as_float(*amax_bits);
-  const float s = (amax > 0.f) ? __fdiv_rn(448.0f, amax) : 1.0f;
-  *scale = s;
-  *dequant = __fdiv_rn(1.0f, s);
+// s = 448 / amax (1 when amax == 0) and the dequantisation factor 1 / s, for
+// both operands: out = {s_x, 1/s_x, s_y, 1/s_y}.
+__global__ void fp8_scales_kernel(const unsigned int* __restrict__ amax_bits,
+                                  float* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (i < 2) {
+    const float amax = __uint_as_float(amax_bits[i]);
+    const float s = (amax > 0.f) ? __fdiv_rn(448.0f, amax) : 1.0f;
+    out[2 * i] = s;
+    out[2 * i + 1] = __fdiv_rn(1.0f, s);
+  }
 }
 
 int grid_for(int64_t total) {
@@ -623,20 +661,23 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
   return COMPAR_OK;
 }
 
-int prepass_amax(const float* X, int64_t rows, int64_t cols, int64_t ldx,
-                 unsigned int* d_amax_bits, cudaStream_t s) {
-  COMPAR_CUDA_TRY(cudaMemsetAsync(d_amax_bits, 0, sizeof(unsigned int), s));
-  if (rows <= 0 || cols <= 0) return COMPAR_OK;
-  amax_kernel<<<std::min(grid_for(rows * cols), 1184), 256, 0, s>>>(X, rows, cols, ldx,
-                                                                   d_amax_bits);
+int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
+                  int64_t yc, int64_t ldy, unsigned int* d_amax_bits, int num_sms,
+                  cudaStream_t s) {
+  COMPAR_CUDA_TRY(cudaMemsetAsync(d_amax_bits, 0, 2 * sizeof(unsigned int), s));
+  const int64_t rows = (xc > 0 ? xr : 0) + (yc > 0 ? yr : 0);
+  if (rows <= 0) return COMPAR_OK;
+  // 8 warps per block, one row per warp at a time; up to 8 blocks per SM
+  const int grid = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8LL * num_sms));
+  amax2_kernel<<<grid, 256, 0, s>>>(X, xc > 0 ? xr : 0, xc, ldx, Y, yc > 0 ? yr : 0, yc, ldy,
+                                    d_amax_bits);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;
 }
 
-int prepass_fp8_scale(const unsigned int* d_amax_bits, float* d_scale, float* d_dequant,
-                      cudaStream_t s) {
-  fp8_scale_kernel<<<1, 1, 0, s>>>(d_amax_bits, d_scale, d_dequant);
+int prepass_fp8_scales(const unsigned int* d_amax_bits, float* d_out, cudaStream_t s) {
+  fp8_scales_kernel<<<1, 32, 0, s>>>(d_amax_bits, d_out);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;
