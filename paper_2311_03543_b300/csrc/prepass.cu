@@ -100,12 +100,12 @@ __global__ void convert_rows_kernel(const float* __restrict__ X, int64_t rows, i
                                     int64_t ldx, void* __restrict__ Y, void* __restrict__ Ylo,
                                     int64_t ldy, int kind, const float* __restrict__ dscale) {
   F32Out o{kind, dscale ? *dscale : 1.f};
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t r = t / cols, c = t % cols;
-    store_converted(o, X[r * ldx + c], Y, Ylo, r * ldy + c);
-  }
+  // rows over blockIdx.y, columns over blockIdx.x / threads (no per-element
+  // division)
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y)
+    for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < cols;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x)
+      store_converted(o, X[r * ldx + c], Y, Ylo, r * ldy + c);
 }
 
 // Transposing f32 conversion: Y[c][r] = f(X[r][c]) through a 32x32 tile.
@@ -280,12 +280,10 @@ __global__ void convert_transpose64_kernel(const float* __restrict__ X, int64_t 
 template <typename T>
 __global__ void copy_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                             T* __restrict__ Y, int64_t ldy) {
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t r = t / cols, c = t % cols;
-    Y[r * ldy + c] = X[r * ldx + c];
-  }
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y)
+    for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < cols;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x)
+      Y[r * ldy + c] = X[r * ldx + c];
 }
 
 template <typename T>
@@ -374,10 +372,6 @@ __global__ void fp8_scales_kernel(const unsigned int* __restrict__ amax_bits,
     out[2 * i] = s;
     out[2 * i + 1] = __fdiv_rn(1.0f, s);
   }
-}
-
-int grid_for(int64_t total) {
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8192)));
 }
 
 // ------------------------------------------------------------------ grouped
@@ -598,6 +592,9 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
   if (rows <= 0 || cols <= 0) return COMPAR_OK;
   const dim3 tb(32, 8);
   const dim3 tg(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
+  // row-wise kernels: 256 columns per block, rows over y (grid-stride past 65535)
+  const dim3 rg(static_cast<unsigned>(std::min<int64_t>((cols + 255) / 256, 64)),
+                static_cast<unsigned>(std::min<int64_t>(rows, 65535)));
   // float32 sources with aligned rows take the vectorised kernels
   if (in_t == COMPAR_F32 && (out_kind != PP_COPY || transpose)) {
     const int kind = out_kind == PP_COPY ? PP_F32 : out_kind;
@@ -629,21 +626,21 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
         transpose_kernel<float><<<tg, tb, 0, s>>>(static_cast<const float*>(X), rows, cols, ldx,
                                                   static_cast<float*>(Y), ldy);
       else
-        copy_kernel<float><<<grid_for(rows * cols), 256, 0, s>>>(
+        copy_kernel<float><<<rg, 256, 0, s>>>(
             static_cast<const float*>(X), rows, cols, ldx, static_cast<float*>(Y), ldy);
     } else if (in_t == COMPAR_BF16) {
       if (transpose)
         transpose_kernel<uint16_t><<<tg, tb, 0, s>>>(static_cast<const uint16_t*>(X), rows, cols,
                                                      ldx, static_cast<uint16_t*>(Y), ldy);
       else
-        copy_kernel<uint16_t><<<grid_for(rows * cols), 256, 0, s>>>(
+        copy_kernel<uint16_t><<<rg, 256, 0, s>>>(
             static_cast<const uint16_t*>(X), rows, cols, ldx, static_cast<uint16_t*>(Y), ldy);
     } else {
       if (transpose)
         transpose_kernel<uint8_t><<<tg, tb, 0, s>>>(static_cast<const uint8_t*>(X), rows, cols,
                                                     ldx, static_cast<uint8_t*>(Y), ldy);
       else
-        copy_kernel<uint8_t><<<grid_for(rows * cols), 256, 0, s>>>(
+        copy_kernel<uint8_t><<<rg, 256, 0, s>>>(
             static_cast<const uint8_t*>(X), rows, cols, ldx, static_cast<uint8_t*>(Y), ldy);
     }
   } else {
@@ -653,8 +650,7 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
       convert_transpose_kernel<<<tg, tb, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, out_kind,
                                                  dscale);
     else
-      convert_rows_kernel<<<grid_for(rows * cols), 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy,
-                                                                out_kind, dscale);
+      convert_rows_kernel<<<rg, 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, out_kind, dscale);
   }
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
