@@ -510,6 +510,17 @@ int compar_set_wait_budget(compar_ctx_t ctx, uint64_t ns);
  * timeout path without faulting or hanging the GPU.  Asynchronous. */
 int compar_selftest_timeout(compar_ctx_t ctx, void* stream);
 
+/* Launch plan of tensor-core variant `variant_id` (COMPAR_V_TC_TF32 ..
+ * COMPAR_V_SPLIT3_FUSED, not GROUPED) for an m x n x k call on a GPU with
+ * `num_sms` SMs, without a device: out[0] K blocks, [1] 128 x 256 output
+ * tiles, [2] K splits (> 1: split-K with a reduce), [3] K blocks per split,
+ * [4] first stream-K tile (tiles before it are dealt whole, round-robin),
+ * [5] stream-K chunks per tile, [6] stream-K chunks in all (0: no stream-K
+ * tail), [7] CTAs sharing the tail, [8] K blocks per stream-K chunk.
+ * COMPAR_ERR_INVALID for other variants or sizes < 1. */
+int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms,
+                   int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,6 +111,7 @@ SIGNATURES = {
     "compar_autotune_batched": (_i, [_vp, _i, ctypes.POINTER(compar_problem_t), _d, _vp, _fp,
                                      ctypes.POINTER(_i)]),
     "compar_set_batched_config": (_i, [_vp, _i]),
+    "compar_tc_plan": (_i, [_i, _i64, _i64, _i64, _i, ctypes.POINTER(_i64)]),
     "compar_mlp_param_count": (_i, []),
     "compar_mlp_forward": (_i, [_vp, _fp, _i, _fp, _i, _fp]),
     "compar_mlp_train_steps": (_i, [_vp, _fp, _fp, _fp, _i, _fp, _fp, _fp, _i,
@@ -371,6 +372,18 @@ class Context:
         arr = problems if isinstance(problems, ctypes.Array) else self.problem_array(problems)
         return _status(compar_gemm_batched(self.handle, len(arr), arr, float(tol),
                                            _stream_handle(stream)), "compar_gemm_batched")
+
+    @staticmethod
+    def tc_plan(variant, m, n, k, num_sms=148):
+        """Launch plan of a tensor-core variant (no device needed): dict of
+        num_kb, tiles, splits, kb_per_split, sk_tile0, sk_cpt, sk_q, sk_ctas,
+        sk_chunk_kb."""
+        out = (_i64 * 9)()
+        _status(compar_tc_plan(int(variant), int(m), int(n), int(k), int(num_sms), out),
+                "tc_plan")
+        keys = ("num_kb", "tiles", "splits", "kb_per_split", "sk_tile0", "sk_cpt", "sk_q",
+                "sk_ctas", "sk_chunk_kb")
+        return dict(zip(keys, (int(x) for x in out)))
 
     def set_batched_config(self, config):
         """Force batched configuration 0..4 (None: autotuned / default)."""

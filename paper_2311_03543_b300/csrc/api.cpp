@@ -737,4 +737,8 @@ int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
   return launch_timeout_selftest(ctx->guard, static_cast<cudaStream_t>(stream));
 }
 
+int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out) {
+  return tc_plan_info(variant_id, m, n, k, num_sms, out);
+}
+
 }  // extern "C"

@@ -108,6 +108,7 @@ void set_last_error_text(const std::string& text);
 int launch_tc(int variant, const GemmCall& c, Workspace& ws, const DeviceGuard& g,
               int num_sms, cudaStream_t s);
 bool tc_supported(int variant, const GemmCall& c);
+int tc_plan_info(int variant, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out);
 
 int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s);
 

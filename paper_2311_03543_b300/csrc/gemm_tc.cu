@@ -1274,6 +1274,21 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   }
 }
 
+int tc_plan_info(int v, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out) {
+  if (v < COMPAR_V_TC_TF32 || v >= COMPAR_V_COUNT || v == COMPAR_V_GROUPED || m < 1 || n < 1 ||
+      k < 1 || num_sms < 1 || !out || m > (1 << 30) || n > (1 << 30) || k > (1 << 30))
+    return COMPAR_ERR_INVALID;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  const TcPlan p = tc_plan(v, c, num_sms);
+  const int64_t vals[9] = {p.num_kb, p.tiles,   p.splits, p.kb_per,      p.sk_tile0,
+                           p.sk_cpt, p.sk_q,    p.sk_ctas, sk_chunk_of(v)};
+  for (int i = 0; i < 9; ++i) out[i] = vals[i];
+  return COMPAR_OK;
+}
+
 int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s) {
   timeout_selftest_kernel<<<1, 32, 0, s>>>(g.err_word, g.budget_ns);
   COMPAR_CUDA_TRY(cudaGetLastError());
