@@ -90,7 +90,20 @@ struct SimtCfg {
   static constexpr int kBElems = BK * BN / kThreads;
   static_assert(TM % 4 == 0 && TN % 4 == 0, "micro tile in 4-wide groups");
   static_assert(kAElems % 4 == 0 && kBElems % 4 == 0, "vector loads");
+  static_assert(BM % 32 == 0, "row swizzle of the A tile");
 };
+
+// The A tile is stored transposed (As[k][m]); row m of K column k sits at
+// m ^ a_swizzle<BK>(k).  Each thread stores 4 K columns of one row, so a
+// warp's 32 stores of one K offset cover 32 * 4 / BK rows and BK / 4 column
+// groups; without the swizzle they hit only 32 * 4 / BK banks.  XOR-ing the
+// row with (k / 4) x (128 / BK) spreads them over all 32; multiples of 4
+// keep the 4-row groups that the FMA loop reads as float4 contiguous.
+template <int BK>
+__device__ __forceinline__ int a_swizzle(int k) {
+  static_assert(BK == 16 || BK == 32, "K tile of 16 or 32");
+  return ((k >> 2) & (BK / 4 - 1)) * (128 / BK);
+}
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool VEC>
 // Two CTAs per SM (registers capped at 128) so one CTA's global loads and
@@ -140,7 +153,7 @@ __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads, 2)
       const int e = (v * Cfg::kThreads + tid) * 4;
       const int r = e / BK, c = e % BK;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) As[buf][c + q][r] = ra[4 * v + q];
+      for (int q = 0; q < 4; ++q) As[buf][c + q][r ^ a_swizzle<BK>(c + q)] = ra[4 * v + q];
     }
   };
   // B tile: BK rows x BN columns
@@ -198,7 +211,8 @@ __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads, 2)
       float a[TM], b[TN];
 #pragma unroll
       for (int g = 0; g < TM / 4; ++g) {
-        const float4 x = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + g * Cfg::kRowStride]);
+        const float4 x = *reinterpret_cast<const float4*>(
+            &As[buf][kk][(ty * 4 + g * Cfg::kRowStride) ^ a_swizzle<BK>(kk)]);
         a[4 * g + 0] = x.x; a[4 * g + 1] = x.y; a[4 * g + 2] = x.z; a[4 * g + 3] = x.w;
       }
 #pragma unroll
