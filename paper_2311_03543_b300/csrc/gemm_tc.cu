@@ -132,6 +132,7 @@ struct Layout {
   // MN-major B (16-bit types): boxes of 64 columns x kElemsPerStage K rows,
   // 128-byte rows, one per 64 columns of the tile
   static constexpr int kMnBox = 64 * 2 * kElemsPerStage;
+  static_assert(kMnBox % 1024 == 0, "MN-major boxes hold whole 8-row swizzle groups");
   static constexpr int kThreads = 64 + 32 * T::epi;
   static constexpr int kEpiThreads = 32 * T::epi;
   static constexpr int kEpiCols = BN * 4 / T::epi;  // columns one epilogue warp handles
