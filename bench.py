@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--selector", default=os.path.join(ROOT, "paper_2311_03543_b300",
                                                         "selector_default.bin"))
     ap.add_argument("--detail", default=None, help="write per-shape detail JSON here")
+    ap.add_argument("--online-study", default=None, metavar="SELECTOR_FILE",
+                    help="online-selection study: regret of the selector in SELECTOR_FILE on "
+                         "held-out contexts before and after a stream of exploring calls")
     ap.add_argument("--cpu-table", action="store_true",
                     help="CPU oracle beside the selected GPU variant on 256^3 .. 8192^3")
     return ap.parse_args()
@@ -341,6 +344,16 @@ def main():
         return 0
     if args.cpu_table:
         print(json.dumps({"cpu_vs_gpu": cpu_table()}), flush=True)
+        return 0
+    if args.online_study:
+        import torch
+        import workloads as W
+        import paper_2311_03543_b300 as cp
+        torch.cuda.set_device(0)
+        with cp.Context(0) as ctx:
+            print(json.dumps({"online_study": online_study(ctx, cp, W, torch,
+                                                           torch.device("cuda", 0),
+                                                           args.online_study)}), flush=True)
         return 0
     if args.peaks or args.variants:
         import torch
@@ -725,6 +738,38 @@ def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):
             rs.append(0.0 if times[pick] <= t_best * (1 + tie) else times[pick] / t_best - 1.0)
     judge.close()
     return 100.0 * float(np.mean(rs)), viol, len(rs)
+
+
+def online_study(ctx, cp, W, torch, dev, selector, count=120, calls=800):
+    """Online selection (exploration and warm-start fine-tuning) from a
+    selector that has not seen the call distribution: its mean regret on the
+    first `count` held-out contexts, then `calls` calls drawn from the same
+    law with another seed (54321) made with exploration probability 0.25 and
+    a fine-tune every 100 new timing records, then the regret on the same
+    held-out contexts again (exploration off)."""
+    ctx.selector_load(selector)
+    before = measure_regret(ctx, cp, W, torch, dev, count=count)
+    ctx.set_online(epsilon=0.25, retrain_every=100, finetune_steps=1000)
+    for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts(count=calls, seed=54321)):
+        g = torch.Generator(device=dev)
+        g.manual_seed(70000 + i)
+        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        if dt == cp.BF16:
+            A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        elif dt == cp.F8E4M3:
+            A = A.to(torch.float8_e4m3fn).view(torch.uint8)
+            B = B.to(torch.float8_e4m3fn).view(torch.uint8)
+        C = torch.empty((m, n), device=dev)
+        ctx.gemm(A, B, C, tol=tol, dtype=dt)
+    torch.cuda.synchronize()
+    explored, retrains = ctx.online_stats()
+    ctx.set_online(0.0, 0, 0)
+    after = measure_regret(ctx, cp, W, torch, dev, count=count)
+    return {"selector": os.path.basename(selector), "contexts": after[2], "calls": calls,
+            "explored": explored, "fine_tunes": retrains,
+            "regret_before_pct": before[0], "violations_before": before[1],
+            "regret_after_pct": after[0], "violations_after": after[1]}
 
 
 if __name__ == "__main__":

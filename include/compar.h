@@ -285,12 +285,15 @@ double compar_error_model_predict(compar_ctx_t ctx, int variant,
 /* ---------------------------------------------------------------- models */
 
 /* Load a selector file (history table, error model, MLP weights, feature
- * normaliser, grouped tile choice).  On any error (missing file, bad magic,
- * version, size or checksum) the models already loaded are kept and
- * COMPAR_ERR_IO is returned. */
+ * normaliser, grouped tile choice, stencil history, and a rehearsal sample of
+ * up to 16384 of the timing records the MLP was trained on).  On any error
+ * (missing file, bad magic, version, size or checksum) the models already
+ * loaded are kept and COMPAR_ERR_IO is returned. */
 int compar_selector_load(compar_ctx_t ctx, const char* path);
 
-/* Write the current selector state to `path` (binary, versioned, checksummed). */
+/* Write the current selector state to `path` (binary, versioned,
+ * checksummed); the rehearsal sample is drawn uniformly from the loaded
+ * sample and the records held. */
 int compar_selector_save(compar_ctx_t ctx, const char* path);
 
 /* ---------------------------------------------------------------- learned cost model */
@@ -339,8 +342,10 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr,
                           uint64_t seed, float* val_loss);
 
 /* Continue training the current model from its weights and standardisation
- * on all records (fine-tuning; a fresh training when none exists yet).
- * Arguments as compar_selector_train. */
+ * on all records held plus the loaded rehearsal sample, so that new records
+ * add to what the model knows instead of replacing it (fine-tuning; a fresh
+ * training on the records held when no model exists yet).  Arguments as
+ * compar_selector_train. */
 int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr,
                              uint64_t seed, float* val_loss);
 

@@ -154,6 +154,10 @@ struct compar_ctx {
   compar::HistoryModel hist;
   compar::MlpModel mlp;
   compar::Recorder rec;
+  // A sample of the timing records the loaded MLP was trained on (from the
+  // selector file): online fine-tunes train on it together with the live
+  // records, so that they add what is new instead of forgetting the rest.
+  std::vector<compar_record_t> rehearsal;
   std::unordered_map<compar::DecisionKey, int, compar::DecisionKeyHash> decisions;
   std::vector<compar::PendingTiming> pending;
   std::vector<cudaEvent_t> event_pool;

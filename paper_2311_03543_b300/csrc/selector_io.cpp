@@ -4,6 +4,9 @@
 // The paper's runtime keeps its performance models across runs; this is the
 // equivalent checkpoint.  Format (little endian):
 //   "CMPRSEL1" | u32 version | u64 payload bytes | payload | u64 FNV-1a(payload)
+// The payload ends with a rehearsal sample of timing records (up to
+// kRehearsal, drawn uniformly from the training records and any sample
+// loaded before) for online fine-tuning.
 // A file that fails any check leaves the loaded models untouched.
 #include <cmath>
 #include <cstring>
@@ -16,7 +19,8 @@ namespace compar {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'M', 'P', 'R', 'S', 'E', 'L', '1'};
-constexpr uint32_t kVersion = 6;  // 6: variant ids 0..9 (20 MLP outputs)
+constexpr uint32_t kVersion = 7;  // 7: rehearsal records; variant ids 0..9 (20 MLP outputs)
+constexpr size_t kRehearsal = 16384;
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
   uint64_t h = 1469598103934665603ull;
@@ -139,6 +143,24 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
     w.put<int32_t>(kv.second);
   }
   put_hist(w, ctx->stencil.hist);
+  {
+    // rehearsal sample: reservoir over the loaded sample and the live records
+    std::vector<compar_record_t> pool = ctx->rehearsal;
+    const auto live = ctx->rec.snapshot();
+    pool.insert(pool.end(), live.begin(), live.end());
+    uint64_t st = 0x9E3779B97F4A7C15ull ^ pool.size();
+    auto next = [&]() {
+      uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    for (size_t i = pool.size(); i > 1 && pool.size() > kRehearsal; --i)
+      std::swap(pool[i - 1], pool[next() % i]);  // shuffle, then keep the first kRehearsal
+    if (pool.size() > kRehearsal) pool.resize(kRehearsal);
+    w.put<uint32_t>(static_cast<uint32_t>(pool.size()));
+    for (const auto& rec : pool) w.put(rec);
+  }
 
   std::ofstream f(path, std::ios::binary | std::ios::trunc);
   if (!f) return COMPAR_ERR_IO;
@@ -206,6 +228,15 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
   }
   HistoryModel stencil_hist;
   get_hist(r, stencil_hist, COMPAR_S_COUNT);
+  const uint32_t nr = r.get<uint32_t>();
+  if (nr > kRehearsal) r.ok = false;
+  std::vector<compar_record_t> rehearsal;
+  for (uint32_t i = 0; r.ok && i < nr; ++i) {
+    const auto rec = r.get<compar_record_t>();
+    if (rec.variant < 0 || rec.variant >= kNumVariants || rec.m < 1 || rec.n < 1 || rec.k < 1)
+      r.ok = false;
+    rehearsal.push_back(rec);
+  }
   if (!r.ok || r.off != nbytes) return COMPAR_ERR_IO;
 
   ctx->hist = std::move(hist);
@@ -213,6 +244,7 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
   ctx->mlp = mm;
   ctx->batched_cfg = std::move(batched);
   ctx->stencil.hist = std::move(stencil_hist);
+  ctx->rehearsal = std::move(rehearsal);
   ctx->stencil.decisions.clear();
   ctx->decisions.clear();
   mlp_release(ctx);  // device copies of the old weights are stale

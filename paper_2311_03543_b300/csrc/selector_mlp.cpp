@@ -248,8 +248,10 @@ static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t
   if (!ctx || steps <= 0 || batch <= 0 || batch > 128 || !(lr > 0)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   warm = warm && ctx->mlp.trained;
-  // ---- assemble rows from the records
+  // ---- assemble rows from the records (a fine-tune also rehearses the
+  // sample of the records the loaded model was trained on)
   auto recs = ctx->rec.snapshot();
+  if (warm) recs.insert(recs.end(), ctx->rehearsal.begin(), ctx->rehearsal.end());
   std::vector<std::array<float, kNumFeatures>> feats;
   std::vector<std::array<float, kOutputs>> tgt, msk;
   uint64_t st = seed ^ 0x5EEDull;

@@ -119,6 +119,39 @@ def test_selector_file_round_trip(hctx, tmp_path):
         other.close()
 
 
+def test_rehearsal_sample_is_saved_capped_and_reloaded(tmp_path):
+    """A selector file carries a uniform sample of at most 16384 timing
+    records (48 bytes each): with 20000 records held the file is exactly
+    16384 records larger than with the same models and none held, and a
+    context that loaded the file and records nothing more writes the same
+    sample size again."""
+    import os
+    recs = []
+    for i in range(20000):
+        r = cp.compar_record_t()
+        r.m, r.n, r.k = 64 + i % 512, 32 + i % 256, 16 + i % 1024
+        r.dtype, r.variant, r.batch = cp.F32, i % cp.NUM_VARIANTS, 1
+        if r.variant == cp.V_GROUPED:
+            r.variant = cp.V_SIMT
+        r.tol, r.time_ms, r.rel_err = 1e-5, 0.01 + 1e-6 * i, -1.0
+        recs.append(r)
+    h = cp.Context.host()
+    h.record_add(recs)                  # records and history observations
+    p1 = str(tmp_path / "with.bin")
+    h.selector_save(p1)
+    assert cp.compar_record_clear(h.handle) == cp.OK   # history kept, records gone
+    p0 = str(tmp_path / "none.bin")
+    h.selector_save(p0)
+    assert os.path.getsize(p1) - os.path.getsize(p0) == 16384 * 48
+    h2 = cp.Context.host()
+    h2.selector_load(p1)
+    p2 = str(tmp_path / "again.bin")
+    h2.selector_save(p2)
+    assert os.path.getsize(p2) == os.path.getsize(p1)
+    for c in (h, h2):
+        c.close()
+
+
 def test_corrupted_selector_file_is_rejected_and_model_kept(hctx, tmp_path):
     hctx.record_add([_rec(2048, 2048, 2048, cp.F32, cp.V_SIMT, 1e-6)])
     path = str(tmp_path / "sel.bin")
