@@ -526,6 +526,18 @@ int compar_selftest_timeout(compar_ctx_t ctx, void* stream);
 int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms,
                    int64_t* out);
 
+/* Launch plan of the SIMT variant (COMPAR_V_SIMT) for an m x n x k call
+ * with inputs of `dtype`, B's row stride `ldb` (elements) and a 16-byte
+ * aligned B, on a GPU with `num_sms` SMs, without a device: out[0] 1 for the
+ * skinny-M kernel (a few rows of A against a wide, deep B: K chunks summed
+ * in thread-block clusters), 0 for the tiled kernel; [1] rows and [2]
+ * columns of C per CTA; [3] partial sums added by the reduce pass (1: none);
+ * [4] K per chunk or split (the longest FMA chain); [5] CTAs per cluster
+ * (1 for the tiled kernel).  COMPAR_ERR_INVALID for sizes < 1, ldb < n or
+ * an unknown dtype. */
+int compar_simt_plan(int64_t m, int64_t n, int64_t k, compar_dtype_t dtype, int64_t ldb,
+                     int num_sms, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

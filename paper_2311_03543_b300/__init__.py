@@ -112,6 +112,7 @@ SIGNATURES = {
                                      ctypes.POINTER(_i)]),
     "compar_set_batched_config": (_i, [_vp, _i]),
     "compar_tc_plan": (_i, [_i, _i64, _i64, _i64, _i, ctypes.POINTER(_i64)]),
+    "compar_simt_plan": (_i, [_i64, _i64, _i64, _i, _i64, _i, ctypes.POINTER(_i64)]),
     "compar_mlp_param_count": (_i, []),
     "compar_mlp_forward": (_i, [_vp, _fp, _i, _fp, _i, _fp]),
     "compar_mlp_train_steps": (_i, [_vp, _fp, _fp, _fp, _i, _fp, _fp, _fp, _i,
@@ -383,6 +384,16 @@ class Context:
                 "tc_plan")
         keys = ("num_kb", "tiles", "splits", "kb_per_split", "sk_tile0", "sk_cpt", "sk_q",
                 "sk_ctas", "sk_chunk_kb")
+        return dict(zip(keys, (int(x) for x in out)))
+
+    @staticmethod
+    def simt_plan(m, n, k, dtype=0, ldb=None, num_sms=148):
+        """Launch plan of the SIMT variant (no device needed): dict of
+        skinny, rows, cols, splits, k_per, cluster."""
+        out = (_i64 * 6)()
+        _status(compar_simt_plan(int(m), int(n), int(k), int(dtype),
+                                 int(n if ldb is None else ldb), int(num_sms), out), "simt_plan")
+        keys = ("skinny", "rows", "cols", "splits", "k_per", "cluster")
         return dict(zip(keys, (int(x) for x in out)))
 
     def set_batched_config(self, config):

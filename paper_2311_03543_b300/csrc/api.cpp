@@ -110,7 +110,7 @@ static uint32_t eligible_mask(const compar_ctx* ctx, const GemmCall& c) {
   for (int v = 0; v < kNumVariants; ++v) {
     if (ctx->quarantined[v] || !variant_supported(ctx, v, c)) continue;
     // SIMT's error follows its longest FMA chain (split K shortens it)
-    const int64_t k_chain = v == COMPAR_V_SIMT ? simt_plan(c.m, c.n, c.k, ctx->num_sms).k_per : c.k;
+    const int64_t k_chain = v == COMPAR_V_SIMT ? simt_plan(c, ctx->num_sms).k_per : c.k;
     if (ctx->err.predict(v, c.dtype, k_chain) * ctx->err.margin > c.tol) continue;
     mask |= 1u << v;
   }
@@ -739,6 +739,29 @@ int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
 
 int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out) {
   return tc_plan_info(variant_id, m, n, k, num_sms, out);
+}
+
+int compar_simt_plan(int64_t m, int64_t n, int64_t k, compar_dtype_t dtype, int64_t ldb,
+                     int num_sms, int64_t* out) {
+  if (!out || m < 1 || n < 1 || k < 1 || ldb < n || num_sms < 1 ||
+      (dtype != COMPAR_F32 && dtype != COMPAR_BF16 && dtype != COMPAR_F8E4M3))
+    return COMPAR_ERR_INVALID;
+  GemmCall c;
+  c.m = m;
+  c.n = n;
+  c.k = k;
+  c.lda = k;
+  c.ldb = ldb;
+  c.ldc = n;
+  c.dtype = dtype;
+  const SimtPlan p = simt_plan(c, num_sms);
+  out[0] = p.skinny ? 1 : 0;
+  out[1] = p.bm;
+  out[2] = p.bn;
+  out[3] = p.splits;
+  out[4] = p.k_per;
+  out[5] = p.cluster;
+  return COMPAR_OK;
 }
 
 }  // extern "C"

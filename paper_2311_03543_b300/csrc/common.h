@@ -93,12 +93,19 @@ int launch_splitk_reduce(int m, int n, int splits, const float* partial, float a
                          float* C, int64_t ldc, int num_sms, cudaStream_t s);
 // Tile shape and split-K plan of the SIMT variant: each output is the sum
 // of `splits` partial dot products, each at most `k_per` terms long.
+// Launch plan of the SIMT variant: the tiled kernel (bm x bn tiles, K split
+// `splits` ways), or the skinny kernel (row groups of bm = 8 or 16,
+// 512-column blocks, K chunks of k_per summed in clusters of `cluster`,
+// `splits` cluster sums added by the reduce pass).  k_per is the longest FMA
+// chain.
 struct SimtPlan {
-  int bm, bn, bk;
-  int splits;
-  int64_t k_per;
+  int bm = 0, bn = 0, bk = 0;
+  int splits = 1;
+  int64_t k_per = 0;
+  bool skinny = false;
+  int cluster = 1;
 };
-SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int num_sms);
+SimtPlan simt_plan(const GemmCall& c, int num_sms);
 int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
                         cudaStream_t s, size_t* need_bytes);
 void set_last_error_text(const std::string& text);

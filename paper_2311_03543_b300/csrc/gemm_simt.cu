@@ -6,10 +6,14 @@
 //  * gemm_simt_kernel : shared-memory tiled, register-blocked, with 128-bit
 //    global loads and double-buffered shared-memory tiles; optional split-K
 //    with a separate reduction pass.
+//  * gemm_skinny_kernel: the same variant's plan for a few rows of A against
+//    a wide, deep B, built to stream B from HBM once (split K, cluster sums
+//    through distributed shared memory).
 //
 // Row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc).  Inputs may be
 // float32, bf16 (uint16 bit patterns) or E4M3 (bytes); they are widened to
 // float32 on load and every product and sum is an FP32 FMA.
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -276,14 +280,199 @@ __global__ void __launch_bounds__(SimtCfg<BM, BN, BK, TM, TN, VEC>::kThreads, 1)
   }
 }
 
-// C = alpha * sum_s partial[s] + beta * C
+
+// ------------------------------------------------------------------ skinny M
+// A few rows of A against a wide, deep B: the work is bound by reading B once
+// from HBM (4 K N bytes for float32 against 2 M N K flop; at M = 16 the FMA
+// pipe needs about 0.7 of the time the copy takes).  Thread t of a CTA owns 4
+// adjacent columns and MT rows of C and walks one K chunk: one vector load of
+// 4 B elements per k, SkinnyUnroll<MT> loads per batch, the next batch issued
+// before the current one is used.  The chunk of A sits in shared memory as
+// [k][row], read with broadcast float4 loads.  Row groups are the fastest
+// grid index, so the CTAs that read one B chunk for different rows run
+// together and share it through L2.
+//
+// K is split into chunks.  The CTAs of a cluster (consecutive chunks of one
+// column block) add their partial tiles through distributed shared memory in
+// rank order; the cluster sums go to C when one cluster covers K, else to
+// workspace slabs that splitk_reduce_kernel adds in cluster order.  Every sum
+// is taken in a fixed order, so results are reproducible.
+constexpr int kSkinnyThreads = 128;
+constexpr int kSkinnyCols = 4 * kSkinnyThreads;  // columns of C per CTA
+constexpr int kSkinnyMaxRows = 16;               // rows of C per thread (MT is 8 or 16)
+constexpr int kSkinnyMaxChunk = 512;             // k per CTA (A chunk of 32 KB)
+constexpr int kSkinnyMaxCluster = 8;             // portable cluster size
+constexpr int kSkinnyMaxM = 64;                  // rows the plan takes this kernel for
+constexpr int kSkinnyCtasPerSm = 3;
+static_assert(kSkinnyMaxChunk >= kSkinnyCols, "the partial tile reuses the A chunk's memory");
+template <int MT>
+constexpr int SkinnyUnroll = MT == 8 ? 12 : 8;  // B loads per batch (registers allow)
+
+template <int MT>
+__device__ __forceinline__ void skinny_fma(float (&acc)[MT][4], const float* a_k,
+                                           const float (&b)[4]) {
+#pragma unroll
+  for (int r = 0; r < MT; r += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(a_k + r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[r + 0][q] = fmaf(a.x, b[q], acc[r + 0][q]);
+      acc[r + 1][q] = fmaf(a.y, b[q], acc[r + 1][q]);
+      acc[r + 2][q] = fmaf(a.z, b[q], acc[r + 2][q]);
+      acc[r + 3][q] = fmaf(a.w, b[q], acc[r + 3][q]);
+    }
+  }
+}
+
+template <typename T, int U>
+__device__ __forceinline__ void skinny_load(const T* b, int64_t ldb, float (&v)[U][4]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) ld4(b + u * ldb, v[u]);
+}
+
+template <int MT, int U>
+__device__ __forceinline__ void skinny_fma_batch(float (&acc)[MT][4], const float* a,
+                                                 const float (&v)[U][4]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) skinny_fma<MT>(acc, a + u * MT, v[u]);
+}
+
+// Four sums of one row (columns n .. n+3) to a partial slab, or to C as
+// alpha * s + beta * C.
+__device__ __forceinline__ void skinny_store(const float4 s, int row, int n, int N, float alpha,
+                                             float beta, float* C, int64_t ldc, bool c_vec,
+                                             float* slab) {
+  if (slab != nullptr) {
+    *reinterpret_cast<float4*>(slab + static_cast<int64_t>(row) * N + n) = s;
+    return;
+  }
+  float* c = C + static_cast<int64_t>(row) * ldc + n;
+  const float v[4] = {s.x, s.y, s.z, s.w};
+  if (c_vec) {
+    float4 out;
+    if (beta == 0.f) {
+      out = make_float4(alpha * v[0], alpha * v[1], alpha * v[2], alpha * v[3]);
+    } else {
+      const float4 old = *reinterpret_cast<const float4*>(c);
+      out = make_float4(fmaf(alpha, v[0], beta * old.x), fmaf(alpha, v[1], beta * old.y),
+                        fmaf(alpha, v[2], beta * old.z), fmaf(alpha, v[3], beta * old.w));
+    }
+    *reinterpret_cast<float4*>(c) = out;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = (beta == 0.f) ? alpha * v[q] : fmaf(alpha, v[q], beta * c[q]);
+  }
+}
+
+// Grid (row groups of MT, column blocks, K chunks); launched with clusters of
+// `cluster` CTAs along K (1, 2, 4 or 8).  Needs N % 4 == 0 and B rows whose
+// 4-element groups are aligned to their size (one vector load per 4 columns).
+template <typename T, int MT>
+__global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
+    gemm_skinny_kernel(int M, int N, int K, int k_chunk, int cluster, float alpha,
+                       const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                       int64_t ldb, float beta, float* __restrict__ C, int64_t ldc, bool c_vec,
+                       float* __restrict__ partial) {
+  static_assert(MT % kSkinnyMaxCluster == 0 && MT <= kSkinnyMaxRows, "rows per thread");
+  constexpr int U = SkinnyUnroll<MT>;
+  __shared__ __align__(16) float sm[kSkinnyMaxChunk * MT];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * MT;
+  const int n = blockIdx.y * kSkinnyCols + 4 * tid;
+  const int k0 = blockIdx.z * k_chunk;
+  const int kc = max(0, min(K - k0, k_chunk));  // trailing chunks may be empty
+  const bool active = n < N;
+  const T* b = B + static_cast<int64_t>(k0) * ldb + n;
+  const int full = kc / U * U;
+  float cur[U][4], nxt[U][4];
+  if (active && full > 0) skinny_load(b, ldb, cur);  // in flight while A is staged
+
+  // the chunk of A, widened to float32, as [k][row]; rows past M read as zero
+  for (int e = tid; e < kc * MT; e += kSkinnyThreads) {
+    const int r = e / kc, kk = e - r * kc;
+    sm[kk * MT + r] = (r0 + r < M) ? ld1(A + static_cast<int64_t>(r0 + r) * lda + k0 + kk) : 0.f;
+  }
+  __syncthreads();
+
+  float acc[MT][4];
+#pragma unroll
+  for (int r = 0; r < MT; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+  if (active) {
+    for (int kk = 0; kk < full; kk += 2 * U) {
+      const int k1 = kk + U;
+      if (k1 < full) skinny_load(b + k1 * ldb, ldb, nxt);
+      skinny_fma_batch<MT, U>(acc, sm + kk * MT, cur);
+      if (k1 >= full) break;
+      if (k1 + U < full) skinny_load(b + (k1 + U) * ldb, ldb, cur);
+      skinny_fma_batch<MT, U>(acc, sm + k1 * MT, nxt);
+    }
+    for (int kk = full; kk < kc; ++kk) {
+      float v[4];
+      ld4(b + kk * ldb, v);
+      skinny_fma<MT>(acc, sm + kk * MT, v);
+    }
+  }
+
+  float* slab =
+      partial ? partial + static_cast<int64_t>(blockIdx.z / cluster) * M * N : nullptr;
+  if (cluster == 1) {  // the same for every CTA of the grid
+    if (active)
+#pragma unroll
+      for (int r = 0; r < MT; ++r)
+        if (r0 + r < M)
+          skinny_store(make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]), r0 + r, n, N,
+                       alpha, beta, C, ldc, c_vec, slab);
+    return;
+  }
+
+  // Cluster sum: every CTA leaves its tile in shared memory as [row][column];
+  // rank q adds rows [q * rows, (q + 1) * rows) over the cluster's tiles.
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __syncthreads();  // the A chunk is no longer read
+#pragma unroll
+  for (int r = 0; r < MT; ++r)
+    *reinterpret_cast<float4*>(sm + r * kSkinnyCols + 4 * tid) =
+        make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  cl.sync();
+  const int rows = MT / cluster;
+  const int rank = static_cast<int>(cl.block_rank());
+  for (int i = 0; i < rows; ++i) {
+    const int r = rank * rows + i;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < cluster; ++q) {
+      const float4 v =
+          *cl.map_shared_rank(reinterpret_cast<float4*>(sm + r * kSkinnyCols) + tid, q);
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    if (active && r0 + r < M) skinny_store(s, r0 + r, n, N, alpha, beta, C, ldc, c_vec, slab);
+  }
+  cl.sync();  // no CTA leaves while a peer still reads its tile
+}
+
+// C = alpha * sum_s partial[s] + beta * C, the slabs added in order; the
+// loads of up to 8 slabs are issued together so that their latencies overlap.
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
                                      float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  constexpr int kBatch = 8;
   const int64_t total = static_cast<int64_t>(M) * N;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += partial[z * total + t];
+    for (int z0 = 0; z0 < splits; z0 += kBatch) {
+      float v[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        v[i] = z0 + i < splits ? __ldg(partial + (z0 + i) * total + t) : 0.f;
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        if (z0 + i < splits) s += v[i];
+    }
     const int64_t i = t / N, j = t % N;
     float* c = C + i * ldc + j;
     *c = (beta == 0.f) ? alpha * s : fmaf(alpha, s, beta * *c);
@@ -296,11 +485,10 @@ float effective_alpha(const GemmCall& c) {
 }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
-int run_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
-             cudaStream_t s) {
+int run_simt(const GemmCall& c, const SimtPlan& plan, Workspace& ws, const DeviceGuard& g,
+             int num_sms, cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const SimtPlan plan = simt_plan(c.m, c.n, c.k, num_sms);
   const int splits = plan.splits, k_per = static_cast<int>(plan.k_per);
   float* partial = nullptr;
   if (splits > 1) {
@@ -354,18 +542,104 @@ int run_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
   return COMPAR_OK;
 }
 
+// The skinny plan's kernel (and its reduce pass when more than one cluster
+// covers K); `partial` holds plan.splits slabs of M x N when splits > 1.
+template <typename T>
+int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int num_sms,
+               cudaStream_t s) {
+  const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
+  const float alpha = effective_alpha(c);
+  const bool c_vec = c.ldc % 4 == 0 && reinterpret_cast<uintptr_t>(c.C) % 16 == 0;
+  float* slabs = plan.splits > 1 ? partial : nullptr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((M + plan.bm - 1) / plan.bm, (N + kSkinnyCols - 1) / kSkinnyCols,
+                     plan.splits * plan.cluster);
+  cfg.blockDim = dim3(kSkinnyThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = plan.cluster;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  auto kernel = plan.bm == 8 ? gemm_skinny_kernel<T, 8> : gemm_skinny_kernel<T, 16>;
+  COMPAR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, M, N, K,
+                                     static_cast<int>(plan.k_per), plan.cluster, alpha,
+                                     static_cast<const T*>(c.A), c.lda,
+                                     static_cast<const T*>(c.B), c.ldb, c.beta, c.C, c.ldc,
+                                     c_vec, slabs));
+  count_launch();
+  if (plan.splits > 1) {
+    const int64_t total = static_cast<int64_t>(M) * N;
+    const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, plan.splits, partial, alpha, c.beta, c.C,
+                                                c.ldc);
+    COMPAR_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  return COMPAR_OK;
+}
+
 template <typename T>
 int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                   cudaStream_t s) {
-  if (simt_plan(c.m, c.n, c.k, num_sms).bm == 32)
-    return run_simt<T, 32, 128, 32, 4, 8>(c, ws, g, num_sms, s);
-  return run_simt<T, 128, 128, 16, 8, 8>(c, ws, g, num_sms, s);
+  const SimtPlan plan = simt_plan(c, num_sms);
+  if (plan.skinny) {
+    float* partial = nullptr;
+    if (plan.splits > 1) {
+      const int rc = ws.ensure(static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float), s);
+      if (rc != COMPAR_OK) return rc;
+      partial = static_cast<float*>(ws.ptr);
+    }
+    cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
+    const int rc = run_skinny<T>(c, plan, partial, num_sms, s);
+    if (rc == COMPAR_OK && g.prof) g.prof->end(ev, s, COMPAR_V_SIMT);
+    return rc;
+  }
+  if (plan.bm == 32) return run_simt<T, 32, 128, 32, 4, 8>(c, plan, ws, g, num_sms, s);
+  return run_simt<T, 128, 128, 16, 8, 8>(c, plan, ws, g, num_sms, s);
 }
+
+size_t dtype_bytes(compar_dtype_t d) { return d == COMPAR_F32 ? 4 : (d == COMPAR_BF16 ? 2 : 1); }
 
 }  // namespace
 
-SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int num_sms) {
+SimtPlan simt_plan(const GemmCall& c, int num_sms) {
+  const int64_t m = c.m, n = c.n, k = c.k;
   SimtPlan p;
+  // A few rows against a wide, deep B whose rows allow 4-element vector
+  // loads: the skinny kernel, K split to fill every SM (three CTAs each),
+  // chunks summed on chip in clusters of up to 8.
+  const bool b_vec = n % 4 == 0 && c.ldb % 4 == 0 &&
+                     reinterpret_cast<uintptr_t>(c.B) % (4 * dtype_bytes(c.dtype)) == 0;
+  if (m <= kSkinnyMaxM && n >= kSkinnyCols / 2 && n <= 65535LL * kSkinnyCols && b_vec &&
+      k <= static_cast<int64_t>(kSkinnyMaxChunk) * 32768) {
+    p.skinny = true;
+    p.bm = m <= 8 ? 8 : 16;  // rows of C per thread
+    p.bn = kSkinnyCols;
+    p.bk = 0;
+    const int64_t ctas = ((m + p.bm - 1) / p.bm) * ((n + kSkinnyCols - 1) / kSkinnyCols);
+    int64_t chunks = std::max<int64_t>(1, kSkinnyCtasPerSm * static_cast<int64_t>(num_sms) / ctas);
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, k / 32));
+    int cl = 1;
+    while (cl < kSkinnyMaxCluster && 2 * cl <= chunks) cl *= 2;
+    chunks = chunks / cl * cl;
+    int64_t chunk = (k + chunks - 1) / chunks;
+    chunk = (chunk + 7) / 8 * 8;
+    chunk = std::min<int64_t>(std::max<int64_t>(chunk, 8), kSkinnyMaxChunk);
+    chunks = (k + chunk - 1) / chunk;
+    // a capped chunk can leave a count that is not a multiple of the
+    // cluster; pad with empty chunks only while the grid still fits
+    const int64_t slots = kSkinnyCtasPerSm * static_cast<int64_t>(num_sms);
+    while (cl > 1 && chunks % cl != 0 && (chunks + cl - 1) / cl * cl * ctas > slots) cl /= 2;
+    chunks = (chunks + cl - 1) / cl * cl;
+    p.cluster = cl;
+    p.splits = static_cast<int>(chunks / cl);
+    p.k_per = chunk;
+    return p;
+  }
   // Short-M shapes take a 32-row tile so fewer rows of work are wasted.
   if (m <= 48) {
     p.bm = 32;
@@ -438,7 +712,7 @@ int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, in
                      cudaStream_t s, size_t* need_bytes) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const SimtPlan plan = simt_plan(c.m, c.n, c.k, num_sms);
+  const SimtPlan plan = simt_plan(c, num_sms);
   const int splits = plan.splits, k_per = static_cast<int>(plan.k_per);
   const size_t need = splits > 1 ? static_cast<size_t>(splits) * M * N * sizeof(float) : 0;
   if (need_bytes) *need_bytes = need;
@@ -474,7 +748,15 @@ int run_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, in
 
 int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes, int num_sms,
                         cudaStream_t s, size_t* need_bytes) {
-  if (simt_plan(c.m, c.n, c.k, num_sms).bm == 32)
+  const SimtPlan plan = simt_plan(c, num_sms);
+  if (plan.skinny) {
+    const size_t need =
+        plan.splits > 1 ? static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float) : 0;
+    if (need_bytes) *need_bytes = need;
+    if (need > scratch_bytes) return COMPAR_ERR_INVALID;
+    return run_skinny<float>(c, plan, scratch, num_sms, s);
+  }
+  if (plan.bm == 32)
     return run_simt_scratch<32, 128, 32, 4, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
   return run_simt_scratch<128, 128, 16, 8, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
 }

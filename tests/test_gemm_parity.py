@@ -343,3 +343,70 @@ def test_sweep_shapes_sampled_rows(ctx, v, m, n, k):
     ref = oracle.gemm_rows(A, B, rows)
     assert N.rel_frobenius(got[rows], ref) <= TOL_F32
     assert np.all(np.isfinite(got))
+
+
+# The SIMT variant's skinny-M plan (a few rows of A against a wide, deep B):
+# every branch of the plan — clusters of 1, 2, 4 or 8 CTAs along K, their
+# sums written straight to C or through the reduce pass — with 8- and 16-row
+# groups and ragged rows, column blocks with idle threads, ragged K chunks,
+# alpha and beta; the same call twice gives the same bits.
+SKINNY = [(16, 512, 64), (5, 300, 20), (16, 16384, 1024), (64, 8192, 1024), (48, 65536, 1030),
+          (64, 15360, 2048), (64, 8192, 4096), (33, 1000, 3000), (7, 4096, 4096)]
+
+
+@pytest.mark.parametrize("m,n,k", SKINNY)
+def test_simt_skinny_plan_matches_oracle_and_is_deterministic(ctx, m, n, k):
+    import paper_2311_03543_b300 as cp
+    assert cp.Context.simt_plan(m, n, k)["skinny"] == 1
+    A = W.uniform(m, k, seed=71); B = W.uniform(k, n, seed=72); C0 = W.uniform(m, n, seed=73)
+    got = _run(ctx, cp.V_SIMT, A, B, alpha=1.5, beta=-0.5, C0=C0)
+    again = _run(ctx, cp.V_SIMT, A, B, alpha=1.5, beta=-0.5, C0=C0)
+    assert np.array_equal(got, again)
+    rows = W.sample_rows(m, 8, seed=74) if m * n * k > 2e9 else np.arange(m)
+    ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.5, C0=C0)
+    assert N.rel_frobenius(got[rows], ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("m,n,k", [(16, 4096, 1000), (3, 1024, 333)])
+def test_simt_skinny_plan_bf16_and_fp8_inputs(ctx, m, n, k):
+    import paper_2311_03543_b300 as cp
+    A = W.bf16_input(m, k, seed=75); B = W.bf16_input(k, n, seed=76)
+    got = _run(ctx, cp.V_SIMT, A, B, dtype=cp.BF16)
+    assert N.rel_frobenius(got, oracle.gemm(N.bf16_to_f32(A), N.bf16_to_f32(B))) <= TOL_F32
+    A8 = W.fp8_input(m, k, seed=77); B8 = W.fp8_input(k, n, seed=78)
+    ctx.set_fp8_scales(0.5, 0.25)
+    try:
+        got = _run(ctx, cp.V_SIMT, A8, B8, dtype=cp.F8E4M3)
+    finally:
+        ctx.set_fp8_scales(1.0, 1.0)
+    ref = 0.125 * oracle.gemm(N.e4m3_to_f64(A8), N.e4m3_to_f64(B8))
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+
+
+def test_simt_skinny_plan_unaligned_c_and_b(ctx):
+    """C one element past a 16-byte boundary takes the scalar stores; B one
+    element past it cannot be read 4 columns at a time and takes the tiled
+    kernel.  Both still match the oracle."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import host
+    m, n, k = 16, 1024, 700
+    A = W.uniform(m, k, seed=79); B = W.uniform(k, n, seed=80); C0 = W.uniform(m, n, seed=81)
+    ref = oracle.gemm(A, B, alpha=2.0, beta=0.5, C0=C0)
+    dA = torch.from_numpy(A).cuda()
+    bbuf = torch.zeros(k * n + 1, device="cuda")
+    cbuf = torch.zeros(m * n + 1, device="cuda")
+    for b_off, c_off in ((0, 1), (1, 0)):
+        dB = bbuf[b_off:b_off + k * n].view(k, n)
+        dB.copy_(torch.from_numpy(B))
+        dC = cbuf[c_off:c_off + m * n].view(m, n)
+        dC.copy_(torch.from_numpy(C0))
+        ctx.set_scalars(2.0, 0.5)
+        ctx.force_variant(cp.V_SIMT)
+        try:
+            ctx.gemm(dA, dB, dC)
+        finally:
+            ctx.force_variant(None)
+            ctx.set_scalars(1.0, 0.0)
+        assert ctx.check_device_error() == cp.OK
+        assert N.rel_frobenius(host(dC), ref) <= TOL_F32
