@@ -519,13 +519,14 @@ def main():
     # selector regret against exhaustive measurement (held-out contexts)
     regret = None
     if not args.no_regret and rank == 0:
-        r_pct, r_viol, r_n = measure_regret(ctx, cp, W, torch, dev)
-        t_pct, t_viol, t_n = measure_regret(ctx, cp, W, torch, dev, count=50,
-                                            contexts=W.heldout_tight_contexts())
-        regret = {"mean_pct": r_pct, "violations": r_viol, "contexts": r_n,
+        r_pct, r_viol, r_n, r_worst = measure_regret(ctx, cp, W, torch, dev)
+        t_pct, t_viol, t_n, t_worst = measure_regret(ctx, cp, W, torch, dev, count=50,
+                                                     contexts=W.heldout_tight_contexts())
+        regret = {"mean_pct": r_pct, "violations": r_viol, "contexts": r_n, "worst": r_worst,
                   "set": "held-out contexts 0..199 (M,N,K log-uniform [16,4096], f32/bf16/fp8, "
                          "tol 1e-5/1e-3/1e-1)", "feasibility": "library FP64 residual check, 8 rows",
                   "tight": {"mean_pct": t_pct, "violations": t_viol, "contexts": t_n,
+                            "worst": t_worst,
                             "set": "f32 contexts 0..49 at tol 1e-6 (same shape law)"}}
 
     batched = None
@@ -701,11 +702,13 @@ def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):
     eligible variant is timed with compar_measure; its error is the library's
     FP64 residual check on 8 rows.  best = fastest feasible variant (ties
     within 2 % go to the lower id); regret = t(pick)/t(best) - 1, and an
-    infeasible pick costs a rerun.  Returns (regret %, violations, contexts).
+    infeasible pick costs a rerun.  A context whose regret exceeds 10 % has
+    its pick and its best variant timed once more (each keeps its faster
+    time).  Returns (regret %, violations, contexts, worst context).
     """
     import numpy as np
     tie = 0.02
-    rs, viol = [], 0
+    rs, viol, worst = [], 0, None
     judge = cp.Context(dev.index)   # measures; the selector's history never sees it
     contexts = W.heldout_contexts() if contexts is None else contexts
     for i, (m, n, k, dt, tol) in enumerate(contexts[:count]):
@@ -730,14 +733,30 @@ def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):
                 feas.add(v)
         if not feas:
             continue
-        t_best = min(times[v] for v in feas)
-        if pick not in feas:
-            viol += 1
-            rs.append((times[pick] + t_best) / t_best - 1.0)
-        else:
-            rs.append(0.0 if times[pick] <= t_best * (1 + tie) else times[pick] / t_best - 1.0)
+
+        def regret():
+            t_best = min(times[v] for v in feas)
+            if pick not in feas:
+                return (times[pick] + t_best) / t_best - 1.0
+            return 0.0 if times[pick] <= t_best * (1 + tie) else times[pick] / t_best - 1.0
+
+        r = regret()
+        if r > 0.1:
+            # a large gap: time the pick and the fastest feasible variant once
+            # more (5 repetitions) and keep each one's faster measurement, so a
+            # single disturbed timing does not decide the context
+            best = min(feas, key=lambda v: times[v])
+            for v in {pick, best}:
+                times[v] = min(times[v], judge.measure(v, A, B, C, tol=tol, warmup=1, reps=5,
+                                                       dtype=dt))
+            r = regret()
+        viol += pick not in feas
+        rs.append(r)
+        if worst is None or r > worst["pct"] / 100.0:
+            worst = {"context": i, "m": m, "n": n, "k": k, "dtype": int(dt), "tol": tol,
+                     "pick": int(pick), "pct": 100.0 * r}
     judge.close()
-    return 100.0 * float(np.mean(rs)), viol, len(rs)
+    return 100.0 * float(np.mean(rs)), viol, len(rs), worst
 
 
 def online_study(ctx, cp, W, torch, dev, selector, count=120, calls=800):
