@@ -571,14 +571,8 @@ int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int num_
                                      static_cast<const T*>(c.B), c.ldb, c.beta, c.C, c.ldc,
                                      c_vec, slabs));
   count_launch();
-  if (plan.splits > 1) {
-    const int64_t total = static_cast<int64_t>(M) * N;
-    const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
-    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, plan.splits, partial, alpha, c.beta, c.C,
-                                                c.ldc);
-    COMPAR_CUDA_TRY(cudaGetLastError());
-    count_launch();
-  }
+  if (plan.splits > 1)
+    return launch_splitk_reduce(M, N, plan.splits, partial, alpha, c.beta, c.C, c.ldc, num_sms, s);
   return COMPAR_OK;
 }
 
