@@ -649,10 +649,13 @@ def measure_stencil(ctx, cp, W, torch, dev, reps=5):
     grid, 100 steps, seeded chip on the device): the selected variant timed
     over `reps` calls after two warm-ups (CUDA events; three grids of 268 MB,
     larger than L2), every variant timed for context, and the roofline of the
-    selected one: HBM for the naive variant (12 bytes per cell and step), the
-    shared-memory pipe for temporal blocking (three 4-byte loads and one store
-    per cell and step over the 80 x 80 region of each 64 x 64 tile), against
-    148 SMs x 128 bytes per clock x 2032 MHz = 38.5 TB/s."""
+    selected one: HBM for the naive variant (12 bytes per cell and step); for
+    temporal blocking the FP32 pipe, which bounds it once a warp's row moves
+    through shared memory in 16-byte pieces (the instruction issue is the
+    limit: 10 FP32 operations per cell and step, counted once per cell of the
+    grid, against 148 SMs x 128 lanes x 2032 MHz = 38.5 T operations/s; the
+    kernel also recomputes the 128 x 80 region of every 112 x 64 tile,
+    x1.43)."""
     rows, cols, iters = W.STENCIL_HEADLINE
     prm = cp.Context.stencil_params(**W.STENCIL_PARAMS)
     g = torch.Generator(device=dev)
@@ -683,10 +686,11 @@ def measure_stencil(ctx, cp, W, torch, dev, reps=5):
         except (OSError, ValueError, KeyError):
             roof["peak"], roof["peak_source"] = 6400.0, "fallback 6.4 TB/s"
     else:
-        region = (80.0 * 80.0) / (64.0 * 64.0)
-        roof = {"bound": "smem", "unit": "TB/s",
-                "achieved": cell_steps * region * 16 / (ms / 1e3) / 1e12, "peak": 38.5,
-                "peak_source": "derived: 148 SMs x 128 B/clock x 2032 MHz"}
+        region = (128.0 * 80.0) / (112.0 * 64.0)
+        roof = {"bound": "alu", "unit": "Tops/s",
+                "achieved": cell_steps * 10 / (ms / 1e3) / 1e12, "peak": 38.5,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz",
+                "with_halo": cell_steps * 10 * region / (ms / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"workload": f"thermal stencil {rows}x{cols}, {iters} steps, seeded chip",
             "chosen": cp.STENCIL_NAMES[chosen], "ms": ms,

@@ -13,8 +13,8 @@
 //
 //   NAIVE : one thread per cell, one launch per step, neighbours from global
 //           memory (through L1/L2); ping-pong between two device grids.
-//   TILED : temporal blocking: a CTA loads the 80 x 80 region around its
-//           64 x 64 tile into shared memory and advances it up to 8 steps
+//   TILED : temporal blocking: a CTA loads the 128 x 80 region around its
+//           112 x 64 tile into shared memory and advances it up to 8 steps
 //           there, writing the centre; ceil(steps / 8) launches.
 //   TMA   : TILED with the region loaded by one TMA box into shared memory,
 //           completion on an mbarrier (bounded wait).
@@ -62,61 +62,88 @@ __global__ void stencil_naive_kernel(const float* __restrict__ T, const float* _
 }
 
 // ------------------------------------------------------------------ TILED / TMA
-// A CTA owns a 64 x 64 output tile and advances the 80 x 80 region around it
-// (8-cell halo) up to 8 steps in shared memory.  The region sits in an
-// 82 x 92 buffer: one pad row above and below, 4 pad columns left and 8
-// right (row pitch 92 floats = 368 bytes, a TMA-friendly multiple of 16; 20
-// rows are 1840 floats = 16 banks apart, so a warp that spans two row groups
-// reads 32 different banks).
-// Thread t owns column t % 80 of the region and the 20 rows of group t / 80:
-// it keeps its 20 power values in registers and walks its column with the
-// north / centre / south values in registers, so a cell costs three shared
-// loads and one store.  Every step recomputes the whole region; cells at
-// distance d from the region border are exact for d >= steps (pad and stale
-// values only reach inward one cell per step), and the 64 x 64 centre is at
-// distance >= 8.  A cell on the grid edge takes itself as the missing
-// neighbour, so tiles on the grid edge need no halo there.
-constexpr int kTile = 64;               // output cells per side
-constexpr int kHalo = 8;                // steps per launch at most
-constexpr int kReg = kTile + 2 * kHalo; // 80: region side
-constexpr int kPitch = 92;              // buffer row pitch (floats)
-constexpr int kBufRows = kReg + 2;      // 82: region + pad row above and below
-constexpr int kColOff = 4;              // region column 0 sits at buffer column 4
-constexpr int kGroupRows = 20;          // rows per thread
-constexpr int kBlockThreads = kReg * (kReg / kGroupRows);  // 320
-constexpr int kBufBytes = kBufRows * kPitch * 4;            // 30,176
+// A CTA owns a 112 x 64 output tile (columns x rows) and advances the
+// 128 x 80 region around it (8-cell halo) up to 8 steps in shared memory.
+// The region sits in an 82 x 136 buffer: one pad row above and below, 4 pad
+// columns on either side (row pitch 136 floats = 544 bytes, a TMA-friendly
+// multiple of 16).  Warp w owns the 10-row strip w of the region and lane l
+// the 4 columns 4l .. 4l+3, so a warp's row is 512 contiguous bytes: the
+// south values arrive with one conflict-free 16-byte load, the new values
+// leave with one 16-byte store, the west neighbour of the lane's first cell
+// and the east neighbour of its last come from the adjacent lanes' registers
+// (shuffles), and only lanes 0 and 31 read theirs from shared memory (one
+// wavefront).  The thread keeps its 40 power values in registers and walks
+// its strip with the north / centre / south values in registers.  Every
+// step recomputes the whole region; cells at distance d from the region
+// border are exact for d >= steps (pad and stale values only reach inward
+// one cell per step), and the 112 x 64 centre is at distance >= 8.  A cell
+// on the grid edge takes itself as the missing neighbour, so tiles on the
+// grid edge need no halo there.
+constexpr int kTileW = 112;              // output columns per tile
+constexpr int kTileH = 64;               // output rows per tile
+constexpr int kHalo = 8;                 // steps per launch at most
+constexpr int kRegW = kTileW + 2 * kHalo;  // 128: region width (32 lanes x 4)
+constexpr int kRegH = kTileH + 2 * kHalo;  // 80: region height
+constexpr int kColOff = 4;               // region column 0 sits at buffer column 4
+constexpr int kPitch = kRegW + 2 * kColOff;  // 136 floats per buffer row
+constexpr int kBufRows = kRegH + 2;      // 82: region + pad row above and below
+constexpr int kStripRows = 10;           // rows per thread
+constexpr int kBlockThreads = 32 * (kRegH / kStripRows);   // 256: one warp per strip
+constexpr int kBufBytes = kBufRows * kPitch * 4;            // 44,608
 constexpr int kTiledSmem = 2 * kBufBytes + 64 + 128;        // two buffers, barrier, alignment
+static_assert(kRegW == 32 * 4 && kRegH % kStripRows == 0, "a warp row covers the region");
+static_assert((kPitch * 4) % 16 == 0 && (kColOff * 4) % 16 == 0, "16-byte rows and cells");
+
+__device__ __forceinline__ float4 lds4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
 
 // Buffer (row, col) of region cell (li, lj): (li + 1, lj + kColOff).  The
-// buffer covers grid rows r0 - 1 .. r0 + 80 and columns c0 - 4 .. c0 + 87,
+// buffer covers grid rows r0 - 1 .. r0 + 80 and columns c0 - 4 .. c0 + 131,
 // r0 / c0 the grid coordinates of region cell (0, 0).
 template <bool kEdge>
-__device__ __forceinline__ const float* advance(float* A, float* B, const float (&p)[kGroupRows],
-                                                int steps, int r0, int c0, int rows, int cols,
+__device__ __forceinline__ const float* advance(float* A, float* B,
+                                                const float (&p)[kStripRows][4], int steps,
+                                                int r0, int c0, int rows, int cols,
                                                 const Coef& k) {
-  const int lj = threadIdx.x % kReg, grp = threadIdx.x / kReg;
-  const int sc = lj + kColOff;
-  const int br0 = 1 + grp * kGroupRows;          // first buffer row of this thread
-  const int gi0 = r0 + grp * kGroupRows, gj = c0 + lj;
-  const bool w_in = !kEdge || gj > 0, e_in = !kEdge || gj < cols - 1;
+  const int lane = threadIdx.x & 31, strip = threadIdx.x >> 5;
+  const int sc = kColOff + 4 * lane;              // buffer column of the first cell
+  const int br0 = 1 + strip * kStripRows;         // first buffer row of the strip
+  const int gi0 = r0 + strip * kStripRows, gj0 = c0 + 4 * lane;
+  const int eoff = lane == 0 ? -1 : 4;            // lanes 0 / 31: west / east in memory
   float* cur = A;
   float* nxt = B;
   for (int s = 0; s < steps; ++s) {
     const float* col = cur + br0 * kPitch + sc;
-    float tn = col[-kPitch], tc = col[0];
+    float4 tn = lds4(col - kPitch), tc = lds4(col);
 #pragma unroll
-    for (int i = 0; i < kGroupRows; ++i) {
-      const float ts = col[(i + 1) * kPitch];
-      float w = col[i * kPitch - 1], e = col[i * kPitch + 1];
-      float n = tn, so = ts;
-      if (kEdge) {
-        const int gi = gi0 + i;
-        if (gi <= 0) n = tc;
-        if (gi >= rows - 1) so = tc;
-        if (!w_in) w = tc;
-        if (!e_in) e = tc;
+    for (int i = 0; i < kStripRows; ++i) {
+      const float4 ts = lds4(col + (i + 1) * kPitch);
+      float edge = 0.f;
+      if (lane == 0 || lane == 31) edge = col[i * kPitch + eoff];
+      float w0 = __shfl_up_sync(0xffffffffu, tc.w, 1);
+      float e3 = __shfl_down_sync(0xffffffffu, tc.x, 1);
+      if (lane == 0) w0 = edge;
+      if (lane == 31) e3 = edge;
+      const float t[4] = {tc.x, tc.y, tc.z, tc.w};
+      const float n[4] = {tn.x, tn.y, tn.z, tn.w};
+      const float so[4] = {ts.x, ts.y, ts.z, ts.w};
+      const float w[4] = {w0, tc.x, tc.y, tc.z};
+      const float e[4] = {tc.y, tc.z, tc.w, e3};
+      float o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float nq = n[q], sq = so[q], wq = w[q], eq = e[q];
+        if (kEdge) {
+          const int gi = gi0 + i, gj = gj0 + q;
+          if (gi <= 0) nq = t[q];
+          if (gi >= rows - 1) sq = t[q];
+          if (gj <= 0) wq = t[q];
+          if (gj >= cols - 1) eq = t[q];
+        }
+        o[q] = cell_update(t[q], nq, sq, wq, eq, p[i][q], k);
       }
-      nxt[(br0 + i) * kPitch + sc] = cell_update(tc, n, so, w, e, p[i], k);
+      *reinterpret_cast<float4*>(nxt + (br0 + i) * kPitch + sc) = make_float4(o[0], o[1], o[2], o[3]);
       tn = tc;
       tc = ts;
     }
@@ -125,29 +152,32 @@ __device__ __forceinline__ const float* advance(float* A, float* B, const float 
     cur = nxt;
     nxt = tmp;
   }
-  (void)rows;
   return cur;
 }
 
 // The thread's power values (0 outside the grid).
 __device__ __forceinline__ void load_power(const float* __restrict__ P, int r0, int c0, int rows,
-                                           int cols, float (&p)[kGroupRows]) {
-  const int lj = threadIdx.x % kReg, grp = threadIdx.x / kReg;
-  const int gj = c0 + lj;
+                                           int cols, float (&p)[kStripRows][4]) {
+  const int lane = threadIdx.x & 31, strip = threadIdx.x >> 5;
+  const int gj0 = c0 + 4 * lane;
 #pragma unroll
-  for (int i = 0; i < kGroupRows; ++i) {
-    const int gi = r0 + grp * kGroupRows + i;
-    p[i] = (gi >= 0 && gi < rows && gj >= 0 && gj < cols)
-               ? __ldg(P + static_cast<int64_t>(gi) * cols + gj)
-               : 0.f;
+  for (int i = 0; i < kStripRows; ++i) {
+    const int gi = r0 + strip * kStripRows + i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gj = gj0 + q;
+      p[i][q] = (gi >= 0 && gi < rows && gj >= 0 && gj < cols)
+                    ? __ldg(P + static_cast<int64_t>(gi) * cols + gj)
+                    : 0.f;
+    }
   }
 }
 
-// Writes the tile's 64 x 64 centre (cells inside the grid).
+// Writes the tile's 112 x 64 centre (cells inside the grid).
 __device__ __forceinline__ void store_centre(const float* buf, float* out, int tr, int tc,
                                              int rows, int cols) {
-  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kBlockThreads) {
-    const int li = idx / kTile, lj = idx % kTile;
+  for (int idx = threadIdx.x; idx < kTileW * kTileH; idx += kBlockThreads) {
+    const int li = idx / kTileW, lj = idx % kTileW;
     const int gi = tr + li, gj = tc + lj;
     if (gi < rows && gj < cols)
       out[static_cast<int64_t>(gi) * cols + gj] =
@@ -156,19 +186,19 @@ __device__ __forceinline__ void store_centre(const float* buf, float* out, int t
 }
 
 __device__ __forceinline__ bool edge_tile(int r0, int c0, int rows, int cols) {
-  return r0 <= 0 || c0 <= 0 || r0 + kReg >= rows || c0 + kReg >= cols;
+  return r0 <= 0 || c0 <= 0 || r0 + kRegH >= rows || c0 + kRegW >= cols;
 }
 
-__global__ void __launch_bounds__(kBlockThreads, 3)
+__global__ void __launch_bounds__(kBlockThreads, 2)
     stencil_tiled_kernel(const float* __restrict__ T, const float* __restrict__ P,
                          float* __restrict__ out, int rows, int cols, int steps, Coef k) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   float* A = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                       ~static_cast<uintptr_t>(127));
   float* B = A + kBufRows * kPitch;
-  const int tr = blockIdx.y * kTile, tc = blockIdx.x * kTile;
+  const int tr = blockIdx.y * kTileH, tc = blockIdx.x * kTileW;
   const int r0 = tr - kHalo, c0 = tc - kHalo;
-  // buffer rows r0-1 .. r0+80, columns c0-4 .. c0+87 (0 outside the grid)
+  // buffer rows r0-1 .. r0+80, columns c0-4 .. c0+131 (0 outside the grid)
   for (int idx = threadIdx.x; idx < kBufRows * kPitch; idx += kBlockThreads) {
     const int bi = idx / kPitch, bj = idx % kPitch;
     const int gi = r0 - 1 + bi, gj = c0 - kColOff + bj;
@@ -176,7 +206,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
                  ? __ldg(T + static_cast<int64_t>(gi) * cols + gj)
                  : 0.f;
   }
-  float p[kGroupRows];
+  float p[kStripRows][4];
   load_power(P, r0, c0, rows, cols, p);
   __syncthreads();
   const float* res = edge_tile(r0, c0, rows, cols)
@@ -189,7 +219,7 @@ struct TmaMaps {
   CUtensorMap t;
 };
 
-__global__ void __launch_bounds__(kBlockThreads, 3)
+__global__ void __launch_bounds__(kBlockThreads, 2)
     stencil_tma_kernel(const __grid_constant__ TmaMaps maps, const float* __restrict__ P,
                        float* __restrict__ out, int rows, int cols, int steps, Coef k,
                        int* err_word, unsigned long long budget_ns) {
@@ -200,7 +230,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
   float* B = A + kBufRows * kPitch;
   uint64_t* bar = reinterpret_cast<uint64_t*>(B + kBufRows * kPitch);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 1);
-  const int tr = blockIdx.y * kTile, tc = blockIdx.x * kTile;
+  const int tr = blockIdx.y * kTileH, tc = blockIdx.x * kTileW;
   const int r0 = tr - kHalo, c0 = tc - kHalo;
   if (threadIdx.x == 0) {
     dev::mbar_init(bar, 1);
@@ -209,12 +239,12 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // one 92 x 82 box at x = c0 - 4 (a multiple of 4 floats: 16 bytes),
+    // one 136 x 82 box at x = c0 - 4 (a multiple of 4 floats: 16 bytes),
     // y = r0 - 1; cells outside the grid read as zero
     dev::mbar_arrive_expect_tx(bar, kBufBytes);
     dev::tma_load_2d(A, &maps.t, bar, c0 - kColOff, r0 - 1);
   }
-  float p[kGroupRows];
+  float p[kStripRows][4];
   load_power(P, r0, c0, rows, cols, p);   // overlaps the box load
   const dev::WaitCtx w{abort_flag, err_word, budget_ns};
   const bool ok = dev::mbar_wait(bar, 0, w);
@@ -263,7 +293,7 @@ int stencil_launch(int v, int64_t rows64, int64_t cols64, int iters,
       const dim3 grid((cols + 31) / 32, (rows + 7) / 8);
       stencil_naive_kernel<<<grid, block, 0, s>>>(src, P, dst, rows, cols, k);
     } else {
-      const dim3 grid((cols + kTile - 1) / kTile, (rows + kTile - 1) / kTile);
+      const dim3 grid((cols + kTileW - 1) / kTileW, (rows + kTileH - 1) / kTileH);
       if (v == COMPAR_S_TILED) {
         static bool attr = false;
         if (!attr) {
@@ -302,11 +332,11 @@ bool stencil_supported(int v, int64_t rows, int64_t cols, bool aligned16) {
   if (rows > (1 << 30) || cols > (1 << 30) || rows * cols > (int64_t(1) << 34)) return false;
   switch (v) {
     case COMPAR_S_NAIVE: return (rows + 7) / 8 <= 65535;
-    case COMPAR_S_TILED: return (rows + kTile - 1) / kTile <= 65535;
+    case COMPAR_S_TILED: return (rows + kTileH - 1) / kTileH <= 65535;
     case COMPAR_S_TMA:
       // TMA needs 16-byte aligned grids and rows (cols a multiple of 4)
       return tma_available() && aligned16 && (cols % 4 == 0) &&
-             (rows + kTile - 1) / kTile <= 65535;
+             (rows + kTileH - 1) / kTileH <= 65535;
     default: return false;
   }
 }

@@ -33,9 +33,9 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
 
 // Roofline prior (ms).  NAIVE: per step, read T and P and write T (12 bytes
 // per cell) at the copy bandwidth, plus a launch.  TILED / TMA: per launch of
-// up to 8 steps, the 80 x 80 region of T and P in and the 64 x 64 centre out
-// (~16.5 bytes per cell), and 8 steps of shared-memory work (~28 bytes of
-// shared traffic per cell and step, 1.27x redundant halo cells) at
+// up to 8 steps, the 128 x 80 region of T and P in and the 112 x 64 centre
+// out (~15.4 bytes per output cell), and 8 steps of shared-memory work (~9
+// bytes of shared traffic per cell and step, 1.43x redundant halo cells) at
 // 128 bytes / clock / SM.
 double stencil_prior_ms(int v, int64_t rows, int64_t cols, int iters, int num_sms) {
   const double cells = static_cast<double>(rows) * cols;
@@ -43,7 +43,7 @@ double stencil_prior_ms(int v, int64_t rows, int64_t cols, int iters, int num_sm
   if (iters == 0) return 1e3 * cells * 8 / bw + 3e-3;
   if (v == COMPAR_S_NAIVE) return iters * (1e3 * cells * 12 / bw + 3e-3);
   const int launches = (iters + 7) / 8;
-  const double per_launch = 1e3 * std::max(cells * 16.5 / bw, cells * 8 * 1.27 * 28 / smem);
+  const double per_launch = 1e3 * std::max(cells * 15.4 / bw, cells * 8 * 1.43 * 9 / smem);
   return launches * (per_launch * (v == COMPAR_S_TMA ? 0.95 : 1.0) + 4e-3);
 }
 

@@ -51,7 +51,8 @@ def _run(ctx, v, T0, P, iters):
 
 
 SHAPES = [(1, 1, 3), (1, 36, 5), (50, 1, 5), (64, 64, 8), (65, 132, 9), (130, 200, 17),
-          (257, 300, 20), (96, 64, 1), (80, 76, 0)]
+          (257, 300, 20), (96, 64, 1), (80, 76, 0), (64, 112, 8), (65, 113, 9), (64, 224, 16),
+          (130, 225, 17), (81, 240, 12), (200, 128, 7)]
 
 
 @pytest.mark.parametrize("rows,cols,iters", SHAPES)
