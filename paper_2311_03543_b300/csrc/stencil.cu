@@ -46,6 +46,26 @@ __device__ __forceinline__ float cell_update(float t, float n, float s, float w,
   return __fmaf_rn(k.c, f, t);
 }
 
+// The same step for two cells with packed FP32 pair instructions: every
+// element is rounded exactly as in cell_update (x - y is x + (-y), the
+// product by -2 is exact, and amb - t is the single rounding of
+// fma(t, -1, amb)), so the results are bit-identical at half the
+// instruction count.
+struct Coef2 {
+  float2 c, gx, gy, gz, amb;
+};
+
+__device__ __forceinline__ float2 cell_update2(float2 t, float2 n, float2 s, float2 w, float2 e,
+                                               float2 p, const Coef2& k) {
+  const float2 m2t = __fmul2_rn(t, make_float2(-2.f, -2.f));
+  const float2 dy = __fadd2_rn(__fadd2_rn(n, s), m2t);
+  const float2 dx = __fadd2_rn(__fadd2_rn(w, e), m2t);
+  float2 f = __ffma2_rn(dy, k.gy, p);
+  f = __ffma2_rn(dx, k.gx, f);
+  f = __ffma2_rn(__ffma2_rn(t, make_float2(-1.f, -1.f), k.amb), k.gz, f);
+  return __ffma2_rn(k.c, f, t);
+}
+
 // ------------------------------------------------------------------ NAIVE
 __global__ void stencil_naive_kernel(const float* __restrict__ T, const float* __restrict__ P,
                                      float* __restrict__ out, int rows, int cols, Coef k) {
@@ -111,6 +131,8 @@ __device__ __forceinline__ const float* advance(float* A, float* B,
   const int br0 = 1 + strip * kStripRows;         // first buffer row of the strip
   const int gi0 = r0 + strip * kStripRows, gj0 = c0 + 4 * lane;
   const int eoff = lane == 0 ? -1 : 4;            // lanes 0 / 31: west / east in memory
+  const Coef2 k2{make_float2(k.c, k.c), make_float2(k.gx, k.gx), make_float2(k.gy, k.gy),
+                 make_float2(k.gz, k.gz), make_float2(k.amb, k.amb)};
   float* cur = A;
   float* nxt = B;
   for (int s = 0; s < steps; ++s) {
@@ -126,24 +148,28 @@ __device__ __forceinline__ const float* advance(float* A, float* B,
       if (lane == 0) w0 = edge;
       if (lane == 31) e3 = edge;
       const float t[4] = {tc.x, tc.y, tc.z, tc.w};
-      const float n[4] = {tn.x, tn.y, tn.z, tn.w};
-      const float so[4] = {ts.x, ts.y, ts.z, ts.w};
-      const float w[4] = {w0, tc.x, tc.y, tc.z};
-      const float e[4] = {tc.y, tc.z, tc.w, e3};
-      float o[4];
+      float n[4] = {tn.x, tn.y, tn.z, tn.w};
+      float so[4] = {ts.x, ts.y, ts.z, ts.w};
+      float w[4] = {w0, tc.x, tc.y, tc.z};
+      float e[4] = {tc.y, tc.z, tc.w, e3};
+      if (kEdge) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float nq = n[q], sq = so[q], wq = w[q], eq = e[q];
-        if (kEdge) {
+        for (int q = 0; q < 4; ++q) {
           const int gi = gi0 + i, gj = gj0 + q;
-          if (gi <= 0) nq = t[q];
-          if (gi >= rows - 1) sq = t[q];
-          if (gj <= 0) wq = t[q];
-          if (gj >= cols - 1) eq = t[q];
+          if (gi <= 0) n[q] = t[q];
+          if (gi >= rows - 1) so[q] = t[q];
+          if (gj <= 0) w[q] = t[q];
+          if (gj >= cols - 1) e[q] = t[q];
         }
-        o[q] = cell_update(t[q], nq, sq, wq, eq, p[i][q], k);
       }
-      *reinterpret_cast<float4*>(nxt + (br0 + i) * kPitch + sc) = make_float4(o[0], o[1], o[2], o[3]);
+      const float2 o01 = cell_update2(make_float2(t[0], t[1]), make_float2(n[0], n[1]),
+                                      make_float2(so[0], so[1]), make_float2(w[0], w[1]),
+                                      make_float2(e[0], e[1]), make_float2(p[i][0], p[i][1]), k2);
+      const float2 o23 = cell_update2(make_float2(t[2], t[3]), make_float2(n[2], n[3]),
+                                      make_float2(so[2], so[3]), make_float2(w[2], w[3]),
+                                      make_float2(e[2], e[3]), make_float2(p[i][2], p[i][3]), k2);
+      *reinterpret_cast<float4*>(nxt + (br0 + i) * kPitch + sc) =
+          make_float4(o01.x, o01.y, o23.x, o23.y);
       tn = tc;
       tc = ts;
     }
