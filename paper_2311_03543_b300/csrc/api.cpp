@@ -44,10 +44,25 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
   return COMPAR_OK;
 }
 
+int Workspace::ensure_counters(size_t n, cudaStream_t s) {
+  if (n <= counter_n) return COMPAR_OK;
+  const size_t grow = std::max<size_t>(n, 4096);
+  if (counters) COMPAR_CUDA_TRY(cudaFreeAsync(counters, s));
+  counters = nullptr;
+  counter_n = 0;
+  COMPAR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&counters), grow * sizeof(int), s));
+  COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, grow * sizeof(int), s));
+  counter_n = grow;
+  return COMPAR_OK;
+}
+
 void Workspace::release() {
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
   bytes = 0;
+  if (counters) cudaFree(counters);
+  counters = nullptr;
+  counter_n = 0;
 }
 
 static const char* kVariantNames[] = {"naive-f32", "simt-f32", "tc-tf32",

@@ -43,7 +43,12 @@ struct GemmCall {
 struct Workspace {
   void* ptr = nullptr;
   size_t bytes = 0;
+  // Arrival counters, zero between calls (a kernel that counts on them puts
+  // each one it used back to zero); grown zeroed, stream-ordered.
+  int* counters = nullptr;
+  size_t counter_n = 0;
   int ensure(size_t need, cudaStream_t s);
+  int ensure_counters(size_t n, cudaStream_t s);
   void release();
 };
 

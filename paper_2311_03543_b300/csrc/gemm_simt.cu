@@ -304,6 +304,7 @@ constexpr int kSkinnyMaxChunk = 512;             // k per CTA (A chunk of 32 KB)
 constexpr int kSkinnyMaxCluster = 8;             // portable cluster size
 constexpr int kSkinnyMaxM = 64;                  // rows the plan takes this kernel for
 constexpr int kSkinnyCtasPerSm = 3;
+constexpr int kSkinnyLastSum = 8;  // at most this many cluster sums: added in the kernel
 static_assert(kSkinnyMaxChunk >= kSkinnyCols, "the partial tile reuses the A chunk's memory");
 template <int MT>
 constexpr int SkinnyUnroll = MT == 8 ? 12 : 8;  // B loads per batch (registers allow)
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
     gemm_skinny_kernel(int M, int N, int K, int k_chunk, int cluster, float alpha,
                        const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
                        int64_t ldb, float beta, float* __restrict__ C, int64_t ldc, bool c_vec,
-                       float* __restrict__ partial) {
+                       float* __restrict__ partial, int* __restrict__ counters) {
   static_assert(MT % kSkinnyMaxCluster == 0 && MT <= kSkinnyMaxRows, "rows per thread");
   constexpr int U = SkinnyUnroll<MT>;
   __shared__ __align__(16) float sm[kSkinnyMaxChunk * MT];
@@ -417,6 +418,9 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
 
   float* slab =
       partial ? partial + static_cast<int64_t>(blockIdx.z / cluster) * M * N : nullptr;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  int rank = 0, row0 = 0, rows = MT;  // the rows of C this CTA writes
   if (cluster == 1) {  // the same for every CTA of the grid
     if (active)
 #pragma unroll
@@ -424,35 +428,70 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
         if (r0 + r < M)
           skinny_store(make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]), r0 + r, n, N,
                        alpha, beta, C, ldc, c_vec, slab);
-    return;
+  } else {
+    // Cluster sum: every CTA leaves its tile in shared memory as [row][column];
+    // rank q adds rows [q * rows, (q + 1) * rows) over the cluster's tiles.
+    __syncthreads();  // the A chunk is no longer read
+#pragma unroll
+    for (int r = 0; r < MT; ++r)
+      *reinterpret_cast<float4*>(sm + r * kSkinnyCols + 4 * tid) =
+          make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    cl.sync();
+    rows = MT / cluster;
+    rank = static_cast<int>(cl.block_rank());
+    row0 = rank * rows;
+    for (int i = 0; i < rows; ++i) {
+      const int r = row0 + i;
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < cluster; ++q) {
+        const float4 v =
+            *cl.map_shared_rank(reinterpret_cast<float4*>(sm + r * kSkinnyCols) + tid, q);
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+      }
+      if (active && r0 + r < M) skinny_store(s, r0 + r, n, N, alpha, beta, C, ldc, c_vec, slab);
+    }
   }
 
-  // Cluster sum: every CTA leaves its tile in shared memory as [row][column];
-  // rank q adds rows [q * rows, (q + 1) * rows) over the cluster's tiles.
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  __syncthreads();  // the A chunk is no longer read
-#pragma unroll
-  for (int r = 0; r < MT; ++r)
-    *reinterpret_cast<float4*>(sm + r * kSkinnyCols + 4 * tid) =
-        make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-  cl.sync();
-  const int rows = MT / cluster;
-  const int rank = static_cast<int>(cl.block_rank());
-  for (int i = 0; i < rows; ++i) {
-    const int r = rank * rows + i;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < cluster; ++q) {
-      const float4 v =
-          *cl.map_shared_rank(reinterpret_cast<float4*>(sm + r * kSkinnyCols) + tid, q);
-      s.x += v.x;
-      s.y += v.y;
-      s.z += v.z;
-      s.w += v.w;
+  // With `counters`, the last cluster of this row group and column block to
+  // finish adds every cluster's slab in cluster order and writes C (the same
+  // sums as splitk_reduce_kernel), and puts the counter back to zero for the
+  // next call.  No CTA waits for another: each one counts its cluster's
+  // arrival and leaves unless it was the last.
+  if (counters != nullptr) {
+    __shared__ int last_flag;
+    const int groups = gridDim.z / cluster;
+    __threadfence();  // this thread's slab stores, before the arrival is counted
+    if (cluster == 1) __syncthreads(); else cl.sync();
+    if (rank == 0 && tid == 0) {
+      int* cnt = counters + blockIdx.y * gridDim.x + blockIdx.x;
+      const int before = atomicAdd(cnt, 1);
+      last_flag = before == groups - 1;
+      if (before == groups - 1) *cnt = 0;
     }
-    if (active && r0 + r < M) skinny_store(s, r0 + r, n, N, alpha, beta, C, ldc, c_vec, slab);
+    if (cluster == 1) __syncthreads(); else cl.sync();
+    const int last = cluster == 1 ? last_flag : *cl.map_shared_rank(&last_flag, 0);
+    if (last) {
+      __threadfence();
+      for (int i = 0; i < rows; ++i) {
+        const int row = r0 + row0 + i;
+        if (!active || row >= M) continue;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int g = 0; g < groups; ++g) {
+          const float4 v = __ldcg(reinterpret_cast<const float4*>(
+              partial + (static_cast<int64_t>(g) * M + row) * N + n));
+          s.x += v.x;
+          s.y += v.y;
+          s.z += v.z;
+          s.w += v.w;
+        }
+        skinny_store(s, row, n, N, alpha, beta, C, ldc, c_vec, nullptr);
+      }
+    }
   }
-  cl.sync();  // no CTA leaves while a peer still reads its tile
+  if (cluster > 1) cl.sync();  // no CTA leaves while a peer still reads its shared memory
 }
 
 // C = alpha * sum_s partial[s] + beta * C, the slabs added in order; the
@@ -542,11 +581,13 @@ int run_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
   return COMPAR_OK;
 }
 
-// The skinny plan's kernel (and its reduce pass when more than one cluster
-// covers K); `partial` holds plan.splits slabs of M x N when splits > 1.
+// The skinny plan's kernel; when more than one cluster covers K, `partial`
+// holds plan.splits slabs of M x N, added by the last cluster to finish when
+// `counters` (zero, one per row group and column block) is given, else by
+// the reduce pass.
 template <typename T>
-int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int num_sms,
-               cudaStream_t s) {
+int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int* counters,
+               int num_sms, cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const float alpha = effective_alpha(c);
   const bool c_vec = c.ldc % 4 == 0 && reinterpret_cast<uintptr_t>(c.C) % 16 == 0;
@@ -569,9 +610,9 @@ int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int num_
                                      static_cast<int>(plan.k_per), plan.cluster, alpha,
                                      static_cast<const T*>(c.A), c.lda,
                                      static_cast<const T*>(c.B), c.ldb, c.beta, c.C, c.ldc,
-                                     c_vec, slabs));
+                                     c_vec, slabs, plan.splits > 1 ? counters : nullptr));
   count_launch();
-  if (plan.splits > 1)
+  if (plan.splits > 1 && counters == nullptr)
     return launch_splitk_reduce(M, N, plan.splits, partial, alpha, c.beta, c.C, c.ldc, num_sms, s);
   return COMPAR_OK;
 }
@@ -582,13 +623,20 @@ int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int nu
   const SimtPlan plan = simt_plan(c, num_sms);
   if (plan.skinny) {
     float* partial = nullptr;
+    int* counters = nullptr;
     if (plan.splits > 1) {
-      const int rc = ws.ensure(static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float), s);
+      int rc = ws.ensure(static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float), s);
       if (rc != COMPAR_OK) return rc;
       partial = static_cast<float*>(ws.ptr);
+      if (plan.splits <= kSkinnyLastSum) {  // few slabs: the last cluster adds them
+        rc = ws.ensure_counters(static_cast<size_t>((c.m + plan.bm - 1) / plan.bm) *
+                                    ((c.n + kSkinnyCols - 1) / kSkinnyCols), s);
+        if (rc != COMPAR_OK) return rc;
+        counters = ws.counters;
+      }
     }
     cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
-    const int rc = run_skinny<T>(c, plan, partial, num_sms, s);
+    const int rc = run_skinny<T>(c, plan, partial, counters, num_sms, s);
     if (rc == COMPAR_OK && g.prof) g.prof->end(ev, s, COMPAR_V_SIMT);
     return rc;
   }
@@ -748,7 +796,7 @@ int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes,
         plan.splits > 1 ? static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float) : 0;
     if (need_bytes) *need_bytes = need;
     if (need > scratch_bytes) return COMPAR_ERR_INVALID;
-    return run_skinny<float>(c, plan, scratch, num_sms, s);
+    return run_skinny<float>(c, plan, scratch, nullptr, num_sms, s);
   }
   if (plan.bm == 32)
     return run_simt_scratch<32, 128, 32, 4, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);
