@@ -757,8 +757,11 @@ def measure_regret(ctx, cp, W, torch, dev, count=200, contexts=None):
         viol += pick not in feas
         rs.append(r)
         if worst is None or r > worst["pct"] / 100.0:
+            best = min(feas, key=lambda v: times[v])
             worst = {"context": i, "m": m, "n": n, "k": k, "dtype": int(dt), "tol": tol,
-                     "pick": int(pick), "pct": 100.0 * r}
+                     "pick": int(pick), "best": int(best), "feasible": sorted(int(v) for v in feas),
+                     "times_us": {int(v): 1e3 * t for v, t in times.items()},
+                     "pct": 100.0 * r}
     judge.close()
     return 100.0 * float(np.mean(rs)), viol, len(rs), worst
 
