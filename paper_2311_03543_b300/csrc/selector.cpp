@@ -164,6 +164,12 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
       ovh_us += K * 0.06;
       break;
     case COMPAR_V_SIMT:
+      if (m <= 64 && n >= 256 && n % 4 == 0) {
+        // the skinny-M plan: B streamed once (~4.5 TB/s measured on long
+        // chunks) overlapping FMAs on the rows padded to 8 or 16 (~30 TF/s)
+        const double mp = m <= 8 ? 8.0 : std::ceil(M / 16) * 16;
+        return 1e-3 * (8 + 1e6 * std::max(K * N * in_elem / 4.5e12, 2 * mp * N * K / 30e12));
+      }
       peak = 45e12;
       flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
       break;
