@@ -74,3 +74,24 @@ def test_noalloc_refuses_a_plan_beyond_its_scratch_limit():
     C = torch.zeros((128, 4096), device="cuda")
     assert _noalloc(A, B, C) == cp.ERR_INVALID
     assert b"16 MiB" in cp.compar_last_error()
+
+
+@pytest.mark.parametrize("m,n,k", [(16, 4096, 4096), (64, 15360, 2048), (8, 227328, 1000)])
+def test_skinny_in_kernel_slab_sum_equals_reduce_pass_bitwise(m, n, k):
+    """The skinny-M plan adds up to 8 cluster sums in the kernel (the last
+    cluster to arrive); the allocation-free entry point adds the same slabs
+    with the reduce pass.  Both add them in cluster order and apply alpha and
+    beta the same way, so the results agree bit for bit."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    plan = cp.Context.simt_plan(m, n, k)
+    assert plan["skinny"] == 1 and 1 < plan["splits"] <= 8
+    with cp.Context(0) as ctx:
+        A = torch.from_numpy(W.uniform(m, k, seed=91)).cuda()
+        B = torch.from_numpy(W.uniform(k, n, seed=92)).cuda()
+        C0 = torch.from_numpy(W.uniform(m, n, seed=93)).cuda()
+        C = C0.clone()
+        assert _noalloc(A, B, C, alpha=1.5, beta=-0.5) == cp.OK
+        ref = _regular(ctx, A, B, alpha=1.5, beta=-0.5, C0=C0)
+        torch.cuda.synchronize()
+        assert torch.equal(C, ref)
