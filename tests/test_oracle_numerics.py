@@ -194,3 +194,171 @@ def test_rel_frobenius_closed_forms():
     assert N.rel_frobenius(2 * a, a) == 1.0
     assert N.rel_frobenius(a + np.array([[0.0, 0.5]]), a) == pytest.approx(0.1)
     assert N.rel_frobenius(np.zeros(3), np.zeros(3)) == 0.0
+
+
+# ------------------------------------------------------------------------------
+# The product compositions of the split methods, pinned by exact arithmetic.
+#
+# Each operand entry is built from pieces chosen first (random mantissas and
+# exponents, the pieces' bit ranges disjoint and every piece away from a
+# rounding boundary), so the split is known without calling the split code,
+# and every one of the piece products has a different size.  The method's
+# product is then fixed by a rule stated apart from the oracle's list of
+# terms: keep the products whose piece orders (hi 0, mid 1, lo 2) add up to
+# at most the number of pieces minus one.  Exact rational sums decide
+# equality, so replacing, dropping or transposing any one term fails.
+
+def _pieces(rows, cols, seed, offsets, sigs):
+    """Matrices of pieces p_0 > p_1 > ... and their exact sum (float32).
+
+    Piece j of an entry has sigs[j] significant bits, a mantissa strictly
+    between 1 and 2 - 2^-(sigs[j]-1) (never a power of two, never the
+    largest mantissa) and exponent e - offsets[j] (e in [-3, 3]).  The
+    offsets put every piece below half the spacing of the piece before it
+    (strictly, with the rest added), so rounding the sum to the first
+    piece's width gives the first piece back, rounding what remains gives
+    the second, and so on; and the widths keep the sum within float32's 24
+    significant bits.  Signs are independent per piece.
+    """
+    r = np.random.default_rng(seed)
+    e = r.integers(-3, 4, size=(rows, cols))
+    out = []
+    for off, sig in zip(offsets, sigs):
+        scale = 2 ** (sig - 1)
+        mant = r.integers(scale + 1, 2 * scale - 1, size=(rows, cols))     # m / 2^(sig-1)
+        sign = r.choice([-1, 1], size=(rows, cols))
+        out.append(sign * mant.astype(np.float64) * np.exp2((e - off - (sig - 1)).astype(np.float64)))
+    total = sum(out)
+    f32 = total.astype(np.float32)
+    assert np.array_equal(f32.astype(np.float64), total)     # the sum is exact in float32
+    return f32, out
+
+
+def _exact_matmul(X, Y):
+    from fractions import Fraction
+    m, k = X.shape
+    n = Y.shape[1]
+    Xf = [[Fraction(float(v)) for v in row] for row in X]
+    Yf = [[Fraction(float(v)) for v in row] for row in Y]
+    return [[sum((Xf[i][p] * Yf[p][j] for p in range(k)), Fraction(0)) for j in range(n)]
+            for i in range(m)]
+
+
+def _as_fractions(C):
+    from fractions import Fraction
+    return [[Fraction(float(v)) for v in row] for row in np.asarray(C, np.float64)]
+
+
+def _add(*mats):
+    return [[sum(vals) for vals in zip(*rows)] for rows in zip(*mats)]
+
+
+def _sub(X, Y):
+    return [[a - b for a, b in zip(rx, ry)] for rx, ry in zip(X, Y)]
+
+
+def _kept_by_order_rule(pa, pb):
+    """Sum of the piece products whose orders add up to <= len(pa) - 1."""
+    n = len(pa)
+    terms = [_exact_matmul(pa[i], pb[j]) for i in range(n) for j in range(n) if i + j <= n - 1]
+    dropped = [_exact_matmul(pa[i], pb[j]) for i in range(n) for j in range(n) if i + j > n - 1]
+    return _add(*terms), _add(*dropped), len(terms), len(dropped)
+
+
+def _all_products_distinct(pa, pb):
+    n = len(pa)
+    prods = {(i, j): _exact_matmul(pa[i], pb[j]) for i in range(n) for j in range(n)}
+    keys = list(prods)
+    for x in range(len(keys)):
+        for y in range(x + 1, len(keys)):
+            assert prods[keys[x]] != prods[keys[y]], (keys[x], keys[y])
+    for key, P in prods.items():                          # and no product is its own transpose
+        assert all(v != 0 for row in P for v in row), key
+
+
+def test_split6_product_is_exactly_the_six_leading_piece_products():
+    import oracle
+    # bf16 pieces: hi and mid 8 significant bits, lo 6, each 9 binades below the last
+    A, pa = _pieces(5, 7, seed=31, offsets=(0, 9, 18), sigs=(8, 8, 6))
+    B, pb = _pieces(7, 4, seed=32, offsets=(0, 9, 18), sigs=(8, 8, 6))
+    # the oracle's split returns the chosen pieces
+    for X, px in ((A, pa), (B, pb)):
+        got = [N.bf16_to_f32(p).astype(np.float64) for p in N.split_bf16_3(X)]
+        for g, want in zip(got, px):
+            assert np.array_equal(g, want)
+    _all_products_distinct(pa, pb)
+    kept, dropped, nk, nd = _kept_by_order_rule(pa, pb)
+    assert (nk, nd) == (6, 3)
+    got = _as_fractions(N.split6_product(A, B, oracle.gemm))
+    assert got == kept
+    # the three dropped products are exactly what separates it from A*B
+    assert _sub(_exact_matmul(A, B), got) == dropped
+
+
+def test_split3_tf32_product_is_exactly_the_three_leading_piece_products():
+    import oracle
+    # TF32 pieces: 11 significant bits each, lo 12 binades below hi
+    A, pa = _pieces(6, 5, seed=33, offsets=(0, 12), sigs=(11, 11))
+    B, pb = _pieces(5, 3, seed=34, offsets=(0, 12), sigs=(11, 11))
+    for X, px in ((A, pa), (B, pb)):
+        got = [p.astype(np.float64) for p in N.split_tf32(X)]
+        for g, want in zip(got, px):
+            assert np.array_equal(g, want)
+    _all_products_distinct(pa, pb)
+    kept, dropped, nk, nd = _kept_by_order_rule(pa, pb)
+    assert (nk, nd) == (3, 1)
+    got = _as_fractions(N.split3_tf32_product(A, B, oracle.gemm))
+    assert got == kept
+    assert _sub(_exact_matmul(A, B), got) == dropped
+
+
+def test_split3_operands_give_the_three_leading_bf16_piece_products():
+    # the 2-piece bf16 split's three products (the 3xBF16 variant's sum)
+    import oracle
+    A, pa = _pieces(4, 6, seed=35, offsets=(0, 9), sigs=(8, 8))
+    B, pb = _pieces(6, 5, seed=36, offsets=(0, 9), sigs=(8, 8))
+    ah, al, bh, bl = N.split3_operands(A, B)
+    for g, want in zip((ah, al, bh, bl), (pa[0], pa[1], pb[0], pb[1])):
+        assert np.array_equal(g, want)
+    kept, dropped, nk, nd = _kept_by_order_rule(pa, pb)
+    got = _as_fractions(oracle.gemm(ah, bh) + oracle.gemm(ah, bl) + oracle.gemm(al, bh))
+    assert got == kept and (nk, nd) == (3, 1)
+
+
+def _abs_product(A, B):
+    import oracle
+    return oracle.gemm(np.abs(A.astype(np.float64)), np.abs(B.astype(np.float64)))
+
+
+def test_split6_product_error_bound_on_float32_data():
+    # |mid| <= 2^-8 |x| and |lo| <= 2^-16 |x| (test_three_piece_split_pieces_shrink),
+    # hi + mid + lo = x exactly, so the dropped mid*lo + lo*mid + lo*lo is at
+    # most (2^-23 + 2^-32) |a||b| per product; the float64 sums add K 2^-53.
+    import oracle
+    for seed, (m, n, k) in ((41, (33, 29, 300)), (42, (16, 64, 1024))):
+        A = W.normal(m, k, seed=seed)
+        B = W.uniform(k, n, seed=seed + 100)
+        exact = oracle.gemm(A, B)
+        s6 = N.split6_product(A, B, oracle.gemm)
+        bound = (2.0 ** -23 + 2.0 ** -32 + 4 * k * 2.0 ** -53) * _abs_product(A, B)
+        assert np.all(np.abs(s6 - exact) <= bound)
+        # and it is closer to A*B than the two-piece, three-product split
+        ah, al, bh, bl = N.split3_operands(A, B)
+        s3 = oracle.gemm(ah, bh) + oracle.gemm(ah, bl) + oracle.gemm(al, bh)
+        assert N.rel_frobenius(s6, exact) < N.rel_frobenius(s3, exact) / 100
+
+
+def test_split3_tf32_product_error_bound_on_float32_data():
+    # a = hi + lo + r with |r| <= 2^-22 |a| and |lo| <= 2^-11 |a| (rounding to
+    # 11 significant bits twice), so a*b - kept = lo_a lo_b + r_a b + (hi_b + lo_b) r_b... is at
+    # most about 3 * 2^-22 |a||b|
+    import oracle
+    for seed, (m, n, k) in ((43, (31, 17, 500)), (44, (8, 40, 2048))):
+        A = W.uniform(m, k, seed=seed)
+        B = W.normal(k, n, seed=seed + 100)
+        exact = oracle.gemm(A, B)
+        s3 = N.split3_tf32_product(A, B, oracle.gemm)
+        bound = (3.01 * 2.0 ** -22 + 4 * k * 2.0 ** -53) * _abs_product(A, B)
+        assert np.all(np.abs(s3 - exact) <= bound)
+        one = oracle.gemm(N.tf32_round(A), N.tf32_round(B))   # the plain TF32 product
+        assert N.rel_frobenius(s3, exact) < N.rel_frobenius(one, exact) / 100
