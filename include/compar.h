@@ -29,7 +29,11 @@
  * found on the host are returned synchronously; kernel-side failures (a
  * bounded wait that ran out) are latched in a device error word and returned
  * by compar_check_device_error.  No call aborts the process.  A context is not
- * thread-safe: use one context per host thread.
+ * thread-safe: use one context per host thread.  The calls on one context
+ * share its device workspace (operand copies, partial sums, arrival
+ * counters), so they must run in order on the GPU: issue them on one stream,
+ * or order the streams yourself (events); calls that overlap on the GPU give
+ * undefined results for those calls.
  *
  * beta == 0 means C is not read (BLAS convention).
  */
@@ -167,7 +171,10 @@ typedef struct {
     float scale_a, scale_b;   /* FP8 dequantisation factors, else ignored */
 } compar_problem_t;
 
-/* Many independent GEMMs of uneven sizes in one call.  `probs` is a HOST
+/* Many independent GEMMs of uneven sizes in one call.  The paper has no
+ * counterpart of this call: its runtime schedules each mmul task on its own
+ * (Sec. 2.2); batching uneven products into one launch is this library's
+ * addition for many small products on one GPU.  `probs` is a HOST
  * array of `count` problems and is copied before return.  F32 problems run at
  * FP32 accuracy when tol <= 1e-5 (3xBF16 mode), else on TF32; BF16 problems
  * on bf16 tensor cores.  The selector picks between one persistent grouped
@@ -191,8 +198,10 @@ int compar_gemm_batched(compar_ctx_t ctx, int count,
  * loads the library holds until the process exits.  A shape whose split-K
  * plan needs more than 16 MiB is refused with COMPAR_ERR_INVALID (the text is
  * in compar_last_error); nothing needs to start zeroed.  The first call on a
- * device does a one-time set-up (it looks up the array's device address and
- * the SM count), so make that first call before any stream capture.  All
+ * device does a one-time set-up (the device check and the SM count; it may
+ * also load the library's device code), so make that first call before any
+ * stream capture.  Every call looks up the array's device address again, so
+ * the call keeps working after the device's context is reset.  All
  * calls share the one array: calls that may overlap on the GPU (different
  * streams or host threads without ordering) race on it; calls on one stream
  * are ordered and safe.  Returns COMPAR_OK, COMPAR_ERR_INVALID,
@@ -284,9 +293,13 @@ double compar_error_model_predict(compar_ctx_t ctx, int variant,
 
 /* ---------------------------------------------------------------- models */
 
-/* Load a selector file (history table, error model, MLP weights, feature
- * normaliser, grouped tile choice, stencil history, and a rehearsal sample of
- * up to 16384 of the timing records the MLP was trained on).  On any error
+/* Load a selector file: the performance models the selection rests on.
+ * In the paper the runtime picks a variant from performance models trained
+ * on earlier runs, their training decides how often it mis-selects (Sec. 3.2,
+ * the matrix-multiply results) and better training is named as future work
+ * (Sec. 5).  The file holds the history table, error model, MLP weights,
+ * feature normaliser, grouped tile choice, stencil history, and a rehearsal
+ * sample of up to 16384 of the timing records the MLP was trained on.  On any error
  * (missing file, bad magic, version, size or checksum) the models already
  * loaded are kept and COMPAR_ERR_IO is returned. */
 int compar_selector_load(compar_ctx_t ctx, const char* path);

@@ -50,8 +50,8 @@ int Workspace::ensure_counters(size_t n, cudaStream_t s) {
   if (counters) COMPAR_CUDA_TRY(cudaFreeAsync(counters, s));
   counters = nullptr;
   counter_n = 0;
-  COMPAR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&counters), grow * sizeof(int), s));
-  COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, grow * sizeof(int), s));
+  COMPAR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&counters), grow * sizeof(*counters), s));
+  COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, grow * sizeof(*counters), s));
   counter_n = grow;
   return COMPAR_OK;
 }

@@ -43,10 +43,19 @@ struct GemmCall {
 struct Workspace {
   void* ptr = nullptr;
   size_t bytes = 0;
-  // Arrival counters, zero between calls (a kernel that counts on them puts
-  // each one it used back to zero); grown zeroed, stream-ordered.
-  int* counters = nullptr;
+  // Arrival counters: each word holds the epoch of the launch that last
+  // counted on it (high 32 bits) and that launch's count (low 32 bits).  A
+  // launch takes a fresh epoch (never 0), so a word from any earlier launch
+  // reads as a count of zero: nothing has to be reset between calls, and a
+  // word left inconsistent by calls that overlapped on the GPU does not
+  // carry over into later calls.  Grown zeroed, stream-ordered.
+  unsigned long long* counters = nullptr;
   size_t counter_n = 0;
+  uint32_t counter_epoch = 0;
+  uint32_t next_epoch() {
+    if (++counter_epoch == 0) counter_epoch = 1;
+    return counter_epoch;
+  }
   int ensure(size_t need, cudaStream_t s);
   int ensure_counters(size_t n, cudaStream_t s);
   void release();

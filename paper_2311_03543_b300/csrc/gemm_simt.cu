@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
     gemm_skinny_kernel(int M, int N, int K, int k_chunk, int cluster, float alpha,
                        const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
                        int64_t ldb, float beta, float* __restrict__ C, int64_t ldc, bool c_vec,
-                       float* __restrict__ partial, int* __restrict__ counters) {
+                       float* __restrict__ partial, unsigned long long* __restrict__ counters,
+                       unsigned int epoch) {
   static_assert(MT % kSkinnyMaxCluster == 0 && MT <= kSkinnyMaxRows, "rows per thread");
   constexpr int U = SkinnyUnroll<MT>;
   __shared__ __align__(16) float sm[kSkinnyMaxChunk * MT];
@@ -457,19 +458,29 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
 
   // With `counters`, the last cluster of this row group and column block to
   // finish adds every cluster's slab in cluster order and writes C (the same
-  // sums as splitk_reduce_kernel), and puts the counter back to zero for the
-  // next call.  No CTA waits for another: each one counts its cluster's
-  // arrival and leaves unless it was the last.
+  // sums as splitk_reduce_kernel).  No CTA waits for another: each one counts
+  // its cluster's arrival and leaves unless it was the last.  A counter word
+  // is (epoch << 32 | count); a word carrying another launch's epoch counts
+  // as zero, so no reset is needed between calls.
   if (counters != nullptr) {
     __shared__ int last_flag;
-    const int groups = gridDim.z / cluster;
+    const unsigned int groups = gridDim.z / cluster;
     __threadfence();  // this thread's slab stores, before the arrival is counted
     if (cluster == 1) __syncthreads(); else cl.sync();
     if (rank == 0 && tid == 0) {
-      int* cnt = counters + blockIdx.y * gridDim.x + blockIdx.x;
-      const int before = atomicAdd(cnt, 1);
+      unsigned long long* cnt = counters + blockIdx.y * gridDim.x + blockIdx.x;
+      unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(cnt);
+      unsigned int before;
+      for (;;) {  // at most `groups` clusters contend for one word
+        before = static_cast<unsigned int>(seen >> 32) == epoch
+                     ? static_cast<unsigned int>(seen) : 0u;
+        const unsigned long long next =
+            (static_cast<unsigned long long>(epoch) << 32) | (before + 1u);
+        const unsigned long long got = atomicCAS(cnt, seen, next);
+        if (got == seen) break;
+        seen = got;
+      }
       last_flag = before == groups - 1;
-      if (before == groups - 1) *cnt = 0;
     }
     if (cluster == 1) __syncthreads(); else cl.sync();
     const int last = cluster == 1 ? last_flag : *cl.map_shared_rank(&last_flag, 0);
@@ -583,11 +594,11 @@ int run_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s) {
 
 // The skinny plan's kernel; when more than one cluster covers K, `partial`
 // holds plan.splits slabs of M x N, added by the last cluster to finish when
-// `counters` (zero, one per row group and column block) is given, else by
+// `counters` (one per row group and column block, with this launch's epoch) is given, else by
 // the reduce pass.
 template <typename T>
-int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int* counters,
-               int num_sms, cudaStream_t s) {
+int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial,
+               unsigned long long* counters, unsigned int epoch, int num_sms, cudaStream_t s) {
   const int M = static_cast<int>(c.m), N = static_cast<int>(c.n), K = static_cast<int>(c.k);
   const float alpha = effective_alpha(c);
   const bool c_vec = c.ldc % 4 == 0 && reinterpret_cast<uintptr_t>(c.C) % 16 == 0;
@@ -610,7 +621,7 @@ int run_skinny(const GemmCall& c, const SimtPlan& plan, float* partial, int* cou
                                      static_cast<int>(plan.k_per), plan.cluster, alpha,
                                      static_cast<const T*>(c.A), c.lda,
                                      static_cast<const T*>(c.B), c.ldb, c.beta, c.C, c.ldc,
-                                     c_vec, slabs, plan.splits > 1 ? counters : nullptr));
+                                     c_vec, slabs, plan.splits > 1 ? counters : nullptr, epoch));
   count_launch();
   if (plan.splits > 1 && counters == nullptr)
     return launch_splitk_reduce(M, N, plan.splits, partial, alpha, c.beta, c.C, c.ldc, num_sms, s);
@@ -623,7 +634,8 @@ int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int nu
   const SimtPlan plan = simt_plan(c, num_sms);
   if (plan.skinny) {
     float* partial = nullptr;
-    int* counters = nullptr;
+    unsigned long long* counters = nullptr;
+    unsigned int epoch = 0;
     if (plan.splits > 1) {
       int rc = ws.ensure(static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float), s);
       if (rc != COMPAR_OK) return rc;
@@ -633,10 +645,11 @@ int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int nu
                                     ((c.n + kSkinnyCols - 1) / kSkinnyCols), s);
         if (rc != COMPAR_OK) return rc;
         counters = ws.counters;
+        epoch = ws.next_epoch();
       }
     }
     cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
-    const int rc = run_skinny<T>(c, plan, partial, counters, num_sms, s);
+    const int rc = run_skinny<T>(c, plan, partial, counters, epoch, num_sms, s);
     if (rc == COMPAR_OK && g.prof) g.prof->end(ev, s, COMPAR_V_SIMT);
     return rc;
   }
@@ -796,7 +809,7 @@ int launch_simt_scratch(const GemmCall& c, float* scratch, size_t scratch_bytes,
         plan.splits > 1 ? static_cast<size_t>(plan.splits) * c.m * c.n * sizeof(float) : 0;
     if (need_bytes) *need_bytes = need;
     if (need > scratch_bytes) return COMPAR_ERR_INVALID;
-    return run_skinny<float>(c, plan, scratch, nullptr, num_sms, s);
+    return run_skinny<float>(c, plan, scratch, nullptr, 0u, num_sms, s);
   }
   if (plan.bm == 32)
     return run_simt_scratch<32, 128, 32, 4, 8>(c, scratch, scratch_bytes, num_sms, s, need_bytes);

@@ -1,5 +1,6 @@
-// Learned cost model kernels: a 3-layer perceptron (8 -> 64 -> 64 -> 18,
-// ReLU) that predicts, for each of the 9 variant ids, log2 of the run time and
+// Learned cost model kernels: a 3-layer perceptron (8 -> 64 -> 64 ->
+// 2 * COMPAR_V_COUNT, ReLU) that predicts, for each of the COMPAR_V_COUNT
+// variant ids, log2 of the run time and
 // log10 of the relative error of a call from the call's context.  The paper's
 // runtime selects variants with performance models it calls machine-learning
 // models and expects more training to select better (Sec. 3.2, Sec. 5).
@@ -13,7 +14,8 @@
 //                        gradients instead of updating (used for gradient checks).
 //
 // Parameter layout per member (floats): W1[64][8] b1[64] W2[64][64] b2[64]
-// W3[18][64] b3[18] — weights stored (out, in), row-major.
+// W3[2 * COMPAR_V_COUNT][64] b3[2 * COMPAR_V_COUNT] — weights stored (out, in),
+// row-major.
 #include <cuda_runtime.h>
 
 #include <cstdint>

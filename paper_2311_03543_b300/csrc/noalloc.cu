@@ -27,50 +27,53 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
 
-// Per-device set-up: the device address of the array (the host-side name of
-// a __device__ array is not a device address) and the SM count.
+// Per-device set-up, once: the device check and the SM count.  The array's
+// device address is looked up on every call instead (the host-side name of a
+// __device__ array is not a device address): the lookup allocates nothing,
+// and a context torn down and made again (cudaDeviceReset) may load the
+// module, and with it the array, at another address.
 constexpr int kMaxDevices = 64;
 struct DeviceSetup {
   bool done = false;
-  float* scratch = nullptr;
   int num_sms = 0;
 };
 std::mutex g_setup_mu;
 DeviceSetup g_setup[kMaxDevices];
 
-int setup_current_device(DeviceSetup** out) {
+int setup_current_device(int* num_sms, float** scratch) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     compar::set_last_error_text("compar_gemm_simt_noalloc: no current CUDA device");
     return COMPAR_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  DeviceSetup& d = g_setup[dev];
-  if (!d.done) {
-    int major = 0, minor = 0, sms = 0;
-    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      compar::set_last_error_text("compar_gemm_simt_noalloc: cannot query the device");
-      return COMPAR_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    DeviceSetup& d = g_setup[dev];
+    if (!d.done) {
+      int major = 0, minor = 0, sms = 0;
+      if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        compar::set_last_error_text("compar_gemm_simt_noalloc: cannot query the device");
+        return COMPAR_ERR_CUDA;
+      }
+      if (major != 10 || minor != 3) {
+        compar::set_last_error_text("compar_gemm_simt_noalloc: built for sm_103 (B300) only");
+        return COMPAR_ERR_UNSUPPORTED;
+      }
+      d.num_sms = sms;
+      d.done = true;
     }
-    if (major != 10 || minor != 3) {
-      compar::set_last_error_text("compar_gemm_simt_noalloc: built for sm_103 (B300) only");
-      return COMPAR_ERR_UNSUPPORTED;
-    }
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      compar::set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__,
-                                  __LINE__);
-      return COMPAR_ERR_CUDA;
-    }
-    d.scratch = static_cast<float*>(p);
-    d.num_sms = sms;
-    d.done = true;
+    *num_sms = d.num_sms;
   }
-  *out = &d;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    compar::set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    return COMPAR_ERR_CUDA;
+  }
+  *scratch = static_cast<float*>(p);
   return COMPAR_OK;
 }
 
@@ -84,8 +87,9 @@ extern "C" int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float a
   if ((m + 31) / 32 > 65535) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && C == nullptr) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && k > 0 && (A == nullptr || B == nullptr)) return COMPAR_ERR_INVALID;
-  DeviceSetup* d = nullptr;
-  int rc = setup_current_device(&d);
+  int num_sms = 0;
+  float* scratch = nullptr;
+  int rc = setup_current_device(&num_sms, &scratch);
   if (rc != COMPAR_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (m == 0 || n == 0) return COMPAR_OK;
@@ -104,7 +108,7 @@ extern "C" int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float a
   c.alpha = alpha;
   c.beta = beta;
   size_t need = 0;
-  rc = compar::launch_simt_scratch(c, d->scratch, kNoAllocScratchBytes, d->num_sms, s, &need);
+  rc = compar::launch_simt_scratch(c, scratch, kNoAllocScratchBytes, num_sms, s, &need);
   if (rc == COMPAR_ERR_INVALID) {
     char buf[256];
     snprintf(buf, sizeof(buf),

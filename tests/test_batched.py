@@ -252,6 +252,6 @@ def test_config4_batch_sampled(ctx):
         A, B, C = keep[i]
         A64 = A.float().cpu().numpy().astype(np.float64)
         B64 = B.float().cpu().numpy().astype(np.float64)
-        rows = W.sample_rows(m, 16, seed=i)
+        rows = W.tile_rows(m, seed=i)
         ref = oracle.gemm_rows(A64, B64, rows)
         assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5, (m, n, k, dt)

@@ -57,10 +57,12 @@ SHAPES = [(1, 1, 1), (3, 5, 7), (16, 16, 16), (33, 65, 17), (127, 129, 130),
 @pytest.mark.parametrize("v", [0, 1, 5, 7, 8])
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_fp32_accurate_variants(ctx, v, m, n, k):
+    from gpu_util import assert_elementwise, elem_bound
     A = W.uniform(m, k, seed=100 + m); B = W.uniform(k, n, seed=200 + n)
     got = _run(ctx, v, A, B)
     ref = oracle.gemm(A, B)
     assert N.rel_frobenius(got, ref) <= (TOL_SPLIT6 if v in (7, 8) else TOL_F32)
+    assert_elementwise(got, ref, oracle.gemm(np.abs(A), np.abs(B)), elem_bound(v, k))
 
 
 def test_config1_naive_then_simt(ctx):
@@ -75,19 +77,26 @@ def test_config1_naive_then_simt(ctx):
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
                                    (256, 512, 1024)])
 def test_tf32_total_error(ctx, m, n, k):
+    from gpu_util import assert_elementwise, elem_bound
     A = W.uniform(m, k, seed=3 + m); B = W.uniform(k, n, seed=4 + n)
-    err = N.rel_frobenius(_run(ctx, 2, A, B), oracle.gemm(A, B))
+    got = _run(ctx, 2, A, B)
+    err = N.rel_frobenius(got, oracle.gemm(A, B))
     assert err <= 2e-3
+    absp = oracle.gemm(np.abs(A), np.abs(B))
+    assert_elementwise(got, oracle.gemm(A, B), absp, elem_bound(2, k))
 
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
                                    (256, 512, 1024)])
 def test_bf16_on_f32_inputs(ctx, m, n, k):
+    from gpu_util import assert_elementwise, elem_bound
     A = W.uniform(m, k, seed=5 + m); B = W.uniform(k, n, seed=6 + n)
     got = _run(ctx, 3, A, B)
-    exact_inputs = oracle.gemm(N.bf16_round(A), N.bf16_round(B))
+    Ar, Br = N.bf16_round(A), N.bf16_round(B)
+    exact_inputs = oracle.gemm(Ar, Br)
     assert N.rel_frobenius(got, exact_inputs) <= TOL_F32
     assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 2.0 ** -7
+    assert_elementwise(got, exact_inputs, oracle.gemm(np.abs(Ar), np.abs(Br)), elem_bound(3, k))
 
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 8), (17, 40, 24), (128, 256, 64), (200, 300, 336),
@@ -117,12 +126,16 @@ def test_fp8_native_inputs_with_scales(ctx, m, n, k):
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 40, 9), (128, 256, 64), (200, 300, 333),
                                    (256, 512, 1024)])
 def test_fp8_on_f32_inputs(ctx, m, n, k):
+    from gpu_util import assert_elementwise, elem_bound
     A = W.normal(m, k, seed=11 + m); B = W.normal(k, n, seed=12 + n)
     got = _run(ctx, 4, A, B)
     qa, sa = N.fp8_quantize(A); qb, sb = N.fp8_quantize(B)
-    exact_inputs = oracle.gemm(N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)) / (float(sa) * float(sb))
+    Aq, Bq = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)
+    exact_inputs = oracle.gemm(Aq, Bq) / (float(sa) * float(sb))
     assert N.rel_frobenius(got, exact_inputs) <= TOL_F32
     assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 0.1
+    absp = oracle.gemm(np.abs(Aq), np.abs(Bq)) / (float(sa) * float(sb))
+    assert_elementwise(got, exact_inputs, absp, elem_bound(4, k))
 
 
 def test_split3_matches_its_three_products(ctx):
@@ -274,9 +287,12 @@ def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     got = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
     again = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
     assert np.array_equal(got, again)
-    rows = W.sample_rows(m, 96, seed=64)
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    rows = W.tile_rows(m, seed=64)
     ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.25, C0=C0)
     assert N.rel_frobenius(got[rows], ref) <= (TOL_F32 if v in (5, 9) else TOL_SPLIT6)
+    scale = 1.5 * abs_product_rows(A, B, rows) + 0.25 * np.abs(C0[rows])
+    assert_elementwise(got[rows], ref, scale, elem_bound(v, k))
 
 
 @pytest.mark.parametrize("v,tol,m,n,k", [(2, 2e-3, 2500, 2000, 4096), (2, 2e-3, 1536, 2048, 8192),
@@ -293,9 +309,16 @@ def test_stream_k_plain_variants(ctx, v, tol, m, n, k):
     got = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
     again = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
     assert np.array_equal(got, again)
-    rows = W.sample_rows(m, 96, seed=84)
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    rows = W.tile_rows(m, seed=84)
     ref = oracle.gemm_rows(A, B, rows, alpha=1.25, beta=0.5, C0=C0)
     assert N.rel_frobenius(got[rows], ref) <= tol
+    # against the float32 values: the format's rounding of each operand
+    # (bf16 2^-9, e4m3 2^-4 plus the subnormal step 2^-10 / s, below
+    # 2^-10 of amax here) on top of the accumulation bound
+    fmt = {2: 0.0, 3: 2.0 ** -8 + 2.0 ** -18, 4: 2.0 ** -3 + 2.0 ** -6}[v]
+    scale = 1.25 * abs_product_rows(A, B, rows) + 0.5 * np.abs(C0[rows])
+    assert_elementwise(got[rows], ref, scale, fmt + elem_bound(v, k))
 
 
 def test_k_zero_scales_c(ctx):
@@ -336,12 +359,17 @@ def test_forced_unsupported_variant_is_refused(ctx):
                                      (7, 4096, 4096, 64), (8, 2048, 2048, 2048),
                                      (8, 16, 4096, 4096)])
 def test_sweep_shapes_sampled_rows(ctx, v, m, n, k):
-    """Full-size sweep shapes, checked on 32 seeded rows against the oracle."""
+    """Full-size sweep shapes, checked against the oracle on the first and
+    last row of every 128-row tile plus one seeded row inside it (every
+    output tile holds a checked row), relative Frobenius and element by
+    element."""
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
     A = W.uniform(m, k, seed=20); B = W.uniform(k, n, seed=21)
     got = _run(ctx, v, A, B)
-    rows = W.sample_rows(m, 32, seed=22)
+    rows = W.tile_rows(m, seed=22)
     ref = oracle.gemm_rows(A, B, rows)
     assert N.rel_frobenius(got[rows], ref) <= TOL_F32
+    assert_elementwise(got[rows], ref, abs_product_rows(A, B, rows), elem_bound(v, k))
     assert np.all(np.isfinite(got))
 
 
@@ -362,9 +390,12 @@ def test_simt_skinny_plan_matches_oracle_and_is_deterministic(ctx, m, n, k):
     got = _run(ctx, cp.V_SIMT, A, B, alpha=1.5, beta=-0.5, C0=C0)
     again = _run(ctx, cp.V_SIMT, A, B, alpha=1.5, beta=-0.5, C0=C0)
     assert np.array_equal(got, again)
-    rows = W.sample_rows(m, 8, seed=74) if m * n * k > 2e9 else np.arange(m)
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    rows = np.arange(m)
     ref = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.5, C0=C0)
     assert N.rel_frobenius(got[rows], ref) <= TOL_F32
+    scale = 1.5 * abs_product_rows(A, B, rows) + 0.5 * np.abs(C0)
+    assert_elementwise(got, ref, scale, elem_bound(1, k))
 
 
 @pytest.mark.parametrize("m,n,k", [(16, 4096, 1000), (3, 1024, 333)])
@@ -410,3 +441,57 @@ def test_simt_skinny_plan_unaligned_c_and_b(ctx):
             ctx.set_scalars(1.0, 0.0)
         assert ctx.check_device_error() == cp.OK
         assert N.rel_frobenius(host(dC), ref) <= TOL_F32
+
+
+def test_simt_skinny_counters_carry_nothing_between_shapes(ctx):
+    """The skinny plan's last-cluster slab sum counts arrivals in one word per
+    (row group, column block) of the context's workspace.  Shapes of
+    different grids and cluster counts run back to back on one context (the
+    later grids cover the earlier ones' words), each checked against the
+    oracle: a count left over from one call would make a later call sum
+    unfinished slabs."""
+    import paper_2311_03543_b300 as cp
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    seq = [(16, 4096, 4096), (64, 15360, 2048), (48, 4096, 2048), (16, 4096, 4096),
+           (8, 227328, 1000), (64, 15360, 2048)]
+    for i, (m, n, k) in enumerate(seq):
+        plan = cp.Context.simt_plan(m, n, k)
+        assert plan["skinny"] == 1 and 1 < plan["splits"] <= 8
+        A = W.uniform(m, k, seed=300 + i); B = W.uniform(k, n, seed=400 + i)
+        got = _run(ctx, cp.V_SIMT, A, B)
+        rows = np.arange(m)
+        ref = oracle.gemm_rows(A, B, rows)
+        assert N.rel_frobenius(got, ref) <= TOL_F32, (m, n, k)
+        assert_elementwise(got, ref, abs_product_rows(A, B, rows), elem_bound(1, k))
+
+
+def test_simt_skinny_counters_recover_after_overlapping_calls(ctx):
+    """Calls on one context must be ordered on the GPU; two that overlap (two
+    streams, no ordering) give undefined results for themselves.  What must
+    not happen is that their mixed-up arrival counts spoil later, ordered
+    calls: every launch counts under its own epoch.  (The skinny kernel has
+    no waits, so overlapping launches cannot block each other.)"""
+    import torch
+    import paper_2311_03543_b300 as cp
+    m, n, k = 16, 4096, 4096
+    A = W.uniform(m, k, seed=501); B = W.uniform(k, n, seed=502)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C1 = torch.empty((m, n), device="cuda"); C2 = torch.empty((m, n), device="cuda")
+    ctx.force_variant(cp.V_SIMT)
+    try:
+        ctx.gemm(dA, dB, C1)                      # sizes the workspace first
+        torch.cuda.synchronize()
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        for _ in range(8):
+            with torch.cuda.stream(s1):
+                ctx.gemm(dA, dB, C1)
+            with torch.cuda.stream(s2):
+                ctx.gemm(dA, dB, C2)
+        torch.cuda.synchronize()
+        C3 = torch.full((m, n), float("nan"), device="cuda")
+        ctx.gemm(dA, dB, C3)
+        torch.cuda.synchronize()
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
+    assert N.rel_frobenius(C3.cpu().numpy(), oracle.gemm(A, B)) <= TOL_F32

@@ -2,9 +2,10 @@
 
 It exists for callers that cannot allocate device memory where they need a
 GEMM (a host framework that owns all device memory, a latency-critical path,
-a plug-in without an allocator).  It must give the same result as the
-regular entry point running the same SIMT variant, call after call, although
-every call reuses one fixed scratch array inside the library.  This file is
+a plug-in without an allocator).  It must match the FP64 oracle
+within the FP32 tolerance and give the same result as the regular entry
+point running the same SIMT variant, call after call, although every call
+reuses one fixed scratch array inside the library.  This file is
 collected last so that a failure here leaves every other test already run.
 """
 import ctypes
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 from oracle import numerics as N
 
@@ -62,7 +64,11 @@ def test_noalloc_matches_regular_entry_point_twice(m, n, k):
             assert _noalloc(A, B, C, alpha=1.5, beta=-0.5) == cp.OK
             ref = _regular(ctx, A, B, alpha=1.5, beta=-0.5, C0=C0)
             torch.cuda.synchronize()
-            assert N.rel_frobenius(C.cpu().numpy(), ref.cpu().numpy()) <= TOL
+            got = C.cpu().numpy()
+            assert N.rel_frobenius(got, ref.cpu().numpy()) <= TOL
+            exact = oracle.gemm(A.cpu().numpy(), B.cpu().numpy(), alpha=1.5, beta=-0.5,
+                                C0=C0.cpu().numpy())
+            assert N.rel_frobenius(got, exact) <= TOL
 
 
 def test_noalloc_refuses_a_plan_beyond_its_scratch_limit():

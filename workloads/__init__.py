@@ -179,3 +179,19 @@ def sample_rows(m, count, seed):
     """Sorted distinct row indices for checking large products row by row."""
     count = min(count, m)
     return np.sort(rng(seed).choice(m, size=count, replace=False)).astype(np.int64)
+
+
+def tile_rows(m, seed, tile=128, inner=1):
+    """Sorted distinct row indices that reach every block of `tile` rows:
+    each block's first and last row (the last block may be ragged) plus
+    `inner` seeded rows inside it.  A fault confined to one row tile of an
+    output (one CTA's work, one lane quarter of it) then meets a checked
+    row."""
+    g = rng(seed)
+    rows = set()
+    for r0 in range(0, m, tile):
+        r1 = min(m, r0 + tile) - 1
+        rows.update((r0, r1))
+        if r1 - r0 > 1 and inner:
+            rows.update(int(x) for x in g.integers(r0 + 1, r1, size=inner))
+    return np.array(sorted(rows), dtype=np.int64)
