@@ -539,6 +539,24 @@ int compar_selftest_timeout(compar_ctx_t ctx, void* stream);
 int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms,
                    int64_t* out);
 
+/* The same plan for the CTA-pair kernels (no counterpart in the paper; a
+ * B300 kernel design): a pair of CTAs on one TPC computes a 256 x 256 tile
+ * with tcgen05 pair MMAs (cta_group::2), each CTA holding half of A's rows
+ * and half of B's columns in its shared memory.  `num_pairs` pairs run at
+ * once; out[] as compar_tc_plan, with tiles of 256 x 256, "CTAs" counting
+ * pairs, and K never split (out[2] = 1).  Variants TF32, BF16, FP8 and
+ * SPLIT3; COMPAR_ERR_INVALID for the others or sizes < 1. */
+int compar_tc_pair_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_pairs,
+                        int64_t* out);
+
+/* When the tensor-core variants TF32, BF16, FP8 and SPLIT3 run on CTA
+ * pairs: mode -1 (default) when the single-CTA plan has a full wave of
+ * 128 x 256 tiles or more, 0 never, 1 always.  Results agree with the
+ * single-CTA kernels within the variant's tolerance (the tile and stream-K
+ * decomposition, and with it the rounding, differ).  Returns COMPAR_OK or
+ * COMPAR_ERR_INVALID. */
+int compar_set_tc_pairs(compar_ctx_t ctx, int mode);
+
 /* Launch plan of the SIMT variant (COMPAR_V_SIMT) for an m x n x k call
  * with inputs of `dtype`, B's row stride `ldb` (elements) and a 16-byte
  * aligned B, on a GPU with `num_sms` SMs, without a device: out[0] 1 for the

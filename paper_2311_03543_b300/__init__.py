@@ -112,6 +112,8 @@ SIGNATURES = {
                                      ctypes.POINTER(_i)]),
     "compar_set_batched_config": (_i, [_vp, _i]),
     "compar_tc_plan": (_i, [_i, _i64, _i64, _i64, _i, ctypes.POINTER(_i64)]),
+    "compar_tc_pair_plan": (_i, [_i, _i64, _i64, _i64, _i, ctypes.POINTER(_i64)]),
+    "compar_set_tc_pairs": (_i, [_vp, _i]),
     "compar_simt_plan": (_i, [_i64, _i64, _i64, _i, _i64, _i, ctypes.POINTER(_i64)]),
     "compar_mlp_param_count": (_i, []),
     "compar_mlp_forward": (_i, [_vp, _fp, _i, _fp, _i, _fp]),
@@ -375,13 +377,18 @@ class Context:
                                            _stream_handle(stream)), "compar_gemm_batched")
 
     @staticmethod
-    def tc_plan(variant, m, n, k, num_sms=148):
+    def tc_plan(variant, m, n, k, num_sms=148, pairs=None):
         """Launch plan of a tensor-core variant (no device needed): dict of
         num_kb, tiles, splits, kb_per_split, sk_tile0, sk_cpt, sk_q, sk_ctas,
-        sk_chunk_kb."""
+        sk_chunk_kb.  With `pairs` (a count of CTA pairs), the plan of the
+        CTA-pair kernel: 256 x 256 tiles, "CTAs" counting pairs."""
         out = (_i64 * 9)()
-        _status(compar_tc_plan(int(variant), int(m), int(n), int(k), int(num_sms), out),
-                "tc_plan")
+        if pairs is not None:
+            _status(compar_tc_pair_plan(int(variant), int(m), int(n), int(k), int(pairs), out),
+                    "tc_pair_plan")
+        else:
+            _status(compar_tc_plan(int(variant), int(m), int(n), int(k), int(num_sms), out),
+                    "tc_plan")
         keys = ("num_kb", "tiles", "splits", "kb_per_split", "sk_tile0", "sk_cpt", "sk_q",
                 "sk_ctas", "sk_chunk_kb")
         return dict(zip(keys, (int(x) for x in out)))
@@ -472,6 +479,10 @@ class Context:
 
     def set_wait_budget(self, ns):
         return _status(compar_set_wait_budget(self.handle, int(ns)), "set_wait_budget")
+
+    def set_tc_pairs(self, mode):
+        """Tensor-core variants on CTA pairs: -1 automatic, 0 never, 1 always."""
+        return _status(compar_set_tc_pairs(self.handle, int(mode)), "set_tc_pairs")
 
     # -- learned cost model ----------------------------------------------------
     def mlp_forward(self, params, X):

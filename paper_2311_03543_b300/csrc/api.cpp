@@ -753,7 +753,18 @@ int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
 }
 
 int compar_tc_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out) {
-  return tc_plan_info(variant_id, m, n, k, num_sms, out);
+  return tc_plan_info(variant_id, m, n, k, num_sms, out, false);
+}
+
+int compar_tc_pair_plan(int variant_id, int64_t m, int64_t n, int64_t k, int num_pairs,
+                        int64_t* out) {
+  return tc_plan_info(variant_id, m, n, k, num_pairs, out, true);
+}
+
+int compar_set_tc_pairs(compar_ctx_t ctx, int mode) {
+  if (!ctx || mode < -1 || mode > 1) return COMPAR_ERR_INVALID;
+  ctx->guard.tc_pair = mode;
+  return COMPAR_OK;
 }
 
 int compar_simt_plan(int64_t m, int64_t n, int64_t k, compar_dtype_t dtype, int64_t ldb,

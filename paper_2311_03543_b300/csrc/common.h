@@ -96,6 +96,8 @@ struct DeviceGuard {  // device error word + wait budget handed to kernels
   int* err_word = nullptr;
   unsigned long long budget_ns = 2000000000ull;
   KernelProfiler* prof = nullptr;
+  // tensor-core variants on CTA pairs: -1 automatic, 0 never, 1 always
+  int tc_pair = -1;
 };
 
 int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
@@ -129,7 +131,8 @@ void set_last_error_text(const std::string& text);
 int launch_tc(int variant, const GemmCall& c, Workspace& ws, const DeviceGuard& g,
               int num_sms, cudaStream_t s);
 bool tc_supported(int variant, const GemmCall& c);
-int tc_plan_info(int variant, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out);
+int tc_plan_info(int variant, int64_t m, int64_t n, int64_t k, int slots, int64_t* out,
+                 bool pair);
 
 int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s);
 

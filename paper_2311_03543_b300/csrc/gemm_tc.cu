@@ -35,9 +35,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "common.h"
 #include "epilogue.cuh"
@@ -115,12 +118,16 @@ struct Traits<COMPAR_V_SPLIT6> {
   static constexpr bool b_mn = false, small_first = true, fused = false;
 };
 
-template <int V>
+// kPair: the tile is computed by a CTA pair (cta_group::2): 2 kBM rows x BN,
+// each CTA holding its kBM rows of A and BN / 2 rows (columns) of B in its
+// shared memory and its kBM rows of the accumulator in its tensor memory.
+template <int V, bool kPair = false>
 struct Layout {
   using T = Traits<V>;
   static constexpr int BN = T::BN;
+  static constexpr int kBRows = kPair ? BN / 2 : BN;  // rows of B this CTA loads
   static constexpr int kABytes = kBM * T::row;
-  static constexpr int kBBytes = BN * T::row;
+  static constexpr int kBBytes = kBRows * T::row;
   static constexpr int kStageBytes = T::pieces * (kABytes + kBBytes);
   static constexpr int kMaxSmem = 232448;  // 227 KB opt-in per CTA
   static constexpr int kBarBytes = 256;
@@ -133,6 +140,10 @@ struct Layout {
   // 128-byte rows, one per 64 columns of the tile
   static constexpr int kMnBox = 64 * 2 * kElemsPerStage;
   static_assert(kMnBox % 1024 == 0, "MN-major boxes hold whole 8-row swizzle groups");
+  static constexpr int kMmaM = kPair ? 2 * kBM : kBM;  // rows of one MMA
+  // arrivals that free an accumulator: every epilogue thread, or in a pair
+  // one elected lane per epilogue warp of both CTAs (on the even CTA's barrier)
+  static constexpr int kTemptyCount = kPair ? 2 * T::epi : 32 * T::epi;
   static constexpr int kThreads = 64 + 32 * T::epi;
   static constexpr int kEpiThreads = 32 * T::epi;
   static constexpr int kEpiCols = BN * 4 / T::epi;  // columns one epilogue warp handles
@@ -157,8 +168,12 @@ struct TcArgs {
   // [b sk_q / sk_ctas, (b+1) sk_q / sk_ctas), at most two pieces of tiles.
   int dp_units;
   int sk_tile0, sk_cpt, sk_q, sk_ctas;
-  float* sk_slab;               // [sk_ctas][2][kBM * BN] published pieces
-  unsigned int* sk_count;       // [tail tiles] arrivals, zero at launch
+  float* sk_slab;               // [sk_ctas * pair][2][kBM * BN] published pieces
+  unsigned int* sk_count;       // [tail tiles * pair] arrivals, zero at launch
+  // 1, or 2 when CTA pairs compute the tiles: a "CTA" of the work list
+  // (blockIdx.x / pair) is then a pair, a tile is 2 kBM x BN, and each CTA
+  // of the pair publishes and counts its own kBM rows of a stream-K tile.
+  int pair;
   float alpha, beta;
   const float* dequant_a;  // optional device factors (fp8 of float32 inputs)
   const float* dequant_b;
@@ -203,7 +218,7 @@ constexpr int kPlainSkChunk = 2;
 template <int kChunkKB>
 __device__ __forceinline__ bool get_item(const TcArgs& p, int i, WorkItem& it) {
   constexpr int kSk = kChunkKB > 0 ? kChunkKB : kPlainSkChunk;
-  const int b = blockIdx.x, grid = gridDim.x;
+  const int b = blockIdx.x / p.pair, grid = gridDim.x / p.pair;
   const int u = b + i * grid;
   if (u < p.dp_units) {
     it.tile = u / p.splits;
@@ -352,14 +367,19 @@ __device__ __forceinline__ bool sk_count_and_sum(const TcArgs& p, const SkPiece&
   if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
   if (etid == 0) {
     __threadfence();
-    *last_flag = atomicAdd(p.sk_count + sp.t, 1u) == static_cast<unsigned int>(sp.nc - 1);
+    // in a CTA pair each CTA counts (and sums) its own rows of the tile
+    *last_flag = atomicAdd(p.sk_count + sp.t * p.pair + static_cast<int>(blockIdx.x) % p.pair,
+                           1u) == static_cast<unsigned int>(sp.nc - 1);
   }
   dev::mbar_arrive(epi_bar);
   if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
   if (!*last_flag) return true;
   __threadfence();
-  // the pieces in contributor order, this CTA's own from its slab too
+  // the pieces in contributor order, this CTA's own from its slab too; the
+  // slabs of contributor b (a pair when p.pair == 2) are those of its CTA
+  // b * pair + rank
   const int k0 = sk_start(p, sp.b0) < sp.first ? 1 : 0;  // b0's piece of this tile
+  const int rank = static_cast<int>(blockIdx.x) % p.pair;
   if (row_q < p.M && col_s < p.N) {
     // G fragments at a time (8 G independent loads in flight per
     // contributor), so a tile costs NF / G * nc L2 round trips; G = 1 when
@@ -370,11 +390,11 @@ __device__ __forceinline__ bool sk_count_and_sum(const TcArgs& p, const SkPiece&
     for (int f0 = 0; f0 < NF; f0 += G) {
       const int64_t base = f0 * 8 * kEpiThreads + etid;
       float4 acc[8 * G];
-      const float4* s0 = sk_slab<BN>(p, sp.b0, k0) + base;
+      const float4* s0 = sk_slab<BN>(p, sp.b0 * p.pair + rank, k0) + base;
 #pragma unroll
       for (int e = 0; e < 8 * G; ++e) acc[e] = __ldcg(s0 + e * kEpiThreads);
       for (int jj = 1; jj < sp.nc; ++jj) {
-        const float4* sj = sk_slab<BN>(p, sp.b0 + jj, 0) + base;
+        const float4* sj = sk_slab<BN>(p, (sp.b0 + jj) * p.pair + rank, 0) + base;
         float4 c[8 * G];
 #pragma unroll
         for (int e = 0; e < 8 * G; ++e) c[e] = __ldcg(sj + e * kEpiThreads);
@@ -439,15 +459,22 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
                                                vec_out);
 }
 
-template <int V>
-__global__ void __launch_bounds__(Layout<V>::kThreads, 1)
+// kPair: launched in clusters of 2 CTAs (a CTA pair on one TPC).  Both CTAs
+// load their halves (A rows, B rows or columns) and run the epilogue on
+// their rows; the even CTA alone issues the pair's MMAs (cta_group::2).  Its
+// `full` barriers count both CTAs' bytes; its commits release the stage and
+// hand over the accumulator in both CTAs (multicast); both CTAs' epilogue
+// warps free an accumulator on the even CTA's `tempty`.
+template <int V, bool kPair>
+__global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB2,
                    const __grid_constant__ CUtensorMap tmA3,
                    const __grid_constant__ CUtensorMap tmB3, const TcArgs p) {
   using T = Traits<V>;
-  using L = Layout<V>;
+  using L = Layout<V, kPair>;
+  static_assert(!(kPair && T::fused), "the fused split runs on single CTAs only");
   constexpr int P = T::pieces;
   constexpr int BN = T::BN;
   constexpr int S = L::kStages;
@@ -479,7 +506,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       dev::mbar_init(&tfull[a], 1);
-      dev::mbar_init(&tempty[a], L::kEpiThreads);
+      dev::mbar_init(&tempty[a], L::kTemptyCount);
     }
     dev::mbar_init(drain, 1);
     dev::mbar_init(epi_bar, L::kEpiThreads);
@@ -500,31 +527,56 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     }
   }
   if (warp == 1) {
-    dev::tmem_alloc(tmem_slot, L::kTmemCols);
-    dev::tmem_relinquish();
+    if constexpr (kPair) {
+      dev::tmem_alloc_pair(tmem_slot, L::kTmemCols);  // with the peer's warp 1
+      dev::tmem_relinquish_pair();
+    } else {
+      dev::tmem_alloc(tmem_slot, L::kTmemCols);
+      dev::tmem_relinquish();
+    }
   }
   dev::tc_fence_before();
   __syncthreads();
+  // a pair's barriers are all initialised before either CTA signals the other's
+  if constexpr (kPair) dev::cluster_sync();
   dev::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
+  const uint32_t rank = kPair ? dev::cluster_ctarank() : 0u;
+  dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
+  if constexpr (kPair)
+    w.peer_abort = cooperative_groups::this_cluster().map_shared_rank(
+        const_cast<int*>(abort_flag), rank ^ 1u);
+  // the even CTA's barriers as shared::cluster addresses (pairs only)
+  const uint32_t full_lead = kPair ? dev::mapa(dev::smem_u32(full), 0) : 0u;
+  const uint32_t tempty_lead = kPair ? dev::mapa(dev::smem_u32(tempty), 0) : 0u;
+  // first row of this CTA's kBM rows of tile row mb
+  auto tile_row0 = [&](int mb) { return (kPair ? 2 * mb + static_cast<int>(rank) : mb) * kBM; };
   WorkItem it;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
     uint32_t stage = 0, phase = 0;
     uint32_t issued = 0, issued_parity = 0;  // per-stage bit masks
-    constexpr uint32_t kTx = static_cast<uint32_t>(L::kStageBytes);
+    // the even CTA's full barrier counts both CTAs' bytes of a pair's stage
+    constexpr uint32_t kTx = static_cast<uint32_t>(L::kStageBytes) * (kPair ? 2 : 1);
     bool ok = true;
     for (int i = 0; ok && get_item<kChunkKB>(p, i, it); ++i) {
       int mb, nb;
       tile_coords(it.tile, p.tiles_m, p.tiles_n, mb, nb);
+      const int a_row = tile_row0(mb);
+      const int b_row = nb * BN + static_cast<int>(rank) * L::kBRows;  // this CTA's B half
       for (int kb = it.kb_begin; kb < it.kb_end; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
           ok = false;
           break;
         }
-        dev::mbar_arrive_expect_tx(&full[stage], kTx);
+        if (rank == 0) dev::mbar_arrive_expect_tx(&full[stage], kTx);
+        auto load = [&](void* dst, const CUtensorMap* map, int cx, int cy) {
+          if constexpr (kPair)
+            dev::tma_load_2d_pair(dst, map, full_lead + 8u * stage, cx, cy);
+          else
+            dev::tma_load_2d(dst, map, &full[stage], cx, cy);
+        };
         const int x = kb * L::kElemsPerStage;
         uint8_t* a_dst = sA + (stage * P) * L::kABytes;
         uint8_t* b_dst = sB + (stage * P) * L::kBBytes;
@@ -539,26 +591,21 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
               dev::tma_load_2d(b_dst + 2048 * (4 * ng + kg), &tmB, &full[stage],
                                nb * BN + 64 * ng, x + 8 * kg);
         } else {
-        dev::tma_load_2d(a_dst, &tmA, &full[stage], x, mb * kBM);
-        if constexpr (P >= 2) dev::tma_load_2d(a_dst + L::kABytes, &tmA2, &full[stage], x, mb * kBM);
-        if constexpr (P == 3)
-          dev::tma_load_2d(a_dst + 2 * L::kABytes, &tmA3, &full[stage], x, mb * kBM);
+        load(a_dst, &tmA, x, a_row);
+        if constexpr (P >= 2) load(a_dst + L::kABytes, &tmA2, x, a_row);
+        if constexpr (P == 3) load(a_dst + 2 * L::kABytes, &tmA3, x, a_row);
         if constexpr (T::b_mn) {
 #pragma unroll
-          for (int h = 0; h < BN / 64; ++h) {
-            const int n0 = nb * BN + h * 64;
-            dev::tma_load_2d(b_dst + h * L::kMnBox, &tmB, &full[stage], n0, x);
-            if constexpr (P >= 2)
-              dev::tma_load_2d(b_dst + L::kBBytes + h * L::kMnBox, &tmB2, &full[stage], n0, x);
-            if constexpr (P == 3)
-              dev::tma_load_2d(b_dst + 2 * L::kBBytes + h * L::kMnBox, &tmB3, &full[stage], n0,
-                               x);
+          for (int h = 0; h < L::kBRows / 64; ++h) {
+            const int n0 = b_row + h * 64;
+            load(b_dst + h * L::kMnBox, &tmB, n0, x);
+            if constexpr (P >= 2) load(b_dst + L::kBBytes + h * L::kMnBox, &tmB2, n0, x);
+            if constexpr (P == 3) load(b_dst + 2 * L::kBBytes + h * L::kMnBox, &tmB3, n0, x);
           }
         } else {
-          dev::tma_load_2d(b_dst, &tmB, &full[stage], x, nb * BN);
-          if constexpr (P >= 2) dev::tma_load_2d(b_dst + L::kBBytes, &tmB2, &full[stage], x, nb * BN);
-          if constexpr (P == 3)
-            dev::tma_load_2d(b_dst + 2 * L::kBBytes, &tmB3, &full[stage], x, nb * BN);
+          load(b_dst, &tmB, x, b_row);
+          if constexpr (P >= 2) load(b_dst + L::kBBytes, &tmB2, x, b_row);
+          if constexpr (P == 3) load(b_dst + 2 * L::kBBytes, &tmB3, x, b_row);
         }
         }
         issued |= 1u << stage;
@@ -570,14 +617,39 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
       }
     }
     if (!ok) {
-      // Let every copy this thread started land before the CTA exits.
-      for (int s = 0; s < S; ++s)
+      // Let every copy this thread started land before the CTA exits (a
+      // pair's copies are all counted on the even CTA's barriers).
+      for (int s = 0; rank == 0 && s < S; ++s)
         if (issued & (1u << s)) drain_wait(&full[s], (issued_parity >> s) & 1, p.budget_ns);
+    } else if constexpr (kPair) {
+      // The even CTA's commits release this CTA's stages from afar: wait
+      // until every stage filled has been released, so that no arrival is
+      // still on its way when the CTA exits.
+      for (int s = 0; s < S; ++s) {
+        if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) break;
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == 1 && lane == 0 && rank == 0) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t idesc = T::b_mn ? dev::make_idesc_bmn(T::fmt, T::fmt, kBM, BN)
-                                       : dev::make_idesc(T::fmt, T::fmt, kBM, BN);
+    constexpr uint32_t idesc = T::b_mn ? dev::make_idesc_bmn(T::fmt, T::fmt, L::kMmaM, BN)
+                                       : dev::make_idesc(T::fmt, T::fmt, L::kMmaM, BN);
+    auto mma_op = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+      if constexpr (kPair)
+        dev::mma_pair<T::kind>(d, a, b, idesc, accumulate);
+      else
+        dev::mma<T::kind>(d, a, b, idesc, accumulate);
+    };
+    // release / hand over in this CTA, or in both CTAs of a pair
+    auto commit = [&](uint64_t* bar) {
+      if constexpr (kPair)
+        dev::mma_commit_pair_mc(bar, 0x3);
+      else
+        dev::mma_commit(bar);
+    };
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;  // accumulator-buffer uses (one per K chunk)
     bool ok = true;
@@ -628,51 +700,54 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
               const uint64_t a_0 = a_desc(0, kk), a_1 = a_desc(1, kk), a_2 = a_desc(2, kk);
               const uint64_t b_0 = b_desc(0, kk), b_1 = b_desc(1, kk), b_2 = b_desc(2, kk);
-              dev::mma<T::kind>(d_tmem, a_0, b_1, idesc, first);
-              dev::mma<T::kind>(d_tmem, a_1, b_0, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, a_0, b_2, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, a_1, b_1, idesc, 1u);
-              dev::mma<T::kind>(d_tmem, a_2, b_0, idesc, 1u);
+              mma_op(d_tmem, a_0, b_1, first);
+              mma_op(d_tmem, a_1, b_0, 1u);
+              mma_op(d_tmem, a_0, b_2, 1u);
+              mma_op(d_tmem, a_1, b_1, 1u);
+              mma_op(d_tmem, a_2, b_0, 1u);
             }
 #pragma unroll
             for (int kk = 0; kk < T::row / 32; ++kk)
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, 1u);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(0, kk), 1u);
           }
           if constexpr (P == 2 && T::small_first) {
             // the cross products of every K step of the stage, then hi * hi
 #pragma unroll
             for (int kk = 0; kk < T::row / 32; ++kk) {
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(1, kk), idesc, first);
-              dev::mma<T::kind>(d_tmem, a_desc(1, kk), b_desc(0, kk), idesc, 1u);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(1, kk), first);
+              mma_op(d_tmem, a_desc(1, kk), b_desc(0, kk), 1u);
             }
 #pragma unroll
             for (int kk = 0; kk < T::row / 32; ++kk)
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, 1u);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(0, kk), 1u);
           }
 #pragma unroll
           for (int kk = 0; P < 3 && !T::small_first && kk < T::row / 32; ++kk) {
             const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
             if constexpr (P == 2) {
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, first);
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(1, kk), idesc, 1u);
-              dev::mma<T::kind>(d_tmem, a_desc(1, kk), b_desc(0, kk), idesc, 1u);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(0, kk), first);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(1, kk), 1u);
+              mma_op(d_tmem, a_desc(1, kk), b_desc(0, kk), 1u);
             } else {
-              dev::mma<T::kind>(d_tmem, a_desc(0, kk), b_desc(0, kk), idesc, first);
+              mma_op(d_tmem, a_desc(0, kk), b_desc(0, kk), first);
             }
           }
-          dev::mma_commit(&empty[stage]);  // stage reusable once these MMAs finish
+          commit(&empty[stage]);  // stage reusable once these MMAs finish
           if (++stage == S) {
             stage = 0;
             phase ^= 1;
           }
         }
         if (!ok) break;
-        dev::mma_commit(&tfull[acc]);  // chunk accumulator ready for the epilogue
+        commit(&tfull[acc]);  // chunk accumulator ready for the epilogue
       }
     }
     // All MMAs issued by this thread complete before TMEM is released.
-    dev::mma_commit(drain);
+    if constexpr (kPair)
+      dev::mma_commit_pair_mc(drain, 0x1);
+    else
+      dev::mma_commit(drain);
     drain_wait(drain, 0, p.budget_ns);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
@@ -697,6 +772,18 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
     const float beta = split ? 0.f : p.beta;
     uint32_t epi_uses = 0;  // completed phases of epi_bar
     const int etid = threadIdx.x - 64;
+    // this warp is done reading accumulator `acc`: every thread arrives, or
+    // in a pair one lane per warp on the even CTA's barrier (tcgen05.ld
+    // waits are warp-wide, so the warp's loads are complete)
+    auto release_acc = [&](uint32_t acc) {
+      dev::tc_fence_before();
+      if constexpr (kPair) {
+        __syncwarp();
+        if (lane == 0) dev::mbar_arrive_cluster(tempty_lead + 8u * acc);
+      } else {
+        dev::mbar_arrive(&tempty[acc]);
+      }
+    };
     if constexpr (T::fused) {
       // The epilogue warps also split the stages: each stage is split as
       // soon as TMA has landed it, and a K chunk is promoted once the split
@@ -760,14 +847,13 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) sum[f][j] += __uint_as_float(r[j]);
           }
-          dev::tc_fence_before();
-          dev::mbar_arrive(&tempty[acc]);
+          release_acc(acc);
           ++acc_iter;
         }
         if (!ok) break;
         int mb, nb;
         tile_coords(pit.tile, p.tiles_m, p.tiles_n, mb, nb);
-        const int row_q = mb * kBM + quarter * 32;
+        const int row_q = tile_row0(mb) + quarter * 32;
         const int col_s = nb * BN + cslice * EC;
         float* out = split ? p.partial + static_cast<int64_t>(pit.split) * p.M * p.N : p.C;
         if (!finish_promoted<NF, L::kEpiThreads, BN>(p, pit, sum, epi_bar, epi_uses, last_flag,
@@ -785,7 +871,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
       const int num_chunks =
           kChunkKB > 0 ? (it.kb_end - it.kb_begin + kChunkKB - 1) / kChunkKB : 1;
       float* out = split ? p.partial + static_cast<int64_t>(it.split) * p.M * p.N : p.C;
-      const int row_q = mb * kBM + quarter * 32;     // first row of this warp's quarter
+      const int row_q = tile_row0(mb) + quarter * 32;     // first row of this warp's quarter
       const int col_s = nb * BN + cslice * EC;       // first column of its slice
       auto frag_taddr = [&](uint32_t acc, int f) {
         return tmem_base + (static_cast<uint32_t>(quarter * 32 + 16 * (f & 1)) << 16) +
@@ -816,8 +902,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) sum[f][j] += __uint_as_float(r[j]);
           }
-          dev::tc_fence_before();
-          dev::mbar_arrive(&tempty[acc]);
+          release_acc(acc);
         }
         if (!ok) break;
         if (!finish_promoted<NF, L::kEpiThreads, BN>(p, it, sum, epi_bar, epi_uses, last_flag, w,
@@ -849,8 +934,7 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
                 make_float4(__uint_as_float(r[4 * j4]), __uint_as_float(r[4 * j4 + 1]),
                             __uint_as_float(r[4 * j4 + 2]), __uint_as_float(r[4 * j4 + 3]));
         }
-        dev::tc_fence_before();
-        dev::mbar_arrive(&tempty[acc]);
+        release_acc(acc);
         if (!sk_count_and_sum<NF, L::kEpiThreads, BN>(p, sp, epi_bar, epi_uses, last_flag, w,
                                                       etid, lane, out, out_ld, row_q, col_s,
                                                       alpha, beta, vec_out))
@@ -869,15 +953,20 @@ __global__ void __launch_bounds__(Layout<V>::kThreads, 1)
           store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
                           alpha, beta, vec_out, lane);
       }
-      dev::tc_fence_before();
-      dev::mbar_arrive(&tempty[acc]);
+      release_acc(acc);
     }
   }
 
   __syncthreads();
+  // a pair frees its tensor memory together, once both CTAs are done (the
+  // even CTA has drained every MMA writing into the odd CTA's columns)
+  if constexpr (kPair) dev::cluster_sync();
   if (warp == 1) {
     dev::tc_fence_after();
-    dev::tmem_dealloc(tmem_base, L::kTmemCols);
+    if constexpr (kPair)
+      dev::tmem_dealloc_pair(tmem_base, L::kTmemCols);
+    else
+      dev::tmem_dealloc(tmem_base, L::kTmemCols);
   }
 }
 
@@ -967,17 +1056,22 @@ double tile_us(int v, int64_t k) {
 // clearly more.
 constexpr double kSkMinSavingUs = 12.0;
 
-TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
+// `slots`: SMs, or CTA pairs that can run at once when `pair` (tiles are
+// then 2 kBM x 256 and K is never split: pairs serve calls with a wave of
+// tiles or more).
+TcPlan tc_plan(int v, const GemmCall& c, int slots, bool pair = false) {
+  const int num_sms = slots;
   const int kelems = v == COMPAR_V_TC_FP8 ? 128
                      : v == COMPAR_V_TC_BF16 ? 64
                      : v == COMPAR_V_SPLIT3_TF32 ? 16
                                                  : 32;
+  const int tile_m = pair ? 2 * kBM : kBM;
   TcPlan p;
   p.num_kb = static_cast<int>((c.k + kelems - 1) / kelems);
-  p.tiles = static_cast<int>(((c.m + kBM - 1) / kBM) * ((c.n + 255) / 256));
+  p.tiles = static_cast<int>(((c.m + tile_m - 1) / tile_m) * ((c.n + 255) / 256));
   p.splits = 1;
   p.kb_per = p.num_kb;
-  if (p.tiles * 2 <= num_sms && p.num_kb >= 16) {
+  if (!pair && p.tiles * 2 <= num_sms && p.num_kb >= 16) {
     const int sp = std::min(num_sms / p.tiles, p.num_kb / 8);
     if (sp > 1) {
       p.kb_per = (p.num_kb + sp - 1) / sp;
@@ -1006,23 +1100,61 @@ TcPlan tc_plan(int v, const GemmCall& c, int num_sms) {
   return p;
 }
 
-template <int V>
+// Launch configuration of the kernel: clusters of 2 for CTA pairs.
+template <int V, bool kPair>
+cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribute* attr) {
+  using L = Layout<V, kPair>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(L::kThreads);
+  cfg.dynamicSmemBytes = L::kSmemBytes;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kPair ? 2 : 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = kPair ? 1 : 0;
+  return cfg;
+}
+
+// Shared-memory opt-in of the kernel, once; for pairs also the number of
+// pairs that can be resident at once (pairs need two SMs of one TPC, so it
+// can be below half the SM count).
+template <int V, bool kPair>
+int tc_kernel_setup(int* pairs_out) {
+  using L = Layout<V, kPair>;
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  static int pairs = 0;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(tc_gemm_kernel<V, kPair>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
+    if (err == cudaSuccess && kPair) {
+      cudaLaunchAttribute attr[1];
+      cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(2, nullptr, attr);
+      err = cudaOccupancyMaxActiveClusters(&pairs, tc_gemm_kernel<V, kPair>, &cfg);
+      if (err == cudaSuccess && pairs < 1) err = cudaErrorInvalidConfiguration;
+    }
+  });
+  if (err != cudaSuccess) {
+    set_last_cuda_error(err, "tensor-core kernel set-up", __FILE__, __LINE__);
+    return COMPAR_ERR_CUDA;
+  }
+  if (pairs_out) *pairs_out = pairs;
+  return COMPAR_OK;
+}
+
+template <int V, bool kPair>
 int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
            const void* A2, const void* B2, const void* A3, const void* B3, const float* dq_a,
            const float* dq_b, const TcPlan& plan, float* partial, float* sk_slab,
-           unsigned int* sk_count, const DeviceGuard& g, int num_sms, cudaStream_t s) {
-  using L = Layout<V>;
+           unsigned int* sk_count, const DeviceGuard& g, int slots, cudaStream_t s) {
+  using L = Layout<V, kPair>;
   using T = Traits<V>;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    L::kSmemBytes);
-  });
-  if (attr_err != cudaSuccess) {
-    set_last_cuda_error(attr_err, "cudaFuncSetAttribute(tc)", __FILE__, __LINE__);
-    return COMPAR_ERR_CUDA;
-  }
+  int rc0 = tc_kernel_setup<V, kPair>(nullptr);
+  if (rc0 != COMPAR_OK) return rc0;
+  if (kPair && plan.splits > 1) return COMPAR_ERR_INVALID;
   CUtensorMap ta, tb, ta2, tb2, ta3, tb3;
   const CUtensorMapDataType dt = map_type(V);
   const uint32_t box_k = static_cast<uint32_t>(L::kElemsPerStage);
@@ -1032,7 +1164,7 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
     if constexpr (T::b_mn)
       return tma_encode_2d(m, dt, 2, base, c.n, c.k, ldb, 64, box_k, 128);
     else
-      return tma_encode_2d(m, dt, T::elem, base, c.k, c.n, ldb, box_k, T::BN, T::row);
+      return tma_encode_2d(m, dt, T::elem, base, c.k, c.n, ldb, box_k, L::kBRows, T::row);
   };
   int rc;
   if constexpr (T::fused) {
@@ -1071,7 +1203,8 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.sk_ctas = plan.sk_ctas;
   a.sk_slab = sk_slab;
   a.sk_count = sk_count;
-  a.tiles_m = static_cast<int>((c.m + kBM - 1) / kBM);
+  a.pair = kPair ? 2 : 1;
+  a.tiles_m = static_cast<int>((c.m + a.pair * kBM - 1) / (a.pair * kBM));
   a.tiles_n = static_cast<int>((c.n + T::BN - 1) / T::BN);
   a.alpha = c.alpha * (V == COMPAR_V_TC_FP8 ? c.scale_a * c.scale_b : 1.f);
   a.beta = c.beta;
@@ -1081,25 +1214,28 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.ldc = c.ldc;
   a.err_word = g.err_word;
   a.budget_ns = g.budget_ns;
+  // `slots` work-list CTAs (pairs when kPair) run at once
   const int units = a.tiles_m * a.tiles_n * a.splits;
-  int grid = std::min(units, num_sms);
+  int grid = std::min(units, slots);
   a.dp_units = units;
   if (plan.sk_q > 0) {
-    // whole waves of tiles, then the stream-K tail on sk_ctas CTAs
+    // whole waves of tiles, then the stream-K tail on sk_ctas CTAs (pairs)
     if (sk_count == nullptr || sk_slab == nullptr) return COMPAR_ERR_INVALID;
     a.dp_units = plan.sk_tile0;
-    grid = plan.sk_tile0 > 0 ? num_sms : plan.sk_ctas;
-    COMPAR_CUDA_TRY(
-        cudaMemsetAsync(sk_count, 0, sizeof(unsigned int) * (units - plan.sk_tile0), s));
+    grid = plan.sk_tile0 > 0 ? slots : plan.sk_ctas;
+    COMPAR_CUDA_TRY(cudaMemsetAsync(
+        sk_count, 0, sizeof(unsigned int) * (units - plan.sk_tile0) * a.pair, s));
   }
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(grid * a.pair, s, attr);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
-  tc_gemm_kernel<V><<<grid, L::kThreads, L::kSmemBytes, s>>>(ta, tb, ta2, tb2, ta3, tb3, a);
-  COMPAR_CUDA_TRY(cudaGetLastError());
+  COMPAR_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<V, kPair>, ta, tb, ta2, tb2, ta3, tb3,
+                                     a));
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();
   // the split units already applied alpha (and the dequantisation)
   if (a.splits > 1)
-    return launch_splitk_reduce(a.M, a.N, a.splits, partial, 1.f, c.beta, c.C, c.ldc, num_sms, s);
+    return launch_splitk_reduce(a.M, a.N, a.splits, partial, 1.f, c.beta, c.C, c.ldc, slots, s);
   return COMPAR_OK;
 }
 
@@ -1128,6 +1264,34 @@ bool tc_supported(int v, const GemmCall& c) {
              (reinterpret_cast<uintptr_t>(c.B) & 15) == 0;
     default: return false;
   }
+}
+
+// Whether a call runs on CTA pairs: the context's setting (-1 automatic, 0
+// never, 1 whenever the variant has a pair kernel), and automatically when
+// the single-CTA plan has a full wave of tiles or more.  Measured on B300
+// (steady load, power-capped): pairs gain 3-4 % for 3xBF16 and 5-11 % for
+// BF16 from 3072^2 up, and lose a few per cent on a single partial wave
+// (2048^2).  Only the variants that hand an accumulator to the epilogue
+// rarely have pair kernels; per-stage promotion (6-product split, 3xTF32)
+// would put a cross-CTA handshake on every stage and measured slower.
+// `pairs`: pairs resident at once.
+bool has_pair_kernel(int v) {
+  return v == COMPAR_V_TC_TF32 || v == COMPAR_V_TC_BF16 || v == COMPAR_V_TC_FP8 ||
+         v == COMPAR_V_SPLIT3;
+}
+
+bool use_pairs(int v, const GemmCall& c, const DeviceGuard& g, int num_sms, int* pairs) {
+  if (g.tc_pair == 0 || !has_pair_kernel(v)) return false;
+  if (g.tc_pair < 0 && tc_plan(v, c, num_sms).tiles < num_sms) return false;
+  int rc = COMPAR_ERR_INVALID;
+  switch (v) {
+    case COMPAR_V_TC_TF32: rc = tc_kernel_setup<COMPAR_V_TC_TF32, true>(pairs); break;
+    case COMPAR_V_TC_BF16: rc = tc_kernel_setup<COMPAR_V_TC_BF16, true>(pairs); break;
+    case COMPAR_V_TC_FP8: rc = tc_kernel_setup<COMPAR_V_TC_FP8, true>(pairs); break;
+    case COMPAR_V_SPLIT3: rc = tc_kernel_setup<COMPAR_V_SPLIT3, true>(pairs); break;
+    default: break;
+  }
+  return rc == COMPAR_OK && *pairs >= 1;
 }
 
 // Pre-passes + launch.  The BF16 variant reads B MN-major, K x N as stored:
@@ -1159,7 +1323,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
       if (slab_bytes) sk_slab = reinterpret_cast<float*>(base + part_bytes);
       if (count_bytes) sk_count = reinterpret_cast<unsigned int*>(base + part_bytes + slab_bytes);
     }
-    return run_tc<COMPAR_V_SPLIT3_FUSED>(c, c.A, c.lda, c.B, c.ldb, nullptr, nullptr, nullptr,
+    return run_tc<COMPAR_V_SPLIT3_FUSED, false>(c, c.A, c.lda, c.B, c.ldb, nullptr, nullptr, nullptr,
                                          nullptr, nullptr, nullptr, plan, partial, sk_slab,
                                          sk_count, g, num_sms, s);
   }
@@ -1176,13 +1340,19 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const int64_t ldn = round_up(c.n, 8);  // MN-major copies: 16-byte rows
   const bool b_in_place = b_mn && c.dtype == COMPAR_BF16 && tma_operand_ok(c.B, c.ldb, 2);
 
-  const TcPlan plan = tc_plan(v, c, num_sms);
+  // CTA pairs (cta_group::2) when the call has a wave of tiles or more
+  int pairs = 0;
+  const bool pair = use_pairs(v, c, g, num_sms, &pairs);
+  const TcPlan plan = pair ? tc_plan(v, c, pairs, true) : tc_plan(v, c, num_sms);
+  const int npair = pair ? 2 : 1;
   const size_t part_bytes =
       plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
   // stream-K: two published pieces per CTA and one counter per tail tile
+  // (per CTA of a pair)
   const size_t slab_bytes =
-      plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kTileN * 4 : 0;
-  const size_t count_bytes = plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
+      plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * npair * 2 * kBM * kTileN * 4 : 0;
+  const size_t count_bytes =
+      plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * npair * 4, 256) : 0;
   // workspace carve: [B pieces][A pieces][fp8 scalars][split-K partials]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
   const size_t b_bytes = b_in_place ? 0
@@ -1250,40 +1420,43 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const void* B2 = pieces >= 2 ? static_cast<const void*>(wb + b_bytes) : nullptr;
   const void* A3 = pieces == 3 ? static_cast<const void*>(wa + 2 * a_bytes) : nullptr;
   const void* B3 = pieces == 3 ? static_cast<const void*>(wb + 2 * b_bytes) : nullptr;
+  auto run = [&](auto vtag, const float* qa, const float* qb) {
+    constexpr int VV = decltype(vtag)::value;
+    if constexpr (VV == COMPAR_V_TC_TF32 || VV == COMPAR_V_TC_BF16 || VV == COMPAR_V_TC_FP8 ||
+                  VV == COMPAR_V_SPLIT3) {
+      if (pair)
+        return run_tc<VV, true>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, qa, qb, plan, partial,
+                                sk_slab, sk_count, g, pairs, s);
+    }
+    return run_tc<VV, false>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, qa, qb, plan, partial,
+                             sk_slab, sk_count, g, num_sms, s);
+  };
   switch (v) {
     case COMPAR_V_TC_TF32:
-      return run_tc<COMPAR_V_TC_TF32>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
-                                      num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_TC_TF32>{}, nullptr, nullptr);
     case COMPAR_V_TC_BF16:
-      return run_tc<COMPAR_V_TC_BF16>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
-                                      num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_TC_BF16>{}, nullptr, nullptr);
     case COMPAR_V_TC_FP8:
-      return run_tc<COMPAR_V_TC_FP8>(c, A, lda, Bop, ldb_op, nullptr, nullptr, nullptr, nullptr,
-                                     dqa, dqb, plan, partial, sk_slab, sk_count, g, num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_TC_FP8>{}, dqa, dqb);
     case COMPAR_V_SPLIT3:
-      return run_tc<COMPAR_V_SPLIT3>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr, nullptr,
-                                     nullptr, plan, partial, sk_slab, sk_count, g, num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_SPLIT3>{}, nullptr, nullptr);
     case COMPAR_V_SPLIT3_TF32:
-      return run_tc<COMPAR_V_SPLIT3_TF32>(c, A, lda, Bop, ldb_op, A2, B2, nullptr, nullptr,
-                                          nullptr, nullptr, plan, partial, sk_slab, sk_count, g,
-                                          num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_SPLIT3_TF32>{}, nullptr, nullptr);
     default:
-      return run_tc<COMPAR_V_SPLIT6>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, nullptr, nullptr,
-                                     plan, partial, sk_slab, sk_count, g, num_sms, s);
+      return run(std::integral_constant<int, COMPAR_V_SPLIT6>{}, nullptr, nullptr);
   }
 }
 
-int tc_plan_info(int v, int64_t m, int64_t n, int64_t k, int num_sms, int64_t* out) {
+int tc_plan_info(int v, int64_t m, int64_t n, int64_t k, int slots, int64_t* out, bool pair) {
   if (v < COMPAR_V_TC_TF32 || v >= COMPAR_V_COUNT || v == COMPAR_V_GROUPED || m < 1 || n < 1 ||
-      k < 1 || num_sms < 1 || !out || m > (1 << 30) || n > (1 << 30) || k > (1 << 30))
+      k < 1 || slots < 1 || !out || m > (1 << 30) || n > (1 << 30) || k > (1 << 30) ||
+      (pair && !has_pair_kernel(v)))
     return COMPAR_ERR_INVALID;
   GemmCall c;
   c.m = m;
   c.n = n;
   c.k = k;
-  const TcPlan p = tc_plan(v, c, num_sms);
+  const TcPlan p = tc_plan(v, c, slots, pair);
   const int64_t vals[9] = {p.num_kb, p.tiles,   p.splits, p.kb_per,      p.sk_tile0,
                            p.sk_cpt, p.sk_q,    p.sk_ctas, sk_chunk_of(v)};
   for (int i = 0; i < 9; ++i) out[i] = vals[i];

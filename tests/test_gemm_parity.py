@@ -33,19 +33,21 @@ def ctx():
     c.close()
 
 
-def _run(ctx, v, A, B, dtype=None, alpha=1.0, beta=0.0, C0=None, tol=0.0):
+def _run(ctx, v, A, B, dtype=None, alpha=1.0, beta=0.0, C0=None, tol=0.0, pairs=-1):
     from gpu_util import dev, empty_c, host
     import paper_2311_03543_b300 as cp
     m, n = A.shape[0], B.shape[1]
     C = dev(C0.astype(np.float32)) if C0 is not None else empty_c(m, n)
     ctx.set_scalars(alpha, beta)
     ctx.force_variant(v)
+    ctx.set_tc_pairs(pairs)
     try:
         ctx.gemm(dev(A), dev(B), C, tol=tol, dtype=dtype)
         out = host(C)
     finally:
         ctx.force_variant(None)
         ctx.set_scalars(1.0, 0.0)
+        ctx.set_tc_pairs(-1)
     assert ctx.check_device_error() == cp.OK
     return out
 
@@ -257,35 +259,44 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8, 9])
-def test_partial_last_wave_with_alpha_beta(ctx, v):
+def test_partial_last_wave_with_alpha_beta(ctx, v, pairs):
     """180 tiles of 128 x 256 on 148 SMs (a partial second wave of the
-    persistent CTAs, cut into stream-K pieces for the promoted variants),
-    integer inputs, alpha and beta."""
+    persistent CTAs, cut into stream-K pieces for the promoted variants), or
+    90 tiles of 256 x 256 on 74 CTA pairs; integer inputs, alpha and beta."""
+    import paper_2311_03543_b300 as cp
+    if pairs and v not in (2, 3, 4, 5):
+        pytest.skip("no pair kernel")
     m, n, k = 2560, 2304, 1024
     A = W.integer_matrix(m, k, seed=41, bound=2)
     B = W.integer_matrix(k, n, seed=42, bound=2)
     C0 = W.integer_matrix(m, n, seed=43)
-    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
+    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0, pairs=pairs)
     ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
     assert N.rel_frobenius(got, ref) <= TOL_F32
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("v,m,n,k", [(5, 2500, 2000, 1000), (7, 2500, 2000, 1000),
                                      (8, 2500, 2000, 1000), (5, 1536, 2048, 4096),
                                      (7, 1400, 2048, 777), (9, 2500, 2000, 1000),
-                                     (9, 1536, 2048, 4096)])
-def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
+                                     (9, 1536, 2048, 4096), (5, 4096, 4096, 2048)])
+def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k, pairs):
     """A partial last wave of tiles (160 tiles: one full wave and 12 more) or
     a single partial wave (96 or 88 tiles) is cut into stream-K pieces of
     whole promotion chunks; 2 - 5 CTAs contribute to a tile and the last to
     finish adds the pieces in a fixed order.  Ragged M, N and K, alpha and
-    beta; the same call twice gives the same bits."""
+    beta; the same call twice gives the same bits.  With pairs (3xBF16),
+    the tiles are 256 x 256 on 74 CTA pairs and each CTA of a pair publishes
+    and sums its own rows of a tail tile."""
+    if pairs and v != 5:
+        pytest.skip("no pair kernel")
     A = W.uniform(m, k, seed=61)
     B = W.uniform(k, n, seed=62)
     C0 = W.uniform(m, n, seed=63)
-    got = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
-    again = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0)
+    got = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0, pairs=pairs)
+    again = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0, pairs=pairs)
     assert np.array_equal(got, again)
     from gpu_util import abs_product_rows, assert_elementwise, elem_bound
     rows = W.tile_rows(m, seed=64)
@@ -295,10 +306,11 @@ def test_stream_k_tail_matches_oracle_and_is_deterministic(ctx, v, m, n, k):
     assert_elementwise(got[rows], ref, scale, elem_bound(v, k))
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("v,tol,m,n,k", [(2, 2e-3, 2500, 2000, 4096), (2, 2e-3, 1536, 2048, 8192),
                                          (3, 5e-3, 2500, 2000, 4096), (3, 5e-3, 1536, 2048, 8192),
                                          (4, 6e-2, 2500, 2000, 8192)])
-def test_stream_k_plain_variants(ctx, v, tol, m, n, k):
+def test_stream_k_plain_variants(ctx, v, tol, m, n, k, pairs):
     """TF32, BF16 and FP8 (float32 inputs) with a stream-K tail: each piece
     is an accumulator of its own K range, published from TMEM; the result is
     within the variant's error level of the oracle and repeatable bit for
@@ -306,8 +318,8 @@ def test_stream_k_plain_variants(ctx, v, tol, m, n, k):
     A = W.uniform(m, k, seed=81)
     B = W.uniform(k, n, seed=82)
     C0 = W.uniform(m, n, seed=83)
-    got = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
-    again = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0)
+    got = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0, pairs=pairs)
+    again = _run(ctx, v, A, B, alpha=1.25, beta=0.5, C0=C0, pairs=pairs)
     assert np.array_equal(got, again)
     from gpu_util import abs_product_rows, assert_elementwise, elem_bound
     rows = W.tile_rows(m, seed=84)
@@ -495,3 +507,49 @@ def test_simt_skinny_counters_recover_after_overlapping_calls(ctx):
         ctx.force_variant(None)
     assert ctx.check_device_error() == cp.OK
     assert N.rel_frobenius(C3.cpu().numpy(), oracle.gemm(A, B)) <= TOL_F32
+
+
+# CTA pairs (cta_group::2): one 256 x 256 tile per pair of CTAs, each CTA
+# holding half of A's rows and half of B's columns; tiles smaller than a
+# pair's, ragged edges in M, N and K, a stream-K tail, alpha and beta.
+PAIR_SHAPES = [(256, 256, 32), (300, 260, 100), (1000, 3000, 777), (2560, 2304, 1024),
+               (4096, 4096, 512)]
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+@pytest.mark.parametrize("m,n,k", PAIR_SHAPES)
+def test_pair_kernels_match_oracle(ctx, v, m, n, k):
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    A = W.uniform(m, k, seed=91); B = W.uniform(k, n, seed=92); C0 = W.uniform(m, n, seed=93)
+    got = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0, pairs=1)
+    again = _run(ctx, v, A, B, alpha=1.5, beta=-0.25, C0=C0, pairs=1)
+    assert np.array_equal(got, again)
+    rows = W.tile_rows(m, seed=94)
+    if v == 3:                      # against the product of the bf16 values multiplied
+        Ae, Be, s = N.bf16_round(A).astype(np.float64), N.bf16_round(B).astype(np.float64), 1.0
+    elif v == 4:                    # ... of the e4m3 codes, dequantised
+        qa, sa = N.fp8_quantize(A); qb, sb = N.fp8_quantize(B)
+        Ae, Be, s = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb), 1.0 / (float(sa) * float(sb))
+    else:                           # TF32: total error; 3xBF16: FP32 accuracy
+        Ae, Be, s = A.astype(np.float64), B.astype(np.float64), 1.0
+    ref = oracle.gemm_rows(Ae, Be, rows, alpha=1.5 * s, beta=-0.25, C0=C0)
+    scale = 1.5 * s * abs_product_rows(Ae, Be, rows) + 0.25 * np.abs(C0[rows])
+    assert_elementwise(got[rows], ref, scale, elem_bound(v, k))
+    if v == 5:
+        exact = oracle.gemm_rows(A, B, rows, alpha=1.5, beta=-0.25, C0=C0)
+        assert N.rel_frobenius(got[rows], exact) <= TOL_F32
+
+
+def test_pairs_are_chosen_for_a_wave_of_tiles(ctx):
+    """The automatic rule takes pairs from a full wave of 128 x 256 tiles up:
+    at 2304^2 (162 tiles) the automatic call gives the bits of the forced
+    pair call."""
+    import paper_2311_03543_b300 as cp
+    assert cp.Context.tc_plan(cp.V_SPLIT3, 2048, 2048, 2048)["tiles"] < 148
+    assert cp.Context.tc_plan(cp.V_SPLIT3, 2304, 2304, 2304)["tiles"] >= 148
+    m = n = 2304
+    k = 512
+    A = W.uniform(m, k, seed=95); B = W.uniform(k, n, seed=96)
+    auto = _run(ctx, cp.V_SPLIT3, A, B, pairs=-1)
+    forced = _run(ctx, cp.V_SPLIT3, A, B, pairs=1)
+    assert np.array_equal(auto, forced)

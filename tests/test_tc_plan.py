@@ -45,12 +45,17 @@ def _items(b, grid, pl):
         i += 1
 
 
-def _check(v, m, n, k):
-    pl = cp.Context.tc_plan(v, m, n, k, P)
+def _check(v, m, n, k, pairs=None):
+    slots = P if pairs is None else pairs
+    pl = cp.Context.tc_plan(v, m, n, k, P, pairs=pairs)
     tiles = pl["tiles"]
-    grid = min(tiles * pl["splits"], P)
+    tm = 128 if pairs is None else 256
+    assert tiles == -(-m // tm) * -(-n // 256)
+    if pairs is not None:
+        assert pl["splits"] == 1
+    grid = min(tiles * pl["splits"], slots)
     if pl["sk_q"]:
-        grid = P if pl["sk_tile0"] > 0 else pl["sk_ctas"]
+        grid = slots if pl["sk_tile0"] > 0 else pl["sk_ctas"]
     cover = {}
     for b in range(grid):
         its = _items(b, grid, pl)
@@ -98,3 +103,28 @@ def test_plan_arguments_are_validated():
     assert cp.compar_tc_plan(cp.V_GROUPED, 64, 64, 64, P, (cp._i64 * 9)()) == cp.ERR_INVALID
     assert cp.compar_tc_plan(cp.V_SIMT, 64, 64, 64, P, (cp._i64 * 9)()) == cp.ERR_INVALID
     assert cp.compar_tc_plan(cp.V_SPLIT3, 0, 64, 64, P, (cp._i64 * 9)()) == cp.ERR_INVALID
+
+
+PAIR = [cp.V_TC_TF32, cp.V_TC_BF16, cp.V_TC_FP8, cp.V_SPLIT3]
+
+
+@pytest.mark.parametrize("v", PAIR)
+@pytest.mark.parametrize("pairs", [74, 71, 1])
+def test_pair_work_lists_cover_every_k_block_once(v, pairs):
+    """CTA-pair plans (256 x 256 tiles, the work list walked per pair): the
+    same coverage rules, for the pair count of a full B300 and for fewer
+    resident pairs."""
+    for m, n, k in itertools.product([256, 1000, 2560, 4096, 5120, 333],
+                                     [256, 2048, 4096, 100], [32, 300, 4096, 8200]):
+        _check(v, m, n, k, pairs=pairs)
+
+
+def test_pair_plan_stream_k_and_validation():
+    # 4096^3 on 74 pairs: 256 tiles = 3 waves + 34 tiles; the tail is cut
+    pl = _check(cp.V_SPLIT3, 4096, 4096, 4096, pairs=74)
+    assert pl["tiles"] == 256 and pl["sk_tile0"] == 222 and pl["sk_q"] > 0
+    out = (cp._i64 * 9)()
+    for v in (cp.V_SPLIT3_FUSED, cp.V_SPLIT6, cp.V_SPLIT3_TF32):   # no pair kernels
+        assert cp.compar_tc_pair_plan(v, 512, 512, 512, 74, out) == cp.ERR_INVALID
+    assert cp.compar_tc_pair_plan(cp.V_SPLIT3, 512, 512, 512, 0, out) == cp.ERR_INVALID
+    assert cp.compar_tc_pair_plan(cp.V_SIMT, 512, 512, 512, 74, out) == cp.ERR_INVALID
