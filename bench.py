@@ -633,15 +633,29 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
     ms_best = timed(None)                      # the autotuned choice
     ms_loop = tuned_ms[0]                      # per-GEMM launches (autotuner's median)
     flops = sum(2.0 * m * n * k for m, n, k, _ in plist)
+    # tensor-pipe work: a float32 problem at tol 1e-5 runs as 3xBF16 (three
+    # bf16 products per useful product), a bf16 problem as one
+    bf16_work = sum(2.0 * m * n * k * (3 if dt == cp.F32 else 1) for m, n, k, dt in plist)
     del keep
     names = ["per-GEMM launches", "grouped BN=128", "grouped BN=256",
              "grouped BN=128 largest-first", "grouped BN=256 largest-first"]
+    roof = {"bound": "tensor", "unit": "TFLOP/s",
+            "achieved": bf16_work / (ms_best / 1e3) / 1e12,
+            "work": "bf16 MMA work: 2MNK per bf16 problem, 3 x 2MNK per float32 (3xBF16) problem"}
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        roof["peak"] = pk["bf16_tflops_sustained"]
+        roof["peak_source"] = "measured bf16 sustained (MEASURED_PEAKS.json) (of measured)"
+        roof["frac_of_burst"] = roof["achieved"] / pk["bf16_tflops"]
+    except (OSError, ValueError, KeyError):
+        roof["peak"], roof["peak_source"] = 1400.0, "fallback 1.4 PFLOP/s sustained (of fallback)"
+    roof["frac"] = roof["achieved"] / roof["peak"]
     return {"problems": len(plist), "gflop": flops / 1e9, "ld": "rounded up to 16 bytes",
             "chosen": names[best],
             "ms_chosen": ms_best, "tflops_chosen": flops / (ms_best / 1e3) / 1e12,
             "ms_per_gemm_launches": ms_loop,
             "tflops_per_gemm_launches": flops / (ms_loop / 1e3) / 1e12,
-            "autotune_ms": dict(zip(names, tuned_ms))}
+            "autotune_ms": dict(zip(names, tuned_ms)), "roofline": roof}
 
 
 def measure_stencil(ctx, cp, W, torch, dev, reps=5):
@@ -771,11 +785,11 @@ def online_study(ctx, cp, W, torch, dev, selector, count=120, calls=800):
     selector that has not seen the call distribution: its mean regret on the
     first `count` held-out contexts, then `calls` calls drawn from the same
     law with another seed (54321) made with exploration probability 0.25 and
-    a fine-tune every 100 new timing records, then the regret on the same
+    a 300-step fine-tune every 100 new timing records, then the regret on the same
     held-out contexts again (exploration off)."""
     ctx.selector_load(selector)
     before = measure_regret(ctx, cp, W, torch, dev, count=count)
-    ctx.set_online(epsilon=0.25, retrain_every=100, finetune_steps=1000)
+    ctx.set_online(epsilon=0.25, retrain_every=100, finetune_steps=300)
     for i, (m, n, k, dt, tol) in enumerate(W.heldout_contexts(count=calls, seed=54321)):
         g = torch.Generator(device=dev)
         g.manual_seed(70000 + i)
@@ -789,11 +803,11 @@ def online_study(ctx, cp, W, torch, dev, selector, count=120, calls=800):
         C = torch.empty((m, n), device=dev)
         ctx.gemm(A, B, C, tol=tol, dtype=dt)
     torch.cuda.synchronize()
-    explored, retrains = ctx.online_stats()
+    explored, retrains, rejected = ctx.online_stats()
     ctx.set_online(0.0, 0, 0)
     after = measure_regret(ctx, cp, W, torch, dev, count=count)
     return {"selector": os.path.basename(selector), "contexts": after[2], "calls": calls,
-            "explored": explored, "fine_tunes": retrains,
+            "explored": explored, "fine_tunes": retrains, "fine_tunes_discarded": rejected,
             "regret_before_pct": before[0], "violations_before": before[1],
             "regret_after_pct": after[0], "violations_after": after[1]}
 

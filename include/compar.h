@@ -247,8 +247,9 @@ int compar_set_scalars(compar_ctx_t ctx, float alpha, float beta);
  * 1, 1).  Must be finite and > 0. */
 int compar_set_fp8_scales(compar_ctx_t ctx, float scale_a, float scale_b);
 
-/* Selection policy: 0 = auto (MLP when confident, else history table),
- * 1 = history table only, 2 = MLP only. */
+/* Selection policy: 0 = auto (the MLP when confident, else the history
+ * table; a variant timed in the call's own history bucket is then ranked by
+ * that measurement), 1 = history table only, 2 = MLP only. */
 int compar_set_selector_mode(compar_ctx_t ctx, int mode);
 
 /* Variant chosen by the most recent compar_gemm call (-1 before any). */
@@ -357,23 +358,32 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr,
 /* Continue training the current model from its weights and standardisation
  * on all records held plus the loaded rehearsal sample, so that new records
  * add to what the model knows instead of replacing it (fine-tuning; a fresh
- * training on the records held when no model exists yet).  Arguments as
- * compar_selector_train. */
+ * training on the records held when no model exists yet).  The fine-tuned
+ * weights are kept only if they lower the held-out loss below that of the
+ * weights they started from; otherwise the model is left as it was (still
+ * COMPAR_OK; *val_loss then holds the unchanged model's loss, and the
+ * context's count of discarded fine-tunes, compar_online_stats, grows).
+ * Arguments as compar_selector_train. */
 int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr,
                              uint64_t seed, float* val_loss);
 
 /* Online selection (the paper expects better-trained models to choose
- * better, Sec. 3.2 and Sec. 5).  With probability `epsilon` a call whose
- * context misses the decision cache runs a uniformly drawn eligible variant
- * instead of the model's pick (exploration; that choice is not cached), every
+ * better, Sec. 3.2 and Sec. 5).  With probability `epsilon` a call (its
+ * decision cached or not) runs another eligible variant instead of the
+ * pick, drawn uniformly among those predicted within 4x of the pick's time
+ * (among all others when none is): exploration, not cached, aimed at the
+ * close calls the models must learn to rank.  Every
  * call is recorded, and once `retrain_every` (> 0) new records have
  * accumulated the MLP is fine-tuned for `finetune_steps` (0: 500) steps
  * inside the call that crosses the threshold (synchronous).  epsilon = 0 and
  * retrain_every = 0 turn it off; recording stays as it was set. */
 int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
                       int finetune_steps);
-/* Exploratory picks and online fine-tunings so far. */
-int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains);
+/* Exploratory picks, fine-tunes run (online or by compar_selector_finetune)
+ * and, of those, fine-tunes discarded because they did not lower the
+ * held-out loss.  `rejected` may be NULL. */
+int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains,
+                        int64_t* rejected);
 
 /* The trained model's prediction for one call: per variant (arrays of
  * COMPAR_V_COUNT floats, indexed by variant id) the ensemble-mean run time in

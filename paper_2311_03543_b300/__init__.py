@@ -122,7 +122,8 @@ SIGNATURES = {
     "compar_selector_train": (_i, [_vp, _i, _i, _f, _u64, _fp]),
     "compar_selector_finetune": (_i, [_vp, _i, _i, _f, _u64, _fp]),
     "compar_set_online": (_i, [_vp, _d, _i64, _i]),
-    "compar_online_stats": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "compar_online_stats": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                 ctypes.POINTER(_i64)]),
     "compar_predict": (_i, [_vp, _i64, _i64, _i64, _i, _d, _i, _fp, _fp, _fp]),
     "compar_residual_check": (_i, [_vp, _i64, _i64, _i64, _i, _vp, _vp, _vp, _f, _i, _u64,
                                    ctypes.POINTER(_d), _vp]),
@@ -555,10 +556,11 @@ class Context:
                                          int(finetune_steps)), "set_online")
 
     def online_stats(self):
-        a, b = ctypes.c_int64(), ctypes.c_int64()
-        _status(compar_online_stats(self.handle, ctypes.byref(a), ctypes.byref(b)),
-                "online_stats")
-        return a.value, b.value
+        """(explored picks, fine-tunes run, fine-tunes discarded)."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _status(compar_online_stats(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)), "online_stats")
+        return a.value, b.value, c.value
 
     def predict(self, m, n, k, dtype=F32, tol=0.0, batch=1):
         """MLP prediction: (time_ms, rel_err, spread), one entry per variant id."""

@@ -133,7 +133,10 @@ static uint32_t eligible_mask(const compar_ctx* ctx, const GemmCall& c) {
 }
 
 // MLP choice; returns -1 when the model is untrained or not confident.
-static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* pred_ms) {
+// `pred_all` (optional) receives the predicted time (ms) of every eligible
+// variant that passes the learned error head, +inf for the others.
+static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* pred_ms,
+                      double* pred_all = nullptr) {
   const MlpModel& mm = ctx->mlp;
   if (!mm.trained) return -1;
   auto x = make_features(c.m, c.n, c.k, c.dtype, c.tol, c.batch);
@@ -166,6 +169,7 @@ static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* 
     // the time head predicts log2(measured / roofline prior)
     const float log2_t = mean_t + static_cast<float>(std::log2(
                                       prior_time_ms(v, c.m, c.n, c.k, c.dtype, ctx->num_sms)));
+    if (pred_all) pred_all[v] = std::exp2(static_cast<double>(log2_t));
     if (log2_t < best_t) {
       best_t = log2_t;
       best = v;
@@ -178,13 +182,14 @@ static int mlp_choice(compar_ctx* ctx, const GemmCall& c, uint32_t mask, float* 
 }
 
 static int history_choice(const compar_ctx* ctx, const GemmCall& c, uint32_t mask,
-                          double* pred_ms) {
+                          double* pred_ms, double* pred_all = nullptr) {
   int best = -1;
   double best_t = INFINITY;
   for (int v = 0; v < kNumVariants; ++v) {
     if (!(mask & (1u << v))) continue;
     double t = ctx->hist.predict(v, c.dtype, c.m, c.n, c.k, c.batch, nullptr);
     if (t < 0) t = prior_time_ms(v, c.m, c.n, c.k, c.dtype, ctx->num_sms);
+    if (pred_all) pred_all[v] = t;
     if (t < best_t) {
       best_t = t;
       best = v;
@@ -199,38 +204,81 @@ static int select_variant(compar_ctx* ctx, const GemmCall& c) {
   const uint32_t mask = eligible_mask(ctx, c);
   if (!mask) return COMPAR_ERR_NO_VARIANT;
   const DecisionKey key{c.m, c.n, c.k, static_cast<int>(c.dtype), tol_class(c.tol), c.batch};
+  // Online exploration is drawn for every call, cached decision or not
+  // (epsilon-greedy): a program that repeats its shapes keeps trying the
+  // alternatives of its cached picks.
+  auto next = [&]() {
+    uint64_t z = (ctx->online.rng += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const bool explore =
+      ctx->online.epsilon > 0 &&
+      static_cast<double>(next() >> 11) * (1.0 / 9007199254740992.0) < ctx->online.epsilon;
   auto it = ctx->decisions.find(key);
-  if (it != ctx->decisions.end() && (mask & (1u << it->second))) return it->second;
-  if (ctx->online.epsilon > 0) {
-    // Exploration: with probability epsilon run a uniformly drawn eligible
-    // variant once (not cached), so its timing is recorded for the models.
-    auto next = [&]() {
-      uint64_t z = (ctx->online.rng += 0x9E3779B97F4A7C15ull);
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      return z ^ (z >> 31);
-    };
-    if (static_cast<double>(next() >> 11) * (1.0 / 9007199254740992.0) < ctx->online.epsilon) {
-      int ids[kNumVariants], nids = 0;
-      for (int v = 0; v < kNumVariants; ++v)
-        if (mask & (1u << v)) ids[nids++] = v;
-      ctx->online.explored += 1;
-      return ids[next() % static_cast<uint64_t>(nids)];
-    }
-  }
+  const int cached =
+      it != ctx->decisions.end() && (mask & (1u << it->second)) ? it->second : -1;
+  if (cached >= 0 && !explore) return cached;
   int v = -1;
   const char* by = "history";
   float mlp_ms = 0;
   double hist_ms = 0;
+  double pred[kNumVariants];
+  for (double& t : pred) t = INFINITY;
   if (ctx->selector_mode != 1) {
-    v = mlp_choice(ctx, c, mask, &mlp_ms);
+    v = mlp_choice(ctx, c, mask, &mlp_ms, pred);
     if (v >= 0) by = "mlp";
   }
   if (v < 0 && ctx->selector_mode == 2 && ctx->mlp.trained) {
     // MLP-only mode still needs an answer when the ensemble disagrees
     by = "history(fallback)";
   }
-  if (v < 0) v = history_choice(ctx, c, mask, &hist_ms);
+  if (v < 0) {
+    for (double& t : pred) t = INFINITY;
+    v = history_choice(ctx, c, mask, &hist_ms, pred);
+  }
+  if (ctx->selector_mode != 2) {
+    // Measured beats predicted: a variant timed in this call's own history
+    // bucket (sizes within ~9 %) is ranked by its fastest measurement instead
+    // of the model's estimate, so live timings correct the choice for the
+    // shapes a program repeats, as a calibrated history model does.
+    bool measured = false;
+    int vm = -1;
+    double best = INFINITY;
+    for (int u = 0; u < kNumVariants; ++u) {
+      if (!(mask & (1u << u))) continue;
+      const double t = ctx->hist.measured_min(u, c.dtype, c.m, c.n, c.k, c.batch);
+      const double e = t > 0 ? t : pred[u];
+      measured = measured || t > 0;
+      if (e < best) {
+        best = e;
+        vm = u;
+      }
+    }
+    if (measured && vm >= 0 && vm != v) {
+      v = vm;
+      by = "measured";
+    }
+  }
+  if (cached >= 0) v = cached;  // exploring around a cached decision
+  if (explore) {
+    // Exploration: run, once and without caching, another eligible variant
+    // whose predicted time is within 4x of the pick's (any other eligible
+    // variant when none is), so its timing is recorded where a mis-ranking
+    // is plausible: the close calls are what the models must learn to rank.
+    int ids[kNumVariants], nids = 0;
+    for (int u = 0; u < kNumVariants; ++u)
+      if (u != v && (mask & (1u << u)) && pred[u] <= 4.0 * pred[v]) ids[nids++] = u;
+    if (nids == 0)
+      for (int u = 0; u < kNumVariants; ++u)
+        if (u != v && (mask & (1u << u))) ids[nids++] = u;
+    if (nids > 0) {
+      ctx->online.explored += 1;
+      return ids[next() % static_cast<uint64_t>(nids)];
+    }
+    if (cached >= 0) return cached;
+  }
   if (ctx->log)
     fprintf(stderr, "[compar] m=%lld n=%lld k=%lld dtype=%d tol=%.1e eligible=0x%x -> %s by %s\n",
             static_cast<long long>(c.m), static_cast<long long>(c.n),
@@ -280,17 +328,50 @@ static compar_record_t make_record(const GemmCall& c, int v) {
   return r;
 }
 
-// Runs one call on variant v (recording it when recording is on).
+// The recorded-call gate's host-mapped word (allocated on first use); false
+// when it cannot be had (the call is then timed without the gate).
+static bool gate_ready(compar_ctx* ctx) {
+  if (ctx->gate_dev) return true;
+  void* h = nullptr;
+  if (cudaHostAlloc(&h, sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFreeHost(h);
+    return false;
+  }
+  ctx->gate_host = static_cast<unsigned int*>(h);
+  *ctx->gate_host = 0;
+  ctx->gate_dev = static_cast<unsigned int*>(d);
+  return true;
+}
+
+// Runs one call on variant v (recording it when recording is on).  A
+// recorded call is held behind the gate kernel until all its launches are
+// enqueued, so its recorded time is the device time of its kernels run back
+// to back (as compar_measure times them), not host launch gaps.
 static int run_one(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool gated = false;
   if (ctx->rec.on) {
     e0 = take_event(ctx);
     e1 = take_event(ctx);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (e0 && e1 && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone && gate_ready(ctx))
+      gated = launch_record_gate(ctx->gate_dev, ctx->gate_ticket + 1, s) == COMPAR_OK;
     if (e0) cudaEventRecord(e0, s);
   }
   const int rc = launch_variant(ctx, v, c, s);
+  if (ctx->rec.on && e0 && e1) cudaEventRecord(e1, s);
+  if (gated) {
+    // the whole call and its end event are enqueued: open the gate
+    __atomic_store_n(ctx->gate_host, ++ctx->gate_ticket, __ATOMIC_RELEASE);
+  }
   if (ctx->rec.on && e0 && e1) {
-    cudaEventRecord(e1, s);
     if (rc == COMPAR_OK) {
       ctx->pending.push_back(PendingTiming{e0, e1, make_record(c, v)});
       if (ctx->pending.size() >= 4096) resolve_pending(ctx);
@@ -315,7 +396,6 @@ static void maybe_retrain(compar_ctx* ctx) {
   float vl = 0;
   const int rc = compar_selector_finetune(ctx, steps, 128, 5e-4f, 0xC0FFEEull + o.retrains, &vl);
   o.records_at_train = static_cast<int64_t>(ctx->rec.ring.size());
-  if (rc == COMPAR_OK) o.retrains += 1;
   if (ctx->log) fprintf(stderr, "[compar] online fine-tune rc=%d loss=%.4f\n", rc, vl);
 }
 
@@ -436,6 +516,7 @@ int compar_terminate(compar_ctx_t ctx) {
   hostio_release(ctx);
   mlp_release(ctx);
   ctx->ws.release();
+  if (ctx->gate_host) cudaFreeHost(ctx->gate_host);
   if (ctx->guard.err_word) cudaFree(ctx->guard.err_word);
   delete ctx;
   return COMPAR_OK;

@@ -135,6 +135,10 @@ int tc_plan_info(int variant, int64_t m, int64_t n, int64_t k, int slots, int64_
                  bool pair);
 
 int launch_timeout_selftest(const DeviceGuard& g, cudaStream_t s);
+// One-thread kernel that holds `s` until *flag_dev (host-mapped) reaches
+// `ticket` or 2 ms pass: put before a recorded call's launches so that they
+// run back to back once the host has enqueued them all.
+int launch_record_gate(const unsigned int* flag_dev, unsigned int ticket, cudaStream_t s);
 
 // Pre-pass kernels (prepass.cu).
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols,

@@ -8,6 +8,7 @@
 
 #include <array>
 #include <cstdint>
+#include <cmath>
 #include <map>
 #include <string>
 #include <tuple>
@@ -60,6 +61,9 @@ struct HistVal {
   double mean_ms = 0;
   double m2 = 0;
   int64_t count = 0;
+  // fastest observation: ranks measured variants (a cold first call or a
+  // disturbed run does not decide against a variant)
+  double min_ms = INFINITY;
 };
 struct HistoryModel {
   std::map<HistKey, HistVal> table;
@@ -69,6 +73,8 @@ struct HistoryModel {
   // Predicted time in ms; *exact receives whether the key was present.
   // Returns < 0 when nothing near is known.
   double predict(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch, bool* exact) const;
+  // Fastest time observed in the call's own bucket, or < 0 if none.
+  double measured_min(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch) const;
 };
 
 // Roofline prior: max(work / pipe peak, bytes / bandwidth) + launch overheads.
@@ -135,6 +141,10 @@ struct PendingTiming {  // events of a recorded compar_gemm call, resolved lazil
 }  // namespace compar
 
 // The opaque context of the C ABI.
+// Internal status of a warm fine-tune whose result was discarded (the
+// model is unchanged); never returned through the C ABI.
+constexpr int COMPAR_FINETUNE_KEPT = 1;
+
 struct compar_ctx {
   bool host_only = false;  // created by compar_init_host: no CUDA calls at all
   int device = 0;
@@ -172,13 +182,17 @@ struct compar_ctx {
     int finetune_steps = 0;
     int64_t records_at_train = 0;
     uint64_t rng = 0x243F6A8885A308D3ull;
-    int64_t explored = 0, retrains = 0;
+    int64_t explored = 0, retrains = 0, rejected = 0;
   } online;
   void* batched_state = nullptr;
   void* hostio_state = nullptr;  // device buffers and streams of compar_gemm_host
   compar::StencilSel stencil;    // the second component's selection state
   // MLP device buffers (selector inference / training), owned here.
   void* mlp_dev = nullptr;
+  // recorded-call gate: a host-mapped word and the last ticket written
+  unsigned int* gate_host = nullptr;
+  unsigned int* gate_dev = nullptr;
+  unsigned int gate_ticket = 0;
 };
 
 namespace compar {

@@ -113,6 +113,16 @@ void HistoryModel::observe(int v, int dtype, int64_t m, int64_t n, int64_t k, in
   const double d = ms - e.mean_ms;
   e.mean_ms += d / static_cast<double>(e.count);
   e.m2 += d * (ms - e.mean_ms);
+  e.min_ms = std::min(e.min_ms, ms);
+}
+
+double HistoryModel::measured_min(int v, int dtype, int64_t m, int64_t n, int64_t k,
+                                  int batch) const {
+  auto it = table.find(key(v, dtype, m, n, k, batch));
+  if (it == table.end() || it->second.count < 1 || !(it->second.min_ms > 0) ||
+      !std::isfinite(it->second.min_ms))
+    return -1;
+  return it->second.min_ms;
 }
 
 double HistoryModel::predict(int v, int dtype, int64_t m, int64_t n, int64_t k, int batch,

@@ -19,7 +19,7 @@ namespace compar {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'M', 'P', 'R', 'S', 'E', 'L', '1'};
-constexpr uint32_t kVersion = 7;  // 7: rehearsal records; variant ids 0..9 (20 MLP outputs)
+constexpr uint32_t kVersion = 8;  // 8: fastest time per history entry; 7 (read too): rehearsal records; variant ids 0..9 (20 MLP outputs)
 constexpr size_t kRehearsal = 16384;
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
@@ -69,7 +69,8 @@ struct Reader {
   }
 };
 
-// History tables: count, then (key, running mean, M2, count) per entry.
+// History tables: count, then (key, running mean, M2, count, fastest) per
+// entry (version 7 files have no fastest time: it is read as the mean).
 void put_hist(Writer& w, const HistoryModel& h) {
   w.put<uint32_t>(static_cast<uint32_t>(h.table.size()));
   for (const auto& kv : h.table) {
@@ -82,10 +83,11 @@ void put_hist(Writer& w, const HistoryModel& h) {
     w.put(kv.second.mean_ms);
     w.put(kv.second.m2);
     w.put(kv.second.count);
+    w.put(kv.second.min_ms);
   }
 }
 
-void get_hist(Reader& r, HistoryModel& h, int num_variants) {
+void get_hist(Reader& r, HistoryModel& h, int num_variants, uint32_t version) {
   const uint32_t n = r.get<uint32_t>();
   for (uint32_t i = 0; r.ok && i < n; ++i) {
     HistKey k;
@@ -99,6 +101,7 @@ void get_hist(Reader& r, HistoryModel& h, int num_variants) {
     v.mean_ms = r.get<double>();
     v.m2 = r.get<double>();
     v.count = r.get<int64_t>();
+    v.min_ms = version >= 8 ? r.get<double>() : v.mean_ms;
     if (k.v < 0 || k.v >= num_variants || k.dtype < 0 || k.dtype > 2) r.ok = false;
     h.table[k] = v;
   }
@@ -185,7 +188,7 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
   uint64_t nbytes, sum;
   memcpy(&version, all.data() + 8, 4);
   memcpy(&nbytes, all.data() + 12, 8);
-  if (version != kVersion) return COMPAR_ERR_IO;
+  if (version != kVersion && version != 7) return COMPAR_ERR_IO;
   if (nbytes != all.size() - 28) return COMPAR_ERR_IO;
   const uint8_t* payload = all.data() + 20;
   memcpy(&sum, payload + nbytes, 8);
@@ -193,7 +196,7 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
 
   Reader r{payload, nbytes};
   HistoryModel hist;
-  get_hist(r, hist, kNumVariants);
+  get_hist(r, hist, kNumVariants, version);
   ErrorModel err;
   for (auto& row : err.c0) for (float& x : row) x = r.get<float>();
   for (auto& row : err.c1) for (float& x : row) x = r.get<float>();
@@ -227,7 +230,7 @@ extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
     batched[sig] = cfg;
   }
   HistoryModel stencil_hist;
-  get_hist(r, stencil_hist, COMPAR_S_COUNT);
+  get_hist(r, stencil_hist, COMPAR_S_COUNT, version);
   const uint32_t nr = r.get<uint32_t>();
   if (nr > kRehearsal) r.ok = false;
   std::vector<compar_record_t> rehearsal;

@@ -351,22 +351,17 @@ static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t
   for (auto& i : idx) i = train_rows[splitmix(st) % train_rows.size()];
   std::vector<float> adam_m(kEnsemble * P, 0.f), adam_v(kEnsemble * P, 0.f);
   std::vector<float> losses(static_cast<size_t>(kEnsemble) * steps);
-  int rc = compar_mlp_train_steps(ctx, params.data(), adam_m.data(), adam_v.data(), kEnsemble,
-                                  X.data(), T.data(), M.data(), rows, idx.data(), steps, B, lr,
-                                  1, nullptr, losses.data());
-  if (rc != COMPAR_OK) return rc;
-  for (int e = 0; e < kEnsemble; ++e) mm.members[e].unflatten(params.data() + e * P);
-  // ---- validation loss (standardised masked MSE, mean over members)
-  double vl = 0;
-  if (!val_rows.empty()) {
-    std::vector<float> vx(val_rows.size() * kNumFeatures);
-    for (size_t i = 0; i < val_rows.size(); ++i)
-      std::copy(X.begin() + val_rows[i] * kNumFeatures, X.begin() + (val_rows[i] + 1) * kNumFeatures,
-                vx.begin() + i * kNumFeatures);
+  // ---- validation loss (standardised masked MSE, mean over members) of a
+  // parameter set on the held-out rows
+  std::vector<float> vx(val_rows.size() * kNumFeatures);
+  for (size_t i = 0; i < val_rows.size(); ++i)
+    std::copy(X.begin() + val_rows[i] * kNumFeatures, X.begin() + (val_rows[i] + 1) * kNumFeatures,
+              vx.begin() + i * kNumFeatures);
+  auto val_loss_of = [&](const std::vector<float>& prm, double* out) -> int {
     std::vector<float> vy(val_rows.size() * kEnsemble * kOutputs);
-    rc = compar_mlp_forward(ctx, params.data(), kEnsemble, vx.data(),
-                            static_cast<int>(val_rows.size()), vy.data());
-    if (rc != COMPAR_OK) return rc;
+    const int r = compar_mlp_forward(ctx, prm.data(), kEnsemble, vx.data(),
+                                     static_cast<int>(val_rows.size()), vy.data());
+    if (r != COMPAR_OK) return r;
     double num = 0, den = 0;
     for (int e = 0; e < kEnsemble; ++e)
       for (size_t i = 0; i < val_rows.size(); ++i)
@@ -376,10 +371,33 @@ static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t
           num += mk * d * d;
           den += mk;
         }
-    vl = den > 0 ? num / den : 0.0;
+    *out = den > 0 ? num / den : 0.0;
+    return COMPAR_OK;
+  };
+  // A fine-tune starts from weights that already fit most of these rows; it
+  // is kept only if it lowers the held-out loss (live records and rehearsed
+  // ones alike), so a fine-tune that drifts on a few new records is dropped.
+  double vl_before = INFINITY;
+  if (warm && !val_rows.empty()) {
+    const int r = val_loss_of(params, &vl_before);
+    if (r != COMPAR_OK) return r;
+  }
+  int rc = compar_mlp_train_steps(ctx, params.data(), adam_m.data(), adam_v.data(), kEnsemble,
+                                  X.data(), T.data(), M.data(), rows, idx.data(), steps, B, lr,
+                                  1, nullptr, losses.data());
+  if (rc != COMPAR_OK) return rc;
+  double vl = 0;
+  if (!val_rows.empty()) {
+    rc = val_loss_of(params, &vl);
+    if (rc != COMPAR_OK) return rc;
   } else {
     vl = losses.back();
   }
+  if (warm && !(vl < vl_before)) {
+    if (val_loss) *val_loss = static_cast<float>(vl_before);
+    return COMPAR_FINETUNE_KEPT;
+  }
+  for (int e = 0; e < kEnsemble; ++e) mm.members[e].unflatten(params.data() + e * P);
   if (val_loss) *val_loss = static_cast<float>(vl);
   mm.trained = true;
   ctx->mlp = mm;
@@ -396,7 +414,13 @@ int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint
 
 int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
                              float* val_loss) {
-  return train_impl(ctx, steps, batch, lr, seed, true, val_loss);
+  const int rc = train_impl(ctx, steps, batch, lr, seed, true, val_loss);
+  if (ctx && (rc == COMPAR_OK || rc == COMPAR_FINETUNE_KEPT)) ctx->online.retrains += 1;
+  if (rc == COMPAR_FINETUNE_KEPT) {
+    ctx->online.rejected += 1;
+    return COMPAR_OK;
+  }
+  return rc;
 }
 
 int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
@@ -412,10 +436,12 @@ int compar_set_online(compar_ctx_t ctx, double epsilon, int64_t retrain_every,
   return COMPAR_OK;
 }
 
-int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains) {
+int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains,
+                        int64_t* rejected) {
   if (!ctx || !explored || !retrains) return COMPAR_ERR_INVALID;
   *explored = ctx->online.explored;
   *retrains = ctx->online.retrains;
+  if (rejected) *rejected = ctx->online.rejected;
   return COMPAR_OK;
 }
 

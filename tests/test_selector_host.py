@@ -196,7 +196,7 @@ def test_online_exploration_stays_within_eligible_variants(hctx):
                      cp.V_SPLIT3_FUSED)
         seen.add(v)
     assert len(seen) >= 2
-    explored, retrains = hctx.online_stats()
+    explored, retrains, _ = hctx.online_stats()
     assert explored == 200 and retrains == 0
     hctx.set_online(epsilon=0.0)
     first = hctx.select(2048, 2048, 2048, cp.F32, 1e-5)
