@@ -166,6 +166,20 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
     const double t = std::ceil(M / bm) * std::ceil(N / bn);
     return std::ceil(t / num_sms) * num_sms;  // wave quantisation
   };
+  // The tensor-core variants' launch plan (compar_tc_plan): tiles of
+  // 128 x 256 times the splits of K, in full waves of the SMs, each unit
+  // running its own share of K; a split of K adds its reduce launch.
+  auto tc_units = [&](double* k_eff) {
+    int64_t pl[9];
+    if (tc_plan_info(v, m, n, k, num_sms, pl, false) != COMPAR_OK) {
+      *k_eff = K;
+      return tiles(128, 256);
+    }
+    const double splits = static_cast<double>(pl[2]);
+    *k_eff = std::ceil(K / splits);
+    if (splits > 1) ovh_us += 4;
+    return std::ceil(static_cast<double>(pl[1]) * splits / num_sms) * num_sms;
+  };
   switch (v) {
     case COMPAR_V_NAIVE:
       peak = 4e12;
@@ -173,59 +187,95 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
       // kernel is bound by that chain's latency (~60 ns per step measured)
       ovh_us += K * 0.06;
       break;
-    case COMPAR_V_SIMT:
-      if (m <= 64 && n >= 256 && n % 4 == 0) {
+    case COMPAR_V_SIMT: {
+      GemmCall g;  // contiguous operands at aligned addresses
+      g.m = m;
+      g.n = n;
+      g.k = k;
+      g.lda = k;
+      g.ldb = n;
+      g.ldc = n;
+      g.dtype = static_cast<compar_dtype_t>(dtype);
+      const SimtPlan pl = simt_plan(g, num_sms);
+      if (pl.skinny) {
         // the skinny-M plan: B streamed once (~4.5 TB/s measured on long
         // chunks) overlapping FMAs on the rows padded to 8 or 16 (~30 TF/s)
         const double mp = m <= 8 ? 8.0 : std::ceil(M / 16) * 16;
         return 1e-3 * (8 + 1e6 * std::max(K * N * in_elem / 4.5e12, 2 * mp * N * K / 30e12));
       }
-      peak = 45e12;
-      flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
+      // the tiled plan: bm x bn tiles times the splits of K in full waves,
+      // each unit k_per long (32-row tiles run at a lower FMA rate)
+      peak = pl.bm == 32 ? 35e12 : 45e12;
+      const double units = std::ceil(M / pl.bm) * std::ceil(N / pl.bn) * pl.splits;
+      flops = 2.0 * std::ceil(units / num_sms) * num_sms * pl.bm * pl.bn *
+              static_cast<double>(pl.k_per);
+      if (pl.splits > 1) ovh_us += 4;  // the reduce launch
       break;
-    case COMPAR_V_TC_TF32:
+    }
+    case COMPAR_V_TC_TF32: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 0.8e15;
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += K * N * 8;
-      ovh_us = 12;
+      ovh_us += 8;
       break;
-    case COMPAR_V_TC_BF16:
+    }
+    case COMPAR_V_TC_BF16: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 1.5e15;
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (dtype == COMPAR_F32 ? (M * K + K * N) * 6 : K * N * 4);
-      ovh_us = 14;
+      ovh_us += 10;
       break;
-    case COMPAR_V_TC_FP8:
+    }
+    case COMPAR_V_TC_FP8: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 3.0e15;
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (dtype == COMPAR_F32 ? (M * K + K * N) * 9 : K * N * 2);
-      ovh_us = dtype == COMPAR_F32 ? 24 : 14;
+      ovh_us += dtype == COMPAR_F32 ? 20 : 10;
       break;
-    case COMPAR_V_SPLIT3:
+    }
+    case COMPAR_V_SPLIT3: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 1.5e15 / 3;
-      flops = 2.0 * tiles(128, 128) * 128 * 128 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (M * K + K * N) * 8;
-      ovh_us = 14;
+      ovh_us += 10;
       break;
-    case COMPAR_V_SPLIT3_FUSED:
+    }
+    case COMPAR_V_SPLIT3_FUSED: {
       // no pre-pass: float32 operands read by the GEMM kernel itself
+      double ke;
+      const double u = tc_units(&ke);
       peak = 1.5e15 / 3;
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (M * K + K * N) * 4;
-      ovh_us = 8;
+      ovh_us += 4;
       break;
-    case COMPAR_V_SPLIT6:
+    }
+    case COMPAR_V_SPLIT6: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 1.5e15 / 6;
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (M * K + K * N) * 10;
-      ovh_us = 16;
+      ovh_us += 12;
       break;
-    case COMPAR_V_SPLIT3_TF32:
+    }
+    case COMPAR_V_SPLIT3_TF32: {
+      double ke;
+      const double u = tc_units(&ke);
       peak = 1.5e15 / 2 / 3;  // three products at the TF32 rate
-      flops = 2.0 * tiles(128, 256) * 128 * 256 * K;
+      flops = 2.0 * u * 128 * 256 * ke;
       bytes += (M * K + K * N) * 12;
-      ovh_us = 16;
+      ovh_us += 12;
       break;
+    }
     default:
       return INFINITY;
   }
