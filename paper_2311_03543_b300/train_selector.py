@@ -6,7 +6,7 @@ on the GPU, and write a selector file.
 Training contexts are the shapes of the three GEMM workloads: the 256^3
 product, the FP32-accuracy size sweep (square n = 64..8192 step 64 plus
 4096x4096x64 and 16x4096x4096) and the 4096^3 precision study, each with
-float32, bf16 and E4M3 inputs, plus 1500 seeded random contexts (rectangular
+float32, bf16 and E4M3 inputs, plus 3000 seeded random contexts (rectangular
 shapes; the seed is disjoint from every evaluation set).  The MLP's time
 head learns a correction to the roofline prior, log2(measured / prior), so
 far from its data it falls back towards the prior.  For every context and
@@ -29,7 +29,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def training_contexts(random_count=1500):
+def training_contexts(random_count=3000):
     """The three workloads' shapes for every dtype, plus seeded random
     contexts (M, N, K log-uniform in [16, 8192], seed disjoint from any
     evaluation set) so that rectangular shapes are seen too."""
@@ -107,12 +107,12 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2311_03543_b300",
                                                   "selector_default.bin"))
-    ap.add_argument("--reps", type=int, default=12)
+    ap.add_argument("--reps", type=int, default=16)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--budget-s", type=float, default=None)
-    ap.add_argument("--random-count", type=int, default=1500,
+    ap.add_argument("--random-count", type=int, default=3000,
                     help="seeded random training contexts added to the workloads' shapes")
     ap.add_argument("--stencil-count", type=int, default=150,
                     help="seeded stencil training contexts (grids 64-8192, 1-1000 steps)")
