@@ -243,7 +243,9 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     G.M = static_cast<int>(p.m);
     G.N = static_cast<int>(p.n);
     G.K = static_cast<int>(p.k);
-    const int kelems = kGroupedRow / P.elem;
+    // the BF16 mode (0) takes K blocks of twice the depth (128-byte rows)
+    const int row_bytes = P.mode == 0 ? 2 * kGroupedRow : kGroupedRow;
+    const int kelems = row_bytes / P.elem;
     G.num_kb = static_cast<int>((p.k + kelems - 1) / kelems);
     G.tiles_m = static_cast<int>((p.m + 127) / 128);
     G.tiles_n = static_cast<int>((p.n + bn - 1) / bn);
@@ -260,14 +262,14 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     uint8_t* aw = ws + P.off_a;
     const void* a_src = P.a_in_place ? p.A : aw;
     const int64_t a_ld = P.a_in_place ? p.lda : P.ldk;
-    rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128, kGroupedRow);
+    rc = tma_encode_2d(&G.map_a, dt, P.elem, a_src, p.k, p.m, a_ld, kelems, 128, row_bytes);
     if (rc == COMPAR_OK) {
       if (P.mode == 2) {  // K-major copy of B: N rows of K
         rc = tma_encode_2d(&G.map_b, dt, P.elem, bw, p.k, p.n, P.ldk, kelems, bn, kGroupedRow);
-      } else {            // B as K rows of N: 64-column x 64-row boxes
+      } else {            // B as K rows of N: boxes of 64 columns x one K block
         const void* b_src = P.b_in_place ? p.B : bw;
         const int64_t b_ld = P.b_in_place ? p.ldb : P.ldn;
-        rc = tma_encode_2d(&G.map_b, dt, 2, b_src, p.n, p.k, b_ld, 64, kGroupedRow / 2);
+        rc = tma_encode_2d(&G.map_b, dt, 2, b_src, p.n, p.k, b_ld, 64, kelems);
       }
     }
     if (rc == COMPAR_OK && P.pieces == 2) {

@@ -42,6 +42,17 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpi = 32 * kEpiWarps;
 constexpr int kMnBox = 64 * kRow;  // one MN-major B box: 64 columns x kRow/2 K rows of bf16
 constexpr int kChunkKB = 512 / kRow;  // promotion every 256 bf16 K elements
+// The BF16 mode has one piece per operand, so it fills a stage's hi and lo
+// regions with one K block of twice the depth: 128-byte rows (128-byte
+// swizzle), A as one 128-row box, B as 64-column x 64-row boxes.  A stage
+// then carries four MMAs for the same TMA instructions and handshakes, as
+// in the single-call BF16 kernel (with 64-byte rows the mode ran at half
+// that kernel's rate on the same problem).
+constexpr int kRowWide = 2 * kRow;
+constexpr int kMnBoxWide = 64 * kRowWide;
+__host__ __device__ constexpr int grouped_chunk_kb(int mode) {
+  return mode == 0 ? kChunkKB / 2 : kChunkKB;  // K blocks per 256 K elements
+}
 constexpr int kMaxIndexed = 4096;  // batches up to this size search a shared-memory index
 
 template <int BN>
@@ -184,10 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const GroupProblem& P = probs[cur.q];
       const int mb = cur.local % cur.tiles_m, nb = cur.local / cur.tiles_m;
+      const bool wide = cur.mode == 0;  // one deep K block fills the stage
       const int pieces = cur.mode == 1 ? 2 : 1;
-      const uint32_t tx = static_cast<uint32_t>(pieces * (L::kA + L::kB));
+      const uint32_t tx = static_cast<uint32_t>((wide ? 2 : pieces) * (L::kA + L::kB));
       const bool tf32 = cur.mode == 2;
-      const int kelems = tf32 ? kRow / 4 : kRow / 2;
+      const int kelems = tf32 ? kRow / 4 : (wide ? kRowWide / 2 : kRow / 2);
       const int num_kb = cur.num_kb;
       for (int kb = 0; kb < num_kb; ++kb) {
         if (!dev::mbar_wait(&empty[stage], phase ^ 1, w)) {
@@ -201,6 +213,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (pieces == 2) dev::tma_load_2d(st + L::kA, &P.map_a2, &full[stage], x, mb * kBM);
         if (tf32) {
           dev::tma_load_2d(st + 2 * L::kA, &P.map_b, &full[stage], x, nb * BN);
+        } else if (wide) {
+#pragma unroll
+          for (int h = 0; h < BN / 64; ++h)
+            dev::tma_load_2d(st + 2 * L::kA + h * kMnBoxWide, &P.map_b, &full[stage],
+                             nb * BN + h * 64, x);
         } else {
 #pragma unroll
           for (int h = 0; h < BN / 64; ++h) {
@@ -238,8 +255,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         nxt = tile_info(probs, s_start, count, tile + gridDim.x);
       const int mode = cur.mode;
       const int num_kb = cur.num_kb;
+      const int ckb = grouped_chunk_kb(mode);
       cur = nxt;
-      for (int kb0 = 0; ok && kb0 < num_kb; kb0 += kChunkKB, ++acc_iter) {
+      for (int kb0 = 0; ok && kb0 < num_kb; kb0 += ckb, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
           ok = false;
@@ -247,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         dev::tc_fence_after();
         const uint32_t d = tmem_base + acc * BN;
-        const int kb_end = min(num_kb, kb0 + kChunkKB);
+        const int kb_end = min(num_kb, kb0 + ckb);
         for (int kb = kb0; kb < kb_end; ++kb) {
           if (!dev::mbar_wait(&full[stage], phase, w)) {
             ok = false;
@@ -255,6 +273,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           dev::tc_fence_after();
           const uint32_t s0 = dev::smem_u32(smem + stage * L::kStage);
+          if (mode == 0) {
+            // one 64-deep K block: A K-major in 128-byte rows, B MN-major in
+            // 64-column x 64-row boxes; four MMAs of 16 K rows
+            const uint64_t dw = dev::smem_desc_kmajor<kRowWide>(s0);
+#pragma unroll
+            for (int kk = 0; kk < kRowWide / 32; ++kk) {
+              const uint64_t ko = static_cast<uint64_t>(kk * 32) >> 4;
+              const uint64_t db =
+                  dev::smem_desc_sw128_mnmajor(s0 + 2 * L::kA + kk * 2048, kMnBoxWide);
+              dev::mma<Kind::F16>(d, dw + ko, db, id_f16, (kb == kb0 && kk == 0) ? 0u : 1u);
+            }
+            dev::mma_commit(&empty[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+            continue;
+          }
           const uint64_t da = dev::smem_desc_kmajor<kRow>(s0);
           const uint64_t da2 = dev::smem_desc_kmajor<kRow>(s0 + L::kA);
 #pragma unroll
@@ -266,15 +302,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t db = dev::smem_desc_kmajor<kRow>(s0 + 2 * L::kA);
               dev::mma<Kind::TF32>(d, da + ko, db + ko, id_tf32, first);
             } else {
-              // B (MN-major): 16 K rows per instruction, 2048 bytes
+              // 3xBF16; B (MN-major): 16 K rows per instruction, 2048 bytes
               const uint32_t bk = s0 + 2 * L::kA + kk * 2048;
               const uint64_t db = dev::smem_desc_sw128_mnmajor(bk, kMnBox);
+              const uint64_t db2 = dev::smem_desc_sw128_mnmajor(bk + L::kB, kMnBox);
               dev::mma<Kind::F16>(d, da + ko, db, id_f16, first);
-              if (mode == 1) {
-                const uint64_t db2 = dev::smem_desc_sw128_mnmajor(bk + L::kB, kMnBox);
-                dev::mma<Kind::F16>(d, da + ko, db2, id_f16, 1u);
-                dev::mma<Kind::F16>(d, da2 + ko, db, id_f16, 1u);
-              }
+              dev::mma<Kind::F16>(d, da + ko, db2, id_f16, 1u);
+              dev::mma<Kind::F16>(d, da2 + ko, db, id_f16, 1u);
             }
           }
           dev::mma_commit(&empty[stage]);
@@ -317,7 +351,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int j = 0; j < 4 * J; ++j) sum[h][j] = 0.f;
-      const int chunks = (num_kb + kChunkKB - 1) / kChunkKB;
+      const int ckb = grouped_chunk_kb(t.mode);
+      const int chunks = (num_kb + ckb - 1) / ckb;
       for (int ch = 0; ch < chunks; ++ch, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tfull[acc], acc_phase, w)) {
