@@ -93,7 +93,7 @@ template <>
 struct Traits<COMPAR_V_SPLIT3> {
   static constexpr Kind kind = Kind::F16;
   static constexpr int elem = 2, fmt = 1, pieces = 2, BN = 256, row = 64, chunk_kb = 8, epi = 8;
-  static constexpr bool b_mn = false, small_first = false, fused = false;
+  static constexpr bool b_mn = true, small_first = false, fused = false;
 };
 // Fused 3xBF16: a stage holds the float32 A tile (128 rows x 32 K, 16 KB)
 // and B tile (32 K x 256 N in 16 boxes of 64 N x 8 K, 32 KB) as TMA wrote
@@ -1336,7 +1336,7 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const bool a_in_place = a_native && tma_operand_ok(c.A, c.lda, elem);
   const bool fp8_from_f32 = (v == COMPAR_V_TC_FP8 && c.dtype == COMPAR_F32);
   // (MN-major B measured slower for the split variants' 64-byte stages)
-  const bool b_mn = (v == COMPAR_V_TC_BF16);
+  const bool b_mn = (v == COMPAR_V_TC_BF16 || v == COMPAR_V_SPLIT3);
   const int64_t ldn = round_up(c.n, 8);  // MN-major copies: 16-byte rows
   const bool b_in_place = b_mn && c.dtype == COMPAR_BF16 && tma_operand_ok(c.B, c.ldb, 2);
 
