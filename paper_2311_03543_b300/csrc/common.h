@@ -143,7 +143,7 @@ int launch_record_gate(const unsigned int* flag_dev, unsigned int ticket, cudaSt
 // Pre-pass kernels (prepass.cu).
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols,
                     int64_t ldx, void* Y, int out_kind, int64_t ldy, bool transpose,
-                    void* Y_lo, const float* dscale, cudaStream_t s);
+                    void* Y_lo, const float* dscale, int num_sms, cudaStream_t s);
 // amax(|X|) and amax(|Y|) (float bits, d_amax_bits[0..1]) in one launch.
 int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
                   int64_t yc, int64_t ldy, unsigned int* d_amax_bits, int num_sms,

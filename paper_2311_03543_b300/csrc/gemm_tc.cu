@@ -1404,14 +1404,14 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   } else {
     // B: K x N row-major -> K x N pieces (MN-major) or N x K (K-major)
     rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldb_op, !b_mn,
-                         pieces >= 2 ? wb + b_bytes : nullptr, sb, s);
+                         pieces >= 2 ? wb + b_bytes : nullptr, sb, num_sms, s);
     if (rc != COMPAR_OK) return rc;
   }
   const void* A = c.A;
   int64_t lda = c.lda;
   if (!a_in_place) {
     rc = prepass_convert(c.A, c.dtype, c.m, c.k, c.lda, wa, out_kind, ldk, false,
-                         pieces >= 2 ? wa + a_bytes : nullptr, sa, s);
+                         pieces >= 2 ? wa + a_bytes : nullptr, sa, num_sms, s);
     if (rc != COMPAR_OK) return rc;
     A = wa;
     lda = ldk;

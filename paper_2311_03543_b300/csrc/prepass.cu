@@ -195,19 +195,39 @@ __device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], v
   }
 }
 
-// Y[r][c..c+7] = f(X[r][c..c+7]); requires cols % 8 == 0, 16-byte aligned rows.
+// Row-wise convert of float32 rows (8 elements per group, 16-byte aligned):
+// each thread takes kRowUnroll groups of one row, 256 groups apart, and
+// issues all their loads before its stores, so that 128 bytes per thread
+// are in flight; rows are dealt to the blocks of a resident-sized grid.
+constexpr int kRowUnroll = 4;
 __global__ void convert_rows_vec8_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
                                          int64_t ldx, void* __restrict__ Y, void* __restrict__ Ylo,
                                          int64_t ldy, int kind, const float* __restrict__ dscale) {
   const float s = dscale ? *dscale : 1.f;
   const int64_t groups = cols / 8;
+  const int64_t span = static_cast<int64_t>(blockDim.x) * kRowUnroll;  // groups per block pass
   for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-    for (int64_t gi = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; gi < groups;
-         gi += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      const float4* src = reinterpret_cast<const float4*>(X + r * ldx + gi * 8);
-      const float4 a = __ldg(src), b = __ldg(src + 1);
-      const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-      store8(kind, s, x, Y, Ylo, r * ldy + gi * 8);
+    const float* xr = X + r * ldx;
+    for (int64_t g0 = blockIdx.x * span + threadIdx.x; g0 < groups;
+         g0 += static_cast<int64_t>(gridDim.x) * span) {
+      float4 a[kRowUnroll], b[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const int64_t gi = g0 + u * static_cast<int64_t>(blockDim.x);
+        if (gi < groups) {
+          const float4* src = reinterpret_cast<const float4*>(xr + gi * 8);
+          a[u] = __ldg(src);
+          b[u] = __ldg(src + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const int64_t gi = g0 + u * static_cast<int64_t>(blockDim.x);
+        if (gi < groups) {
+          const float x[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+          store8(kind, s, x, Y, Ylo, r * ldy + gi * 8);
+        }
+      }
     }
   }
 }
@@ -588,7 +608,7 @@ int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles,
 
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols, int64_t ldx,
                     void* Y, int out_kind, int64_t ldy, bool transpose, void* Y_lo,
-                    const float* dscale, cudaStream_t s) {
+                    const float* dscale, int num_sms, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return COMPAR_OK;
   const dim3 tb(32, 8);
   const dim3 tg(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
@@ -611,9 +631,13 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
     }
     if (!transpose && cols % 8 == 0 && ldx % 4 == 0 && xa % 16 == 0 && ldy % 8 == 0 &&
         ya % 16 == 0 && la % 16 == 0) {
+      // blocks across a row cover it in passes of 256 x kRowUnroll groups;
+      // rows are dealt to about eight resident blocks per SM
       const int64_t groups = cols / 8;
-      const dim3 gv(static_cast<unsigned>(std::min<int64_t>((groups + 255) / 256, 64)),
-                    static_cast<unsigned>(std::min<int64_t>(rows, 65535)));
+      const int64_t bx = std::min<int64_t>((groups + 256 * kRowUnroll - 1) / (256 * kRowUnroll), 64);
+      const int64_t by = std::max<int64_t>(1, std::min<int64_t>(rows, std::min<int64_t>(
+                                                  65535, (8 * static_cast<int64_t>(num_sms) + bx - 1) / bx)));
+      const dim3 gv(static_cast<unsigned>(bx), static_cast<unsigned>(by));
       convert_rows_vec8_kernel<<<gv, 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, kind, dscale);
       COMPAR_CUDA_TRY(cudaGetLastError());
       count_launch();
