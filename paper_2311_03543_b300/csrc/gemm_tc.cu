@@ -148,6 +148,8 @@ struct Layout {
   static constexpr int kEpiThreads = 32 * T::epi;
   static constexpr int kEpiCols = BN * 4 / T::epi;  // columns one epilogue warp handles
   static_assert(kStages >= 2, "pipeline needs two stages");
+  static_assert(kPair || kStages * kStageBytes >= kBM * BN * 4,
+                "an in-cluster K split stages a kBM x BN float tile in the ring");
   static_assert(kTmemCols <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM columns");
   static_assert(T::epi % 4 == 0 && kEpiCols % 32 == 0, "epilogue split");
 };
@@ -157,9 +159,13 @@ struct TcArgs {
   int num_kb;
   int tiles_m, tiles_n;
   // Split K (few tiles, long K): work unit u = tile u / splits, K blocks
-  // [(u % splits) * kb_per_split, +kb_per_split); each unit writes
-  // alpha * partial to partial[split][M][N] and a reduce kernel forms C.
+  // [(u % splits) * kb_per_split, +kb_per_split).  With split_cluster the
+  // splits of a tile are one thread-block cluster (split = rank in it) that
+  // adds its accumulators through distributed shared memory; otherwise each
+  // unit writes alpha * partial to partial[split][M][N] and a reduce kernel
+  // forms C.
   int splits, kb_per_split;
+  int split_cluster;
   float* partial;
   // Work list of a CTA: the `dp_units` classic units (whole tiles, or tile x
   // K-split units when splits > 1) dealt round-robin, then, when sk_q > 0, a
@@ -425,6 +431,100 @@ __device__ __forceinline__ bool sk_count_and_sum(const TcArgs& p, const SkPiece&
   return true;
 }
 
+// ------------------------------------------------------------------ in-cluster split K
+// The kernel's shared-memory ring: dynamic shared memory rounded up to 1 KB.
+__device__ __forceinline__ uint8_t* ring_base() {
+  extern __shared__ uint8_t smem_raw[];
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                    ~static_cast<uintptr_t>(1023));
+}
+
+// Stages one fragment of raw accumulator values in this CTA's split-K
+// staging buffer (its idle ring), float4 slot (f * 8 + j4) * kEpiThreads +
+// epilogue thread: a warp writes 512 contiguous bytes.
+template <int kEpiThreads>
+__device__ __forceinline__ void stage_frag(float4* staging, int f, const float (&v)[32],
+                                           int etid) {
+#pragma unroll
+  for (int j4 = 0; j4 < 8; ++j4)
+    staging[(f * 8 + j4) * kEpiThreads + etid] =
+        make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+}
+
+// The cluster's CTAs are the K splits of one tile, each with its accumulator
+// staged.  This CTA (rank r) takes the float4 slots r, r + NS, ... of every
+// epilogue thread position, adds the NS splits' values in split order (the
+// same sum whichever CTA computes it), and stores alpha * sum (+ beta C)
+// with the thread position's row and column mapping.  G slots at a time, so
+// that G * NS (<= 16) distributed-shared-memory loads are in flight.
+template <int NS, int NF, int kEpiThreads, int EC, int BN>
+__device__ __forceinline__ void cluster_split_sum_n(const TcArgs& p, const float4* staging,
+                                                    int etid, int warp, int lane, int mb, int nb,
+                                                    float alpha) {
+  constexpr int G = 16 / NS;
+  constexpr int kSlots = NF * 8;
+  auto cl = cooperative_groups::this_cluster();
+  const int r = static_cast<int>(cl.block_rank());
+  const int row_q = mb * kBM + (warp & 3) * 32;
+  const int col_s = nb * BN + ((warp - 2) / 4) * EC;
+  if (row_q >= p.M || col_s >= p.N) return;
+  const bool vec2 = (p.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(p.C) & 7) == 0);
+  const float4* src[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) src[s] = cl.map_shared_rank(staging, s);
+#pragma unroll 1
+  for (int q0 = r; q0 < kSlots; q0 += G * NS) {
+    float4 c[G][NS];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int q = q0 + g * NS;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (q < kSlots) c[g][s] = src[s][q * kEpiThreads + etid];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int q = q0 + g * NS;
+      if (q >= kSlots) break;
+      float4 a = c[g][0];
+#pragma unroll
+      for (int s = 1; s < NS; ++s) {
+        a.x += c[g][s].x;
+        a.y += c[g][s].y;
+        a.z += c[g][s].z;
+        a.w += c[g][s].w;
+      }
+      const float v[4] = {a.x, a.y, a.z, a.w};
+      const int f = q >> 3, j4 = q & 7;
+      store_frag<1>(v, p.C, p.ldc, p.M, p.N, row_q + 16 * (f & 1),
+                    col_s + 64 * (f >> 1) + 8 * j4, alpha, p.beta, vec2, lane);
+    }
+  }
+}
+
+// The sum above for the cluster's size (2 to 8 splits).
+template <int NF, int kEpiThreads, int EC, int BN>
+__device__ __forceinline__ void cluster_split_sum(const TcArgs& p, const float4* staging,
+                                                  int etid, int warp, int lane, int mb, int nb,
+                                                  float alpha) {
+  switch (p.splits) {
+#define COMPAR_SPLIT_SUM(ns)                                                                  \
+  case ns:                                                                                    \
+    cluster_split_sum_n<ns, NF, kEpiThreads, EC, BN>(p, staging, etid, warp, lane, mb, nb, \
+                                                     alpha);                                \
+    break;
+    COMPAR_SPLIT_SUM(2)
+    COMPAR_SPLIT_SUM(3)
+    COMPAR_SPLIT_SUM(4)
+    COMPAR_SPLIT_SUM(5)
+    COMPAR_SPLIT_SUM(6)
+    COMPAR_SPLIT_SUM(7)
+    COMPAR_SPLIT_SUM(8)
+#undef COMPAR_SPLIT_SUM
+    default: break;
+  }
+}
+
 // End of a promoted item in the epilogue: stores the tile from `sum` (a
 // classic unit, or a stream-K tile with one contributor) or publishes this
 // CTA's stream-K piece and takes part in the count-and-sum.  `sum` is not
@@ -438,6 +538,12 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
                                                 float* out, int64_t out_ld, int row_q, int col_s,
                                                 float alpha, float beta, bool vec_out) {
   const SkPiece sp = sk_piece(p, it);
+  if (p.split_cluster) {  // an in-cluster K split: the cluster adds the sums
+    float4* staging = reinterpret_cast<float4*>(ring_base());
+#pragma unroll
+    for (int f = 0; f < NF; ++f) stage_frag<kEpiThreads>(staging, f, sum[f], etid);
+    return true;
+  }
   if (sp.nc == 1) {
     if (row_q < p.M && col_s < p.N) {
 #pragma unroll
@@ -480,9 +586,7 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
   constexpr int S = L::kStages;
   constexpr int kChunkKB = T::chunk_kb;
 
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* smem = ring_base();
   uint8_t* sA = smem;                              // [S][P][kABytes]
   uint8_t* sB = smem + S * P * L::kABytes;         // [S][P][kBBytes]
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * P * L::kBBytes);
@@ -949,7 +1053,11 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-        if (row_q < p.M && col_s < p.N)
+        // an in-cluster K split stages the accumulator in the ring, idle by
+        // now (a CTA of a K split has one item: no copy or MMA is left)
+        if (p.split_cluster)
+          stage_frag<L::kEpiThreads>(reinterpret_cast<float4*>(ring_base()), f, v, etid);
+        else if (row_q < p.M && col_s < p.N)
           store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
                           alpha, beta, vec_out, lane);
       }
@@ -958,6 +1066,25 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
   }
 
   __syncthreads();
+  if constexpr (!kPair) {
+    if (p.split_cluster) {
+      // every CTA of the cluster has staged its split (or given up: the sum
+      // is then wrong, and the error word says so)
+      dev::cluster_sync();
+      if (warp >= 2 && get_item<kChunkKB>(p, 0, it)) {
+        int mb, nb;
+        tile_coords(it.tile, p.tiles_m, p.tiles_n, mb, nb);
+        float alpha = p.alpha;
+        if (p.dequant_a) alpha *= *p.dequant_a;
+        if (p.dequant_b) alpha *= *p.dequant_b;
+        constexpr int EC = L::kEpiCols;
+        cluster_split_sum<2 * (EC / 64), L::kEpiThreads, EC, BN>(
+            p, reinterpret_cast<const float4*>(sA), static_cast<int>(threadIdx.x) - 64, warp,
+            lane, mb, nb, alpha);
+      }
+      dev::cluster_sync();  // no CTA leaves while a peer still reads its staging
+    }
+  }
   // a pair frees its tensor memory together, once both CTAs are done (the
   // even CTA has drained every MMA writing into the odd CTA's columns)
   if constexpr (kPair) dev::cluster_sync();
@@ -1100,9 +1227,11 @@ TcPlan tc_plan(int v, const GemmCall& c, int slots, bool pair = false) {
   return p;
 }
 
-// Launch configuration of the kernel: clusters of 2 for CTA pairs.
+// Launch configuration of the kernel: clusters of 2 for CTA pairs, of
+// `cluster` CTAs for an in-cluster K split.
 template <int V, bool kPair>
-cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribute* attr) {
+cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribute* attr,
+                                    int cluster = 1) {
   using L = Layout<V, kPair>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1110,12 +1239,35 @@ cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribut
   cfg.dynamicSmemBytes = L::kSmemBytes;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kPair ? 2 : 1;
+  attr[0].val.clusterDim.x = kPair ? 2 : cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = kPair ? 1 : 0;
+  cfg.numAttrs = (kPair || cluster > 1) ? 1 : 0;
   return cfg;
+}
+
+// Largest in-cluster K split (portable cluster size).
+constexpr int kMaxSplitCluster = 8;
+
+// Clusters of `cs` single CTAs of variant V that can be resident at once
+// (queried once per size; 0 when the query fails).
+template <int V>
+int tc_split_cluster_capacity(int cs) {
+  static std::once_flag once[kMaxSplitCluster + 1];
+  static int cap[kMaxSplitCluster + 1] = {};
+  if (cs < 2 || cs > kMaxSplitCluster) return 0;
+  std::call_once(once[cs], [cs] {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_launch_config<V, false>(cs, nullptr, attr, cs);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<V, false>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    cap[cs] = n;
+  });
+  return cap[cs];
 }
 
 // Shared-memory opt-in of the kernel, once; for pairs also the number of
@@ -1226,15 +1378,25 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
     COMPAR_CUDA_TRY(cudaMemsetAsync(
         sk_count, 0, sizeof(unsigned int) * (units - plan.sk_tile0) * a.pair, s));
   }
+  // K splits of a tile as one cluster when every cluster of the call can be
+  // resident at once (one unit per CTA); otherwise partials and a reduce
+  int cluster = 1;
+  if constexpr (!kPair) {
+    if (a.splits > 1 && a.splits <= kMaxSplitCluster && plan.sk_q == 0 && units <= slots &&
+        tc_split_cluster_capacity<V>(a.splits) * a.splits >= units) {
+      cluster = a.splits;
+      a.split_cluster = 1;
+    }
+  }
   cudaLaunchAttribute attr[1];
-  const cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(grid * a.pair, s, attr);
+  const cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(grid * a.pair, s, attr, cluster);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   COMPAR_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<V, kPair>, ta, tb, ta2, tb2, ta3, tb3,
                                      a));
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();
   // the split units already applied alpha (and the dequantisation)
-  if (a.splits > 1)
+  if (a.splits > 1 && !a.split_cluster)
     return launch_splitk_reduce(a.M, a.N, a.splits, partial, 1.f, c.beta, c.C, c.ldc, slots, s);
   return COMPAR_OK;
 }

@@ -259,6 +259,45 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
     assert N.rel_frobenius(got, ref) <= tol
 
 
+_KELEMS = {2: 32, 3: 64, 4: 128, 5: 32, 9: 32}
+
+
+@pytest.mark.parametrize("splits", [2, 3, 5, 7, 8])
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 9])
+def test_k_split_summed_in_cluster(ctx, v, splits):
+    """Four ragged tiles (200 x 300) with K = 8 * splits K blocks: the plan
+    splits K `splits` ways and the splits of a tile, one thread-block cluster,
+    add their accumulators through distributed shared memory (every slot of
+    the tile shared out over the cluster's CTAs, odd cluster sizes included).
+    Small integers are exact in every format, so a split counted twice or
+    not at all, or a slot stored at the wrong element, changes the result."""
+    import paper_2311_03543_b300 as cp
+    m, n, k = 200, 300, _KELEMS[v] * 8 * splits
+    assert cp.Context.tc_plan(v, m, n, k, 148)["splits"] == splits
+    A = W.integer_matrix(m, k, seed=61, bound=2)
+    B = W.integer_matrix(k, n, seed=62, bound=2)
+    C0 = W.integer_matrix(m, n, seed=63)
+    got = _run(ctx, v, A, B, alpha=2.0, beta=-0.5, C0=C0)
+    ref = oracle.gemm(A, B, alpha=2.0, beta=-0.5, C0=C0)
+    if v == 4:   # the fp8 scales of float32 inputs are not powers of two
+        assert N.rel_frobenius(got, ref) <= 1e-3
+    else:
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("v", [5, 9])
+def test_k_split_in_cluster_normal_data(ctx, v):
+    """The in-cluster K split on normal data (five splits): element by element
+    within the variant's bound of the oracle."""
+    from gpu_util import assert_elementwise, elem_bound
+    m, n, k = 250, 500, 32 * 8 * 5
+    A = W.normal(m, k, seed=64); B = W.normal(k, n, seed=65)
+    got = _run(ctx, v, A, B)
+    ref = oracle.gemm(A, B)
+    assert N.rel_frobenius(got, ref) <= TOL_F32
+    assert_elementwise(got, ref, oracle.gemm(np.abs(A), np.abs(B)), elem_bound(v, k))
+
+
 @pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8, 9])
 def test_partial_last_wave_with_alpha_beta(ctx, v, pairs):
