@@ -1,11 +1,15 @@
 // Epilogue stores shared by the tensor-core kernels: fragments of the
 // accumulator as tcgen05.ld 16x256b delivers them (ptx.cuh), written to C
-// with whole 32-byte sectors per row and instruction.
+// with whole 32-byte sectors per row and instruction, or staged in shared
+// memory and written by TMA bulk-tensor stores.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+
+#include "ptx.cuh"
 
 namespace compar {
 
@@ -42,6 +46,48 @@ __device__ __forceinline__ void store_frag(const float (&v)[4 * J], float* C, in
         if (col + 1 < N) crow[col + 1] = beta != 0.f ? fmaf(beta, crow[col + 1], b) : b;
       }
     }
+  }
+}
+
+// TMA-store epilogue: each epilogue warp owns two 2 KB staging boxes (16
+// rows x 32 float columns, 128-byte rows in the 128-byte swizzle: 16-byte
+// chunk c of row r sits at chunk c ^ (r % 8)).  Stores the 16-row x
+// 64-column fragment of store_frag's register layout as alpha * v, box by
+// box: wait until the box's previous store has read it, write it (each
+// float2 row pair lands in distinct banks: two wavefronts a store), make it
+// visible to the async proxy, and lane 0 issues the bulk-tensor store.
+// Boxes that start past the matrix are skipped; the tensor map clips the
+// rest.  `nbox` counts the warp's boxes (buffer nbox & 1).
+__device__ __forceinline__ void tma_store_frag(const CUtensorMap* tmC, uint8_t* stage,
+                                               uint32_t& nbox, const float (&v)[32], int row0,
+                                               int col0, int M, int N, float alpha, int lane) {
+  if (row0 >= M) return;
+  const int rq = lane >> 2;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int cb0 = col0 + 32 * b;
+    if (cb0 >= N) break;
+    uint8_t* buf = stage + (nbox & 1u) * 2048u;
+    if (lane == 0) dev::bulk_wait_read<1>();
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * b + jj;
+      const int c = 2 * jj + ((lane & 3) >> 1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = rq + 8 * h;
+        *reinterpret_cast<float2*>(buf + r * 128 + ((c ^ rq) << 4) + ((lane & 1) << 3)) =
+            make_float2(alpha * v[4 * j + 2 * h], alpha * v[4 * j + 2 * h + 1]);
+      }
+    }
+    dev::fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      dev::tma_store_2d(tmC, buf, cb0, row0);
+      dev::bulk_commit();
+    }
+    ++nbox;
   }
 }
 

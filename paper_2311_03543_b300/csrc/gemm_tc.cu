@@ -133,7 +133,14 @@ struct Layout {
   static constexpr int kBarBytes = 256;
   static constexpr int kStagesRaw = (kMaxSmem - 1024 - kBarBytes) / kStageBytes;
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
-  static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes;
+  static constexpr int kRingBytes = kStages * kStageBytes;
+  // TMA-store epilogue: two 2 KB staging boxes per epilogue warp, where the
+  // ring leaves room for them
+  static constexpr int kEpiWarpBytes = 2 * 2048;
+  static constexpr bool kTmaStore =
+      1024 + kRingBytes + T::epi * kEpiWarpBytes + kBarBytes <= kMaxSmem;
+  static constexpr int kEpiStageBytes = kTmaStore ? T::epi * kEpiWarpBytes : 0;
+  static constexpr int kSmemBytes = 1024 + kRingBytes + kEpiStageBytes + kBarBytes;
   static constexpr int kTmemCols = 2 * BN;  // two accumulators
   static constexpr int kElemsPerStage = T::row / T::elem;
   // MN-major B (16-bit types): boxes of 64 columns x kElemsPerStage K rows,
@@ -180,6 +187,9 @@ struct TcArgs {
   // (blockIdx.x / pair) is then a pair, a tile is 2 kBM x BN, and each CTA
   // of the pair publishes and counts its own kBM rows of a stream-K tile.
   int pair;
+  // 1: whole-tile stores of C go through the TMA-store epilogue (beta == 0,
+  // no K split, C rows 16-byte aligned)
+  int tma_c;
   float alpha, beta;
   const float* dequant_a;  // optional device factors (fp8 of float32 inputs)
   const float* dequant_b;
@@ -536,7 +546,9 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
                                                 uint32_t& epi_uses, volatile int* last_flag,
                                                 const dev::WaitCtx& w, int etid, int lane,
                                                 float* out, int64_t out_ld, int row_q, int col_s,
-                                                float alpha, float beta, bool vec_out) {
+                                                float alpha, float beta, bool vec_out,
+                                                const CUtensorMap* tmC, uint8_t* estage,
+                                                uint32_t& nbox) {
   const SkPiece sp = sk_piece(p, it);
   if (p.split_cluster) {  // an in-cluster K split: the cluster adds the sums
     float4* staging = reinterpret_cast<float4*>(ring_base());
@@ -546,10 +558,17 @@ __device__ __forceinline__ bool finish_promoted(const TcArgs& p, const WorkItem&
   }
   if (sp.nc == 1) {
     if (row_q < p.M && col_s < p.N) {
+      if (estage != nullptr) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
-        store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
-                      alpha, beta, vec_out, lane);
+        for (int f = 0; f < NF; ++f)
+          tma_store_frag(tmC, estage, nbox, sum[f], row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                         p.M, p.N, alpha, lane);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          store_frag<8>(sum[f], out, out_ld, p.M, p.N, row_q + 16 * (f & 1),
+                        col_s + 64 * (f >> 1), alpha, beta, vec_out, lane);
+      }
     }
     return true;
   }
@@ -577,7 +596,8 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
                    const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmB2,
                    const __grid_constant__ CUtensorMap tmA3,
-                   const __grid_constant__ CUtensorMap tmB3, const TcArgs p) {
+                   const __grid_constant__ CUtensorMap tmB3,
+                   const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
   using T = Traits<V>;
   using L = Layout<V, kPair>;
   static_assert(!(kPair && T::fused), "the fused split runs on single CTAs only");
@@ -589,7 +609,8 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
   uint8_t* smem = ring_base();
   uint8_t* sA = smem;                              // [S][P][kABytes]
   uint8_t* sB = smem + S * P * L::kABytes;         // [S][P][kBBytes]
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * P * L::kBBytes);
+  uint8_t* epi_stage = sB + S * P * L::kBBytes;   // [epi warps][2][2 KB] (TMA stores)
+  uint64_t* full = reinterpret_cast<uint64_t*>(epi_stage + L::kEpiStageBytes);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;   // [2]
   uint64_t* tempty = tfull + 2;  // [2]
@@ -629,6 +650,7 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
       dev::tma_prefetch_desc(&tmA3);
       dev::tma_prefetch_desc(&tmB3);
     }
+    if (L::kTmaStore && p.tma_c) dev::tma_prefetch_desc(&tmC);
   }
   if (warp == 1) {
     if constexpr (kPair) {
@@ -875,6 +897,12 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
     const bool vec_out = split ? (p.N % 2 == 0) : vec2;
     const float beta = split ? 0.f : p.beta;
     uint32_t epi_uses = 0;  // completed phases of epi_bar
+    // TMA-store epilogue: this warp's staging boxes (null: plain stores) and
+    // the boxes it has staged so far
+    uint32_t nbox = 0;
+    auto estage = [&]() -> uint8_t* {
+      return L::kTmaStore && p.tma_c ? epi_stage + (warp - 2) * L::kEpiWarpBytes : nullptr;
+    };
     const int etid = threadIdx.x - 64;
     // this warp is done reading accumulator `acc`: every thread arrives, or
     // in a pair one lane per warp on the even CTA's barrier (tcgen05.ld
@@ -962,7 +990,7 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
         float* out = split ? p.partial + static_cast<int64_t>(pit.split) * p.M * p.N : p.C;
         if (!finish_promoted<NF, L::kEpiThreads, BN>(p, pit, sum, epi_bar, epi_uses, last_flag,
                                                      w, etid, lane, out, out_ld, row_q, col_s,
-                                                     alpha, beta, vec_out)) {
+                                                     alpha, beta, vec_out, &tmC, estage(), nbox)) {
           ok = false;
           break;
         }
@@ -1011,7 +1039,7 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
         if (!ok) break;
         if (!finish_promoted<NF, L::kEpiThreads, BN>(p, it, sum, epi_bar, epi_uses, last_flag, w,
                                                      etid, lane, out, out_ld, row_q, col_s,
-                                                     alpha, beta, vec_out)) {
+                                                     alpha, beta, vec_out, &tmC, estage(), nbox)) {
           ok = false;
           break;
         }
@@ -1057,6 +1085,9 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
         // now (a CTA of a K split has one item: no copy or MMA is left)
         if (p.split_cluster)
           stage_frag<L::kEpiThreads>(reinterpret_cast<float4*>(ring_base()), f, v, etid);
+        else if (L::kTmaStore && p.tma_c)
+          tma_store_frag(&tmC, estage(), nbox, v, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
+                         p.M, p.N, alpha, lane);
         else if (row_q < p.M && col_s < p.N)
           store_frag<8>(v, out, out_ld, p.M, p.N, row_q + 16 * (f & 1), col_s + 64 * (f >> 1),
                           alpha, beta, vec_out, lane);
@@ -1065,6 +1096,9 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
     }
   }
 
+  // the TMA-store epilogue's last stores have read their staging boxes (and
+  // are complete) before the CTA can leave
+  if (L::kTmaStore && p.tma_c && warp >= 2 && lane == 0) dev::bulk_wait_all();
   __syncthreads();
   if constexpr (!kPair) {
     if (p.split_cluster) {
@@ -1391,8 +1425,15 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(grid * a.pair, s, attr, cluster);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
+  // C through the TMA-store epilogue where it applies (otherwise tc is an
+  // unused copy of ta)
+  CUtensorMap tc = ta;
+  if (L::kTmaStore && c.beta == 0.f && a.splits == 1 &&
+      tma_encode_2d(&tc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c.C, c.n, c.m, c.ldc, 32, 16, 128) ==
+          COMPAR_OK)
+    a.tma_c = 1;
   COMPAR_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<V, kPair>, ta, tb, ta2, tb2, ta3, tb3,
-                                     a));
+                                     tc, a));
   if (g.prof) g.prof->end(ev, s, V);
   count_launch();
   // the split units already applied alpha (and the dequantisation)
