@@ -222,10 +222,20 @@ def torch_dtype_code(t):
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
-class Context:
-    """A libcompar context bound to one CUDA device (tensor-level API)."""
+# The trained selector shipped with the package (MLP, history table, error
+# models, stencil models), written by train_selector.
+DEFAULT_SELECTOR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_default.bin")
 
-    def __init__(self, device=0, host_only=False, num_sms=148):
+
+class Context:
+    """A libcompar context bound to one CUDA device (tensor-level API).
+
+    `selector`: the selector file loaded at creation — by default the
+    shipped trained selector for a device context and none for a host-only
+    one; None starts from the untrained models (roofline prior only), as a
+    context that trains its own selector must."""
+
+    def __init__(self, device=0, host_only=False, num_sms=148, selector="default"):
         load()
         h = ctypes.c_void_p()
         if host_only:
@@ -234,6 +244,14 @@ class Context:
             _status(compar_init(ctypes.byref(h), device), "compar_init")
         self.handle = h
         self.device = None if host_only else device
+        if selector == "default":
+            selector = None if host_only else DEFAULT_SELECTOR
+        if selector is not None:
+            try:
+                self.selector_load(selector)
+            except BaseException:
+                self.close()
+                raise
 
     @classmethod
     def host(cls, num_sms=148):

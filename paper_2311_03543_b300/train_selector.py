@@ -121,7 +121,7 @@ def main(argv=None):
     import paper_2311_03543_b300 as cp
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    with cp.Context(0) as ctx:
+    with cp.Context(0, selector=None) as ctx:   # trained from its own records only
         ctx.record_enable(True)
         n = collect(ctx, cp, torch, training_contexts(args.random_count), args.reps, dev,
                     budget_s=args.budget_s)

@@ -56,7 +56,7 @@ def _square_selector(path, steps=6000):
     from paper_2311_03543_b300 import train_selector as TS
     sizes = sorted({int(round(16 * 2 ** (8 * i / 17))) for i in range(18)})
     contexts = [(n, n, n, dt) for dt in (W.F32, W.BF16, W.F8E4M3) for n in sizes]
-    with cp.Context(0) as ctx:
+    with cp.Context(0, selector=None) as ctx:
         ctx.record_enable(True)
         TS.collect(ctx, cp, torch, contexts, 4, torch.device("cuda", 0), log=lambda *a: None)
         ctx.selector_train(steps=steps, batch=128, lr=1e-3, seed=1)

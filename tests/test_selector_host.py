@@ -242,3 +242,21 @@ def test_stencil_history_round_trips_through_selector_file(hctx, tmp_path):
             == picks
     finally:
         h2.close()
+
+
+def test_context_loads_a_selector_file_at_creation(tmp_path):
+    """`selector=` loads a file as selector_load does (the shipped selector
+    here, the default of a device context); a missing file is an error."""
+    a = cp.Context(host_only=True, selector=cp.DEFAULT_SELECTOR)
+    b = cp.Context.host()
+    try:
+        b.selector_load(cp.DEFAULT_SELECTOR)
+        for m, n, k, dt, tol in [(4096, 4096, 4096, cp.F32, 1e-5), (512, 512, 512, cp.F32, 1e-5),
+                                 (16, 4096, 4096, cp.F32, 1e-5), (2048, 64, 2048, cp.BF16, 1e-3),
+                                 (1000, 1000, 1000, cp.F8E4M3, 1e-1)]:
+            assert a.select(m, n, k, dt, tol) == b.select(m, n, k, dt, tol)
+    finally:
+        a.close()
+        b.close()
+    with pytest.raises(cp.ComparError):
+        cp.Context(host_only=True, selector=str(tmp_path / "missing.bin"))
