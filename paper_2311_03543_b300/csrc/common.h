@@ -144,6 +144,24 @@ int launch_record_gate(const unsigned int* flag_dev, unsigned int ticket, cudaSt
 int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t cols,
                     int64_t ldx, void* Y, int out_kind, int64_t ldy, bool transpose,
                     void* Y_lo, const float* dscale, int num_sms, cudaStream_t s);
+// One float32 matrix of a row-wise convert: rows x cols of X (pitch ldx)
+// into Y (and Y_lo for the splits; pitch ldy), scaled by *dscale (fp8).
+struct RowConvert {
+  const float* X;
+  int64_t rows, cols, ldx;
+  void* Y;
+  void* Y_lo;
+  int64_t ldy;
+  const float* dscale;
+};
+// Row-wise converts of two float32 matrices (out_kind PP_BF16 or a split)
+// in one launch of the vectorised row kernel, launched programmatically (it
+// waits for the stream's previous kernel before touching memory).
+// COMPAR_ERR_UNSUPPORTED, with nothing launched, when either matrix misses
+// the kernel's rules (cols % 8 == 0, 16-byte rows and bases): the caller
+// then converts them one by one with prepass_convert.
+int prepass_convert_rows2(const RowConvert& a, const RowConvert& b, int out_kind, int num_sms,
+                          cudaStream_t s);
 // amax(|X|) and amax(|Y|) (float bits, d_amax_bits[0..1]) in one launch.
 int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
                   int64_t yc, int64_t ldy, unsigned int* d_amax_bits, int num_sms,

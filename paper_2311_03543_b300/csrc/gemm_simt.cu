@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "common.h"
+#include "ptx.cuh"
 
 namespace compar {
 namespace {
@@ -507,8 +508,11 @@ __global__ void __launch_bounds__(kSkinnyThreads, kSkinnyCtasPerSm)
 
 // C = alpha * sum_s partial[s] + beta * C, the slabs added in order; the
 // loads of up to 8 slabs are issued together so that their latencies overlap.
+// May be launched programmatically after the kernel that writes the slabs.
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
                                      float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  dev::griddep_wait();
+  dev::griddep_launch_dependents();
   constexpr int kBatch = 8;
   const int64_t total = static_cast<int64_t>(M) * N;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
@@ -741,8 +745,17 @@ int launch_splitk_reduce(int m, int n, int splits, const float* partial, float a
   const int64_t total = static_cast<int64_t>(m) * n;
   if (total <= 0) return COMPAR_OK;
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * num_sms));
-  splitk_reduce_kernel<<<blocks, 256, 0, s>>>(m, n, splits, partial, alpha, beta, C, ldc);
-  COMPAR_CUDA_TRY(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  COMPAR_CUDA_TRY(
+      cudaLaunchKernelEx(&cfg, splitk_reduce_kernel, m, n, splits, partial, alpha, beta, C, ldc));
   count_launch();
   return COMPAR_OK;
 }

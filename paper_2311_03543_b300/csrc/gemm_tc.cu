@@ -182,7 +182,10 @@ struct TcArgs {
   int dp_units;
   int sk_tile0, sk_cpt, sk_q, sk_ctas;
   float* sk_slab;               // [sk_ctas * pair][2][kBM * BN] published pieces
-  unsigned int* sk_count;       // [tail tiles * pair] arrivals, zero at launch
+  // [tail tiles * pair] arrival words: (epoch << 32 | count), a word with
+  // another launch's epoch counting as zero (no reset between calls)
+  unsigned long long* sk_count;
+  unsigned int sk_epoch;
   // 1, or 2 when CTA pairs compute the tiles: a "CTA" of the work list
   // (blockIdx.x / pair) is then a pair, a tile is 2 kBM x BN, and each CTA
   // of the pair publishes and counts its own kBM rows of a stream-K tile.
@@ -384,8 +387,20 @@ __device__ __forceinline__ bool sk_count_and_sum(const TcArgs& p, const SkPiece&
   if (etid == 0) {
     __threadfence();
     // in a CTA pair each CTA counts (and sums) its own rows of the tile
-    *last_flag = atomicAdd(p.sk_count + sp.t * p.pair + static_cast<int>(blockIdx.x) % p.pair,
-                           1u) == static_cast<unsigned int>(sp.nc - 1);
+    unsigned long long* cnt =
+        p.sk_count + sp.t * p.pair + static_cast<int>(blockIdx.x) % p.pair;
+    unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(cnt);
+    unsigned int before;
+    for (;;) {  // at most nc contributors contend for one word
+      before = static_cast<unsigned int>(seen >> 32) == p.sk_epoch ? static_cast<unsigned int>(seen)
+                                                                  : 0u;
+      const unsigned long long next =
+          (static_cast<unsigned long long>(p.sk_epoch) << 32) | (before + 1u);
+      const unsigned long long got = atomicCAS(cnt, seen, next);
+      if (got == seen) break;
+      seen = got;
+    }
+    *last_flag = before == static_cast<unsigned int>(sp.nc - 1);
   }
   dev::mbar_arrive(epi_bar);
   if (!dev::mbar_wait(epi_bar, epi_uses++ & 1, w)) return false;
@@ -666,6 +681,9 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
   // a pair's barriers are all initialised before either CTA signals the other's
   if constexpr (kPair) dev::cluster_sync();
   dev::tc_fence_after();
+  // launched programmatically: the set-up above overlapped the stream's
+  // previous kernel (the pre-pass), whose results are read from here on
+  dev::griddep_wait();
   const uint32_t tmem_base = *tmem_slot;
   const uint32_t rank = kPair ? dev::cluster_ctarank() : 0u;
   dev::WaitCtx w{abort_flag, p.err_word, p.budget_ns};
@@ -742,6 +760,9 @@ __global__ void __launch_bounds__(Layout<V, kPair>::kThreads, 1)
         }
       }
     }
+    // every load of this CTA is issued: the stream's next kernel may be
+    // scheduled (it waits for this one to complete before touching memory)
+    dev::griddep_launch_dependents();
     if (!ok) {
       // Let every copy this thread started land before the CTA exits (a
       // pair's copies are all counted on the even CTA's barriers).
@@ -1262,22 +1283,32 @@ TcPlan tc_plan(int v, const GemmCall& c, int slots, bool pair = false) {
 }
 
 // Launch configuration of the kernel: clusters of 2 for CTA pairs, of
-// `cluster` CTAs for an in-cluster K split.
+// `cluster` CTAs for an in-cluster K split; `programmatic`: the kernel may
+// start (and run its set-up) before the stream's previous kernel completes.
+// attr: room for two attributes.
 template <int V, bool kPair>
 cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribute* attr,
-                                    int cluster = 1) {
+                                    int cluster = 1, bool programmatic = false) {
   using L = Layout<V, kPair>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(L::kThreads);
   cfg.dynamicSmemBytes = L::kSmemBytes;
   cfg.stream = s;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kPair ? 2 : cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = (kPair || cluster > 1) ? 1 : 0;
+  cfg.numAttrs = 0;
+  if (kPair || cluster > 1) {
+    attr[cfg.numAttrs].id = cudaLaunchAttributeClusterDimension;
+    attr[cfg.numAttrs].val.clusterDim.x = kPair ? 2 : cluster;
+    attr[cfg.numAttrs].val.clusterDim.y = 1;
+    attr[cfg.numAttrs].val.clusterDim.z = 1;
+    ++cfg.numAttrs;
+  }
+  if (programmatic) {
+    attr[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+    ++cfg.numAttrs;
+  }
   return cfg;
 }
 
@@ -1292,7 +1323,7 @@ int tc_split_cluster_capacity(int cs) {
   static int cap[kMaxSplitCluster + 1] = {};
   if (cs < 2 || cs > kMaxSplitCluster) return 0;
   std::call_once(once[cs], [cs] {
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = tc_launch_config<V, false>(cs, nullptr, attr, cs);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<V, false>, &cfg) != cudaSuccess) {
@@ -1317,7 +1348,7 @@ int tc_kernel_setup(int* pairs_out) {
     err = cudaFuncSetAttribute(tc_gemm_kernel<V, kPair>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
     if (err == cudaSuccess && kPair) {
-      cudaLaunchAttribute attr[1];
+      cudaLaunchAttribute attr[2];
       cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(2, nullptr, attr);
       err = cudaOccupancyMaxActiveClusters(&pairs, tc_gemm_kernel<V, kPair>, &cfg);
       if (err == cudaSuccess && pairs < 1) err = cudaErrorInvalidConfiguration;
@@ -1335,7 +1366,8 @@ template <int V, bool kPair>
 int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t ldb,
            const void* A2, const void* B2, const void* A3, const void* B3, const float* dq_a,
            const float* dq_b, const TcPlan& plan, float* partial, float* sk_slab,
-           unsigned int* sk_count, const DeviceGuard& g, int slots, cudaStream_t s) {
+           unsigned long long* sk_count, unsigned int sk_epoch, const DeviceGuard& g, int slots,
+           cudaStream_t s) {
   using L = Layout<V, kPair>;
   using T = Traits<V>;
   int rc0 = tc_kernel_setup<V, kPair>(nullptr);
@@ -1389,6 +1421,7 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
   a.sk_ctas = plan.sk_ctas;
   a.sk_slab = sk_slab;
   a.sk_count = sk_count;
+  a.sk_epoch = sk_epoch;
   a.pair = kPair ? 2 : 1;
   a.tiles_m = static_cast<int>((c.m + a.pair * kBM - 1) / (a.pair * kBM));
   a.tiles_n = static_cast<int>((c.n + T::BN - 1) / T::BN);
@@ -1409,8 +1442,6 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
     if (sk_count == nullptr || sk_slab == nullptr) return COMPAR_ERR_INVALID;
     a.dp_units = plan.sk_tile0;
     grid = plan.sk_tile0 > 0 ? slots : plan.sk_ctas;
-    COMPAR_CUDA_TRY(cudaMemsetAsync(
-        sk_count, 0, sizeof(unsigned int) * (units - plan.sk_tile0) * a.pair, s));
   }
   // K splits of a tile as one cluster when every cluster of the call can be
   // resident at once (one unit per CTA); otherwise partials and a reduce
@@ -1422,8 +1453,9 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
       a.split_cluster = 1;
     }
   }
-  cudaLaunchAttribute attr[1];
-  const cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(grid * a.pair, s, attr, cluster);
+  cudaLaunchAttribute attr[2];
+  const cudaLaunchConfig_t cfg =
+      tc_launch_config<V, kPair>(grid * a.pair, s, attr, cluster, /*programmatic=*/true);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   // C through the TMA-store epilogue where it applies (otherwise tc is an
   // unused copy of ta)
@@ -1513,22 +1545,26 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
         plan.splits > 1 ? align_up(static_cast<size_t>(plan.splits) * c.m * c.n * 4, 256) : 0;
     const size_t slab_bytes =
         plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * 2 * kBM * kTileN * 4 : 0;
-    const size_t count_bytes =
-        plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * 4, 256) : 0;
     float* partial = nullptr;
     float* sk_slab = nullptr;
-    unsigned int* sk_count = nullptr;
-    if (part_bytes + slab_bytes + count_bytes > 0) {
-      const int rc = ws.ensure(part_bytes + slab_bytes + count_bytes, s);
+    if (part_bytes + slab_bytes > 0) {
+      const int rc = ws.ensure(part_bytes + slab_bytes, s);
       if (rc != COMPAR_OK) return rc;
       uint8_t* base = static_cast<uint8_t*>(ws.ptr);
       if (part_bytes) partial = reinterpret_cast<float*>(base);
       if (slab_bytes) sk_slab = reinterpret_cast<float*>(base + part_bytes);
-      if (count_bytes) sk_count = reinterpret_cast<unsigned int*>(base + part_bytes + slab_bytes);
+    }
+    unsigned long long* sk_count = nullptr;
+    unsigned int sk_epoch = 0;
+    if (plan.sk_q > 0) {
+      const int rc = ws.ensure_counters(static_cast<size_t>(plan.tiles), s);
+      if (rc != COMPAR_OK) return rc;
+      sk_count = ws.counters;
+      sk_epoch = ws.next_epoch();
     }
     return run_tc<COMPAR_V_SPLIT3_FUSED, false>(c, c.A, c.lda, c.B, c.ldb, nullptr, nullptr, nullptr,
                                          nullptr, nullptr, nullptr, plan, partial, sk_slab,
-                                         sk_count, g, num_sms, s);
+                                         sk_count, sk_epoch, g, num_sms, s);
   }
   const int elem = (v == COMPAR_V_TC_TF32 || v == COMPAR_V_SPLIT3_TF32) ? 4
                    : (v == COMPAR_V_TC_FP8 ? 1 : 2);
@@ -1554,17 +1590,24 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   // (per CTA of a pair)
   const size_t slab_bytes =
       plan.sk_q > 0 ? static_cast<size_t>(plan.sk_ctas) * npair * 2 * kBM * kTileN * 4 : 0;
-  const size_t count_bytes =
-      plan.sk_q > 0 ? align_up(static_cast<size_t>(plan.tiles) * npair * 4, 256) : 0;
   // workspace carve: [B pieces][A pieces][fp8 scalars][split-K partials]
   const size_t a_bytes = align_up(static_cast<size_t>(c.m) * ldk * elem, 256);
   const size_t b_bytes = b_in_place ? 0
                          : b_mn     ? align_up(static_cast<size_t>(c.k) * ldn * 2, 256)
                                     : align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
   size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256 + part_bytes +
-                slab_bytes + count_bytes;
+                slab_bytes;
   int rc = ws.ensure(need, s);
   if (rc != COMPAR_OK) return rc;
+  // stream-K arrival words (one per tail tile and CTA of a pair)
+  unsigned long long* sk_count = nullptr;
+  unsigned int sk_epoch = 0;
+  if (plan.sk_q > 0) {
+    rc = ws.ensure_counters(static_cast<size_t>(plan.tiles) * npair, s);
+    if (rc != COMPAR_OK) return rc;
+    sk_count = ws.counters;
+    sk_epoch = ws.next_epoch();
+  }
   uint8_t* base = static_cast<uint8_t*>(ws.ptr);
   uint8_t* wb = base;
   uint8_t* wa = base + pieces * b_bytes;
@@ -1573,8 +1616,6 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   float* fscal = reinterpret_cast<float*>(scal + 16);               // sA, dA, sB, dB
   float* partial = part_bytes ? reinterpret_cast<float*>(scal + 256) : nullptr;
   float* sk_slab = slab_bytes ? reinterpret_cast<float*>(scal + 256 + part_bytes) : nullptr;
-  unsigned int* sk_count =
-      count_bytes ? reinterpret_cast<unsigned int*>(scal + 256 + part_bytes + slab_bytes) : nullptr;
 
   int out_kind;
   switch (v) {
@@ -1601,10 +1642,22 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   }
   const void* Bop = wb;
   int64_t ldb_op = b_mn ? ldn : ldk;
+  // float32 A and MN-major B converted row by row: one launch for both
+  // when the row kernel takes them
+  bool converted = false;
+  if (!b_in_place && !a_in_place && b_mn && c.dtype == COMPAR_F32 && sa == nullptr) {
+    const RowConvert jb{static_cast<const float*>(c.B), c.k, c.n, c.ldb, wb,
+                        pieces >= 2 ? wb + b_bytes : nullptr, ldb_op, nullptr};
+    const RowConvert ja{static_cast<const float*>(c.A), c.m, c.k, c.lda, wa,
+                        pieces >= 2 ? wa + a_bytes : nullptr, ldk, nullptr};
+    rc = prepass_convert_rows2(jb, ja, out_kind, num_sms, s);
+    if (rc != COMPAR_OK && rc != COMPAR_ERR_UNSUPPORTED) return rc;
+    converted = rc == COMPAR_OK;
+  }
   if (b_in_place) {
     Bop = c.B;
     ldb_op = c.ldb;
-  } else {
+  } else if (!converted) {
     // B: K x N row-major -> K x N pieces (MN-major) or N x K (K-major)
     rc = prepass_convert(c.B, c.dtype, c.k, c.n, c.ldb, wb, out_kind, ldb_op, !b_mn,
                          pieces >= 2 ? wb + b_bytes : nullptr, sb, num_sms, s);
@@ -1613,9 +1666,11 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const void* A = c.A;
   int64_t lda = c.lda;
   if (!a_in_place) {
-    rc = prepass_convert(c.A, c.dtype, c.m, c.k, c.lda, wa, out_kind, ldk, false,
-                         pieces >= 2 ? wa + a_bytes : nullptr, sa, num_sms, s);
-    if (rc != COMPAR_OK) return rc;
+    if (!converted) {
+      rc = prepass_convert(c.A, c.dtype, c.m, c.k, c.lda, wa, out_kind, ldk, false,
+                           pieces >= 2 ? wa + a_bytes : nullptr, sa, num_sms, s);
+      if (rc != COMPAR_OK) return rc;
+    }
     A = wa;
     lda = ldk;
   }
@@ -1629,10 +1684,10 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
                   VV == COMPAR_V_SPLIT3) {
       if (pair)
         return run_tc<VV, true>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, qa, qb, plan, partial,
-                                sk_slab, sk_count, g, pairs, s);
+                                sk_slab, sk_count, sk_epoch, g, pairs, s);
     }
     return run_tc<VV, false>(c, A, lda, Bop, ldb_op, A2, B2, A3, B3, qa, qb, plan, partial,
-                             sk_slab, sk_count, g, num_sms, s);
+                             sk_slab, sk_count, sk_epoch, g, num_sms, s);
   };
   switch (v) {
     case COMPAR_V_TC_TF32:

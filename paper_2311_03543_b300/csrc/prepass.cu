@@ -21,6 +21,7 @@
 
 #include "common.h"
 #include "grouped.h"
+#include "ptx.cuh"
 
 namespace compar {
 namespace {
@@ -195,19 +196,30 @@ __device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], v
   }
 }
 
-// Row-wise convert of float32 rows (8 elements per group, 16-byte aligned):
-// each thread takes kRowUnroll groups of one row, 256 groups apart, and
-// issues all their loads before its stores, so that 128 bytes per thread
-// are in flight; rows are dealt to the blocks of a resident-sized grid.
+// Row-wise convert of float32 rows (8 elements per group, 16-byte aligned)
+// of one or two matrices (rows of j0, then rows of j1): each thread takes
+// kRowUnroll groups of one row, 256 groups apart, and issues all their
+// loads before its stores, so that 128 bytes per thread are in flight; rows
+// are dealt to the blocks of a resident-sized grid.  Launched
+// programmatically: it waits for the stream's previous kernel first, and
+// lets the next one (the GEMM) be scheduled at once.
 constexpr int kRowUnroll = 4;
-__global__ void convert_rows_vec8_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
-                                         int64_t ldx, void* __restrict__ Y, void* __restrict__ Ylo,
-                                         int64_t ldy, int kind, const float* __restrict__ dscale) {
-  const float s = dscale ? *dscale : 1.f;
-  const int64_t groups = cols / 8;
+__global__ void convert_rows_vec8_kernel(const RowConvert j0, const RowConvert j1, int kind) {
+  dev::griddep_wait();
+  dev::griddep_launch_dependents();
+  const float s0 = j0.dscale ? *j0.dscale : 1.f;
+  const float s1 = (j1.rows > 0 && j1.dscale) ? *j1.dscale : 1.f;
+  const int64_t rows_all = j0.rows + j1.rows;
   const int64_t span = static_cast<int64_t>(blockDim.x) * kRowUnroll;  // groups per block pass
-  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-    const float* xr = X + r * ldx;
+  for (int64_t r_all = blockIdx.y; r_all < rows_all; r_all += gridDim.y) {
+    const bool first = r_all < j0.rows;
+    const int64_t r = first ? r_all : r_all - j0.rows;
+    const int64_t groups = (first ? j0.cols : j1.cols) / 8;
+    const float* xr = (first ? j0.X : j1.X) + r * (first ? j0.ldx : j1.ldx);
+    void* Y = first ? j0.Y : j1.Y;
+    void* Ylo = first ? j0.Y_lo : j1.Y_lo;
+    const int64_t yoff = r * (first ? j0.ldy : j1.ldy);
+    const float sc = first ? s0 : s1;
     for (int64_t g0 = blockIdx.x * span + threadIdx.x; g0 < groups;
          g0 += static_cast<int64_t>(gridDim.x) * span) {
       float4 a[kRowUnroll], b[kRowUnroll];
@@ -225,11 +237,44 @@ __global__ void convert_rows_vec8_kernel(const float* __restrict__ X, int64_t ro
         const int64_t gi = g0 + u * static_cast<int64_t>(blockDim.x);
         if (gi < groups) {
           const float x[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
-          store8(kind, s, x, Y, Ylo, r * ldy + gi * 8);
+          store8(kind, sc, x, Y, Ylo, yoff + gi * 8);
         }
       }
     }
   }
+}
+
+// The vectorised row kernel's rules for one matrix.
+bool rows_vec8_ok(const RowConvert& j) {
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(j.X), ya = reinterpret_cast<uintptr_t>(j.Y),
+                  la = reinterpret_cast<uintptr_t>(j.Y_lo);
+  return j.cols % 8 == 0 && j.ldx % 4 == 0 && xa % 16 == 0 && j.ldy % 8 == 0 && ya % 16 == 0 &&
+         la % 16 == 0;
+}
+
+// One launch of the row kernel over j0 and j1 (j1.rows may be 0): blocks
+// across a row cover it in passes of 256 x kRowUnroll groups; rows are dealt
+// to about eight resident blocks per SM.
+int launch_rows_vec8(const RowConvert& j0, const RowConvert& j1, int kind, int num_sms,
+                     cudaStream_t s) {
+  const int64_t groups = std::max(j0.cols, j1.rows > 0 ? j1.cols : 0) / 8;
+  const int64_t rows = j0.rows + j1.rows;
+  const int64_t bx = std::max<int64_t>(
+      1, std::min<int64_t>((groups + 256 * kRowUnroll - 1) / (256 * kRowUnroll), 64));
+  const int64_t by = std::max<int64_t>(1, std::min<int64_t>(rows, std::min<int64_t>(
+                                              65535, (8 * static_cast<int64_t>(num_sms) + bx - 1) / bx)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(bx), static_cast<unsigned>(by));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  COMPAR_CUDA_TRY(cudaLaunchKernelEx(&cfg, convert_rows_vec8_kernel, j0, j1, kind));
+  count_launch();
+  return COMPAR_OK;
 }
 
 // Transposing convert through a 64 x 64 tile: float2 loads, each thread
@@ -629,19 +674,10 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
       count_launch();
       return COMPAR_OK;
     }
-    if (!transpose && cols % 8 == 0 && ldx % 4 == 0 && xa % 16 == 0 && ldy % 8 == 0 &&
-        ya % 16 == 0 && la % 16 == 0) {
-      // blocks across a row cover it in passes of 256 x kRowUnroll groups;
-      // rows are dealt to about eight resident blocks per SM
-      const int64_t groups = cols / 8;
-      const int64_t bx = std::min<int64_t>((groups + 256 * kRowUnroll - 1) / (256 * kRowUnroll), 64);
-      const int64_t by = std::max<int64_t>(1, std::min<int64_t>(rows, std::min<int64_t>(
-                                                  65535, (8 * static_cast<int64_t>(num_sms) + bx - 1) / bx)));
-      const dim3 gv(static_cast<unsigned>(bx), static_cast<unsigned>(by));
-      convert_rows_vec8_kernel<<<gv, 256, 0, s>>>(Xf, rows, cols, ldx, Y, Y_lo, ldy, kind, dscale);
-      COMPAR_CUDA_TRY(cudaGetLastError());
-      count_launch();
-      return COMPAR_OK;
+    const RowConvert j{Xf, rows, cols, ldx, Y, Y_lo, ldy, dscale};
+    if (!transpose && rows_vec8_ok(j)) {
+      const RowConvert none{nullptr, 0, 0, 0, nullptr, nullptr, 0, nullptr};
+      return launch_rows_vec8(j, none, kind, num_sms, s);
     }
   }
   if (out_kind == PP_COPY) {
@@ -679,6 +715,13 @@ int prepass_convert(const void* X, compar_dtype_t in_t, int64_t rows, int64_t co
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;
+}
+
+int prepass_convert_rows2(const RowConvert& a, const RowConvert& b, int out_kind, int num_sms,
+                          cudaStream_t s) {
+  if (out_kind == PP_COPY || !rows_vec8_ok(a) || !rows_vec8_ok(b)) return COMPAR_ERR_UNSUPPORTED;
+  if (a.rows <= 0 || a.cols <= 0 || b.rows <= 0 || b.cols <= 0) return COMPAR_ERR_UNSUPPORTED;
+  return launch_rows_vec8(a, b, out_kind, num_sms, s);
 }
 
 int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
