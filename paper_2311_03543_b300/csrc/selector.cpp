@@ -168,7 +168,8 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
   };
   // The tensor-core variants' launch plan (compar_tc_plan): tiles of
   // 128 x 256 times the splits of K, in full waves of the SMs, each unit
-  // running its own share of K; a split of K adds its reduce launch.
+  // running its own share of K; a split of K adds its in-cluster sum (up to
+  // 8 splits) or its reduce launch.
   auto tc_units = [&](double* k_eff) {
     int64_t pl[9];
     if (tc_plan_info(v, m, n, k, num_sms, pl, false) != COMPAR_OK) {
@@ -177,7 +178,7 @@ double prior_time_ms(int v, int64_t m, int64_t n, int64_t k, int dtype, int num_
     }
     const double splits = static_cast<double>(pl[2]);
     *k_eff = std::ceil(K / splits);
-    if (splits > 1) ovh_us += 4;
+    if (splits > 1) ovh_us += splits <= 8 ? 1 : 4;
     return std::ceil(static_cast<double>(pl[1]) * splits / num_sms) * num_sms;
   };
   switch (v) {
