@@ -592,3 +592,39 @@ def test_pairs_are_chosen_for_a_wave_of_tiles(ctx):
     auto = _run(ctx, cp.V_SPLIT3, A, B, pairs=-1)
     forced = _run(ctx, cp.V_SPLIT3, A, B, pairs=1)
     assert np.array_equal(auto, forced)
+
+
+@pytest.mark.parametrize("m,n,k", [(2560, 2304, 1024), (256, 512, 4096), (1024, 1024, 1024)])
+def test_dependent_calls_back_to_back(ctx, m, n, k):
+    """Calls enqueued with no synchronisation between them, each reading what
+    the previous one wrote (C of one call is A of the next, then the C input
+    with beta = 1): the tensor-core chain starts its pre-pass and GEMM
+    set-up before the previous kernel completes, so this checks that no
+    operand is read early and that no workspace is overwritten while a
+    previous GEMM still reads it.  Shapes: a stream-K tail on CTA pairs, an
+    in-cluster K split, and one wave of single CTAs."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev, host
+    A0 = (W.uniform(m, k, seed=81) * 0.5).astype(np.float32)
+    B0 = (W.uniform(k, k, seed=82) / np.sqrt(k)).astype(np.float32)
+    B1 = (W.uniform(k, n, seed=83) / np.sqrt(k)).astype(np.float32)
+    X = torch.empty((m, k), device="cuda")
+    Y = torch.empty((m, n), device="cuda")
+    dA0, dB0, dB1 = dev(A0), dev(B0), dev(B1)
+    torch.cuda.synchronize()
+    ctx.force_variant(cp.V_SPLIT3)
+    try:
+        ctx.gemm(dA0, dB0, X, tol=1e-5)          # X = A0 B0
+        ctx.gemm(X, dB1, Y, tol=1e-5)            # Y = X B1 (reads X right after it is written)
+        ctx.set_scalars(1.0, 1.0)
+        ctx.gemm(X, dB1, Y, tol=1e-5)            # Y = X B1 + Y
+        got = host(Y)
+    finally:
+        ctx.force_variant(None)
+        ctx.set_scalars(1.0, 0.0)
+    assert ctx.check_device_error() == cp.OK
+    x = oracle.gemm(A0, B0)
+    y = oracle.gemm(x, B1)
+    ref = 2.0 * y
+    assert N.rel_frobenius(got, ref) <= 3 * TOL_F32
