@@ -262,13 +262,14 @@ def test_split_k_few_tiles_with_alpha_beta(ctx, v):
 _KELEMS = {2: 32, 3: 64, 4: 128, 5: 32, 9: 32}
 
 
-@pytest.mark.parametrize("splits", [2, 3, 5, 7, 8])
+@pytest.mark.parametrize("splits", [2, 3, 5, 7, 8, 12, 16])
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 9])
 def test_k_split_summed_in_cluster(ctx, v, splits):
     """Four ragged tiles (200 x 300) with K = 8 * splits K blocks: the plan
     splits K `splits` ways and the splits of a tile, one thread-block cluster,
     add their accumulators through distributed shared memory (every slot of
-    the tile shared out over the cluster's CTAs, odd cluster sizes included).
+    the tile shared out over the cluster's CTAs, odd cluster sizes included);
+    12 and 16 splits take the HBM partials and the reduce kernel.
     Small integers are exact in every format, so a split counted twice or
     not at all, or a slot stored at the wrong element, changes the result."""
     import paper_2311_03543_b300 as cp
