@@ -231,9 +231,10 @@ class Context:
     """A libcompar context bound to one CUDA device (tensor-level API).
 
     `selector`: the selector file loaded at creation — by default the
-    shipped trained selector for a device context and none for a host-only
-    one; None starts from the untrained models (roofline prior only), as a
-    context that trains its own selector must."""
+    shipped trained selector for a device context (unless COMPAR_SELECTOR_FILE
+    names one, which compar_init has loaded) and none for a host-only one;
+    None starts from the untrained models (roofline prior only), as a context
+    that trains its own selector must."""
 
     def __init__(self, device=0, host_only=False, num_sms=148, selector="default"):
         load()
@@ -245,7 +246,8 @@ class Context:
         self.handle = h
         self.device = None if host_only else device
         if selector == "default":
-            selector = None if host_only else DEFAULT_SELECTOR
+            selector = None if (host_only or os.environ.get("COMPAR_SELECTOR_FILE")) \
+                else DEFAULT_SELECTOR
         if selector is not None:
             try:
                 self.selector_load(selector)
