@@ -41,7 +41,12 @@ struct BatchedState {
   size_t cap_probs = 0, cap_jobs = 0;
   cudaEvent_t staged = nullptr;  // last graph launch (staging may be rewritten after it)
   cudaStream_t capture = nullptr;
-  std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+  // the graph's second branch (pre-pass, then the problems that need it)
+  cudaStream_t capture2 = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // (problems, tiles, jobs, pre-pass tiles, bn, problems needing no pre-pass, their tiles)
+  using Key = std::tuple<int, int, int, int, int, int, int>;
+  std::map<Key, cudaGraphExec_t> graphs;
   // the batch whose descriptors are in the staging buffers now: the same batch
   // again (same problems, configuration, tolerance and workspace) only
   // relaunches its graph
@@ -50,7 +55,7 @@ struct BatchedState {
   int last_cfg = -1;
   double last_tol = 0;
   void* last_ws = nullptr;
-  std::tuple<int, int, int, int, int> last_key{};
+  Key last_key{};
 };
 
 BatchedState* state(compar_ctx* ctx) {
@@ -86,10 +91,20 @@ int ensure_staging(BatchedState* b, size_t nprobs, size_t njobs) {
   }
   if (!b->staged) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
   if (!b->capture) COMPAR_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+  if (!b->capture2) COMPAR_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture2, cudaStreamNonBlocking));
+  if (!b->fork_ev) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+  if (!b->join_ev) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming));
   return COMPAR_OK;
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Kernels one replay of a batch graph runs: the pre-pass when there are
+// jobs, and one grouped GEMM per non-empty group.
+int graph_kernels(const BatchedState::Key& k) {
+  const int n = std::get<0>(k), jobs = std::get<2>(k), n0 = std::get<5>(k);
+  return (jobs > 0 ? 1 : 0) + (n0 > 0 ? 1 : 0) + (n - n0 > 0 ? 1 : 0);
+}
 
 int grouped_mode(const compar_problem_t& p, double tol) {
   if (p.dtype == COMPAR_BF16) return 0;
@@ -213,6 +228,28 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     P.off_a = ws_need;
     if (!P.a_in_place) ws_need += P.pieces * P.a_bytes;
   }
+  // Problems whose operands are used in place (no pre-pass job) first, the
+  // others after them, each group in the order above: the graph runs the
+  // first group's GEMM beside the pre-pass, the second group's after it.
+  int n0 = 0;
+  bool any_transpose = false;
+  {
+    std::vector<int> o2;
+    std::vector<Plan> p2;
+    o2.reserve(order.size());
+    p2.reserve(order.size());
+    for (int pass = 0; pass < 2; ++pass)
+      for (size_t q = 0; q < order.size(); ++q) {
+        const bool needs = !plan[q].a_in_place || !plan[q].b_in_place;
+        if (needs != (pass == 1)) continue;
+        o2.push_back(order[q]);
+        p2.push_back(plan[q]);
+        if (pass == 0) ++n0;
+        if (plan[q].mode == 2) any_transpose = true;  // K-major B copy
+      }
+    order.swap(o2);
+    plan.swap(p2);
+  }
   int rc = ctx->ws.ensure(ws_need, s);
   if (rc != COMPAR_OK) return rc;
   BatchedState* b = state(ctx);
@@ -225,7 +262,7 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     auto same = b->graphs.find(b->last_key);
     if (same != b->graphs.end()) {
       COMPAR_CUDA_TRY(cudaGraphLaunch(same->second, s));
-      count_launch(2);
+      count_launch(graph_kernels(b->last_key));
       COMPAR_CUDA_TRY(cudaEventRecord(b->staged, s));
       return run_rest();
     }
@@ -234,10 +271,15 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
   // the previous launch must have consumed the staging buffers
   COMPAR_CUDA_TRY(cudaEventSynchronize(b->staged));
   uint8_t* ws = static_cast<uint8_t*>(ctx->ws.ptr);
-  int tile_acc = 0, ptile_acc = 0, njobs = 0;
+  // tiles are numbered within each group (one grouped launch per group)
+  int tile_acc = 0, ptile_acc = 0, njobs = 0, tiles0 = 0;
   for (size_t q = 0; q < nprob; ++q) {
     const compar_problem_t& p = probs[order[q]];
     const Plan& P = plan[q];
+    if (q == static_cast<size_t>(n0)) {
+      tiles0 = tile_acc;
+      tile_acc = 0;
+    }
     GroupProblem& G = b->h_probs[q];
     memset(&G, 0, sizeof(G));
     G.M = static_cast<int>(p.m);
@@ -311,7 +353,10 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
       add_job(p.A, p.lda, p.m, p.k, aw, P.pieces == 2 ? aw + P.a_bytes : nullptr, 0, P.ldk);
   }
   const int ngroup = static_cast<int>(nprob);
-  const auto key = std::make_tuple(ngroup, tile_acc, njobs, ptile_acc, bn);
+  if (static_cast<size_t>(n0) == nprob) tiles0 = tile_acc;
+  const int n1 = ngroup - n0, tiles1 = n1 > 0 ? tile_acc : 0;
+  const BatchedState::Key key = std::make_tuple(ngroup, tiles0 + tiles1, njobs, ptile_acc, bn, n0,
+                                                tiles0);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraph_t graph = nullptr;
@@ -322,15 +367,37 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
                     b->capture);
     cudaMemcpyAsync(b->d_jobs, b->h_jobs, njobs * sizeof(PrepassJob), cudaMemcpyHostToDevice,
                     b->capture);
-    int rc1 = launch_grouped_prepass(b->d_jobs, njobs, ptile_acc, ctx->num_sms, b->capture);
-    int rc2 = launch_grouped_gemm(bn, b->d_probs, ngroup, tile_acc, ctx->guard, ctx->num_sms,
-                                  b->capture);
+    // Two branches: the problems used in place on the capture stream, and on
+    // the second stream the pre-pass, then the problems that needed it.  The
+    // pre-pass (no shared memory when nothing transposes) fits beside the
+    // first branch's CTAs.
+    int rc1 = COMPAR_OK, rc2 = COMPAR_OK, rc3 = COMPAR_OK;
+    cudaStream_t s2 = b->capture;
+    if (n0 > 0 && n1 > 0) {
+      cudaEventRecord(b->fork_ev, b->capture);
+      cudaStreamWaitEvent(b->capture2, b->fork_ev, 0);
+      s2 = b->capture2;
+    }
+    if (n0 > 0)
+      rc1 = launch_grouped_gemm(bn, b->d_probs, n0, tiles0, ctx->guard, ctx->num_sms, b->capture);
+    if (n1 > 0) {
+      rc2 = launch_grouped_prepass(b->d_jobs, njobs, ptile_acc, ctx->num_sms, any_transpose, s2);
+      if (rc2 == COMPAR_OK)
+        rc3 = launch_grouped_gemm(bn, b->d_probs + n0, n1, tiles1, ctx->guard, ctx->num_sms, s2);
+    }
+    if (s2 != b->capture) {
+      cudaEventRecord(b->join_ev, s2);
+      cudaStreamWaitEvent(b->capture, b->join_ev, 0);
+    }
     count_launch(static_cast<int>(before - launch_count()));  // captured, not run
     const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);
-    if (rc1 != COMPAR_OK || rc2 != COMPAR_OK || ec != cudaSuccess) {
+    if (rc1 != COMPAR_OK || rc2 != COMPAR_OK || rc3 != COMPAR_OK || ec != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       if (ec != cudaSuccess) set_last_cuda_error(ec, "cudaStreamEndCapture", __FILE__, __LINE__);
-      return rc1 != COMPAR_OK ? rc1 : (rc2 != COMPAR_OK ? rc2 : COMPAR_ERR_CUDA);
+      return rc1 != COMPAR_OK ? rc1
+             : rc2 != COMPAR_OK ? rc2
+             : rc3 != COMPAR_OK ? rc3
+                                : COMPAR_ERR_CUDA;
     }
     const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -341,7 +408,7 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
     it = b->graphs.emplace(key, exec).first;
   }
   COMPAR_CUDA_TRY(cudaGraphLaunch(it->second, s));
-  count_launch(2);
+  count_launch(graph_kernels(key));
   COMPAR_CUDA_TRY(cudaEventRecord(b->staged, s));
   b->last_probs.assign(probs, probs + count);
   b->last_cfg = cfg;
@@ -403,6 +470,9 @@ void batched_release(compar_ctx* ctx) {
   cudaFree(b->d_jobs);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->capture2) cudaStreamDestroy(b->capture2);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   delete b;
   ctx->batched_state = nullptr;
 }

@@ -598,9 +598,13 @@ __device__ __forceinline__ void tile_transpose(const PrepassJob& J, int64_t r0, 
   __syncthreads();
 }
 
+// kTranspose: the batch has transposing jobs (the 64 x 64 staging tile in
+// shared memory); without them the kernel uses no shared memory, so its
+// blocks fit beside a grouped GEMM CTA on the same SM.
+template <bool kTranspose>
 __global__ void __launch_bounds__(256, 6) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
                                                               int njobs, int total_tiles) {
-  __shared__ float tile[64][65];
+  __shared__ float tile[kTranspose ? 64 : 1][65];
   const int per = (total_tiles + gridDim.x - 1) / gridDim.x;
   const int t_begin = blockIdx.x * per;
   const int t_end = min(total_tiles, t_begin + per);
@@ -620,10 +624,12 @@ __global__ void __launch_bounds__(256, 6) grouped_prepass_kernel(const PrepassJo
     const int64_t r0 = static_cast<int64_t>(lt / J.tiles_c) * 64;
     const int64_t c0 = static_cast<int64_t>(lt % J.tiles_c) * 64;
     const bool f32 = J.in_type == COMPAR_F32;
-    if (J.transpose) {
-      if (!f32) tile_transpose<__nv_bfloat16, PP_BF16>(J, r0, c0, tile);
-      else if (J.out_kind == PP_SPLIT_BF16) tile_transpose<float, PP_SPLIT_BF16>(J, r0, c0, tile);
-      else tile_transpose<float, PP_F32>(J, r0, c0, tile);
+    if (kTranspose && J.transpose) {
+      if constexpr (kTranspose) {
+        if (!f32) tile_transpose<__nv_bfloat16, PP_BF16>(J, r0, c0, tile);
+        else if (J.out_kind == PP_SPLIT_BF16) tile_transpose<float, PP_SPLIT_BF16>(J, r0, c0, tile);
+        else tile_transpose<float, PP_F32>(J, r0, c0, tile);
+      }
     } else {
       if (!f32) tile_rows<__nv_bfloat16, PP_BF16>(J, r0, c0);
       else if (J.out_kind == PP_SPLIT_BF16) tile_rows<float, PP_SPLIT_BF16>(J, r0, c0);
@@ -635,17 +641,22 @@ __global__ void __launch_bounds__(256, 6) grouped_prepass_kernel(const PrepassJo
 }  // namespace
 
 int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles, int num_sms,
-                           cudaStream_t s) {
+                           bool transpose, cudaStream_t s) {
   if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
   // one full wave of resident blocks
-  static int resident = 0;
-  if (resident == 0) {
-    int r = 0;
-    COMPAR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, grouped_prepass_kernel, 256, 0));
-    resident = std::max(r, 1);
+  static int resident[2] = {0, 0};
+  int& r = resident[transpose ? 1 : 0];
+  if (r == 0) {
+    int n = 0;
+    COMPAR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, transpose ? grouped_prepass_kernel<true> : grouped_prepass_kernel<false>, 256, 0));
+    r = std::max(n, 1);
   }
-  const int grid = static_cast<int>(std::min<int64_t>(total_tiles, static_cast<int64_t>(num_sms) * resident));
-  grouped_prepass_kernel<<<grid, 256, 0, s>>>(d_jobs, njobs, total_tiles);
+  const int grid = static_cast<int>(std::min<int64_t>(total_tiles, static_cast<int64_t>(num_sms) * r));
+  if (transpose)
+    grouped_prepass_kernel<true><<<grid, 256, 0, s>>>(d_jobs, njobs, total_tiles);
+  else
+    grouped_prepass_kernel<false><<<grid, 256, 0, s>>>(d_jobs, njobs, total_tiles);
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();
   return COMPAR_OK;
