@@ -533,11 +533,13 @@ __device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16* p, b
   return v;
 }
 
-// Row-wise job: Y[r][c] = f(X[r][c]); thread = 4 consecutive columns.
+// Row-wise job: Y[r][c] = f(X[r][c]); thread = 4 consecutive columns of 4
+// rows, all four loads issued before the first store.
 template <typename In, int KIND>
 __device__ __forceinline__ void tile_rows(const PrepassJob& J, int64_t r0, int64_t c0) {
   const In* X = static_cast<const In*>(J.src);
   const bool vec = J.vec != 0;
+  float4 vq[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int idx = threadIdx.x + 256 * q;  // 64 rows x 16 groups of 4
@@ -545,8 +547,17 @@ __device__ __forceinline__ void tile_rows(const PrepassJob& J, int64_t r0, int64
     const int64_t c = c0 + 4 * (idx & 15);
     if (r >= J.rows || c >= J.cols) continue;
     const int64_t rem = J.cols - c;
+    vq[q] = load4<In>(X + r * J.ld_src + c, vec, rem >= 4 ? 4 : static_cast<int>(rem));
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    const int64_t r = r0 + (idx >> 4);
+    const int64_t c = c0 + 4 * (idx & 15);
+    if (r >= J.rows || c >= J.cols) continue;
+    const int64_t rem = J.cols - c;
     const int n_valid = rem >= 4 ? 4 : static_cast<int>(rem);
-    const float4 v = load4<In>(X + r * J.ld_src + c, vec, n_valid);
+    const float4 v = vq[q];
     const int64_t o = r * J.ld_dst + c;
     if (n_valid == 4) {  // outputs rows have pitch ldk (a multiple of 16): aligned
       PieceOut<KIND>::put4(J.dst, J.dst_lo, o, v);
@@ -602,7 +613,7 @@ __device__ __forceinline__ void tile_transpose(const PrepassJob& J, int64_t r0, 
 // shared memory); without them the kernel uses no shared memory, so its
 // blocks fit beside a grouped GEMM CTA on the same SM.
 template <bool kTranspose>
-__global__ void __launch_bounds__(256, 6) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 4) grouped_prepass_kernel(const PrepassJob* __restrict__ jobs,
                                                               int njobs, int total_tiles) {
   __shared__ float tile[kTranspose ? 64 : 1][65];
   const int per = (total_tiles + gridDim.x - 1) / gridDim.x;
