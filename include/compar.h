@@ -138,7 +138,12 @@ const char* compar_last_error(void);
  * model (when confident) > history-table model.  Returns COMPAR_OK,
  * COMPAR_ERR_INVALID, COMPAR_ERR_NO_VARIANT (nothing meets tol) or
  * COMPAR_ERR_CUDA.  alpha/beta and FP8 scales come from compar_set_scalars /
- * compar_set_fp8_scales (the listed signature has no slot for them). */
+ * compar_set_fp8_scales (the listed signature has no slot for them).
+ * Stream capture: a call may be captured into a CUDA graph and replayed
+ * once a call of the same shape has run on the context outside the capture
+ * (the decision is cached and the workspace has its size); a call that
+ * would grow the workspace while `stream` is captured returns
+ * COMPAR_ERR_UNSUPPORTED. */
 int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
                 compar_dtype_t dtype, double tol, const void* A,
                 const void* B, float* C, void* stream);

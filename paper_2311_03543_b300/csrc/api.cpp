@@ -32,8 +32,21 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 std::string last_error_text() { return g_last_error; }
 void set_last_error_text(const std::string& text) { g_last_error = text; }
 
+// Growing a workspace inside a stream capture would hand the context memory
+// that only the captured graph owns: refused (a call of the same shape before
+// the capture grows it).
+static int refuse_growth_in_capture(cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  COMPAR_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap == cudaStreamCaptureStatusNone) return COMPAR_OK;
+  g_last_error =
+      "the workspace must grow while the stream is captured: run the call once before capturing";
+  return COMPAR_ERR_UNSUPPORTED;
+}
+
 int Workspace::ensure(size_t need, cudaStream_t s) {
   if (need <= bytes) return COMPAR_OK;
+  if (int rc = refuse_growth_in_capture(s); rc != COMPAR_OK) return rc;
   size_t grow = std::max(need, bytes + bytes / 2);
   grow = (grow + (1 << 20) - 1) & ~static_cast<size_t>((1 << 20) - 1);
   if (ptr) COMPAR_CUDA_TRY(cudaFreeAsync(ptr, s));
@@ -46,6 +59,7 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
 
 int Workspace::ensure_counters(size_t n, cudaStream_t s) {
   if (n <= counter_n) return COMPAR_OK;
+  if (int rc = refuse_growth_in_capture(s); rc != COMPAR_OK) return rc;
   const size_t grow = std::max<size_t>(n, 4096);
   if (counters) COMPAR_CUDA_TRY(cudaFreeAsync(counters, s));
   counters = nullptr;
@@ -53,6 +67,17 @@ int Workspace::ensure_counters(size_t n, cudaStream_t s) {
   COMPAR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&counters), grow * sizeof(*counters), s));
   COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, grow * sizeof(*counters), s));
   counter_n = grow;
+  return COMPAR_OK;
+}
+
+int Workspace::take_counters(size_t n, cudaStream_t s, uint32_t* epoch) {
+  int rc = ensure_counters(n, s);
+  if (rc != COMPAR_OK) return rc;
+  *epoch = next_epoch();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  COMPAR_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, n * sizeof(*counters), s));
   return COMPAR_OK;
 }
 

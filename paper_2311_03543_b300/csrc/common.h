@@ -58,6 +58,11 @@ struct Workspace {
   }
   int ensure(size_t need, cudaStream_t s);
   int ensure_counters(size_t n, cudaStream_t s);
+  // Counter words [0, n) for one launch, with a fresh epoch in *epoch.  When
+  // `s` is being captured into a graph, the words are also zeroed in the
+  // captured work: every replay of the graph runs the same epoch, so each
+  // must start from zero counts.
+  int take_counters(size_t n, cudaStream_t s, uint32_t* epoch);
   void release();
 };
 

@@ -645,11 +645,11 @@ int dispatch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int nu
       if (rc != COMPAR_OK) return rc;
       partial = static_cast<float*>(ws.ptr);
       if (plan.splits <= kSkinnyLastSum) {  // few slabs: the last cluster adds them
-        rc = ws.ensure_counters(static_cast<size_t>((c.m + plan.bm - 1) / plan.bm) *
-                                    ((c.n + kSkinnyCols - 1) / kSkinnyCols), s);
+        rc = ws.take_counters(static_cast<size_t>((c.m + plan.bm - 1) / plan.bm) *
+                                  ((c.n + kSkinnyCols - 1) / kSkinnyCols),
+                              s, &epoch);
         if (rc != COMPAR_OK) return rc;
         counters = ws.counters;
-        epoch = ws.next_epoch();
       }
     }
     cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;

@@ -1557,10 +1557,9 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
     unsigned long long* sk_count = nullptr;
     unsigned int sk_epoch = 0;
     if (plan.sk_q > 0) {
-      const int rc = ws.ensure_counters(static_cast<size_t>(plan.tiles), s);
+      const int rc = ws.take_counters(static_cast<size_t>(plan.tiles), s, &sk_epoch);
       if (rc != COMPAR_OK) return rc;
       sk_count = ws.counters;
-      sk_epoch = ws.next_epoch();
     }
     return run_tc<COMPAR_V_SPLIT3_FUSED, false>(c, c.A, c.lda, c.B, c.ldb, nullptr, nullptr, nullptr,
                                          nullptr, nullptr, nullptr, plan, partial, sk_slab,
@@ -1603,10 +1602,9 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   unsigned long long* sk_count = nullptr;
   unsigned int sk_epoch = 0;
   if (plan.sk_q > 0) {
-    rc = ws.ensure_counters(static_cast<size_t>(plan.tiles) * npair, s);
+    rc = ws.take_counters(static_cast<size_t>(plan.tiles) * npair, s, &sk_epoch);
     if (rc != COMPAR_OK) return rc;
     sk_count = ws.counters;
-    sk_epoch = ws.next_epoch();
   }
   uint8_t* base = static_cast<uint8_t*>(ws.ptr);
   uint8_t* wb = base;

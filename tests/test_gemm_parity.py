@@ -629,3 +629,37 @@ def test_dependent_calls_back_to_back(ctx, m, n, k):
     y = oracle.gemm(x, B1)
     ref = 2.0 * y
     assert N.rel_frobenius(got, ref) <= 3 * TOL_F32
+
+
+@pytest.mark.parametrize("m,n,k", [(2560, 2304, 1024), (16, 4096, 4096), (1024, 1024, 1024)])
+def test_captured_call_replays(ctx, m, n, k):
+    """A call captured into a CUDA graph (after one call of the shape outside
+    the capture) and replayed three times gives the oracle's result every
+    time: the counter words of a stream-K tail (first shape) or of the
+    skinny plan's cluster sums (second, forced SIMT) start from zero on each
+    replay, and in-cluster K splits (third) need none."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev, host
+    A = W.uniform(m, k, seed=95); B = W.uniform(k, n, seed=96)
+    ref = oracle.gemm(A, B)
+    dA, dB = dev(A), dev(B)
+    C = torch.empty((m, n), device="cuda")
+    v = cp.V_SIMT if m == 16 else cp.V_SPLIT3
+    ctx.force_variant(v)
+    try:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ctx.gemm(dA, dB, C, tol=1e-5, stream=s)        # decision and workspace
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctx.gemm(dA, dB, C, tol=1e-5, stream=s)
+        for _ in range(3):
+            C.fill_(float("nan"))
+            g.replay()
+            got = host(C)
+            assert N.rel_frobenius(got, ref) <= TOL_F32
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
