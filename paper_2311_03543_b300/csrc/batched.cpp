@@ -38,6 +38,7 @@ struct BatchedState {
   PrepassJob* h_jobs = nullptr;
   GroupProblem* d_probs = nullptr;
   PrepassJob* d_jobs = nullptr;
+  int* d_tile_ctr = nullptr;  // the two grouped launches' tile counters
   size_t cap_probs = 0, cap_jobs = 0;
   cudaEvent_t staged = nullptr;  // last graph launch (staging may be rewritten after it)
   cudaStream_t capture = nullptr;
@@ -92,6 +93,7 @@ int ensure_staging(BatchedState* b, size_t nprobs, size_t njobs) {
   if (!b->staged) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
   if (!b->capture) COMPAR_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
   if (!b->capture2) COMPAR_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture2, cudaStreamNonBlocking));
+  if (!b->d_tile_ctr) COMPAR_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&b->d_tile_ctr), 2 * sizeof(int)));
   if (!b->fork_ev) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
   if (!b->join_ev) COMPAR_CUDA_TRY(cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming));
   return COMPAR_OK;
@@ -379,11 +381,13 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
       s2 = b->capture2;
     }
     if (n0 > 0)
-      rc1 = launch_grouped_gemm(bn, b->d_probs, n0, tiles0, ctx->guard, ctx->num_sms, b->capture);
+      rc1 = launch_grouped_gemm(bn, b->d_probs, n0, tiles0, b->d_tile_ctr, ctx->guard,
+                                ctx->num_sms, b->capture);
     if (n1 > 0) {
       rc2 = launch_grouped_prepass(b->d_jobs, njobs, ptile_acc, ctx->num_sms, any_transpose, s2);
       if (rc2 == COMPAR_OK)
-        rc3 = launch_grouped_gemm(bn, b->d_probs + n0, n1, tiles1, ctx->guard, ctx->num_sms, s2);
+        rc3 = launch_grouped_gemm(bn, b->d_probs + n0, n1, tiles1, b->d_tile_ctr + 1, ctx->guard,
+                                  ctx->num_sms, s2);
     }
     if (s2 != b->capture) {
       cudaEventRecord(b->join_ev, s2);
@@ -468,6 +472,7 @@ void batched_release(compar_ctx* ctx) {
   cudaFreeHost(b->h_jobs);
   cudaFree(b->d_probs);
   cudaFree(b->d_jobs);
+  cudaFree(b->d_tile_ctr);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->capture) cudaStreamDestroy(b->capture);
   if (b->capture2) cudaStreamDestroy(b->capture2);

@@ -60,7 +60,7 @@ struct GLayout {
   static constexpr int kA = kBM * kRow;       // one A piece
   static constexpr int kB = BN * kRow;        // one B piece
   static constexpr int kStage = 2 * (kA + kB);
-  static constexpr int kBar = 256;
+  static constexpr int kBar = 1024;  // barriers, the tile ring, TMEM slot, abort flag
   static constexpr int kIndex = kMaxIndexed * 4;    // problems' tile_start values
   static constexpr int kStagesRaw = (232448 - 1024 - kBar - kIndex) / kStage;
   static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
@@ -82,10 +82,8 @@ __device__ __forceinline__ int find_problem(const GroupProblem* __restrict__ P,
   return lo;
 }
 
-// The fields of a tile's problem that the roles need, fetched one tile
-// ahead: the loads are issued while the current tile runs, so a role does
-// not stall on global memory at every tile boundary (tiles of small problems
-// take only a few stages).
+// The fields of a tile's problem that the roles need: the producer looks
+// them up once per tile and passes them to the other roles with the tile.
 struct TileInfo {
   int q, local, tiles_m, num_kb, mode, M, N;
   float* C;
@@ -111,6 +109,18 @@ __device__ __forceinline__ TileInfo tile_info(const GroupProblem* __restrict__ P
   return t;
 }
 
+// Dynamic tile scheduling: the producer takes tile indices from a
+// launch-wide counter (zero at launch) and hands each tile, with its
+// problem's fields, to the MMA thread and the epilogue warps through a ring
+// in shared memory; a CTA that starts late (beside another kernel's CTAs)
+// simply takes fewer tiles.  A slot is filled by one arrival and freed by
+// the MMA thread and one lane of each epilogue warp once they have read it.
+constexpr int kRing = 8;
+struct RingTile {
+  TileInfo t;
+  int tile;  // < 0: no tile left
+};
+
 __device__ __forceinline__ bool drain(uint64_t* bar, uint32_t parity, uint64_t budget) {
   const uint64_t t0 = dev::globaltimer_ns();
   while (!dev::mbar_try_wait(bar, parity))
@@ -119,11 +129,13 @@ __device__ __forceinline__ bool drain(uint64_t* bar, uint32_t parity, uint64_t b
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(152)
     grouped_gemm_kernel(const GroupProblem* __restrict__ probs, int count, int total_tiles,
-                        int* err_word, unsigned long long budget_ns) {
+                        int* __restrict__ tile_ctr, int* err_word, unsigned long long budget_ns) {
   using L = GLayout<BN>;
   constexpr int S = L::kStages;
+  static_assert((2 * S + 5 + 2 * kRing) * 8 + kRing * sizeof(RingTile) + 8 <= L::kBar,
+                "barriers and tile ring fit their region");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -133,7 +145,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint64_t* drainb = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drainb + 1);
+  uint64_t* ring_full = drainb + 1;     // [kRing]
+  uint64_t* ring_empty = ring_full + kRing;
+  RingTile* ring = reinterpret_cast<RingTile*>(ring_empty + kRing);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ring + kRing);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* s_index = reinterpret_cast<int*>(smem + S * L::kStage + L::kBar);
   const int* s_start = count <= kMaxIndexed ? s_index : nullptr;
@@ -151,6 +166,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       dev::mbar_init(&tempty[a], kEpi);
     }
     dev::mbar_init(drainb, 1);
+    for (int r = 0; r < kRing; ++r) {
+      dev::mbar_init(&ring_full[r], 1);
+      dev::mbar_init(&ring_empty[r], 1 + kEpiWarps);
+    }
     *abort_flag = 0;
     dev::fence_barrier_init();
   }
@@ -170,8 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     // The descriptors were written by the host for this launch; earlier
     // launches may have left other bytes at these addresses in the cache:
-    // acquire (and prefetch) a problem's maps before its first TMA use, one
-    // tile ahead.
+    // acquire (and prefetch) a problem's maps before its first TMA use.
     auto acquire_maps = [&](int q) {
       const GroupProblem& P = probs[q];
       dev::tensormap_acquire(&P.map_a);
@@ -181,17 +199,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       dev::tma_prefetch_desc(&P.map_a);
       dev::tma_prefetch_desc(&P.map_b);
     };
-    TileInfo cur{};
-    if (blockIdx.x < total_tiles) {
-      cur = tile_info(probs, s_start, count, blockIdx.x);
-      acquire_maps(cur.q);
-    }
-    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      TileInfo nxt{};
-      const int tn = tile + gridDim.x;
-      if (tn < total_tiles) {
-        nxt = tile_info(probs, s_start, count, tn);
-        if (nxt.q != cur.q) acquire_maps(nxt.q);
+    int next = atomicAdd(tile_ctr, 1);
+    int last_q = -1;
+    for (int i = 0; ok; ++i) {
+      const int tile = next < total_tiles ? next : -1;
+      // the following tile's index is in flight while this tile loads
+      if (tile >= 0) next = atomicAdd(tile_ctr, 1);
+      const int slot = i % kRing;
+      if (!dev::mbar_wait(&ring_empty[slot], ((i / kRing) & 1) ^ 1, w)) {
+        ok = false;
+        break;
+      }
+      TileInfo cur{};
+      if (tile >= 0) cur = tile_info(probs, s_start, count, tile);
+      ring[slot].t = cur;
+      ring[slot].tile = tile;
+      dev::mbar_arrive(&ring_full[slot]);
+      if (tile < 0) break;
+      if (cur.q != last_q) {
+        acquire_maps(cur.q);
+        last_q = cur.q;
       }
       const GroupProblem& P = probs[cur.q];
       const int mb = cur.local % cur.tiles_m, nb = cur.local / cur.tiles_m;
@@ -235,7 +262,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           phase ^= 1;
         }
       }
-      cur = nxt;
     }
     if (!ok)
       for (int s = 0; s < S; ++s)
@@ -247,16 +273,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t stage = 0, phase = 0;
     int acc_iter = 0;
     bool ok = true;
-    TileInfo cur{};
-    if (blockIdx.x < total_tiles) cur = tile_info(probs, s_start, count, blockIdx.x);
-    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      TileInfo nxt{};
-      if (tile + static_cast<int>(gridDim.x) < total_tiles)
-        nxt = tile_info(probs, s_start, count, tile + gridDim.x);
-      const int mode = cur.mode;
-      const int num_kb = cur.num_kb;
+    for (int i = 0; ok; ++i) {
+      const int slot = i % kRing;
+      if (!dev::mbar_wait(&ring_full[slot], (i / kRing) & 1, w)) {
+        ok = false;
+        break;
+      }
+      const int tile = ring[slot].tile;
+      const int mode = ring[slot].t.mode;
+      const int num_kb = ring[slot].t.num_kb;
+      dev::mbar_arrive(&ring_empty[slot]);
+      if (tile < 0) break;
       const int ckb = grouped_chunk_kb(mode);
-      cur = nxt;
       for (int kb0 = 0; ok && kb0 < num_kb; kb0 += ckb, ++acc_iter) {
         const uint32_t acc = acc_iter & 1, acc_phase = (acc_iter >> 1) & 1;
         if (!dev::mbar_wait(&tempty[acc], acc_phase ^ 1, w)) {
@@ -334,12 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cslice = (warp - 2) / 4;
     int acc_iter = 0;
     bool ok = true;
-    TileInfo cur{};
-    if (blockIdx.x < total_tiles) cur = tile_info(probs, s_start, count, blockIdx.x);
-    for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
-      const TileInfo t = cur;
-      if (tile + static_cast<int>(gridDim.x) < total_tiles)
-        cur = tile_info(probs, s_start, count, tile + gridDim.x);
+    for (int i = 0; ok; ++i) {
+      const int slot = i % kRing;
+      if (!dev::mbar_wait(&ring_full[slot], (i / kRing) & 1, w)) {
+        ok = false;
+        break;
+      }
+      const int tile = ring[slot].tile;
+      const TileInfo t = ring[slot].t;
+      __syncwarp();
+      if (lane == 0) dev::mbar_arrive(&ring_empty[slot]);
+      if (tile < 0) break;
       const int mb = t.local % t.tiles_m, nb = t.local / t.tiles_m;
       const int pM = t.M, pN = t.N, num_kb = t.num_kb;
       float* const pC = t.C;
@@ -413,8 +446,11 @@ int grouped_smem_bytes(int bn) {
 }
 
 int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int total_tiles,
-                        const DeviceGuard& g, int num_sms, cudaStream_t s) {
+                        int* d_tile_ctr, const DeviceGuard& g, int num_sms, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return COMPAR_OK;
+  if (d_tile_ctr == nullptr) return COMPAR_ERR_INVALID;
+  // the launch's tile counter starts from zero (a memset node in a graph)
+  COMPAR_CUDA_TRY(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int), s));
   const int grid = std::min(total_tiles, num_sms);
   if (bn == 256) {
     static bool attr = false;
@@ -425,7 +461,7 @@ int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int tota
       attr = true;
     }
     grouped_gemm_kernel<256><<<grid, kThreads, GLayout<256>::kSmem, s>>>(
-        d_probs, count, total_tiles, g.err_word, g.budget_ns);
+        d_probs, count, total_tiles, d_tile_ctr, g.err_word, g.budget_ns);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -435,7 +471,7 @@ int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int tota
       attr = true;
     }
     grouped_gemm_kernel<128><<<grid, kThreads, GLayout<128>::kSmem, s>>>(
-        d_probs, count, total_tiles, g.err_word, g.budget_ns);
+        d_probs, count, total_tiles, d_tile_ctr, g.err_word, g.budget_ns);
   }
   COMPAR_CUDA_TRY(cudaGetLastError());
   count_launch();

@@ -47,8 +47,10 @@ struct PrepassJob {
 };
 
 int grouped_smem_bytes(int bn);
+// d_tile_ctr: one device int, the launch's tile counter (zeroed on `s`
+// before the kernel).
 int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int total_tiles,
-                        const DeviceGuard& g, int num_sms, cudaStream_t s);
+                        int* d_tile_ctr, const DeviceGuard& g, int num_sms, cudaStream_t s);
 // transpose: some job transposes (the kernel then stages tiles in shared
 // memory; without, it uses none).
 int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles, int num_sms,
