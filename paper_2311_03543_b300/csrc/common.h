@@ -167,12 +167,15 @@ struct RowConvert {
 // then converts them one by one with prepass_convert.
 int prepass_convert_rows2(const RowConvert& a, const RowConvert& b, int out_kind, int num_sms,
                           cudaStream_t s);
-// amax(|X|) and amax(|Y|) (float bits, d_amax_bits[0..1]) in one launch.
+// amax(|X|) and amax(|Y|) in one launch, as per-block maxima: block b
+// writes d_block_max[2 b] and [2 b + 1]; at most max_blocks blocks, the
+// number used in *nblocks (0 when both are empty).
 int prepass_amax2(const float* X, int64_t xr, int64_t xc, int64_t ldx, const float* Y, int64_t yr,
-                  int64_t yc, int64_t ldy, unsigned int* d_amax_bits, int num_sms,
-                  cudaStream_t s);
-// {s_x, 1/s_x, s_y, 1/s_y} with s = 448 / amax (1 when amax == 0).
-int prepass_fp8_scales(const unsigned int* d_amax_bits, float* d_out, cudaStream_t s);
+                  int64_t yc, int64_t ldy, float* d_block_max, int max_blocks, int num_sms,
+                  int* nblocks, cudaStream_t s);
+// {s_x, 1/s_x, s_y, 1/s_y} with s = 448 / amax (1 when amax == 0), the
+// amaxes reduced from prepass_amax2's per-block maxima.
+int prepass_fp8_scales(const float* d_block_max, int nblocks, float* d_out, cudaStream_t s);
 
 // out_kind values for prepass_convert.  The split kinds write piece p of
 // element idx at Y + p * (Y_lo - Y) (pieces equally spaced, Y_lo = piece 1):

@@ -1594,7 +1594,10 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const size_t b_bytes = b_in_place ? 0
                          : b_mn     ? align_up(static_cast<size_t>(c.k) * ldn * 2, 256)
                                     : align_up(static_cast<size_t>(c.n) * ldk * elem, 256);
-  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + 256 + part_bytes +
+  // scalars: the fp8 scales (16 bytes), then the amax pass's per-block maxima
+  constexpr int kMaxAmaxBlocks = 2048;
+  constexpr size_t kScalBytes = 256 + 2 * kMaxAmaxBlocks * sizeof(float);
+  size_t need = pieces * b_bytes + (a_in_place ? 0 : pieces * a_bytes) + kScalBytes + part_bytes +
                 slab_bytes;
   int rc = ws.ensure(need, s);
   if (rc != COMPAR_OK) return rc;
@@ -1610,10 +1613,10 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   uint8_t* wb = base;
   uint8_t* wa = base + pieces * b_bytes;
   uint8_t* scal = wa + (a_in_place ? 0 : pieces * a_bytes);
-  unsigned int* amax_bits = reinterpret_cast<unsigned int*>(scal);  // [2]
-  float* fscal = reinterpret_cast<float*>(scal + 16);               // sA, dA, sB, dB
-  float* partial = part_bytes ? reinterpret_cast<float*>(scal + 256) : nullptr;
-  float* sk_slab = slab_bytes ? reinterpret_cast<float*>(scal + 256 + part_bytes) : nullptr;
+  float* fscal = reinterpret_cast<float*>(scal);              // sA, dA, sB, dB
+  float* block_max = reinterpret_cast<float*>(scal + 256);    // [2 kMaxAmaxBlocks]
+  float* partial = part_bytes ? reinterpret_cast<float*>(scal + kScalBytes) : nullptr;
+  float* sk_slab = slab_bytes ? reinterpret_cast<float*>(scal + kScalBytes + part_bytes) : nullptr;
 
   int out_kind;
   switch (v) {
@@ -1629,9 +1632,11 @@ int launch_tc(int v, const GemmCall& c, Workspace& ws, const DeviceGuard& g, int
   const float* dqa = nullptr;
   const float* dqb = nullptr;
   if (fp8_from_f32) {
+    int nblocks = 0;
     rc = prepass_amax2(static_cast<const float*>(c.A), c.m, c.k, c.lda,
-                       static_cast<const float*>(c.B), c.k, c.n, c.ldb, amax_bits, num_sms, s);
-    if (rc == COMPAR_OK) rc = prepass_fp8_scales(amax_bits, fscal, s);
+                       static_cast<const float*>(c.B), c.k, c.n, c.ldb, block_max, kMaxAmaxBlocks,
+                       num_sms, &nblocks, s);
+    if (rc == COMPAR_OK) rc = prepass_fp8_scales(block_max, nblocks, fscal, s);
     if (rc != COMPAR_OK) return rc;
     sa = fscal + 0;
     dqa = fscal + 1;
