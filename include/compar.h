@@ -28,8 +28,12 @@
  * given cudaStream_t (passed as void*; NULL = legacy default stream).  Errors
  * found on the host are returned synchronously; kernel-side failures (a
  * bounded wait that ran out) are latched in a device error word and returned
- * by compar_check_device_error.  No call aborts the process.  A context is not
- * thread-safe: use one context per host thread.  The calls on one context
+ * by compar_check_device_error.  No call aborts the process.  Each call runs
+ * on its context's device: the call makes that device current and restores
+ * the caller's current device before returning, so one process may drive
+ * several GPUs with one context each; the stream passed must belong to the
+ * context's device.  A context is not thread-safe: use one context per host
+ * thread.  The calls on one context
  * share its device workspace (operand copies, partial sums, arrival
  * counters), so they must run in order on the GPU: issue them on one stream,
  * or order the streams yourself (events); calls that overlap on the GPU give

@@ -15,7 +15,9 @@
 #include <cstring>
 #include <fstream>
 #include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 
 #include "runtime.h"
 
@@ -31,6 +33,42 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 }
 std::string last_error_text() { return g_last_error; }
 void set_last_error_text(const std::string& text) { g_last_error = text; }
+
+int current_device_index() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  return (d >= 0 && d < kMaxDevices) ? d : -1;
+}
+
+cudaError_t smem_opt_in(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  const int d = current_device_index();
+  if (d < 0) return cudaErrorInvalidDevice;
+  const auto key = std::make_tuple(d, func, bytes);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
+
+DeviceScope::DeviceScope(int device) {
+  if (device < 0) return;
+  if (cudaGetDevice(&prev_) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  if (prev_ != device && cudaSetDevice(device) == cudaSuccess) switched_ = true;
+}
+
+DeviceScope::~DeviceScope() {
+  if (switched_) cudaSetDevice(prev_);
+}
 
 // Growing a workspace inside a stream capture would hand the context memory
 // that only the captured graph owns: refused (a call of the same shape before
@@ -532,7 +570,7 @@ int compar_terminate(compar_ctx_t ctx) {
     delete ctx;
     return COMPAR_OK;
   }
-  cudaSetDevice(ctx->device);
+  DeviceScope device_scope(ctx->device);
   cudaDeviceSynchronize();
   resolve_pending(ctx);
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
@@ -564,6 +602,7 @@ const char* compar_last_error(void) { return g_last_error.c_str(); }
 
 int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                 double tol, const void* A, const void* B, float* C, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   int rc = check_ptrs(m, n, k, A, B, C);
@@ -589,6 +628,7 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_
 
 int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                      double tol, const void* A, const void* B, float* C, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   int rc = check_ptrs(m, n, k, A, B, C);
@@ -646,6 +686,7 @@ const char* compar_variant_name(int v) {
 
 int compar_variant_supported(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
                              compar_dtype_t dtype) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0)
     return COMPAR_ERR_INVALID;
   GemmCall c;
@@ -660,6 +701,7 @@ int compar_variant_supported(compar_ctx_t ctx, int v, int64_t m, int64_t n, int6
 }
 
 int compar_clear_decisions(compar_ctx_t ctx) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   ctx->decisions.clear();
   return COMPAR_OK;
@@ -667,6 +709,7 @@ int compar_clear_decisions(compar_ctx_t ctx) {
 
 int compar_select(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                   double tol, int batch) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol) || m <= 0 || n <= 0 || k <= 0 ||
       batch < 1)
     return COMPAR_ERR_INVALID;
@@ -722,6 +765,7 @@ double compar_error_model_predict(compar_ctx_t ctx, int v, compar_dtype_t dtype,
 int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
                    compar_dtype_t dtype, double tol, const void* A, const void* B, float* C,
                    int warmup, int reps, void* stream, float* median_ms) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !median_ms || v < 0 || v >= kNumVariants || !valid_dtype(dtype) || reps < 1 ||
       warmup < 0)
     return COMPAR_ERR_INVALID;
@@ -795,6 +839,7 @@ int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
 }
 
 int compar_record_enable(compar_ctx_t ctx, int on) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   if (!on) resolve_pending(ctx);
   ctx->rec.on = on != 0;
@@ -802,12 +847,14 @@ int compar_record_enable(compar_ctx_t ctx, int on) {
 }
 
 int64_t compar_record_count(compar_ctx_t ctx) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   resolve_pending(ctx);
   return static_cast<int64_t>(ctx->rec.ring.size());
 }
 
 int64_t compar_record_get(compar_ctx_t ctx, compar_record_t* out, int64_t max) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || (!out && max > 0) || max < 0) return COMPAR_ERR_INVALID;
   resolve_pending(ctx);
   auto snap = ctx->rec.snapshot();
@@ -828,6 +875,7 @@ int compar_record_add(compar_ctx_t ctx, const compar_record_t* recs, int64_t cou
 }
 
 int compar_record_clear(compar_ctx_t ctx) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   resolve_pending(ctx);
   ctx->rec.clear();
@@ -835,6 +883,7 @@ int compar_record_clear(compar_ctx_t ctx) {
 }
 
 int compar_check_device_error(compar_ctx_t ctx, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -853,6 +902,7 @@ int compar_set_wait_budget(compar_ctx_t ctx, uint64_t ns) {
 }
 
 int compar_selftest_timeout(compar_ctx_t ctx, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   return launch_timeout_selftest(ctx->guard, static_cast<cudaStream_t>(stream));

@@ -493,6 +493,7 @@ using namespace compar;
 
 extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
                                    double tol, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   int rc = validate(ctx, count, probs);
   if (rc != COMPAR_OK) return rc;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
@@ -518,6 +519,7 @@ extern "C" int compar_set_batched_config(compar_ctx_t ctx, int config) {
 
 extern "C" int compar_autotune_batched(compar_ctx_t ctx, int count, const compar_problem_t* probs,
                                        double tol, void* stream, float* times_ms, int* best) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   int rc = validate(ctx, count, probs);
   if (rc != COMPAR_OK) return rc;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;

@@ -105,6 +105,33 @@ struct DeviceGuard {  // device error word + wait budget handed to kernels
   int tc_pair = -1;
 };
 
+// One process may drive several GPUs (one context each), so one-time kernel
+// set-up (shared-memory opt-ins, occupancy queries) is kept per device.
+constexpr int kMaxDevices = 64;
+
+// The calling thread's current device, or -1 when there is none or it is
+// numbered kMaxDevices or above.
+int current_device_index();
+
+// Raises `func`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per (device, kernel, size).
+cudaError_t smem_opt_in(const void* func, int bytes);
+
+// Makes a context's device current for one API call and puts the caller's
+// device back when the call returns.  Does nothing when that device is
+// already current, or for device -1 (host-only contexts).
+class DeviceScope {
+ public:
+  explicit DeviceScope(int device);
+  ~DeviceScope();
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool switched_ = false;
+};
+
 int launch_naive(const GemmCall& c, const DeviceGuard& g, cudaStream_t s);
 int launch_simt(const GemmCall& c, Workspace& ws, const DeviceGuard& g, int num_sms,
                 cudaStream_t s);

@@ -453,23 +453,13 @@ int launch_grouped_gemm(int bn, const GroupProblem* d_probs, int count, int tota
   COMPAR_CUDA_TRY(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int), s));
   const int grid = std::min(total_tiles, num_sms);
   if (bn == 256) {
-    static bool attr = false;
-    if (!attr) {
-      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<256>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           GLayout<256>::kSmem));
-      attr = true;
-    }
+    COMPAR_CUDA_TRY(smem_opt_in(reinterpret_cast<const void*>(grouped_gemm_kernel<256>),
+                                GLayout<256>::kSmem));
     grouped_gemm_kernel<256><<<grid, kThreads, GLayout<256>::kSmem, s>>>(
         d_probs, count, total_tiles, d_tile_ctr, g.err_word, g.budget_ns);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      COMPAR_CUDA_TRY(cudaFuncSetAttribute(grouped_gemm_kernel<128>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           GLayout<128>::kSmem));
-      attr = true;
-    }
+    COMPAR_CUDA_TRY(smem_opt_in(reinterpret_cast<const void*>(grouped_gemm_kernel<128>),
+                                GLayout<128>::kSmem));
     grouped_gemm_kernel<128><<<grid, kThreads, GLayout<128>::kSmem, s>>>(
         d_probs, count, total_tiles, d_tile_ctr, g.err_word, g.budget_ns);
   }

@@ -1315,14 +1315,17 @@ cudaLaunchConfig_t tc_launch_config(int grid, cudaStream_t s, cudaLaunchAttribut
 // Largest in-cluster K split (portable cluster size).
 constexpr int kMaxSplitCluster = 8;
 
-// Clusters of `cs` single CTAs of variant V that can be resident at once
-// (queried once per size; 0 when the query fails).
+// Clusters of `cs` single CTAs of variant V that can be resident at once on
+// the current device (queried once per device and size; 0 when the query
+// fails or there is no usable device).
 template <int V>
 int tc_split_cluster_capacity(int cs) {
-  static std::once_flag once[kMaxSplitCluster + 1];
-  static int cap[kMaxSplitCluster + 1] = {};
+  static std::once_flag once[kMaxDevices][kMaxSplitCluster + 1];
+  static int cap[kMaxDevices][kMaxSplitCluster + 1] = {};
   if (cs < 2 || cs > kMaxSplitCluster) return 0;
-  std::call_once(once[cs], [cs] {
+  const int d = current_device_index();
+  if (d < 0) return 0;
+  std::call_once(once[d][cs], [d, cs] {
     cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = tc_launch_config<V, false>(cs, nullptr, attr, cs);
     int n = 0;
@@ -1330,35 +1333,40 @@ int tc_split_cluster_capacity(int cs) {
       cudaGetLastError();
       n = 0;
     }
-    cap[cs] = n;
+    cap[d][cs] = n;
   });
-  return cap[cs];
+  return cap[d][cs];
 }
 
-// Shared-memory opt-in of the kernel, once; for pairs also the number of
-// pairs that can be resident at once (pairs need two SMs of one TPC, so it
-// can be below half the SM count).
+// Shared-memory opt-in of the kernel, once per device; for pairs also the
+// number of pairs that can be resident at once (pairs need two SMs of one
+// TPC, so it can be below half the SM count).
 template <int V, bool kPair>
 int tc_kernel_setup(int* pairs_out) {
   using L = Layout<V, kPair>;
-  static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
-  static int pairs = 0;
-  std::call_once(once, [] {
-    err = cudaFuncSetAttribute(tc_gemm_kernel<V, kPair>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
-    if (err == cudaSuccess && kPair) {
-      cudaLaunchAttribute attr[2];
-      cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(2, nullptr, attr);
-      err = cudaOccupancyMaxActiveClusters(&pairs, tc_gemm_kernel<V, kPair>, &cfg);
-      if (err == cudaSuccess && pairs < 1) err = cudaErrorInvalidConfiguration;
-    }
-  });
-  if (err != cudaSuccess) {
-    set_last_cuda_error(err, "tensor-core kernel set-up", __FILE__, __LINE__);
+  static std::once_flag once[kMaxDevices];
+  static cudaError_t err[kMaxDevices] = {};
+  static int pairs[kMaxDevices] = {};
+  const int d = current_device_index();
+  if (d < 0) {
+    set_last_error_text("tensor-core kernel set-up: no usable current device");
     return COMPAR_ERR_CUDA;
   }
-  if (pairs_out) *pairs_out = pairs;
+  std::call_once(once[d], [d] {
+    err[d] = cudaFuncSetAttribute(tc_gemm_kernel<V, kPair>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmemBytes);
+    if (err[d] == cudaSuccess && kPair) {
+      cudaLaunchAttribute attr[2];
+      cudaLaunchConfig_t cfg = tc_launch_config<V, kPair>(2, nullptr, attr);
+      err[d] = cudaOccupancyMaxActiveClusters(&pairs[d], tc_gemm_kernel<V, kPair>, &cfg);
+      if (err[d] == cudaSuccess && pairs[d] < 1) err[d] = cudaErrorInvalidConfiguration;
+    }
+  });
+  if (err[d] != cudaSuccess) {
+    set_last_cuda_error(err[d], "tensor-core kernel set-up", __FILE__, __LINE__);
+    return COMPAR_ERR_CUDA;
+  }
+  if (pairs_out) *pairs_out = pairs[d];
   return COMPAR_OK;
 }
 

@@ -303,13 +303,8 @@ int mlp_train_device(float* d_params, float* d_m, float* d_v, int members, const
                      float lr, int step0, int apply, float* d_grads, float* d_loss,
                      cudaStream_t s) {
   if (members <= 0 || steps <= 0 || batch <= 0 || batch > kB) return COMPAR_ERR_INVALID;
-  static bool attr = false;
-  if (!attr) {
-    COMPAR_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kTrainSmem)));
-    attr = true;
-  }
+  COMPAR_CUDA_TRY(smem_opt_in(reinterpret_cast<const void*>(mlp_train_kernel),
+                              static_cast<int>(kTrainSmem)));
   TrainArgs a{};
   a.params = d_params;
   a.adam_m = d_m;

@@ -32,7 +32,7 @@ static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / 
 // __device__ array is not a device address): the lookup allocates nothing,
 // and a context torn down and made again (cudaDeviceReset) may load the
 // module, and with it the array, at another address.
-constexpr int kMaxDevices = 64;
+using compar::kMaxDevices;
 struct DeviceSetup {
   bool done = false;
   int num_sms = 0;

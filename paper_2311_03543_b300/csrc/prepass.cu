@@ -685,8 +685,13 @@ int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles,
                            bool transpose, cudaStream_t s) {
   if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
   // one full wave of resident blocks
-  static int resident[2] = {0, 0};
-  int& r = resident[transpose ? 1 : 0];
+  static int resident[kMaxDevices][2] = {};
+  const int d = current_device_index();
+  if (d < 0) {
+    set_last_error_text("grouped pre-pass: no usable current device");
+    return COMPAR_ERR_CUDA;
+  }
+  int& r = resident[d][transpose ? 1 : 0];
   if (r == 0) {
     int n = 0;
     COMPAR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -73,6 +73,7 @@ using namespace compar;
 extern "C" {
 
 int compar_profile_enable(compar_ctx_t ctx, int on) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   ctx->prof.on = on != 0;
   if (!on) ctx->prof.resolve();
@@ -80,6 +81,7 @@ int compar_profile_enable(compar_ctx_t ctx, int on) {
 }
 
 int compar_profile_read(compar_ctx_t ctx, int variant, double* kernel_ms, int64_t* launches) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || variant < 0 || variant >= KernelProfiler::kSlots || !kernel_ms || !launches)
     return COMPAR_ERR_INVALID;
   ctx->prof.resolve();
@@ -89,6 +91,7 @@ int compar_profile_read(compar_ctx_t ctx, int variant, double* kernel_ms, int64_
 }
 
 int compar_profile_reset(compar_ctx_t ctx) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx) return COMPAR_ERR_INVALID;
   ctx->prof.reset();
   return COMPAR_OK;

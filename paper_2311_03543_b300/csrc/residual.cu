@@ -80,6 +80,7 @@ extern "C" int compar_residual_check(compar_ctx_t ctx, int64_t m, int64_t n, int
                                      compar_dtype_t dtype, const void* A, const void* B,
                                      const float* C, float alpha, int nrows, uint64_t seed,
                                      double* rel_err, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !rel_err || m <= 0 || n <= 0 || k <= 0 || nrows <= 0 || !A || !B || !C ||
       m > INT32_MAX || n > INT32_MAX || k > INT32_MAX ||
       (dtype != COMPAR_F32 && dtype != COMPAR_BF16 && dtype != COMPAR_F8E4M3))

@@ -113,6 +113,7 @@ void get_hist(Reader& r, HistoryModel& h, int num_variants, uint32_t version) {
 using namespace compar;
 
 extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !path) return COMPAR_ERR_INVALID;
   Writer w;
   put_hist(w, ctx->hist);
@@ -178,6 +179,7 @@ extern "C" int compar_selector_save(compar_ctx_t ctx, const char* path) {
 }
 
 extern "C" int compar_selector_load(compar_ctx_t ctx, const char* path) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !path) return COMPAR_ERR_INVALID;
   std::ifstream f(path, std::ios::binary);
   if (!f) return COMPAR_ERR_IO;

@@ -158,6 +158,7 @@ int compar_mlp_param_count(void) { return mlp_param_count(); }
 
 int compar_mlp_forward(compar_ctx_t ctx, const float* params, int members, const float* X,
                        int rows, float* Y) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !params || !X || !Y || members <= 0 || rows <= 0) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   MlpDevice* d = dev_state(ctx);
@@ -186,6 +187,7 @@ int compar_mlp_train_steps(compar_ctx_t ctx, float* params, float* adam_m, float
                            int members, const float* X, const float* T, const float* mask,
                            int rows, const int32_t* batch_idx, int steps, int batch, float lr,
                            int step0, float* grads, float* loss) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !params || !X || !T || !mask || !batch_idx || members <= 0 || rows <= 0 ||
       steps <= 0 || batch <= 0 || batch > 128 || step0 < 1 || !(lr >= 0))
     return COMPAR_ERR_INVALID;
@@ -409,11 +411,13 @@ static int train_impl(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t
 
 int compar_selector_train(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
                           float* val_loss) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   return train_impl(ctx, steps, batch, lr, seed, false, val_loss);
 }
 
 int compar_selector_finetune(compar_ctx_t ctx, int steps, int batch, float lr, uint64_t seed,
                              float* val_loss) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   const int rc = train_impl(ctx, steps, batch, lr, seed, true, val_loss);
   if (ctx && (rc == COMPAR_OK || rc == COMPAR_FINETUNE_KEPT)) ctx->online.retrains += 1;
   if (rc == COMPAR_FINETUNE_KEPT) {
@@ -447,6 +451,7 @@ int compar_online_stats(compar_ctx_t ctx, int64_t* explored, int64_t* retrains,
 
 int compar_predict(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                    double tol, int batch, float* time_ms, float* rel_err, float* spread) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !time_ms || !rel_err || m <= 0 || n <= 0 || k <= 0 || batch < 1)
     return COMPAR_ERR_INVALID;
   if (!ctx->mlp.trained) return COMPAR_ERR_UNSUPPORTED;

@@ -321,23 +321,11 @@ int stencil_launch(int v, int64_t rows64, int64_t cols64, int iters,
     } else {
       const dim3 grid((cols + kTileW - 1) / kTileW, (rows + kTileH - 1) / kTileH);
       if (v == COMPAR_S_TILED) {
-        static bool attr = false;
-        if (!attr) {
-          COMPAR_CUDA_TRY(cudaFuncSetAttribute(stencil_tiled_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               kTiledSmem));
-          attr = true;
-        }
+        COMPAR_CUDA_TRY(smem_opt_in(reinterpret_cast<const void*>(stencil_tiled_kernel), kTiledSmem));
         stencil_tiled_kernel<<<grid, kBlockThreads, kTiledSmem, s>>>(src, P, dst, rows, cols,
                                                                        steps, k);
       } else {
-        static bool attr = false;
-        if (!attr) {
-          COMPAR_CUDA_TRY(cudaFuncSetAttribute(stencil_tma_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               kTiledSmem));
-          attr = true;
-        }
+        COMPAR_CUDA_TRY(smem_opt_in(reinterpret_cast<const void*>(stencil_tma_kernel), kTiledSmem));
         TmaMaps maps;
         const int rc = tma_encode_2d(&maps.t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, src, cols, rows,
                                      cols, kPitch, kBufRows, 0);

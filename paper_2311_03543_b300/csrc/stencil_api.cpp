@@ -107,6 +107,7 @@ extern "C" {
 int compar_stencil(compar_ctx_t ctx, int64_t rows, int64_t cols, int iters,
                    const compar_stencil_params_t* params, const float* T_in, const float* P,
                    float* T_out, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   int rc = check_call(ctx, rows, cols, iters, params, T_in, P, T_out);
   if (rc != COMPAR_OK) return rc;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
@@ -132,12 +133,14 @@ const char* compar_stencil_variant_name(int v) {
 }
 
 int compar_stencil_supported(compar_ctx_t ctx, int v, int64_t rows, int64_t cols) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || v < 0 || v >= COMPAR_S_COUNT || rows < 0 || cols < 0) return COMPAR_ERR_INVALID;
   if (v == COMPAR_S_TMA && ctx->host_only) return (cols % 4 == 0) ? 1 : 0;
   return stencil_supported(v, rows, cols, true) ? 1 : 0;
 }
 
 int compar_stencil_select(compar_ctx_t ctx, int64_t rows, int64_t cols, int iters) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || rows <= 0 || cols <= 0 || iters < 0) return COMPAR_ERR_INVALID;
   if (ctx->host_only) {
     // no device to ask about TMA: judge by the grid alone
@@ -163,6 +166,7 @@ int compar_stencil_measure(compar_ctx_t ctx, int v, int64_t rows, int64_t cols, 
                            const compar_stencil_params_t* params, const float* T_in,
                            const float* P, float* T_out, int warmup, int reps, void* stream,
                            float* median_ms) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   int rc = check_call(ctx, rows, cols, iters, params, T_in, P, T_out);
   if (rc != COMPAR_OK) return rc;
   if (v < 0 || v >= COMPAR_S_COUNT || reps < 1 || warmup < 0 || !median_ms || rows == 0 ||
