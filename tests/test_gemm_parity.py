@@ -425,6 +425,24 @@ def test_sweep_shapes_sampled_rows(ctx, v, m, n, k):
     assert np.all(np.isfinite(got))
 
 
+def test_largest_sweep_shape_through_the_selector(ctx):
+    """8192^3, the sweep's largest shape, through the selector at tol 1e-5 as
+    the benchmark calls it (3xBF16 on CTA pairs): the first and last row of
+    every 128-row tile plus one seeded row inside it, element by element."""
+    import paper_2311_03543_b300 as cp
+    from gpu_util import abs_product_rows, assert_elementwise, elem_bound
+    n = 8192
+    A = W.uniform(n, n, seed=30); B = W.uniform(n, n, seed=31)
+    got = _run(ctx, None, A, B, tol=1e-5)
+    v = ctx.last_variant()
+    assert v in (cp.V_SPLIT3, cp.V_SPLIT3_FUSED)
+    rows = W.tile_rows(n, seed=32)
+    ref = oracle.gemm_rows(A, B, rows)
+    assert N.rel_frobenius(got[rows], ref) <= TOL_F32
+    assert_elementwise(got[rows], ref, abs_product_rows(A, B, rows), elem_bound(v, n))
+    assert np.all(np.isfinite(got))
+
+
 # The SIMT variant's skinny-M plan (a few rows of A against a wide, deep B):
 # every branch of the plan — clusters of 1, 2, 4 or 8 CTAs along K, their
 # sums written straight to C or through the reduce pass — with 8- and 16-row
