@@ -462,8 +462,7 @@ def main():
     except (OSError, ValueError):
         pass
     if dom in (cp.V_NAIVE, cp.V_SIMT):
-        mhz = peaks.get("sm_max_mhz", 2032.0)
-        peak, bound, src = 148 * 128 * 2 * mhz * 1e6 / 1e12, "alu", "derived: 148 SM x 128 FP32 lanes x 2 x max clock"
+        peak, bound, src = ctx.peak_ffma(), "alu", "measured FFMA loop (compar_peak_ffma)"
     else:
         scale = {cp.V_TC_TF32: 0.5, cp.V_SPLIT3_TF32: 0.5, cp.V_TC_FP8: 2.0}.get(dom, 1.0)
         base = peaks.get("bf16_tflops_sustained")
@@ -477,7 +476,8 @@ def main():
     roofline = {"bound": bound, "kernel": cp.VARIANT_NAMES[dom], "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
                 "traffic": traffic, "traffic_note": traffic_note,
-                "peak_source": src + " (of measured)", "launches": dom_n,
+                "peak_source": src + (" (of fallback)" if src.startswith("fallback")
+                                      else " (of measured)"), "launches": dom_n,
                 "kernel_ms_per_step": dom_ms / args.steps,
                 "share_of_step": (dom_ms / args.steps) / ms if ms else None}
 
@@ -667,9 +667,10 @@ def measure_stencil(ctx, cp, W, torch, dev, reps=5):
     temporal blocking the FP32 pipe, which bounds it once a warp's row moves
     through shared memory in 16-byte pieces (the instruction issue is the
     limit: 10 FP32 operations per cell and step, counted once per cell of the
-    grid, against 148 SMs x 128 lanes x 2032 MHz = 38.5 T operations/s; the
-    kernel also recomputes the 128 x 80 region of every 112 x 64 tile,
-    x1.43)."""
+    grid, against the FP32 lane-operation rate of the library's measured FFMA
+    loop, near the 148 SMs x 128 lanes x 2032 MHz = 38.5 T operations/s of the
+    data sheet; the kernel also recomputes the 128 x 80 region of every
+    112 x 64 tile, x1.43)."""
     rows, cols, iters = W.STENCIL_HEADLINE
     prm = cp.Context.stencil_params(**W.STENCIL_PARAMS)
     g = torch.Generator(device=dev)
@@ -700,10 +701,14 @@ def measure_stencil(ctx, cp, W, torch, dev, reps=5):
         except (OSError, ValueError, KeyError):
             roof["peak"], roof["peak_source"] = 6400.0, "fallback 6.4 TB/s"
     else:
+        # FP32 lane operations per second of the measured FFMA loop (an FMA
+        # counts once here, as in the 10 operations per cell and step)
         region = (128.0 * 80.0) / (112.0 * 64.0)
         roof = {"bound": "alu", "unit": "Tops/s",
-                "achieved": cell_steps * 10 / (ms / 1e3) / 1e12, "peak": 38.5,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz",
+                "achieved": cell_steps * 10 / (ms / 1e3) / 1e12, "peak": ctx.peak_ffma() / 2,
+                "peak_source": "measured FFMA loop (compar_peak_ffma, FMA instructions x 32 "
+                               "lanes per second) (of measured)",
+                "derived_peak": 38.5, "derived_source": "148 SMs x 128 FP32 lanes x 2032 MHz",
                 "with_halo": cell_steps * 10 * region / (ms / 1e3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return {"workload": f"thermal stencil {rows}x{cols}, {iters} steps, seeded chip",
