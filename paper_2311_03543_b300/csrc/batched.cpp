@@ -45,8 +45,11 @@ struct BatchedState {
   // the graph's second branch (pre-pass, then the problems that need it)
   cudaStream_t capture2 = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-  // (problems, tiles, jobs, pre-pass tiles, bn, problems needing no pre-pass, their tiles)
-  using Key = std::tuple<int, int, int, int, int, int, int>;
+  // (problems, tiles, jobs, pre-pass tiles, bn, problems needing no pre-pass,
+  // their tiles, whether a pre-pass job transposes): everything the captured
+  // launches bake in (grids, kernel instances, branch shape); the rest is in
+  // the descriptors the graph copies from the staging buffers at each replay
+  using Key = std::tuple<int, int, int, int, int, int, int, int>;
   std::map<Key, cudaGraphExec_t> graphs;
   // the batch whose descriptors are in the staging buffers now: the same batch
   // again (same problems, configuration, tolerance and workspace) only
@@ -363,7 +366,7 @@ int run_grouped(compar_ctx* ctx, int count, const compar_problem_t* probs, doubl
   if (static_cast<size_t>(n0) == nprob) tiles0 = tile_acc;
   const int n1 = ngroup - n0, tiles1 = n1 > 0 ? tile_acc : 0;
   const BatchedState::Key key = std::make_tuple(ngroup, tiles0 + tiles1, njobs, ptile_acc, bn, n0,
-                                                tiles0);
+                                                tiles0, any_transpose ? 1 : 0);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraph_t graph = nullptr;

@@ -197,6 +197,28 @@ def test_graph_replay_with_new_data(ctx):
         _check(specs, host, 1e-5)
 
 
+def test_graph_cache_separates_3xbf16_and_tf32_batches(ctx):
+    """The same float32 shapes at a 3xBF16 tolerance and at a TF32 one.  With
+    A's rows not 16-byte aligned, A is copied in both modes, so the two
+    batches have the same counts of problems, tiles, pre-pass jobs and
+    pre-pass tiles.  Only the TF32 batch's pre-pass transposes B, though, and
+    each batch must replay a graph captured for its own mode.  K > N
+    throughout; fresh data every round."""
+    import paper_2311_03543_b300 as cp
+    specs = [(50, 20, 300, W.F32, 1, 0, 0, 1.0, 0.0), (130, 40, 257, W.F32, 1, 0, 0, 0.5, 1.0),
+             (70, 64, 190, W.F32, 3, 0, 0, 1.0, 0.0)]
+    assert all((k + pa) % 4 != 0 and k > n for (m, n, k, dt, pa, *_rest) in specs)
+    for rnd, (tol, lim) in enumerate([(1e-5, 1e-5), (1e-2, 2e-3), (1e-5, 1e-5), (1e-2, 2e-3)]):
+        probs, host = _make_batch(specs, 700 + 50 * rnd)
+        ctx.force_variant(cp.V_GROUPED)
+        try:
+            ctx.gemm_batched(probs, tol=tol)
+        finally:
+            ctx.force_variant(None)
+        assert ctx.check_device_error() == cp.OK
+        _check(specs, host, lim)
+
+
 def test_loop_and_grouped_agree(ctx):
     import paper_2311_03543_b300 as cp
     specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(12, seed=4, lo=16, hi=200)]
