@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-GEMM batched measurement (profiling runs)")
     ap.add_argument("--peaks", action="store_true",
@@ -537,6 +538,10 @@ def main():
     if not args.no_stencil and rank == 0:
         stencil = measure_stencil(ctx, cp, W, torch, dev)
 
+    accuracy = None
+    if not args.no_accuracy and rank == 0:
+        accuracy = measure_accuracy(ctx, cp, W, torch, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_sample()
@@ -555,7 +560,7 @@ def main():
                                         for v in sorted(set(picks))}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches, "regret_pct": regret, "batched_512": batched,
-                "stencil": stencil}
+                "stencil": stencil, "accuracy": accuracy}
         print(json.dumps(line), flush=True)
         if args.detail:
             with open(args.detail, "w") as f:
@@ -656,6 +661,36 @@ def measure_batched(ctx, cp, W, torch, dev, reps=5):
             "ms_per_gemm_launches": ms_loop,
             "tflops_per_gemm_launches": flops / (ms_loop / 1e3) / 1e12,
             "autotune_ms": dict(zip(names, tuned_ms)), "roofline": roof}
+
+
+def measure_accuracy(ctx, cp, W, torch, dev, nrows=32):
+    """The metric's error, both ways, outside the timed region: for a few sweep
+    shapes (f32 uniform[-1,1], seeded), the variant selected at the metric's
+    tolerance is checked (a) against FP64 products of `nrows` sampled rows by
+    the library's residual check, the gate, and (b) against the forced FP32
+    SIMT variant's output on the same inputs (relative Frobenius difference
+    over all of C), the metric's wording."""
+    out = []
+    for i, (m, n, k) in enumerate([(256, 256, 256), (1024, 1024, 1024), (4096, 4096, 4096),
+                                   (4096, 4096, 64), (16, 4096, 4096)]):
+        g = torch.Generator(device=dev)
+        g.manual_seed(900 + i)
+        A = torch.rand((m, k), generator=g, device=dev) * 2 - 1
+        B = torch.rand((k, n), generator=g, device=dev) * 2 - 1
+        C = torch.empty((m, n), device=dev)
+        ctx.gemm(A, B, C, tol=TOL)
+        v = ctx.last_variant()
+        fp64 = ctx.residual_check(A, B, C, nrows=nrows, seed=7 + i)
+        S = torch.empty_like(C)
+        ctx.force_variant(cp.V_SIMT)
+        try:
+            ctx.gemm(A, B, S, tol=TOL)
+        finally:
+            ctx.force_variant(None)
+        vs_simt = float((C.double() - S.double()).norm() / S.double().norm())
+        out.append({"shape": f"{m}x{n}x{k}", "variant": cp.VARIANT_NAMES[v],
+                    "rel_err_vs_fp64_rows": fp64, "rel_err_vs_fp32_simt": vs_simt})
+    return {"tol": TOL, "fp64_rows": nrows, "shapes": out}
 
 
 def measure_stencil(ctx, cp, W, torch, dev, reps=5):
