@@ -1,6 +1,9 @@
 """Precision study (GPU): 4096^3 with float32 inputs normal(0,1) and
 ill-scaled (column k of A times 10^U(-3,3)), every variant forced in turn.
 
+A secondary ill-scaled row scales the columns of B instead (the output
+columns; per-tensor FP8 scaling then fits the largest column).
+
 Two errors per variant, both against the FP64 oracle on the first and last
 row of every 128-row tile plus one seeded row inside it:
 * total      — against the product of the float32 inputs;
@@ -39,6 +42,8 @@ def ctx():
 def _data(kind):
     if kind == "normal":
         return W.normal(M, K, seed=3), W.normal(K, N_, seed=33)
+    if kind == "ill_scaled_b":   # secondary row: column j of B times 10^U(-3,3)
+        return W.normal(M, K, seed=3), W.ill_scaled(K, N_, seed_values=33, seed_scales=5)
     return W.ill_scaled(M, K, seed_values=3, seed_scales=4), W.normal(K, N_, seed=33)
 
 
@@ -52,7 +57,7 @@ def _exact_operands(v, A, B):
     return A.astype(np.float64), B.astype(np.float64), 1.0
 
 
-@pytest.mark.parametrize("kind", ["normal", "ill_scaled"])
+@pytest.mark.parametrize("kind", ["normal", "ill_scaled", "ill_scaled_b"])
 def test_precision_study(ctx, kind):
     import torch
     from gpu_util import abs_product_rows, assert_elementwise, elem_bound
@@ -86,8 +91,8 @@ def test_precision_study(ctx, kind):
             assert arith <= max(1e-5, 0.05 * K * u), (v, arith)
         else:
             assert arith <= 1e-5, (v, arith)
-    if kind == "normal":
-        assert report[1][0] <= 1e-5 and report[5][0] <= 1e-5
+    if kind in ("normal", "ill_scaled_b"):   # scaling whole output columns keeps
+        assert report[1][0] <= 1e-5 and report[5][0] <= 1e-5   # each column's relative error
     assert report[3][0] <= 2.0 ** -7
     assert report[4][0] <= 2.0 ** -3
     assert report[2][0] <= 2.0 ** -9
