@@ -143,7 +143,7 @@ int compar_stencil_select(compar_ctx_t ctx, int64_t rows, int64_t cols, int iter
   DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || rows <= 0 || cols <= 0 || iters < 0) return COMPAR_ERR_INVALID;
   if (ctx->host_only) {
-    // no device to ask about TMA: judge by the grid alone
+    // no device to ask about TMA: decide by the grid alone
     StencilSel& st = ctx->stencil;
     if (st.forced >= 0) return st.forced;
     int best = -1;
