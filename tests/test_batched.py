@@ -219,6 +219,46 @@ def test_graph_cache_separates_3xbf16_and_tf32_batches(ctx):
         _check(specs, host, lim)
 
 
+def _check_elementwise(specs, host):
+    """Every problem element by element within its mode's worst-case bound
+    relative to |alpha| |A||B| + |beta| |C0| (3xBF16 for float32, exact-input
+    accumulation for bf16).  For tiny random problems this is the right test:
+    a short dot product can cancel, and then the relative Frobenius error of a
+    two-element output says little about the arithmetic."""
+    import torch
+    from gpu_util import assert_elementwise, elem_bound
+    torch.cuda.synchronize()
+    for (m, n, k, dt, pa, pb, pc, alpha, beta), (A, B, C0, dA, dB, dC) in zip(specs, host):
+        if m == 0 or n == 0:
+            continue
+        out = dC.cpu().numpy()
+        Ax, Bx = _exact(A[:, :k], dt), _exact(B[:, :n], dt)
+        c0 = C0[:, :n].astype(np.float64)
+        ref = oracle.gemm(Ax, Bx, alpha=alpha, beta=beta, C0=c0)
+        scale = abs(alpha) * oracle.gemm(np.abs(Ax), np.abs(Bx)) + abs(beta) * np.abs(c0)
+        assert_elementwise(out[:, :n], ref, scale, elem_bound(5 if dt == W.F32 else 3, k))
+        assert np.array_equal(out[:, n:], C0[:, n:])
+
+
+def test_staging_growth_drops_and_recaptures_graphs(ctx):
+    """A small batch, then one far larger (the descriptor staging buffers
+    grow, which frees the old ones and drops every graph that copies from
+    them), then the small batch again, captured anew: all against the
+    oracle, element by element."""
+    import paper_2311_03543_b300 as cp
+    small = _random_specs(12, seed=21, hi=120)
+    big = _random_specs(1500, seed=22, lo=1, hi=40)
+    for rnd, specs in enumerate([small, big, small]):
+        probs, host = _make_batch(specs, 800 + 100 * rnd)
+        ctx.force_variant(cp.V_GROUPED)
+        try:
+            ctx.gemm_batched(probs, tol=1e-5)
+        finally:
+            ctx.force_variant(None)
+        assert ctx.check_device_error() == cp.OK
+        _check_elementwise(specs, host)
+
+
 def test_loop_and_grouped_agree(ctx):
     import paper_2311_03543_b300 as cp
     specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(12, seed=4, lo=16, hi=200)]
