@@ -133,8 +133,13 @@ const char* compar_last_error(void);
  *               k == 0: C = beta * C).
  *   dtype     : element type of A and B.
  *   tol       : relative Frobenius error asked for, measured against the
- *               exact product of the inputs as given; tol <= 0 means the
- *               default (1e-5 for F32, "best available" for BF16/F8).
+ *               exact product of the inputs as given; tol <= 0 means 1e-5
+ *               for every dtype.  A variant is eligible when its error
+ *               model (relative Frobenius error on data that does not
+ *               cancel) times the margin is at most tol; every input gets
+ *               the variant's element-wise worst-case bound relative to
+ *               |alpha| |A||B| + |beta| |C|, so a short dot product that
+ *               cancels may exceed tol relatively.
  *   A, B      : device pointers, row-major contiguous (lda = k, ldb = n).
  *   C         : device float32, row-major contiguous (ldc = n).
  *   stream    : cudaStream_t.
