@@ -152,7 +152,10 @@ const char* compar_last_error(void);
  * once a call of the same shape has run on the context outside the capture
  * (the decision is cached and the workspace has its size); a call that
  * would grow the workspace while `stream` is captured returns
- * COMPAR_ERR_UNSUPPORTED. */
+ * COMPAR_ERR_UNSUPPORTED.  Such a refusal, or device memory that runs out
+ * while the workspace grows (COMPAR_ERR_CUDA), is the caller's to handle:
+ * it changes no later selection.  A variant whose own launch fails is
+ * quarantined for the context and the call re-dispatched. */
 int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
                 compar_dtype_t dtype, double tol, const void* A,
                 const void* B, float* C, void* stream);

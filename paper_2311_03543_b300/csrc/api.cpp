@@ -73,13 +73,30 @@ DeviceScope::~DeviceScope() {
 // Growing a workspace inside a stream capture would hand the context memory
 // that only the captured graph owns: refused (a call of the same shape before
 // the capture grows it).
+// Set when a call failed for a reason of the caller's (a workspace that
+// would have to grow inside a stream capture, or device memory that ran
+// out), not because its variant cannot run: such a failure is returned to
+// the caller and quarantines nothing.
+static thread_local bool g_transient_failure = false;
+
 static int refuse_growth_in_capture(cudaStream_t s) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   COMPAR_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   if (cap == cudaStreamCaptureStatusNone) return COMPAR_OK;
   g_last_error =
       "the workspace must grow while the stream is captured: run the call once before capturing";
+  g_transient_failure = true;
   return COMPAR_ERR_UNSUPPORTED;
+}
+
+static int workspace_alloc(void** p, size_t bytes, cudaStream_t s) {
+  const cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaSuccess) return COMPAR_OK;
+  (void)cudaGetLastError();
+  *p = nullptr;
+  set_last_cuda_error(e, "cudaMallocAsync (workspace)", __FILE__, __LINE__);
+  g_transient_failure = true;
+  return COMPAR_ERR_CUDA;
 }
 
 int Workspace::ensure(size_t need, cudaStream_t s) {
@@ -90,7 +107,7 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
   if (ptr) COMPAR_CUDA_TRY(cudaFreeAsync(ptr, s));
   ptr = nullptr;
   bytes = 0;
-  COMPAR_CUDA_TRY(cudaMallocAsync(&ptr, grow, s));
+  if (int rc = workspace_alloc(&ptr, grow, s); rc != COMPAR_OK) return rc;
   bytes = grow;
   return COMPAR_OK;
 }
@@ -102,7 +119,9 @@ int Workspace::ensure_counters(size_t n, cudaStream_t s) {
   if (counters) COMPAR_CUDA_TRY(cudaFreeAsync(counters, s));
   counters = nullptr;
   counter_n = 0;
-  COMPAR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&counters), grow * sizeof(*counters), s));
+  if (int rc = workspace_alloc(reinterpret_cast<void**>(&counters), grow * sizeof(*counters), s);
+      rc != COMPAR_OK)
+    return rc;
   COMPAR_CUDA_TRY(cudaMemsetAsync(counters, 0, grow * sizeof(*counters), s));
   counter_n = grow;
   return COMPAR_OK;
@@ -477,11 +496,13 @@ int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
     const int v = select_variant(ctx, c);
     if (v < 0) return v;
     ctx->last_variant = v;
+    g_transient_failure = false;
     const int rc = run_one(ctx, v, c, s);
     if (rc == COMPAR_OK) {
       maybe_retrain(ctx);
       return rc;
     }
+    if (g_transient_failure) return rc;  // the caller's condition: nothing quarantined
     // A variant that failed to launch is quarantined for this context and
     // the call is re-dispatched to the next choice.
     if (ctx->log)

@@ -7,6 +7,8 @@
 * Host side: COMPAR_TEST_FAIL_VARIANT makes the dispatcher treat one variant's
   launch as failed; the runtime quarantines it and re-dispatches the call to
   the next choice, which still computes the right product.
+* A call refused for the caller's reasons (its workspace would have to grow
+  inside a stream capture) returns its status and quarantines nothing.
 * Bad arguments are refused synchronously."""
 import os
 
@@ -59,6 +61,44 @@ def test_injected_variant_failure_is_quarantined(monkeypatch):
         # the quarantined variant stays out of later calls of this context
         ctx.clear_decisions()
         assert ctx.select(m, n, k, cp.F32, 1e-5) != first
+
+
+# the refused call enqueues nothing, so the capture ends with an empty graph
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_capture_refusal_quarantines_nothing():
+    """With the decision cached but the workspace still empty, the call inside
+    a stream capture is refused (COMPAR_ERR_UNSUPPORTED); the refused variant
+    is still the selection afterwards, and the same call outside the capture
+    runs it and matches the oracle."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    m = n = k = 2048
+    A = torch.from_numpy(W.uniform(m, k, 13)).cuda()
+    B = torch.from_numpy(W.uniform(k, n, 14)).cuda()
+    C = torch.empty((m, n), device="cuda")
+    with cp.Context(0) as ctx:
+        v = ctx.select(m, n, k, cp.F32, 1e-5)     # cached; nothing has run yet
+        assert v == cp.V_SPLIT3, cp.VARIANT_NAMES[v]  # its pre-pass needs the workspace
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        status = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            try:
+                ctx.gemm(A, B, C, tol=1e-5, stream=s)
+            except cp.ComparError as e:
+                status = e.status
+        del g                                     # never replayed
+        assert status == cp.ERR_UNSUPPORTED
+        ctx.clear_decisions()
+        assert ctx.select(m, n, k, cp.F32, 1e-5) == v
+        ctx.gemm(A, B, C, tol=1e-5)
+        assert ctx.last_variant() == v
+        torch.cuda.synchronize()
+        rows = W.sample_rows(m, 16, 15)
+        ref = oracle.gemm_rows(A.cpu().numpy(), B.cpu().numpy(), rows)
+        assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5
+        assert ctx.check_device_error() == cp.OK
 
 
 def test_bad_arguments_are_refused():
