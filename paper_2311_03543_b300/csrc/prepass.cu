@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "common.h"
@@ -685,18 +686,21 @@ int launch_grouped_prepass(const PrepassJob* d_jobs, int njobs, int total_tiles,
                            bool transpose, cudaStream_t s) {
   if (njobs <= 0 || total_tiles <= 0) return COMPAR_OK;
   // one full wave of resident blocks
-  static int resident[kMaxDevices][2] = {};
+  // (queried once per device; threads driving other contexts may race to
+  // fill it, with the same value)
+  static std::atomic<int> resident[kMaxDevices][2] = {};
   const int d = current_device_index();
   if (d < 0) {
     set_last_error_text("grouped pre-pass: no usable current device");
     return COMPAR_ERR_CUDA;
   }
-  int& r = resident[d][transpose ? 1 : 0];
+  int r = resident[d][transpose ? 1 : 0].load(std::memory_order_relaxed);
   if (r == 0) {
     int n = 0;
     COMPAR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &n, transpose ? grouped_prepass_kernel<true> : grouped_prepass_kernel<false>, 256, 0));
     r = std::max(n, 1);
+    resident[d][transpose ? 1 : 0].store(r, std::memory_order_relaxed);
   }
   const int grid = static_cast<int>(std::min<int64_t>(total_tiles, static_cast<int64_t>(num_sms) * r));
   if (transpose)
