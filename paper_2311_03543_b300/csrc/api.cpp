@@ -377,7 +377,10 @@ static cudaEvent_t take_event(compar_ctx* ctx) {
     return e;
   }
   cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    (void)cudaGetLastError();  // the call goes untimed
+    return nullptr;
+  }
   return e;
 }
 
@@ -389,6 +392,8 @@ static void resolve_pending(compar_ctx* ctx) {
       p.rec.time_ms = ms;
       ctx->rec.push(p.rec);
       ctx->hist.observe(p.rec.variant, p.rec.dtype, p.rec.m, p.rec.n, p.rec.k, p.rec.batch, ms);
+    } else {
+      (void)cudaGetLastError();  // a record lost, not an error of a later launch
     }
     ctx->event_pool.push_back(p.start);
     ctx->event_pool.push_back(p.stop);
@@ -438,22 +443,34 @@ static bool gate_ready(compar_ctx* ctx) {
 static int run_one(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   bool gated = false;
+  // A call captured into a graph is not timed: its events would belong to
+  // the graph, not to this call.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  bool record = false;
   if (ctx->rec.on) {
+    if (cudaStreamIsCapturing(s, &cap) == cudaSuccess) record = cap == cudaStreamCaptureStatusNone;
+    else (void)cudaGetLastError();
+  }
+  if (record) {
     e0 = take_event(ctx);
     e1 = take_event(ctx);
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (e0 && e1 && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
-        cap == cudaStreamCaptureStatusNone && gate_ready(ctx))
+    if (!e0 || !e1) {  // untimed: give back the one that was taken
+      if (e0) ctx->event_pool.push_back(e0);
+      if (e1) ctx->event_pool.push_back(e1);
+      e0 = e1 = nullptr;
+      record = false;
+    }
+    if (record && gate_ready(ctx))
       gated = launch_record_gate(ctx->gate_dev, ctx->gate_ticket + 1, s) == COMPAR_OK;
     if (e0) cudaEventRecord(e0, s);
   }
   const int rc = launch_variant(ctx, v, c, s);
-  if (ctx->rec.on && e0 && e1) cudaEventRecord(e1, s);
+  if (record && e0 && e1) cudaEventRecord(e1, s);
   if (gated) {
     // the whole call and its end event are enqueued: open the gate
     __atomic_store_n(ctx->gate_host, ++ctx->gate_ticket, __ATOMIC_RELEASE);
   }
-  if (ctx->rec.on && e0 && e1) {
+  if (record && e0 && e1) {
     if (rc == COMPAR_OK) {
       ctx->pending.push_back(PendingTiming{e0, e1, make_record(c, v)});
       if (ctx->pending.size() >= 4096) resolve_pending(ctx);
@@ -468,11 +485,18 @@ static int run_one(compar_ctx* ctx, int v, const GemmCall& c, cudaStream_t s) {
 // Online mode: after `retrain_every` new timing records, fine-tune the MLP
 // from its current weights on every record (synchronous, on the model's own
 // stream) and start using it for new decisions.
-static void maybe_retrain(compar_ctx* ctx) {
+static void maybe_retrain(compar_ctx* ctx, cudaStream_t s) {
   auto& o = ctx->online;
   if (o.retrain_every <= 0) return;
   const int64_t have = static_cast<int64_t>(ctx->rec.ring.size() + ctx->pending.size());
   if (have - o.records_at_train < o.retrain_every) return;
+  // not while the caller's stream is captured: training synchronises
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return;
   resolve_pending(ctx);
   const int steps = o.finetune_steps > 0 ? o.finetune_steps : 500;
   float vl = 0;
@@ -499,7 +523,7 @@ int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
     g_transient_failure = false;
     const int rc = run_one(ctx, v, c, s);
     if (rc == COMPAR_OK) {
-      maybe_retrain(ctx);
+      maybe_retrain(ctx, s);
       return rc;
     }
     if (g_transient_failure) return rc;  // the caller's condition: nothing quarantined

@@ -649,6 +649,44 @@ def test_dependent_calls_back_to_back(ctx, m, n, k):
     assert N.rel_frobenius(got, ref) <= 3 * TOL_F32
 
 
+def test_recording_skips_captured_calls():
+    """With timing records on, a call captured into a graph records nothing
+    (its events would belong to the graph), and the eager calls around it are
+    recorded, run the same variant and match the oracle; nothing is
+    quarantined."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import dev, host
+    m, n, k = 1024, 768, 512
+    A = W.uniform(m, k, seed=97); B = W.uniform(k, n, seed=98)
+    ref = oracle.gemm(A, B)
+    dA, dB = dev(A), dev(B)
+    C = torch.empty((m, n), device="cuda")
+    with cp.Context(0) as c:
+        c.record_enable(True)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            c.gemm(dA, dB, C, tol=1e-5, stream=s)             # decision and workspace
+        s.synchronize()
+        v = c.last_variant()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            c.gemm(dA, dB, C, tol=1e-5, stream=s)
+        for _ in range(2):
+            C.fill_(float("nan"))
+            g.replay()
+            assert N.rel_frobenius(host(C), ref) <= TOL_F32
+        C.fill_(float("nan"))
+        c.gemm(dA, dB, C, tol=1e-5)
+        assert c.last_variant() == v
+        assert N.rel_frobenius(host(C), ref) <= TOL_F32
+        recs = c.records()
+        assert len(recs) == 2 and all(r.variant == v and r.time_ms > 0 for r in recs)
+        c.clear_decisions()
+        assert c.select(m, n, k, cp.F32, 1e-5) == v
+        assert c.check_device_error() == cp.OK
+
+
 @pytest.mark.parametrize("m,n,k", [(2560, 2304, 1024), (16, 4096, 4096), (1024, 1024, 1024)])
 def test_captured_call_replays(ctx, m, n, k):
     """A call captured into a CUDA graph (after one call of the shape outside
