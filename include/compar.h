@@ -32,8 +32,9 @@
  * on its context's device: the call makes that device current and restores
  * the caller's current device before returning, so one process may drive
  * several GPUs with one context each; the stream passed must belong to the
- * context's device.  A context is not thread-safe: use one context per host
- * thread.  The calls on one context
+ * context's device.  A call clears a non-sticky CUDA error left pending on
+ * the calling thread (cudaGetLastError) before it starts.  A context is not
+ * thread-safe: use one context per host thread.  The calls on one context
  * share its device workspace (operand copies, partial sums, arrival
  * counters), so they must run in order on the GPU: issue them on one stream,
  * or order the streams yourself (events); calls that overlap on the GPU give

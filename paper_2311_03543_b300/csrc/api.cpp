@@ -59,6 +59,9 @@ cudaError_t smem_opt_in(const void* func, int bytes) {
 
 DeviceScope::DeviceScope(int device) {
   if (device < 0) return;
+  // A non-sticky error the caller left pending would otherwise be read by the
+  // library's post-launch check as its own launch failing.
+  (void)cudaGetLastError();
   if (cudaGetDevice(&prev_) != cudaSuccess) {
     (void)cudaGetLastError();
     return;

@@ -119,7 +119,9 @@ cudaError_t smem_opt_in(const void* func, int bytes);
 
 // Makes a context's device current for one API call and puts the caller's
 // device back when the call returns.  Does nothing when that device is
-// already current, or for device -1 (host-only contexts).
+// already current, or for device -1 (host-only contexts).  It also clears a
+// non-sticky CUDA error the caller left pending, which the call's launch
+// checks would otherwise read as their own.
 class DeviceScope {
  public:
   explicit DeviceScope(int device);

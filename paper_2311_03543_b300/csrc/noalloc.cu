@@ -87,6 +87,9 @@ extern "C" int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float a
   if ((m + 31) / 32 > 65535) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && C == nullptr) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && k > 0 && (A == nullptr || B == nullptr)) return COMPAR_ERR_INVALID;
+  // a non-sticky error the caller left pending is not this call's launch
+  // failing (clearing it allocates nothing)
+  (void)cudaGetLastError();
   int num_sms = 0;
   float* scratch = nullptr;
   int rc = setup_current_device(&num_sms, &scratch);

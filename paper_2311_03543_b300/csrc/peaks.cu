@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) ffma_kernel(int iters, float seed, float*
 using namespace compar;
 
 extern "C" int compar_peak_ffma(compar_ctx_t ctx, float* tflops, void* stream) {
+  DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !tflops) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -101,6 +101,32 @@ def test_capture_refusal_quarantines_nothing():
         assert ctx.check_device_error() == cp.OK
 
 
+def test_error_left_pending_by_the_caller_fails_no_launch():
+    """A CUDA error the caller left pending (an ignored failing runtime call)
+    is not read as the library's launch failing: the selected variant runs,
+    stays the selection, and matches the oracle."""
+    import ctypes
+    import torch
+    import paper_2311_03543_b300 as cp
+    rt = ctypes.CDLL("libcudart.so.13")      # the runtime the library runs on
+    m = n = k = 1024
+    A = torch.from_numpy(W.uniform(m, k, 16)).cuda()
+    B = torch.from_numpy(W.uniform(k, n, 17)).cuda()
+    C = torch.empty((m, n), device="cuda")
+    with cp.Context(0) as ctx:
+        v = ctx.select(m, n, k, cp.F32, 1e-5)
+        torch.cuda.synchronize()
+        assert rt.cudaSetDevice(ctypes.c_int(1 << 20)) != 0   # leaves an error pending
+        ctx.gemm(A, B, C, tol=1e-5)
+        assert ctx.last_variant() == v
+        ctx.clear_decisions()
+        assert ctx.select(m, n, k, cp.F32, 1e-5) == v
+        torch.cuda.synchronize()
+        rows = W.sample_rows(m, 16, 18)
+        ref = oracle.gemm_rows(A.cpu().numpy(), B.cpu().numpy(), rows)
+        assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5
+
+
 def test_bad_arguments_are_refused():
     import torch
     import paper_2311_03543_b300 as cp
