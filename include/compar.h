@@ -172,7 +172,8 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
  * Ordering: A and B are read from the moment of the call (they must be
  * ready in host memory then, not merely by the time `stream` gets there);
  * C is in host memory once `stream` reaches the end of the call.  Errors
- * as compar_gemm. */
+ * as compar_gemm; on a stream being captured into a CUDA graph it returns
+ * COMPAR_ERR_UNSUPPORTED (its copy streams are its own). */
 int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_t dtype,
                      double tol, const void* A, const void* B, float* C, void* stream);
 
@@ -197,7 +198,9 @@ typedef struct {
  * FP32 accuracy when tol <= 1e-5 (3xBF16 mode), else on TF32; BF16 problems
  * on bf16 tensor cores.  The selector picks between one persistent grouped
  * launch captured in a CUDA graph (cached per batch signature) and one launch
- * per problem.  Returns as compar_gemm. */
+ * per problem.  Returns as compar_gemm.  The call runs a graph of its own and
+ * waits on its staging buffers, so it cannot itself be captured: on a stream
+ * being captured it returns COMPAR_ERR_UNSUPPORTED and enqueues nothing. */
 int compar_gemm_batched(compar_ctx_t ctx, int count,
                         const compar_problem_t* probs, double tol,
                         void* stream);
@@ -235,7 +238,8 @@ int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
  * once untimed and three times timed (CUDA events on `stream`), so C is
  * written several times: with beta != 0 the final contents are not the
  * product.  times_ms (nullable, 5 floats) receives the medians, *best
- * (nullable) the choice.  Synchronises `stream`. */
+ * (nullable) the choice.  Synchronises `stream`, so a stream being captured
+ * into a CUDA graph is refused (COMPAR_ERR_UNSUPPORTED). */
 int compar_autotune_batched(compar_ctx_t ctx, int count,
                             const compar_problem_t* probs, double tol,
                             void* stream, float* times_ms, int* best);

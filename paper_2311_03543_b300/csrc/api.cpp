@@ -92,6 +92,14 @@ static int refuse_growth_in_capture(cudaStream_t s) {
   return COMPAR_ERR_UNSUPPORTED;
 }
 
+int refuse_capture(cudaStream_t s, const char* call) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  COMPAR_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap == cudaStreamCaptureStatusNone) return COMPAR_OK;
+  g_last_error = std::string(call) + " cannot be captured into a CUDA graph";
+  return COMPAR_ERR_UNSUPPORTED;
+}
+
 static int workspace_alloc(void** p, size_t bytes, cudaStream_t s) {
   const cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e == cudaSuccess) return COMPAR_OK;
@@ -680,6 +688,9 @@ int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_d
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   int rc = check_ptrs(m, n, k, A, B, C);
+  if (rc != COMPAR_OK) return rc;
+  // its copy streams and events are its own: not a capturable call
+  rc = refuse_capture(static_cast<cudaStream_t>(stream), "compar_gemm_host");
   if (rc != COMPAR_OK) return rc;
   if (m == 0 || n == 0) return COMPAR_OK;
   GemmCall c;

@@ -503,6 +503,9 @@ extern "C" int compar_gemm_batched(compar_ctx_t ctx, int count, const compar_pro
   if (count == 0) return COMPAR_OK;
   tol = tol > 0 ? tol : 1e-5;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the grouped path waits on its staging event and runs a graph of its own
+  rc = refuse_capture(s, "compar_gemm_batched");
+  if (rc != COMPAR_OK) return rc;
   if (ctx->forced >= 0 && ctx->forced != COMPAR_V_GROUPED)
     return run_loop(ctx, count, probs, tol, s);
   int cfg = 1;
@@ -529,6 +532,8 @@ extern "C" int compar_autotune_batched(compar_ctx_t ctx, int count, const compar
   if (count == 0) return COMPAR_ERR_INVALID;
   tol = tol > 0 ? tol : 1e-5;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = refuse_capture(s, "compar_autotune_batched");  // it times and synchronises
+  if (rc != COMPAR_OK) return rc;
   cudaEvent_t e0, e1;
   COMPAR_CUDA_TRY(cudaEventCreate(&e0));
   COMPAR_CUDA_TRY(cudaEventCreate(&e1));

@@ -122,6 +122,11 @@ cudaError_t smem_opt_in(const void* func, int bytes);
 // already current, or for device -1 (host-only contexts).  It also clears a
 // non-sticky CUDA error the caller left pending, which the call's launch
 // checks would otherwise read as their own.
+// COMPAR_OK, or COMPAR_ERR_UNSUPPORTED (with the error text) when `s` is being
+// captured into a CUDA graph: for calls that synchronise or run a graph of
+// their own.
+int refuse_capture(cudaStream_t s, const char* call);
+
 class DeviceScope {
  public:
   explicit DeviceScope(int device);

@@ -127,6 +127,48 @@ def test_error_left_pending_by_the_caller_fails_no_launch():
         assert N.rel_frobenius(C.cpu().numpy()[rows], ref) <= 1e-5
 
 
+# the refused calls enqueue nothing, so the capture ends with an empty graph
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_uncapturable_calls_refuse_a_capturing_stream():
+    """The batched call (it runs a graph of its own), the autotuner (it
+    synchronises) and the host-buffer call (its copy streams are its own)
+    return COMPAR_ERR_UNSUPPORTED on a stream being captured and enqueue
+    nothing; the context then runs the same calls normally."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    m, n, k = 96, 80, 64
+    A = torch.from_numpy(W.uniform(m, k, 19)).cuda()
+    B = torch.from_numpy(W.uniform(k, n, 20)).cuda()
+    C = torch.empty((m, n), device="cuda")
+    probs = [dict(m=m, n=n, k=k, lda=k, ldb=n, ldc=n, dtype=cp.F32, A=A.data_ptr(),
+                  B=B.data_ptr(), C=C.data_ptr())]
+    hA, hB = A.cpu().numpy(), B.cpu().numpy()
+    hC = np.zeros((m, n), np.float32)
+    with cp.Context(0) as ctx:
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        codes = []
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for call in (lambda: ctx.gemm_batched(probs, tol=1e-5, stream=s),
+                         lambda: ctx.autotune_batched(probs, tol=1e-5, stream=s),
+                         lambda: ctx.gemm_host(hA, hB, hC, stream=s)):
+                try:
+                    call()
+                    codes.append(cp.OK)
+                except cp.ComparError as e:
+                    codes.append(e.status)
+        del g
+        assert codes == [cp.ERR_UNSUPPORTED] * 3
+        ref = oracle.gemm(hA, hB)
+        ctx.gemm_batched(probs, tol=1e-5)
+        torch.cuda.synchronize()
+        assert N.rel_frobenius(C.cpu().numpy(), ref) <= 1e-5
+        ctx.gemm_host(hA, hB, hC)
+        torch.cuda.synchronize()
+        assert N.rel_frobenius(hC, ref) <= 1e-5
+
+
 def test_bad_arguments_are_refused():
     import torch
     import paper_2311_03543_b300 as cp
