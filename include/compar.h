@@ -419,7 +419,8 @@ int compar_predict(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
  * FP64 on the GPU over `nrows` rows drawn from `seed` (all rows when nrows >=
  * m); op_scale is the context's fp8 scales for F8E4M3 inputs, else 1.  A, B,
  * C are device pointers, row-major contiguous; C was computed with beta = 0.
- * Labels the accuracy of recorded runs.  Synchronises `stream`. */
+ * Labels the accuracy of recorded runs.  Synchronises `stream` (refused,
+ * COMPAR_ERR_UNSUPPORTED, while `stream` is being captured into a graph). */
 int compar_residual_check(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
                           compar_dtype_t dtype, const void* A, const void* B,
                           const float* C, float alpha, int nrows, uint64_t seed,
@@ -430,7 +431,8 @@ int compar_residual_check(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k,
 /* Time variant `variant_id` on one call with CUDA events on `stream`:
  * `warmup` untimed runs, then `reps` timed runs; *median_ms receives the
  * median.  Adds one timing record per timed run when recording is on, and one
- * observation to the history table.  Synchronises the stream. */
+ * observation to the history table.  Synchronises the stream (refused,
+ * COMPAR_ERR_UNSUPPORTED, while it is being captured into a graph). */
 int compar_measure(compar_ctx_t ctx, int variant_id, int64_t m, int64_t n,
                    int64_t k, compar_dtype_t dtype, double tol, const void* A,
                    const void* B, float* C, int warmup, int reps,
@@ -513,7 +515,9 @@ int compar_stencil_supported(compar_ctx_t ctx, int v, int64_t rows, int64_t cols
 /* The variant compar_stencil would choose (works on host-only contexts). */
 int compar_stencil_select(compar_ctx_t ctx, int64_t rows, int64_t cols, int iters);
 /* Median time (ms, CUDA events on `stream`) of `reps` runs of variant v
- * after `warmup` runs; the result also feeds the stencil history table. */
+ * after `warmup` runs; the result also feeds the stencil history table.
+ * Synchronises `stream` (refused, COMPAR_ERR_UNSUPPORTED, while it is being
+ * captured into a graph). */
 int compar_stencil_measure(compar_ctx_t ctx, int v, int64_t rows, int64_t cols, int iters,
                            const compar_stencil_params_t* params, const float* T_in,
                            const float* P, float* T_out, int warmup, int reps,

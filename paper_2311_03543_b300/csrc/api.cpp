@@ -832,6 +832,8 @@ int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
   int rc = check_ptrs(m, n, k, A, B, C);
   if (rc != COMPAR_OK) return rc;
   if (m == 0 || n == 0 || k == 0) return COMPAR_ERR_INVALID;
+  rc = refuse_capture(static_cast<cudaStream_t>(stream), "compar_measure");  // it synchronises
+  if (rc != COMPAR_OK) return rc;
   GemmCall c;
   c.m = m;
   c.n = n;

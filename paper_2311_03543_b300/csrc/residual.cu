@@ -87,6 +87,8 @@ extern "C" int compar_residual_check(compar_ctx_t ctx, int64_t m, int64_t n, int
     return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = refuse_capture(s, "compar_residual_check"); rc != COMPAR_OK)
+    return rc;  // it reads its result back on the host
   // distinct sampled rows (all rows when nrows >= m)
   std::vector<int64_t> rows;
   if (nrows >= m) {

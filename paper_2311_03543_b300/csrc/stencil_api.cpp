@@ -173,6 +173,8 @@ int compar_stencil_measure(compar_ctx_t ctx, int v, int64_t rows, int64_t cols, 
       cols == 0)
     return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
+  rc = refuse_capture(static_cast<cudaStream_t>(stream), "compar_stencil_measure");
+  if (rc != COMPAR_OK) return rc;  // it synchronises
   const bool a16 = aligned16(T_in) && aligned16(P) && aligned16(T_out);
   if (!stencil_supported(v, rows, cols, a16)) return COMPAR_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

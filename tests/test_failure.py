@@ -130,10 +130,11 @@ def test_error_left_pending_by_the_caller_fails_no_launch():
 # the refused calls enqueue nothing, so the capture ends with an empty graph
 @pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_uncapturable_calls_refuse_a_capturing_stream():
-    """The batched call (it runs a graph of its own), the autotuner (it
-    synchronises) and the host-buffer call (its copy streams are its own)
-    return COMPAR_ERR_UNSUPPORTED on a stream being captured and enqueue
-    nothing; the context then runs the same calls normally."""
+    """The batched call (it runs a graph of its own), the autotuner, the
+    variant timer and the residual check (they synchronise) and the
+    host-buffer call (its copy streams are its own) return
+    COMPAR_ERR_UNSUPPORTED on a stream being captured and enqueue nothing;
+    the context then runs the same calls normally."""
     import torch
     import paper_2311_03543_b300 as cp
     m, n, k = 96, 80, 64
@@ -152,14 +153,16 @@ def test_uncapturable_calls_refuse_a_capturing_stream():
         with torch.cuda.graph(g, stream=s):
             for call in (lambda: ctx.gemm_batched(probs, tol=1e-5, stream=s),
                          lambda: ctx.autotune_batched(probs, tol=1e-5, stream=s),
-                         lambda: ctx.gemm_host(hA, hB, hC, stream=s)):
+                         lambda: ctx.gemm_host(hA, hB, hC, stream=s),
+                         lambda: ctx.measure(cp.V_SIMT, A, B, C, stream=s),
+                         lambda: ctx.residual_check(A, B, C, stream=s)):
                 try:
                     call()
                     codes.append(cp.OK)
                 except cp.ComparError as e:
                     codes.append(e.status)
         del g
-        assert codes == [cp.ERR_UNSUPPORTED] * 3
+        assert codes == [cp.ERR_UNSUPPORTED] * 5
         ref = oracle.gemm(hA, hB)
         ctx.gemm_batched(probs, tol=1e-5)
         torch.cuda.synchronize()
