@@ -211,6 +211,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # torchrun gives every rank one OpenMP thread; rank 0 runs alone here,
+        # on all of the host's cores (set before the oracle's runtime starts)
+        os.environ["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
     shapes = [(n, n, n) for n in range(64, 1025, 64)]
     import oracle
     import workloads as W
