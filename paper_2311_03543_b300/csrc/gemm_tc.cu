@@ -1466,9 +1466,12 @@ int run_tc(const GemmCall& c, const void* A, int64_t lda, const void* B, int64_t
       tc_launch_config<V, kPair>(grid * a.pair, s, attr, cluster, /*programmatic=*/true);
   cudaEvent_t ev = g.prof ? g.prof->begin(s) : nullptr;
   // C through the TMA-store epilogue where it applies (otherwise tc is an
-  // unused copy of ta)
+  // unused copy of ta).  Rows of C must be whole 16-byte chunks (N a
+  // multiple of 4): a bulk-tensor store clipped at the row's end was measured
+  // writing the rest of the last 16-byte chunk, i.e. columns N .. N rounded
+  // up to 4, which with ldc > N are the caller's.
   CUtensorMap tc = ta;
-  if (L::kTmaStore && c.beta == 0.f && a.splits == 1 &&
+  if (L::kTmaStore && c.beta == 0.f && a.splits == 1 && c.n % 4 == 0 &&
       tma_encode_2d(&tc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c.C, c.n, c.m, c.ldc, 32, 16, 128) ==
           COMPAR_OK)
     a.tma_c = 1;

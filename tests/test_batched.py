@@ -259,6 +259,34 @@ def test_staging_growth_drops_and_recaptures_graphs(ctx):
         _check_elementwise(specs, host)
 
 
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 7, 8, 9])
+def test_problems_run_singly_leave_c_padding_alone(ctx, v):
+    """Problems run one by one (a forced tensor-core variant) with ldc > n
+    and beta == 0: the padding columns of every row of C keep their
+    contents, also when n is not a multiple of 4 (a bulk-tensor store
+    clipped at the row's end writes up to the next 16-byte boundary, so those
+    calls store C with plain stores)."""
+    import paper_2311_03543_b300 as cp
+    specs = [(52, 77, 796, W.F32, 5, 2, 3, 1.0, 0.0), (13, 1011, 1201, W.F32, 1, 8, 5, 0.5, 0.0),
+             (130, 66, 300, W.F32, 0, 2, 6, 1.0, 0.0), (40, 64, 128, W.F32, 0, 0, 4, 1.0, 0.0)]
+    if v == 4:
+        specs += [(52, 77, 796, W.F8E4M3, 5, 2, 3, 1.0, 0.0)]
+    if v == 9:   # the fused split reads float32 A and B in place: 16-byte rows
+        specs = [(m, n, k, dt, (-k) % 4, (-n) % 4, pc, al, be)
+                 for (m, n, k, dt, pa, pb, pc, al, be) in specs]
+    else:        # (the support query assumes contiguous operands: padded ones run too)
+        specs = [sp for sp in specs if ctx.supported(v, sp[0], sp[1], sp[2], sp[3])]
+    assert specs
+    probs, host = _make_batch(specs, 1200 + v)
+    ctx.force_variant(v)
+    try:
+        ctx.gemm_batched(probs, tol=1e-5)
+    finally:
+        ctx.force_variant(None)
+    assert ctx.check_device_error() == cp.OK
+    _check(specs, host, {2: 2e-3, 3: 1e-2, 4: 1e-1}.get(v, 1e-5))
+
+
 def test_loop_and_grouped_agree(ctx):
     import paper_2311_03543_b300 as cp
     specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(12, seed=4, lo=16, hi=200)]
