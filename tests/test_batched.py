@@ -287,6 +287,50 @@ def test_problems_run_singly_leave_c_padding_alone(ctx, v):
     _check(specs, host, {2: 2e-3, 3: 1e-2, 4: 1e-1}.get(v, 1e-5))
 
 
+def test_random_batches_every_mode(ctx):
+    """Ten seeded random batches on one context (float32 / bf16 / E4M3
+    problems, shapes 1-400, padded leading dimensions, alpha and beta, C
+    NaN-filled where beta == 0), at tolerances that select each float32 mode
+    (3xBF16 at 1e-5, TF32 at 1e-2, one-by-one selection at 2e-6); every third
+    batch repeats an earlier one, so its graph is replayed.  Element by
+    element against the oracle, padding untouched."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import assert_elementwise, elem_bound
+    g = np.random.default_rng(2024)
+    made = []
+    for b in range(10):
+        if b % 3 == 2:
+            specs, tol = made[int(g.integers(0, len(made)))]
+        else:
+            specs = []
+            for _ in range(int(g.integers(1, 60))):
+                m, n, k = (int(x) for x in np.exp(g.uniform(0, np.log(400), size=3)).round())
+                dt = [W.F32, W.F32, W.BF16, W.F8E4M3][int(g.integers(0, 4))]
+                pads = [int(x) for x in g.integers(0, 9, size=3)]
+                specs.append((m, n, k, dt, pads[0], pads[1], pads[2],
+                              float(g.choice([1.0, -1.5])), float(g.choice([0.0, 0.0, 0.5]))))
+            tol = float(g.choice([1e-5, 1e-2, 2e-6]))
+            made.append((specs, tol))
+        probs, host = _make_batch(specs, 3000 + 100 * b)
+        for (m, n, k, dt, pa, pb, pc, al, be), (A, B, C0, dA, dB, dC) in zip(specs, host):
+            if be == 0.0:
+                dC[:, :n] = float("nan")   # C is not read when beta == 0
+        ctx.gemm_batched(probs, tol=tol)
+        assert ctx.check_device_error() == cp.OK
+        torch.cuda.synchronize()
+        for (m, n, k, dt, pa, pb, pc, al, be), (A, B, C0, dA, dB, dC) in zip(specs, host):
+            out = dC.cpu().numpy()
+            Ax, Bx = _exact(A[:, :k], dt), _exact(B[:, :n], dt)
+            c0 = C0[:, :n].astype(np.float64)
+            ref = oracle.gemm(Ax, Bx, alpha=al, beta=be, C0=c0)
+            scale = abs(al) * oracle.gemm(np.abs(Ax), np.abs(Bx)) + abs(be) * np.abs(c0)
+            # the loosest mode a problem of this type can take at this tol
+            v = (2 if tol >= 2e-3 else 5) if dt == W.F32 else 3
+            assert_elementwise(out[:, :n], ref, scale, elem_bound(v, k))
+            assert np.array_equal(out[:, n:], C0[:, n:]), (b, m, n, k, dt)
+
+
 def test_loop_and_grouped_agree(ctx):
     import paper_2311_03543_b300 as cp
     specs = [s[:6] + (0, 1.0, 0.0) for s in _random_specs(12, seed=4, lo=16, hi=200)]
