@@ -649,6 +649,73 @@ def test_dependent_calls_back_to_back(ctx, m, n, k):
     assert N.rel_frobenius(got, ref) <= 3 * TOL_F32
 
 
+@pytest.mark.parametrize("dt_name", ["f32", "bf16", "e4m3"])
+def test_operands_one_element_off_alignment(ctx, dt_name):
+    """A, B and C each start one element past an aligned address (4, 2 or 1
+    byte for A and B, 4 bytes for C): no 16-byte rows or bases, so TMA,
+    vector loads and vector or bulk stores must all step aside.  Every
+    variant the library accepts is forced in turn and matches the oracle
+    element by element; one it cannot run on such operands refuses with
+    COMPAR_ERR_UNSUPPORTED.  Then the selector's own pick."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import assert_elementwise, elem_bound
+    m, n, k = 130, 203, 517
+    if dt_name == "f32":
+        A, B, dt = W.uniform(m, k, seed=61), W.uniform(k, n, seed=62), cp.F32
+        Ax, Bx = A.astype(np.float64), B.astype(np.float64)
+        tdt = torch.float32
+    elif dt_name == "bf16":
+        A, B, dt = W.bf16_input(m, k, seed=61), W.bf16_input(k, n, seed=62), cp.BF16
+        Ax, Bx = N.bf16_to_f32(A).astype(np.float64), N.bf16_to_f32(B).astype(np.float64)
+        tdt = torch.int16
+    else:
+        A, B, dt = W.fp8_input(m, k, seed=61), W.fp8_input(k, n, seed=62), cp.F8E4M3
+        Ax, Bx = N.e4m3_to_f64(A), N.e4m3_to_f64(B)
+        tdt = torch.uint8
+
+    def off_by_one(x):     # a contiguous view one element past the allocation
+        t = torch.empty(x.size + 1, dtype=tdt, device="cuda")[1:].view(x.shape)
+        t.copy_(torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).cuda())
+        return t
+    dA, dB = off_by_one(A), off_by_one(B)
+    assert dA.data_ptr() % 16 != 0 and dB.data_ptr() % 16 != 0
+    ref = oracle.gemm(Ax, Bx)
+    absp = oracle.gemm(np.abs(Ax), np.abs(Bx))
+    ran = []
+    for v in (None, 0, 1, 2, 3, 4, 5, 7, 8, 9):
+        if v is not None and not ctx.supported(v, m, n, k, dt):
+            continue
+        C = torch.full((m * n + 1,), float("nan"), device="cuda")[1:].view(m, n)
+        assert C.data_ptr() % 8 != 0
+        ctx.force_variant(v)
+        try:
+            ctx.gemm(dA, dB, C, tol=1e-5, dtype=dt)
+        except cp.ComparError as e:
+            assert e.status == cp.ERR_UNSUPPORTED and v is not None, (v, e.status)
+            continue
+        finally:
+            ctx.force_variant(None)
+        used = ctx.last_variant() if v is None else v
+        got = C.cpu().numpy()
+        if dt == cp.F32 and used == 3:        # bf16 tensor cores multiply the roundings
+            Ar, Br = N.bf16_round(A), N.bf16_round(B)
+            assert_elementwise(got, oracle.gemm(Ar, Br), oracle.gemm(np.abs(Ar), np.abs(Br)),
+                               elem_bound(3, k))
+        elif dt == cp.F32 and used == 4:      # e4m3 with per-tensor scales
+            qa, sa = N.fp8_quantize(A)
+            qb, sb = N.fp8_quantize(B)
+            Aq, Bq = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)
+            d = float(sa) * float(sb)
+            assert_elementwise(got, oracle.gemm(Aq, Bq) / d, oracle.gemm(np.abs(Aq), np.abs(Bq)) / d,
+                               elem_bound(4, k))
+        else:
+            assert_elementwise(got, ref, absp, elem_bound(used, k))
+        ran.append(used)
+    assert ctx.check_device_error() == cp.OK
+    assert len(ran) >= 3, ran
+
+
 def test_recording_skips_captured_calls():
     """With timing records on, a call captured into a graph records nothing
     (its events would belong to the graph), and the eager calls around it are
