@@ -716,6 +716,39 @@ def test_operands_one_element_off_alignment(ctx, dt_name):
     assert len(ran) >= 3, ran
 
 
+@pytest.mark.parametrize("m,n,k", [(8, 24, 600000), (130, 40, 200000)])
+def test_very_deep_k_many_splits(ctx, m, n, k):
+    """A few outputs over a very deep K: the tensor-core plans split K 72 -
+    148 ways (partial slabs and the reduce pass over them, batched 8 at a
+    time) and SIMT 32 ways.  Every variant forced, and the selector's pick,
+    element by element against the oracle."""
+    import paper_2311_03543_b300 as cp
+    from gpu_util import assert_elementwise, elem_bound
+    A = W.uniform(m, k, seed=63); B = W.uniform(k, n, seed=64)
+    ref = oracle.gemm(A, B)
+    absp = oracle.gemm(np.abs(A), np.abs(B))
+    for v in (None, 0, 1, 2, 3, 4, 5, 7, 8, 9):
+        if v is not None and not ctx.supported(v, m, n, k, cp.F32):
+            continue
+        got = _run(ctx, v, A, B, tol=1e-5)
+        used = ctx.last_variant() if v is None else v
+        if used == 3:
+            Ar, Br = N.bf16_round(A), N.bf16_round(B)
+            assert_elementwise(got, oracle.gemm(Ar, Br), oracle.gemm(np.abs(Ar), np.abs(Br)),
+                               elem_bound(3, k))
+        elif used == 4:
+            qa, sa = N.fp8_quantize(A)
+            qb, sb = N.fp8_quantize(B)
+            Aq, Bq = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)
+            d = float(sa) * float(sb)
+            assert_elementwise(got, oracle.gemm(Aq, Bq) / d,
+                               oracle.gemm(np.abs(Aq), np.abs(Bq)) / d, elem_bound(4, k))
+        else:
+            assert_elementwise(got, ref, absp, elem_bound(used, k))
+            if used in (1, 5, 7, 8, 9):        # FP32-accurate, split K shortens the chains
+                assert N.rel_frobenius(got, ref) <= TOL_F32, (used, N.rel_frobenius(got, ref))
+
+
 def test_recording_skips_captured_calls():
     """With timing records on, a call captured into a graph records nothing
     (its events would belong to the graph), and the eager calls around it are
