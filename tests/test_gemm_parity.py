@@ -749,6 +749,44 @@ def test_very_deep_k_many_splits(ctx, m, n, k):
                 assert N.rel_frobenius(got, ref) <= TOL_F32, (used, N.rel_frobenius(got, ref))
 
 
+def test_output_beyond_two_to_the_31_elements(ctx):
+    """C of 46341 x 46344 (2.15e9 elements, 8.6 GB: offsets past 2^31) with
+    K = 3: the selector's pick and the SIMT, TF32, BF16 and 3xBF16 variants
+    forced.  Rows sampled per 128-row tile (the last ones included) against
+    the oracle, element by element."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    from gpu_util import assert_elementwise, elem_bound
+    m, n, k = 46341, 46344, 3
+    assert m * n > 2 ** 31
+    A = W.uniform(m, k, seed=65); B = W.uniform(k, n, seed=66)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    rows = W.tile_rows(m, seed=67)
+    rows = np.unique(np.concatenate([rows, [m - 1]]))
+    ref = oracle.gemm_rows(A, B, rows)
+    absp = oracle.gemm_rows(np.abs(A), np.abs(B), rows)
+    C = torch.empty((m, n), device="cuda")
+    for v in (None, 1, 2, 3, 5):
+        C.fill_(float("nan"))
+        ctx.force_variant(v)
+        try:
+            ctx.gemm(dA, dB, C, tol=1e-5)
+        finally:
+            ctx.force_variant(None)
+        used = ctx.last_variant() if v is None else v
+        got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+        if used == 3:
+            Ar, Br = N.bf16_round(A), N.bf16_round(B)
+            assert_elementwise(got, oracle.gemm_rows(Ar, Br, rows),
+                               oracle.gemm_rows(np.abs(Ar), np.abs(Br), rows), elem_bound(3, k))
+        else:
+            assert_elementwise(got, ref, absp, elem_bound(used, k))
+        assert not torch.isnan(C[-1]).any()
+    del C
+    torch.cuda.empty_cache()
+    assert ctx.check_device_error() == cp.OK
+
+
 def test_recording_skips_captured_calls():
     """With timing records on, a call captured into a graph records nothing
     (its events would belong to the graph), and the eager calls around it are
