@@ -114,13 +114,47 @@ def e4m3_codes(x):
     return np.where(neg, code | 0x80, code).astype(np.uint8)
 
 
+FP8_SCALE_MAX = np.float32(2.0 ** 126)
+
+
 def fp8_scale(x):
-    """Per-tensor scale ``s = 448 / amax(|x|)`` in float32 (1 when amax = 0)."""
+    """Per-tensor scale ``s = min(448 / amax(|x|), 2^126)`` in float32 (1 when
+    amax = 0).  The cap: 448 / amax overflows float32 for amax < 448 / FLT_MAX,
+    and the dequantisation factor 1 / s must stay a normal float32 (2^-126 is
+    the smallest)."""
     x = np.asarray(x, dtype=np.float32)
     amax = np.float32(np.max(np.abs(x))) if x.size else np.float32(0)
     if amax == 0:
         return np.float32(1.0)
-    return np.float32(np.float32(E4M3_MAX) / amax)
+    with np.errstate(over="ignore"):
+        s = np.float32(np.float32(E4M3_MAX) / amax)
+    return min(s, FP8_SCALE_MAX)
+
+
+def fp8_scales_pair(A, B):
+    """Per-tensor scales of the two operands of one FP8 product: each
+    ``min(448 / amax, 2^126)`` (``fp8_scale``); then, because the
+    dequantisation 1 / (s_a s_b) is one float32 factor and must stay normal,
+    when ilogb(s_a) + ilogb(s_b) exceeds 124 that excess d is taken off the
+    exponents, ceil(d / 2) from s_a and floor(d / 2) from s_b (exact)."""
+    sa, sb = fp8_scale(A), fp8_scale(B)
+    ea = int(np.frexp(sa)[1]) - 1          # ilogb
+    eb = int(np.frexp(sb)[1]) - 1
+    d = ea + eb - 124
+    if d > 0:
+        sa = np.float32(np.ldexp(sa, -((d + 1) // 2)))
+        sb = np.float32(np.ldexp(sb, -(d // 2)))
+    return sa, sb
+
+
+def fp8_quantize_pair(A, B):
+    """Both operands of one FP8 product quantised with ``fp8_scales_pair``:
+    returns (codes_a, s_a, codes_b, s_b)."""
+    A = np.asarray(A, dtype=np.float32)
+    B = np.asarray(B, dtype=np.float32)
+    sa, sb = fp8_scales_pair(A, B)
+    return (e4m3_codes((A * sa).astype(np.float32)), sa,
+            e4m3_codes((B * sb).astype(np.float32)), sb)
 
 
 def fp8_quantize(x):

@@ -437,8 +437,9 @@ __global__ void amax2_kernel(const float* __restrict__ X, int64_t xr, int64_t xc
 }
 
 // The per-block maxima of amax2_kernel (nblocks pairs) reduced to the two
-// amaxes, then {s_x, 1/s_x, s_y, 1/s_y} with s = 448 / amax (1 when amax is
-// 0).  One block of 256 threads; launched programmatically.
+// amaxes, then {s_x, 1/s_x, s_y, 1/s_y} with s = min(448 / amax, 2^126) (1
+// when amax is 0), jointly reduced by powers of two so that 1 / (s_x s_y)
+// stays a normal float32.  One block of 256 threads; launched programmatically.
 __global__ void fp8_scales_kernel(const float* __restrict__ block_max, int nblocks,
                                   float* __restrict__ out) {
   dev::griddep_wait();
@@ -460,13 +461,28 @@ __global__ void fp8_scales_kernel(const float* __restrict__ block_max, int nbloc
     wy[warp] = my;
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
-    float amax = 0.f;
-    for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w)
-      amax = fmaxf(amax, threadIdx.x == 0 ? wx[w] : wy[w]);
-    const float sc = (amax > 0.f) ? __fdiv_rn(448.0f, amax) : 1.0f;
-    out[2 * threadIdx.x] = sc;
-    out[2 * threadIdx.x + 1] = __fdiv_rn(1.0f, sc);
+  if (threadIdx.x == 0) {
+    float ax = 0.f, ay = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) {
+      ax = fmaxf(ax, wx[w]);
+      ay = fmaxf(ay, wy[w]);
+    }
+    // Each scale is capped at 2^126 (448 / amax overflows float32 for amax <
+    // 448 / FLT_MAX).  The dequantisation 1 / (s_x s_y) multiplies into
+    // alpha, so it must stay a normal float32: when the scales' exponents
+    // add up past 124, that many powers of two come off them, split evenly
+    // (exact, so the product stays below 2^126).
+    float sx = fminf(ax > 0.f ? __fdiv_rn(448.0f, ax) : 1.0f, 0x1p126f);
+    float sy = fminf(ay > 0.f ? __fdiv_rn(448.0f, ay) : 1.0f, 0x1p126f);
+    const int d = ilogbf(sx) + ilogbf(sy) - 124;
+    if (d > 0) {
+      sx = ldexpf(sx, -((d + 1) / 2));
+      sy = ldexpf(sy, -(d / 2));
+    }
+    out[0] = sx;
+    out[1] = __fdiv_rn(1.0f, sx);
+    out[2] = sy;
+    out[3] = __fdiv_rn(1.0f, sy);
   }
 }
 

@@ -140,6 +140,29 @@ def test_fp8_on_f32_inputs(ctx, m, n, k):
     assert_elementwise(got, exact_inputs, absp, elem_bound(4, k))
 
 
+@pytest.mark.parametrize("ea,eb", [(-120, 0), (-64, -64), (-140, 0)])
+def test_fp8_on_tiny_f32_inputs(ctx, ea, eb):
+    """Float32 operands far below 1 (A times 2^ea, B times 2^eb; 2^-140 is
+    subnormal).  The per-tensor scales are capped at 2^126, where 448 / amax
+    would overflow, and jointly reduced by powers of two so that the
+    dequantisation 1 / (s_a s_b) stays a normal float32.  The result is finite,
+    matches the oracle on the codes it multiplies element by element, and
+    keeps FP8's usual accuracy while the operands are normal floats."""
+    from gpu_util import assert_elementwise, elem_bound
+    m, n, k = 96, 80, 256
+    A = (W.uniform(m, k, seed=41) * np.float32(2.0 ** ea)).astype(np.float32)
+    B = (W.uniform(k, n, seed=42) * np.float32(2.0 ** eb)).astype(np.float32)
+    got = _run(ctx, 4, A, B)
+    assert np.all(np.isfinite(got))
+    qa, sa, qb, sb = N.fp8_quantize_pair(A, B)
+    Aq, Bq = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)
+    d = float(sa) * float(sb)
+    assert_elementwise(got, oracle.gemm(Aq, Bq) / d, oracle.gemm(np.abs(Aq), np.abs(Bq)) / d,
+                       elem_bound(4, k))
+    if ea > -126:   # operands in the normal range keep FP8's usual accuracy
+        assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 0.1
+
+
 def test_split3_matches_its_three_products(ctx):
     m, n, k = 192, 320, 512
     A = W.uniform(m, k, seed=13); B = W.uniform(k, n, seed=14)

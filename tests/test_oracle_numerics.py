@@ -86,6 +86,44 @@ def test_fp8_quantize_scale_and_amax():
     assert zs == 1.0 and np.all(zc == 0)
 
 
+def test_fp8_scale_is_capped_for_tiny_tensors():
+    # amax = 2^-120: 448 / amax = 2^128.8 overflows float32; the cap gives
+    # s = 2^126, so x * s <= 64 and the largest code is exactly 64
+    x = W.uniform(16, 16, seed=10) * np.float32(2.0 ** -121)
+    x[2, 3] = np.float32(2.0 ** -120)
+    codes, s = N.fp8_quantize(x)
+    assert s == np.float32(2.0 ** 126)
+    assert N.e4m3_to_f64(codes)[2, 3] == 64.0
+    assert np.float32(1.0) / s == np.float32(2.0 ** -126)   # a normal float32
+    # a subnormal amax: still the cap, and every code finite
+    y = np.full((4, 4), np.float32(2.0 ** -130), np.float32)
+    cy, sy = N.fp8_quantize(y)
+    assert sy == np.float32(2.0 ** 126) and np.all(np.isfinite(N.e4m3_to_f64(cy)))
+    # below the cap the rule is unchanged: amax = 2^-117 gives 448 * 2^117 < 2^126
+    z = np.full((2, 2), np.float32(2.0 ** -117), np.float32)
+    assert N.fp8_scale(z) == np.float32(448.0 * 2.0 ** 117)
+
+
+def test_fp8_pair_scales():
+    a = W.uniform(16, 16, seed=11)
+    b = W.uniform(16, 16, seed=12)
+    # ordinary data: the pair rule changes nothing
+    assert N.fp8_scales_pair(a, b) == (N.fp8_scale(a), N.fp8_scale(b))
+    for ea, eb in [(-120, 0), (-64, -64), (-140, -10), (0, -126)]:
+        A, B = a * np.float32(2.0 ** ea), b * np.float32(2.0 ** eb)
+        sa, sb = N.fp8_scales_pair(A, B)
+        # the dequantisation of the product stays a normal float32
+        assert 1.0 / (float(sa) * float(sb)) >= 2.0 ** -126
+        # each scale is its own scale divided by a power of two, split evenly
+        ra = float(N.fp8_scale(A)) / float(sa)
+        rb = float(N.fp8_scale(B)) / float(sb)
+        assert ra == 2.0 ** round(np.log2(ra)) and rb == 2.0 ** round(np.log2(rb))
+        assert 0 <= np.log2(ra) - np.log2(rb) <= 1
+    # the worked case: A at 2^-120 (scale capped at 2^126), B ordinary
+    sa, sb = N.fp8_scales_pair(a * np.float32(2.0 ** -120), b)
+    assert sa == np.float32(2.0 ** 121) and sb == np.float32(N.fp8_scale(b) / 32)
+
+
 def test_fp8_quantize_exact_multiples_round_trip():
     codes = W.fp8_input(16, 16, seed=9)
     vals = N.e4m3_to_f64(codes)
