@@ -118,12 +118,13 @@ FP8_SCALE_MAX = np.float32(2.0 ** 126)
 
 
 def fp8_scale(x):
-    """Per-tensor scale ``s = min(448 / amax(|x|), 2^126)`` in float32 (1 when
-    amax = 0).  The cap: 448 / amax overflows float32 for amax < 448 / FLT_MAX,
+    """Per-tensor scale ``s = min(448 / amax(|x|), 2^126)`` in float32 over the
+    finite values of x (1 when amax = 0).  The cap: 448 / amax overflows float32 for amax < 448 / FLT_MAX,
     and the dequantisation factor 1 / s must stay a normal float32 (2^-126 is
     the smallest)."""
     x = np.asarray(x, dtype=np.float32)
-    amax = np.float32(np.max(np.abs(x))) if x.size else np.float32(0)
+    fin = x[np.isfinite(x)]           # non-finite values take no part in amax
+    amax = np.float32(np.max(np.abs(fin))) if fin.size else np.float32(0)
     if amax == 0:
         return np.float32(1.0)
     with np.errstate(over="ignore"):
@@ -147,25 +148,35 @@ def fp8_scales_pair(A, B):
     return sa, sb
 
 
+def _quantised_codes(x, s):
+    """E4M3 codes of x * s (rounded to float32 first); a non-finite x gives
+    the NaN code 0x7F, so infinities stay non-finite instead of saturating."""
+    fin = np.isfinite(x)
+    codes = e4m3_codes(np.where(fin, x * s, 0).astype(np.float32))
+    return np.where(fin, codes, np.uint8(0x7F)).astype(np.uint8)
+
+
 def fp8_quantize_pair(A, B):
     """Both operands of one FP8 product quantised with ``fp8_scales_pair``:
     returns (codes_a, s_a, codes_b, s_b)."""
     A = np.asarray(A, dtype=np.float32)
     B = np.asarray(B, dtype=np.float32)
     sa, sb = fp8_scales_pair(A, B)
-    return (e4m3_codes((A * sa).astype(np.float32)), sa,
-            e4m3_codes((B * sb).astype(np.float32)), sb)
+    with np.errstate(invalid="ignore", over="ignore"):
+        return _quantised_codes(A, sa), sa, _quantised_codes(B, sb), sb
 
 
 def fp8_quantize(x):
     """Per-tensor quantisation: returns (codes, s) with codes = e4m3(x * s).
 
     The product x*s is rounded to float32 first (that is the value converted).
-    The real tensor is approximated by ``e4m3_to_f64(codes) / s``.
+    The real tensor is approximated by ``e4m3_to_f64(codes) / s``.  Non-finite
+    values take no part in the scale and give the NaN code 0x7F.
     """
     x = np.asarray(x, dtype=np.float32)
     s = fp8_scale(x)
-    return e4m3_codes((x * s).astype(np.float32)), s
+    with np.errstate(invalid="ignore", over="ignore"):
+        return _quantised_codes(x, s), s
 
 
 # ---------------------------------------------------------------- TF32

@@ -27,6 +27,19 @@
 namespace compar {
 namespace {
 
+// One float32 value of a per-tensor FP8 quantisation: x * s rounded, then
+// converted to E4M3 (round to nearest, saturating).  A non-finite x gives the
+// E4M3 NaN code 0x7F, so an infinity stays non-finite (saturation would make
+// it +-448) and stays local: the scale is taken over finite values only.
+__device__ __forceinline__ __nv_fp8_storage_t e4m3_of(float x, float s) {
+  return isfinite(x) ? __nv_cvt_float_to_fp8(__fmul_rn(x, s), __NV_SATFINITE, __NV_E4M3)
+                     : static_cast<__nv_fp8_storage_t>(0x7F);
+}
+
+// |x| for the amax of a quantisation: non-finite values do not count.
+__device__ __forceinline__ float finite_abs(float x) { return isfinite(x) ? fabsf(x) : 0.f; }
+
+
 // Three-piece split; both residuals are exact in float32.
 __device__ __forceinline__ void split3p(float x, __nv_bfloat16& h, __nv_bfloat16& m,
                                         __nv_bfloat16& l) {
@@ -86,12 +99,9 @@ __device__ __forceinline__ void store_converted(const F32Out& o, float x, void* 
       static_cast<float*>(Ylo)[idx] = tf32_rna(x - h);
       break;
     }
-    case PP_E4M3: {
-      const float v = __fmul_rn(x, o.s);
-      static_cast<__nv_fp8_storage_t*>(Y)[idx] =
-          __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    case PP_E4M3:
+      static_cast<__nv_fp8_storage_t*>(Y)[idx] = e4m3_of(x, o.s);
       break;
-    }
     default:
       break;
   }
@@ -190,9 +200,7 @@ __device__ __forceinline__ void store8(int kind, float s, const float (&x)[8], v
     uint32_t w[2] = {0u, 0u};
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      w[q / 4] |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(__fmul_rn(x[q], s), __NV_SATFINITE,
-                                                              __NV_E4M3))
-                  << (8 * (q % 4));
+      w[q / 4] |= static_cast<uint32_t>(e4m3_of(x[q], s)) << (8 * (q % 4));
     *reinterpret_cast<uint2*>(static_cast<uint8_t*>(Y) + idx) = make_uint2(w[0], w[1]);
   }
 }
@@ -337,8 +345,8 @@ __global__ void convert_transpose64_kernel(const float* __restrict__ X, int64_t 
         *reinterpret_cast<__nv_bfloat162*>(piece2(Y, Ylo) + idx) = __halves2bfloat162(l0, l1);
       } else {
         uint8_t* y = static_cast<uint8_t*>(Y) + idx;
-        y[0] = __nv_cvt_float_to_fp8(__fmul_rn(x0, s), __NV_SATFINITE, __NV_E4M3);
-        y[1] = __nv_cvt_float_to_fp8(__fmul_rn(x1, s), __NV_SATFINITE, __NV_E4M3);
+        y[0] = e4m3_of(x0, s);
+        y[1] = e4m3_of(x1, s);
       }
     } else {
       store_converted(F32Out{kind, s}, x0, Y, Ylo, idx);
@@ -385,11 +393,12 @@ __device__ __forceinline__ float row_amax(const float* __restrict__ row, int64_t
     const int64_t n4 = cols / 4;
     for (int64_t i = lane; i < n4; i += 32) {
       const float4 v = __ldg(r4 + i);
-      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      m = fmaxf(m, fmaxf(fmaxf(finite_abs(v.x), finite_abs(v.y)),
+                         fmaxf(finite_abs(v.z), finite_abs(v.w))));
     }
     c = n4 * 4;
   }
-  for (int64_t i = c + lane; i < cols; i += 32) m = fmaxf(m, fabsf(__ldg(row + i)));
+  for (int64_t i = c + lane; i < cols; i += 32) m = fmaxf(m, finite_abs(__ldg(row + i)));
   return m;
 }
 

@@ -163,6 +163,39 @@ def test_fp8_on_tiny_f32_inputs(ctx, ea, eb):
         assert N.rel_frobenius(got, oracle.gemm(A, B)) <= 0.1
 
 
+def test_non_finite_operands_stay_local(ctx):
+    """An infinity and a NaN in A reach only their rows of C, in every
+    variant.  The split variants give NaN there (inf - inf), and FP8
+    encodes both as its NaN code after taking the scale over finite values.
+    The other rows match the oracle: FP8's on the codes it multiplies."""
+    import paper_2311_03543_b300 as cp
+    from gpu_util import assert_elementwise, elem_bound
+    m, n, k = 96, 80, 128
+    A = W.uniform(m, k, seed=43); B = W.uniform(k, n, seed=44)
+    A[5, 7], A[9, 2] = np.inf, np.nan
+    ok_rows = np.setdiff1d(np.arange(m), [5, 9])
+    Af = A.copy(); Af[5, 7] = Af[9, 2] = 0.0
+    ref = oracle.gemm(Af, B)
+    absp = oracle.gemm(np.abs(Af), np.abs(B))
+    for v in (0, 1, 2, 3, 4, 5, 7, 8, 9):
+        got = _run(ctx, v, A, B)
+        assert not np.isfinite(got[[5, 9]]).any(), v
+        assert np.isfinite(got[ok_rows]).all(), v
+        if v == 4:
+            qa, sa, qb, sb = N.fp8_quantize_pair(A, B)
+            Aq, Bq = N.e4m3_to_f64(qa), N.e4m3_to_f64(qb)
+            d = float(sa) * float(sb)
+            assert_elementwise(got[ok_rows], (oracle.gemm_rows(Aq, Bq, ok_rows)) / d,
+                               oracle.gemm_rows(np.abs(Aq), np.abs(Bq), ok_rows) / d,
+                               elem_bound(4, k))
+        elif v == 3:
+            Ar, Br = N.bf16_round(Af), N.bf16_round(B)
+            assert_elementwise(got[ok_rows], oracle.gemm(Ar, Br)[ok_rows],
+                               oracle.gemm(np.abs(Ar), np.abs(Br))[ok_rows], elem_bound(3, k))
+        else:
+            assert_elementwise(got[ok_rows], ref[ok_rows], absp[ok_rows], elem_bound(v, k))
+
+
 def test_split3_matches_its_three_products(ctx):
     m, n, k = 192, 320, 512
     A = W.uniform(m, k, seed=13); B = W.uniform(k, n, seed=14)

@@ -124,6 +124,19 @@ def test_fp8_pair_scales():
     assert sa == np.float32(2.0 ** 121) and sb == np.float32(N.fp8_scale(b) / 32)
 
 
+def test_fp8_quantize_non_finite_values():
+    x = W.uniform(8, 8, seed=13)
+    x[1, 1] = -4.0                       # the largest finite magnitude
+    y = x.copy()
+    y[2, 5], y[6, 0], y[7, 7] = np.inf, -np.inf, np.nan
+    cx, sx = N.fp8_quantize(x)
+    cy, sy = N.fp8_quantize(y)
+    assert sy == sx == np.float32(112.0)  # non-finite values leave amax alone
+    bad = ~np.isfinite(y)
+    assert np.all(cy[bad] == 0x7F) and np.all(np.isnan(N.e4m3_to_f64(cy[bad])))
+    assert np.array_equal(cy[~bad], cx[~bad])
+
+
 def test_fp8_quantize_exact_multiples_round_trip():
     codes = W.fp8_input(16, 16, seed=9)
     vals = N.e4m3_to_f64(codes)
