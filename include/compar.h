@@ -40,7 +40,8 @@
  * or order the streams yourself (events); calls that overlap on the GPU give
  * undefined results for those calls.
  *
- * beta == 0 means C is not read (BLAS convention).
+ * beta == 0 means C is not read, and alpha == 0 that A and B are not read
+ * (C = beta * C), as in BLAS.
  */
 #ifndef COMPAR_H_
 #define COMPAR_H_

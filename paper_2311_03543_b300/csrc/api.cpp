@@ -518,7 +518,7 @@ static void maybe_retrain(compar_ctx* ctx, cudaStream_t s) {
 
 int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
   if (c.m == 0 || c.n == 0) return COMPAR_OK;
-  if (c.k == 0) {
+  if (c.k == 0 || c.alpha == 0.f) {  // A and B are not read (BLAS convention)
     ctx->last_variant = -1;
     return launch_scale_c(c.C, c.m, c.n, c.ldc, c.beta, s);
   }

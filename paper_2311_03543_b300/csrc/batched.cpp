@@ -126,8 +126,9 @@ int mode_variant(int mode) {
 // A problem joins the grouped launch only if its mode meets the tolerance;
 // the others (e.g. below 3xBF16's error level) are selected one by one.
 bool grouped_eligible(const compar_ctx* ctx, const compar_problem_t& p, double tol) {
+  // (alpha == 0 problems run singly: C = beta * C without reading A and B)
   if (!((p.dtype == COMPAR_F32 || p.dtype == COMPAR_BF16) && p.m > 0 && p.n > 0 && p.k > 0 &&
-        p.m <= INT32_MAX && p.n <= INT32_MAX && p.k <= INT32_MAX))
+        p.alpha != 0.f && p.m <= INT32_MAX && p.n <= INT32_MAX && p.k <= INT32_MAX))
     return false;
   const int v = mode_variant(grouped_mode(p, tol));
   return ctx->err.predict(v, p.dtype, p.k) * ctx->err.margin <= tol;

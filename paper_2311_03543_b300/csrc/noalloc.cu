@@ -96,7 +96,8 @@ extern "C" int compar_gemm_simt_noalloc(int64_t m, int64_t n, int64_t k, float a
   if (rc != COMPAR_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (m == 0 || n == 0) return COMPAR_OK;
-  if (k == 0) return compar::launch_scale_c(C, m, n, n, beta, s);
+  // A and B are not read when k == 0 or alpha == 0 (BLAS convention)
+  if (k == 0 || alpha == 0.f) return compar::launch_scale_c(C, m, n, n, beta, s);
   compar::GemmCall c;
   c.m = m;
   c.n = n;

@@ -429,6 +429,30 @@ def test_stream_k_plain_variants(ctx, v, tol, m, n, k, pairs):
     assert_elementwise(got[rows], ref, scale, fmt + elem_bound(v, k))
 
 
+@pytest.mark.parametrize("beta", [0.0, 0.5])
+def test_alpha_zero_reads_neither_a_nor_b(ctx, beta):
+    """alpha == 0: C = beta * C and A and B are not read (BLAS convention), so
+    NaNs and infinities in them do not reach C; also with a variant forced
+    and through the batched call."""
+    import torch
+    import paper_2311_03543_b300 as cp
+    m, n, k = 70, 90, 110
+    A = W.uniform(m, k, seed=45); B = W.uniform(k, n, seed=46)
+    A[3, 4], B[7, 8] = np.nan, np.inf
+    C0 = W.uniform(m, n, seed=47)
+    want = np.float32(beta) * C0 if beta != 0.0 else np.zeros_like(C0)
+    for v in (None, 1, 5):
+        got = _run(ctx, v, A, B, alpha=0.0, beta=beta,
+                   C0=C0 if beta != 0.0 else np.full_like(C0, np.nan))
+        assert np.array_equal(got, want), v
+    from gpu_util import dev, host
+    dA, dB, dC = dev(A), dev(B), dev(C0 if beta != 0.0 else np.full_like(C0, np.nan))
+    probs = [dict(m=m, n=n, k=k, lda=k, ldb=n, ldc=n, dtype=cp.F32, A=dA.data_ptr(),
+                  B=dB.data_ptr(), C=dC.data_ptr(), alpha=0.0, beta=beta)]
+    ctx.gemm_batched(probs, tol=1e-5)
+    assert np.array_equal(host(dC), want)
+
+
 def test_k_zero_scales_c(ctx):
     from gpu_util import dev, host
     import torch
