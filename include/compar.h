@@ -143,7 +143,8 @@ const char* compar_last_error(void);
  *               |alpha| |A||B| + |beta| |C|, so a short dot product that
  *               cancels may exceed tol relatively.
  *   A, B      : device pointers, row-major contiguous (lda = k, ldb = n).
- *   C         : device float32, row-major contiguous (ldc = n).
+ *   C         : device float32, row-major contiguous (ldc = n); C must not
+ *               overlap A or B (COMPAR_ERR_INVALID).
  *   stream    : cudaStream_t.
  * Variant choice: compar_force_variant > decision cache > learned MLP cost
  * model (when confident) > history-table model.  Returns COMPAR_OK,
@@ -201,7 +202,10 @@ typedef struct {
  * launch captured in a CUDA graph (cached per batch signature) and one launch
  * per problem.  Returns as compar_gemm.  The call runs a graph of its own and
  * waits on its staging buffers, so it cannot itself be captured: on a stream
- * being captured it returns COMPAR_ERR_UNSUPPORTED and enqueues nothing. */
+ * being captured it returns COMPAR_ERR_UNSUPPORTED and enqueues nothing.
+ * The problems run concurrently: a problem's C may not share an element
+ * with any problem's A, B or C (not checked; disjoint column blocks of one
+ * matrix are fine). */
 int compar_gemm_batched(compar_ctx_t ctx, int count,
                         const compar_problem_t* probs, double tol,
                         void* stream);

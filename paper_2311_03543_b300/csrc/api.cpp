@@ -551,12 +551,27 @@ int gemm_call(compar_ctx* ctx, GemmCall& c, cudaStream_t s) {
 
 static bool valid_dtype(int d) { return d == COMPAR_F32 || d == COMPAR_BF16 || d == COMPAR_F8E4M3; }
 
+static int dtype_bytes_of(compar_dtype_t d) { return d == COMPAR_F32 ? 4 : (d == COMPAR_BF16 ? 2 : 1); }
+
+// Contiguous operands of a call: C must not share a byte with A or B (a
+// kernel would read what another writes).
 static int check_ptrs(int64_t m, int64_t n, int64_t k, const void* A, const void* B,
-                      const void* C) {
+                      const void* C, compar_dtype_t dtype) {
   if (m < 0 || n < 0 || k < 0) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && C == nullptr) return COMPAR_ERR_INVALID;
   if (m > 0 && n > 0 && k > 0 && (A == nullptr || B == nullptr)) return COMPAR_ERR_INVALID;
   if (C && (reinterpret_cast<uintptr_t>(C) % 4)) return COMPAR_ERR_INVALID;
+  if (m > 0 && n > 0 && k > 0) {
+    const uintptr_t c0 = reinterpret_cast<uintptr_t>(C);
+    const uintptr_t c1 = c0 + static_cast<uintptr_t>(m) * n * 4;
+    const uintptr_t e = static_cast<uintptr_t>(dtype_bytes_of(dtype));
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(A), a1 = a0 + static_cast<uintptr_t>(m) * k * e;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(B), b1 = b0 + static_cast<uintptr_t>(k) * n * e;
+    if ((c0 < a1 && a0 < c1) || (c0 < b1 && b0 < c1)) {
+      g_last_error = "C overlaps A or B";
+      return COMPAR_ERR_INVALID;
+    }
+  }
   return COMPAR_OK;
 }
 
@@ -661,7 +676,7 @@ int compar_gemm(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_dtype_
   DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
-  int rc = check_ptrs(m, n, k, A, B, C);
+  int rc = check_ptrs(m, n, k, A, B, C, dtype);
   if (rc != COMPAR_OK) return rc;
   GemmCall c;
   c.m = m;
@@ -687,7 +702,7 @@ int compar_gemm_host(compar_ctx_t ctx, int64_t m, int64_t n, int64_t k, compar_d
   DeviceScope device_scope(ctx ? ctx->device : -1);
   if (!ctx || !valid_dtype(dtype) || std::isnan(tol)) return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
-  int rc = check_ptrs(m, n, k, A, B, C);
+  int rc = check_ptrs(m, n, k, A, B, C, dtype);
   if (rc != COMPAR_OK) return rc;
   // its copy streams and events are its own: not a capturable call
   rc = refuse_capture(static_cast<cudaStream_t>(stream), "compar_gemm_host");
@@ -829,7 +844,7 @@ int compar_measure(compar_ctx_t ctx, int v, int64_t m, int64_t n, int64_t k,
       warmup < 0)
     return COMPAR_ERR_INVALID;
   if (ctx->host_only) return COMPAR_ERR_UNSUPPORTED;
-  int rc = check_ptrs(m, n, k, A, B, C);
+  int rc = check_ptrs(m, n, k, A, B, C, dtype);
   if (rc != COMPAR_OK) return rc;
   if (m == 0 || n == 0 || k == 0) return COMPAR_ERR_INVALID;
   rc = refuse_capture(static_cast<cudaStream_t>(stream), "compar_measure");  // it synchronises

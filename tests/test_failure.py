@@ -183,4 +183,7 @@ def test_bad_arguments_are_refused():
         assert cp.compar_gemm(h, 4, 4, 4, cp.F32, float("nan"), 16, 16, 16, None) == cp.ERR_INVALID
         assert cp.compar_set_fp8_scales(h, 0.0, 1.0) == cp.ERR_INVALID
         assert cp.compar_set_scalars(h, float("inf"), 0.0) == cp.ERR_INVALID
-        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 1e-30, 16, 16, 16, None) == cp.ERR_NO_VARIANT
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 1e-30, 16, 4096, 8192, None) == cp.ERR_NO_VARIANT
+        # C sharing bytes with A or B (a 4 x 4 float32 operand spans 64 bytes)
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 0.0, 4096, 8192, 4096 + 48, None) == cp.ERR_INVALID
+        assert cp.compar_gemm(h, 4, 4, 4, cp.F32, 0.0, 4096, 8192, 8192 - 48, None) == cp.ERR_INVALID
